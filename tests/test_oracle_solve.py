@@ -1,0 +1,226 @@
+"""Pins of the oracle's solves and time stepping (Alg. 1, Alg. 2, Sec. 2.7, App. A).
+
+  * static condensation equals the uncondensed direct solve (brute force, tiny meshes);
+  * Alg. 2 converges to the monolithic stage solution, and drives the constraint residual
+    (the discrete divergence) down;
+  * step II alone is the HDG mixed Poisson discretisation: optimal convergence on a smooth
+    manufactured solution;
+  * the steady Taylor-Green vortex is preserved to discretisation error, which falls with h;
+  * the IMEX tableaus satisfy their order conditions and the stepper shows the temporal order;
+  * the Taylor-Green pressure used by the tests solves grad p = -(Q.grad)Q.
+"""
+import numpy as np
+import pytest
+
+from oracle import Mesh, HDG, Oracle, bdm_project, TABLEAUS
+from oracle.element import lattice, triangle_quadrature
+import hdg_workloads as W
+
+
+def interp(hdg, fun):
+    m = hdg.mesh
+    X = m.cell_points(np.arange(m.ncells), lattice(hdg.k + 1))
+    return np.stack(fun(X[..., 0], X[..., 1]), 1).reshape(-1)
+
+
+def l2_error_Q(hdg, Q, fun):
+    m = hdg.mesh
+    qp, qw = triangle_quadrature(10)
+    X = m.cell_points(np.arange(m.ncells), qp)
+    ex = np.stack(fun(X[..., 0], X[..., 1]), -1)
+    num = np.einsum('qa,cda->cqd', hdg.Vu.values(qp), Q.reshape(m.ncells, 2, hdg.mu))
+    return np.sqrt(np.sum(qw[None, :, None] * m.detJ[:, None, None] * (num - ex) ** 2))
+
+
+def l2_error_p(hdg, p, fun):
+    m = hdg.mesh
+    qp, qw = triangle_quadrature(10)
+    X = m.cell_points(np.arange(m.ncells), qp)
+    ex = fun(X[..., 0], X[..., 1])
+    num = np.einsum('qb,cb->cq', hdg.Vp.values(qp), p.reshape(m.ncells, hdg.npn))
+    return np.sqrt(np.sum(qw[None, :] * m.detJ[:, None] * (num - ex) ** 2))
+
+
+@pytest.mark.parametrize('n', [1, 2, 4])
+@pytest.mark.parametrize('per', [(False, False), (True, False), (True, True)])
+def test_condensed_equals_monolithic(n, per):
+    for k in (1, 2, 3, 4):
+        if n == 4 and k > 2:
+            continue
+        h = HDG(Mesh(n, periodic_x=per[0], periodic_y=per[1]), k)
+        o = Oracle(h)
+        rng = np.random.default_rng(10 * n + k)
+        Ru = rng.standard_normal(h.nQ)
+        Ry = -o.B @ rng.standard_normal(h.nQ)          # a compatible constraint right-hand side
+        for c in (1e-3, 0.7):
+            Q1, p1, l1 = o.mixed_solve(c, Ru, Ry)
+            Q2, p2, l2, _ = o.condensed_mixed_solve(c, Ru, Ry)
+            for a, b in ((Q1, Q2), (p1, p2), (l1, l2)):
+                assert np.abs(a - b).max() <= 1e-11 * np.abs(a).max()
+            # the direct solve satisfies every equation, including the dropped one
+            A, x = o.mixed_matrix(c), np.concatenate([Q1, p1, l1])
+            res = A @ x - np.concatenate([Ru, Ry])
+            assert np.abs(res).max() < 1e-13 * (abs(A) @ np.abs(x)).max()
+            assert abs(h.mean_p(p1)) < 1e-14 * np.abs(p1).max()
+
+
+def test_richardson_converges_to_monolithic_stage_solution():
+    h = HDG(Mesh(4, periodic_x=True), 2)
+    o = Oracle(h)
+    rng = np.random.default_rng(0)
+    Q = interp(h, W.taylor_green) + 1e-2 * rng.standard_normal(h.nQ)
+    Q, p, l = o.div_free_project(Q)
+    Qs = bdm_project(h, Q)
+    c = 0.0025
+    r = o.M @ Q
+    Qd, pd, ld = o.stage_solve(c, r, Qs)
+    hist = []
+    Qr, pr, lr, it = o.richardson(c, r, Qs, Q, p, l, tol=1e-13, max_iter=60, history=hist)
+    assert it < 60
+    assert np.abs(Qr - Qd).max() < 1e-11 * np.abs(Qd).max()
+    assert np.abs(pr - pd).max() < 1e-9 * np.abs(pd).max()
+    # updates shrink geometrically
+    d = np.array([x['dQ'] for x in hist])
+    assert np.all(d[1:] < d[:-1])
+    # the monolithic solution satisfies the constraint; a single Chorin step already does
+    assert np.linalg.norm(o.constraint(Qd, pd, ld)) < 1e-12
+    assert hist[0]['gamma'] < 1e-12
+
+
+def test_richardson_reduces_discrete_divergence_from_inconsistent_start():
+    # starting from a state that violates stage i's constraint, the Gamma-residual is driven down
+    h = HDG(Mesh(4), 2)
+    o = Oracle(h)
+    rng = np.random.default_rng(3)
+    Q = rng.standard_normal(h.nQ)
+    p = rng.standard_normal(h.nP); l = rng.standard_normal(h.nL)
+    Qs = bdm_project(h, interp(h, W.taylor_green))
+    g0 = np.linalg.norm(o.constraint(Q, p, l))
+    hist = []
+    o.richardson(0.002, o.M @ Q, Qs, Q, p, l, n_iter=4, history=hist)
+    assert g0 > 1.0 and all(x['gamma'] < 1e-10 * g0 for x in hist)
+
+
+@pytest.mark.parametrize('k', [1, 2])
+def test_mixed_poisson_convergence(k):
+    # U + grad p = 0, div U = f, n.U = 0: p = cos(pi x) cos(pi y), f = 2 pi^2 p
+    pex = lambda x, y: np.cos(np.pi * x) * np.cos(np.pi * y)
+    Uex = lambda x, y: (np.pi * np.sin(np.pi * x) * np.cos(np.pi * y),
+                        np.pi * np.cos(np.pi * x) * np.sin(np.pi * y))
+    errs = []
+    for n in (4, 8):
+        m = Mesh(n)
+        h = HDG(m, k)
+        o = Oracle(h)
+        qp, qw = triangle_quadrature(8)
+        X = m.cell_points(np.arange(m.ncells), qp)
+        fq = 2 * np.pi ** 2 * pex(X[..., 0], X[..., 1])
+        Rp = np.einsum('q,cq,qb->cb', qw, fq, h.Vp.values(qp)) * m.detJ[:, None]
+        Ry = np.concatenate([Rp.ravel(), np.zeros(h.nL)])
+        U, p, l = o.mixed_solve(1.0, np.zeros(h.nQ), Ry)
+        errs.append((l2_error_p(h, p, pex), l2_error_Q(h, U, Uex)))
+    rate_p = np.log2(errs[0][0] / errs[1][0])
+    rate_U = np.log2(errs[0][1] / errs[1][1])
+    # p in P_k converges at k+1; U ~ -grad p is limited by the pressure degree: rate k
+    assert rate_p > k + 0.8 and rate_U > k - 0.2, (rate_p, rate_U)
+
+
+def test_taylor_green_steady_preserved():
+    tab = TABLEAUS['ARS222']()
+    errs = []
+    for n in (4, 8):
+        h = HDG(Mesh(n), 2)
+        o = Oracle(h)
+        Q = interp(h, W.taylor_green)
+        _, p, l = o.reconstruct_pressure(Q)
+        for s in range(5):
+            Q, p, l = o.imex_step(tab, 0.01, 0.01 * s, Q, p, l)
+        errs.append((l2_error_Q(h, Q, W.taylor_green), l2_error_p(h, p, W.taylor_green_pressure)))
+    assert errs[0][0] < 5e-3 and errs[1][0] < errs[0][0] / 4
+    assert errs[1][1] < errs[0][1] / 2
+
+
+def test_taylor_green_pressure_formula():
+    sympy = pytest.importorskip('sympy')
+    x, y = sympy.symbols('x y')
+    u = sympy.sin(sympy.pi * x) * sympy.cos(sympy.pi * y)
+    v = -sympy.cos(sympy.pi * x) * sympy.sin(sympy.pi * y)
+    p = (sympy.cos(2 * sympy.pi * x) + sympy.cos(2 * sympy.pi * y)) / 4
+    assert sympy.simplify(sympy.diff(u, x) + sympy.diff(v, y)) == 0
+    assert sympy.simplify(u * sympy.diff(u, x) + v * sympy.diff(u, y) + sympy.diff(p, x)) == 0
+    assert sympy.simplify(u * sympy.diff(v, x) + v * sympy.diff(v, y) + sympy.diff(p, y)) == 0
+    assert sympy.integrate(sympy.integrate(p, (x, 0, 1)), (y, 0, 1)) == 0
+    # the printed pressure of eq. exact_solution (4/pi^2 - sin(pi x) sin(pi y)) is not a solution
+    q = 4 / sympy.pi ** 2 - sympy.sin(sympy.pi * x) * sympy.sin(sympy.pi * y)
+    assert sympy.simplify(u * sympy.diff(u, x) + v * sympy.diff(u, y) + sympy.diff(q, x)) != 0
+    # the paper's Q0 is the same field as taylor_green on the unit square
+    Q0 = (-sympy.cos((2 * x - 1) * sympy.pi / 2) * sympy.sin((2 * y - 1) * sympy.pi / 2),
+          sympy.sin((2 * x - 1) * sympy.pi / 2) * sympy.cos((2 * y - 1) * sympy.pi / 2))
+    assert sympy.simplify(Q0[0] - u) == 0 and sympy.simplify(Q0[1] - v) == 0
+
+
+def _order_conditions(tab):
+    Ai, Ae, bi, be, c = tab.A_im, tab.A_ex, tab.b_im, tab.b_ex, tab.c
+    out = {}
+    for nm, b, A in (('ii', bi, Ai), ('ee', be, Ae), ('ie', bi, Ae), ('ei', be, Ai)):
+        out['b1' + nm[0]] = b.sum() - 1
+        out['bc' + nm[0]] = b @ c - 0.5
+        out['bc2' + nm[0]] = b @ c ** 2 - 1 / 3
+        out['bAc' + nm] = b @ A @ c - 1 / 6
+    out['rows_i'] = np.abs(Ai.sum(1) - c).max()
+    out['rows_e'] = np.abs(Ae.sum(1) - c).max()
+    return out
+
+
+def test_ars_order_conditions():
+    oc = _order_conditions(TABLEAUS['ARS222']())
+    for key in ('b1i', 'b1e', 'bci', 'bce', 'rows_i', 'rows_e'):
+        assert abs(oc[key]) < 1e-14, key
+    t3 = TABLEAUS['ARS343']()
+    assert abs(6 * t3.c[1] ** 3 - 18 * t3.c[1] ** 2 + 9 * t3.c[1] - 1) < 1e-14
+    assert abs(t3.c[1] - 0.4358665215) < 1e-10
+    oc = _order_conditions(t3)
+    for key, v in oc.items():
+        # the explicit coefficients are published to ten digits
+        assert abs(v) < 2e-9, (key, v)
+    for t in (TABLEAUS['ARS222'](), t3, TABLEAUS['IMEX_EULER']()):
+        assert t.fits_alg1
+    # the paper's SSP tableaus (App. A) are consistent (row sums, order 2 / 3) once the swapped
+    # c column of SSP2(3,3,2) is read as (0, 1/2, 1), but do not have a zero first implicit column
+    for nm, order in (('SSP2_332', 2), ('SSP3_433', 3)):
+        t = TABLEAUS[nm]()
+        oc = _order_conditions(t)
+        assert oc['rows_e'] < 1e-12   # (the implicit rows sum to their own abscissae)
+        keys = ['b1i', 'b1e', 'bci', 'bce'] + (['bc2i', 'bc2e', 'bAcii', 'bAcee', 'bAcie', 'bAcei'] if order == 3 else [])
+        for key in keys:
+            assert abs(oc[key]) < 1e-10, (nm, key)
+        assert not t.fits_alg1
+
+
+@pytest.mark.parametrize('name,order', [('ARS222', 2), ('ARS343', 3)])
+def test_temporal_order_of_the_imex_recursion(name, order):
+    # The advecting velocity of stage i is P(Q_{i-1}) (Alg. 1), lagged by one stage; with an
+    # O(1) flow that lag limits the scheme to first order unless its error is a gradient (as
+    # for the Taylor-Green vortex). A small-amplitude forced flow (|Q| ~ 1e-6) makes the lagged
+    # quadratic term negligible, leaving the linear stiff part (penalty, pressure, constraint)
+    # implicit and the forcing explicit: the stage recursion, final update and tableau must then
+    # show the tableau's order (self-convergence in dt on a fixed mesh).
+    h = HDG(Mesh(2), 2)
+    o = Oracle(h)
+    F0 = 1e-6 * (o.M @ interp(h, W.taylor_green))
+    forcing = lambda t: np.cos(5.0 * t) * F0
+    tab = TABLEAUS[name]()
+
+    def run(nsteps, T=0.5):
+        Q, p, l = np.zeros(h.nQ), np.zeros(h.nP), np.zeros(h.nL)
+        dt = T / nsteps
+        for s in range(nsteps):
+            Q, p, l = o.imex_step(tab, dt, s * dt, Q, p, l, forcing=forcing)
+        return Q
+    ref = run(128)
+    e = []
+    for n in (2, 4, 8):
+        d = run(n) - ref
+        e.append(np.sqrt(d @ (o.M @ d)))
+    rates = np.log2(np.array(e[:-1]) / np.array(e[1:]))
+    assert np.all(rates > order - 0.2), rates
