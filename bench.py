@@ -1,0 +1,301 @@
+"""Benchmark: IMEX stage solves/s of the HDG incompressible-Euler stage solver on GB300.
+
+Workload (the plain-FP64 GPU configuration): periodic-in-x channel [0,1]^2 with walls at
+y = 0, 1, 64 x 64 rectangles -> 8192 triangles, k = 3 (velocity P4, pressure/trace P3),
+ARS(3,4,3), dt = 2e-3; every stage solved to a relative stage residual of 1e-10 (flexible GMRES
+preconditioned by Alg. 2's Chorin split; Step I GMRES to 1e-1, Step II trace CG to 1e-6 inside;
+the paper's fixed n_R = 2 is unstable on this flow); final update and pressure reconstruction
+trace CG rtol 1e-12; initial u = (tanh((y-1/2)/0.05), 1e-3 sin 2 pi x) + seeded N(0,1) 1e-4
+noise per nodal value, projected to divergence-free. One bench step = one IMEX time step of
+Alg. 1 (3 stage solves, final update, pressure reconstruction) through hdg_imex_step.
+
+Output: one JSON line (rank 0). value = stage solves/s (whole job); trace_dof_per_s = trace
+unknowns x trace solves / s. e2e: the same through the C-ABI with the state copied from pinned
+host memory to the device and back every step. roofline: the trace-apply CG kernel timed alone
+with CUDA events on the context's stream, algorithmic bytes / time vs the measured HBM peak.
+cpu_baseline / --impl reference: the oracle (plain FP64 SciPy) on the host cores.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(n=64, k=3, periodic_x=True, tableau='ARS343', dt=2e-3, n_richardson=0, stage_rtol=1e-10,
+                inner_stepI_rtol=1e-1, inner_trace_rtol=1e-6, trace_rtol=1e-12, stepI_rtol=1e-10,
+                init='shear_layer', width=0.05, amp=1e-3, noise=1e-4, seed=0)
+STAGES = {'ARS343': 3, 'ARS222': 2, 'IMEX_EULER': 1}
+METRIC = 'IMEX stage solves/s (trace-DoF/s alongside)'
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, 'MEASURED_PEAKS.json')) as f:
+            d = json.load(f)
+        return float(d['hbm_gbs']), 'measured'
+    except Exception:
+        return 6800.0, 'fallback'
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+         'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+         'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(['nvidia-smi', '-i', str(self.idx), f'--query-gpu={self.Q}',
+                                      '--format=csv,noheader,nounits'], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(',')])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['unavailable']}
+        sm = sorted(float(s[1]) for s in self.samples if s[1].replace('.', '').isdigit())
+        mx = max((float(s[2]) for s in self.samples if s[2].replace('.', '').isdigit()), default=None)
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 5 + i and s[5 + i] == 'Active'})
+        return {'sm_mhz': sm[len(sm) // 2] if sm else None, 'sm_max_mhz': mx, 'reasons': reasons,
+                'samples': len(self.samples)}
+
+
+def initial_velocity(w, n_override=None, seed_offset=0):
+    import hdg_workloads as W
+    n = n_override or w['n']
+    return W.nodal_velocity(n, w['k'], lambda x, y: W.shear_layer(x, y, w['width'], w['amp']),
+                            noise=w['noise'], seed=w['seed'] + seed_offset)
+
+
+# ---------------------------------------------------------------------------------- oracle arm
+def oracle_sample(w, n_sample=16, steps=1):
+    """The oracle (as it stands) on a bounded sample of the workload: `steps` IMEX steps of the
+    same configuration on an n_sample x n_sample mesh. Returns (stage solves/s scaled to the
+    full mesh by the cell-count ratio, seconds, description, threads)."""
+    os.environ.setdefault('OMP_NUM_THREADS', '1')
+    os.environ.setdefault('OPENBLAS_NUM_THREADS', '1')
+    from oracle import Mesh, HDG, Oracle, TABLEAUS
+    m = Mesh(n_sample, periodic_x=w['periodic_x'])
+    h = HDG(m, w['k'])
+    o = Oracle(h)
+    Q0 = initial_velocity(w, n_override=n_sample).reshape(-1)
+    Q, _, _ = o.div_free_project(Q0)
+    _, p, lam = o.reconstruct_pressure(Q)
+    tab = TABLEAUS[w['tableau']]()
+    t0 = time.perf_counter()
+    for s in range(steps):
+        Q, p, lam = o.imex_step(tab, w['dt'], s * w['dt'], Q, p, lam, solver='direct')
+    sec = time.perf_counter() - t0
+    stages = STAGES[w['tableau']] * steps
+    scale = (n_sample / w['n']) ** 2
+    rate = stages / sec * scale
+    desc = (f'{steps} IMEX step(s) ({stages} stage solves by direct sparse LU of the monolithic stage system, '
+            f'final update, reconstruction) of the same workload on a {n_sample}x{n_sample} mesh in {sec:.1f} s; '
+            f'rate scaled by the cell ratio ({n_sample}/{w["n"]})^2 to the {w["n"]}x{w["n"]} mesh')
+    return rate, sec, desc, int(os.environ.get('OMP_NUM_THREADS', '1'))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = WORKLOAD
+    for _ in range(args.warmup):
+        oracle_sample(w, steps=1)
+    rates, secs = [], []
+    for _ in range(args.steps):
+        r, s, desc, cores = oracle_sample(w, steps=1)
+        rates.append(r)
+        secs.append(s)
+    value = len(rates) / sum(1.0 / r for r in rates)
+    line = {'metric': METRIC, 'value': value, 'unit': 'stage_solves/s', 'impl': 'reference',
+            'n_gpus': args.gpus, 'steps': args.steps, 'warmup': args.warmup,
+            'ms_per_step': 1e3 * sum(secs) / len(secs), 'higher_is_better': True, 'scaling': 'weak',
+            'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
+            'config': {'workload': 'shear-layer channel 64x64, k=3, ARS(3,4,3), dt=2e-3, stages to 1e-10', 'n': w['n'],
+                       'k': w['k'], 'periodic_x': True, 'sample_n': 16},
+            'cpu_baseline': {'value': value, 'unit': 'stage_solves/s', 'cores': cores, 'kind': 'oracle',
+                             'sample': desc},
+            'e2e': {'value': value, 'unit': 'stage_solves/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import paper_2410_09790_gb300 as H
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device('cuda', local_rank)
+    w = WORKLOAD
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        ctx = H.Context(w['n'], w['k'], periodic_x=w['periodic_x'], stream=stream, tableau=w['tableau'],
+                        dt=w['dt'], n_richardson=w['n_richardson'], richardson_rtol=w['stage_rtol'],
+                        richardson_max=600, stage_krylov=1, inner_stepI_rtol=w['inner_stepI_rtol'],
+                        inner_trace_rtol=w['inner_trace_rtol'], trace_rtol=w['trace_rtol'],
+                        stepI_rtol=w['stepI_rtol'])
+        Q0 = torch.from_numpy(initial_velocity(w, seed_offset=rank)).to(dev)
+        ctx.hdg_set_state(Q0)
+        ctx.hdg_div_free_project()
+        flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)   # > L2 (129 MB)
+        stats_all = []
+        for _ in range(args.warmup):
+            ctx.hdg_imex_step(1)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with ClockSampler(local_rank) as clk:
+            for i in range(args.steps):
+                flush.fill_(float(i))                      # evict the previous step's working set
+                torch.cuda.nvtx.range_push('bench_step')
+                ev[i][0].record(stream)
+                st = ctx.hdg_imex_step(1)
+                ev[i][1].record(stream)
+                torch.cuda.nvtx.range_pop()
+                stats_all.append(st)
+            torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        # roofline: the trace-apply CG kernel alone, same operators and stream
+        gamma = 0.43586652150845899942                   # ARS(3,4,3) diagonal
+        c_stage = gamma * w['dt']
+        k_ms, k_bytes = ctx.hdg_time_kernel(0, c_stage, 50)
+        s_ms, s_bytes = ctx.hdg_time_kernel(1, 1.0, 20)
+        # end to end through the C-ABI with host buffers
+        Qh, ph, lh, _ = ctx.hdg_get_state()
+        Qh, ph, lh = Qh.cpu().pin_memory(), ph.cpu().pin_memory(), lh.cpu().pin_memory()
+        Qd, pd, ld = torch.empty_like(Qh, device=dev), torch.empty_like(ph, device=dev), torch.empty_like(lh, device=dev)
+        e2e_ms = []
+        tsim = w['dt'] * (args.warmup + args.steps)
+        for i in range(args.e2e_steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Qd.copy_(Qh, non_blocking=True); pd.copy_(ph, non_blocking=True); ld.copy_(lh, non_blocking=True)
+            ctx.hdg_set_state(Qd, pd, ld, tsim)
+            ctx.hdg_imex_step(1)
+            Qo, po, lo, tsim = ctx.hdg_get_state()
+            Qh.copy_(Qo); ph.copy_(po); lh.copy_(lo)
+            torch.cuda.synchronize()
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        h2d = (Qh.numel() + ph.numel() + lh.numel()) * 8
+        ctx.close()
+
+    stages = STAGES[w['tableau']]
+    ms_step = float(np.mean(ms))
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms, float(np.mean(e2e_ms)) if e2e_ms else float('nan')], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms, e2e_mean = t.tolist()
+    else:
+        e2e_mean = float(np.mean(e2e_ms)) if e2e_ms else float('nan')
+    value = world * stages * args.steps / (total_ms / 1e3)
+    ntrace = ctx.nL
+    trace_solves = sum(s['trace_solves'] for s in stats_all)
+    trace_iters = sum(s['trace_iters'] for s in stats_all)
+    stepI_iters = sum(s['stepI_iters'] for s in stats_all)
+    peak, peak_kind = measured_peaks()
+    achieved = k_bytes / (k_ms * 1e-3) / 1e9
+    line = {
+        'metric': METRIC, 'value': value, 'unit': 'stage_solves/s', 'n_gpus': world, 'steps': args.steps,
+        'warmup': args.warmup, 'ms_per_step': ms_step, 'higher_is_better': True, 'scaling': 'weak',
+        'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic (seeded shear layer + noise)',
+        'config': {'workload': 'shear-layer channel 64x64, k=3, ARS(3,4,3), dt=2e-3, stages to 1e-10', 'n': w['n'],
+                   'k': w['k'], 'periodic_x': True, 'trace_dofs': ntrace, 'dg_dofs': ctx.nQ + ctx.nP,
+                   'l2': 'flushed (256 MB write) between timed steps', 'parallelism': f'replicas x{world}'},
+        'trace_dof_per_s': world * ntrace * trace_solves / (total_ms / 1e3),
+        'per_step': {'trace_solves': trace_solves / args.steps, 'trace_cg_iters': trace_iters / args.steps,
+                     'stage_outer_iters': sum(s['richardson_iters'] for s in stats_all) / args.steps,
+                     'gmres_iters': stepI_iters / args.steps},
+        'e2e': {'value': world * stages / (e2e_mean / 1e3), 'unit': 'stage_solves/s', 'h2d_bytes_per_step': h2d,
+                'd2h_bytes_per_step': h2d},
+        'roofline': {'kernel': 'k_cg_apply (trace operator apply + CG direction + dot)', 'bound': 'hbm',
+                     'achieved': achieved, 'peak': peak, 'unit': 'GB/s', 'frac': achieved / peak,
+                     'peak_kind': peak_kind, 'traffic': None, 'ms_per_launch': k_ms,
+                     'algorithmic_bytes': k_bytes},
+        'stepI_matvec': {'achieved_gbs': s_bytes / (s_ms * 1e-3) / 1e9, 'ms_per_launch': s_ms, 'bytes': s_bytes},
+        'clocks': clk.summary(),
+        'gpu_launches': None,
+    }
+    # kernel launches inside one step, counted from the solver statistics
+    per_step = stats_all[-1]
+    line['gpu_launches'] = int(args.steps * launches_per_step(per_step, stages))
+    if rank == 0 and not args.no_cpu_baseline:
+        r, s, desc, cores = oracle_sample(w, steps=1)
+        line['cpu_baseline'] = {'value': r, 'unit': 'stage_solves/s', 'cores': cores, 'kind': 'oracle', 'sample': desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def launches_per_step(st, stages):
+    """Kernel launches of one IMEX step: per CG solve 2 setup + 2 per iteration rounded up to the
+    16-iteration chunk; per GMRES cycle 1 + 4 x 30 + 3; plus the fixed per-stage,
+    per-solve and per-step kernels (stage rhs, BDM, assembly, residual, updates, condensation rhs
+    / gather / back-substitution, mean shift)."""
+    import math
+    cg = st['trace_solves'] * 2 + 2 * 16 * math.ceil(st['trace_iters'] / max(st['trace_solves'], 1) / 16) * st['trace_solves']
+    bi = st['stepI_solves'] * (1 + 4 * 30 + 3) * math.ceil(st['stepI_iters'] / max(st['stepI_solves'], 1) / 30)
+    fixed = st['trace_solves'] * 3 + st['stepI_solves'] * 4 + stages * 3 + 8
+    return cg + bi + fixed
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=10)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--impl', default='gpu', choices=['gpu', 'reference'])
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--e2e-steps', type=int, default=3)
+    args = ap.parse_args()
+    world = int(os.environ.get('WORLD_SIZE', '1'))
+    rank = int(os.environ.get('RANK', '0'))
+    local_rank = int(os.environ.get('LOCAL_RANK', '0'))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = 'nccl' if args.impl == 'gpu' else 'gloo'
+        if args.impl == 'gpu':
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend)
+    if args.impl == 'reference':
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == '__main__':
+    main()

@@ -1,0 +1,188 @@
+/*
+ * hdg.h — C-ABI of the GB300 hybridised DG IMEX stage solver for the incompressible Euler
+ * equations (Mueller, "A Higher-order Hybridisable Discontinuous Galerkin IMEX method for the
+ * incompressible Euler equations", arXiv 2410.09790).
+ *
+ * Discretisation (Sec. 2.2-2.4): on a structured triangulation of [0,Lx]x[0,Ly] (Sec. 3.2),
+ * velocity Q in [DG_{k+1}]^2, pressure p in DG_k with (p)_Omega = 0, trace lambda in P_k on
+ * every facet. Time stepping: the s-stage IMEX scheme of Alg. 1, each implicit stage solved by
+ * the Chorin-preconditioned Richardson iteration of Alg. 2; Step II is condensed onto the
+ * trace (Sec. 2.8) and solved by preconditioned CG on the GPU.
+ *
+ * Exchange format. Every array crossing this interface holds NODAL VALUES on the canonical
+ * mesh (independent of the library's internal modal basis):
+ *   cells: n x n rectangles, rectangle (i,j) split along its (i,j)-(i+1,j+1) diagonal into
+ *          cell 2(jn+i) = (A,B,C) and cell 2(jn+i)+1 = (A,C,D) with A=(i,j), B=(i+1,j),
+ *          C=(i+1,j+1), D=(i,j+1) (in units Lx/n, Ly/n), vertices v0,v1,v2 in that order;
+ *   a degree-m cell field: values at v0 + (i/m)(v1-v0) + (j/m)(v2-v0), i+j <= m, j outer,
+ *          i inner;  Q: double[ncells][2][(k+2)(k+3)/2];  p: double[ncells][(k+1)(k+2)/2];
+ *   facets: horizontal H(i,j) from (i,j) to (i+1,j), then vertical V(i,j) from (i,j) to
+ *          (i,j+1), then diagonals D(i,j) from (i,j) to (i+1,j+1), each j-major; periodic
+ *          directions omit the duplicate edges; lambda: double[nfacets][k+1] at the points
+ *          t = i/k along the facet from its first to its second end point.
+ *   dual vectors (one-forms on V_Q, e.g. the stage residual r_i of eq. imex_residual) are
+ *          passed by their L2 Riesz representer R (r(w) = (R, w)_Omega), as a velocity field.
+ *
+ * Memory. Array arguments are DEVICE pointers (e.g. torch CUDA tensors) unless the name says
+ * host; the library copies in/out on the context's stream and keeps no caller pointer. All
+ * arrays are contiguous float64 in the layouts above. The context owns every internal buffer
+ * (allocated in hdg_setup_mesh and on first use of a new coefficient c; freed by hdg_destroy).
+ *
+ * Errors. Every call returns an hdg_status; nothing aborts or traps. HDG_ERR_NOT_CONVERGED still
+ * leaves the last iterate in place and fills the stats. Iteration counts are bounded by
+ * hdg_params.max_iters. Calls on one context must not overlap (one host thread at a time).
+ */
+#ifndef HDG_GB300_H
+#define HDG_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hdg_ctx hdg_ctx;
+
+typedef enum {
+    HDG_OK = 0,
+    HDG_ERR_INVALID_ARG = 1,   /* bad size, degree, pointer or parameter                   */
+    HDG_ERR_CUDA = 2,          /* a CUDA runtime call failed (message: hdg_last_error)      */
+    HDG_ERR_OOM = 3,           /* device allocation failed                                  */
+    HDG_ERR_NOT_CONVERGED = 4, /* an iteration hit its cap; best iterate kept               */
+    HDG_ERR_NUMERIC = 5,       /* NaN / Inf in a residual norm                              */
+    HDG_ERR_UNSUPPORTED = 6    /* valid request this build does not handle                  */
+} hdg_status;
+
+typedef enum { HDG_ARS222 = 0, HDG_ARS343 = 1, HDG_IMEX_EULER = 2 } hdg_tableau;
+
+/* Mesh (Sec. 3.2): n x n rectangles over [0,Lx]x[0,Ly]; walls (n.Q = 0, weakly) on every
+ * non-periodic side. */
+typedef struct {
+    int n;
+    double Lx, Ly;
+    int periodic_x, periodic_y;
+} hdg_mesh_desc;
+
+/* Method parameters. Defaults (hdg_default_params): alpha = tau = delta_up = 1 (Sec. 3.2),
+ * n_richardson = 2 (Sec. 3.2), trace_rtol = 1e-12, stepI_rtol = 1e-10 (Sec. 3.4.2). */
+typedef struct {
+    int k;                    /* pressure degree, 1..4 (velocity k+1, trace k)             */
+    double alpha;             /* normal-jump penalty of eq. f_impl                         */
+    double tau;               /* HDG stabilisation of eq. flux_hdg                         */
+    double delta_up;          /* upwind switch/weight of eq. f_impl                        */
+    int tableau;              /* hdg_tableau                                               */
+    double dt;                /* time step                                                 */
+    int n_richardson;         /* > 0: fixed number of Alg. 2 iterations                    */
+    double richardson_rtol;   /* used when n_richardson <= 0: stop at ||dQ||_M <= rtol ||Q||_M */
+    int richardson_max;       /* cap for the tolerance mode                                */
+    double trace_rtol;        /* CG on the trace system: preconditioned residual           */
+    double stepI_rtol;        /* GMRES(30) on the tentative velocity system (residual)     */
+    int max_iters;            /* cap for each Krylov solve                                 */
+    /* Stage solves to tolerance (n_richardson <= 0): stage_krylov = 0 iterates Alg. 2 until
+     * ||dQ||_M <= richardson_rtol ||Q||_M; stage_krylov = 1 (default) runs flexible GMRES(30) on
+     * the monolithic stage system with Alg. 2's Chorin split as the preconditioner (Step I and
+     * Step II solved to inner_stepI_rtol / inner_trace_rtol) until the stage residual is
+     * <= richardson_rtol times the right-hand side; richardson_max caps the outer iterations.
+     * Both reach the same fixed point, the monolithic stage solution. */
+    int stage_krylov;
+    double inner_stepI_rtol;
+    double inner_trace_rtol;
+} hdg_params;
+
+typedef struct {
+    int richardson_iters;     /* Alg. 2 iterations of the last stage solve                 */
+    int trace_solves;         /* trace (Step II type) solves in the last call               */
+    int trace_iters;          /* CG iterations summed over those solves                    */
+    int stepI_solves;
+    int stepI_iters;          /* GMRES iterations summed                                   */
+    int stage_solves;         /* Alg. 2 solves in the last call                            */
+    double last_update_norm;  /* ||Q^(m) - Q^(m-1)||_M of the last Richardson iteration     */
+    double last_trace_relres; /* final relative (preconditioned) residual of the last CG    */
+    double ms_total;          /* device time of the call (CUDA events)                     */
+} hdg_stats;
+
+void hdg_default_params(hdg_params *p);
+const char *hdg_status_string(hdg_status s);
+/* Text of the last CUDA error seen by any context (host string, valid until the next call). */
+const char *hdg_last_error(void);
+
+/* Host-only queries (no GPU needed). Sizes of the exchange arrays for a mesh and degree. */
+hdg_status hdg_mesh_counts(const hdg_mesh_desc *mesh, int k, int64_t *ncells, int64_t *nfacets);
+
+/* Host-only: the library's reference element, for tests.
+ * which = 0: volume rule on the reference triangle (0,0),(1,0),(0,1) used for degree k forms;
+ * which = 1: facet rule on [0,1] (Gauss-Legendre, (3k+5)/2 points, shared with eq. f_impl's
+ *            upwind term). pts (host) gets 2 (which=0) or 1 (which=1) coordinates per point.
+ * Call with pts = wts = NULL to get *npts. */
+hdg_status hdg_reference_rule(int k, int which, double *pts, double *wts, int *npts);
+/* Host-only: values of the library's orthonormal basis of P_m on the reference triangle at
+ * npts points (host, x/y interleaved) -> vals[npts][dim P_m] (host). */
+hdg_status hdg_reference_basis(int m, int npts, const double *pts, double *vals);
+
+/* Create a context: build the mesh and reference tables, upload them, allocate state. The
+ * stream (cudaStream_t, may be NULL for the legacy default stream) orders all work of the
+ * context. Uses the current CUDA device. */
+hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_params *params,
+                          void *cuda_stream);
+void hdg_destroy(hdg_ctx *ctx);
+
+/* Sizes (doubles) of the nodal Q, p and lambda arrays. */
+hdg_status hdg_dof_sizes(const hdg_ctx *ctx, int64_t *nQ, int64_t *np, int64_t *nlambda);
+
+/* State (device pointers, nodal). p and lam may be NULL (taken as zero). */
+hdg_status hdg_set_state(hdg_ctx *ctx, const double *Q, const double *p, const double *lam, double t);
+hdg_status hdg_get_state(hdg_ctx *ctx, double *Q, double *p, double *lam, double *t_host);
+
+/* Forcing f(x, t) = phi(t) F(x) with F a velocity field (nodal, device): f^ex(w, t) =
+ * (w . f(t)) (eq. f_expl). phi is called on the host; NULL phi means phi = 1. F = NULL
+ * removes the forcing. */
+hdg_status hdg_set_forcing(hdg_ctx *ctx, const double *F, double (*phi)(double t, void *user), void *user);
+
+/* Alg. 1 x nsteps: s-1 stage solves (Alg. 2), final update (eq. final_update) and pressure
+ * reconstruction (Sec. 2.7) per step, on the context's state. */
+hdg_status hdg_imex_step(hdg_ctx *ctx, int nsteps, hdg_stats *stats);
+
+/* One stage solve (Alg. 2): find (Q, p, lambda) with
+ *   (Q.w) - c (f^impl(w, Q, Q*) + g(w, p, lambda)) = (R, w),  Gamma(psi, mu, Q, p, lambda) = 0
+ * (eq. imex_implicit_solve + constraint). R: Riesz representer of the right-hand side; Qstar:
+ * the advecting velocity (used as given; pass P(Q_{i-1}) for the paper's scheme). Q, p, lam:
+ * initial iterate in, result out (nodal, device). */
+hdg_status hdg_solve_stage(hdg_ctx *ctx, double c, const double *R, const double *Qstar,
+                           double *Q, double *p, double *lam, hdg_stats *stats);
+
+/* Component entry points (each one row of the hot path, for verification):
+ * BDM^0_{k+1} projection Q* = P(Q) (Sec. 2.3). */
+hdg_status hdg_bdm_project(hdg_ctx *ctx, const double *Q, double *Qstar);
+/* Riesz representer of w -> f^impl(w, Q, Q*) (eq. f_impl). */
+hdg_status hdg_fimpl_apply(hdg_ctx *ctx, const double *Qstar, const double *Q, double *out);
+/* Tentative velocity (Alg. 2 Step I): (Qbar.w) - c f^impl(w, Qbar, Q*) = (R, w). */
+hdg_status hdg_tentative_solve(hdg_ctx *ctx, double c, const double *Qstar, const double *R,
+                               double *Qbar, hdg_stats *stats);
+/* Mixed solve (the operator of Step II, eq. final_update and Sec. 2.7):
+ *   (U.w) - c g(w, p, lambda) = (R, w),   Gamma(psi, mu, U, p, lambda) = -Gamma(psi, mu, X, 0, 0)
+ * with (p)_Omega = 0. R or X may be NULL (zero). Outputs nodal, device. */
+hdg_status hdg_mixed_solve(hdg_ctx *ctx, double c, const double *R, const double *X,
+                           double *U, double *p, double *lam, hdg_stats *stats);
+/* Riesz representer (on the trace space) of the condensed trace operator applied to lam:
+ * mu -> sum_K <S_K lam, mu> for coefficient c (Sec. 2.8, the operator the CG solves with). */
+hdg_status hdg_trace_apply(hdg_ctx *ctx, double c, const double *lam, double *out);
+/* Replace the state's Q by its discretely divergence-free part (Step II with c = 1), and set
+ * (p, lambda) to the pressure reconstruction of the result (Sec. 2.7). */
+hdg_status hdg_div_free_project(hdg_ctx *ctx, hdg_stats *stats);
+/* Pressure reconstruction (Sec. 2.7) of the state's Q at the state's time. */
+hdg_status hdg_reconstruct_pressure(hdg_ctx *ctx, hdg_stats *stats);
+
+/* Instrumentation: launch one kernel of the path `reps` times on the context's stream between
+ * CUDA events (after one untimed launch) and report the mean device time per launch and the
+ * algorithmic bytes one launch moves (operator entries it must read + vectors read/written
+ * once). which = 0: trace operator apply fused with the CG direction update and dot product
+ * (the kernel the trace CG runs every iteration) for coefficient c; which = 1: tentative-velocity
+ * operator apply (the GMRES matrix-vector product) for the operator last assembled (call
+ * hdg_tentative_solve or hdg_imex_step first). Operands are the context's current buffers. */
+hdg_status hdg_time_kernel(hdg_ctx *ctx, int which, double c, int reps, double *ms_per_launch,
+                           double *bytes_per_launch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,541 @@
+// Per-cell operations of the HDG stage solver, written for a "team" of threads that cooperates
+// on one cell through a scratch buffer (shared memory on the GPU). Every function is
+// __host__ __device__ and only uses team-strided loops and team barriers, so the same code runs
+// inside the kernels of hdg_kernels.cuh.
+//
+// Conventions (see refelem.h, mesh.h):
+//  * cell velocity Q|_K = sum_a q[d][a] phi_a e_d with phi_a = phi^_a o F_K^{-1} (orthonormal
+//    Dubiner on the reference cell), so (phi_a, phi_b)_K = detJ delta_ab; coefficient index
+//    d*MU + a. Pressure: first NP functions of the same basis. Dual vectors (one-forms on V_Q)
+//    are stored by their values on the basis, r[d*MU + a] = r(phi_a e_d).
+//  * trace on facet F: lambda_F = sum_j l[j] L_j(t), L_j orthonormal Legendre on [0,1] in the
+//    facet's canonical direction t. A cell sees lambda in its local edge direction s; where the
+//    two directions differ (flip), s = 1 - t and the coefficient picks up (-1)^j.
+//  * mixed operator (Step II, eq. final_update, Sec. 2.7) with coefficient c, per cell:
+//      M U - c (D^T p - E^T l) = Ru ,   D U + tau (Tpp p - Tpl l) = Rp ,
+//      sum_K [E U + tau (Tlp p - Tll l)] = Rl
+//    with D = (psi_b, div(phi_a e_d))_K, E = <(phi_a e_d).n, L_j>_dK, Tpp/Tpl/Tll the tau facet
+//    masses (eq. implicit_HDG_scheme's g and Gamma, one cell at a time). Eliminating (U, p):
+//      A = (c/detJ) D D^T + tau Tpp,  H = (c/detJ) D E^T + tau Tpl,  Z = A^{-1} H,
+//      S_K = (c/detJ) E E^T + tau Tll - H^T Z    (symmetric positive semidefinite),
+//      sum_K S_K l_K = sum_K [E Ru/detJ + Z^T w_K] - Rl,  w_K = Rp - D Ru/detJ,
+//      p = A^{-1} w + Z l,  U = (Ru - c E^T l + c D^T p)/detJ.
+#pragma once
+#include <cmath>
+
+#include "mesh.h"
+
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#define __forceinline__ inline
+#endif
+
+namespace hdg {
+
+template <int K>
+struct Dims {
+    static constexpr int MU = (K + 2) * (K + 3) / 2;     // P_{k+1}
+    static constexpr int NU = 2 * MU;
+    static constexpr int NP = (K + 1) * (K + 2) / 2;     // P_k
+    static constexpr int NT = K + 1;                     // trace per facet
+    static constexpr int NL = 3 * NT;                    // trace per cell
+    static constexpr int NB = K + 2;                     // BDM edge moments
+    static constexpr int NV = K * (K + 2);               // BDM interior moments
+    static constexpr int NQ1 = (3 * K + 4) / 2;
+    static constexpr int NQ = NQ1 * (NQ1 + 1);           // volume points
+    static constexpr int NFQ = (3 * K + 5) / 2;          // facet points
+};
+
+// Device copies of the reference tables (layouts as in RefTables).
+struct RefDev {
+    const double *qw, *phi, *dphi, *fw, *ephi, *leg, *Dhat, *Ehat, *Tpp, *bdm_inv, *Iv;
+    const double *nod_u, *nod_p, *mod_u, *mod_p, *nod_t, *mod_t;
+};
+
+struct MeshDev {
+    const CellGeo *geo;
+    const int *cell_facet, *cell_flip, *cell_nbr, *cell_nbr_edge, *facet_cell, *facet_edge;
+    int ncells, nfacets;
+};
+
+struct Team {
+    int tid, nthr;
+    __host__ __device__ __forceinline__ void sync() const {
+#ifdef __CUDA_ARCH__
+        if (nthr <= 32) __syncwarp(); else __syncthreads();
+#endif
+    }
+};
+
+#define TFOR(i, n) for (int i = tm.tid; i < (n); i += tm.nthr)
+
+__host__ __device__ __forceinline__ double ldg(const double *p) {
+#ifdef __CUDA_ARCH__
+    return __ldg(p);
+#else
+    return *p;
+#endif
+}
+
+// sign of trace coefficient j on local edge e of a cell (flip = local edge against the facet)
+__host__ __device__ __forceinline__ double tsign(int flip, int j) { return (flip && (j & 1)) ? -1.0 : 1.0; }
+
+// ------------------------------------------------------------------------------------------
+// Static condensation of the mixed operator for one cell (coefficient c).
+// Outputs: S (NL x NL, canonical facet orientation), Z (NP x NL, local orientation),
+// Ainv (NP x NP). Scratch: NP*NU + NL*NU + NP*NP*2 + NP*NL*2 + NL*NL doubles.
+template <int K>
+__host__ __device__ void cell_condense(const Team &tm, const RefDev &R, const CellGeo &g,
+                                       const int *flip, double c, double tau, double *sm,
+                                       double *S_out, double *Z_out, double *Ainv_out) {
+    typedef Dims<K> Dm;
+    constexpr int MU = Dm::MU, NU = Dm::NU, NP = Dm::NP, NT = Dm::NT, NL = Dm::NL;
+    double *D = sm;                 // NP x NU
+    double *E = D + NP * NU;        // NL x NU
+    double *A = E + NL * NU;        // NP x NP  (Cholesky factor in place)
+    double *Ai = A + NP * NP;       // NP x NP
+    double *H = Ai + NP * NP;       // NP x NL
+    double *Z = H + NP * NL;        // NP x NL
+    double *S = Z + NP * NL;        // NL x NL
+    const double cj = c / g.detJ;
+    TFOR(i, NP * NU) {
+        int b = i / NU, x = i % NU, d = x / MU, a = x % MU;
+        D[i] = g.detJ * (g.Jinv[d] * ldg(&R.Dhat[(0 * NP + b) * MU + a]) +
+                         g.Jinv[2 + d] * ldg(&R.Dhat[(1 * NP + b) * MU + a]));
+    }
+    TFOR(i, NL * NU) {
+        int ej = i / NU, x = i % NU, e = ej / NT, j = ej % NT, d = x / MU, a = x % MU;
+        double nd = d == 0 ? g.nx[e] : g.ny[e];
+        E[i] = g.h[e] * nd * ldg(&R.Ehat[(e * NT + j) * MU + a]);
+    }
+    tm.sync();
+    TFOR(i, NP * NP) {
+        int b = i / NP, b2 = i % NP;
+        double s = 0;
+        for (int x = 0; x < NU; ++x) s += D[b * NU + x] * D[b2 * NU + x];
+        double t = 0;
+        for (int e = 0; e < 3; ++e) t += g.h[e] * ldg(&R.Tpp[(e * NP + b) * NP + b2]);
+        A[i] = cj * s + tau * t;
+    }
+    TFOR(i, NP * NL) {
+        int b = i / NL, ej = i % NL, e = ej / NT, j = ej % NT;
+        double s = 0;
+        for (int x = 0; x < NU; ++x) s += D[b * NU + x] * E[ej * NU + x];
+        H[i] = cj * s + tau * g.h[e] * ldg(&R.Ehat[(e * NT + j) * MU + b]);
+    }
+    tm.sync();
+    if (tm.tid == 0) {                        // Cholesky A = L L^T (lower part of A)
+        for (int j = 0; j < NP; ++j) {
+            double s = A[j * NP + j];
+            for (int k = 0; k < j; ++k) s -= A[j * NP + k] * A[j * NP + k];
+            s = sqrt(s);
+            A[j * NP + j] = s;
+            for (int i = j + 1; i < NP; ++i) {
+                double t = A[i * NP + j];
+                for (int k = 0; k < j; ++k) t -= A[i * NP + k] * A[j * NP + k];
+                A[i * NP + j] = t / s;
+            }
+        }
+    }
+    tm.sync();
+    TFOR(col, NP) {                           // column col of A^{-1}
+        double y[NP];
+        for (int i = 0; i < NP; ++i) {
+            double t = (i == col) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) t -= A[i * NP + k] * y[k];
+            y[i] = t / A[i * NP + i];
+        }
+        for (int i = NP - 1; i >= 0; --i) {
+            double t = y[i];
+            for (int k = i + 1; k < NP; ++k) t -= A[k * NP + i] * y[k];
+            y[i] = t / A[i * NP + i];
+        }
+        for (int i = 0; i < NP; ++i) Ai[i * NP + col] = y[i];
+    }
+    tm.sync();
+    TFOR(i, NP * NL) {
+        int b = i / NL, ej = i % NL;
+        double s = 0;
+        for (int k = 0; k < NP; ++k) s += Ai[b * NP + k] * H[k * NL + ej];
+        Z[i] = s;
+    }
+    tm.sync();
+    TFOR(i, NL * NL) {
+        int r = i / NL, q = i % NL;
+        double s = 0;
+        for (int x = 0; x < NU; ++x) s += E[r * NU + x] * E[q * NU + x];
+        double t = 0;
+        for (int b = 0; b < NP; ++b) t += H[b * NL + r] * Z[b * NL + q];
+        double v = cj * s - t + ((r == q) ? tau * g.h[r / NT] : 0.0);
+        S[i] = v;
+    }
+    tm.sync();
+    TFOR(i, NL * NL) {
+        int r = i / NL, q = i % NL;
+        S_out[i] = tsign(flip[r / NT], r % NT) * tsign(flip[q / NT], q % NT) * S[i];
+    }
+    TFOR(i, NP * NL) Z_out[i] = Z[i];
+    TFOR(i, NP * NP) Ainv_out[i] = Ai[i];
+}
+
+// ------------------------------------------------------------------------------------------
+// Right-hand side of the condensed trace system for one cell.
+//   Ru: dual vector (NU) or null; X: velocity (NU) or null whose constraint residual enters
+//   as Rp = -[D X + tau (Tpp p - Tpl l)] + Rp_add, Rl = -[E X + tau (Tlp p - Tll l)] (p, l of the
+//   current iterate; pK/lK/Rp_add may be null = zero; a global Rl_add is subtracted by the
+//   facet gather).
+// Outputs: v (NL, canonical orientation) = E Ru/detJ + Z^T w - Rl,  w (NP) = Rp - D Ru/detJ.
+// Scratch: 2*2*MU + NP + NL + NP doubles.
+template <int K>
+__host__ __device__ void cell_mixed_rhs(const Team &tm, const RefDev &R, const CellGeo &g,
+                                        const int *flip, double tau, const double *Ru,
+                                        const double *X, const double *pK, const double *lK_local,
+                                        const double *Rp_add, const double *Z, double *sm,
+                                        double *v_out, double *w_out) {
+    typedef Dims<K> Dm;
+    constexpr int MU = Dm::MU, NP = Dm::NP, NT = Dm::NT, NL = Dm::NL;
+    double *xr = sm;              // 2 x MU  Jinv X (reference-frame components)
+    double *ur = xr + 2 * MU;     // 2 x MU  Jinv Ru
+    double *w = ur + 2 * MU;      // NP
+    double *rl = w + NP;          // NL: -Rl + E Ru/detJ
+    TFOR(a, MU) {
+        double x0 = X ? X[a] : 0.0, x1 = X ? X[MU + a] : 0.0;
+        xr[a] = g.Jinv[0] * x0 + g.Jinv[1] * x1;
+        xr[MU + a] = g.Jinv[2] * x0 + g.Jinv[3] * x1;
+        double u0 = Ru ? Ru[a] : 0.0, u1 = Ru ? Ru[MU + a] : 0.0;
+        ur[a] = g.Jinv[0] * u0 + g.Jinv[1] * u1;
+        ur[MU + a] = g.Jinv[2] * u0 + g.Jinv[3] * u1;
+    }
+    tm.sync();
+    TFOR(b, NP) {
+        double dx = 0, du = 0;
+        for (int r = 0; r < 2; ++r)
+            for (int a = 0; a < MU; ++a) {
+                double dh = ldg(&R.Dhat[(r * NP + b) * MU + a]);
+                dx += dh * xr[r * MU + a];
+                du += dh * ur[r * MU + a];
+            }
+        double tp = 0, tl = 0;
+        for (int e = 0; e < 3; ++e) {
+            double s = 0;
+            if (pK)
+                for (int b2 = 0; b2 < NP; ++b2) s += ldg(&R.Tpp[(e * NP + b) * NP + b2]) * pK[b2];
+            double s2 = 0;
+            if (lK_local)
+                for (int j = 0; j < NT; ++j) s2 += ldg(&R.Ehat[(e * NT + j) * MU + b]) * lK_local[e * NT + j];
+            tp += g.h[e] * s;
+            tl += g.h[e] * s2;
+        }
+        double Rp = -(g.detJ * dx + tau * (tp - tl)) + (Rp_add ? Rp_add[b] : 0.0);
+        w[b] = Rp - du;                    // D Ru / detJ = du (detJ cancels)
+    }
+    TFOR(ej, NL) {
+        int e = ej / NT, j = ej % NT;
+        double ex = 0, eu = 0, ep = 0;
+        for (int a = 0; a < MU; ++a) {
+            double eh = ldg(&R.Ehat[(e * NT + j) * MU + a]);
+            double xn = X ? (g.nx[e] * X[a] + g.ny[e] * X[MU + a]) : 0.0;
+            double un = Ru ? (g.nx[e] * Ru[a] + g.ny[e] * Ru[MU + a]) : 0.0;
+            ex += eh * xn;
+            eu += eh * un;
+            if (pK && a < NP) ep += eh * pK[a];
+        }
+        double ll = lK_local ? lK_local[ej] : 0.0;
+        double Rl = -(g.h[e] * ex + tau * g.h[e] * (ep - ll));
+        rl[ej] = g.h[e] * eu / g.detJ - Rl;
+    }
+    tm.sync();
+    TFOR(ej, NL) {
+        double s = rl[ej];
+        for (int b = 0; b < NP; ++b) s += Z[b * NL + ej] * w[b];
+        v_out[ej] = tsign(flip[ej / NT], ej % NT) * s;
+    }
+    TFOR(b, NP) w_out[b] = w[b];
+    tm.sync();
+}
+
+// Constraint rows of one cell (eq. implicit_HDG_scheme's Gamma): psi-rows
+//   yp = D Q + tau (Tpp p - Tpl l)  and the cell's contribution to the mu-rows
+//   yl = E Q + tau (Tlp p - Tll l)  (canonical orientation; summed over the facet's cells).
+template <int K>
+__host__ __device__ void cell_constraint(const Team &tm, const RefDev &R, const CellGeo &g,
+                                         const int *flip, double tau, const double *Q, const double *pK,
+                                         const double *lK_local, double *sm, double *yp_out,
+                                         double *yl_out) {
+    typedef Dims<K> Dm;
+    constexpr int MU = Dm::MU, NP = Dm::NP, NT = Dm::NT, NL = Dm::NL;
+    double *xr = sm;              // 2 x MU
+    TFOR(a, MU) {
+        xr[a] = g.Jinv[0] * Q[a] + g.Jinv[1] * Q[MU + a];
+        xr[MU + a] = g.Jinv[2] * Q[a] + g.Jinv[3] * Q[MU + a];
+    }
+    tm.sync();
+    TFOR(b, NP) {
+        double dx = 0;
+        for (int r = 0; r < 2; ++r)
+            for (int a = 0; a < MU; ++a) dx += ldg(&R.Dhat[(r * NP + b) * MU + a]) * xr[r * MU + a];
+        double tp = 0, tl = 0;
+        for (int e = 0; e < 3; ++e) {
+            double s = 0, s2 = 0;
+            for (int b2 = 0; b2 < NP; ++b2) s += ldg(&R.Tpp[(e * NP + b) * NP + b2]) * pK[b2];
+            for (int j = 0; j < NT; ++j) s2 += ldg(&R.Ehat[(e * NT + j) * MU + b]) * lK_local[e * NT + j];
+            tp += g.h[e] * s;
+            tl += g.h[e] * s2;
+        }
+        yp_out[b] = g.detJ * dx + tau * (tp - tl);
+    }
+    TFOR(ej, NL) {
+        int e = ej / NT, j = ej % NT;
+        double ex = 0, ep = 0;
+        for (int a = 0; a < MU; ++a) {
+            double eh = ldg(&R.Ehat[(e * NT + j) * MU + a]);
+            ex += eh * (g.nx[e] * Q[a] + g.ny[e] * Q[MU + a]);
+            if (a < NP) ep += eh * pK[a];
+        }
+        yl_out[ej] = tsign(flip[e], j) * g.h[e] * (ex + tau * (ep - lK_local[ej]));
+    }
+    tm.sync();
+}
+
+// Back-substitution for one cell: p = Ainv w + Z l, U = (Ru - c E^T l + c D^T p)/detJ.
+// lK_local: the cell's trace (local orientation). Ru may be null.
+// Scratch: NP doubles.
+template <int K>
+__host__ __device__ void cell_mixed_backsub(const Team &tm, const RefDev &R, const CellGeo &g,
+                                            double c, const double *Ru, const double *w,
+                                            const double *lK_local, const double *Z,
+                                            const double *Ainv, double *sm, double *U_out,
+                                            double *p_out) {
+    typedef Dims<K> Dm;
+    constexpr int MU = Dm::MU, NU = Dm::NU, NP = Dm::NP, NT = Dm::NT, NL = Dm::NL;
+    double *p = sm;
+    TFOR(b, NP) {
+        double s = 0;
+        for (int k = 0; k < NP; ++k) s += Ainv[b * NP + k] * w[k];
+        for (int q = 0; q < NL; ++q) s += Z[b * NL + q] * lK_local[q];
+        p[b] = s;
+    }
+    tm.sync();
+    TFOR(x, NU) {
+        int d = x / MU, a = x % MU;
+        double et = 0;
+        for (int e = 0; e < 3; ++e) {
+            double nd = d == 0 ? g.nx[e] : g.ny[e];
+            double s = 0;
+            for (int j = 0; j < NT; ++j) s += ldg(&R.Ehat[(e * NT + j) * MU + a]) * lK_local[e * NT + j];
+            et += g.h[e] * nd * s;
+        }
+        double dt = 0;
+        for (int r = 0; r < 2; ++r) {
+            double s = 0;
+            for (int b = 0; b < NP; ++b) s += ldg(&R.Dhat[(r * NP + b) * MU + a]) * p[b];
+            dt += g.Jinv[r * 2 + d] * s;
+        }
+        double ru = Ru ? Ru[x] : 0.0;
+        U_out[x] = (ru - c * et) / g.detJ + c * dt;     // c D^T p / detJ = c Jinv^T Dhat^T p
+    }
+    TFOR(b, NP) p_out[b] = p[b];
+    tm.sync();
+}
+
+// ------------------------------------------------------------------------------------------
+// BDM^0_{k+1} projection of one cell (Sec. 2.3, canonical interpolant): edge normal moments of
+// the average {Q}.n (0 on walls) against L_j, j < k+2; interior moments against N_k; solved on
+// the reference cell through the Piola map. QK, Qnbr[e] (null on walls): modal velocities.
+// Scratch: NU (moments) + NU doubles.
+template <int K>
+__host__ __device__ void cell_bdm(const Team &tm, const RefDev &R, const CellGeo &g,
+                                  const double *QK, const double *const *Qnbr, const int *nbr_edge,
+                                  double *sm, double *Qs_out) {
+    typedef Dims<K> Dm;
+    constexpr int MU = Dm::MU, NU = Dm::NU, NB = Dm::NB, NV = Dm::NV, NFQ = Dm::NFQ;
+    double *m = sm;                 // NU moments
+    double *qh = m + NU;            // NU reference coefficients
+    TFOR(i, 3 * NB) {
+        int e = i / NB, j = i % NB;
+        double s = 0;
+        if (Qnbr[e]) {
+            const double *Qo = Qnbr[e];
+            int eo = nbr_edge[e];
+            for (int q = 0; q < NFQ; ++q) {
+                const double *pk = &R.ephi[(e * NFQ + q) * MU];
+                const double *po = &R.ephi[(eo * NFQ + (NFQ - 1 - q)) * MU];
+                double k0 = 0, k1 = 0, o0 = 0, o1 = 0;
+                for (int a = 0; a < MU; ++a) {
+                    double fk = ldg(pk + a), fo = ldg(po + a);
+                    k0 += fk * QK[a]; k1 += fk * QK[MU + a];
+                    o0 += fo * Qo[a]; o1 += fo * Qo[MU + a];
+                }
+                double an = 0.5 * ((k0 + o0) * g.nx[e] + (k1 + o1) * g.ny[e]);
+                s += ldg(&R.fw[q]) * an * ldg(&R.leg[q * NB + j]);
+            }
+            s *= g.h[e];
+        }
+        m[i] = s;
+    }
+    TFOR(v, NV) {
+        double s = 0;
+        for (int a = 0; a < MU; ++a) {
+            double r0 = g.Jinv[0] * QK[a] + g.Jinv[1] * QK[MU + a];
+            double r1 = g.Jinv[2] * QK[a] + g.Jinv[3] * QK[MU + a];
+            s += r0 * ldg(&R.Iv[(a * NV + v) * 2]) + r1 * ldg(&R.Iv[(a * NV + v) * 2 + 1]);
+        }
+        m[3 * NB + v] = g.detJ * s;
+    }
+    tm.sync();
+    TFOR(x, NU) {
+        double s = 0;
+        for (int k = 0; k < NU; ++k) s += ldg(&R.bdm_inv[x * NU + k]) * m[k];
+        qh[x] = s;
+    }
+    tm.sync();
+    TFOR(x, NU) {
+        int d = x / MU, a = x % MU;
+        Qs_out[x] = (g.J[2 * d] * qh[a] + g.J[2 * d + 1] * qh[MU + a]) / g.detJ;
+    }
+    tm.sync();
+}
+
+// ------------------------------------------------------------------------------------------
+// Blocks of the tentative-velocity operator M - c F(Q*) (eq. f_impl; Alg. 2 Step I) for one
+// cell: diagonal block (NU x NU) and the three neighbour blocks (test on this cell, trial on
+// the neighbour across local edge e; zero on walls). F's facet terms with test functions on
+// this cell:
+//   central  +<(Q*.n+)(Q+ - Q-).{w}>      -> diag +1/2 h (Q*.n_K) ,  off -1/2 h (Q*.n_K)
+//   upwind   -delta <|Q*.n+|(Q+-Q-).(w+-w-)> -> diag -delta h |Q*.n| , off +delta h |Q*.n|
+//   penalty  -alpha/h <[[Q.n]][[w.n]]>    -> diag -alpha n n^T ,     off +alpha n n^T
+// with Q*.n_K = {Q*}.n_K at the facet points (the two cells traverse a shared edge in opposite
+// directions, so point q of one side is point NFQ-1-q of the other).
+// Scratch: NU + 3*NU + 2*NQ + 3*NFQ + MU*MU doubles.
+// Output blocks row-major [row][col] in out[0..3][NU*NU].
+template <int K>
+__host__ __device__ void cell_fimpl_blocks(const Team &tm, const RefDev &R, const CellGeo &g,
+                                           const double *QsK, const double *const *Qsn,
+                                           const int *nbr_edge, double c, double alpha,
+                                           double dup, double *sm, double *const *out) {
+    typedef Dims<K> Dm;
+    constexpr int MU = Dm::MU, NU = Dm::NU, NQ = Dm::NQ, NFQ = Dm::NFQ;
+    double *beta = sm;               // NQ x 2: Jinv Q* at the volume points
+    double *qsn = beta + 2 * NQ;     // 3 x NFQ: {Q*}.n_e
+    double *adv = qsn + 3 * NFQ;     // MU x MU
+    TFOR(q, NQ) {
+        double v0 = 0, v1 = 0;
+        for (int a = 0; a < MU; ++a) {
+            double f = ldg(&R.phi[q * MU + a]);
+            v0 += f * QsK[a]; v1 += f * QsK[MU + a];
+        }
+        beta[2 * q] = g.Jinv[0] * v0 + g.Jinv[1] * v1;
+        beta[2 * q + 1] = g.Jinv[2] * v0 + g.Jinv[3] * v1;
+    }
+    TFOR(i, 3 * NFQ) {
+        int e = i / NFQ, q = i % NFQ;
+        double s = 0;
+        if (Qsn[e]) {
+            const double *pk = &R.ephi[(e * NFQ + q) * MU];
+            const double *po = &R.ephi[(nbr_edge[e] * NFQ + (NFQ - 1 - q)) * MU];
+            const double *Qo = Qsn[e];
+            double k0 = 0, k1 = 0, o0 = 0, o1 = 0;
+            for (int a = 0; a < MU; ++a) {
+                double fk = ldg(pk + a), fo = ldg(po + a);
+                k0 += fk * QsK[a]; k1 += fk * QsK[MU + a];
+                o0 += fo * Qo[a]; o1 += fo * Qo[MU + a];
+            }
+            s = 0.5 * ((k0 + o0) * g.nx[e] + (k1 + o1) * g.ny[e]);
+        }
+        qsn[i] = s;
+    }
+    tm.sync();
+    TFOR(i, MU * MU) {                  // -(w.(Q*.grad)Q)_K for one component
+        int a = i / MU, b = i % MU;
+        double s = 0;
+        for (int q = 0; q < NQ; ++q)
+            s += ldg(&R.qw[q]) * ldg(&R.phi[q * MU + a]) *
+                 (beta[2 * q] * ldg(&R.dphi[(q * MU + b) * 2]) + beta[2 * q + 1] * ldg(&R.dphi[(q * MU + b) * 2 + 1]));
+        adv[i] = -g.detJ * s;
+    }
+    tm.sync();
+    TFOR(i, NU * NU) {                  // diagonal block
+        int r = i / NU, x = i % NU, d = r / MU, a = r % MU, d2 = x / MU, b = x % MU;
+        double F = (d == d2) ? adv[a * MU + b] : 0.0;
+        for (int e = 0; e < 3; ++e) {
+            double nd = d == 0 ? g.nx[e] : g.ny[e], nd2 = d2 == 0 ? g.nx[e] : g.ny[e];
+            double spen = 0, sadv = 0;
+            bool inter = Qsn[e] != nullptr;
+            for (int q = 0; q < NFQ; ++q) {
+                double ff = ldg(&R.fw[q]) * ldg(&R.ephi[(e * NFQ + q) * MU + a]) * ldg(&R.ephi[(e * NFQ + q) * MU + b]);
+                spen += ff;
+                if (inter) sadv += ff * (0.5 * qsn[e * NFQ + q] - dup * fabs(qsn[e * NFQ + q]));
+            }
+            F += -alpha * nd * nd2 * spen;
+            if (inter && d == d2) F += g.h[e] * sadv;
+        }
+        out[0][i] = ((r == x) ? g.detJ : 0.0) - c * F;
+    }
+    for (int e = 0; e < 3; ++e) {
+        TFOR(i, NU * NU) {
+            double v = 0;
+            if (Qsn[e]) {
+                int r = i / NU, x = i % NU, d = r / MU, a = r % MU, d2 = x / MU, b = x % MU;
+                int eo = nbr_edge[e];
+                double nd = d == 0 ? g.nx[e] : g.ny[e], nd2 = d2 == 0 ? g.nx[e] : g.ny[e];
+                double spen = 0, sadv = 0;
+                for (int q = 0; q < NFQ; ++q) {
+                    double ff = ldg(&R.fw[q]) * ldg(&R.ephi[(e * NFQ + q) * MU + a]) *
+                                ldg(&R.ephi[(eo * NFQ + (NFQ - 1 - q)) * MU + b]);
+                    spen += ff;
+                    sadv += ff * (-0.5 * qsn[e * NFQ + q] + dup * fabs(qsn[e * NFQ + q]));
+                }
+                double F = alpha * nd * nd2 * spen + ((d == d2) ? g.h[e] * sadv : 0.0);
+                v = -c * F;
+            }
+            out[1 + e][i] = v;
+        }
+    }
+    tm.sync();
+}
+
+// In-place inverse of an n x n row-major matrix A (Gauss-Jordan, partial pivoting) with the
+// team; Inv receives the inverse. Scratch: 1 int (pivot). Returns false if singular.
+template <int N>
+__host__ __device__ bool team_invert(const Team &tm, double *A, double *Inv, int *piv_sm) {
+    TFOR(i, N * N) Inv[i] = (i / N == i % N) ? 1.0 : 0.0;
+    tm.sync();
+    bool ok = true;
+    for (int col = 0; col < N; ++col) {
+        if (tm.tid == 0) {
+            int p = col;
+            double best = fabs(A[col * N + col]);
+            for (int r = col + 1; r < N; ++r)
+                if (fabs(A[r * N + col]) > best) { best = fabs(A[r * N + col]); p = r; }
+            *piv_sm = (best > 0.0) ? p : -1;
+        }
+        tm.sync();
+        int p = *piv_sm;
+        if (p < 0) { ok = false; break; }
+        if (p != col) {
+            TFOR(j, N) {
+                double t = A[col * N + j]; A[col * N + j] = A[p * N + j]; A[p * N + j] = t;
+                t = Inv[col * N + j]; Inv[col * N + j] = Inv[p * N + j]; Inv[p * N + j] = t;
+            }
+            tm.sync();
+        }
+        double inv_d = 1.0 / A[col * N + col];
+        tm.sync();
+        TFOR(j, N) { A[col * N + j] *= inv_d; Inv[col * N + j] *= inv_d; }
+        tm.sync();
+        TFOR(i, (N - 1) * N) {
+            int r = i / N, j = i % N;
+            if (r >= col) ++r;
+            double f = A[r * N + col];
+            if (j != col) A[r * N + j] -= f * A[col * N + j];
+            Inv[r * N + j] -= f * Inv[col * N + j];
+        }
+        tm.sync();
+        TFOR(r, N) if (r != col) A[r * N + col] = 0.0;
+        tm.sync();
+    }
+    return ok;
+}
+
+}  // namespace hdg

@@ -1,0 +1,882 @@
+// CUDA kernels of the HDG stage solver (sm_103a).
+//
+// Layouts (FP64):
+//  * velocity-like vectors: [cell][NU], modal (hdg_cell.cuh); pressure [cell][NP];
+//    trace [facet][NT] (Legendre, canonical facet direction).
+//  * trace operator S = sum_K S_K in ELL form with 5 block columns per facet row block
+//    (the facet itself and the two other facets of each side cell):
+//        Sell[((b*NT + col) * nrows) + f*NT + row],  tcol[b*nfacets + f] (facet or -1);
+//    a warp reads 32 consecutive rows of one (b, col) slice: fully coalesced.
+//  * tentative-velocity operator M - cF in ELL form with 4 block columns per cell (the cell and
+//    its three neighbours): Bell[((b*NU + col) * nrowsQ) + cell*NU + row].
+//  * block-Jacobi inverses: Dinv[col*nrows + f*NT + row], Binv[col*nrowsQ + cell*NU + row].
+// Reductions are deterministic: each block writes a partial, the last block to finish (atomic
+// ticket, no waiting) sums the partials in a fixed order and updates the solver scalars.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "hdg_cell.cuh"
+
+namespace hdg {
+
+constexpr int VEC_THREADS = 256;
+constexpr int MAX_RED_BLOCKS = 2048;
+
+struct Scalars {
+    double rz, rz0, pAp, alpha, beta, omega, rho, bnorm, rr, rv, ts, tt;
+    double bmean, red0, red1, red2;
+    int done, iters, breakdown, maxit;
+    double rtol, relres;
+};
+
+struct RedBuf {
+    double *partials;
+    unsigned int *counter;
+};
+
+// ------------------------------------------------------------------ block / grid reductions
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[32]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double x = v[i];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[i][warp] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double x = (lane < nw) ? sh[i][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            v[i] = x;                                   // valid in thread 0
+        }
+    }
+    __syncthreads();
+}
+
+// Returns true in thread 0 of the last block, with the grid totals in tot.
+template <int NV>
+__device__ bool grid_sum(const RedBuf rb, double (&v)[NV], double (&tot)[NV]) {
+    __shared__ double sh[NV][32];
+    __shared__ int last;
+    block_sum<NV>(v, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) rb.partials[blockIdx.x * NV + i] = v[i];
+        __threadfence();
+        unsigned t = atomicAdd(rb.counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] += __ldcg(&rb.partials[b * NV + i]);
+    block_sum<NV>(acc, sh);
+    if (threadIdx.x == 0) {
+        *rb.counter = 0u;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) tot[i] = acc[i];
+        return true;
+    }
+    return false;
+}
+
+inline int red_grid(long long n) {
+    long long g = (n + VEC_THREADS - 1) / VEC_THREADS;
+    if (g < 1) g = 1;
+    if (g > MAX_RED_BLOCKS) g = MAX_RED_BLOCKS;
+    return (int)g;
+}
+
+#define GRID_STRIDE(i, n) for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
+
+// ------------------------------------------------------------------ nodal <-> modal
+// out[item][blk][a] = sum_n T[a][n] in[item][blk][n]  (T is n x n)
+__global__ void k_basis_change(const double *__restrict__ T, int n, const double *__restrict__ in,
+                               double *__restrict__ out, long long nvec) {
+    GRID_STRIDE(i, nvec * n) {
+        long long v = i / n;
+        int a = (int)(i % n);
+        double s = 0;
+        for (int m = 0; m < n; ++m) s += __ldg(&T[a * n + m]) * in[v * n + m];
+        out[i] = s;
+    }
+}
+
+// dual <-> Riesz on V_Q: M = detJ I per cell. mode 0: out = detJ * in; mode 1: out = in / detJ.
+__global__ void k_mass_scale(const CellGeo *__restrict__ geo, int nu, const double *in, double *out,
+                             long long ncells, int mode) {
+    GRID_STRIDE(i, ncells * nu) {
+        double dj = geo[i / nu].detJ;
+        out[i] = mode == 0 ? in[i] * dj : in[i] / dj;
+    }
+}
+
+// trace dual -> Riesz: facet mass h_F I
+__global__ void k_trace_riesz(const CellGeo *__restrict__ geo, const int *__restrict__ facet_cell,
+                              const int *__restrict__ facet_edge, int nt, const double *in,
+                              double *out, long long nfacets) {
+    GRID_STRIDE(i, nfacets * nt) {
+        long long f = i / nt;
+        int c = facet_cell[2 * f], e = facet_edge[2 * f];
+        out[i] = in[i] / geo[c].h[e];
+    }
+}
+
+// out = sum_t coef[t] * (mass[t] ? detJ : 1) * vec[t]   (up to 12 terms; vec may alias out
+// only for t = 0 when out is written after all reads of the element)
+struct LinComb {
+    int nterms;
+    double coef[12];
+    const double *vec[12];
+    int mass[12];
+};
+__global__ void k_lincomb(const CellGeo *__restrict__ geo, int nu, LinComb L, double *out, long long ncells) {
+    GRID_STRIDE(i, ncells * nu) {
+        double dj = geo[i / nu].detJ;
+        double s = 0;
+        for (int t = 0; t < L.nterms; ++t) s += L.coef[t] * (L.mass[t] ? dj : 1.0) * L.vec[t][i];
+        out[i] = s;
+    }
+}
+
+__global__ void k_axpby(double a, const double *x, double b, double *y, long long n) {
+    GRID_STRIDE(i, n) y[i] = a * x[i] + b * y[i];
+}
+
+// ------------------------------------------------------------------ condensation (CTA / cell)
+template <int K>
+__global__ void k_condense(RefDev R, MeshDev M, double c, double tau, double *Scell, double *Zc,
+                           double *Ac) {
+    typedef Dims<K> Dm;
+    extern __shared__ double sm[];
+    const int cell = blockIdx.x;
+    if (cell >= M.ncells) return;
+    Team tm{(int)threadIdx.x, (int)blockDim.x};
+    CellGeo g = M.geo[cell];
+    int flip[3] = {M.cell_flip[3 * cell], M.cell_flip[3 * cell + 1], M.cell_flip[3 * cell + 2]};
+    cell_condense<K>(tm, R, g, flip, c, tau, sm, Scell + (size_t)cell * Dm::NL * Dm::NL,
+                     Zc + (size_t)cell * Dm::NP * Dm::NL, Ac + (size_t)cell * Dm::NP * Dm::NP);
+}
+
+// Assemble the ELL trace operator and its facet-block-Jacobi inverse (thread / facet).
+template <int NT>
+__global__ void k_assemble_trace(MeshDev M, const double *__restrict__ Scell, double *Sell,
+                                 int *tcol, double *Dinv) {
+    const int NL = 3 * NT;
+    GRID_STRIDE(fl, M.nfacets) {
+        int f = (int)fl;
+        long long nrows = (long long)M.nfacets * NT;
+        double blk[5][NT][NT];
+        int col[5];
+        for (int b = 0; b < 5; ++b) {
+            col[b] = -1;
+            for (int i = 0; i < NT; ++i)
+                for (int j = 0; j < NT; ++j) blk[b][i][j] = 0.0;
+        }
+        col[0] = f;
+        for (int s = 0; s < 2; ++s) {
+            int c = M.facet_cell[2 * f + s];
+            if (c < 0) continue;
+            int e = M.facet_edge[2 * f + s];
+            const double *S = Scell + (size_t)c * NL * NL;
+            int ob = 1 + 2 * s;
+            for (int e2 = 0; e2 < 3; ++e2) {
+                int b = (e2 == e) ? 0 : ob++;
+                if (b != 0) col[b] = M.cell_facet[3 * c + e2];
+                for (int i = 0; i < NT; ++i)
+                    for (int j = 0; j < NT; ++j) blk[b][i][j] += S[(e * NT + i) * NL + e2 * NT + j];
+            }
+        }
+        for (int b = 0; b < 5; ++b) {
+            tcol[b * M.nfacets + f] = col[b];
+            for (int j = 0; j < NT; ++j)
+                for (int i = 0; i < NT; ++i) Sell[((size_t)(b * NT + j)) * nrows + (size_t)f * NT + i] = blk[b][i][j];
+        }
+        // inverse of the diagonal block (symmetric positive definite): Gauss-Jordan
+        double A[NT][NT], I[NT][NT];
+        for (int i = 0; i < NT; ++i)
+            for (int j = 0; j < NT; ++j) { A[i][j] = blk[0][i][j]; I[i][j] = (i == j) ? 1.0 : 0.0; }
+        for (int k = 0; k < NT; ++k) {
+            double d = 1.0 / A[k][k];
+            for (int j = 0; j < NT; ++j) { A[k][j] *= d; I[k][j] *= d; }
+            for (int i = 0; i < NT; ++i) {
+                if (i == k) continue;
+                double t = A[i][k];
+                for (int j = 0; j < NT; ++j) { A[i][j] -= t * A[k][j]; I[i][j] -= t * I[k][j]; }
+            }
+        }
+        for (int j = 0; j < NT; ++j)
+            for (int i = 0; i < NT; ++i) Dinv[(size_t)j * nrows + (size_t)f * NT + i] = I[i][j];
+    }
+}
+
+// y = S x (ELL, thread / row)
+template <int NT>
+__global__ void k_trace_apply(const double *__restrict__ Sell, const int *__restrict__ tcol,
+                              const double *__restrict__ x, double *__restrict__ y, int nfacets) {
+    long long nrows = (long long)nfacets * NT;
+    GRID_STRIDE(g, nrows) {
+        int f = (int)(g / NT);
+        double s = 0;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+            int cf = __ldg(&tcol[b * nfacets + f]);
+            if (cf < 0) continue;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) s += __ldg(&Sell[(size_t)(b * NT + j) * nrows + g]) * x[(size_t)cf * NT + j];
+        }
+        y[g] = s;
+    }
+}
+
+// ------------------------------------------------------------------ trace CG
+// b -> sum of b_F[0] (constant-mode content), for the null-space projection
+template <int NT>
+__global__ void k_trace_mean(const double *__restrict__ b, int nfacets, RedBuf rb, Scalars *sc) {
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(f, nfacets) v[0] += b[(size_t)f * NT];
+    if (grid_sum<1>(rb, v, tot)) sc->bmean = tot[0] / nfacets;
+}
+
+// r = b - mean e0, x = 0, pold = 0, z = Dinv r; rz = (r, z)
+template <int NT>
+__global__ void k_cg_setup(const double *__restrict__ b, const double *__restrict__ Dinv, double *x,
+                           double *r, double *z, double *pold, int nfacets, RedBuf rb, Scalars *sc,
+                           double rtol, int maxit) {
+    long long nrows = (long long)nfacets * NT;
+    const double mean = sc->bmean;
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(f, nfacets) {
+        double rl[NT];
+        for (int i = 0; i < NT; ++i) {
+            rl[i] = b[f * NT + i] - (i == 0 ? mean : 0.0);
+            r[f * NT + i] = rl[i];
+            x[f * NT + i] = 0.0;
+            pold[f * NT + i] = 0.0;
+        }
+        for (int i = 0; i < NT; ++i) {
+            double s = 0;
+            for (int j = 0; j < NT; ++j) s += __ldg(&Dinv[(size_t)j * nrows + f * NT + i]) * rl[j];
+            z[f * NT + i] = s;
+            v[0] += s * rl[i];
+        }
+    }
+    if (grid_sum<1>(rb, v, tot)) {
+        sc->rz = tot[0];
+        sc->rz0 = tot[0];
+        sc->beta = 0.0;
+        sc->iters = 0;
+        sc->breakdown = 0;
+        sc->rtol = rtol;
+        sc->maxit = maxit;
+        sc->relres = tot[0] > 0.0 ? 1.0 : 0.0;
+        sc->done = !(tot[0] > 0.0);
+        if (!isfinite(tot[0])) { sc->done = 1; sc->breakdown = 2; }
+    }
+}
+
+// pnew = z + beta pold; Ap = S pnew; pAp -> alpha = rz / pAp
+template <int NT>
+__global__ void k_cg_apply(const double *__restrict__ Sell, const int *__restrict__ tcol,
+                           const double *__restrict__ z, const double *__restrict__ pold,
+                           double *__restrict__ pnew, double *__restrict__ Ap, int nfacets,
+                           RedBuf rb, Scalars *sc) {
+    if (sc->done) return;
+    const double beta = sc->beta;
+    long long nrows = (long long)nfacets * NT;
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(g, nrows) {
+        int f = (int)(g / NT);
+        double s = 0;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+            int cf = __ldg(&tcol[b * nfacets + f]);
+            if (cf < 0) continue;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                size_t k = (size_t)cf * NT + j;
+                s += __ldg(&Sell[(size_t)(b * NT + j) * nrows + g]) * (z[k] + beta * pold[k]);
+            }
+        }
+        double pn = z[g] + beta * pold[g];
+        pnew[g] = pn;
+        Ap[g] = s;
+        v[0] += pn * s;
+    }
+    if (grid_sum<1>(rb, v, tot)) {
+        sc->pAp = tot[0];
+        if (tot[0] > 0.0 && isfinite(tot[0])) sc->alpha = sc->rz / tot[0];
+        else { sc->alpha = 0.0; sc->done = 1; sc->breakdown = isfinite(tot[0]) ? 1 : 2; }
+    }
+}
+
+// x += alpha p; r -= alpha Ap; z = Dinv r; rz_new -> beta, convergence
+template <int NT>
+__global__ void k_cg_update(const double *__restrict__ Dinv, const double *__restrict__ p,
+                            const double *__restrict__ Ap, double *x, double *r, double *z,
+                            int nfacets, RedBuf rb, Scalars *sc) {
+    if (sc->done) return;
+    const double alpha = sc->alpha;
+    long long nrows = (long long)nfacets * NT;
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(f, nfacets) {
+        double rl[NT];
+        for (int i = 0; i < NT; ++i) {
+            size_t g = f * NT + i;
+            x[g] += alpha * p[g];
+            rl[i] = r[g] - alpha * Ap[g];
+            r[g] = rl[i];
+        }
+        for (int i = 0; i < NT; ++i) {
+            double s = 0;
+            for (int j = 0; j < NT; ++j) s += __ldg(&Dinv[(size_t)j * nrows + f * NT + i]) * rl[j];
+            z[f * NT + i] = s;
+            v[0] += s * rl[i];
+        }
+    }
+    if (grid_sum<1>(rb, v, tot)) {
+        double rz_new = tot[0];
+        sc->beta = rz_new / sc->rz;
+        sc->rz = rz_new;
+        sc->iters += 1;
+        double rel = sc->rz0 > 0 ? sqrt(fmax(rz_new, 0.0) / sc->rz0) : 0.0;
+        sc->relres = rel;
+        if (!isfinite(rz_new)) { sc->done = 1; sc->breakdown = 2; }
+        else if (rel <= sc->rtol || sc->iters >= sc->maxit) sc->done = 1;
+    }
+}
+
+// ------------------------------------------------------------------ Step-II per-cell kernels
+template <int K>
+__device__ __forceinline__ void gather_trace_local(const MeshDev &M, int cell, const double *lam,
+                                                   double *lK, const Team &tm) {
+    constexpr int NT = Dims<K>::NT;
+    TFOR(i, 3 * NT) {
+        int e = i / NT, j = i % NT;
+        int f = M.cell_facet[3 * cell + e];
+        lK[i] = lam ? tsign(M.cell_flip[3 * cell + e], j) * lam[(size_t)f * NT + j] : 0.0;
+    }
+    tm.sync();
+}
+
+template <int K>
+__global__ void k_mixed_rhs(RefDev R, MeshDev M, double tau, const double *Ru, const double *X,
+                            const double *p, const double *lam, const double *Rp_add,
+                            const double *__restrict__ Zc, double *v, double *w) {
+    typedef Dims<K> Dm;
+    constexpr int SCR = Dm::NL + 4 * Dm::MU + Dm::NP + Dm::NL;
+    extern __shared__ double sm[];
+    const int warp = threadIdx.x >> 5;
+    const int cell = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (cell >= M.ncells) return;
+    Team tm{(int)(threadIdx.x & 31), 32};
+    double *mine = sm + warp * SCR;
+    double *lK = mine;
+    gather_trace_local<K>(M, cell, lam, lK, tm);
+    CellGeo g = M.geo[cell];
+    int flip[3] = {M.cell_flip[3 * cell], M.cell_flip[3 * cell + 1], M.cell_flip[3 * cell + 2]};
+    cell_mixed_rhs<K>(tm, R, g, flip, tau, Ru ? Ru + (size_t)cell * Dm::NU : nullptr,
+                      X ? X + (size_t)cell * Dm::NU : nullptr, p ? p + (size_t)cell * Dm::NP : nullptr,
+                      lam ? lK : nullptr, Rp_add ? Rp_add + (size_t)cell * Dm::NP : nullptr,
+                      Zc + (size_t)cell * Dm::NP * Dm::NL, mine + Dm::NL,
+                      v + (size_t)cell * Dm::NL, w + (size_t)cell * Dm::NP);
+}
+
+// b_F = sum over the facet's cells of v_K (canonical rows of the facet's local edge) - sub_F
+template <int NT>
+__global__ void k_facet_gather(MeshDev M, const double *__restrict__ v, const double *sub, double *b) {
+    GRID_STRIDE(g, (long long)M.nfacets * NT) {
+        int f = (int)(g / NT), j = (int)(g % NT);
+        double s = sub ? -sub[g] : 0.0;
+        for (int side = 0; side < 2; ++side) {
+            int c = M.facet_cell[2 * f + side];
+            if (c < 0) continue;
+            s += v[(size_t)c * 3 * NT + M.facet_edge[2 * f + side] * NT + j];
+        }
+        b[g] = s;
+    }
+}
+
+template <int K>
+__global__ void k_mixed_backsub(RefDev R, MeshDev M, double c, const double *Ru,
+                                const double *__restrict__ w, const double *lam,
+                                const double *__restrict__ Zc, const double *__restrict__ Ac,
+                                double *U, double *p) {
+    typedef Dims<K> Dm;
+    constexpr int SCR = Dm::NL + Dm::NP;
+    extern __shared__ double sm[];
+    const int warp = threadIdx.x >> 5;
+    const int cell = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (cell >= M.ncells) return;
+    Team tm{(int)(threadIdx.x & 31), 32};
+    double *lK = sm + warp * SCR;
+    gather_trace_local<K>(M, cell, lam, lK, tm);
+    CellGeo g = M.geo[cell];
+    cell_mixed_backsub<K>(tm, R, g, c, Ru ? Ru + (size_t)cell * Dm::NU : nullptr,
+                          w + (size_t)cell * Dm::NP, lK, Zc + (size_t)cell * Dm::NP * Dm::NL,
+                          Ac + (size_t)cell * Dm::NP * Dm::NP, lK + Dm::NL,
+                          U + (size_t)cell * Dm::NU, p + (size_t)cell * Dm::NP);
+}
+
+// ------------------------------------------------------------------ BDM projection (warp / cell)
+template <int K>
+__global__ void k_bdm(RefDev R, MeshDev M, const double *Q, double *Qs) {
+    typedef Dims<K> Dm;
+    constexpr int SCR = 2 * Dm::NU;
+    extern __shared__ double sm[];
+    const int warp = threadIdx.x >> 5;
+    const int cell = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (cell >= M.ncells) return;
+    Team tm{(int)(threadIdx.x & 31), 32};
+    CellGeo g = M.geo[cell];
+    const double *Qn[3];
+    int ne[3];
+    for (int e = 0; e < 3; ++e) {
+        int o = M.cell_nbr[3 * cell + e];
+        Qn[e] = o >= 0 ? Q + (size_t)o * Dm::NU : nullptr;
+        ne[e] = M.cell_nbr_edge[3 * cell + e];
+    }
+    cell_bdm<K>(tm, R, g, Q + (size_t)cell * Dm::NU, Qn, ne, sm + warp * SCR, Qs + (size_t)cell * Dm::NU);
+}
+
+// ------------------------------------------------------------------ tentative-velocity operator
+template <int K>
+constexpr int fimpl_smem_doubles() {
+    typedef Dims<K> Dm;
+    return 2 * Dm::NQ + 3 * Dm::NFQ + Dm::MU * Dm::MU + 4 * Dm::NU * Dm::NU + Dm::NU * Dm::NU + 2;
+}
+
+template <int K>
+__global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c, double alpha,
+                                 double dup, double *Bell, double *Binv, int *status) {
+    typedef Dims<K> Dm;
+    constexpr int NU = Dm::NU;
+    extern __shared__ double sm[];
+    const int cell = blockIdx.x;
+    if (cell >= M.ncells) return;
+    Team tm{(int)threadIdx.x, (int)blockDim.x};
+    CellGeo g = M.geo[cell];
+    const double *Qn[3];
+    int ne[3];
+    for (int e = 0; e < 3; ++e) {
+        int o = M.cell_nbr[3 * cell + e];
+        Qn[e] = o >= 0 ? Qs + (size_t)o * NU : nullptr;
+        ne[e] = M.cell_nbr_edge[3 * cell + e];
+    }
+    double *blk = sm + 2 * Dm::NQ + 3 * Dm::NFQ + Dm::MU * Dm::MU;
+    double *outp[4] = {blk, blk + NU * NU, blk + 2 * NU * NU, blk + 3 * NU * NU};
+    cell_fimpl_blocks<K>(tm, R, g, Qs + (size_t)cell * NU, Qn, ne, c, alpha, dup, sm, outp);
+    const long long nrows = (long long)M.ncells * NU;
+    for (int b = 0; b < 4; ++b)
+        TFOR(i, NU * NU) {
+            int col = i / NU, row = i % NU;
+            Bell[((size_t)(b * NU + col)) * nrows + (size_t)cell * NU + row] = outp[b][row * NU + col];
+        }
+    tm.sync();
+    double *inv = blk + 4 * NU * NU;
+    int *piv = (int *)(inv + NU * NU);
+    // the diagonal block is consumed by the inversion (outp[0] in place)
+    bool ok = team_invert<NU>(tm, outp[0], inv, piv);
+    TFOR(i, NU * NU) {
+        int col = i / NU, row = i % NU;
+        Binv[(size_t)col * nrows + (size_t)cell * NU + row] = inv[row * NU + col];
+    }
+    if (!ok && tm.tid == 0) atomicExch(status, 1);
+}
+
+// y = B x (ELL, 4 block columns)
+template <int K>
+__global__ void k_cell_apply(MeshDev M, const double *__restrict__ Bell, const double *__restrict__ x,
+                             double *__restrict__ y) {
+    constexpr int NU = Dims<K>::NU;
+    const long long nrows = (long long)M.ncells * NU;
+    GRID_STRIDE(g, nrows) {
+        int cell = (int)(g / NU);
+        double s = 0;
+        for (int b = 0; b < 4; ++b) {
+            int cc = b == 0 ? cell : __ldg(&M.cell_nbr[3 * cell + b - 1]);
+            if (cc < 0) continue;
+            const double *xc = x + (size_t)cc * NU;
+            const double *Bc = Bell + (size_t)(b * NU) * nrows + g;
+#pragma unroll 6
+            for (int j = 0; j < NU; ++j) s += __ldg(&Bc[(size_t)j * nrows]) * xc[j];
+        }
+        y[g] = s;
+    }
+}
+
+// ------------------------------------------------------------------ restarted GMRES (right block-Jacobi)
+// Krylov basis V (GM_M+1 vectors of n), Hessenberg column / Givens rotations and the residual
+// estimate live in device memory; the last block of each reduction does the small serial
+// updates, so one host read per restart cycle suffices.
+constexpr int GM_M = 30;
+struct GmresState {
+    double H[(GM_M + 1) * GM_M];     // column-major: H[j*(GM_M+1) + i]
+    double cs[GM_M], sn[GM_M], g[GM_M + 1], y[GM_M], hcol[GM_M + 2], h2[GM_M + 2];
+    double bnorm, beta, resid, rtol;
+    int j, cycle_end, converged, total, maxit, breakdown;
+};
+
+// w (local row values) dotted with V_0..V_{nvec-1}: each thread holds its rows' w in a loop
+template <class WF>
+__device__ bool multidot_rows(const RedBuf rb, const double *V, long long n, int nvec, WF wfun, double *out) {
+    __shared__ double sh[1][32];
+    __shared__ int last;
+    for (int i = 0; i < nvec; ++i) {
+        double v[1] = {0.0};
+        GRID_STRIDE(g, n) v[0] += V[(size_t)i * n + g] * wfun(g);
+        block_sum<1>(v, sh);
+        if (threadIdx.x == 0) rb.partials[blockIdx.x * (GM_M + 2) + i] = v[0];
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned t = atomicAdd(rb.counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    for (int i = 0; i < nvec; ++i) {
+        double acc[1] = {0.0};
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc[0] += __ldcg(&rb.partials[b * (GM_M + 2) + i]);
+        block_sum<1>(acc, sh);
+        if (threadIdx.x == 0) out[i] = acc[0];
+    }
+    if (threadIdx.x == 0) *rb.counter = 0u;
+    return threadIdx.x == 0;
+}
+
+// start of a cycle: w = b - B x (x = 0 on the first cycle: w = b); beta = ||w||
+template <int K>
+__global__ void k_gm_start(MeshDev M, const double *__restrict__ Bell, const double *__restrict__ b,
+                           const double *__restrict__ x, double *w, int first, RedBuf rb, GmresState *gs,
+                           double rtol, int maxit) {
+    constexpr int NU = Dims<K>::NU;
+    const long long nrows = (long long)M.ncells * NU;
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(g, nrows) {
+        double s = 0;
+        if (!first) {
+            int cell = (int)(g / NU);
+            for (int bb = 0; bb < 4; ++bb) {
+                int cc = bb == 0 ? cell : __ldg(&M.cell_nbr[3 * cell + bb - 1]);
+                if (cc < 0) continue;
+                const double *xc = x + (size_t)cc * NU;
+                const double *Bc = Bell + (size_t)(bb * NU) * nrows + g;
+                for (int j = 0; j < NU; ++j) s += __ldg(&Bc[(size_t)j * nrows]) * xc[j];
+            }
+        }
+        double r = b[g] - s;
+        w[g] = r;
+        v[0] += r * r;
+    }
+    if (grid_sum<1>(rb, v, tot)) {
+        double beta = sqrt(tot[0]);
+        if (first) {
+            gs->bnorm = beta;
+            gs->total = 0;
+            gs->rtol = rtol;
+            gs->maxit = maxit;
+            gs->converged = 0;
+            gs->breakdown = 0;
+        }
+        gs->beta = beta;
+        gs->resid = beta;
+        for (int i = 0; i <= GM_M; ++i) gs->g[i] = 0.0;
+        gs->g[0] = beta;
+        gs->j = 0;
+        if (!isfinite(beta)) { gs->breakdown = 2; gs->cycle_end = 1; }
+        else if (beta <= rtol * gs->bnorm || beta == 0.0) { gs->converged = 1; gs->cycle_end = 1; }
+        else gs->cycle_end = 0;
+    }
+}
+
+// v_j = w / h (h = beta for j = 0, H[j, j-1] otherwise); z = Binv v_j
+template <int K>
+__global__ void k_gm_precond(const double *__restrict__ Binv, const double *__restrict__ w, double *V,
+                             double *z, long long ncells, const GmresState *gs) {
+    if (gs->cycle_end) return;
+    constexpr int NU = Dims<K>::NU;
+    const int j = gs->j;
+    const double h = j == 0 ? gs->beta : gs->H[(j - 1) * (GM_M + 1) + j];
+    const double inv = 1.0 / h;
+    const long long nrows = ncells * NU;
+    double *vj = V + (size_t)j * nrows;
+    GRID_STRIDE(g, nrows) {
+        long long base = (g / NU) * NU;
+        double acc = 0;
+#pragma unroll 6
+        for (int q = 0; q < NU; ++q) acc += __ldg(&Binv[(size_t)q * nrows + g]) * (w[base + q] * inv);
+        vj[g] = w[g] * inv;
+        z[g] = acc;
+    }
+}
+
+// w = B z; hcol[i] = (V_i, w), i <= j
+template <int K>
+__global__ void k_gm_apply_dot(MeshDev M, const double *__restrict__ Bell, const double *__restrict__ z,
+                               double *__restrict__ w, const double *__restrict__ V, RedBuf rb, GmresState *gs) {
+    if (gs->cycle_end) return;
+    constexpr int NU = Dims<K>::NU;
+    const long long nrows = (long long)M.ncells * NU;
+    GRID_STRIDE(g, nrows) {
+        int cell = (int)(g / NU);
+        double s = 0;
+        for (int bb = 0; bb < 4; ++bb) {
+            int cc = bb == 0 ? cell : __ldg(&M.cell_nbr[3 * cell + bb - 1]);
+            if (cc < 0) continue;
+            const double *zc = z + (size_t)cc * NU;
+            const double *Bc = Bell + (size_t)(bb * NU) * nrows + g;
+#pragma unroll 6
+            for (int q = 0; q < NU; ++q) s += __ldg(&Bc[(size_t)q * nrows]) * zc[q];
+        }
+        w[g] = s;
+    }
+    // w written by this thread only is read back by the same thread below (same g mapping)
+    const int nvec = gs->j + 1;
+    multidot_rows(rb, V, nrows, nvec, [&](long long g) { return w[g]; }, gs->hcol);
+}
+
+// w -= V hcol; h2 = (V_i, w)  (second Gram-Schmidt pass)
+__global__ void k_gm_orth1(double *w, const double *__restrict__ V, long long nrows, RedBuf rb, GmresState *gs) {
+    if (gs->cycle_end) return;
+    const int nvec = gs->j + 1;
+    GRID_STRIDE(g, nrows) {
+        double s = w[g];
+        for (int i = 0; i < nvec; ++i) s -= gs->hcol[i] * V[(size_t)i * nrows + g];
+        w[g] = s;
+    }
+    multidot_rows(rb, V, nrows, nvec, [&](long long g) { return w[g]; }, gs->h2);
+}
+
+// w -= V h2; ||w|| -> H[j+1, j]; Givens rotations; residual estimate
+__global__ void k_gm_orth2(double *w, const double *__restrict__ V, long long nrows, RedBuf rb, GmresState *gs) {
+    if (gs->cycle_end) return;
+    const int j = gs->j, nvec = j + 1;
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(g, nrows) {
+        double s = w[g];
+        for (int i = 0; i < nvec; ++i) s -= gs->h2[i] * V[(size_t)i * nrows + g];
+        w[g] = s;
+        v[0] += s * s;
+    }
+    if (grid_sum<1>(rb, v, tot)) {
+        double *Hc = gs->H + j * (GM_M + 1);
+        for (int i = 0; i <= j; ++i) Hc[i] = gs->hcol[i] + gs->h2[i];
+        double hn = sqrt(tot[0]);
+        Hc[j + 1] = hn;
+        for (int i = 0; i < j; ++i) {                     // previous rotations
+            double a = Hc[i], b2 = Hc[i + 1];
+            Hc[i] = gs->cs[i] * a + gs->sn[i] * b2;
+            Hc[i + 1] = -gs->sn[i] * a + gs->cs[i] * b2;
+        }
+        double a = Hc[j], b2 = Hc[j + 1];
+        double r = sqrt(a * a + b2 * b2);
+        double c_ = r > 0 ? a / r : 1.0, s_ = r > 0 ? b2 / r : 0.0;
+        gs->cs[j] = c_; gs->sn[j] = s_;
+        Hc[j] = r;
+        Hc[j + 1] = 0.0;
+        gs->g[j + 1] = -s_ * gs->g[j];
+        gs->g[j] = c_ * gs->g[j];
+        gs->resid = fabs(gs->g[j + 1]);
+        gs->total += 1;
+        // keep H[j+1, j] (the norm) for the next v; stored separately in hcol[GM_M+1]
+        gs->H[j * (GM_M + 1) + j + 1] = hn;            // restored after the rotation (used by k_gm_precond)
+        gs->hcol[GM_M + 1] = hn;
+        gs->j = j + 1;
+        if (!isfinite(gs->resid)) { gs->breakdown = 2; gs->cycle_end = 1; }
+        else if (gs->resid <= gs->rtol * gs->bnorm) { gs->converged = 1; gs->cycle_end = 1; }
+        else if (gs->j >= GM_M || gs->total >= gs->maxit || hn == 0.0) gs->cycle_end = 1;
+    }
+}
+
+// y = R^{-1} g (upper triangular part of the rotated H, without the subdiagonal)
+__global__ void k_gm_solve(GmresState *gs, const double *Hdiag_unused) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int m = gs->j;
+    for (int i = m - 1; i >= 0; --i) {
+        double s = gs->g[i];
+        for (int k = i + 1; k < m; ++k) s -= gs->H[k * (GM_M + 1) + i] * gs->y[k];
+        double d = gs->H[i * (GM_M + 1) + i];
+        gs->y[i] = d != 0.0 ? s / d : 0.0;
+    }
+}
+
+// u = V y (rows), then x += Binv u (cell-local)
+__global__ void k_gm_combine(const double *__restrict__ V, double *u, long long nrows, const GmresState *gs) {
+    const int m = gs->j;
+    GRID_STRIDE(g, nrows) {
+        double s = 0;
+        for (int i = 0; i < m; ++i) s += gs->y[i] * V[(size_t)i * nrows + g];
+        u[g] = s;
+    }
+}
+
+template <int K>
+__global__ void k_gm_update_x(const double *__restrict__ Binv, const double *__restrict__ u, double *x,
+                              long long ncells, int first) {
+    constexpr int NU = Dims<K>::NU;
+    const long long nrows = ncells * NU;
+    GRID_STRIDE(g, nrows) {
+        long long base = (g / NU) * NU;
+        double acc = 0;
+#pragma unroll 6
+        for (int q = 0; q < NU; ++q) acc += __ldg(&Binv[(size_t)q * nrows + g]) * u[base + q];
+        x[g] = (first ? 0.0 : x[g]) + acc;
+    }
+}
+
+// ------------------------------------------------------------------ Richardson pieces
+// dr = sgn * (r - BQ + c (D^T p - E^T l))   (warp / cell; BQ precomputed; r may be null)
+template <int K>
+__global__ void k_rich_residual(RefDev R, MeshDev M, double c, const double *r, const double *BQ,
+                                const double *p, const double *lam, double *dr, double sgn) {
+    typedef Dims<K> Dm;
+    constexpr int MU = Dm::MU, NU = Dm::NU, NP = Dm::NP, NT = Dm::NT, NL = Dm::NL;
+    constexpr int SCR = NL;
+    extern __shared__ double sm[];
+    const int warp = threadIdx.x >> 5;
+    const int cell = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (cell >= M.ncells) return;
+    Team tm{(int)(threadIdx.x & 31), 32};
+    double *lK = sm + warp * SCR;
+    gather_trace_local<K>(M, cell, lam, lK, tm);
+    CellGeo g = M.geo[cell];
+    const double *pK = p + (size_t)cell * NP;
+    TFOR(x, NU) {
+        int d = x / MU, a = x % MU;
+        double et = 0;
+        for (int e = 0; e < 3; ++e) {
+            double nd = d == 0 ? g.nx[e] : g.ny[e];
+            double s = 0;
+            for (int j = 0; j < NT; ++j) s += ldg(&R.Ehat[(e * NT + j) * MU + a]) * lK[e * NT + j];
+            et += g.h[e] * nd * s;
+        }
+        double dt = 0;
+        for (int rr = 0; rr < 2; ++rr) {
+            double s = 0;
+            for (int b = 0; b < NP; ++b) s += ldg(&R.Dhat[(rr * NP + b) * MU + a]) * pK[b];
+            dt += g.Jinv[rr * 2 + d] * s;
+        }
+        size_t gi = (size_t)cell * NU + x;
+        dr[gi] = sgn * ((r ? r[gi] : 0.0) - BQ[gi] + c * (g.detJ * dt - et));
+    }
+}
+
+
+// Constraint rows of the stage operator: yp (per cell) and the cells' mu-row contributions
+// (gathered per facet by k_facet_gather).
+template <int K>
+__global__ void k_constraint(RefDev R, MeshDev M, double tau, const double *Q, const double *p,
+                             const double *lam, double *yp, double *v) {
+    typedef Dims<K> Dm;
+    constexpr int SCR = Dm::NL + 2 * Dm::MU;
+    extern __shared__ double sm[];
+    const int warp = threadIdx.x >> 5;
+    const int cell = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (cell >= M.ncells) return;
+    Team tm{(int)(threadIdx.x & 31), 32};
+    double *lK = sm + warp * SCR;
+    gather_trace_local<K>(M, cell, lam, lK, tm);
+    CellGeo g = M.geo[cell];
+    int flip[3] = {M.cell_flip[3 * cell], M.cell_flip[3 * cell + 1], M.cell_flip[3 * cell + 2]};
+    cell_constraint<K>(tm, R, g, flip, tau, Q + (size_t)cell * Dm::NU, p + (size_t)cell * Dm::NP, lK,
+                       lK + Dm::NL, yp + (size_t)cell * Dm::NP, v + (size_t)cell * Dm::NL);
+}
+
+// --------------------------------------------------------------- generic (flexible) GMRES pieces
+// beta = ||r||, g = beta e1 (cycle start on an already formed residual r)
+__global__ void k_vec_start(const double *__restrict__ r, long long n, int first, RedBuf rb, GmresState *gs,
+                            double rtol, int maxit) {
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(i, n) v[0] += r[i] * r[i];
+    if (grid_sum<1>(rb, v, tot)) {
+        double beta = sqrt(tot[0]);
+        if (first) {
+            gs->total = 0; gs->rtol = rtol; gs->maxit = maxit; gs->converged = 0; gs->breakdown = 0;
+            if (first == 1) gs->bnorm = beta;           // first == 2: bnorm set by the caller
+        }
+        gs->beta = beta;
+        gs->resid = beta;
+        for (int i = 0; i <= GM_M; ++i) gs->g[i] = 0.0;
+        gs->g[0] = beta;
+        gs->j = 0;
+        if (!isfinite(beta)) { gs->breakdown = 2; gs->cycle_end = 1; }
+        else if (beta <= rtol * gs->bnorm || beta == 0.0) { gs->converged = 1; gs->cycle_end = 1; }
+        else gs->cycle_end = 0;
+    }
+}
+
+__global__ void k_vec_norm_into(const double *__restrict__ b, long long n, RedBuf rb, GmresState *gs) {
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(i, n) v[0] += b[i] * b[i];
+    if (grid_sum<1>(rb, v, tot)) gs->bnorm = sqrt(tot[0]);
+}
+
+// V_j = w / h  (h = beta for j = 0, else H[j, j-1])
+__global__ void k_vec_normalize(const double *__restrict__ w, double *V, long long n, const GmresState *gs) {
+    if (gs->cycle_end) return;
+    const int j = gs->j;
+    const double h = j == 0 ? gs->beta : gs->H[(j - 1) * (GM_M + 1) + j];
+    const double inv = 1.0 / h;
+    double *vj = V + (size_t)j * n;
+    GRID_STRIDE(i, n) vj[i] = w[i] * inv;
+}
+
+// hcol = V^T w over V_0..V_j
+__global__ void k_vec_dot(const double *__restrict__ w, const double *__restrict__ V, long long n, RedBuf rb,
+                          GmresState *gs) {
+    if (gs->cycle_end) return;
+    multidot_rows(rb, V, n, gs->j + 1, [&](long long g) { return w[g]; }, gs->hcol);
+}
+
+// x += u
+__global__ void k_vec_add(const double *__restrict__ u, double *x, long long n) {
+    GRID_STRIDE(i, n) x[i] += u[i];
+}
+
+// Q += Qbar + U; p += dp; l += dl; norms ||Qbar+U||_M^2, ||Q||_M^2
+template <int K>
+__global__ void k_rich_update(MeshDev M, double *Q, const double *Qbar, const double *U, double *p,
+                              const double *dp, double *lam, const double *dl, RedBuf rb, Scalars *sc) {
+    typedef Dims<K> Dm;
+    double v[2] = {0.0, 0.0}, tot[2];
+    const long long nQ = (long long)M.ncells * Dm::NU;
+    GRID_STRIDE(i, nQ) {
+        double dj = M.geo[i / Dm::NU].detJ;
+        double dq = Qbar[i] + U[i];
+        double q = Q[i] + dq;
+        Q[i] = q;
+        v[0] += dj * dq * dq;
+        v[1] += dj * q * q;
+    }
+    GRID_STRIDE(i, (long long)M.ncells * Dm::NP) p[i] += dp[i];
+    GRID_STRIDE(i, (long long)M.nfacets * Dm::NT) lam[i] += dl[i];
+    if (grid_sum<2>(rb, v, tot)) { sc->red0 = tot[0]; sc->red1 = tot[1]; }
+}
+
+// (p)_Omega: sum_K detJ p_K0 * int_T phi_0 = detJ p_K0 / sqrt(2)
+template <int K>
+__global__ void k_p_integral(MeshDev M, const double *p, RedBuf rb, Scalars *sc) {
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(cl, M.ncells) v[0] += M.geo[cl].detJ * p[(size_t)cl * Dims<K>::NP] * 0.70710678118654752440;
+    if (grid_sum<1>(rb, v, tot)) sc->red2 = tot[0];
+}
+
+// p -= m (constant), lam -= m, with m = (p)_Omega / area
+template <int K>
+__global__ void k_p_shift(MeshDev M, double area, double *p, double *lam, const Scalars *sc) {
+    const double m = sc->red2 / area;
+    GRID_STRIDE(cl, M.ncells) p[(size_t)cl * Dims<K>::NP] -= m * 0.70710678118654752440;   // m = (m/sqrt2) phi_0
+    if (lam) GRID_STRIDE(f, M.nfacets) lam[(size_t)f * Dims<K>::NT] -= m;
+}
+
+}  // namespace hdg

@@ -1,0 +1,1118 @@
+// Host orchestration and C-ABI of the GB300 HDG IMEX stage solver (include/hdg.h).
+//
+// Every step of the path runs in the kernels of hdg_kernels.cuh; the host only sequences
+// launches on the context's stream and reads back solver scalars between chunks of Krylov
+// iterations (convergence tests).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/hdg.h"
+#include "hdg_kernels.cuh"
+#include "mesh.h"
+#include "refelem.h"
+
+using namespace hdg;
+
+namespace {
+thread_local std::string g_last_error;
+
+struct CudaError : std::runtime_error {
+    explicit CudaError(const std::string &s) : std::runtime_error(s) {}
+};
+struct OomError : std::runtime_error {
+    explicit OomError(const std::string &s) : std::runtime_error(s) {}
+};
+
+#define CK(x)                                                                                  \
+    do {                                                                                       \
+        cudaError_t e_ = (x);                                                                  \
+        if (e_ != cudaSuccess) {                                                               \
+            if (e_ == cudaErrorMemoryAllocation) throw OomError(cudaGetErrorString(e_));       \
+            throw CudaError(std::string(#x) + ": " + cudaGetErrorString(e_));                  \
+        }                                                                                      \
+    } while (0)
+#define CKL() CK(cudaGetLastError())
+
+// IMEX tableaus (Alg. 1 form: stage 0 explicit, a_im[i][0] = b_im[0] = 0).
+struct Tab {
+    int s = 0;
+    double Ae[4][4] = {}, Ai[4][4] = {}, be[4] = {}, bi[4] = {}, c[4] = {};
+};
+
+Tab make_tableau(int which) {
+    Tab T;
+    if (which == HDG_ARS222) {              // Ascher, Ruuth & Spiteri (1997), (2,2,2)
+        double g = 1.0 - 1.0 / std::sqrt(2.0), d = 1.0 - 1.0 / (2.0 * g);
+        T.s = 3;
+        T.Ai[1][1] = g; T.Ai[2][1] = 1 - g; T.Ai[2][2] = g;
+        T.Ae[1][0] = g; T.Ae[2][0] = d; T.Ae[2][1] = 1 - d;
+        T.bi[1] = 1 - g; T.bi[2] = g;
+        T.be[0] = d; T.be[1] = 1 - d;
+        T.c[1] = g; T.c[2] = 1.0;
+    } else if (which == HDG_ARS343) {       // ARS (3,4,3); gamma: root of 6g^3-18g^2+9g-1 in (0,1)
+        double g = 0.4358665215;
+        for (int it = 0; it < 8; ++it) g -= (6 * g * g * g - 18 * g * g + 9 * g - 1) / (18 * g * g - 36 * g + 9);
+        double b1 = -1.5 * g * g + 4 * g - 0.25, b2 = 1.5 * g * g - 5 * g + 1.25;
+        T.s = 4;
+        T.Ai[1][1] = g;
+        T.Ai[2][1] = (1 - g) / 2; T.Ai[2][2] = g;
+        T.Ai[3][1] = b1; T.Ai[3][2] = b2; T.Ai[3][3] = g;
+        T.Ae[1][0] = g;
+        T.Ae[2][0] = 0.3212788860; T.Ae[2][1] = 0.3966543747;
+        T.Ae[3][0] = -0.105858296; T.Ae[3][1] = 0.5529291479; T.Ae[3][2] = 0.5529291479;
+        T.bi[1] = b1; T.bi[2] = b2; T.bi[3] = g;
+        T.be[1] = b1; T.be[2] = b2; T.be[3] = g;
+        T.c[1] = g; T.c[2] = (1 + g) / 2; T.c[3] = 1.0;
+    } else if (which == HDG_IMEX_EULER) {   // App. A, IMEX Euler
+        T.s = 2;
+        T.Ai[1][1] = 1.0; T.Ae[1][0] = 1.0;
+        T.bi[1] = 1.0; T.be[0] = 1.0;
+        T.c[1] = 1.0;
+    } else {
+        throw std::invalid_argument("unknown tableau");
+    }
+    return T;
+}
+
+struct CondCache {
+    double c = 0;
+    double *Scell = nullptr, *Zc = nullptr, *Ac = nullptr, *Sell = nullptr, *Dinv = nullptr;
+    int *tcol = nullptr;
+};
+}  // namespace
+
+struct hdg_ctx {
+    hdg_params P{};
+    hdg_mesh_desc D{};
+    cudaStream_t st = nullptr;
+    RefTables T;
+    HostMesh H;
+    int K = 0, MU = 0, NU = 0, NP = 0, NT = 0, NL = 0;
+    long long ncells = 0, nfacets = 0, nQ = 0, nPv = 0, nL = 0;
+    double area = 1.0;
+    Tab tab;
+    // device allocations (freed in hdg_destroy)
+    std::vector<void *> allocs;
+    double *dref = nullptr;
+    RefDev R{};
+    MeshDev M{};
+    CellGeo *geo = nullptr;
+    // state (modal)
+    double *Q = nullptr, *p = nullptr, *lam = nullptr;
+    double t = 0.0;
+    // IMEX stages
+    std::vector<double *> Qs, rs, ps, ls;
+    // forcing
+    double *Fload = nullptr;
+    bool has_forcing = false;
+    double (*phi)(double, void *) = nullptr;
+    void *phi_user = nullptr;
+    // Step I
+    double *Bell = nullptr, *Binv = nullptr;
+    int *dstatus = nullptr;
+    // Step II
+    double *vK = nullptr, *wK = nullptr, *tb = nullptr, *tx = nullptr, *tr = nullptr, *tz = nullptr,
+           *tp[2] = {nullptr, nullptr}, *tAp = nullptr;
+    // GMRES (Step I)
+    double *gV = nullptr, *gw = nullptr, *gz = nullptr, *gu = nullptr;
+    GmresState *gs = nullptr, *hgs = nullptr;
+    // flexible GMRES on the stage system (vectors of nQ + np + nlambda)
+    double *fV = nullptr, *fZ = nullptr, *fx = nullptr, *fb = nullptr, *fw = nullptr, *fr = nullptr, *fu = nullptr;
+    GmresState *fgs = nullptr, *hfgs = nullptr;
+    // temporaries
+    double *q[8] = {};
+    double *pp[3] = {};
+    double *ll[3] = {};
+    // reductions
+    double *partials = nullptr;
+    unsigned *counter = nullptr;
+    Scalars *sc = nullptr;
+    Scalars *hsc = nullptr;     // pinned host mirror
+    std::deque<CondCache> cache;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // running stats of the current call
+    hdg_stats S{};
+
+    template <class T_>
+    T_ *alloc(size_t n) {
+        void *p_ = nullptr;
+        CK(cudaMalloc(&p_, n * sizeof(T_) > 0 ? n * sizeof(T_) : 16));
+        allocs.push_back(p_);
+        return (T_ *)p_;
+    }
+    RedBuf rb() const { return RedBuf{partials, counter}; }
+};
+
+namespace {
+
+// ------------------------------------------------------------------ helpers
+void read_scalars(hdg_ctx *c) {
+    CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+}
+
+int grid_for(long long n) { return red_grid(n); }
+
+template <int K>
+struct Impl {
+    typedef Dims<K> Dm;
+    static constexpr int MU = Dm::MU, NU = Dm::NU, NP = Dm::NP, NT = Dm::NT, NL = Dm::NL, K_ = K;
+
+    static void to_modal(hdg_ctx *c, const double *nodal, double *modal, int kind) {
+        // kind 0: velocity, 1: pressure, 2: trace
+        const double *Tm = kind == 0 ? c->R.nod_u : kind == 1 ? c->R.nod_p : c->R.nod_t;
+        int n = kind == 0 ? MU : kind == 1 ? NP : NT;
+        long long nvec = kind == 0 ? 2 * c->ncells : kind == 1 ? c->ncells : c->nfacets;
+        k_basis_change<<<grid_for(nvec * n), VEC_THREADS, 0, c->st>>>(Tm, n, nodal, modal, nvec);
+        CKL();
+    }
+    static void to_nodal(hdg_ctx *c, const double *modal, double *nodal, int kind) {
+        const double *Tm = kind == 0 ? c->R.mod_u : kind == 1 ? c->R.mod_p : c->R.mod_t;
+        int n = kind == 0 ? MU : kind == 1 ? NP : NT;
+        long long nvec = kind == 0 ? 2 * c->ncells : kind == 1 ? c->ncells : c->nfacets;
+        k_basis_change<<<grid_for(nvec * n), VEC_THREADS, 0, c->st>>>(Tm, n, modal, nodal, nvec);
+        CKL();
+    }
+    static void mass(hdg_ctx *c, const double *in, double *out, int mode) {
+        k_mass_scale<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, in, out, c->ncells, mode);
+        CKL();
+    }
+
+    // ---------------------------------------------------------------- condensation cache
+    static CondCache &condense(hdg_ctx *c, double cc) {
+        for (auto &e : c->cache)
+            if (e.c == cc) return e;
+        CondCache E;
+        E.c = cc;
+        E.Scell = c->alloc<double>((size_t)c->ncells * NL * NL);
+        E.Zc = c->alloc<double>((size_t)c->ncells * NP * NL);
+        E.Ac = c->alloc<double>((size_t)c->ncells * NP * NP);
+        E.Sell = c->alloc<double>((size_t)5 * NT * c->nL);
+        E.tcol = c->alloc<int>((size_t)5 * c->nfacets);
+        E.Dinv = c->alloc<double>((size_t)NT * c->nL);
+        size_t smem = sizeof(double) * (NP * NU + NL * NU + 2 * NP * NP + 2 * NP * NL + NL * NL);
+        CK(cudaFuncSetAttribute(k_condense<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_condense<K><<<(unsigned)c->ncells, 128, smem, c->st>>>(c->R, c->M, cc, c->P.tau, E.Scell, E.Zc, E.Ac);
+        CKL();
+        k_assemble_trace<NT><<<grid_for(c->nfacets), VEC_THREADS, 0, c->st>>>(c->M, E.Scell, E.Sell, E.tcol, E.Dinv);
+        CKL();
+        c->cache.push_back(E);
+        return c->cache.back();
+    }
+
+    // ---------------------------------------------------------------- trace CG: S x = b
+    static void trace_solve(hdg_ctx *c, CondCache &E, const double *b, double *x, double rtol) {
+        const int nf = (int)c->nfacets;
+        k_trace_mean<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(b, nf, c->rb(), c->sc);
+        CKL();
+        k_cg_setup<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(b, E.Dinv, x, c->tr, c->tz, c->tp[0], nf, c->rb(),
+                                                               c->sc, rtol, c->P.max_iters);
+        CKL();
+        const int gr = grid_for(c->nL), gf = grid_for(nf);
+        const int chunk = 16;
+        for (long long launched = 0;; launched += chunk) {
+            if (launched > (long long)c->P.max_iters + 2 * chunk)
+                throw std::length_error("trace CG: no convergence flag from the device");
+            for (int m = 0; m < chunk; ++m) {
+                double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
+                k_cg_apply<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf, c->rb(), c->sc);
+                k_cg_update<NT><<<gf, VEC_THREADS, 0, c->st>>>(E.Dinv, pnew, c->tAp, x, c->tr, c->tz, nf, c->rb(), c->sc);
+            }
+            CKL();
+            read_scalars(c);
+            if (c->hsc->done) break;
+        }
+        c->S.trace_solves += 1;
+        c->S.trace_iters += c->hsc->iters;
+        c->S.last_trace_relres = c->hsc->relres;
+        if (c->hsc->breakdown == 2) throw std::domain_error("trace CG: non-finite residual");
+        if (c->hsc->relres > rtol && c->hsc->breakdown == 0) {
+            char msg[256];
+            snprintf(msg, sizeof msg, "trace CG: iteration cap %d reached, relres %.3e", c->hsc->iters, c->hsc->relres);
+            throw std::length_error(msg);
+        }
+    }
+
+    // Mixed solve: [[M, -cG], [B, C]] (U, dp, dl) = (Ru, -Gamma(X, p, lam)) ; outputs U, dp, dl
+    // (no mean shift). Ru: dual (modal) or null; X, p, lam: or null.
+    static void mixed_solve(hdg_ctx *c, double cc, const double *Ru, const double *X, const double *p,
+                            const double *lam, double *U, double *dp, double *dl, const double *Rp_add = nullptr,
+                            const double *Rl_add = nullptr, double rtol = -1.0) {
+        CondCache &E = condense(c, cc);
+        size_t smem_rhs = sizeof(double) * 4 * (NL + 4 * MU + NP + NL);
+        unsigned nb = (unsigned)((c->ncells + 3) / 4);
+        k_mixed_rhs<K><<<nb, 128, smem_rhs, c->st>>>(c->R, c->M, c->P.tau, Ru, X, p, lam, Rp_add, E.Zc, c->vK, c->wK);
+        CKL();
+        k_facet_gather<NT><<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(c->M, c->vK, Rl_add, c->tb);
+        CKL();
+        trace_solve(c, E, c->tb, dl, rtol > 0 ? rtol : c->P.trace_rtol);
+        size_t smem_bs = sizeof(double) * 4 * (NL + NP);
+        k_mixed_backsub<K><<<nb, 128, smem_bs, c->st>>>(c->R, c->M, cc, Ru, c->wK, dl, E.Zc, E.Ac, U, dp);
+        CKL();
+    }
+
+    static void mean_shift(hdg_ctx *c, double *p, double *lam) {
+        k_p_integral<K><<<grid_for(c->ncells), VEC_THREADS, 0, c->st>>>(c->M, p, c->rb(), c->sc);
+        CKL();
+        k_p_shift<K><<<grid_for(c->ncells > c->nfacets ? c->ncells : c->nfacets), VEC_THREADS, 0, c->st>>>(
+            c->M, c->area, p, lam, c->sc);
+        CKL();
+    }
+
+    // ---------------------------------------------------------------- Step I operator
+    static void assemble_stepI(hdg_ctx *c, const double *Qs, double cc) {
+        size_t smem = sizeof(double) * fimpl_smem_doubles<K>();
+        CK(cudaFuncSetAttribute(k_fimpl_assemble<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st));
+        k_fimpl_assemble<K><<<(unsigned)c->ncells, 128, smem, c->st>>>(c->R, c->M, Qs, cc, c->P.alpha, c->P.delta_up,
+                                                                      c->Bell, c->Binv, c->dstatus);
+        CKL();
+    }
+
+    static void cell_apply(hdg_ctx *c, const double *x, double *y) {
+        k_cell_apply<K><<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->M, c->Bell, x, y);
+        CKL();
+    }
+
+    // Restarted GMRES(GM_M) on the assembled Step-I operator with right block-Jacobi
+    // preconditioning: B x = b, x0 = 0, stop at ||b - B x|| <= stepI_rtol ||b||.
+    static void stepI_solve(hdg_ctx *c, const double *b, double *x, double rtol = -1.0) {
+        if (!(rtol > 0)) rtol = c->P.stepI_rtol;
+        const long long n = c->nQ;
+        const int g = grid_for(n);
+        bool first = true;
+        for (int cyc = 0;; ++cyc) {
+            if (cyc > c->P.max_iters / GM_M + 2) throw std::length_error("GMRES: no convergence flag from the device");
+            k_gm_start<K><<<g, VEC_THREADS, 0, c->st>>>(c->M, c->Bell, b, x, c->gw, first ? 1 : 0, c->rb(), c->gs,
+                                                       rtol, c->P.max_iters);
+            for (int j = 0; j < GM_M; ++j) {
+                k_gm_precond<K><<<g, VEC_THREADS, 0, c->st>>>(c->Binv, c->gw, c->gV, c->gz, c->ncells, c->gs);
+                k_gm_apply_dot<K><<<g, VEC_THREADS, 0, c->st>>>(c->M, c->Bell, c->gz, c->gw, c->gV, c->rb(), c->gs);
+                k_gm_orth1<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
+                k_gm_orth2<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
+            }
+            k_gm_solve<<<1, 32, 0, c->st>>>(c->gs, nullptr);
+            k_gm_combine<<<g, VEC_THREADS, 0, c->st>>>(c->gV, c->gu, n, c->gs);
+            k_gm_update_x<K><<<g, VEC_THREADS, 0, c->st>>>(c->Binv, c->gu, x, c->ncells, first ? 1 : 0);
+            CKL();
+            CK(cudaMemcpyAsync(c->hgs, c->gs, sizeof(GmresState), cudaMemcpyDeviceToHost, c->st));
+            CK(cudaStreamSynchronize(c->st));
+            first = false;
+            const GmresState &G = *c->hgs;
+            if (G.breakdown == 2) throw std::domain_error("GMRES: non-finite residual");
+            if (G.converged) break;
+            if (G.total >= c->P.max_iters) {
+                char msg[256];
+                snprintf(msg, sizeof msg, "GMRES: iteration cap %d reached, relres %.3e", G.total,
+                         G.bnorm > 0 ? G.resid / G.bnorm : 0.0);
+                throw std::length_error(msg);
+            }
+        }
+        c->S.stepI_solves += 1;
+        c->S.stepI_iters += c->hgs->total;
+    }
+
+    // ---------------------------------------------------------------- Alg. 2
+    // r: dual (modal); Qs: advecting velocity (modal); Q, p, lam: in/out (modal)
+    static int richardson(hdg_ctx *c, double cc, const double *r, const double *Qsv, double *Q, double *p,
+                          double *lam) {
+        assemble_stepI(c, Qsv, cc);
+        int hstat = 0;
+        CK(cudaMemcpyAsync(&hstat, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        condense(c, cc);
+        CK(cudaStreamSynchronize(c->st));
+        if (hstat) throw std::domain_error("singular tentative-velocity block");
+        const bool fixed = c->P.n_richardson > 0;
+        const int nmax = fixed ? c->P.n_richardson : c->P.richardson_max;
+        double *BQ = c->q[0], *dr = c->q[1], *Qbar = c->q[2], *X = c->q[3], *U = c->q[4];
+        double *dp = c->pp[0], *dl = c->ll[0];
+        size_t smem_res = sizeof(double) * 4 * NL;
+        unsigned nb = (unsigned)((c->ncells + 3) / 4);
+        int it = 0;
+        for (it = 0; it < nmax; ++it) {
+            cell_apply(c, Q, BQ);
+            k_rich_residual<K><<<nb, 128, smem_res, c->st>>>(c->R, c->M, cc, r, BQ, p, lam, dr, 1.0);
+            CKL();
+            stepI_solve(c, dr, Qbar);                                            // Step I
+            LinComb L{};
+            L.nterms = 2; L.coef[0] = 1; L.vec[0] = Q; L.coef[1] = 1; L.vec[1] = Qbar;
+            k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, L, X, c->ncells);
+            CKL();
+            mixed_solve(c, cc, nullptr, X, p, lam, U, dp, dl);                  // Step II
+            k_rich_update<K><<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->M, Q, Qbar, U, p, dp, lam, dl, c->rb(), c->sc);
+            CKL();                                                               // Step III
+            mean_shift(c, p, lam);
+            read_scalars(c);
+            double dq = std::sqrt(std::fmax(c->hsc->red0, 0.0)), qn = std::sqrt(std::fmax(c->hsc->red1, 0.0));
+            c->S.last_update_norm = dq;
+            if (!std::isfinite(dq)) throw std::domain_error("Richardson: non-finite update");
+            if (!fixed && dq <= c->P.richardson_rtol * qn) { ++it; break; }
+        }
+        c->S.richardson_iters = it;
+        c->S.stage_solves += 1;
+        if (!fixed && !(c->S.last_update_norm <= c->P.richardson_rtol * std::sqrt(std::fmax(c->hsc->red1, 0.0))))
+            return 1;
+        return 0;
+    }
+
+    // Stage operator y = A(c) x, x = (Q | p | lam) contiguous:
+    //   yQ = (M - cF) Q - c G (p, lam),  (yp | ylam) = B Q + C (p, lam)   (Step-I blocks assembled)
+    static void stage_apply(hdg_ctx *c, double cc, const double *x, double *y) {
+        const double *Q = x, *p = x + c->nQ, *lam = x + c->nQ + c->nPv;
+        double *yQ = y, *yp = y + c->nQ, *yl = y + c->nQ + c->nPv;
+        unsigned nb = (unsigned)((c->ncells + 3) / 4);
+        cell_apply(c, Q, c->q[6]);
+        k_rich_residual<K><<<nb, 128, sizeof(double) * 4 * NL, c->st>>>(c->R, c->M, cc, nullptr, c->q[6], p, lam, yQ, -1.0);
+        CKL();
+        k_constraint<K><<<nb, 128, sizeof(double) * 4 * (NL + 2 * MU), c->st>>>(c->R, c->M, c->P.tau, Q, p, lam, yp, c->vK);
+        CKL();
+        k_facet_gather<NT><<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(c->M, c->vK, nullptr, yl);
+        CKL();
+    }
+
+    // Chorin split as a preconditioner: z = P^{-1} v (Step I, then Step II on the constraint rows)
+    static void chorin_precond(hdg_ctx *c, double cc, const double *v, double *z) {
+        const double *vQ = v, *vp = v + c->nQ, *vl = v + c->nQ + c->nPv;
+        double *zQ = z, *zp = z + c->nQ, *zl = z + c->nQ + c->nPv;
+        double *Qbar = c->q[2], *U = c->q[4];
+        stepI_solve(c, vQ, Qbar, c->P.inner_stepI_rtol);
+        mixed_solve(c, cc, nullptr, Qbar, nullptr, nullptr, U, zp, zl, vp, vl, c->P.inner_trace_rtol);
+        LinComb L{};
+        L.nterms = 2; L.coef[0] = 1; L.vec[0] = Qbar; L.coef[1] = 1; L.vec[1] = U;
+        k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, L, zQ, c->ncells);
+        CKL();
+    }
+
+    // Stage solve to tolerance: flexible GMRES(GM_M) on A(c) x = (r, 0, 0) right-preconditioned by
+    // the Chorin split (Alg. 2's preconditioner; plain Alg. 2 is its Richardson iteration).
+    static int stage_fgmres(hdg_ctx *c, double cc, const double *r, const double *Qsv, double *Q, double *p,
+                            double *lam) {
+        assemble_stepI(c, Qsv, cc);
+        int hstat = 0;
+        CK(cudaMemcpyAsync(&hstat, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        condense(c, cc);
+        CK(cudaStreamSynchronize(c->st));
+        if (hstat) throw std::domain_error("singular tentative-velocity block");
+        const long long N = c->nQ + c->nPv + c->nL;
+        const int g = grid_for(N);
+        double *x = c->fx, *b = c->fb, *w = c->fw, *res = c->fr, *u = c->fu;
+        // x = (Q, p, lam), b = (r, 0, 0)
+        CK(cudaMemcpyAsync(x, Q, 8 * c->nQ, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(x + c->nQ, p, 8 * c->nPv, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(x + c->nQ + c->nPv, lam, 8 * c->nL, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(b, r, 8 * c->nQ, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemsetAsync(b + c->nQ, 0, 8 * (c->nPv + c->nL), c->st));
+        k_vec_norm_into<<<g, VEC_THREADS, 0, c->st>>>(b, N, c->rb(), c->fgs);
+        CKL();
+        int outer = 0, converged = 0;
+        for (int cyc = 0; cyc < 1000; ++cyc) {
+            stage_apply(c, cc, x, w);                                            // res = b - A x
+            CK(cudaMemcpyAsync(res, b, 8 * N, cudaMemcpyDeviceToDevice, c->st));
+            k_axpby<<<g, VEC_THREADS, 0, c->st>>>(-1.0, w, 1.0, res, N);
+            k_vec_start<<<g, VEC_THREADS, 0, c->st>>>(res, N, cyc == 0 ? 2 : 0, c->rb(), c->fgs,
+                                                     c->P.richardson_rtol, c->P.richardson_max);
+            CKL();
+            CK(cudaMemcpyAsync(c->hfgs, c->fgs, sizeof(GmresState), cudaMemcpyDeviceToHost, c->st));
+            CK(cudaStreamSynchronize(c->st));
+            if (c->hfgs->breakdown == 2) throw std::domain_error("stage FGMRES: non-finite residual");
+            if (c->hfgs->converged) { converged = 1; break; }
+            for (int j = 0; j < GM_M; ++j) {
+                k_vec_normalize<<<g, VEC_THREADS, 0, c->st>>>(j == 0 ? res : w, c->fV, N, c->fgs);
+                CKL();
+                double *Vj = c->fV + (size_t)j * N, *Zj = c->fZ + (size_t)j * N;
+                chorin_precond(c, cc, Vj, Zj);
+                stage_apply(c, cc, Zj, w);
+                k_vec_dot<<<g, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), c->fgs);
+                k_gm_orth1<<<g, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), c->fgs);
+                k_gm_orth2<<<g, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), c->fgs);
+                CKL();
+                CK(cudaMemcpyAsync(c->hfgs, c->fgs, sizeof(GmresState), cudaMemcpyDeviceToHost, c->st));
+                CK(cudaStreamSynchronize(c->st));
+                ++outer;
+                if (c->hfgs->breakdown == 2) throw std::domain_error("stage FGMRES: non-finite residual");
+                if (c->hfgs->cycle_end) break;
+            }
+            k_gm_solve<<<1, 32, 0, c->st>>>(c->fgs, nullptr);
+            k_gm_combine<<<g, VEC_THREADS, 0, c->st>>>(c->fZ, u, N, c->fgs);
+            k_vec_add<<<g, VEC_THREADS, 0, c->st>>>(u, x, N);
+            CKL();
+            if (c->hfgs->converged) { converged = 1; break; }
+            if (outer >= c->P.richardson_max) break;
+        }
+        CK(cudaMemcpyAsync(Q, x, 8 * c->nQ, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(p, x + c->nQ, 8 * c->nPv, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(lam, x + c->nQ + c->nPv, 8 * c->nL, cudaMemcpyDeviceToDevice, c->st));
+        mean_shift(c, p, lam);
+        c->S.richardson_iters = outer;
+        c->S.stage_solves += 1;
+        c->S.last_update_norm = c->hfgs->bnorm > 0 ? c->hfgs->resid / c->hfgs->bnorm : 0.0;
+        return converged ? 0 : 1;
+    }
+
+    // A stage solve in the configured mode: fixed n_R (Alg. 2 as printed), Alg. 2 to tolerance,
+    // or Alg. 2's preconditioner inside flexible GMRES to tolerance.
+    static int stage_solve(hdg_ctx *c, double cc, const double *r, const double *Qsv, double *Q, double *p,
+                           double *lam) {
+        if (c->P.n_richardson <= 0 && c->P.stage_krylov) return stage_fgmres(c, cc, r, Qsv, Q, p, lam);
+        return richardson(c, cc, r, Qsv, Q, p, lam);
+    }
+
+    static void bdm(hdg_ctx *c, const double *Q, double *Qs) {
+        unsigned nb = (unsigned)((c->ncells + 3) / 4);
+        k_bdm<K><<<nb, 128, sizeof(double) * 4 * 2 * NU, c->st>>>(c->R, c->M, Q, Qs);
+        CKL();
+    }
+
+    // f^impl(w, Q, P(Q)) + phi(t) (w.F) as a dual vector, using the Step-I buffers (c = 1)
+    static void fimpl_dual(hdg_ctx *c, const double *Q, const double *Qs, double tt, double *out) {
+        assemble_stepI(c, Qs, 1.0);
+        cell_apply(c, Q, c->q[6]);
+        LinComb L{};
+        L.nterms = 2;
+        L.coef[0] = 1.0; L.vec[0] = Q; L.mass[0] = 1;
+        L.coef[1] = -1.0; L.vec[1] = c->q[6];
+        if (c->has_forcing) {
+            L.nterms = 3;
+            L.coef[2] = c->phi ? c->phi(tt, c->phi_user) : 1.0;
+            L.vec[2] = c->Fload;
+        }
+        k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, L, out, c->ncells);
+        CKL();
+    }
+
+    // Sec. 2.7: (U.w) - g(w,p,l) = f^impl(w,Q,P(Q)) + (w.f(t)), Gamma(U,p,l) = 0
+    static void reconstruct(hdg_ctx *c, const double *Q, double tt, double *p, double *lam) {
+        double *Qs = c->q[5], *Ru = c->q[7];
+        bdm(c, Q, Qs);
+        fimpl_dual(c, Q, Qs, tt, Ru);
+        mixed_solve(c, 1.0, Ru, nullptr, nullptr, nullptr, c->q[4], p, lam);
+        mean_shift(c, p, lam);
+    }
+
+    // ---------------------------------------------------------------- Alg. 1
+    static int imex_step(hdg_ctx *c) {
+        const Tab &T = c->tab;
+        const double dt = c->P.dt, t0 = c->t;
+        const int s = T.s;
+        double fval[4] = {0, 0, 0, 0};
+        for (int j = 0; j < s; ++j) fval[j] = c->has_forcing ? (c->phi ? c->phi(t0 + T.c[j] * dt, c->phi_user) : 1.0) : 0.0;
+        size_t bq = sizeof(double) * c->nQ;
+        CK(cudaMemcpyAsync(c->Qs[0], c->Q, bq, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(c->ps[0], c->p, sizeof(double) * c->nPv, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(c->ls[0], c->lam, sizeof(double) * c->nL, cudaMemcpyDeviceToDevice, c->st));
+        int nc = 0;
+        for (int i = 1; i < s; ++i) {
+            // eq. imex_residual: r_i = M Q^n + sum_j (a_ij/a_jj)(M Q_j - r_j) + dt sum_j aex_ij (w.f_j)
+            LinComb L{};
+            int n = 0;
+            L.coef[n] = 1.0; L.vec[n] = c->Qs[0]; L.mass[n] = 1; ++n;
+            for (int j = 1; j < i; ++j) {
+                double w = T.Ai[i][j] / T.Ai[j][j];
+                if (w == 0.0) continue;
+                L.coef[n] = w; L.vec[n] = c->Qs[j]; L.mass[n] = 1; ++n;
+                L.coef[n] = -w; L.vec[n] = c->rs[j]; L.mass[n] = 0; ++n;
+            }
+            if (c->has_forcing) {
+                double f = 0;
+                for (int j = 0; j < i; ++j) f += dt * T.Ae[i][j] * fval[j];
+                if (f != 0.0) { L.coef[n] = f; L.vec[n] = c->Fload; L.mass[n] = 0; ++n; }
+            }
+            L.nterms = n;
+            k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, L, c->rs[i], c->ncells);
+            CKL();
+            bdm(c, c->Qs[i - 1], c->q[5]);                                       // Q*_{i-1}
+            CK(cudaMemcpyAsync(c->Qs[i], c->Qs[i - 1], bq, cudaMemcpyDeviceToDevice, c->st));
+            CK(cudaMemcpyAsync(c->ps[i], c->ps[i - 1], sizeof(double) * c->nPv, cudaMemcpyDeviceToDevice, c->st));
+            CK(cudaMemcpyAsync(c->ls[i], c->ls[i - 1], sizeof(double) * c->nL, cudaMemcpyDeviceToDevice, c->st));
+            nc |= stage_solve(c, T.Ai[i][i] * dt, c->rs[i], c->q[5], c->Qs[i], c->ps[i], c->ls[i]);
+        }
+        // eq. final_residual and eq. final_update (coefficient b_{s-1}^im dt)
+        LinComb L{};
+        int n = 0;
+        L.coef[n] = 1.0; L.vec[n] = c->Qs[0]; L.mass[n] = 1; ++n;
+        for (int i = 1; i < s; ++i) {
+            double w = T.bi[i] / T.Ai[i][i];
+            if (w == 0.0) continue;
+            L.coef[n] = w; L.vec[n] = c->Qs[i]; L.mass[n] = 1; ++n;
+            L.coef[n] = -w; L.vec[n] = c->rs[i]; L.mass[n] = 0; ++n;
+        }
+        if (c->has_forcing) {
+            double f = 0;
+            for (int i = 0; i < s; ++i) f += dt * T.be[i] * fval[i];
+            if (f != 0.0) { L.coef[n] = f; L.vec[n] = c->Fload; L.mass[n] = 0; ++n; }
+        }
+        L.nterms = n;
+        double *rn = c->q[7];
+        k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, L, rn, c->ncells);
+        CKL();
+        mixed_solve(c, dt * T.bi[s - 1], rn, nullptr, nullptr, nullptr, c->Q, c->pp[1], c->ll[1]);
+        c->t = t0 + dt;
+        reconstruct(c, c->Q, c->t, c->p, c->lam);                               // Sec. 2.7
+        return nc;
+    }
+};
+
+hdg_status map_exception() {
+    try {
+        throw;
+    } catch (const OomError &e) {
+        g_last_error = e.what();
+        return HDG_ERR_OOM;
+    } catch (const CudaError &e) {
+        g_last_error = e.what();
+        return HDG_ERR_CUDA;
+    } catch (const std::length_error &e) {
+        g_last_error = e.what();
+        return HDG_ERR_NOT_CONVERGED;
+    } catch (const std::domain_error &e) {
+        g_last_error = e.what();
+        return HDG_ERR_NUMERIC;
+    } catch (const std::invalid_argument &e) {
+        g_last_error = e.what();
+        return HDG_ERR_INVALID_ARG;
+    } catch (const std::bad_alloc &e) {
+        g_last_error = e.what();
+        return HDG_ERR_OOM;
+    } catch (const std::exception &e) {
+        g_last_error = e.what();
+        return HDG_ERR_INVALID_ARG;
+    }
+}
+
+#define DISPATCH(ctx, ...)                                                     \
+    switch ((ctx)->K) {                                                        \
+        case 1: { typedef Impl<1> I; __VA_ARGS__; } break;                     \
+        case 2: { typedef Impl<2> I; __VA_ARGS__; } break;                     \
+        case 3: { typedef Impl<3> I; __VA_ARGS__; } break;                     \
+        case 4: { typedef Impl<4> I; __VA_ARGS__; } break;                     \
+        default: throw std::invalid_argument("unsupported degree");            \
+    }
+
+void begin_call(hdg_ctx *c) {
+    c->S = hdg_stats{};
+    CK(cudaEventRecord(c->e0, c->st));
+}
+void end_call(hdg_ctx *c, hdg_stats *out) {
+    CK(cudaEventRecord(c->e1, c->st));
+    CK(cudaEventSynchronize(c->e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, c->e0, c->e1));
+    c->S.ms_total = ms;
+    if (out) *out = c->S;
+}
+
+
+}  // namespace
+
+// =========================================================================== C-ABI
+extern "C" {
+
+void hdg_default_params(hdg_params *p) {
+    if (!p) return;
+    p->k = 2;
+    p->alpha = 1.0;
+    p->tau = 1.0;
+    p->delta_up = 1.0;
+    p->tableau = HDG_ARS222;
+    p->dt = 0.01;
+    p->n_richardson = 2;
+    p->richardson_rtol = 1e-10;
+    p->richardson_max = 50;
+    p->trace_rtol = 1e-12;
+    p->stepI_rtol = 1e-10;
+    p->max_iters = 5000;
+    p->stage_krylov = 1;
+    p->inner_stepI_rtol = 1e-1;
+    p->inner_trace_rtol = 1e-6;
+}
+
+const char *hdg_status_string(hdg_status s) {
+    switch (s) {
+        case HDG_OK: return "ok";
+        case HDG_ERR_INVALID_ARG: return "invalid argument";
+        case HDG_ERR_CUDA: return "CUDA error";
+        case HDG_ERR_OOM: return "out of device memory";
+        case HDG_ERR_NOT_CONVERGED: return "iteration did not converge";
+        case HDG_ERR_NUMERIC: return "non-finite value";
+        case HDG_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *hdg_last_error(void) { return g_last_error.c_str(); }
+
+hdg_status hdg_mesh_counts(const hdg_mesh_desc *mesh, int k, int64_t *ncells, int64_t *nfacets) {
+    if (!mesh || mesh->n < 1 || k < 1 || k > 4) return HDG_ERR_INVALID_ARG;
+    if (ncells) *ncells = 2LL * mesh->n * mesh->n;
+    if (nfacets) *nfacets = mesh_facet_count(mesh->n, mesh->periodic_x != 0, mesh->periodic_y != 0);
+    return HDG_OK;
+}
+
+hdg_status hdg_reference_rule(int k, int which, double *pts, double *wts, int *npts) {
+    if (k < 1 || k > 4 || !npts || (which != 0 && which != 1)) return HDG_ERR_INVALID_ARG;
+    try {
+        if (which == 0) {
+            std::vector<double> x, y, w;
+            int n = triangle_rule(volume_points_1d(k), x, y, w);
+            if (pts && wts) {
+                if (*npts < n) return HDG_ERR_INVALID_ARG;
+                for (int i = 0; i < n; ++i) { pts[2 * i] = x[i]; pts[2 * i + 1] = y[i]; wts[i] = w[i]; }
+            }
+            *npts = n;
+        } else {
+            int n = facet_points(k);
+            if (pts && wts) {
+                if (*npts < n) return HDG_ERR_INVALID_ARG;
+                gauss_legendre01(n, pts, wts);
+            }
+            *npts = n;
+        }
+    } catch (...) {
+        return map_exception();
+    }
+    return HDG_OK;
+}
+
+hdg_status hdg_reference_basis(int m, int npts, const double *pts, double *vals) {
+    if (m < 0 || m > 8 || npts < 0 || (npts > 0 && (!pts || !vals))) return HDG_ERR_INVALID_ARG;
+    int d = dim_P(m);
+    for (int i = 0; i < npts; ++i) dubiner(m, pts[2 * i], pts[2 * i + 1], vals + (size_t)i * d, nullptr);
+    return HDG_OK;
+}
+
+hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_params *params,
+                          void *cuda_stream) {
+    if (!out || !mesh || !params) return HDG_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (mesh->n < 1 || mesh->n > 4096 || !(mesh->Lx > 0) || !(mesh->Ly > 0)) return HDG_ERR_INVALID_ARG;
+    if (params->k < 1 || params->k > 4 || !(params->dt > 0) || !(params->tau > 0) || params->alpha < 0 ||
+        params->delta_up < 0 || params->max_iters < 1 || !(params->trace_rtol > 0) || !(params->stepI_rtol > 0))
+        return HDG_ERR_INVALID_ARG;
+    if (params->n_richardson <= 0 && (!(params->richardson_rtol > 0) || params->richardson_max < 1))
+        return HDG_ERR_INVALID_ARG;
+    if (params->n_richardson <= 0 && params->stage_krylov &&
+        (!(params->inner_stepI_rtol > 0) || !(params->inner_trace_rtol > 0)))
+        return HDG_ERR_INVALID_ARG;
+    if (params->tableau < HDG_ARS222 || params->tableau > HDG_IMEX_EULER) return HDG_ERR_INVALID_ARG;
+    hdg_ctx *c = new (std::nothrow) hdg_ctx();
+    if (!c) return HDG_ERR_OOM;
+    try {
+        c->P = *params;
+        c->D = *mesh;
+        c->st = (cudaStream_t)cuda_stream;
+        c->tab = make_tableau(params->tableau);
+        c->T = build_tables(params->k);
+        c->H = build_mesh(mesh->n, mesh->Lx, mesh->Ly, mesh->periodic_x != 0, mesh->periodic_y != 0);
+        c->K = params->k;
+        c->MU = c->T.mu; c->NU = 2 * c->T.mu; c->NP = c->T.np; c->NT = c->T.nt; c->NL = 3 * c->T.nt;
+        c->ncells = c->H.ncells;
+        c->nfacets = c->H.nfacets;
+        c->nQ = c->ncells * c->NU;
+        c->nPv = c->ncells * c->NP;
+        c->nL = c->nfacets * c->NT;
+        c->area = mesh->Lx * mesh->Ly;
+        // reference tables: one allocation
+        const RefTables &T = c->T;
+        std::vector<const std::vector<double> *> tabs = {&T.qw, &T.phi, &T.dphi, &T.fw, &T.ephi, &T.leg,
+                                                         &T.Dhat, &T.Ehat, &T.Tpp, &T.bdm_inv, &T.Iv, &T.nod_u,
+                                                         &T.nod_p, &T.mod_u, &T.mod_p, &T.nod_t, &T.mod_t};
+        size_t tot = 0;
+        for (auto *v : tabs) tot += v->size();
+        std::vector<double> hbuf;
+        hbuf.reserve(tot);
+        std::vector<size_t> offs;
+        for (auto *v : tabs) { offs.push_back(hbuf.size()); hbuf.insert(hbuf.end(), v->begin(), v->end()); }
+        c->dref = c->alloc<double>(tot);
+        CK(cudaMemcpy(c->dref, hbuf.data(), tot * sizeof(double), cudaMemcpyHostToDevice));
+        const double **dst[] = {&c->R.qw, &c->R.phi, &c->R.dphi, &c->R.fw, &c->R.ephi, &c->R.leg, &c->R.Dhat,
+                                &c->R.Ehat, &c->R.Tpp, &c->R.bdm_inv, &c->R.Iv, &c->R.nod_u, &c->R.nod_p,
+                                &c->R.mod_u, &c->R.mod_p, &c->R.nod_t, &c->R.mod_t};
+        for (size_t i = 0; i < tabs.size(); ++i) *dst[i] = c->dref + offs[i];
+        // mesh
+        c->geo = c->alloc<CellGeo>(c->ncells);
+        CK(cudaMemcpy(c->geo, c->H.geo.data(), sizeof(CellGeo) * c->ncells, cudaMemcpyHostToDevice));
+        auto up = [&](const std::vector<int> &v) {
+            int *d = c->alloc<int>(v.size());
+            CK(cudaMemcpy(d, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice));
+            return (const int *)d;
+        };
+        c->M.geo = c->geo;
+        c->M.cell_facet = up(c->H.cell_facet);
+        c->M.cell_flip = up(c->H.cell_flip);
+        c->M.cell_nbr = up(c->H.cell_nbr);
+        c->M.cell_nbr_edge = up(c->H.cell_nbr_edge);
+        c->M.facet_cell = up(c->H.facet_cell);
+        c->M.facet_edge = up(c->H.facet_edge);
+        c->M.ncells = (int)c->ncells;
+        c->M.nfacets = (int)c->nfacets;
+        // state and work buffers
+        const size_t nQ = c->nQ, nP = c->nPv, nL = c->nL;
+        c->Q = c->alloc<double>(nQ); c->p = c->alloc<double>(nP); c->lam = c->alloc<double>(nL);
+        CK(cudaMemset(c->Q, 0, nQ * 8)); CK(cudaMemset(c->p, 0, nP * 8)); CK(cudaMemset(c->lam, 0, nL * 8));
+        for (int i = 0; i < c->tab.s; ++i) {
+            c->Qs.push_back(c->alloc<double>(nQ)); c->rs.push_back(c->alloc<double>(nQ));
+            c->ps.push_back(c->alloc<double>(nP)); c->ls.push_back(c->alloc<double>(nL));
+        }
+        c->Fload = c->alloc<double>(nQ);
+        c->Bell = c->alloc<double>((size_t)4 * c->NU * nQ);
+        c->Binv = c->alloc<double>((size_t)c->NU * nQ);
+        c->dstatus = c->alloc<int>(1);
+        c->vK = c->alloc<double>((size_t)c->ncells * c->NL);
+        c->wK = c->alloc<double>(nP);
+        c->tb = c->alloc<double>(nL); c->tx = c->alloc<double>(nL); c->tr = c->alloc<double>(nL);
+        c->tz = c->alloc<double>(nL); c->tp[0] = c->alloc<double>(nL); c->tp[1] = c->alloc<double>(nL);
+        c->tAp = c->alloc<double>(nL);
+        c->gV = c->alloc<double>((size_t)(GM_M + 1) * nQ);
+        c->gw = c->alloc<double>(nQ); c->gz = c->alloc<double>(nQ); c->gu = c->alloc<double>(nQ);
+        c->gs = c->alloc<GmresState>(1);
+        CK(cudaMemset(c->gs, 0, sizeof(GmresState)));
+        CK(cudaMallocHost(&c->hgs, sizeof(GmresState)));
+        if (params->n_richardson <= 0 && params->stage_krylov) {
+            const size_t N = nQ + nP + nL;
+            c->fV = c->alloc<double>((size_t)(GM_M + 1) * N);
+            c->fZ = c->alloc<double>((size_t)GM_M * N);
+            c->fx = c->alloc<double>(N); c->fb = c->alloc<double>(N); c->fw = c->alloc<double>(N);
+            c->fr = c->alloc<double>(N); c->fu = c->alloc<double>(N);
+            c->fgs = c->alloc<GmresState>(1);
+            CK(cudaMemset(c->fgs, 0, sizeof(GmresState)));
+            CK(cudaMallocHost(&c->hfgs, sizeof(GmresState)));
+        }
+        for (auto &x : c->q) x = c->alloc<double>(nQ);
+        for (auto &x : c->pp) x = c->alloc<double>(nP);
+        for (auto &x : c->ll) x = c->alloc<double>(nL);
+        c->partials = c->alloc<double>((size_t)MAX_RED_BLOCKS * (GM_M + 2));
+        c->counter = c->alloc<unsigned>(1);
+        CK(cudaMemset(c->counter, 0, sizeof(unsigned)));
+        c->sc = c->alloc<Scalars>(1);
+        CK(cudaMemset(c->sc, 0, sizeof(Scalars)));
+        CK(cudaMallocHost(&c->hsc, sizeof(Scalars)));
+        CK(cudaEventCreate(&c->e0));
+        CK(cudaEventCreate(&c->e1));
+        CK(cudaDeviceSynchronize());
+    } catch (...) {
+        hdg_status s = map_exception();
+        hdg_destroy(c);
+        return s;
+    }
+    *out = c;
+    return HDG_OK;
+}
+
+void hdg_destroy(hdg_ctx *c) {
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    else cudaDeviceSynchronize();
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->hsc) cudaFreeHost(c->hsc);
+    if (c->hgs) cudaFreeHost(c->hgs);
+    if (c->hfgs) cudaFreeHost(c->hfgs);
+    if (c->e0) cudaEventDestroy(c->e0);
+    if (c->e1) cudaEventDestroy(c->e1);
+    delete c;
+}
+
+hdg_status hdg_dof_sizes(const hdg_ctx *c, int64_t *nQ, int64_t *np, int64_t *nlambda) {
+    if (!c) return HDG_ERR_INVALID_ARG;
+    if (nQ) *nQ = c->nQ;
+    if (np) *np = c->nPv;
+    if (nlambda) *nlambda = c->nL;
+    return HDG_OK;
+}
+
+hdg_status hdg_set_state(hdg_ctx *c, const double *Q, const double *p, const double *lam, double t) {
+    if (!c || !Q) return HDG_ERR_INVALID_ARG;
+    try {
+        DISPATCH(c, {
+            I::to_modal(c, Q, c->Q, 0);
+            if (p) I::to_modal(c, p, c->p, 1); else CK(cudaMemsetAsync(c->p, 0, c->nPv * 8, c->st));
+            if (lam) I::to_modal(c, lam, c->lam, 2); else CK(cudaMemsetAsync(c->lam, 0, c->nL * 8, c->st));
+        });
+        c->t = t;
+        CK(cudaStreamSynchronize(c->st));
+    } catch (...) {
+        return map_exception();
+    }
+    return HDG_OK;
+}
+
+hdg_status hdg_get_state(hdg_ctx *c, double *Q, double *p, double *lam, double *t) {
+    if (!c) return HDG_ERR_INVALID_ARG;
+    try {
+        DISPATCH(c, {
+            if (Q) I::to_nodal(c, c->Q, Q, 0);
+            if (p) I::to_nodal(c, c->p, p, 1);
+            if (lam) I::to_nodal(c, c->lam, lam, 2);
+        });
+        if (t) *t = c->t;
+        CK(cudaStreamSynchronize(c->st));
+    } catch (...) {
+        return map_exception();
+    }
+    return HDG_OK;
+}
+
+hdg_status hdg_set_forcing(hdg_ctx *c, const double *F, double (*phi)(double, void *), void *user) {
+    if (!c) return HDG_ERR_INVALID_ARG;
+    try {
+        if (!F) {
+            c->has_forcing = false;
+            c->phi = nullptr;
+            return HDG_OK;
+        }
+        DISPATCH(c, {
+            I::to_modal(c, F, c->q[0], 0);
+            I::mass(c, c->q[0], c->Fload, 0);
+        });
+        c->has_forcing = true;
+        c->phi = phi;
+        c->phi_user = user;
+        CK(cudaStreamSynchronize(c->st));
+    } catch (...) {
+        return map_exception();
+    }
+    return HDG_OK;
+}
+
+hdg_status hdg_imex_step(hdg_ctx *c, int nsteps, hdg_stats *stats) {
+    if (!c || nsteps < 0) return HDG_ERR_INVALID_ARG;
+    int nc = 0;
+    try {
+        begin_call(c);
+        for (int s = 0; s < nsteps; ++s) DISPATCH(c, nc |= I::imex_step(c));
+        end_call(c, stats);
+    } catch (...) {
+        hdg_status s = map_exception();
+        if (stats) *stats = c->S;
+        return s;
+    }
+    return nc ? HDG_ERR_NOT_CONVERGED : HDG_OK;
+}
+
+hdg_status hdg_solve_stage(hdg_ctx *c, double cc, const double *R, const double *Qstar, double *Q,
+                           double *p, double *lam, hdg_stats *stats) {
+    if (!c || !(cc > 0) || !R || !Qstar || !Q || !p || !lam) return HDG_ERR_INVALID_ARG;
+    int nc = 0;
+    try {
+        begin_call(c);
+        DISPATCH(c, {
+            double *r = c->Qs[0], *Qs = c->Qs[1 % c->tab.s], *Qm = c->rs[0];
+            I::to_modal(c, R, c->q[0], 0);
+            I::mass(c, c->q[0], r, 0);
+            I::to_modal(c, Qstar, Qs, 0);
+            I::to_modal(c, Q, Qm, 0);
+            I::to_modal(c, p, c->ps[0], 1);
+            I::to_modal(c, lam, c->ls[0], 2);
+            nc = I::stage_solve(c, cc, r, Qs, Qm, c->ps[0], c->ls[0]);
+            I::to_nodal(c, Qm, Q, 0);
+            I::to_nodal(c, c->ps[0], p, 1);
+            I::to_nodal(c, c->ls[0], lam, 2);
+        });
+        end_call(c, stats);
+    } catch (...) {
+        hdg_status s = map_exception();
+        if (stats) *stats = c->S;
+        return s;
+    }
+    return nc ? HDG_ERR_NOT_CONVERGED : HDG_OK;
+}
+
+hdg_status hdg_bdm_project(hdg_ctx *c, const double *Q, double *Qstar) {
+    if (!c || !Q || !Qstar) return HDG_ERR_INVALID_ARG;
+    try {
+        DISPATCH(c, {
+            I::to_modal(c, Q, c->q[0], 0);
+            I::bdm(c, c->q[0], c->q[1]);
+            I::to_nodal(c, c->q[1], Qstar, 0);
+        });
+        CK(cudaStreamSynchronize(c->st));
+    } catch (...) {
+        return map_exception();
+    }
+    return HDG_OK;
+}
+
+hdg_status hdg_fimpl_apply(hdg_ctx *c, const double *Qstar, const double *Q, double *out) {
+    if (!c || !Qstar || !Q || !out) return HDG_ERR_INVALID_ARG;
+    try {
+        DISPATCH(c, {
+            I::to_modal(c, Qstar, c->q[1], 0);
+            I::to_modal(c, Q, c->q[2], 0);
+            bool hf = c->has_forcing;
+            c->has_forcing = false;
+            I::fimpl_dual(c, c->q[2], c->q[1], 0.0, c->q[3]);
+            c->has_forcing = hf;
+            I::mass(c, c->q[3], c->q[4], 1);
+            I::to_nodal(c, c->q[4], out, 0);
+        });
+        CK(cudaStreamSynchronize(c->st));
+    } catch (...) {
+        return map_exception();
+    }
+    return HDG_OK;
+}
+
+hdg_status hdg_tentative_solve(hdg_ctx *c, double cc, const double *Qstar, const double *R, double *Qbar,
+                               hdg_stats *stats) {
+    if (!c || !(cc > 0) || !Qstar || !R || !Qbar) return HDG_ERR_INVALID_ARG;
+    try {
+        begin_call(c);
+        DISPATCH(c, {
+            I::to_modal(c, Qstar, c->q[1], 0);
+            I::to_modal(c, R, c->q[2], 0);
+            I::mass(c, c->q[2], c->q[3], 0);
+            I::assemble_stepI(c, c->q[1], cc);
+            I::stepI_solve(c, c->q[3], c->q[4], c->P.stepI_rtol);
+            I::to_nodal(c, c->q[4], Qbar, 0);
+        });
+        end_call(c, stats);
+    } catch (...) {
+        hdg_status s = map_exception();
+        if (stats) *stats = c->S;
+        return s;
+    }
+    return HDG_OK;
+}
+
+hdg_status hdg_mixed_solve(hdg_ctx *c, double cc, const double *R, const double *X, double *U, double *p,
+                           double *lam, hdg_stats *stats) {
+    if (!c || !(cc > 0) || !U || !p || !lam) return HDG_ERR_INVALID_ARG;
+    try {
+        begin_call(c);
+        DISPATCH(c, {
+            double *Ru = nullptr, *Xm = nullptr;
+            if (R) { I::to_modal(c, R, c->q[0], 0); I::mass(c, c->q[0], c->q[1], 0); Ru = c->q[1]; }
+            if (X) { I::to_modal(c, X, c->q[2], 0); Xm = c->q[2]; }
+            I::mixed_solve(c, cc, Ru, Xm, nullptr, nullptr, c->q[3], c->pp[0], c->ll[0]);
+            I::mean_shift(c, c->pp[0], c->ll[0]);
+            I::to_nodal(c, c->q[3], U, 0);
+            I::to_nodal(c, c->pp[0], p, 1);
+            I::to_nodal(c, c->ll[0], lam, 2);
+        });
+        end_call(c, stats);
+    } catch (...) {
+        hdg_status s = map_exception();
+        if (stats) *stats = c->S;
+        return s;
+    }
+    return HDG_OK;
+}
+
+hdg_status hdg_trace_apply(hdg_ctx *c, double cc, const double *lam, double *out) {
+    if (!c || !(cc > 0) || !lam || !out) return HDG_ERR_INVALID_ARG;
+    try {
+        DISPATCH(c, {
+            CondCache &E = I::condense(c, cc);
+            I::to_modal(c, lam, c->ll[0], 2);
+            k_trace_apply<I::NT><<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->ll[0], c->ll[1], (int)c->nfacets);
+            CKL();
+            k_trace_riesz<<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(c->geo, c->M.facet_cell, c->M.facet_edge, I::NT,
+                                                                      c->ll[1], c->ll[2], c->nfacets);
+            CKL();
+            I::to_nodal(c, c->ll[2], out, 2);
+        });
+        CK(cudaStreamSynchronize(c->st));
+    } catch (...) {
+        return map_exception();
+    }
+    return HDG_OK;
+}
+
+hdg_status hdg_div_free_project(hdg_ctx *c, hdg_stats *stats) {
+    if (!c) return HDG_ERR_INVALID_ARG;
+    try {
+        begin_call(c);
+        DISPATCH(c, {
+            I::mixed_solve(c, 1.0, nullptr, c->Q, nullptr, nullptr, c->q[0], c->pp[0], c->ll[0]);
+            LinComb L{};
+            L.nterms = 2; L.coef[0] = 1; L.vec[0] = c->Q; L.coef[1] = 1; L.vec[1] = c->q[0];
+            k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, I::NU, L, c->Q, c->ncells);
+            CKL();
+            I::reconstruct(c, c->Q, c->t, c->p, c->lam);
+        });
+        end_call(c, stats);
+    } catch (...) {
+        hdg_status s = map_exception();
+        if (stats) *stats = c->S;
+        return s;
+    }
+    return HDG_OK;
+}
+
+hdg_status hdg_reconstruct_pressure(hdg_ctx *c, hdg_stats *stats) {
+    if (!c) return HDG_ERR_INVALID_ARG;
+    try {
+        begin_call(c);
+        DISPATCH(c, I::reconstruct(c, c->Q, c->t, c->p, c->lam));
+        end_call(c, stats);
+    } catch (...) {
+        hdg_status s = map_exception();
+        if (stats) *stats = c->S;
+        return s;
+    }
+    return HDG_OK;
+}
+
+hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *ms, double *bytes) {
+    if (!c || reps < 1 || !ms || !bytes || (which != 0 && which != 1) || (which == 0 && !(cc > 0)))
+        return HDG_ERR_INVALID_ARG;
+    try {
+        DISPATCH(c, {
+            const int NT = I::NT, NU = I::NU;
+            double b = 0;
+            std::vector<int> hc;
+            if (which == 0) {
+                CondCache &E = I::condense(c, cc);
+                // operator blocks actually read (wall facets have 3 of 5) + block-column indices
+                long long nblk = 0;
+                for (long long f = 0; f < c->nfacets; ++f) nblk += 1 + 2 * (c->H.facet_cell[2 * f + 1] >= 0 ? 2 : 1);
+                b = 8.0 * nblk * NT * NT + 4.0 * 5 * c->nfacets + 8.0 * 4 * c->nL;   // + z, pold read; pnew, Ap written
+                Scalars h{};
+                h.done = 0; h.beta = 0.5; h.rz = 1.0;
+                CK(cudaMemcpyAsync(c->sc, &h, sizeof(Scalars), cudaMemcpyHostToDevice, c->st));
+                const int nf = (int)c->nfacets, gr = grid_for(c->nL);
+                auto launch = [&]() {
+                    k_cg_apply<I::NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->tz, c->tp[0], c->tp[1], c->tAp, nf,
+                                                                    c->rb(), c->sc);
+                };
+                launch();
+                CKL();
+                CK(cudaEventRecord(c->e0, c->st));
+                for (int r = 0; r < reps; ++r) launch();
+                CK(cudaEventRecord(c->e1, c->st));
+            } else {
+                long long nblk = 0;
+                for (long long cl = 0; cl < c->ncells; ++cl)
+                    for (int e = 0; e < 3; ++e) nblk += c->H.cell_nbr[3 * cl + e] >= 0;
+                nblk += c->ncells;
+                b = 8.0 * nblk * NU * NU + 4.0 * 3 * c->ncells + 8.0 * 2 * c->nQ;     // + x read; y written
+                const int g = grid_for(c->nQ);
+                auto launch = [&]() {
+                    k_cell_apply<I::K_><<<g, VEC_THREADS, 0, c->st>>>(c->M, c->Bell, c->gz, c->gw);
+                };
+                launch();
+                CKL();
+                CK(cudaEventRecord(c->e0, c->st));
+                for (int r = 0; r < reps; ++r) launch();
+                CK(cudaEventRecord(c->e1, c->st));
+            }
+            CK(cudaEventSynchronize(c->e1));
+            float t = 0;
+            CK(cudaEventElapsedTime(&t, c->e0, c->e1));
+            *ms = t / reps;
+            *bytes = b;
+        });
+    } catch (...) {
+        return map_exception();
+    }
+    return HDG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,289 @@
+"""ctypes binding of the C-ABI in include/hdg.h (argument marshalling only).
+
+Every function of the C-ABI has a Python counterpart of the same name. Array arguments are
+torch CUDA float64 tensors in the exchange layouts of hdg.h (nodal values on the canonical
+mesh); they are passed by device pointer, on the context's stream. Failures raise HdgError
+with the library's status and message. Nothing here computes any part of the method.
+"""
+import ctypes
+import os
+
+from .build import LIB, build_library
+
+_lib = None
+
+
+class HdgError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.hdg_status_string(status).decode() if _lib else str(status)
+        detail = _lib.hdg_last_error().decode() if _lib else ''
+        super().__init__(f'{where}: {msg} ({detail})' if detail else f'{where}: {msg}')
+
+
+HDG_OK, HDG_ERR_INVALID_ARG, HDG_ERR_CUDA, HDG_ERR_OOM, HDG_ERR_NOT_CONVERGED, HDG_ERR_NUMERIC, \
+    HDG_ERR_UNSUPPORTED = range(7)
+TABLEAUS = {'ARS222': 0, 'ARS343': 1, 'IMEX_EULER': 2}
+
+
+class hdg_mesh_desc(ctypes.Structure):
+    _fields_ = [('n', ctypes.c_int), ('Lx', ctypes.c_double), ('Ly', ctypes.c_double),
+                ('periodic_x', ctypes.c_int), ('periodic_y', ctypes.c_int)]
+
+
+class hdg_params(ctypes.Structure):
+    _fields_ = [('k', ctypes.c_int), ('alpha', ctypes.c_double), ('tau', ctypes.c_double),
+                ('delta_up', ctypes.c_double), ('tableau', ctypes.c_int), ('dt', ctypes.c_double),
+                ('n_richardson', ctypes.c_int), ('richardson_rtol', ctypes.c_double),
+                ('richardson_max', ctypes.c_int), ('trace_rtol', ctypes.c_double),
+                ('stepI_rtol', ctypes.c_double), ('max_iters', ctypes.c_int),
+                ('stage_krylov', ctypes.c_int), ('inner_stepI_rtol', ctypes.c_double),
+                ('inner_trace_rtol', ctypes.c_double)]
+
+
+class hdg_stats(ctypes.Structure):
+    _fields_ = [('richardson_iters', ctypes.c_int), ('trace_solves', ctypes.c_int),
+                ('trace_iters', ctypes.c_int), ('stepI_solves', ctypes.c_int),
+                ('stepI_iters', ctypes.c_int), ('stage_solves', ctypes.c_int),
+                ('last_update_norm', ctypes.c_double), ('last_trace_relres', ctypes.c_double),
+                ('ms_total', ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+PHI = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_double, ctypes.c_void_p)
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_DP = ctypes.POINTER(ctypes.c_double)
+
+_SIGNATURES = {
+    'hdg_default_params': (None, [ctypes.POINTER(hdg_params)]),
+    'hdg_status_string': (ctypes.c_char_p, [_I]),
+    'hdg_last_error': (ctypes.c_char_p, []),
+    'hdg_mesh_counts': (_I, [ctypes.POINTER(hdg_mesh_desc), _I, _I64P, _I64P]),
+    'hdg_reference_rule': (_I, [_I, _I, _DP, _DP, ctypes.POINTER(_I)]),
+    'hdg_reference_basis': (_I, [_I, _I, _DP, _DP]),
+    'hdg_setup_mesh': (_I, [ctypes.POINTER(_P), ctypes.POINTER(hdg_mesh_desc), ctypes.POINTER(hdg_params), _P]),
+    'hdg_destroy': (None, [_P]),
+    'hdg_dof_sizes': (_I, [_P, _I64P, _I64P, _I64P]),
+    'hdg_set_state': (_I, [_P, _P, _P, _P, _D]),
+    'hdg_get_state': (_I, [_P, _P, _P, _P, _DP]),
+    'hdg_set_forcing': (_I, [_P, _P, PHI, _P]),
+    'hdg_imex_step': (_I, [_P, _I, ctypes.POINTER(hdg_stats)]),
+    'hdg_solve_stage': (_I, [_P, _D, _P, _P, _P, _P, _P, ctypes.POINTER(hdg_stats)]),
+    'hdg_bdm_project': (_I, [_P, _P, _P]),
+    'hdg_fimpl_apply': (_I, [_P, _P, _P, _P]),
+    'hdg_tentative_solve': (_I, [_P, _D, _P, _P, _P, ctypes.POINTER(hdg_stats)]),
+    'hdg_mixed_solve': (_I, [_P, _D, _P, _P, _P, _P, _P, ctypes.POINTER(hdg_stats)]),
+    'hdg_trace_apply': (_I, [_P, _D, _P, _P]),
+    'hdg_div_free_project': (_I, [_P, ctypes.POINTER(hdg_stats)]),
+    'hdg_reconstruct_pressure': (_I, [_P, ctypes.POINTER(hdg_stats)]),
+    'hdg_time_kernel': (_I, [_P, _I, _D, _I, _DP, _DP]),
+}
+
+
+def load(build=True):
+    """Load (building if needed) the in-tree CUDA library. Raises if it cannot be loaded:
+    there is no fallback path."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = build_library() if build else LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f'CUDA library missing: {path}')
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status, where):
+    if status != HDG_OK:
+        raise HdgError(status, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError('expected a contiguous CUDA float64 tensor')
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ host-only functions
+def hdg_default_params():
+    p = hdg_params()
+    load().hdg_default_params(ctypes.byref(p))
+    return p
+
+
+def hdg_mesh_counts(n, k, periodic_x=False, periodic_y=False, Lx=1.0, Ly=1.0):
+    d = hdg_mesh_desc(n, Lx, Ly, int(periodic_x), int(periodic_y))
+    nc, nf = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().hdg_mesh_counts(ctypes.byref(d), k, ctypes.byref(nc), ctypes.byref(nf)), 'hdg_mesh_counts')
+    return nc.value, nf.value
+
+
+def hdg_reference_rule(k, which):
+    import numpy as np
+    n = _I(0)
+    _check(load().hdg_reference_rule(k, which, None, None, ctypes.byref(n)), 'hdg_reference_rule')
+    dim = 2 if which == 0 else 1
+    pts = np.zeros(n.value * dim)
+    wts = np.zeros(n.value)
+    _check(load().hdg_reference_rule(k, which, pts.ctypes.data_as(_DP), wts.ctypes.data_as(_DP),
+                                     ctypes.byref(n)), 'hdg_reference_rule')
+    return pts.reshape(n.value, dim), wts
+
+
+def hdg_reference_basis(m, pts):
+    import numpy as np
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
+    d = (m + 1) * (m + 2) // 2
+    vals = np.zeros((len(pts), d))
+    _check(load().hdg_reference_basis(m, len(pts), pts.ctypes.data_as(_DP), vals.ctypes.data_as(_DP)),
+           'hdg_reference_basis')
+    return vals
+
+
+# ------------------------------------------------------------------ context
+class Context:
+    """An hdg_ctx: mesh, operators and state on the current CUDA device."""
+
+    def __init__(self, n, k, periodic_x=False, periodic_y=False, Lx=1.0, Ly=1.0, stream=None, **params):
+        import torch
+        lib = load()
+        p = hdg_default_params()
+        p.k = k
+        for key, val in params.items():
+            if key == 'tableau' and isinstance(val, str):
+                val = TABLEAUS[val]
+            if not hasattr(p, key):
+                raise KeyError(key)
+            setattr(p, key, val)
+        self.params = p
+        self.mesh = hdg_mesh_desc(n, Lx, Ly, int(periodic_x), int(periodic_y))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self._ctx = ctypes.c_void_p()
+        _check(lib.hdg_setup_mesh(ctypes.byref(self._ctx), ctypes.byref(self.mesh), ctypes.byref(p),
+                                  ctypes.c_void_p(stream.cuda_stream)), 'hdg_setup_mesh')
+        nQ, nP, nL = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.hdg_dof_sizes(self._ctx, ctypes.byref(nQ), ctypes.byref(nP), ctypes.byref(nL)), 'hdg_dof_sizes')
+        self.nQ, self.nP, self.nL = nQ.value, nP.value, nL.value
+        self.k, self.n = k, n
+        self.ncells = 2 * n * n
+        self._phi = None
+
+    def close(self):
+        if self._ctx:
+            load().hdg_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # shapes of the exchange arrays
+    def shapes(self):
+        mu = (self.k + 2) * (self.k + 3) // 2
+        npn = (self.k + 1) * (self.k + 2) // 2
+        return (self.ncells, 2, mu), (self.ncells, npn), (self.nL // (self.k + 1), self.k + 1)
+
+    def zeros(self):
+        import torch
+        sQ, sP, sL = self.shapes()
+        z = lambda s: torch.zeros(s, dtype=torch.float64, device='cuda')
+        return z(sQ), z(sP), z(sL)
+
+    def hdg_set_state(self, Q, p=None, lam=None, t=0.0):
+        _check(load().hdg_set_state(self._ctx, _ptr(Q), _ptr(p), _ptr(lam), t), 'hdg_set_state')
+
+    def hdg_get_state(self):
+        Q, p, lam = self.zeros()
+        t = ctypes.c_double()
+        _check(load().hdg_get_state(self._ctx, _ptr(Q), _ptr(p), _ptr(lam), ctypes.byref(t)), 'hdg_get_state')
+        return Q, p, lam, t.value
+
+    def hdg_set_forcing(self, F, phi=None):
+        if F is None:
+            _check(load().hdg_set_forcing(self._ctx, None, PHI(), None), 'hdg_set_forcing')
+            self._phi = None
+            return
+        cb = PHI(lambda t, user: float(phi(t))) if phi is not None else PHI()
+        self._phi = cb                                   # keep the callback alive
+        _check(load().hdg_set_forcing(self._ctx, _ptr(F), cb, None), 'hdg_set_forcing')
+
+    def hdg_imex_step(self, nsteps=1, check=True):
+        st = hdg_stats()
+        s = load().hdg_imex_step(self._ctx, nsteps, ctypes.byref(st))
+        if check:
+            _check(s, 'hdg_imex_step')
+        return st.as_dict() | {'status': s}
+
+    def hdg_solve_stage(self, c, R, Qstar, Q, p, lam, check=True):
+        st = hdg_stats()
+        s = load().hdg_solve_stage(self._ctx, c, _ptr(R), _ptr(Qstar), _ptr(Q), _ptr(p), _ptr(lam), ctypes.byref(st))
+        if check:
+            _check(s, 'hdg_solve_stage')
+        return st.as_dict() | {'status': s}
+
+    def hdg_bdm_project(self, Q):
+        out = self.zeros()[0]
+        _check(load().hdg_bdm_project(self._ctx, _ptr(Q), _ptr(out)), 'hdg_bdm_project')
+        return out
+
+    def hdg_fimpl_apply(self, Qstar, Q):
+        out = self.zeros()[0]
+        _check(load().hdg_fimpl_apply(self._ctx, _ptr(Qstar), _ptr(Q), _ptr(out)), 'hdg_fimpl_apply')
+        return out
+
+    def hdg_tentative_solve(self, c, Qstar, R):
+        out = self.zeros()[0]
+        st = hdg_stats()
+        _check(load().hdg_tentative_solve(self._ctx, c, _ptr(Qstar), _ptr(R), _ptr(out), ctypes.byref(st)),
+               'hdg_tentative_solve')
+        return out, st.as_dict()
+
+    def hdg_mixed_solve(self, c, R=None, X=None):
+        U, p, lam = self.zeros()
+        st = hdg_stats()
+        _check(load().hdg_mixed_solve(self._ctx, c, _ptr(R), _ptr(X), _ptr(U), _ptr(p), _ptr(lam), ctypes.byref(st)),
+               'hdg_mixed_solve')
+        return U, p, lam, st.as_dict()
+
+    def hdg_trace_apply(self, c, lam):
+        out = self.zeros()[2]
+        _check(load().hdg_trace_apply(self._ctx, c, _ptr(lam), _ptr(out)), 'hdg_trace_apply')
+        return out
+
+    def hdg_div_free_project(self):
+        st = hdg_stats()
+        _check(load().hdg_div_free_project(self._ctx, ctypes.byref(st)), 'hdg_div_free_project')
+        return st.as_dict()
+
+    def hdg_reconstruct_pressure(self):
+        st = hdg_stats()
+        _check(load().hdg_reconstruct_pressure(self._ctx, ctypes.byref(st)), 'hdg_reconstruct_pressure')
+        return st.as_dict()
+
+    def hdg_time_kernel(self, which, c=1.0, reps=20):
+        ms, b = ctypes.c_double(), ctypes.c_double()
+        _check(load().hdg_time_kernel(self._ctx, which, c, reps, ctypes.byref(ms), ctypes.byref(b)), 'hdg_time_kernel')
+        return ms.value, b.value

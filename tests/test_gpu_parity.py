@@ -1,0 +1,280 @@
+"""Parity of the CUDA path (through the C-ABI) with the oracle, row by row of the hot path.
+
+Bar: relative L2 difference <= 1e-10 and relative max difference <= 1e-9 per field (FP64 path),
+with the iterative solves run at tight tolerances (the oracle's inner solves are direct).
+Inputs: seeded random nodal fields (hdg_workloads) on meshes of several tiles with walls and
+periodic directions, k = 1..4.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import hdg_workloads as W
+from oracle import Mesh, HDG, Oracle, bdm_project, TABLEAUS
+
+torch = pytest.importorskip('torch')
+pytestmark = pytest.mark.gpu
+
+TIGHT = dict(trace_rtol=1e-14, stepI_rtol=1e-14, max_iters=20000)
+MESHES = [(3, False, False), (4, True, False), (3, True, True)]
+
+
+def H():
+    import paper_2410_09790_gb300 as mod
+    return mod
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().reshape(-1)
+
+
+def assert_close(got, ref, tol=1e-10, name=''):
+    got, ref = np.asarray(got).ravel(), np.asarray(ref).ravel()
+    scale = max(np.linalg.norm(ref), 1e-300)
+    l2 = np.linalg.norm(got - ref) / scale
+    mx = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+    assert l2 <= tol and mx <= 10 * tol, f'{name}: rel L2 {l2:.3e}, rel max {mx:.3e}'
+
+
+def setup(n, px, py, k, **kw):
+    m = Mesh(n, periodic_x=px, periodic_y=py)
+    h = HDG(m, k)
+    ctx = H().Context(n, k, periodic_x=px, periodic_y=py, **(TIGHT | kw))
+    return m, h, ctx
+
+
+def trace_mass(h):
+    """Oracle trace mass matrix (block diagonal, nodal basis)."""
+    m = h.mesh
+    blk = np.einsum('q,qi,qj->ij', h.tw, h.mut, h.mut)
+    return sp.block_diag([m.f_h[f] * blk for f in range(m.nfacets)], format='csc')
+
+
+@pytest.mark.parametrize('k', [1, 2, 3, 4])
+@pytest.mark.parametrize('mesh', MESHES)
+def test_bdm_projection(k, mesh):
+    m, h, ctx = setup(*mesh, k)
+    Q = np.random.default_rng(k).standard_normal(h.nQ)
+    got = host(ctx.hdg_bdm_project(cuda(Q.reshape(ctx.shapes()[0]))))
+    assert_close(got, bdm_project(h, Q), 1e-11, 'Q*')
+
+
+@pytest.mark.parametrize('k', [1, 2, 3, 4])
+@pytest.mark.parametrize('mesh', MESHES)
+def test_fimpl_apply(k, mesh):
+    m, h, ctx = setup(*mesh, k)
+    rng = np.random.default_rng(10 + k)
+    Qs = bdm_project(h, rng.standard_normal(h.nQ))
+    Q = rng.standard_normal(h.nQ)
+    sQ = ctx.shapes()[0]
+    got = host(ctx.hdg_fimpl_apply(cuda(Qs.reshape(sQ)), cuda(Q.reshape(sQ))))
+    M = h.static()[0]
+    ref = spla.spsolve(M.tocsc(), h.fimpl(Qs) @ Q)
+    assert_close(got, ref, 1e-11, 'f_impl')
+
+
+@pytest.mark.parametrize('k', [1, 2, 3, 4])
+@pytest.mark.parametrize('mesh', MESHES)
+def test_trace_operator(k, mesh):
+    m, h, ctx = setup(*mesh, k)
+    o = Oracle(h)
+    lam = np.random.default_rng(20 + k).standard_normal(h.nL)
+    for c in (2e-3, 1.0):
+        got = host(ctx.hdg_trace_apply(c, cuda(lam.reshape(ctx.shapes()[2]))))
+        *_, S = o.condensed_mixed_solve(c, np.zeros(h.nQ), np.zeros(o.nY))
+        ref = -spla.spsolve(trace_mass(h), S @ lam)      # oracle's S is negative semidefinite
+        assert_close(got, ref, 1e-11, f'S lambda (c={c})')
+
+
+@pytest.mark.parametrize('k', [1, 2, 3, 4])
+@pytest.mark.parametrize('mesh', MESHES)
+def test_mixed_solve(k, mesh):
+    m, h, ctx = setup(*mesh, k)
+    o = Oracle(h)
+    rng = np.random.default_rng(30 + k)
+    R, X = rng.standard_normal(h.nQ), rng.standard_normal(h.nQ)
+    sQ = ctx.shapes()[0]
+    for c in (2e-3, 1.0):
+        U, p, lam, st = ctx.hdg_mixed_solve(c, cuda(R.reshape(sQ)), cuda(X.reshape(sQ)))
+        Uo, po, lo = o.mixed_solve(c, o.M @ R, -o.B @ X)
+        assert_close(host(U), Uo, 1e-10, 'U')
+        assert_close(host(p), po, 1e-10, 'p')
+        assert_close(host(lam), lo, 1e-10, 'lambda')
+        assert st['trace_iters'] > 0
+
+
+@pytest.mark.parametrize('k', [1, 2, 3, 4])
+@pytest.mark.parametrize('mesh', MESHES)
+def test_tentative_solve(k, mesh):
+    m, h, ctx = setup(*mesh, k)
+    o = Oracle(h)
+    rng = np.random.default_rng(40 + k)
+    Qs = bdm_project(h, W.nodal_velocity(mesh[0], k, W.taylor_green).reshape(-1) + 0.3 * rng.standard_normal(h.nQ))
+    R = rng.standard_normal(h.nQ)
+    sQ = ctx.shapes()[0]
+    c = 0.01
+    got, st = ctx.hdg_tentative_solve(c, cuda(Qs.reshape(sQ)), cuda(R.reshape(sQ)))
+    F = h.fimpl(Qs)
+    ref = spla.spsolve((o.M - c * F).tocsc(), o.M @ R)
+    assert_close(host(got), ref, 1e-10, 'Qbar')
+
+
+@pytest.mark.parametrize('k', [2, 3])
+@pytest.mark.parametrize('mesh', MESHES)
+def test_solve_stage_fixed_richardson(k, mesh):
+    # Alg. 2 with the paper's n_R = 2 against the oracle's Alg. 2 with direct inner solves
+    m, h, ctx = setup(*mesh, k, n_richardson=2)
+    o = Oracle(h)
+    rng = np.random.default_rng(50 + k)
+    Q0 = W.nodal_velocity(mesh[0], k, W.taylor_green).reshape(-1) + 0.05 * rng.standard_normal(h.nQ)
+    p0, l0 = rng.standard_normal(h.nP), rng.standard_normal(h.nL)
+    Qs = bdm_project(h, Q0)
+    R = Q0 + 0.1 * rng.standard_normal(h.nQ)
+    c = 0.004
+    sQ, sP, sL = ctx.shapes()
+    Q, p, lam = cuda(Q0.reshape(sQ)), cuda(p0.reshape(sP)), cuda(l0.reshape(sL))
+    st = ctx.hdg_solve_stage(c, cuda(R.reshape(sQ)), cuda(Qs.reshape(sQ)), Q, p, lam)
+    Qo, po, lo, it = o.richardson(c, o.M @ R, Qs, Q0, p0 - h.mean_p(p0), l0 - h.mean_p(p0), n_iter=2)
+    assert st['richardson_iters'] == 2 and it == 2
+    assert_close(host(Q), Qo, 1e-10, 'Q')
+    assert_close(host(p), po, 1e-9, 'p')
+    assert_close(host(lam), lo, 1e-9, 'lambda')
+
+
+def test_solve_stage_tolerance_reaches_monolithic():
+    # Alg. 2 iterated to tolerance (plain Richardson)
+    m, h, ctx = setup(4, True, False, 2, n_richardson=0, stage_krylov=0, richardson_rtol=1e-13, richardson_max=200)
+    o = Oracle(h)
+    rng = np.random.default_rng(60)
+    Q0 = W.nodal_velocity(4, 2, W.taylor_green).reshape(-1) + 0.05 * rng.standard_normal(h.nQ)
+    Qs = bdm_project(h, Q0)
+    c = 0.003
+    sQ, sP, sL = ctx.shapes()
+    Q, p, lam = cuda(Q0.reshape(sQ)), cuda(np.zeros(sP)), cuda(np.zeros(sL))
+    st = ctx.hdg_solve_stage(c, cuda(Q0.reshape(sQ)), cuda(Qs.reshape(sQ)), Q, p, lam)
+    Qd, pd, ld = o.stage_solve(c, o.M @ Q0, Qs)
+    assert st['richardson_iters'] > 2
+    assert_close(host(Q), Qd, 1e-10, 'Q')
+    assert_close(host(p), pd, 1e-9, 'p')
+
+
+@pytest.mark.parametrize('n,k,c', [(4, 2, 0.003), (16, 2, 3.6 / 256), (8, 3, 0.9 / 64)])
+def test_solve_stage_krylov_reaches_monolithic(n, k, c):
+    # Alg. 2's preconditioner inside flexible GMRES, including the stiff regime c/h^2 = 3.6 where
+    # the plain Richardson iteration contracts slowly
+    m, h, ctx = setup(n, True, False, k, n_richardson=0, stage_krylov=1, richardson_rtol=1e-12, richardson_max=400)
+    o = Oracle(h)
+    rng = np.random.default_rng(61)
+    Q0 = W.nodal_velocity(n, k, lambda x, y: W.shear_layer(x, y, width=0.1, amp=0.05), noise=1e-3, seed=2).reshape(-1)
+    Q0, p0, l0 = o.div_free_project(Q0)
+    Qs = bdm_project(h, Q0)
+    sQ, sP, sL = ctx.shapes()
+    Q, p, lam = cuda(Q0.reshape(sQ)), cuda(p0.reshape(sP)), cuda(l0.reshape(sL))
+    st = ctx.hdg_solve_stage(c, cuda(Q0.reshape(sQ)), cuda(Qs.reshape(sQ)), Q, p, lam)
+    Qd, pd, ld = o.stage_solve(c, o.M @ Q0, Qs)
+    assert st['richardson_iters'] >= 1
+    assert_close(host(Q), Qd, 1e-10, 'Q')
+    assert_close(host(p), pd, 1e-9, 'p')
+    assert_close(host(lam), ld, 1e-9, 'lambda')
+
+
+def _run_imex(n, k, px, tab, dt, steps, Q0, gpu_kw, oracle_solver, oracle_kw):
+    m = Mesh(n, periodic_x=px)
+    h = HDG(m, k)
+    o = Oracle(h)
+    ctx = H().Context(n, k, periodic_x=px, tableau=tab, dt=dt, **(TIGHT | gpu_kw))
+    ctx.hdg_set_state(cuda(Q0))
+    ctx.hdg_reconstruct_pressure()
+    st = ctx.hdg_imex_step(steps)
+    Q, p, lam, t = ctx.hdg_get_state()
+    Qo = Q0.reshape(-1)
+    _, po, lo = o.reconstruct_pressure(Qo)
+    for s in range(steps):
+        Qo, po, lo = o.imex_step(TABLEAUS[tab](), dt, s * dt, Qo, po, lo, solver=oracle_solver,
+                                 richardson_kw=oracle_kw)
+    return (host(Q), host(p), host(lam), t), (Qo, po, lo), st
+
+
+def test_imex_taylor_green_8x8_k2_converged_stages():
+    # the plain-FP64 Taylor-Green workload (8x8, k=2, ARS(2,2,2), dt=0.01, 10 steps); stages
+    # iterated to 1e-13 against the oracle's monolithic (direct) stage solves
+    Q0 = W.nodal_velocity(8, 2, W.taylor_green)
+    (Q, p, lam, t), (Qo, po, lo), st = _run_imex(8, 2, False, 'ARS222', 0.01, 10, Q0,
+                                                dict(n_richardson=0, richardson_rtol=1e-12, richardson_max=200),
+                                                'direct', None)
+    assert abs(t - 0.1) < 1e-14
+    assert_close(Q, Qo, 1e-10, 'Q')
+    assert_close(p, po, 1e-9, 'p')
+    assert_close(lam, lo, 1e-9, 'lambda')
+
+
+@pytest.mark.parametrize('k,tab', [(1, 'IMEX_EULER'), (3, 'ARS343')])
+def test_imex_fixed_richardson_shear_channel(k, tab):
+    # periodic channel, shear layer + noise, divergence-free projected, n_R = 2 (the paper's setting)
+    n = 4
+    Qb = W.nodal_velocity(n, k, lambda x, y: W.shear_layer(x, y, width=0.2, amp=0.1), noise=1e-3, seed=1)
+    m = Mesh(n, periodic_x=True)
+    o = Oracle(HDG(m, k))
+    Q0, _, _ = o.div_free_project(Qb.reshape(-1))
+    (Q, p, lam, t), (Qo, po, lo), st = _run_imex(n, k, True, tab, 0.02, 3, Q0.reshape(Qb.shape),
+                                                dict(n_richardson=2), 'richardson', dict(n_iter=2))
+    assert_close(Q, Qo, 1e-10, 'Q')
+    assert_close(p, po, 1e-9, 'p')
+
+
+def test_div_free_projection_and_forcing():
+    n, k = 4, 2
+    m = Mesh(n)
+    h = HDG(m, k)
+    o = Oracle(h)
+    Qb = W.nodal_velocity(n, k, W.taylor_green, noise=0.05, seed=3)
+    ctx = H().Context(n, k, tableau='ARS222', dt=0.02, n_richardson=3, **TIGHT)
+    ctx.hdg_set_state(cuda(Qb))
+    ctx.hdg_div_free_project()
+    Q, p, lam, _ = ctx.hdg_get_state()
+    Qo, _, _ = o.div_free_project(Qb.reshape(-1))
+    _, po, lo = o.reconstruct_pressure(Qo)
+    assert_close(host(Q), Qo, 1e-10, 'Q div-free')
+    assert_close(host(p), po, 1e-9, 'p reconstructed')
+    # forcing f = phi(t) F through the explicit tableau (eq. f_expl)
+    F = W.nodal_velocity(n, k, W.taylor_green)
+    phi = lambda t: np.exp(-t)
+    ctx.hdg_set_forcing(cuda(F), phi)
+    ctx.hdg_imex_step(2)
+    Q, p, lam, _ = ctx.hdg_get_state()
+    fd = o.M @ F.reshape(-1)
+    forcing = lambda t: phi(t) * fd
+    Qo2, po2, lo2 = Qo, *o.reconstruct_pressure(Qo)[1:]
+    for s in range(2):
+        Qo2, po2, lo2 = o.imex_step(TABLEAUS['ARS222'](), 0.02, s * 0.02, Qo2, po2, lo2, forcing=forcing,
+                                    solver='richardson', richardson_kw=dict(n_iter=3))
+    assert_close(host(Q), Qo2, 1e-10, 'Q forced')
+    assert_close(host(p), po2, 1e-9, 'p forced')
+
+
+def test_deterministic_bitwise():
+    n, k = 6, 3
+    Q0 = W.nodal_velocity(n, k, W.taylor_green, noise=1e-3, seed=5)
+    outs = []
+    for _ in range(2):
+        ctx = H().Context(n, k, tableau='ARS343', dt=0.01, n_richardson=2)
+        ctx.hdg_set_state(cuda(Q0))
+        ctx.hdg_reconstruct_pressure()
+        ctx.hdg_imex_step(2)
+        outs.append([host(x) for x in ctx.hdg_get_state()[:3]])
+        ctx.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_invalid_inputs_rejected_on_device():
+    ctx = H().Context(3, 2)
+    with pytest.raises(H().HdgError):
+        ctx.hdg_mixed_solve(-1.0)
+    with pytest.raises(ValueError):
+        ctx.hdg_set_state(torch.zeros(3, device='cuda'))          # wrong dtype
