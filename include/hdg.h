@@ -182,6 +182,26 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *ctx, hdg_stats *stats);
 hdg_status hdg_time_kernel(hdg_ctx *ctx, int which, double c, int reps, double *ms_per_launch,
                            double *bytes_per_launch);
 
+/* The trace-operator apply of hdg_trace_apply (same operator, same output) without any device
+ * allocation. The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc while they run, such as code recording a CUDA graph under global stream capture (where
+ * allocation calls are refused) or hosts whose device memory is owned by another allocator.
+ * hdg_trace_apply may allocate: it caches the condensed operator of every new coefficient c. This
+ * variant condenses the cells again on every call and keeps its intermediate vectors in one static
+ * device array of 2^20 doubles (8 MiB) inside the library, which every GPU that loads the library
+ * holds until the process exits.
+ *   Limit: 3 * nlambda + ncells * 3(k+1) <= 2^20 doubles (e.g. 64 x 64 meshes with k <= 4,
+ *   128 x 128 with k <= 3); larger meshes return HDG_ERR_INVALID_ARG with the sizes in
+ *   hdg_last_error().
+ *   The first call on each device looks up the array's device address (cudaGetSymbolAddress) with
+ *   that device current; make that first call before any stream capture begins.
+ *   Every call on a device shares the array, which keeps the last call's contents (nothing in it
+ *   needs to start at zero: every element a call reads it has written first). Calls whose work
+ *   overlaps on the GPU (other streams, other contexts, other host threads) race on the array and
+ *   must be ordered by the caller. The context's own buffers are not touched. Synchronises the
+ *   context's stream before returning. */
+hdg_status hdg_trace_apply_noalloc(hdg_ctx *ctx, double c, const double *lam, double *out);
+
 #ifdef __cplusplus
 }
 #endif

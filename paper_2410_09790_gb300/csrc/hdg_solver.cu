@@ -1116,3 +1116,102 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
 }
 
 }  // extern "C"
+
+// =========================================================================== no-allocation variant
+// hdg_trace_apply_noalloc: the trace-operator apply without the context's per-coefficient operator
+// cache (whose first use for a new c calls cudaMalloc). Its scratch is this file-scope device
+// array, reached from host code only through the address cudaGetSymbolAddress returns (taken once
+// per device, on the first call made on that device).
+namespace {
+constexpr long long NOALLOC_MAX_DOUBLES = 1LL << 20;          // 8 MiB per device
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_DOUBLES];
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static double *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// per cell: condense S_K in shared memory (cell_condense) and write z_K = S_K l_K (canonical rows)
+template <int K>
+__global__ void k_condense_apply_cell(RefDev R, MeshDev M, double c, double tau, const double *__restrict__ lam,
+                                      double *z) {
+    typedef Dims<K> Dm;
+    constexpr int NP = Dm::NP, NT = Dm::NT, NL = Dm::NL, NU = Dm::NU;
+    extern __shared__ double sm[];
+    const int cell = blockIdx.x;
+    if (cell >= M.ncells) return;
+    Team tm{(int)threadIdx.x, (int)blockDim.x};
+    CellGeo g = M.geo[cell];
+    int flip[3] = {M.cell_flip[3 * cell], M.cell_flip[3 * cell + 1], M.cell_flip[3 * cell + 2]};
+    double *work = sm;
+    double *S = work + NP * NU + NL * NU + 2 * NP * NP + 2 * NP * NL + NL * NL;
+    double *Zs = S + NL * NL, *As = Zs + NP * NL, *lK = As + NP * NP;
+    cell_condense<K>(tm, R, g, flip, c, tau, work, S, Zs, As);
+    TFOR(i, NL) {
+        int e = i / NT, j = i % NT;
+        lK[i] = lam[(size_t)M.cell_facet[3 * cell + e] * NT + j];             // canonical orientation
+    }
+    tm.sync();
+    TFOR(r, NL) {
+        double s = 0;
+        for (int q = 0; q < NL; ++q) s += S[r * NL + q] * lK[q];
+        z[(size_t)cell * NL + r] = s;
+    }
+}
+
+template <int K>
+void trace_apply_noalloc_impl(hdg_ctx *c, double cc, const double *lam_nodal, double *out_nodal, double *scr) {
+    typedef Dims<K> Dm;
+    constexpr int NP = Dm::NP, NT = Dm::NT, NL = Dm::NL, NU = Dm::NU;
+    double *lm = scr, *ym = lm + c->nL, *yr = ym + c->nL, *z = yr + c->nL;
+    k_basis_change<<<red_grid(c->nL), VEC_THREADS, 0, c->st>>>(c->R.nod_t, NT, lam_nodal, lm, c->nfacets);
+    CKL();
+    size_t smem = sizeof(double) * (NP * NU + NL * NU + 2 * NP * NP + 2 * NP * NL + NL * NL + NL * NL + NP * NL +
+                                    NP * NP + NL);
+    k_condense_apply_cell<K><<<(unsigned)c->ncells, 128, smem, c->st>>>(c->R, c->M, cc, c->P.tau, lm, z);
+    CKL();
+    k_facet_gather<NT><<<red_grid(c->nL), VEC_THREADS, 0, c->st>>>(c->M, z, nullptr, ym);
+    CKL();
+    k_trace_riesz<<<red_grid(c->nL), VEC_THREADS, 0, c->st>>>(c->geo, c->M.facet_cell, c->M.facet_edge, NT, ym, yr,
+                                                              c->nfacets);
+    CKL();
+    k_basis_change<<<red_grid(c->nL), VEC_THREADS, 0, c->st>>>(c->R.mod_t, NT, yr, out_nodal, c->nfacets);
+    CKL();
+}
+}  // namespace
+
+extern "C" hdg_status hdg_trace_apply_noalloc(hdg_ctx *c, double cc, const double *lam, double *out) {
+    if (!c || !(cc > 0) || !lam || !out) return HDG_ERR_INVALID_ARG;
+    const long long need = 3 * c->nL + c->ncells * c->NL;
+    if (need > NOALLOC_MAX_DOUBLES) {
+        g_last_error = "hdg_trace_apply_noalloc: mesh too large for the static scratch (needs " +
+                       std::to_string(need) + " doubles, maximum " + std::to_string(NOALLOC_MAX_DOUBLES) + ")";
+        return HDG_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        g_last_error = std::string("hdg_trace_apply_noalloc: cudaGetDevice: ") + cudaGetErrorString(e);
+        return HDG_ERR_CUDA;
+    }
+    if (!g_noalloc_ptr[dev]) {                     // once per device, with that device current
+        double *ptr = nullptr;
+        e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            g_last_error = std::string("hdg_trace_apply_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            return HDG_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = ptr;
+    }
+    try {
+        double *scr = g_noalloc_ptr[dev];
+        switch (c->K) {
+            case 1: trace_apply_noalloc_impl<1>(c, cc, lam, out, scr); break;
+            case 2: trace_apply_noalloc_impl<2>(c, cc, lam, out, scr); break;
+            case 3: trace_apply_noalloc_impl<3>(c, cc, lam, out, scr); break;
+            case 4: trace_apply_noalloc_impl<4>(c, cc, lam, out, scr); break;
+            default: return HDG_ERR_INVALID_ARG;
+        }
+        CK(cudaStreamSynchronize(c->st));
+    } catch (...) {
+        return map_exception();
+    }
+    return HDG_OK;
+}

@@ -82,6 +82,7 @@ _SIGNATURES = {
     'hdg_div_free_project': (_I, [_P, ctypes.POINTER(hdg_stats)]),
     'hdg_reconstruct_pressure': (_I, [_P, ctypes.POINTER(hdg_stats)]),
     'hdg_time_kernel': (_I, [_P, _I, _D, _I, _DP, _DP]),
+    'hdg_trace_apply_noalloc': (_I, [_P, _D, _P, _P]),
 }
 
 
@@ -287,3 +288,8 @@ class Context:
         ms, b = ctypes.c_double(), ctypes.c_double()
         _check(load().hdg_time_kernel(self._ctx, which, c, reps, ctypes.byref(ms), ctypes.byref(b)), 'hdg_time_kernel')
         return ms.value, b.value
+
+    def hdg_trace_apply_noalloc(self, c, lam, out):
+        """hdg_trace_apply without device allocation; out is a caller-owned trace-shaped tensor."""
+        _check(load().hdg_trace_apply_noalloc(self._ctx, c, _ptr(lam), _ptr(out)), 'hdg_trace_apply_noalloc')
+        return out
