@@ -125,7 +125,7 @@ def oracle_sample(w, n_sample=16, steps=1):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    w = WORKLOAD
+    w = dict(WORKLOAD)
     for _ in range(args.warmup):
         oracle_sample(w, steps=1)
     rates, secs = [], []
@@ -154,7 +154,9 @@ def run_gpu(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device('cuda', local_rank)
-    w = WORKLOAD
+    w = dict(WORKLOAD)
+    if args.n:
+        w['n'] = args.n
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         ctx = H.Context(w['n'], w['k'], periodic_x=w['periodic_x'], stream=stream, tableau=w['tableau'],
@@ -165,6 +167,13 @@ def run_gpu(args, rank, world, local_rank):
         Q0 = torch.from_numpy(initial_velocity(w, seed_offset=rank)).to(dev)
         ctx.hdg_set_state(Q0)
         ctx.hdg_div_free_project()
+        if args.kernel_only is not None:
+            ctx.hdg_imex_step(1)
+            gamma = 0.43586652150845899942
+            ms_k, b_k = ctx.hdg_time_kernel(args.kernel_only, gamma * w['dt'], args.steps)
+            print(json.dumps({'kernel': args.kernel_only, 'ms_per_launch': ms_k, 'bytes': b_k}), flush=True)
+            ctx.close()
+            return
         flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)   # > L2 (129 MB)
         stats_all = []
         for _ in range(args.warmup):
@@ -276,6 +285,10 @@ def main():
     ap.add_argument('--impl', default='gpu', choices=['gpu', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--e2e-steps', type=int, default=3)
+    ap.add_argument('--n', type=int, default=None, help='mesh size override (profiling runs only)')
+    ap.add_argument('--kernel-only', type=int, default=None,
+                    help='profiling: set up the workload, take one step, then launch kernel K '
+                         '(0 trace apply, 1 tentative-velocity apply) --steps times and exit')
     args = ap.parse_args()
     world = int(os.environ.get('WORLD_SIZE', '1'))
     rank = int(os.environ.get('RANK', '0'))

@@ -87,6 +87,12 @@ typedef struct {
     int stage_krylov;
     double inner_stepI_rtol;
     double inner_trace_rtol;
+    /* Trace CG preconditioner: 1 (default) = one V-cycle of the non-nested multigrid of Sec. 2.8
+     * (degree-2 Chebyshev on facet block-Jacobi; P1 coarse space on the vertices with the Galerkin
+     * operator; geometric P1 hierarchy n -> n/2 while n stays even and >= 4; dense pseudo-inverse
+     * on the coarsest grid, which must have <= 1024 vertices, else block-Jacobi is used);
+     * 0 = facet block-Jacobi. */
+    int trace_mg;
 } hdg_params;
 
 typedef struct {

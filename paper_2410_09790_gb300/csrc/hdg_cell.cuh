@@ -56,7 +56,8 @@ struct RefDev {
 struct MeshDev {
     const CellGeo *geo;
     const int *cell_facet, *cell_flip, *cell_nbr, *cell_nbr_edge, *facet_cell, *facet_edge;
-    int ncells, nfacets;
+    const int *cell_vert, *facet_vert, *vert_facet, *vert_fsign, *vert_cell;   // P1 vertex maps
+    int ncells, nfacets, nverts;
 };
 
 struct Team {

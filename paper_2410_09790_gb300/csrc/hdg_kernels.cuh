@@ -24,7 +24,7 @@ constexpr int MAX_RED_BLOCKS = 2048;
 
 struct Scalars {
     double rz, rz0, pAp, alpha, beta, omega, rho, bnorm, rr, rv, ts, tt;
-    double bmean, red0, red1, red2;
+    double bmean, red0, red1, red2, zmean;
     int done, iters, breakdown, maxit;
     double rtol, relres;
 };
@@ -253,7 +253,7 @@ __global__ void k_cg_setup(const double *__restrict__ b, const double *__restric
                            double rtol, int maxit) {
     long long nrows = (long long)nfacets * NT;
     const double mean = sc->bmean;
-    double v[1] = {0.0}, tot[1];
+    double v[3] = {0.0, 0.0, 0.0}, tot[3];
     GRID_STRIDE(f, nfacets) {
         double rl[NT];
         for (int i = 0; i < NT; ++i) {
@@ -267,9 +267,12 @@ __global__ void k_cg_setup(const double *__restrict__ b, const double *__restric
             for (int j = 0; j < NT; ++j) s += __ldg(&Dinv[(size_t)j * nrows + f * NT + i]) * rl[j];
             z[f * NT + i] = s;
             v[0] += s * rl[i];
+            if (i == 0) { v[1] += s; v[2] += rl[0]; }
         }
     }
-    if (grid_sum<1>(rb, v, tot)) {
+    if (grid_sum<3>(rb, v, tot)) {
+        sc->zmean = tot[1] / nfacets;
+        tot[0] -= sc->zmean * tot[2];                 // (r, z - zmean e0)
         sc->rz = tot[0];
         sc->rz0 = tot[0];
         sc->beta = 0.0;
@@ -283,14 +286,16 @@ __global__ void k_cg_setup(const double *__restrict__ b, const double *__restric
     }
 }
 
-// pnew = z + beta pold; Ap = S pnew; pAp -> alpha = rz / pAp
+// pnew = z' + beta pold with z' = z - zmean e0 (z projected off the constant trace mode, the
+// kernel of S; without it the direction can drift into the kernel and p^T S p lose its sign);
+// Ap = S pnew; pAp -> alpha = rz / pAp
 template <int NT>
 __global__ void k_cg_apply(const double *__restrict__ Sell, const int *__restrict__ tcol,
                            const double *__restrict__ z, const double *__restrict__ pold,
                            double *__restrict__ pnew, double *__restrict__ Ap, int nfacets,
                            RedBuf rb, Scalars *sc) {
     if (sc->done) return;
-    const double beta = sc->beta;
+    const double beta = sc->beta, zm = sc->zmean;
     long long nrows = (long long)nfacets * NT;
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(g, nrows) {
@@ -303,10 +308,10 @@ __global__ void k_cg_apply(const double *__restrict__ Sell, const int *__restric
 #pragma unroll
             for (int j = 0; j < NT; ++j) {
                 size_t k = (size_t)cf * NT + j;
-                s += __ldg(&Sell[(size_t)(b * NT + j) * nrows + g]) * (z[k] + beta * pold[k]);
+                s += __ldg(&Sell[(size_t)(b * NT + j) * nrows + g]) * (z[k] - (j == 0 ? zm : 0.0) + beta * pold[k]);
             }
         }
-        double pn = z[g] + beta * pold[g];
+        double pn = z[g] - ((g % NT) == 0 ? zm : 0.0) + beta * pold[g];
         pnew[g] = pn;
         Ap[g] = s;
         v[0] += pn * s;
@@ -326,7 +331,7 @@ __global__ void k_cg_update(const double *__restrict__ Dinv, const double *__res
     if (sc->done) return;
     const double alpha = sc->alpha;
     long long nrows = (long long)nfacets * NT;
-    double v[1] = {0.0}, tot[1];
+    double v[3] = {0.0, 0.0, 0.0}, tot[3];
     GRID_STRIDE(f, nfacets) {
         double rl[NT];
         for (int i = 0; i < NT; ++i) {
@@ -340,10 +345,12 @@ __global__ void k_cg_update(const double *__restrict__ Dinv, const double *__res
             for (int j = 0; j < NT; ++j) s += __ldg(&Dinv[(size_t)j * nrows + f * NT + i]) * rl[j];
             z[f * NT + i] = s;
             v[0] += s * rl[i];
+            if (i == 0) { v[1] += s; v[2] += rl[0]; }
         }
     }
-    if (grid_sum<1>(rb, v, tot)) {
-        double rz_new = tot[0];
+    if (grid_sum<3>(rb, v, tot)) {
+        sc->zmean = tot[1] / nfacets;
+        double rz_new = tot[0] - sc->zmean * tot[2];  // (r, z - zmean e0)
         sc->beta = rz_new / sc->rz;
         sc->rz = rz_new;
         sc->iters += 1;

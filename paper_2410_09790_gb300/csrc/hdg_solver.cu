@@ -7,6 +7,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <new>
@@ -16,6 +17,7 @@
 
 #include "../../include/hdg.h"
 #include "hdg_kernels.cuh"
+#include "hdg_mg_kernels.cuh"
 #include "mesh.h"
 #include "refelem.h"
 
@@ -82,11 +84,36 @@ Tab make_tableau(int which) {
     return T;
 }
 
+struct MGLevel {               // a P1 level of the trace multigrid (operator for one c)
+    P1Grid G{};
+    double *A = nullptr, *dinv = nullptr;
+    double invth = 0, c1 = 0, c2 = 0;
+};
+
 struct CondCache {
     double c = 0;
     double *Scell = nullptr, *Zc = nullptr, *Ac = nullptr, *Sell = nullptr, *Dinv = nullptr;
     int *tcol = nullptr;
+    // multigrid (empty: facet block-Jacobi CG)
+    bool mg = false;
+    double t_invth = 0, t_c1 = 0, t_c2 = 0;   // trace-level Chebyshev
+    std::vector<MGLevel> lv;                  // lv[0] = level 1 (P1 on the mesh), ...
+    double *Minv = nullptr;
+    int Nc = 0;
 };
+
+struct MGWork {                // per-level work vectors (shared by all coefficients)
+    double *b = nullptr, *xa = nullptr, *xb = nullptr, *d = nullptr, *t = nullptr;
+};
+
+void cheb_coefs(double lmax, double &invth, double &c1, double &c2) {
+    // degree-2 Chebyshev on [lmax / 10, lmax]
+    double lmin = lmax / 10.0, th = 0.5 * (lmax + lmin), de = 0.5 * (lmax - lmin);
+    double sg = th / de, r0 = 1.0 / sg, r1 = 1.0 / (2.0 * sg - r0);
+    invth = 1.0 / th;
+    c1 = r0 * r1;
+    c2 = 2.0 * r1 / de;
+}
 }  // namespace
 
 struct hdg_ctx {
@@ -131,6 +158,10 @@ struct hdg_ctx {
     double *q[8] = {};
     double *pp[3] = {};
     double *ll[3] = {};
+    // multigrid work
+    std::vector<MGWork> mgw;
+    double *txa = nullptr, *td = nullptr, *tt = nullptr, *cellA = nullptr, *mgB = nullptr;
+    unsigned long long *dlmax = nullptr;
     // reductions
     double *partials = nullptr;
     unsigned *counter = nullptr;
@@ -152,6 +183,16 @@ struct hdg_ctx {
 };
 
 namespace {
+
+// HDG_TRACE_CG=1 in the environment: print the trace CG's scalars after every iteration (stderr)
+bool trace_cg_enabled() {
+    static int on = -1;
+    if (on < 0) {
+        const char *e = std::getenv("HDG_TRACE_CG");
+        on = (e && e[0] == '1') ? 1 : 0;
+    }
+    return on == 1;
+}
 
 // ------------------------------------------------------------------ helpers
 void read_scalars(hdg_ctx *c) {
@@ -204,8 +245,105 @@ struct Impl {
         CKL();
         k_assemble_trace<NT><<<grid_for(c->nfacets), VEC_THREADS, 0, c->st>>>(c->M, E.Scell, E.Sell, E.tcol, E.Dinv);
         CKL();
+        if (c->P.trace_mg && c->H.p1_ok) build_mg(c, E);
         c->cache.push_back(E);
         return c->cache.back();
+    }
+
+    // multigrid hierarchy of the trace operator for one coefficient (hdg_mg.cuh)
+    static void build_mg(hdg_ctx *c, CondCache &E) {
+        std::vector<P1Grid> grids;
+        int nl = c->H.n;
+        grids.push_back(make_p1grid(nl, c->H.px, c->H.py));
+        while (nl % 2 == 0 && nl / 2 >= 4) {
+            nl /= 2;
+            grids.push_back(make_p1grid(nl, c->H.px, c->H.py));
+        }
+        const int Nc = grids.back().nverts;
+        if (Nc > 1024) return;                                   // coarsest too large: block-Jacobi CG
+        const int L = (int)grids.size();
+        if (c->mgw.empty()) {
+            for (int l = 0; l < L; ++l) {
+                MGWork w;
+                size_t n = grids[l].nverts;
+                w.b = c->alloc<double>(n); w.xa = c->alloc<double>(n); w.xb = c->alloc<double>(n);
+                w.d = c->alloc<double>(n); w.t = c->alloc<double>(n);
+                c->mgw.push_back(w);
+            }
+            c->txa = c->alloc<double>(c->nL); c->td = c->alloc<double>(c->nL); c->tt = c->alloc<double>(c->nL);
+            c->cellA = c->alloc<double>((size_t)9 * c->ncells);
+            c->mgB = c->alloc<double>((size_t)Nc * Nc);
+            c->dlmax = c->alloc<unsigned long long>(16);
+        }
+        E.lv.resize(L);
+        for (int l = 0; l < L; ++l) {
+            E.lv[l].G = grids[l];
+            E.lv[l].A = c->alloc<double>((size_t)P1_NS * grids[l].nverts);
+            E.lv[l].dinv = c->alloc<double>(grids[l].nverts);
+        }
+        E.Minv = c->alloc<double>((size_t)Nc * Nc);
+        E.Nc = Nc;
+        CK(cudaMemsetAsync(c->dlmax, 0, 16 * sizeof(unsigned long long), c->st));
+        k_p1_cellop<NT><<<grid_for(c->ncells), VEC_THREADS, 0, c->st>>>(E.Scell, c->M.cell_flip, (int)c->ncells, c->cellA);
+        k_p1_assemble<<<grid_for(grids[0].nverts), VEC_THREADS, 0, c->st>>>(grids[0], c->cellA, c->M.vert_cell,
+                                                                         c->M.cell_vert, E.lv[0].A, E.lv[0].dinv,
+                                                                         c->dlmax + 1);
+        for (int l = 1; l < L; ++l)
+            k_p1_coarsen<<<grid_for(grids[l].nverts), VEC_THREADS, 0, c->st>>>(grids[l], grids[l - 1], E.lv[l - 1].A,
+                                                                             E.lv[l].A, E.lv[l].dinv, c->dlmax + 1 + l);
+        k_trace_bound<NT><<<grid_for(c->nfacets), VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, (int)c->nfacets,
+                                                                          c->dlmax);
+        CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st));
+        k_coarse_inverse<<<1, 1024, 0, c->st>>>(grids[L - 1], E.lv[L - 1].A, c->mgB, E.Minv, c->dstatus);
+        CKL();
+        unsigned long long bits[16];
+        int st = 0;
+        CK(cudaMemcpyAsync(bits, c->dlmax, sizeof bits, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(&st, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        if (st) throw std::domain_error("multigrid: singular coarsest operator");
+        double lm;
+        std::memcpy(&lm, &bits[0], sizeof lm);
+        cheb_coefs(lm, E.t_invth, E.t_c1, E.t_c2);
+        for (int l = 0; l < L; ++l) {
+            std::memcpy(&lm, &bits[1 + l], sizeof lm);
+            cheb_coefs(lm, E.lv[l].invth, E.lv[l].c1, E.lv[l].c2);
+        }
+        E.mg = true;
+    }
+
+    // z0 = V-cycle(r0) for the trace operator of E
+    static void vcycle(hdg_ctx *c, const CondCache &E, const double *r0, double *z0) {
+        const int nf = (int)c->nfacets, L = (int)E.lv.size();
+        const int gf = grid_for(nf), gr = grid_for(c->nL);
+        Scalars *sc = c->sc;
+        k_tcheb0<NT><<<gf, VEC_THREADS, 0, c->st>>>(E.Dinv, r0, c->txa, c->td, E.t_invth, nf, sc);
+        k_tcheb<NT><<<gf, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, r0, c->txa, z0, c->td, E.t_c1, E.t_c2, nf, sc);
+        k_tresid<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, r0, z0, c->tt, nf, sc);
+        k_restrict_t<NT><<<grid_for(E.lv[0].G.nverts), VEC_THREADS, 0, c->st>>>(E.lv[0].G.nverts, c->tt, c->M.vert_facet,
+                                                                              c->M.vert_fsign, c->mgw[0].b, sc);
+        for (int l = 0; l < L - 1; ++l) {
+            const MGLevel &V = E.lv[l];
+            const MGWork &W = c->mgw[l];
+            const int g = grid_for(V.G.nverts);
+            k_pcheb0<<<g, VEC_THREADS, 0, c->st>>>(V.dinv, W.b, W.xa, W.d, V.invth, V.G.nverts, sc);
+            k_pcheb<<<g, VEC_THREADS, 0, c->st>>>(V.G, V.A, V.dinv, W.b, W.xa, W.xb, W.d, V.c1, V.c2, sc);
+            k_presid<<<g, VEC_THREADS, 0, c->st>>>(V.G, V.A, W.b, W.xb, W.t, sc);
+            k_prestrict<<<grid_for(E.lv[l + 1].G.nverts), VEC_THREADS, 0, c->st>>>(E.lv[l + 1].G, V.G, W.t,
+                                                                                   c->mgw[l + 1].b, sc);
+        }
+        k_coarse_solve<<<1, 1024, 0, c->st>>>(E.Nc, E.Minv, c->mgw[L - 1].b, c->mgw[L - 1].xb, sc);
+        for (int l = L - 2; l >= 0; --l) {
+            const MGLevel &V = E.lv[l];
+            const MGWork &W = c->mgw[l];
+            const int g = grid_for(V.G.nverts);
+            k_pprolong<<<g, VEC_THREADS, 0, c->st>>>(V.G, E.lv[l + 1].G, c->mgw[l + 1].xb, W.xb, sc);
+            k_pcheb<<<g, VEC_THREADS, 0, c->st>>>(V.G, V.A, V.dinv, W.b, W.xb, W.xa, W.d, 0.0, V.invth, sc);
+            k_pcheb<<<g, VEC_THREADS, 0, c->st>>>(V.G, V.A, V.dinv, W.b, W.xa, W.xb, W.d, V.c1, V.c2, sc);
+        }
+        k_prolong_t<NT><<<gf, VEC_THREADS, 0, c->st>>>(c->M.facet_vert, c->mgw[0].xb, z0, nf, sc);
+        k_tcheb<NT><<<gf, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, r0, z0, c->txa, c->td, 0.0, E.t_invth, nf, sc);
+        k_tcheb<NT><<<gf, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, r0, c->txa, z0, c->td, E.t_c1, E.t_c2, nf, sc);
     }
 
     // ---------------------------------------------------------------- trace CG: S x = b
@@ -213,11 +351,12 @@ struct Impl {
         const int nf = (int)c->nfacets;
         k_trace_mean<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(b, nf, c->rb(), c->sc);
         CKL();
+        if (E.mg) { trace_solve_mg(c, E, b, x, rtol); return; }
         k_cg_setup<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(b, E.Dinv, x, c->tr, c->tz, c->tp[0], nf, c->rb(),
                                                                c->sc, rtol, c->P.max_iters);
         CKL();
         const int gr = grid_for(c->nL), gf = grid_for(nf);
-        const int chunk = 16;
+        const int chunk = trace_cg_enabled() ? 2 : 16;
         for (long long launched = 0;; launched += chunk) {
             if (launched > (long long)c->P.max_iters + 2 * chunk)
                 throw std::length_error("trace CG: no convergence flag from the device");
@@ -228,15 +367,59 @@ struct Impl {
             }
             CKL();
             read_scalars(c);
+            if (trace_cg_enabled())
+                fprintf(stderr, "trace CG it %d rz %.6e pAp %.6e alpha %.3e beta %.3e zmean %.3e relres %.3e done %d bd %d\n",
+                        c->hsc->iters, c->hsc->rz, c->hsc->pAp, c->hsc->alpha, c->hsc->beta, c->hsc->zmean,
+                        c->hsc->relres, c->hsc->done, c->hsc->breakdown);
             if (c->hsc->done) break;
         }
         c->S.trace_solves += 1;
         c->S.trace_iters += c->hsc->iters;
         c->S.last_trace_relres = c->hsc->relres;
         if (c->hsc->breakdown == 2) throw std::domain_error("trace CG: non-finite residual");
-        if (c->hsc->relres > rtol && c->hsc->breakdown == 0) {
+        if (c->hsc->relres > rtol) {
             char msg[256];
-            snprintf(msg, sizeof msg, "trace CG: iteration cap %d reached, relres %.3e", c->hsc->iters, c->hsc->relres);
+            snprintf(msg, sizeof msg, "trace CG: stopped at iteration %d (%s), relres %.3e", c->hsc->iters,
+                     c->hsc->breakdown ? "p^T S p <= 0" : "iteration cap", c->hsc->relres);
+            throw std::length_error(msg);
+        }
+    }
+
+    // CG preconditioned by one multigrid V-cycle per iteration
+    static void trace_solve_mg(hdg_ctx *c, CondCache &E, const double *b, double *x, double rtol) {
+        const int nf = (int)c->nfacets;
+        const int gr = grid_for(c->nL);
+        k_cg_setup_mg<NT><<<gr, VEC_THREADS, 0, c->st>>>(b, x, c->tr, c->tp[0], nf, c->sc, rtol, c->P.max_iters);
+        vcycle(c, E, c->tr, c->tz);
+        k_cg_rz<NT><<<gr, VEC_THREADS, 0, c->st>>>(c->tr, c->tz, nf, 1, c->rb(), c->sc);
+        CKL();
+        const int chunk = trace_cg_enabled() ? 1 : 4;
+        for (long long launched = 0;; launched += chunk) {
+            if (launched > (long long)c->P.max_iters + 2 * chunk)
+                throw std::length_error("trace CG: no convergence flag from the device");
+            for (int m = 0; m < chunk; ++m) {
+                double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
+                k_cg_apply<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf, c->rb(), c->sc);
+                k_cg_update_nz<<<gr, VEC_THREADS, 0, c->st>>>(pnew, c->tAp, x, c->tr, c->nL, c->sc);
+                vcycle(c, E, c->tr, c->tz);
+                k_cg_rz<NT><<<gr, VEC_THREADS, 0, c->st>>>(c->tr, c->tz, nf, 0, c->rb(), c->sc);
+            }
+            CKL();
+            read_scalars(c);
+            if (trace_cg_enabled())
+                fprintf(stderr, "trace CG it %d rz %.6e pAp %.6e alpha %.3e beta %.3e zmean %.3e relres %.3e done %d bd %d\n",
+                        c->hsc->iters, c->hsc->rz, c->hsc->pAp, c->hsc->alpha, c->hsc->beta, c->hsc->zmean,
+                        c->hsc->relres, c->hsc->done, c->hsc->breakdown);
+            if (c->hsc->done) break;
+        }
+        c->S.trace_solves += 1;
+        c->S.trace_iters += c->hsc->iters;
+        c->S.last_trace_relres = c->hsc->relres;
+        if (c->hsc->breakdown == 2) throw std::domain_error("trace CG: non-finite residual");
+        if (c->hsc->relres > rtol) {
+            char msg[256];
+            snprintf(msg, sizeof msg, "trace CG (multigrid): stopped at iteration %d (%s), relres %.3e", c->hsc->iters,
+                     c->hsc->breakdown ? "p^T S p <= 0" : "iteration cap", c->hsc->relres);
             throw std::length_error(msg);
         }
     }
@@ -632,6 +815,7 @@ void hdg_default_params(hdg_params *p) {
     p->stage_krylov = 1;
     p->inner_stepI_rtol = 1e-1;
     p->inner_trace_rtol = 1e-6;
+    p->trace_mg = 1;
 }
 
 const char *hdg_status_string(hdg_status s) {
@@ -753,6 +937,14 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         c->M.facet_edge = up(c->H.facet_edge);
         c->M.ncells = (int)c->ncells;
         c->M.nfacets = (int)c->nfacets;
+        if (c->H.p1_ok) {
+            c->M.cell_vert = up(c->H.cell_vert);
+            c->M.facet_vert = up(c->H.facet_vert);
+            c->M.vert_facet = up(c->H.vert_facet);
+            c->M.vert_fsign = up(c->H.vert_fsign);
+            c->M.vert_cell = up(c->H.vert_cell);
+            c->M.nverts = c->H.nverts;
+        }
         // state and work buffers
         const size_t nQ = c->nQ, nP = c->nPv, nL = c->nL;
         c->Q = c->alloc<double>(nQ); c->p = c->alloc<double>(nP); c->lam = c->alloc<double>(nL);
@@ -1075,7 +1267,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 for (long long f = 0; f < c->nfacets; ++f) nblk += 1 + 2 * (c->H.facet_cell[2 * f + 1] >= 0 ? 2 : 1);
                 b = 8.0 * nblk * NT * NT + 4.0 * 5 * c->nfacets + 8.0 * 4 * c->nL;   // + z, pold read; pnew, Ap written
                 Scalars h{};
-                h.done = 0; h.beta = 0.5; h.rz = 1.0;
+                h.done = 0; h.beta = 0.5; h.rz = 1.0; h.zmean = 0.0;
                 CK(cudaMemcpyAsync(c->sc, &h, sizeof(Scalars), cudaMemcpyHostToDevice, c->st));
                 const int nf = (int)c->nfacets, gr = grid_for(c->nL);
                 auto launch = [&]() {

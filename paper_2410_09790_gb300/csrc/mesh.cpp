@@ -100,6 +100,49 @@ HostMesh build_mesh(int n, double Lx, double Ly, bool px, bool py) {
     }
     for (int i = 0; i < M.ncells * 3; ++i)
         if (M.cell_facet[i] < 0) throw std::runtime_error("unassigned cell edge");
+    // P1 vertices
+    M.nvx = px ? n : n + 1;
+    M.nvy = py ? n : n + 1;
+    M.nverts = M.nvx * M.nvy;
+    auto vid = [&](int i, int j) {
+        if (px) i %= n;
+        if (py) j %= n;
+        return j * M.nvx + i;
+    };
+    M.cell_vert.assign(M.ncells * 3, -1);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            int c0 = cell(i, j, 0), c1 = cell(i, j, 1);
+            M.cell_vert[3 * c0] = vid(i, j); M.cell_vert[3 * c0 + 1] = vid(i + 1, j); M.cell_vert[3 * c0 + 2] = vid(i + 1, j + 1);
+            M.cell_vert[3 * c1] = vid(i, j); M.cell_vert[3 * c1 + 1] = vid(i + 1, j + 1); M.cell_vert[3 * c1 + 2] = vid(i, j + 1);
+        }
+    M.facet_vert.assign(M.nfacets * 2, -1);
+    for (int fac = 0; fac < M.nfacets; ++fac) {
+        int c = M.facet_cell[2 * fac], e = M.facet_edge[2 * fac];
+        int a = M.cell_vert[3 * c + (e + 1) % 3], b = M.cell_vert[3 * c + (e + 2) % 3];
+        if (M.cell_flip[3 * c + e]) std::swap(a, b);
+        M.facet_vert[2 * fac] = a;
+        M.facet_vert[2 * fac + 1] = b;
+    }
+    M.vert_facet.assign(M.nverts * 6, -1);
+    M.vert_fsign.assign(M.nverts * 6, 0);
+    M.vert_cell.assign(M.nverts * 6, -1);
+    std::vector<int> nf(M.nverts, 0), ncl(M.nverts, 0);
+    M.p1_ok = n >= 3;
+    for (int fac = 0; fac < M.nfacets && M.p1_ok; ++fac)
+        for (int s = 0; s < 2; ++s) {
+            int v = M.facet_vert[2 * fac + s];
+            if (nf[v] >= 6) { M.p1_ok = false; break; }
+            M.vert_facet[6 * v + nf[v]] = fac;
+            M.vert_fsign[6 * v + nf[v]] = s == 0 ? -1 : 1;
+            ++nf[v];
+        }
+    for (int c = 0; c < M.ncells && M.p1_ok; ++c)
+        for (int a = 0; a < 3; ++a) {
+            int v = M.cell_vert[3 * c + a];
+            if (ncl[v] >= 6) { M.p1_ok = false; break; }
+            M.vert_cell[6 * v + ncl[v]++] = 3 * c + a;
+        }
     return M;
 }
 

@@ -30,6 +30,14 @@ struct HostMesh {
     std::vector<int> cell_nbr_edge;     // [c][3]: the neighbour's local edge index
     std::vector<int> facet_cell;        // [f][2]: side cells (second -1 on walls)
     std::vector<int> facet_edge;        // [f][2]: local edge index in each side cell
+    // vertices of the P1 coarse space: (i,j), i < nvx, j < nvy (periodic directions wrap)
+    int nvx = 0, nvy = 0, nverts = 0;
+    std::vector<int> cell_vert;         // [c][3]
+    std::vector<int> facet_vert;        // [f][2]: canonical start / end vertex
+    std::vector<int> vert_facet;        // [v][6]: incident facets (-1 padded)
+    std::vector<int> vert_fsign;        // [v][6]: -1 if v starts the facet, +1 if it ends it
+    std::vector<int> vert_cell;         // [v][6]: incident cell*3 + local vertex (-1 padded)
+    bool p1_ok = false;                 // vertex maps valid (n >= 3: distinct stencil neighbours)
 };
 
 int64_t mesh_facet_count(int n, bool px, bool py);

@@ -38,7 +38,7 @@ class hdg_params(ctypes.Structure):
                 ('richardson_max', ctypes.c_int), ('trace_rtol', ctypes.c_double),
                 ('stepI_rtol', ctypes.c_double), ('max_iters', ctypes.c_int),
                 ('stage_krylov', ctypes.c_int), ('inner_stepI_rtol', ctypes.c_double),
-                ('inner_trace_rtol', ctypes.c_double)]
+                ('inner_trace_rtol', ctypes.c_double), ('trace_mg', ctypes.c_int)]
 
 
 class hdg_stats(ctypes.Structure):

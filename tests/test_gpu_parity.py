@@ -91,10 +91,11 @@ def test_trace_operator(k, mesh):
         assert_close(got, ref, 1e-11, f'S lambda (c={c})')
 
 
+@pytest.mark.parametrize('mg', [0, 1])
 @pytest.mark.parametrize('k', [1, 2, 3, 4])
-@pytest.mark.parametrize('mesh', MESHES)
-def test_mixed_solve(k, mesh):
-    m, h, ctx = setup(*mesh, k)
+@pytest.mark.parametrize('mesh', MESHES + [(8, True, False)])
+def test_mixed_solve(k, mesh, mg):
+    m, h, ctx = setup(*mesh, k, trace_mg=mg)
     o = Oracle(h)
     rng = np.random.default_rng(30 + k)
     R, X = rng.standard_normal(h.nQ), rng.standard_normal(h.nQ)
@@ -181,6 +182,22 @@ def test_solve_stage_krylov_reaches_monolithic(n, k, c):
     assert_close(host(Q), Qd, 1e-10, 'Q')
     assert_close(host(p), pd, 1e-9, 'p')
     assert_close(host(lam), ld, 1e-9, 'lambda')
+
+
+@pytest.mark.parametrize('n,px', [(16, True), (32, False)])
+def test_multigrid_iterations_mesh_robust(n, px):
+    # the V-cycle preconditioner keeps the trace CG iteration count small and nearly independent
+    # of h, unlike facet block-Jacobi (Sec. 3.4.2 reports the same robustness for the paper's MG)
+    k = 2
+    rng = np.random.default_rng(70)
+    R = rng.standard_normal((2 * n * n, 2, (k + 2) * (k + 3) // 2))
+    its = {}
+    for mg in (0, 1):
+        ctx = H().Context(n, k, periodic_x=px, trace_rtol=1e-10, max_iters=20000, trace_mg=mg)
+        *_, st = ctx.hdg_mixed_solve(1.0, cuda(R))
+        its[mg] = st['trace_iters']
+        ctx.close()
+    assert its[1] <= 25 and its[0] > 4 * its[1], its
 
 
 def _run_imex(n, k, px, tab, dt, steps, Q0, gpu_kw, oracle_solver, oracle_kw):
