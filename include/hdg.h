@@ -81,9 +81,9 @@ typedef struct {
     /* Stage solves to tolerance (n_richardson <= 0): stage_krylov = 0 iterates Alg. 2 until
      * ||dQ||_M <= richardson_rtol ||Q||_M; stage_krylov = 1 (default) runs flexible GMRES(30) on
      * the monolithic stage system with Alg. 2's Chorin split as the preconditioner (Step I and
-     * Step II solved to inner_stepI_rtol / inner_trace_rtol) until the stage residual is
-     * <= richardson_rtol times the right-hand side; richardson_max caps the outer iterations.
-     * Both reach the same fixed point, the monolithic stage solution. */
+     * Step II solved to inner_stepI_rtol / inner_trace_rtol, defaults 1e-1 / 1e-1) until the
+     * stage residual is <= richardson_rtol times the right-hand side; richardson_max caps the
+     * outer iterations. Both reach the same fixed point, the monolithic stage solution. */
     int stage_krylov;
     double inner_stepI_rtol;
     double inner_trace_rtol;
@@ -96,7 +96,7 @@ typedef struct {
 } hdg_params;
 
 typedef struct {
-    int richardson_iters;     /* Alg. 2 iterations of the last stage solve                 */
+    int richardson_iters;     /* Alg. 2 (or outer Krylov) iterations, summed over the call  */
     int trace_solves;         /* trace (Step II type) solves in the last call               */
     int trace_iters;          /* CG iterations summed over those solves                    */
     int stepI_solves;
@@ -105,6 +105,13 @@ typedef struct {
     double last_update_norm;  /* ||Q^(m) - Q^(m-1)||_M of the last Richardson iteration     */
     double last_trace_relres; /* final relative (preconditioned) residual of the last CG    */
     double ms_total;          /* device time of the call (CUDA events)                     */
+    /* per-component device time of the call (CUDA events; Sec. 3.4.1's buckets): trace
+     * solves (pressure / Step II, incl. their condensed right-hand sides and back-substitution),
+     * tentative-velocity solves (Step I), assembly of the Step-I operator, BDM projections */
+    double ms_trace;
+    double ms_stepI;
+    double ms_assembly;
+    double ms_bdm;
 } hdg_stats;
 
 void hdg_default_params(hdg_params *p);

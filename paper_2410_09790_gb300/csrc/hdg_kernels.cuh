@@ -374,18 +374,25 @@ __device__ __forceinline__ void gather_trace_local(const MeshDev &M, int cell, c
     tm.sync();
 }
 
+// Per-cell kernels run one cell per TEAM_LANES lanes (two cells per warp: their row loops have
+// 10..15 rows, so a full warp per cell would leave half of it idle). The mesh has an even number
+// of cells, so both halves of a warp are either in range or out of range together.
+constexpr int TEAM_LANES = 16;
+#define CELL_TEAM(SCR)                                                              \
+    extern __shared__ double sm[];                                                  \
+    const int team = threadIdx.x / TEAM_LANES;                                      \
+    const int cell = (blockIdx.x * blockDim.x + threadIdx.x) / TEAM_LANES;          \
+    if (cell >= M.ncells) return;                                                   \
+    Team tm{(int)(threadIdx.x % TEAM_LANES), TEAM_LANES};                           \
+    double *mine = sm + team * (SCR);
+
 template <int K>
 __global__ void k_mixed_rhs(RefDev R, MeshDev M, double tau, const double *Ru, const double *X,
                             const double *p, const double *lam, const double *Rp_add,
                             const double *__restrict__ Zc, double *v, double *w) {
     typedef Dims<K> Dm;
     constexpr int SCR = Dm::NL + 4 * Dm::MU + Dm::NP + Dm::NL;
-    extern __shared__ double sm[];
-    const int warp = threadIdx.x >> 5;
-    const int cell = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (cell >= M.ncells) return;
-    Team tm{(int)(threadIdx.x & 31), 32};
-    double *mine = sm + warp * SCR;
+    CELL_TEAM(SCR)
     double *lK = mine;
     gather_trace_local<K>(M, cell, lam, lK, tm);
     CellGeo g = M.geo[cell];
@@ -419,12 +426,8 @@ __global__ void k_mixed_backsub(RefDev R, MeshDev M, double c, const double *Ru,
                                 double *U, double *p) {
     typedef Dims<K> Dm;
     constexpr int SCR = Dm::NL + Dm::NP;
-    extern __shared__ double sm[];
-    const int warp = threadIdx.x >> 5;
-    const int cell = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (cell >= M.ncells) return;
-    Team tm{(int)(threadIdx.x & 31), 32};
-    double *lK = sm + warp * SCR;
+    CELL_TEAM(SCR)
+    double *lK = mine;
     gather_trace_local<K>(M, cell, lam, lK, tm);
     CellGeo g = M.geo[cell];
     cell_mixed_backsub<K>(tm, R, g, c, Ru ? Ru + (size_t)cell * Dm::NU : nullptr,
@@ -438,11 +441,7 @@ template <int K>
 __global__ void k_bdm(RefDev R, MeshDev M, const double *Q, double *Qs) {
     typedef Dims<K> Dm;
     constexpr int SCR = 2 * Dm::NU;
-    extern __shared__ double sm[];
-    const int warp = threadIdx.x >> 5;
-    const int cell = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (cell >= M.ncells) return;
-    Team tm{(int)(threadIdx.x & 31), 32};
+    CELL_TEAM(SCR)
     CellGeo g = M.geo[cell];
     const double *Qn[3];
     int ne[3];
@@ -451,7 +450,7 @@ __global__ void k_bdm(RefDev R, MeshDev M, const double *Q, double *Qs) {
         Qn[e] = o >= 0 ? Q + (size_t)o * Dm::NU : nullptr;
         ne[e] = M.cell_nbr_edge[3 * cell + e];
     }
-    cell_bdm<K>(tm, R, g, Q + (size_t)cell * Dm::NU, Qn, ne, sm + warp * SCR, Qs + (size_t)cell * Dm::NU);
+    cell_bdm<K>(tm, R, g, Q + (size_t)cell * Dm::NU, Qn, ne, mine, Qs + (size_t)cell * Dm::NU);
 }
 
 // ------------------------------------------------------------------ tentative-velocity operator
@@ -524,13 +523,16 @@ __global__ void k_cell_apply(MeshDev M, const double *__restrict__ Bell, const d
 // Krylov basis V (GM_M+1 vectors of n), Hessenberg column / Givens rotations and the residual
 // estimate live in device memory; the last block of each reduction does the small serial
 // updates, so one host read per restart cycle suffices.
-constexpr int GM_M = 30;
+constexpr int GM_M = 30;        // restart length of the GMRES cycles
+constexpr int GM_SHORT = 8;     // restart length for loose (inner) tolerances
 struct GmresState {
     double H[(GM_M + 1) * GM_M];     // column-major: H[j*(GM_M+1) + i]
     double cs[GM_M], sn[GM_M], g[GM_M + 1], y[GM_M], hcol[GM_M + 2], h2[GM_M + 2];
     double bnorm, beta, resid, rtol;
-    int j, cycle_end, converged, total, maxit, breakdown;
+    int j, cycle_end, converged, total, maxit, breakdown, m;   // m: restart length of this cycle
 };
+
+__global__ void k_gm_set_cycle(GmresState *gs, int m) { gs->m = m; }
 
 // w (local row values) dotted with V_0..V_{nvec-1}: each thread holds its rows' w in a loop
 template <class WF>
@@ -587,11 +589,10 @@ __global__ void k_gm_start(MeshDev M, const double *__restrict__ Bell, const dou
     }
     if (grid_sum<1>(rb, v, tot)) {
         double beta = sqrt(tot[0]);
-        if (first) {
+        if (first) {                    // (rtol, maxit: set when not captured, see k_gm_set_tol)
             gs->bnorm = beta;
             gs->total = 0;
-            gs->rtol = rtol;
-            gs->maxit = maxit;
+            if (rtol > 0) { gs->rtol = rtol; gs->maxit = maxit; }
             gs->converged = 0;
             gs->breakdown = 0;
         }
@@ -701,7 +702,7 @@ __global__ void k_gm_orth2(double *w, const double *__restrict__ V, long long nr
         gs->j = j + 1;
         if (!isfinite(gs->resid)) { gs->breakdown = 2; gs->cycle_end = 1; }
         else if (gs->resid <= gs->rtol * gs->bnorm) { gs->converged = 1; gs->cycle_end = 1; }
-        else if (gs->j >= GM_M || gs->total >= gs->maxit || hn == 0.0) gs->cycle_end = 1;
+        else if (gs->j >= gs->m || gs->total >= gs->maxit || hn == 0.0) gs->cycle_end = 1;
     }
 }
 
@@ -749,12 +750,8 @@ __global__ void k_rich_residual(RefDev R, MeshDev M, double c, const double *r, 
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NP = Dm::NP, NT = Dm::NT, NL = Dm::NL;
     constexpr int SCR = NL;
-    extern __shared__ double sm[];
-    const int warp = threadIdx.x >> 5;
-    const int cell = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (cell >= M.ncells) return;
-    Team tm{(int)(threadIdx.x & 31), 32};
-    double *lK = sm + warp * SCR;
+    CELL_TEAM(SCR)
+    double *lK = mine;
     gather_trace_local<K>(M, cell, lam, lK, tm);
     CellGeo g = M.geo[cell];
     const double *pK = p + (size_t)cell * NP;
@@ -786,12 +783,8 @@ __global__ void k_constraint(RefDev R, MeshDev M, double tau, const double *Q, c
                              const double *lam, double *yp, double *v) {
     typedef Dims<K> Dm;
     constexpr int SCR = Dm::NL + 2 * Dm::MU;
-    extern __shared__ double sm[];
-    const int warp = threadIdx.x >> 5;
-    const int cell = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (cell >= M.ncells) return;
-    Team tm{(int)(threadIdx.x & 31), 32};
-    double *lK = sm + warp * SCR;
+    CELL_TEAM(SCR)
+    double *lK = mine;
     gather_trace_local<K>(M, cell, lam, lK, tm);
     CellGeo g = M.geo[cell];
     int flip[3] = {M.cell_flip[3 * cell], M.cell_flip[3 * cell + 1], M.cell_flip[3 * cell + 2]};

@@ -272,7 +272,7 @@ __global__ void k_coarse_solve(int N, const double *__restrict__ Minv, const dou
 // r = b - mean e0, x = 0, pold = 0 (z = M r follows)
 template <int NT>
 __global__ void k_cg_setup_mg(const double *__restrict__ b, double *x, double *r, double *pold, int nfacets,
-                              Scalars *sc, double rtol, int maxit) {
+                              Scalars *sc) {
     const double mean = sc->bmean;
     GRID_STRIDE(g, (long long)nfacets * NT) {
         r[g] = b[g] - ((g % NT) == 0 ? mean : 0.0);
@@ -280,7 +280,7 @@ __global__ void k_cg_setup_mg(const double *__restrict__ b, double *x, double *r
         pold[g] = 0.0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        sc->done = 0; sc->beta = 0.0; sc->iters = 0; sc->breakdown = 0; sc->rtol = rtol; sc->maxit = maxit;
+        sc->done = 0; sc->beta = 0.0; sc->iters = 0; sc->breakdown = 0;      // rtol, maxit: k_set_tol
     }
 }
 
@@ -309,6 +309,192 @@ __global__ void k_cg_rz(const double *__restrict__ r, const double *__restrict__
     if (grid_sum<3>(rb, v, tot)) {
         sc->zmean = tot[1] / nfacets;
         double rz = tot[0] - sc->zmean * tot[2];      // (r, z - zmean e0)
+        if (first) {
+            sc->rz = rz; sc->rz0 = rz; sc->relres = rz > 0 ? 1.0 : 0.0;
+            if (!isfinite(rz)) { sc->done = 1; sc->breakdown = 2; }
+            else if (!(rz > 0.0)) sc->done = 1;
+        } else {
+            sc->beta = rz / sc->rz;
+            sc->rz = rz;
+            sc->iters += 1;
+            double rel = sc->rz0 > 0 ? sqrt(fmax(rz, 0.0) / sc->rz0) : 0.0;
+            sc->relres = rel;
+            if (!isfinite(rz)) { sc->done = 1; sc->breakdown = 2; }
+            else if (rel <= sc->rtol || sc->iters >= sc->maxit) sc->done = 1;
+        }
+    }
+}
+
+// tolerances of the next solve (kept out of the captured graphs, which serve every tolerance)
+__global__ void k_set_tol(Scalars *sc, double rtol, int maxit) {
+    sc->rtol = rtol;
+    sc->maxit = maxit;
+}
+
+__global__ void k_gm_set_tol(GmresState *gs, double rtol, int maxit) {
+    gs->rtol = rtol;
+    gs->maxit = maxit;
+}
+
+}  // namespace hdg
+
+namespace hdg {
+
+// ---------------------------------------------------------------- fused coarse part of the V-cycle
+// The P1 levels from `first` down (their grids are small) and the coarsest solve run in one thread
+// block, levels separated by __syncthreads (global writes of a block are visible to the block after
+// the barrier). With first == 0 the kernel also restricts the trace residual to level 1 and
+// prolongs the level-1 correction back to the trace.
+constexpr int MG_MAX_LEVELS = 16;
+struct MGTail {
+    int first, L, Nc, nfacets;
+    P1Grid G[MG_MAX_LEVELS];
+    const double *A[MG_MAX_LEVELS];
+    const double *dinv[MG_MAX_LEVELS];
+    double invth[MG_MAX_LEVELS], c1[MG_MAX_LEVELS], c2[MG_MAX_LEVELS];
+    double *b[MG_MAX_LEVELS], *xa[MG_MAX_LEVELS], *xb[MG_MAX_LEVELS], *d[MG_MAX_LEVELS], *t[MG_MAX_LEVELS];
+    const double *Minv;
+    const int *vert_facet, *vert_fsign, *facet_vert;
+    const double *tres;      // trace residual (first == 0)
+    double *z;               // trace iterate to correct (first == 0)
+};
+
+template <int NT>
+__global__ void __launch_bounds__(1024) k_mg_tail(MGTail T, const Scalars *sc) {
+    if (sc->done) return;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    if (T.first == 0)
+        for (int v = tid; v < T.G[0].nverts; v += nth) T.b[0][v] = restrict_trace<NT>(v, T.tres, T.vert_facet, T.vert_fsign);
+    __syncthreads();
+    for (int l = T.first; l < T.L - 1; ++l) {
+        const P1Grid G = T.G[l];
+        const double *A = T.A[l], *dv = T.dinv[l];
+        double *b = T.b[l], *xa = T.xa[l], *xb = T.xb[l], *d = T.d[l], *t = T.t[l];
+        for (int v = tid; v < G.nverts; v += nth) { double s = dv[v] * b[v] * T.invth[l]; d[v] = s; xa[v] = s; }
+        __syncthreads();
+        for (int v = tid; v < G.nverts; v += nth) {
+            double dn = T.c1[l] * d[v] + T.c2[l] * dv[v] * (b[v] - p1_apply(v, G, A, xa));
+            d[v] = dn;
+            xb[v] = xa[v] + dn;
+        }
+        __syncthreads();
+        for (int v = tid; v < G.nverts; v += nth) t[v] = b[v] - p1_apply(v, G, A, xb);
+        __syncthreads();
+        for (int V = tid; V < T.G[l + 1].nverts; V += nth) T.b[l + 1][V] = restrict_p1(V, T.G[l + 1], G, t);
+        __syncthreads();
+    }
+    {   // coarsest: x = Minv (b - mean b)
+        __shared__ double sh[1][32];
+        __shared__ double mean;
+        const int N = T.Nc;
+        const double *b = T.b[T.L - 1];
+        double v[1] = {0.0};
+        for (int i = tid; i < N; i += nth) v[0] += b[i];
+        block_sum<1>(v, sh);
+        if (tid == 0) mean = v[0] / N;
+        __syncthreads();
+        for (int i = tid; i < N; i += nth) {
+            double s = 0;
+            for (int j = 0; j < N; ++j) s += T.Minv[(size_t)i * N + j] * (b[j] - mean);
+            T.xb[T.L - 1][i] = s;
+        }
+        __syncthreads();
+    }
+    for (int l = T.L - 2; l >= T.first; --l) {
+        const P1Grid G = T.G[l];
+        const double *A = T.A[l], *dv = T.dinv[l];
+        double *b = T.b[l], *xa = T.xa[l], *xb = T.xb[l], *d = T.d[l];
+        for (int a = tid; a < G.nverts; a += nth) xb[a] += prolong_p1(a, G, T.G[l + 1], T.xb[l + 1]);
+        __syncthreads();
+        for (int v = tid; v < G.nverts; v += nth) {
+            double dn = T.invth[l] * dv[v] * (b[v] - p1_apply(v, G, A, xb));
+            d[v] = dn;
+            xa[v] = xb[v] + dn;
+        }
+        __syncthreads();
+        for (int v = tid; v < G.nverts; v += nth) {
+            double dn = T.c1[l] * d[v] + T.c2[l] * dv[v] * (b[v] - p1_apply(v, G, A, xa));
+            d[v] = dn;
+            xb[v] = xa[v] + dn;
+        }
+        __syncthreads();
+    }
+    if (T.first == 0) {
+        const double s3 = 0.28867513459481288225;
+        const double *e1 = T.xb[0];
+        for (int f = tid; f < T.nfacets; f += nth) {
+            double a = e1[T.facet_vert[2 * f]], bb = e1[T.facet_vert[2 * f + 1]];
+            T.z[(size_t)f * NT] += 0.5 * (a + bb);
+            T.z[(size_t)f * NT + 1] += s3 * (bb - a);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- fused CG steps
+// x += alpha p; r -= alpha Ap; then the first Chebyshev step of the V-cycle on r:
+// d = Dinv r / theta, z = d
+template <int NT>
+__global__ void k_cg_update_cheb0(const double *__restrict__ p, const double *__restrict__ Ap, double *x, double *r,
+                                  const double *__restrict__ Dinv, double *z, double *d, double invth, int nfacets,
+                                  const Scalars *sc) {
+    if (sc->done) return;
+    const double alpha = sc->alpha;
+    const long long nrows = (long long)nfacets * NT;
+    GRID_STRIDE(fl, nfacets) {
+        double rl[NT];
+        for (int i = 0; i < NT; ++i) {
+            size_t g = (size_t)fl * NT + i;
+            x[g] += alpha * p[g];
+            rl[i] = r[g] - alpha * Ap[g];
+            r[g] = rl[i];
+        }
+        for (int i = 0; i < NT; ++i) {
+            double s = 0;
+            for (int j = 0; j < NT; ++j) s += Dinv[(size_t)j * nrows + fl * NT + i] * rl[j];
+            s *= invth;
+            d[fl * NT + i] = s;
+            z[fl * NT + i] = s;
+        }
+    }
+}
+
+// last Chebyshev step of the V-cycle (b = the CG residual r) fused with the CG reduction:
+// xout = z; rz = (r, z - zmean e0), zmean; first: rz0, else beta and convergence
+template <int NT>
+__global__ void k_tcheb_rz(const double *__restrict__ Sell, const int *__restrict__ tcol,
+                           const double *__restrict__ Dinv, const double *__restrict__ b,
+                           const double *__restrict__ xin, double *__restrict__ xout, double *d, double c1, double c2,
+                           int nfacets, int first, RedBuf rb, Scalars *sc) {
+    if (sc->done) return;
+    const long long nrows = (long long)nfacets * NT;
+    double v[3] = {0.0, 0.0, 0.0}, tot[3];
+    GRID_STRIDE(fl, nfacets) {
+        int f = (int)fl;
+        double r[NT], bl[NT];
+        for (int i = 0; i < NT; ++i) { bl[i] = b[(size_t)f * NT + i]; r[i] = bl[i]; }
+        for (int bb = 0; bb < 5; ++bb) {
+            int cf = __ldg(&tcol[bb * nfacets + f]);
+            if (cf < 0) continue;
+            for (int j = 0; j < NT; ++j) {
+                double xv = xin[(size_t)cf * NT + j];
+                for (int i = 0; i < NT; ++i) r[i] -= __ldg(&Sell[(size_t)(bb * NT + j) * nrows + (size_t)f * NT + i]) * xv;
+            }
+        }
+        for (int i = 0; i < NT; ++i) {
+            double s = 0;
+            for (int j = 0; j < NT; ++j) s += Dinv[(size_t)j * nrows + (size_t)f * NT + i] * r[j];
+            size_t g = (size_t)f * NT + i;
+            double dn = c1 * d[g] + c2 * s;
+            d[g] = dn;
+            double zn = xin[g] + dn;
+            xout[g] = zn;
+            v[0] += bl[i] * zn;
+            if (i == 0) { v[1] += zn; v[2] += bl[0]; }
+        }
+    }
+    if (grid_sum<3>(rb, v, tot)) {
+        sc->zmean = tot[1] / nfacets;
+        double rz = tot[0] - sc->zmean * tot[2];
         if (first) {
             sc->rz = rz; sc->rz0 = rz; sc->relres = rz > 0 ? 1.0 : 0.0;
             if (!isfinite(rz)) { sc->done = 1; sc->breakdown = 2; }

@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <exception>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -96,6 +97,7 @@ struct CondCache {
     int *tcol = nullptr;
     // multigrid (empty: facet block-Jacobi CG)
     bool mg = false;
+    cudaGraphExec_t g_setup = nullptr, g_chunk = nullptr;   // captured MG-CG setup / 8 iterations
     double t_invth = 0, t_c1 = 0, t_c2 = 0;   // trace-level Chebyshev
     std::vector<MGLevel> lv;                  // lv[0] = level 1 (P1 on the mesh), ...
     double *Minv = nullptr;
@@ -168,7 +170,11 @@ struct hdg_ctx {
     Scalars *sc = nullptr;
     Scalars *hsc = nullptr;     // pinned host mirror
     std::deque<CondCache> cache;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, te0 = nullptr, te1 = nullptr;
+    cudaStream_t cap = nullptr;                              // capture stream for CUDA graphs
+    cudaGraphExec_t gm_first = nullptr, gm_restart = nullptr;   // captured GMRES(30) cycles
+    cudaGraphExec_t gms_first = nullptr, gms_restart = nullptr; // captured GMRES(GM_SHORT) cycles
+    double *gb = nullptr, *gx = nullptr;                     // their fixed right-hand side / solution
     // running stats of the current call
     hdg_stats S{};
 
@@ -201,6 +207,58 @@ void read_scalars(hdg_ctx *c) {
 }
 
 int grid_for(long long n) { return red_grid(n); }
+
+// per-cell team kernels: 128 threads = TEAMS_PER_BLOCK teams of TEAM_LANES lanes
+constexpr int TEAMS_PER_BLOCK = 128 / TEAM_LANES;
+inline unsigned cell_blocks(const hdg_ctx *c) { return (unsigned)((c->ncells + TEAMS_PER_BLOCK - 1) / TEAMS_PER_BLOCK); }
+
+// thread-per-facet trace kernels use small blocks so that a few thousand facets still spread
+// over all SMs
+constexpr int FACET_THREADS = 64;
+inline int grid_facets(long long nf) { return (int)((nf + FACET_THREADS - 1) / FACET_THREADS); }
+
+// Component timer: events around one component on the context's stream; the elapsed time is
+// added to a hdg_stats bucket when the component ends (each component ends with a host sync).
+struct CompTimer {
+    hdg_ctx *c;
+    double *bucket;
+    CompTimer(hdg_ctx *c_, double *b) : c(c_), bucket(b) { CK(cudaEventRecord(c->te0, c->st)); }
+    ~CompTimer() noexcept(false) {
+        if (std::uncaught_exceptions()) return;
+        CK(cudaEventRecord(c->te1, c->st));
+        CK(cudaEventSynchronize(c->te1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, c->te0, c->te1));
+        *bucket += ms;
+    }
+};
+
+// Record the launches issued by f (on c->st, temporarily the capture stream) into a graph.
+template <class F>
+cudaGraphExec_t capture_graph(hdg_ctx *c, F &&f) {
+    cudaStream_t user = c->st;
+    c->st = c->cap;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        try {
+            f();
+        } catch (...) {
+            cudaStreamEndCapture(c->cap, &g);
+            if (g) cudaGraphDestroy(g);
+            c->st = user;
+            throw;
+        }
+        e = cudaStreamEndCapture(c->cap, &g);
+    }
+    c->st = user;
+    CK(e);
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return ex;
+}
 
 template <int K>
 struct Impl {
@@ -312,17 +370,48 @@ struct Impl {
         E.mg = true;
     }
 
-    // z0 = V-cycle(r0) for the trace operator of E
-    static void vcycle(hdg_ctx *c, const CondCache &E, const double *r0, double *z0) {
+    // Parameters of the fused coarse part of the V-cycle, from level `first` down
+    static MGTail tail_params(hdg_ctx *c, const CondCache &E, int first, const double *tres, double *z) {
+        MGTail T{};
+        T.first = first;
+        T.L = (int)E.lv.size();
+        T.Nc = E.Nc;
+        T.nfacets = (int)c->nfacets;
+        for (int l = 0; l < T.L; ++l) {
+            T.G[l] = E.lv[l].G; T.A[l] = E.lv[l].A; T.dinv[l] = E.lv[l].dinv;
+            T.invth[l] = E.lv[l].invth; T.c1[l] = E.lv[l].c1; T.c2[l] = E.lv[l].c2;
+            T.b[l] = c->mgw[l].b; T.xa[l] = c->mgw[l].xa; T.xb[l] = c->mgw[l].xb; T.d[l] = c->mgw[l].d; T.t[l] = c->mgw[l].t;
+        }
+        T.Minv = E.Minv;
+        T.vert_facet = c->M.vert_facet; T.vert_fsign = c->M.vert_fsign; T.facet_vert = c->M.facet_vert;
+        T.tres = tres;
+        T.z = z;
+        return T;
+    }
+
+    // P1 levels with more vertices than this run as separate grid-wide kernels; the smaller ones
+    // share one block (HDG_MG_FUSE_MAX overrides the default)
+    static int mg_fuse_max() {
+        static int v = -1;
+        if (v < 0) {
+            const char *e = std::getenv("HDG_MG_FUSE_MAX");
+            v = e ? std::atoi(e) : 300;
+            if (v < 0) v = 0;
+        }
+        return v;
+    }
+
+    // Middle of the V-cycle: from the trace residual tt, correct z0 through the P1 hierarchy
+    static void vcycle_p1(hdg_ctx *c, const CondCache &E, double *z0) {
         const int nf = (int)c->nfacets, L = (int)E.lv.size();
-        const int gf = grid_for(nf), gr = grid_for(c->nL);
         Scalars *sc = c->sc;
-        k_tcheb0<NT><<<gf, VEC_THREADS, 0, c->st>>>(E.Dinv, r0, c->txa, c->td, E.t_invth, nf, sc);
-        k_tcheb<NT><<<gf, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, r0, c->txa, z0, c->td, E.t_c1, E.t_c2, nf, sc);
-        k_tresid<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, r0, z0, c->tt, nf, sc);
-        k_restrict_t<NT><<<grid_for(E.lv[0].G.nverts), VEC_THREADS, 0, c->st>>>(E.lv[0].G.nverts, c->tt, c->M.vert_facet,
-                                                                              c->M.vert_fsign, c->mgw[0].b, sc);
-        for (int l = 0; l < L - 1; ++l) {
+        int first = 0;
+        while (first < L - 1 && E.lv[first].G.nverts > mg_fuse_max()) ++first;
+        if (first > 0)
+            k_restrict_t<NT><<<grid_for(E.lv[0].G.nverts), VEC_THREADS, 0, c->st>>>(E.lv[0].G.nverts, c->tt,
+                                                                                  c->M.vert_facet, c->M.vert_fsign,
+                                                                                  c->mgw[0].b, sc);
+        for (int l = 0; l < first; ++l) {
             const MGLevel &V = E.lv[l];
             const MGWork &W = c->mgw[l];
             const int g = grid_for(V.G.nverts);
@@ -332,8 +421,8 @@ struct Impl {
             k_prestrict<<<grid_for(E.lv[l + 1].G.nverts), VEC_THREADS, 0, c->st>>>(E.lv[l + 1].G, V.G, W.t,
                                                                                    c->mgw[l + 1].b, sc);
         }
-        k_coarse_solve<<<1, 1024, 0, c->st>>>(E.Nc, E.Minv, c->mgw[L - 1].b, c->mgw[L - 1].xb, sc);
-        for (int l = L - 2; l >= 0; --l) {
+        k_mg_tail<NT><<<1, 1024, 0, c->st>>>(tail_params(c, E, first, c->tt, z0), sc);
+        for (int l = first - 1; l >= 0; --l) {
             const MGLevel &V = E.lv[l];
             const MGWork &W = c->mgw[l];
             const int g = grid_for(V.G.nverts);
@@ -341,17 +430,36 @@ struct Impl {
             k_pcheb<<<g, VEC_THREADS, 0, c->st>>>(V.G, V.A, V.dinv, W.b, W.xb, W.xa, W.d, 0.0, V.invth, sc);
             k_pcheb<<<g, VEC_THREADS, 0, c->st>>>(V.G, V.A, V.dinv, W.b, W.xa, W.xb, W.d, V.c1, V.c2, sc);
         }
-        k_prolong_t<NT><<<gf, VEC_THREADS, 0, c->st>>>(c->M.facet_vert, c->mgw[0].xb, z0, nf, sc);
-        k_tcheb<NT><<<gf, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, r0, z0, c->txa, c->td, 0.0, E.t_invth, nf, sc);
-        k_tcheb<NT><<<gf, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, r0, c->txa, z0, c->td, E.t_c1, E.t_c2, nf, sc);
+        if (first > 0)
+            k_prolong_t<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(c->M.facet_vert, c->mgw[0].xb, z0, nf, sc);
+    }
+
+    // z0 = V-cycle(r0); with fused_start the first Chebyshev step (txa = d = Dinv r0 / theta) has
+    // already been done by the CG update kernel; with rz_first >= 0 the last smoothing step also
+    // performs the CG reduction (k_tcheb_rz).
+    static void vcycle(hdg_ctx *c, const CondCache &E, const double *r0, double *z0, bool fused_start = false,
+                       int rz_first = -1) {
+        const int nf = (int)c->nfacets;
+        const int gf = grid_facets(nf), gr = grid_for(c->nL);
+        Scalars *sc = c->sc;
+        if (!fused_start) k_tcheb0<NT><<<gf, FACET_THREADS, 0, c->st>>>(E.Dinv, r0, c->txa, c->td, E.t_invth, nf, sc);
+        k_tcheb<NT><<<gf, FACET_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, r0, c->txa, z0, c->td, E.t_c1, E.t_c2, nf, sc);
+        k_tresid<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, r0, z0, c->tt, nf, sc);
+        vcycle_p1(c, E, z0);
+        k_tcheb<NT><<<gf, FACET_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, r0, z0, c->txa, c->td, 0.0, E.t_invth, nf, sc);
+        if (rz_first < 0)
+            k_tcheb<NT><<<gf, FACET_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, r0, c->txa, z0, c->td, E.t_c1, E.t_c2, nf, sc);
+        else
+            k_tcheb_rz<NT><<<gf, FACET_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, r0, c->txa, z0, c->td, E.t_c1, E.t_c2, nf,
+                                                           rz_first, c->rb(), sc);
     }
 
     // ---------------------------------------------------------------- trace CG: S x = b
     static void trace_solve(hdg_ctx *c, CondCache &E, const double *b, double *x, double rtol) {
         const int nf = (int)c->nfacets;
+        if (E.mg) { trace_solve_mg(c, E, b, x, rtol); return; }
         k_trace_mean<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(b, nf, c->rb(), c->sc);
         CKL();
-        if (E.mg) { trace_solve_mg(c, E, b, x, rtol); return; }
         k_cg_setup<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(b, E.Dinv, x, c->tr, c->tz, c->tp[0], nf, c->rb(),
                                                                c->sc, rtol, c->P.max_iters);
         CKL();
@@ -385,33 +493,48 @@ struct Impl {
         }
     }
 
-    // CG preconditioned by one multigrid V-cycle per iteration
+    // CG preconditioned by one multigrid V-cycle per iteration. The setup and chunks of 8
+    // iterations are CUDA graphs captured once per operator (input c->tb, solution c->tx); kernels
+    // of a chunk return at once after convergence.
     static void trace_solve_mg(hdg_ctx *c, CondCache &E, const double *b, double *x, double rtol) {
         const int nf = (int)c->nfacets;
         const int gr = grid_for(c->nL);
-        k_cg_setup_mg<NT><<<gr, VEC_THREADS, 0, c->st>>>(b, x, c->tr, c->tp[0], nf, c->sc, rtol, c->P.max_iters);
-        vcycle(c, E, c->tr, c->tz);
-        k_cg_rz<NT><<<gr, VEC_THREADS, 0, c->st>>>(c->tr, c->tz, nf, 1, c->rb(), c->sc);
+        if (b != c->tb) CK(cudaMemcpyAsync(c->tb, b, 8 * c->nL, cudaMemcpyDeviceToDevice, c->st));
+        k_set_tol<<<1, 1, 0, c->st>>>(c->sc, rtol, c->P.max_iters);
         CKL();
-        const int chunk = trace_cg_enabled() ? 1 : 4;
+        const int chunk = trace_cg_enabled() ? 1 : 8;
+        if (!E.g_setup) {
+            E.g_setup = capture_graph(c, [&]() {
+                k_trace_mean<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(c->tb, nf, c->rb(), c->sc);
+                k_cg_setup_mg<NT><<<gr, VEC_THREADS, 0, c->st>>>(c->tb, c->tx, c->tr, c->tp[0], nf, c->sc);
+                vcycle(c, E, c->tr, c->tz, false, 1);
+                CKL();
+            });
+            E.g_chunk = capture_graph(c, [&]() {
+                for (int m = 0; m < chunk; ++m) {
+                    double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
+                    k_cg_apply<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
+                                                                 c->rb(), c->sc);
+                    k_cg_update_cheb0<NT><<<grid_facets(nf), FACET_THREADS, 0, c->st>>>(pnew, c->tAp, c->tx, c->tr, E.Dinv,
+                                                                                        c->txa, c->td, E.t_invth, nf, c->sc);
+                    vcycle(c, E, c->tr, c->tz, true, 0);
+                }
+                CKL();
+            });
+        }
+        CK(cudaGraphLaunch(E.g_setup, c->st));
         for (long long launched = 0;; launched += chunk) {
             if (launched > (long long)c->P.max_iters + 2 * chunk)
                 throw std::length_error("trace CG: no convergence flag from the device");
-            for (int m = 0; m < chunk; ++m) {
-                double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
-                k_cg_apply<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf, c->rb(), c->sc);
-                k_cg_update_nz<<<gr, VEC_THREADS, 0, c->st>>>(pnew, c->tAp, x, c->tr, c->nL, c->sc);
-                vcycle(c, E, c->tr, c->tz);
-                k_cg_rz<NT><<<gr, VEC_THREADS, 0, c->st>>>(c->tr, c->tz, nf, 0, c->rb(), c->sc);
-            }
-            CKL();
+            CK(cudaGraphLaunch(E.g_chunk, c->st));
             read_scalars(c);
             if (trace_cg_enabled())
-                fprintf(stderr, "trace CG it %d rz %.6e pAp %.6e alpha %.3e beta %.3e zmean %.3e relres %.3e done %d bd %d\n",
+                fprintf(stderr, "mg CG it %d rz %.6e pAp %.6e alpha %.3e beta %.3e zmean %.3e relres %.3e done %d bd %d\n",
                         c->hsc->iters, c->hsc->rz, c->hsc->pAp, c->hsc->alpha, c->hsc->beta, c->hsc->zmean,
                         c->hsc->relres, c->hsc->done, c->hsc->breakdown);
             if (c->hsc->done) break;
         }
+        if (x != c->tx) CK(cudaMemcpyAsync(x, c->tx, 8 * c->nL, cudaMemcpyDeviceToDevice, c->st));
         c->S.trace_solves += 1;
         c->S.trace_iters += c->hsc->iters;
         c->S.last_trace_relres = c->hsc->relres;
@@ -430,14 +553,15 @@ struct Impl {
                             const double *lam, double *U, double *dp, double *dl, const double *Rp_add = nullptr,
                             const double *Rl_add = nullptr, double rtol = -1.0) {
         CondCache &E = condense(c, cc);
-        size_t smem_rhs = sizeof(double) * 4 * (NL + 4 * MU + NP + NL);
-        unsigned nb = (unsigned)((c->ncells + 3) / 4);
+        CompTimer tm_(c, &c->S.ms_trace);
+        size_t smem_rhs = sizeof(double) * TEAMS_PER_BLOCK * (NL + 4 * MU + NP + NL);
+        unsigned nb = cell_blocks(c);
         k_mixed_rhs<K><<<nb, 128, smem_rhs, c->st>>>(c->R, c->M, c->P.tau, Ru, X, p, lam, Rp_add, E.Zc, c->vK, c->wK);
         CKL();
         k_facet_gather<NT><<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(c->M, c->vK, Rl_add, c->tb);
         CKL();
         trace_solve(c, E, c->tb, dl, rtol > 0 ? rtol : c->P.trace_rtol);
-        size_t smem_bs = sizeof(double) * 4 * (NL + NP);
+        size_t smem_bs = sizeof(double) * TEAMS_PER_BLOCK * (NL + NP);
         k_mixed_backsub<K><<<nb, 128, smem_bs, c->st>>>(c->R, c->M, cc, Ru, c->wK, dl, E.Zc, E.Ac, U, dp);
         CKL();
     }
@@ -452,6 +576,7 @@ struct Impl {
 
     // ---------------------------------------------------------------- Step I operator
     static void assemble_stepI(hdg_ctx *c, const double *Qs, double cc) {
+        CompTimer tm_(c, &c->S.ms_assembly);
         size_t smem = sizeof(double) * fimpl_smem_doubles<K>();
         CK(cudaFuncSetAttribute(k_fimpl_assemble<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st));
@@ -466,29 +591,45 @@ struct Impl {
     }
 
     // Restarted GMRES(GM_M) on the assembled Step-I operator with right block-Jacobi
-    // preconditioning: B x = b, x0 = 0, stop at ||b - B x|| <= stepI_rtol ||b||.
-    static void stepI_solve(hdg_ctx *c, const double *b, double *x, double rtol = -1.0) {
-        if (!(rtol > 0)) rtol = c->P.stepI_rtol;
+    // preconditioning: B x = b, x0 = 0, stop at ||b - B x|| <= rtol ||b||. One restart cycle is a
+    // CUDA graph (right-hand side c->gb, solution c->gx; kernels return at once after convergence).
+    static void gmres_cycle(hdg_ctx *c, int first, int m) {
         const long long n = c->nQ;
         const int g = grid_for(n);
-        bool first = true;
+        k_gm_start<K><<<g, VEC_THREADS, 0, c->st>>>(c->M, c->Bell, c->gb, c->gx, c->gw, first, c->rb(), c->gs, -1.0, 0);
+        k_gm_set_cycle<<<1, 1, 0, c->st>>>(c->gs, m);
+        for (int j = 0; j < m; ++j) {
+            k_gm_precond<K><<<g, VEC_THREADS, 0, c->st>>>(c->Binv, c->gw, c->gV, c->gz, c->ncells, c->gs);
+            k_gm_apply_dot<K><<<g, VEC_THREADS, 0, c->st>>>(c->M, c->Bell, c->gz, c->gw, c->gV, c->rb(), c->gs);
+            k_gm_orth1<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
+            k_gm_orth2<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
+        }
+        k_gm_solve<<<1, 32, 0, c->st>>>(c->gs, nullptr);
+        k_gm_combine<<<g, VEC_THREADS, 0, c->st>>>(c->gV, c->gu, n, c->gs);
+        k_gm_update_x<K><<<g, VEC_THREADS, 0, c->st>>>(c->Binv, c->gu, c->gx, c->ncells, first);
+        CKL();
+    }
+
+    static void stepI_solve(hdg_ctx *c, const double *b, double *x, double rtol = -1.0) {
+        if (!(rtol > 0)) rtol = c->P.stepI_rtol;
+        CompTimer tm_(c, &c->S.ms_stepI);
+        if (b != c->gb) CK(cudaMemcpyAsync(c->gb, b, 8 * c->nQ, cudaMemcpyDeviceToDevice, c->st));
+        k_gm_set_tol<<<1, 1, 0, c->st>>>(c->gs, rtol, c->P.max_iters);
+        CKL();
+        // loose tolerances (inner solves of the stage preconditioner) converge in a few
+        // iterations: a short cycle avoids launching a full 30-iteration cycle of idle kernels
+        const bool shortc = rtol >= 1e-4;
+        const int m = shortc ? GM_SHORT : GM_M;
+        cudaGraphExec_t &gf = shortc ? c->gms_first : c->gm_first, &gr = shortc ? c->gms_restart : c->gm_restart;
+        if (!gf) {
+            gf = capture_graph(c, [&]() { gmres_cycle(c, 1, m); });
+            gr = capture_graph(c, [&]() { gmres_cycle(c, 0, m); });
+        }
         for (int cyc = 0;; ++cyc) {
-            if (cyc > c->P.max_iters / GM_M + 2) throw std::length_error("GMRES: no convergence flag from the device");
-            k_gm_start<K><<<g, VEC_THREADS, 0, c->st>>>(c->M, c->Bell, b, x, c->gw, first ? 1 : 0, c->rb(), c->gs,
-                                                       rtol, c->P.max_iters);
-            for (int j = 0; j < GM_M; ++j) {
-                k_gm_precond<K><<<g, VEC_THREADS, 0, c->st>>>(c->Binv, c->gw, c->gV, c->gz, c->ncells, c->gs);
-                k_gm_apply_dot<K><<<g, VEC_THREADS, 0, c->st>>>(c->M, c->Bell, c->gz, c->gw, c->gV, c->rb(), c->gs);
-                k_gm_orth1<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
-                k_gm_orth2<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
-            }
-            k_gm_solve<<<1, 32, 0, c->st>>>(c->gs, nullptr);
-            k_gm_combine<<<g, VEC_THREADS, 0, c->st>>>(c->gV, c->gu, n, c->gs);
-            k_gm_update_x<K><<<g, VEC_THREADS, 0, c->st>>>(c->Binv, c->gu, x, c->ncells, first ? 1 : 0);
-            CKL();
+            if (cyc > c->P.max_iters / m + 2) throw std::length_error("GMRES: no convergence flag from the device");
+            CK(cudaGraphLaunch(cyc == 0 ? gf : gr, c->st));
             CK(cudaMemcpyAsync(c->hgs, c->gs, sizeof(GmresState), cudaMemcpyDeviceToHost, c->st));
             CK(cudaStreamSynchronize(c->st));
-            first = false;
             const GmresState &G = *c->hgs;
             if (G.breakdown == 2) throw std::domain_error("GMRES: non-finite residual");
             if (G.converged) break;
@@ -499,6 +640,7 @@ struct Impl {
                 throw std::length_error(msg);
             }
         }
+        if (x != c->gx) CK(cudaMemcpyAsync(x, c->gx, 8 * c->nQ, cudaMemcpyDeviceToDevice, c->st));
         c->S.stepI_solves += 1;
         c->S.stepI_iters += c->hgs->total;
     }
@@ -517,8 +659,8 @@ struct Impl {
         const int nmax = fixed ? c->P.n_richardson : c->P.richardson_max;
         double *BQ = c->q[0], *dr = c->q[1], *Qbar = c->q[2], *X = c->q[3], *U = c->q[4];
         double *dp = c->pp[0], *dl = c->ll[0];
-        size_t smem_res = sizeof(double) * 4 * NL;
-        unsigned nb = (unsigned)((c->ncells + 3) / 4);
+        size_t smem_res = sizeof(double) * TEAMS_PER_BLOCK * NL;
+        unsigned nb = cell_blocks(c);
         int it = 0;
         for (it = 0; it < nmax; ++it) {
             cell_apply(c, Q, BQ);
@@ -539,7 +681,7 @@ struct Impl {
             if (!std::isfinite(dq)) throw std::domain_error("Richardson: non-finite update");
             if (!fixed && dq <= c->P.richardson_rtol * qn) { ++it; break; }
         }
-        c->S.richardson_iters = it;
+        c->S.richardson_iters += it;
         c->S.stage_solves += 1;
         if (!fixed && !(c->S.last_update_norm <= c->P.richardson_rtol * std::sqrt(std::fmax(c->hsc->red1, 0.0))))
             return 1;
@@ -551,11 +693,11 @@ struct Impl {
     static void stage_apply(hdg_ctx *c, double cc, const double *x, double *y) {
         const double *Q = x, *p = x + c->nQ, *lam = x + c->nQ + c->nPv;
         double *yQ = y, *yp = y + c->nQ, *yl = y + c->nQ + c->nPv;
-        unsigned nb = (unsigned)((c->ncells + 3) / 4);
+        unsigned nb = cell_blocks(c);
         cell_apply(c, Q, c->q[6]);
-        k_rich_residual<K><<<nb, 128, sizeof(double) * 4 * NL, c->st>>>(c->R, c->M, cc, nullptr, c->q[6], p, lam, yQ, -1.0);
+        k_rich_residual<K><<<nb, 128, sizeof(double) * TEAMS_PER_BLOCK * NL, c->st>>>(c->R, c->M, cc, nullptr, c->q[6], p, lam, yQ, -1.0);
         CKL();
-        k_constraint<K><<<nb, 128, sizeof(double) * 4 * (NL + 2 * MU), c->st>>>(c->R, c->M, c->P.tau, Q, p, lam, yp, c->vK);
+        k_constraint<K><<<nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (NL + 2 * MU), c->st>>>(c->R, c->M, c->P.tau, Q, p, lam, yp, c->vK);
         CKL();
         k_facet_gather<NT><<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(c->M, c->vK, nullptr, yl);
         CKL();
@@ -602,6 +744,7 @@ struct Impl {
             k_axpby<<<g, VEC_THREADS, 0, c->st>>>(-1.0, w, 1.0, res, N);
             k_vec_start<<<g, VEC_THREADS, 0, c->st>>>(res, N, cyc == 0 ? 2 : 0, c->rb(), c->fgs,
                                                      c->P.richardson_rtol, c->P.richardson_max);
+            k_gm_set_cycle<<<1, 1, 0, c->st>>>(c->fgs, GM_M);
             CKL();
             CK(cudaMemcpyAsync(c->hfgs, c->fgs, sizeof(GmresState), cudaMemcpyDeviceToHost, c->st));
             CK(cudaStreamSynchronize(c->st));
@@ -634,7 +777,7 @@ struct Impl {
         CK(cudaMemcpyAsync(p, x + c->nQ, 8 * c->nPv, cudaMemcpyDeviceToDevice, c->st));
         CK(cudaMemcpyAsync(lam, x + c->nQ + c->nPv, 8 * c->nL, cudaMemcpyDeviceToDevice, c->st));
         mean_shift(c, p, lam);
-        c->S.richardson_iters = outer;
+        c->S.richardson_iters += outer;
         c->S.stage_solves += 1;
         c->S.last_update_norm = c->hfgs->bnorm > 0 ? c->hfgs->resid / c->hfgs->bnorm : 0.0;
         return converged ? 0 : 1;
@@ -649,8 +792,9 @@ struct Impl {
     }
 
     static void bdm(hdg_ctx *c, const double *Q, double *Qs) {
-        unsigned nb = (unsigned)((c->ncells + 3) / 4);
-        k_bdm<K><<<nb, 128, sizeof(double) * 4 * 2 * NU, c->st>>>(c->R, c->M, Q, Qs);
+        CompTimer tm_(c, &c->S.ms_bdm);
+        unsigned nb = cell_blocks(c);
+        k_bdm<K><<<nb, 128, sizeof(double) * TEAMS_PER_BLOCK * 2 * NU, c->st>>>(c->R, c->M, Q, Qs);
         CKL();
     }
 
@@ -814,7 +958,7 @@ void hdg_default_params(hdg_params *p) {
     p->max_iters = 5000;
     p->stage_krylov = 1;
     p->inner_stepI_rtol = 1e-1;
-    p->inner_trace_rtol = 1e-6;
+    p->inner_trace_rtol = 1e-1;
     p->trace_mg = 1;
 }
 
@@ -964,6 +1108,7 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         c->tAp = c->alloc<double>(nL);
         c->gV = c->alloc<double>((size_t)(GM_M + 1) * nQ);
         c->gw = c->alloc<double>(nQ); c->gz = c->alloc<double>(nQ); c->gu = c->alloc<double>(nQ);
+        c->gb = c->alloc<double>(nQ); c->gx = c->alloc<double>(nQ);
         c->gs = c->alloc<GmresState>(1);
         CK(cudaMemset(c->gs, 0, sizeof(GmresState)));
         CK(cudaMallocHost(&c->hgs, sizeof(GmresState)));
@@ -988,6 +1133,9 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         CK(cudaMallocHost(&c->hsc, sizeof(Scalars)));
         CK(cudaEventCreate(&c->e0));
         CK(cudaEventCreate(&c->e1));
+        CK(cudaEventCreate(&c->te0));
+        CK(cudaEventCreate(&c->te1));
+        CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
         CK(cudaDeviceSynchronize());
     } catch (...) {
         hdg_status s = map_exception();
@@ -1002,12 +1150,23 @@ void hdg_destroy(hdg_ctx *c) {
     if (!c) return;
     if (c->st) cudaStreamSynchronize(c->st);
     else cudaDeviceSynchronize();
+    for (auto &E : c->cache) {
+        if (E.g_setup) cudaGraphExecDestroy(E.g_setup);
+        if (E.g_chunk) cudaGraphExecDestroy(E.g_chunk);
+    }
+    if (c->gm_first) cudaGraphExecDestroy(c->gm_first);
+    if (c->gm_restart) cudaGraphExecDestroy(c->gm_restart);
+    if (c->gms_first) cudaGraphExecDestroy(c->gms_first);
+    if (c->gms_restart) cudaGraphExecDestroy(c->gms_restart);
+    if (c->cap) cudaStreamDestroy(c->cap);
     for (void *p : c->allocs) cudaFree(p);
     if (c->hsc) cudaFreeHost(c->hsc);
     if (c->hgs) cudaFreeHost(c->hgs);
     if (c->hfgs) cudaFreeHost(c->hfgs);
     if (c->e0) cudaEventDestroy(c->e0);
     if (c->e1) cudaEventDestroy(c->e1);
+    if (c->te0) cudaEventDestroy(c->te0);
+    if (c->te1) cudaEventDestroy(c->te1);
     delete c;
 }
 

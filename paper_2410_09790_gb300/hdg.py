@@ -46,7 +46,8 @@ class hdg_stats(ctypes.Structure):
                 ('trace_iters', ctypes.c_int), ('stepI_solves', ctypes.c_int),
                 ('stepI_iters', ctypes.c_int), ('stage_solves', ctypes.c_int),
                 ('last_update_norm', ctypes.c_double), ('last_trace_relres', ctypes.c_double),
-                ('ms_total', ctypes.c_double)]
+                ('ms_total', ctypes.c_double), ('ms_trace', ctypes.c_double), ('ms_stepI', ctypes.c_double),
+                ('ms_assembly', ctypes.c_double), ('ms_bdm', ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
