@@ -167,7 +167,7 @@ def run_gpu(args, rank, world, local_rank):
                         dt=w['dt'], n_richardson=w['n_richardson'], richardson_rtol=w['stage_rtol'],
                         richardson_max=600, stage_krylov=1, inner_stepI_rtol=w['inner_stepI_rtol'],
                         inner_trace_rtol=w['inner_trace_rtol'], trace_rtol=w['trace_rtol'],
-                        stepI_rtol=w['stepI_rtol'])
+                        stepI_rtol=w['stepI_rtol'], device_loops=0 if args.host_loops else 1)
         Q0 = torch.from_numpy(initial_velocity(w, seed_offset=rank)).to(dev)
         ctx.hdg_set_state(Q0)
         ctx.hdg_div_free_project()
@@ -264,26 +264,16 @@ def run_gpu(args, rank, world, local_rank):
         'clocks': clk.summary(),
         'gpu_launches': None,
     }
-    # kernel launches inside one step, counted from the solver statistics
-    per_step = stats_all[-1]
-    line['gpu_launches'] = int(args.steps * launches_per_step(per_step, stages))
+    # kernels launched inside the timed steps: counted exactly by the library (graph kernel nodes
+    # plus every pass of the device-side loops); with host-driven loops it is not counted (None)
+    launches = sum(s['graph_kernels'] for s in stats_all)
+    line['gpu_launches'] = int(launches) if launches > 0 else None
+    line['config']['loops'] = 'host' if args.host_loops else 'device (one CUDA graph per IMEX step)'
     if rank == 0 and not args.no_cpu_baseline:
         r, s, desc, cores = oracle_sample(w, steps=1)
         line['cpu_baseline'] = {'value': r, 'unit': 'stage_solves/s', 'cores': cores, 'kind': 'oracle', 'sample': desc}
     if rank == 0:
         print(json.dumps(line), flush=True)
-
-
-def launches_per_step(st, stages):
-    """Kernel launches of one IMEX step: per CG solve 2 setup + 2 per iteration rounded up to the
-    16-iteration chunk; per GMRES cycle 1 + 4 x 30 + 3; plus the fixed per-stage,
-    per-solve and per-step kernels (stage rhs, BDM, assembly, residual, updates, condensation rhs
-    / gather / back-substitution, mean shift)."""
-    import math
-    cg = st['trace_solves'] * 2 + 2 * 16 * math.ceil(st['trace_iters'] / max(st['trace_solves'], 1) / 16) * st['trace_solves']
-    bi = st['stepI_solves'] * (1 + 4 * 30 + 3) * math.ceil(st['stepI_iters'] / max(st['stepI_solves'], 1) / 30)
-    fixed = st['trace_solves'] * 3 + st['stepI_solves'] * 4 + stages * 3 + 8
-    return cg + bi + fixed
 
 
 def main():
@@ -297,6 +287,8 @@ def main():
     ap.add_argument('--n', type=int, default=None, help='mesh size override (profiling runs only)')
     ap.add_argument('--inner-trace-rtol', type=float, default=None, help='tuning: inner Step II tolerance')
     ap.add_argument('--inner-stepI-rtol', type=float, default=None, help='tuning: inner Step I tolerance')
+    ap.add_argument('--host-loops', action='store_true',
+                    help='drive the Krylov loops from the host (fills the per-component timings)')
     ap.add_argument('--kernel-only', type=int, default=None,
                     help='profiling: set up the workload, take one step, then launch kernel K '
                          '(0 trace apply, 1 tentative-velocity apply) --steps times and exit')

@@ -93,6 +93,13 @@ typedef struct {
      * on the coarsest grid, which must have <= 1024 vertices, else block-Jacobi is used);
      * 0 = facet block-Jacobi. */
     int trace_mg;
+    /* Stage solves with stage_krylov = 1: 1 (default) records the whole flexible GMRES, with its
+     * inner Step-I GMRES and trace CG, as one CUDA graph whose loops run on the device
+     * (conditional graph nodes, each with an iteration guard) and replays it per stage: no host
+     * round trip inside a stage solve; inner solves that stop at their iteration cap do not raise
+     * an error there (the outer residual test decides). 0 = loops driven from the host (per-
+     * component timings in hdg_stats are only filled in this mode). */
+    int device_loops;
 } hdg_params;
 
 typedef struct {
@@ -112,6 +119,10 @@ typedef struct {
     double ms_stepI;
     double ms_assembly;
     double ms_bdm;
+    /* kernels run by the call's CUDA graphs (device_loops = 1): the graphs' kernel nodes plus
+     * every pass of their device-side loops, counted exactly on the device; in that mode an IMEX
+     * step (stage_krylov = 1, no forcing callback) is one graph, so this counts all of its kernels */
+    long long graph_kernels;
 } hdg_stats;
 
 void hdg_default_params(hdg_params *p);

@@ -534,6 +534,72 @@ struct GmresState {
 
 __global__ void k_gm_set_cycle(GmresState *gs, int m) { gs->m = m; }
 
+// ------------------------------------------------------------------ device-side loops
+// Control of a while loop that runs as a CUDA graph conditional node: one thread sets the
+// node's condition. Every loop carries a guard counter with a hard limit, so that it ends
+// even if the solver never raises its stop flag. Each pass also adds the number of kernels in
+// the loop body (*nk, filled in after the body is recorded) to the launch counter.
+struct LoopCtl {
+    cudaGraphConditionalHandle h;
+    int *guard;
+    const int *nk;
+    unsigned long long *launches;
+};
+
+__global__ void k_loop_init(LoopCtl L, const int *stop) {
+    *L.guard = 0;
+    cudaGraphSetConditional(L.h, *stop ? 0u : 1u);
+}
+
+__global__ void k_loop_ctl(LoopCtl L, int limit, const int *stop) {
+    const int gd = ++*L.guard;
+    *L.launches += (unsigned long long)*L.nk;
+    cudaGraphSetConditional(L.h, (!*stop && gd < limit) ? 1u : 0u);
+}
+
+// restart loop of a GMRES: continue while not converged, finite and under the iteration cap
+__global__ void k_gm_loop_ctl(LoopCtl L, int limit, const GmresState *gs, int init) {
+    int gd = 0;
+    if (init) *L.guard = 0;
+    else {
+        gd = ++*L.guard;
+        *L.launches += (unsigned long long)*L.nk;
+    }
+    const bool more = !gs->converged && gs->breakdown != 2 && gs->total < gs->maxit && gd < limit;
+    cudaGraphSetConditional(L.h, more ? 1u : 0u);
+}
+
+// Z[j] = z with j = gs->j (basis slot of the current Arnoldi step)
+__global__ void k_slot_store(const double *__restrict__ z, double *Z, long long n, const GmresState *gs) {
+    if (gs->cycle_end) return;
+    double *zj = Z + (size_t)gs->j * n;
+    GRID_STRIDE(i, n) zj[i] = z[i];
+}
+
+// Solve counters kept on the device (DevCount fields: see the struct)
+struct DevCount {
+    long long stepI_iters, stepI_solves, trace_iters, trace_solves;
+    long long outer_iters, stage_solves, stage_unconverged, breakdowns;
+    unsigned long long launches;      // kernels run inside device-side loops
+    long long pad[7];
+};
+
+__global__ void k_count_solve(DevCount *acc, const GmresState *gs, const Scalars *sc) {
+    if (gs) { acc->stepI_iters += gs->total; acc->stepI_solves += 1; }
+    if (sc) {
+        acc->trace_iters += sc->iters; acc->trace_solves += 1;
+        if (sc->breakdown == 2) acc->breakdowns += 1;
+    }
+}
+
+// after a stage solve by flexible GMRES
+__global__ void k_count_stage(DevCount *acc, const GmresState *fgs) {
+    acc->outer_iters += fgs->total;
+    acc->stage_solves += 1;
+    if (!fgs->converged) acc->stage_unconverged += 1;
+    if (fgs->breakdown == 2) acc->breakdowns += 1;
+}
+
 // w (local row values) dotted with V_0..V_{nvec-1}: each thread holds its rows' w in a loop
 template <class WF>
 __device__ bool multidot_rows(const RedBuf rb, const double *V, long long n, int nvec, WF wfun, double *out) {
@@ -810,7 +876,7 @@ __global__ void k_vec_start(const double *__restrict__ r, long long n, int first
         gs->g[0] = beta;
         gs->j = 0;
         if (!isfinite(beta)) { gs->breakdown = 2; gs->cycle_end = 1; }
-        else if (beta <= rtol * gs->bnorm || beta == 0.0) { gs->converged = 1; gs->cycle_end = 1; }
+        else if (beta <= gs->rtol * gs->bnorm || beta == 0.0) { gs->converged = 1; gs->cycle_end = 1; }
         else gs->cycle_end = 0;
     }
 }
@@ -821,14 +887,21 @@ __global__ void k_vec_norm_into(const double *__restrict__ b, long long n, RedBu
     if (grid_sum<1>(rb, v, tot)) gs->bnorm = sqrt(tot[0]);
 }
 
-// V_j = w / h  (h = beta for j = 0, else H[j, j-1])
-__global__ void k_vec_normalize(const double *__restrict__ w, double *V, long long n, const GmresState *gs) {
+// V_j = w / h  (w = w0 and h = beta for j = 0, else w and H[j, j-1]); vfix (optional) gets a
+// copy of V_j at a fixed address
+__global__ void k_vec_normalize(const double *__restrict__ w0, const double *__restrict__ w, double *V,
+                                double *vfix, long long n, const GmresState *gs) {
     if (gs->cycle_end) return;
     const int j = gs->j;
     const double h = j == 0 ? gs->beta : gs->H[(j - 1) * (GM_M + 1) + j];
     const double inv = 1.0 / h;
+    const double *src = j == 0 ? w0 : w;
     double *vj = V + (size_t)j * n;
-    GRID_STRIDE(i, n) vj[i] = w[i] * inv;
+    GRID_STRIDE(i, n) {
+        double v = src[i] * inv;
+        vj[i] = v;
+        if (vfix) vfix[i] = v;
+    }
 }
 
 // hcol = V^T w over V_0..V_j

@@ -98,6 +98,8 @@ struct CondCache {
     // multigrid (empty: facet block-Jacobi CG)
     bool mg = false;
     cudaGraphExec_t g_setup = nullptr, g_chunk = nullptr;   // captured MG-CG setup / 8 iterations
+    cudaGraphExec_t g_stage = nullptr;                      // whole stage solve, device-side loops
+    int stage_kernels = 0;                                  // its kernels outside the loops
     double t_invth = 0, t_c1 = 0, t_c2 = 0;   // trace-level Chebyshev
     std::vector<MGLevel> lv;                  // lv[0] = level 1 (P1 on the mesh), ...
     double *Minv = nullptr;
@@ -155,6 +157,7 @@ struct hdg_ctx {
     GmresState *gs = nullptr, *hgs = nullptr;
     // flexible GMRES on the stage system (vectors of nQ + np + nlambda)
     double *fV = nullptr, *fZ = nullptr, *fx = nullptr, *fb = nullptr, *fw = nullptr, *fr = nullptr, *fu = nullptr;
+    double *fv = nullptr, *fz = nullptr;                     // preconditioner input / output (fixed)
     GmresState *fgs = nullptr, *hfgs = nullptr;
     // temporaries
     double *q[8] = {};
@@ -172,6 +175,18 @@ struct hdg_ctx {
     std::deque<CondCache> cache;
     cudaEvent_t e0 = nullptr, e1 = nullptr, te0 = nullptr, te1 = nullptr;
     cudaStream_t cap = nullptr;                              // capture stream for CUDA graphs
+    static constexpr int CAP_LEVELS = 8;
+    cudaStream_t capst[CAP_LEVELS] = {};                     // capture streams of nested loop bodies
+    int cap_level = 0;                                       // nesting depth of the current capture
+    bool capturing = false;
+    int *dguard = nullptr;                                   // loop guards, one per nesting level
+    static constexpr int MAX_LOOPS = 512;
+    int *dnk = nullptr;                                      // kernels per pass of each recorded loop
+    int nloops = 0;
+    std::vector<int> nk_host;                                // host copy of dnk
+    DevCount *dcnt = nullptr, *hcnt = nullptr;               // device-side counters (+ pinned mirror)
+    cudaGraphExec_t g_step = nullptr;                        // one IMEX step (device-side loops)
+    int step_kernels = 0;                                    // kernels of g_step outside its loops
     cudaGraphExec_t gm_first = nullptr, gm_restart = nullptr;   // captured GMRES(30) cycles
     cudaGraphExec_t gms_first = nullptr, gms_restart = nullptr; // captured GMRES(GM_SHORT) cycles
     double *gb = nullptr, *gx = nullptr;                     // their fixed right-hand side / solution
@@ -219,12 +234,16 @@ inline int grid_facets(long long nf) { return (int)((nf + FACET_THREADS - 1) / F
 
 // Component timer: events around one component on the context's stream; the elapsed time is
 // added to a hdg_stats bucket when the component ends (each component ends with a host sync).
+// Inside a graph capture the timer does nothing.
 struct CompTimer {
     hdg_ctx *c;
     double *bucket;
-    CompTimer(hdg_ctx *c_, double *b) : c(c_), bucket(b) { CK(cudaEventRecord(c->te0, c->st)); }
+    CompTimer(hdg_ctx *c_, double *b) : c(c_), bucket(b) {
+        if (c->capturing) bucket = nullptr;
+        else CK(cudaEventRecord(c->te0, c->st));
+    }
     ~CompTimer() noexcept(false) {
-        if (std::uncaught_exceptions()) return;
+        if (!bucket || std::uncaught_exceptions()) return;
         CK(cudaEventRecord(c->te1, c->st));
         CK(cudaEventSynchronize(c->te1));
         float ms = 0;
@@ -234,10 +253,27 @@ struct CompTimer {
 };
 
 // Record the launches issued by f (on c->st, temporarily the capture stream) into a graph.
+// kernel nodes of a graph, not counting the bodies of its conditional nodes
+int count_kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    CK(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n) CK(cudaGraphGetNodes(g, nodes.data(), &n));
+    int k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        CK(cudaGraphNodeGetType(nodes[i], &t));
+        if (t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
 template <class F>
-cudaGraphExec_t capture_graph(hdg_ctx *c, F &&f) {
+cudaGraphExec_t capture_graph(hdg_ctx *c, F &&f, int *nkernels = nullptr) {
     cudaStream_t user = c->st;
     c->st = c->cap;
+    c->capturing = true;
+    c->cap_level = 0;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
@@ -247,17 +283,78 @@ cudaGraphExec_t capture_graph(hdg_ctx *c, F &&f) {
             cudaStreamEndCapture(c->cap, &g);
             if (g) cudaGraphDestroy(g);
             c->st = user;
+            c->capturing = false;
             throw;
         }
         e = cudaStreamEndCapture(c->cap, &g);
     }
     c->st = user;
+    c->capturing = false;
     CK(e);
+    if (nkernels) *nkernels = count_kernel_nodes(g);
+    // kernels per pass of the loops recorded in this capture
+    CK(cudaMemcpy(c->dnk, c->nk_host.data(), sizeof(int) * c->nloops, cudaMemcpyHostToDevice));
     cudaGraphExec_t ex = nullptr;
     e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
     CK(e);
     return ex;
+}
+
+// Inside a capture on c->st: append a device-side while loop (a conditional graph node).
+// init(L) launches, on c->st, the kernel that sets the loop's first condition; the body is
+// recorded from body(L) on the next nesting level's stream into the node's body graph and must
+// end with a kernel that sets the condition for the next pass (k_loop_ctl or k_gm_loop_ctl).
+template <class Init, class Body>
+void capture_while(hdg_ctx *c, Init &&init, Body &&body) {
+    if (!c->capturing) throw std::logic_error("capture_while outside a graph capture");
+    const int lev = c->cap_level + 1;
+    if (lev >= hdg_ctx::CAP_LEVELS) throw std::logic_error("device loops nested too deeply");
+    if (c->nloops >= hdg_ctx::MAX_LOOPS) throw std::logic_error("too many device loops recorded");
+    const int id = c->nloops++;
+    c->nk_host.resize(c->nloops, 0);
+    cudaStream_t s = c->st;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    LoopCtl L{};
+    CK(cudaGraphConditionalHandleCreate(&L.h, g, 0, 0));
+    L.guard = c->dguard + lev;
+    L.nk = c->dnk + id;
+    L.launches = &c->dcnt->launches;
+    init(L);
+    CKL();
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = L.h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+    cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+    if (!c->capst[lev]) CK(cudaStreamCreateWithFlags(&c->capst[lev], cudaStreamNonBlocking));
+    cudaStream_t bs = c->capst[lev];
+    CK(cudaStreamBeginCaptureToGraph(bs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    c->st = bs;
+    c->cap_level = lev;
+    cudaGraph_t outg = nullptr;
+    try {
+        body(L);
+        CKL();
+    } catch (...) {
+        cudaStreamEndCapture(bs, &outg);
+        c->st = s;
+        c->cap_level = lev - 1;
+        throw;
+    }
+    c->st = s;
+    c->cap_level = lev - 1;
+    CK(cudaStreamEndCapture(bs, &outg));
+    c->nk_host[id] = count_kernel_nodes(bodyg);
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
 }
 
 template <int K>
@@ -289,6 +386,7 @@ struct Impl {
     static CondCache &condense(hdg_ctx *c, double cc) {
         for (auto &e : c->cache)
             if (e.c == cc) return e;
+        if (c->capturing) throw std::logic_error("condensation for a new coefficient inside a graph capture");
         CondCache E;
         E.c = cc;
         E.Scell = c->alloc<double>((size_t)c->ncells * NL * NL);
@@ -464,6 +562,23 @@ struct Impl {
                                                                c->sc, rtol, c->P.max_iters);
         CKL();
         const int gr = grid_for(c->nL), gf = grid_for(nf);
+        if (c->capturing) {             // device-side loop, two iterations per pass
+            capture_while(
+                c, [&](LoopCtl L) { k_loop_init<<<1, 1, 0, c->st>>>(L, &c->sc->done); },
+                [&](LoopCtl L) {
+                    for (int m = 0; m < 2; ++m) {
+                        double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
+                        k_cg_apply<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
+                                                                     c->rb(), c->sc);
+                        k_cg_update<NT><<<gf, VEC_THREADS, 0, c->st>>>(E.Dinv, pnew, c->tAp, x, c->tr, c->tz, nf,
+                                                                      c->rb(), c->sc);
+                    }
+                    k_loop_ctl<<<1, 1, 0, c->st>>>(L, c->P.max_iters / 2 + 2, &c->sc->done);
+                });
+            k_count_solve<<<1, 1, 0, c->st>>>(c->dcnt, nullptr, c->sc);
+            CKL();
+            return;
+        }
         const int chunk = trace_cg_enabled() ? 2 : 16;
         for (long long launched = 0;; launched += chunk) {
             if (launched > (long long)c->P.max_iters + 2 * chunk)
@@ -502,6 +617,28 @@ struct Impl {
         if (b != c->tb) CK(cudaMemcpyAsync(c->tb, b, 8 * c->nL, cudaMemcpyDeviceToDevice, c->st));
         k_set_tol<<<1, 1, 0, c->st>>>(c->sc, rtol, c->P.max_iters);
         CKL();
+        if (c->capturing) {             // device-side loop, two iterations per pass
+            k_trace_mean<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(c->tb, nf, c->rb(), c->sc);
+            k_cg_setup_mg<NT><<<gr, VEC_THREADS, 0, c->st>>>(c->tb, c->tx, c->tr, c->tp[0], nf, c->sc);
+            vcycle(c, E, c->tr, c->tz, false, 1);
+            capture_while(
+                c, [&](LoopCtl L) { k_loop_init<<<1, 1, 0, c->st>>>(L, &c->sc->done); },
+                [&](LoopCtl L) {
+                    for (int m = 0; m < 2; ++m) {
+                        double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
+                        k_cg_apply<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
+                                                                     c->rb(), c->sc);
+                        k_cg_update_cheb0<NT><<<grid_facets(nf), FACET_THREADS, 0, c->st>>>(
+                            pnew, c->tAp, c->tx, c->tr, E.Dinv, c->txa, c->td, E.t_invth, nf, c->sc);
+                        vcycle(c, E, c->tr, c->tz, true, 0);
+                    }
+                    k_loop_ctl<<<1, 1, 0, c->st>>>(L, c->P.max_iters / 2 + 2, &c->sc->done);
+                });
+            if (x != c->tx) CK(cudaMemcpyAsync(x, c->tx, 8 * c->nL, cudaMemcpyDeviceToDevice, c->st));
+            k_count_solve<<<1, 1, 0, c->st>>>(c->dcnt, nullptr, c->sc);
+            CKL();
+            return;
+        }
         const int chunk = trace_cg_enabled() ? 1 : 8;
         if (!E.g_setup) {
             E.g_setup = capture_graph(c, [&]() {
@@ -579,7 +716,7 @@ struct Impl {
         CompTimer tm_(c, &c->S.ms_assembly);
         size_t smem = sizeof(double) * fimpl_smem_doubles<K>();
         CK(cudaFuncSetAttribute(k_fimpl_assemble<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st));
+        if (!c->capturing) CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st));   // (graphs: once per launch)
         k_fimpl_assemble<K><<<(unsigned)c->ncells, 128, smem, c->st>>>(c->R, c->M, Qs, cc, c->P.alpha, c->P.delta_up,
                                                                       c->Bell, c->Binv, c->dstatus);
         CKL();
@@ -610,6 +747,27 @@ struct Impl {
         CKL();
     }
 
+    // The same cycle with its Arnoldi steps as a device-side loop (inside a graph capture).
+    static void gmres_cycle_dev(hdg_ctx *c, int first, int m) {
+        const long long n = c->nQ;
+        const int g = grid_for(n);
+        k_gm_start<K><<<g, VEC_THREADS, 0, c->st>>>(c->M, c->Bell, c->gb, c->gx, c->gw, first, c->rb(), c->gs, -1.0, 0);
+        k_gm_set_cycle<<<1, 1, 0, c->st>>>(c->gs, m);
+        capture_while(
+            c, [&](LoopCtl L) { k_loop_init<<<1, 1, 0, c->st>>>(L, &c->gs->cycle_end); },
+            [&](LoopCtl L) {
+                k_gm_precond<K><<<g, VEC_THREADS, 0, c->st>>>(c->Binv, c->gw, c->gV, c->gz, c->ncells, c->gs);
+                k_gm_apply_dot<K><<<g, VEC_THREADS, 0, c->st>>>(c->M, c->Bell, c->gz, c->gw, c->gV, c->rb(), c->gs);
+                k_gm_orth1<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
+                k_gm_orth2<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
+                k_loop_ctl<<<1, 1, 0, c->st>>>(L, m + 1, &c->gs->cycle_end);
+            });
+        k_gm_solve<<<1, 32, 0, c->st>>>(c->gs, nullptr);
+        k_gm_combine<<<g, VEC_THREADS, 0, c->st>>>(c->gV, c->gu, n, c->gs);
+        k_gm_update_x<K><<<g, VEC_THREADS, 0, c->st>>>(c->Binv, c->gu, c->gx, c->ncells, first);
+        CKL();
+    }
+
     static void stepI_solve(hdg_ctx *c, const double *b, double *x, double rtol = -1.0) {
         if (!(rtol > 0)) rtol = c->P.stepI_rtol;
         CompTimer tm_(c, &c->S.ms_stepI);
@@ -620,6 +778,20 @@ struct Impl {
         // iterations: a short cycle avoids launching a full 30-iteration cycle of idle kernels
         const bool shortc = rtol >= 1e-4;
         const int m = shortc ? GM_SHORT : GM_M;
+        if (c->capturing) {             // restarts as a device-side loop
+            gmres_cycle_dev(c, 1, m);
+            const int limit = c->P.max_iters + 2;
+            capture_while(
+                c, [&](LoopCtl L) { k_gm_loop_ctl<<<1, 1, 0, c->st>>>(L, limit, c->gs, 1); },
+                [&](LoopCtl L) {
+                    gmres_cycle_dev(c, 0, m);
+                    k_gm_loop_ctl<<<1, 1, 0, c->st>>>(L, limit, c->gs, 0);
+                });
+            if (x != c->gx) CK(cudaMemcpyAsync(x, c->gx, 8 * c->nQ, cudaMemcpyDeviceToDevice, c->st));
+            k_count_solve<<<1, 1, 0, c->st>>>(c->dcnt, c->gs, nullptr);
+            CKL();
+            return;
+        }
         cudaGraphExec_t &gf = shortc ? c->gms_first : c->gm_first, &gr = shortc ? c->gms_restart : c->gm_restart;
         if (!gf) {
             gf = capture_graph(c, [&]() { gmres_cycle(c, 1, m); });
@@ -716,16 +888,85 @@ struct Impl {
         CKL();
     }
 
+    // The flexible GMRES of a stage solve recorded into the current graph capture (x = c->fx,
+    // b = c->fb): restart cycles, Arnoldi steps, and the inner Step-I GMRES and trace CG are
+    // device-side while loops (conditional graph nodes), so a stage solve needs no host round trip.
+    static void stage_fgmres_capture(hdg_ctx *c, double cc) {
+        const long long N = c->nQ + c->nPv + c->nL;
+        const int g = grid_for(N);
+        double *x = c->fx, *b = c->fb, *w = c->fw, *res = c->fr, *u = c->fu;
+        GmresState *fgs = c->fgs;
+        const double rtol = c->P.richardson_rtol;
+        const int maxit = c->P.richardson_max;
+        auto residual = [&](int first) {            // res = b - A x; cycle start
+            stage_apply(c, cc, x, w);
+            CK(cudaMemcpyAsync(res, b, 8 * N, cudaMemcpyDeviceToDevice, c->st));
+            k_axpby<<<g, VEC_THREADS, 0, c->st>>>(-1.0, w, 1.0, res, N);
+            k_vec_start<<<g, VEC_THREADS, 0, c->st>>>(res, N, first, c->rb(), fgs, rtol, maxit);
+            k_gm_set_cycle<<<1, 1, 0, c->st>>>(fgs, GM_M);
+            CKL();
+        };
+        k_vec_norm_into<<<g, VEC_THREADS, 0, c->st>>>(b, N, c->rb(), fgs);
+        residual(2);
+        capture_while(
+            c, [&](LoopCtl L) { k_gm_loop_ctl<<<1, 1, 0, c->st>>>(L, maxit + 2, fgs, 1); },
+            [&](LoopCtl L) {
+                capture_while(
+                    c, [&](LoopCtl L2) { k_loop_init<<<1, 1, 0, c->st>>>(L2, &fgs->cycle_end); },
+                    [&](LoopCtl L2) {
+                        k_vec_normalize<<<g, VEC_THREADS, 0, c->st>>>(res, w, c->fV, c->fv, N, fgs);
+                        CKL();
+                        chorin_precond(c, cc, c->fv, c->fz);
+                        k_slot_store<<<g, VEC_THREADS, 0, c->st>>>(c->fz, c->fZ, N, fgs);
+                        stage_apply(c, cc, c->fz, w);
+                        k_vec_dot<<<g, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
+                        k_gm_orth1<<<g, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
+                        k_gm_orth2<<<g, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
+                        k_loop_ctl<<<1, 1, 0, c->st>>>(L2, GM_M + 1, &fgs->cycle_end);
+                        CKL();
+                    });
+                k_gm_solve<<<1, 32, 0, c->st>>>(fgs, nullptr);
+                k_gm_combine<<<g, VEC_THREADS, 0, c->st>>>(c->fZ, u, N, fgs);
+                k_vec_add<<<g, VEC_THREADS, 0, c->st>>>(u, x, N);
+                residual(0);
+                k_gm_loop_ctl<<<1, 1, 0, c->st>>>(L, maxit + 2, fgs, 0);
+                CKL();
+            });
+        k_count_stage<<<1, 1, 0, c->st>>>(c->dcnt, fgs);
+        CKL();
+    }
+
+    // device counters of a graph launch -> stats; errors the device recorded
+    static void graph_stats(hdg_ctx *c, int static_kernels) {
+        const DevCount &D = *c->hcnt;
+        c->S.stepI_iters += (int)D.stepI_iters;
+        c->S.stepI_solves += (int)D.stepI_solves;
+        c->S.trace_iters += (int)D.trace_iters;
+        c->S.trace_solves += (int)D.trace_solves;
+        c->S.richardson_iters += (int)D.outer_iters;
+        c->S.stage_solves += (int)D.stage_solves;
+        c->S.graph_kernels += (long long)static_kernels + (long long)D.launches;
+        if (D.breakdowns) throw std::domain_error("device-side solve: non-finite residual");
+    }
+
+    static void launch_counted(hdg_ctx *c, cudaGraphExec_t ex) {
+        CK(cudaMemsetAsync(c->dcnt, 0, sizeof(DevCount), c->st));
+        CK(cudaGraphLaunch(ex, c->st));
+        CK(cudaMemcpyAsync(c->hcnt, c->dcnt, sizeof(DevCount), cudaMemcpyDeviceToHost, c->st));
+    }
+
     // Stage solve to tolerance: flexible GMRES(GM_M) on A(c) x = (r, 0, 0) right-preconditioned by
     // the Chorin split (Alg. 2's preconditioner; plain Alg. 2 is its Richardson iteration).
     static int stage_fgmres(hdg_ctx *c, double cc, const double *r, const double *Qsv, double *Q, double *p,
                             double *lam) {
         assemble_stepI(c, Qsv, cc);
-        int hstat = 0;
-        CK(cudaMemcpyAsync(&hstat, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-        condense(c, cc);
-        CK(cudaStreamSynchronize(c->st));
-        if (hstat) throw std::domain_error("singular tentative-velocity block");
+        CondCache &E = condense(c, cc);
+        if (!c->capturing) {
+            int hstat = 0;
+            CK(cudaMemcpyAsync(&hstat, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+            CK(cudaStreamSynchronize(c->st));
+            if (hstat) throw std::domain_error("singular tentative-velocity block");
+        }
         const long long N = c->nQ + c->nPv + c->nL;
         const int g = grid_for(N);
         double *x = c->fx, *b = c->fb, *w = c->fw, *res = c->fr, *u = c->fu;
@@ -735,6 +976,23 @@ struct Impl {
         CK(cudaMemcpyAsync(x + c->nQ + c->nPv, lam, 8 * c->nL, cudaMemcpyDeviceToDevice, c->st));
         CK(cudaMemcpyAsync(b, r, 8 * c->nQ, cudaMemcpyDeviceToDevice, c->st));
         CK(cudaMemsetAsync(b + c->nQ, 0, 8 * (c->nPv + c->nL), c->st));
+        if (c->capturing || c->P.device_loops) {
+            if (c->capturing) {
+                stage_fgmres_capture(c, cc);
+            } else {
+                if (!E.g_stage) E.g_stage = capture_graph(c, [&]() { stage_fgmres_capture(c, cc); }, &E.stage_kernels);
+                launch_counted(c, E.g_stage);
+                CK(cudaMemcpyAsync(c->hfgs, c->fgs, sizeof(GmresState), cudaMemcpyDeviceToHost, c->st));
+                CK(cudaStreamSynchronize(c->st));
+                graph_stats(c, E.stage_kernels);
+                c->S.last_update_norm = c->hfgs->bnorm > 0 ? c->hfgs->resid / c->hfgs->bnorm : 0.0;
+            }
+            CK(cudaMemcpyAsync(Q, x, 8 * c->nQ, cudaMemcpyDeviceToDevice, c->st));
+            CK(cudaMemcpyAsync(p, x + c->nQ, 8 * c->nPv, cudaMemcpyDeviceToDevice, c->st));
+            CK(cudaMemcpyAsync(lam, x + c->nQ + c->nPv, 8 * c->nL, cudaMemcpyDeviceToDevice, c->st));
+            mean_shift(c, p, lam);
+            return c->capturing ? 0 : (c->hfgs->converged ? 0 : 1);
+        }
         k_vec_norm_into<<<g, VEC_THREADS, 0, c->st>>>(b, N, c->rb(), c->fgs);
         CKL();
         int outer = 0, converged = 0;
@@ -751,7 +1009,7 @@ struct Impl {
             if (c->hfgs->breakdown == 2) throw std::domain_error("stage FGMRES: non-finite residual");
             if (c->hfgs->converged) { converged = 1; break; }
             for (int j = 0; j < GM_M; ++j) {
-                k_vec_normalize<<<g, VEC_THREADS, 0, c->st>>>(j == 0 ? res : w, c->fV, N, c->fgs);
+                k_vec_normalize<<<g, VEC_THREADS, 0, c->st>>>(res, w, c->fV, nullptr, N, c->fgs);
                 CKL();
                 double *Vj = c->fV + (size_t)j * N, *Zj = c->fZ + (size_t)j * N;
                 chorin_precond(c, cc, Vj, Zj);
@@ -825,9 +1083,11 @@ struct Impl {
     }
 
     // ---------------------------------------------------------------- Alg. 1
-    static int imex_step(hdg_ctx *c) {
+    // One step from t0 (c->t is not advanced here). Inside a graph capture every solve is recorded
+    // with device-side loops and the return value is 0 (non-convergence is counted on the device).
+    static int imex_step_body(hdg_ctx *c, double t0) {
         const Tab &T = c->tab;
-        const double dt = c->P.dt, t0 = c->t;
+        const double dt = c->P.dt;
         const int s = T.s;
         double fval[4] = {0, 0, 0, 0};
         for (int j = 0; j < s; ++j) fval[j] = c->has_forcing ? (c->phi ? c->phi(t0 + T.c[j] * dt, c->phi_user) : 1.0) : 0.0;
@@ -881,9 +1141,39 @@ struct Impl {
         k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, L, rn, c->ncells);
         CKL();
         mixed_solve(c, dt * T.bi[s - 1], rn, nullptr, nullptr, nullptr, c->Q, c->pp[1], c->ll[1]);
-        c->t = t0 + dt;
-        reconstruct(c, c->Q, c->t, c->p, c->lam);                               // Sec. 2.7
+        reconstruct(c, c->Q, t0 + dt, c->p, c->lam);                            // Sec. 2.7
         return nc;
+    }
+
+    // The step as one CUDA graph: stages solved by flexible GMRES with device-side loops, no
+    // time-dependent forcing callback (its values would be frozen into the graph).
+    static bool step_graph_ok(const hdg_ctx *c) {
+        return c->P.device_loops && c->P.n_richardson <= 0 && c->P.stage_krylov && !(c->has_forcing && c->phi);
+    }
+
+    static int imex_step(hdg_ctx *c) {
+        const double t0 = c->t, dt = c->P.dt;
+        if (!step_graph_ok(c)) {
+            int nc = imex_step_body(c, t0);
+            c->t = t0 + dt;
+            return nc;
+        }
+        if (!c->g_step) {
+            const Tab &T = c->tab;                      // condensations the step uses, built first
+            for (int i = 1; i < T.s; ++i) condense(c, T.Ai[i][i] * dt);
+            condense(c, dt * T.bi[T.s - 1]);
+            condense(c, 1.0);
+            c->g_step = capture_graph(c, [&]() { imex_step_body(c, t0); }, &c->step_kernels);
+        }
+        CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st));
+        launch_counted(c, c->g_step);
+        int hstat = 0;
+        CK(cudaMemcpyAsync(&hstat, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        if (hstat) throw std::domain_error("singular tentative-velocity block");
+        graph_stats(c, c->step_kernels);
+        c->t = t0 + dt;
+        return c->hcnt->stage_unconverged ? 1 : 0;
     }
 };
 
@@ -960,6 +1250,7 @@ void hdg_default_params(hdg_params *p) {
     p->inner_stepI_rtol = 1e-1;
     p->inner_trace_rtol = 1e-1;
     p->trace_mg = 1;
+    p->device_loops = 1;
 }
 
 const char *hdg_status_string(hdg_status s) {
@@ -1118,6 +1409,7 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
             c->fZ = c->alloc<double>((size_t)GM_M * N);
             c->fx = c->alloc<double>(N); c->fb = c->alloc<double>(N); c->fw = c->alloc<double>(N);
             c->fr = c->alloc<double>(N); c->fu = c->alloc<double>(N);
+            c->fv = c->alloc<double>(N); c->fz = c->alloc<double>(N);
             c->fgs = c->alloc<GmresState>(1);
             CK(cudaMemset(c->fgs, 0, sizeof(GmresState)));
             CK(cudaMallocHost(&c->hfgs, sizeof(GmresState)));
@@ -1136,6 +1428,13 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         CK(cudaEventCreate(&c->te0));
         CK(cudaEventCreate(&c->te1));
         CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+        c->dguard = c->alloc<int>(hdg_ctx::CAP_LEVELS);
+        c->dnk = c->alloc<int>(hdg_ctx::MAX_LOOPS);
+        c->dcnt = c->alloc<DevCount>(1);
+        CK(cudaMemset(c->dguard, 0, hdg_ctx::CAP_LEVELS * sizeof(int)));
+        CK(cudaMemset(c->dnk, 0, hdg_ctx::MAX_LOOPS * sizeof(int)));
+        CK(cudaMemset(c->dcnt, 0, sizeof(DevCount)));
+        CK(cudaMallocHost(&c->hcnt, sizeof(DevCount)));
         CK(cudaDeviceSynchronize());
     } catch (...) {
         hdg_status s = map_exception();
@@ -1153,16 +1452,21 @@ void hdg_destroy(hdg_ctx *c) {
     for (auto &E : c->cache) {
         if (E.g_setup) cudaGraphExecDestroy(E.g_setup);
         if (E.g_chunk) cudaGraphExecDestroy(E.g_chunk);
+        if (E.g_stage) cudaGraphExecDestroy(E.g_stage);
     }
     if (c->gm_first) cudaGraphExecDestroy(c->gm_first);
     if (c->gm_restart) cudaGraphExecDestroy(c->gm_restart);
     if (c->gms_first) cudaGraphExecDestroy(c->gms_first);
     if (c->gms_restart) cudaGraphExecDestroy(c->gms_restart);
+    if (c->g_step) cudaGraphExecDestroy(c->g_step);
     if (c->cap) cudaStreamDestroy(c->cap);
+    for (cudaStream_t s : c->capst)
+        if (s) cudaStreamDestroy(s);
     for (void *p : c->allocs) cudaFree(p);
     if (c->hsc) cudaFreeHost(c->hsc);
     if (c->hgs) cudaFreeHost(c->hgs);
     if (c->hfgs) cudaFreeHost(c->hfgs);
+    if (c->hcnt) cudaFreeHost(c->hcnt);
     if (c->e0) cudaEventDestroy(c->e0);
     if (c->e1) cudaEventDestroy(c->e1);
     if (c->te0) cudaEventDestroy(c->te0);
@@ -1213,6 +1517,11 @@ hdg_status hdg_get_state(hdg_ctx *c, double *Q, double *p, double *lam, double *
 hdg_status hdg_set_forcing(hdg_ctx *c, const double *F, double (*phi)(double, void *), void *user) {
     if (!c) return HDG_ERR_INVALID_ARG;
     try {
+        if (c->g_step) {                      // the recorded step depends on the forcing terms
+            CK(cudaStreamSynchronize(c->st));
+            CK(cudaGraphExecDestroy(c->g_step));
+            c->g_step = nullptr;
+        }
         if (!F) {
             c->has_forcing = false;
             c->phi = nullptr;

@@ -38,7 +38,8 @@ class hdg_params(ctypes.Structure):
                 ('richardson_max', ctypes.c_int), ('trace_rtol', ctypes.c_double),
                 ('stepI_rtol', ctypes.c_double), ('max_iters', ctypes.c_int),
                 ('stage_krylov', ctypes.c_int), ('inner_stepI_rtol', ctypes.c_double),
-                ('inner_trace_rtol', ctypes.c_double), ('trace_mg', ctypes.c_int)]
+                ('inner_trace_rtol', ctypes.c_double), ('trace_mg', ctypes.c_int),
+                ('device_loops', ctypes.c_int)]
 
 
 class hdg_stats(ctypes.Structure):
@@ -47,7 +48,8 @@ class hdg_stats(ctypes.Structure):
                 ('stepI_iters', ctypes.c_int), ('stage_solves', ctypes.c_int),
                 ('last_update_norm', ctypes.c_double), ('last_trace_relres', ctypes.c_double),
                 ('ms_total', ctypes.c_double), ('ms_trace', ctypes.c_double), ('ms_stepI', ctypes.c_double),
-                ('ms_assembly', ctypes.c_double), ('ms_bdm', ctypes.c_double)]
+                ('ms_assembly', ctypes.c_double), ('ms_bdm', ctypes.c_double),
+                ('graph_kernels', ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -184,6 +184,27 @@ def test_solve_stage_krylov_reaches_monolithic(n, k, c):
     assert_close(host(lam), ld, 1e-9, 'lambda')
 
 
+@pytest.mark.parametrize('mg', [0, 1])
+def test_device_loops_match_host_loops(mg):
+    # the stage solve recorded as one graph with device-side loops runs the same kernels in the same
+    # order as the host-driven loops: identical results, bit for bit
+    n, k = 8, 2
+    Q0 = W.nodal_velocity(n, k, lambda x, y: W.shear_layer(x, y, width=0.1, amp=0.05), noise=1e-3, seed=4)
+    outs, stats = [], []
+    for dl in (0, 1):
+        ctx = H().Context(n, k, periodic_x=True, tableau='ARS343', dt=0.01, n_richardson=0, stage_krylov=1,
+                          richardson_rtol=1e-11, richardson_max=300, trace_mg=mg, device_loops=dl)
+        ctx.hdg_set_state(cuda(Q0))
+        ctx.hdg_reconstruct_pressure()
+        stats.append(ctx.hdg_imex_step(2))
+        outs.append([host(x) for x in ctx.hdg_get_state()[:3]])
+        ctx.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    for key in ('richardson_iters', 'stepI_solves', 'stepI_iters', 'trace_solves', 'trace_iters'):
+        assert stats[0][key] == stats[1][key] > 0, key
+
+
 @pytest.mark.parametrize('n,px', [(16, True), (32, False)])
 def test_multigrid_iterations_mesh_robust(n, px):
     # the V-cycle preconditioner keeps the trace CG iteration count small and nearly independent
