@@ -87,6 +87,23 @@ class ClockSampler:
                 'samples': len(self.samples)}
 
 
+def aggregate_ranks(total_ms, e2e_ms, world, device):
+    """Whole-job timing over the ranks of a replica run: the slowest rank's time (MAX) for the
+    timed steps and for the end-to-end steps. world == 1 returns the inputs."""
+    if world == 1:
+        return total_ms, e2e_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0]), float(t[1])
+
+
+def job_rate(world, stages, steps, total_ms):
+    """Stage solves per second of the whole job: every rank solves `stages` x `steps` stages."""
+    return world * stages * steps / (total_ms / 1e3)
+
+
 def initial_velocity(w, n_override=None, seed_offset=0):
     import hdg_workloads as W
     n = n_override or w['n']
@@ -196,6 +213,8 @@ def run_gpu(args, rank, world, local_rank):
                 torch.cuda.nvtx.range_pop()
                 stats_all.append(st)
             torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
         ms = [a.elapsed_time(b) for a, b in ev]
         # roofline: the trace-apply CG kernel alone, same operators and stream
         gamma = 0.43586652150845899942                   # ARS(3,4,3) diagonal
@@ -224,14 +243,8 @@ def run_gpu(args, rank, world, local_rank):
 
     stages = STAGES[w['tableau']]
     ms_step = float(np.mean(ms))
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms, float(np.mean(e2e_ms)) if e2e_ms else float('nan')], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, e2e_mean = t.tolist()
-    else:
-        e2e_mean = float(np.mean(e2e_ms)) if e2e_ms else float('nan')
-    value = world * stages * args.steps / (total_ms / 1e3)
+    total_ms, e2e_mean = aggregate_ranks(sum(ms), float(np.mean(e2e_ms)) if e2e_ms else float('nan'), world, dev)
+    value = job_rate(world, stages, args.steps, total_ms)
     ntrace = ctx.nL
     trace_solves = sum(s['trace_solves'] for s in stats_all)
     trace_iters = sum(s['trace_iters'] for s in stats_all)

@@ -202,7 +202,12 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *ctx, hdg_stats *stats);
  * once). which = 0: trace operator apply fused with the CG direction update and dot product
  * (the kernel the trace CG runs every iteration) for coefficient c; which = 1: tentative-velocity
  * operator apply (the GMRES matrix-vector product) for the operator last assembled (call
- * hdg_tentative_solve or hdg_imex_step first). Operands are the context's current buffers. */
+ * hdg_tentative_solve or hdg_imex_step first). Operands are the context's current buffers.
+ * which = 2..5 (stage solves to tolerance only; bytes = 0) time one component of the stage
+ * preconditioner, recorded as a CUDA graph with device-side loops, for the stage operator at
+ * coefficient c around the current state and v = (M Q, 0, 0): 2 = Step-I solve to
+ * inner_stepI_rtol, 3 = Step-II (mixed) solve to inner_trace_rtol, 4 = the whole Chorin-split
+ * preconditioner, 5 = the stage operator apply. */
 hdg_status hdg_time_kernel(hdg_ctx *ctx, int which, double c, int reps, double *ms_per_launch,
                            double *bytes_per_launch);
 

@@ -1721,9 +1721,40 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *c, hdg_stats *stats) {
 }
 
 hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *ms, double *bytes) {
-    if (!c || reps < 1 || !ms || !bytes || (which != 0 && which != 1) || (which == 0 && !(cc > 0)))
+    if (!c || reps < 1 || !ms || !bytes || which < 0 || which > 5 || (which != 1 && !(cc > 0)))
         return HDG_ERR_INVALID_ARG;
+    if (which >= 2 && !c->fv) return HDG_ERR_INVALID_ARG;
     try {
+        if (which >= 2) {
+            DISPATCH(c, {
+                // operator of a stage at coefficient cc around the current state; v = (M Q, 0, 0)
+                I::bdm(c, c->Q, c->q[5]);
+                I::assemble_stepI(c, c->q[5], cc);
+                I::condense(c, cc);
+                I::mass(c, c->Q, c->fv, 0);
+                const long long N = c->nQ + c->nPv + c->nL;
+                CK(cudaMemsetAsync(c->fv + c->nQ, 0, 8 * (N - c->nQ), c->st));
+                cudaGraphExec_t ex = capture_graph(c, [&]() {
+                    if (which == 2) I::stepI_solve(c, c->fv, c->q[2], c->P.inner_stepI_rtol);
+                    else if (which == 3)
+                        I::mixed_solve(c, cc, nullptr, c->fv, nullptr, nullptr, c->q[4], c->fz + c->nQ,
+                                       c->fz + c->nQ + c->nPv, nullptr, nullptr, c->P.inner_trace_rtol);
+                    else if (which == 4) I::chorin_precond(c, cc, c->fv, c->fz);
+                    else I::stage_apply(c, cc, c->fv, c->fw);
+                });
+                CK(cudaGraphLaunch(ex, c->st));
+                CK(cudaEventRecord(c->e0, c->st));
+                for (int r = 0; r < reps; ++r) CK(cudaGraphLaunch(ex, c->st));
+                CK(cudaEventRecord(c->e1, c->st));
+                CK(cudaEventSynchronize(c->e1));
+                cudaGraphExecDestroy(ex);
+            });
+            float t = 0;
+            CK(cudaEventElapsedTime(&t, c->e0, c->e1));
+            *ms = t / reps;
+            *bytes = 0;
+            return HDG_OK;
+        }
         DISPATCH(c, {
             const int NT = I::NT, NU = I::NU;
             double b = 0;
