@@ -201,8 +201,9 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *ctx, hdg_stats *stats);
  * algorithmic bytes one launch moves (operator entries it must read + vectors read/written
  * once). which = 0: trace operator apply fused with the CG direction update and dot product
  * (the kernel the trace CG runs every iteration) for coefficient c; which = 1: tentative-velocity
- * operator apply (the GMRES matrix-vector product) for the operator last assembled (call
- * hdg_tentative_solve or hdg_imex_step first). Operands are the context's current buffers.
+ * operator apply (dense diagonal blocks, matrix-free neighbour coupling) for the operator last
+ * assembled (call hdg_tentative_solve or hdg_imex_step first). Operands are the context's
+ * current buffers.
  * which = 2..5 (stage solves to tolerance only; bytes = 0) time one component of the stage
  * preconditioner, recorded as a CUDA graph with device-side loops, for the stage operator at
  * coefficient c around the current state and v = (M Q, 0, 0): 2 = Step-I solve to

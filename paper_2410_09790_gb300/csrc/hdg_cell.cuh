@@ -399,22 +399,22 @@ __host__ __device__ void cell_bdm(const Team &tm, const RefDev &R, const CellGeo
 }
 
 // ------------------------------------------------------------------------------------------
-// Blocks of the tentative-velocity operator M - c F(Q*) (eq. f_impl; Alg. 2 Step I) for one
-// cell: diagonal block (NU x NU) and the three neighbour blocks (test on this cell, trial on
-// the neighbour across local edge e; zero on walls). F's facet terms with test functions on
-// this cell:
-//   central  +<(Q*.n+)(Q+ - Q-).{w}>      -> diag +1/2 h (Q*.n_K) ,  off -1/2 h (Q*.n_K)
-//   upwind   -delta <|Q*.n+|(Q+-Q-).(w+-w-)> -> diag -delta h |Q*.n| , off +delta h |Q*.n|
-//   penalty  -alpha/h <[[Q.n]][[w.n]]>    -> diag -alpha n n^T ,     off +alpha n n^T
+// The tentative-velocity operator M - c F(Q*) (eq. f_impl; Alg. 2 Step I) for one cell. F's
+// facet terms with test functions on this cell (h = edge length, n = this cell's normal):
+//   central  +<(Q*.n+)(Q+ - Q-).{w}>      -> diag +1/2 h (Q*.n_K) ,  neighbour -1/2 h (Q*.n_K)
+//   upwind   -delta <|Q*.n+|(Q+-Q-).(w+-w-)> -> diag -delta h |Q*.n| , neighbour +delta h |Q*.n|
+//   penalty  -alpha/h <[[Q.n]][[w.n]]>    -> diag -alpha n n^T ,     neighbour +alpha n n^T
 // with Q*.n_K = {Q*}.n_K at the facet points (the two cells traverse a shared edge in opposite
-// directions, so point q of one side is point NFQ-1-q of the other).
-// Scratch: NU + 3*NU + 2*NQ + 3*NFQ + MU*MU doubles.
-// Output blocks row-major [row][col] in out[0..3][NU*NU].
+// directions, so point q of one side is point NFQ-1-q of the other). The diagonal block (NU x
+// NU, with the volume advection) is formed densely; the neighbour coupling only needs, per edge
+// point, wq[e*NFQ + q] = -c fw_q h_e (-Q*.n_K/2 + delta |Q*.n_K|) (0 on walls) besides the
+// penalty -c alpha fw_q n n^T, and is applied matrix-free (k_cell_apply_mf and friends).
+// Scratch: 2*NQ + 3*NFQ + MU*MU doubles. D: row-major [row][col].
 template <int K>
-__host__ __device__ void cell_fimpl_blocks(const Team &tm, const RefDev &R, const CellGeo &g,
-                                           const double *QsK, const double *const *Qsn,
-                                           const int *nbr_edge, double c, double alpha,
-                                           double dup, double *sm, double *const *out) {
+__host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const CellGeo &g,
+                                         const double *QsK, const double *const *Qsn,
+                                         const int *nbr_edge, double c, double alpha,
+                                         double dup, double *sm, double *D, double *wq) {
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NQ = Dm::NQ, NFQ = Dm::NFQ;
     double *beta = sm;               // NQ x 2: Jinv Q* at the volume points
@@ -455,6 +455,10 @@ __host__ __device__ void cell_fimpl_blocks(const Team &tm, const RefDev &R, cons
                  (beta[2 * q] * ldg(&R.dphi[(q * MU + b) * 2]) + beta[2 * q + 1] * ldg(&R.dphi[(q * MU + b) * 2 + 1]));
         adv[i] = -g.detJ * s;
     }
+    TFOR(i, 3 * NFQ) {
+        int e = i / NFQ, q = i % NFQ;
+        wq[i] = Qsn[e] ? -c * ldg(&R.fw[q]) * g.h[e] * (-0.5 * qsn[i] + dup * fabs(qsn[i])) : 0.0;
+    }
     tm.sync();
     TFOR(i, NU * NU) {                  // diagonal block
         int r = i / NU, x = i % NU, d = r / MU, a = r % MU, d2 = x / MU, b = x % MU;
@@ -471,27 +475,7 @@ __host__ __device__ void cell_fimpl_blocks(const Team &tm, const RefDev &R, cons
             F += -alpha * nd * nd2 * spen;
             if (inter && d == d2) F += g.h[e] * sadv;
         }
-        out[0][i] = ((r == x) ? g.detJ : 0.0) - c * F;
-    }
-    for (int e = 0; e < 3; ++e) {
-        TFOR(i, NU * NU) {
-            double v = 0;
-            if (Qsn[e]) {
-                int r = i / NU, x = i % NU, d = r / MU, a = r % MU, d2 = x / MU, b = x % MU;
-                int eo = nbr_edge[e];
-                double nd = d == 0 ? g.nx[e] : g.ny[e], nd2 = d2 == 0 ? g.nx[e] : g.ny[e];
-                double spen = 0, sadv = 0;
-                for (int q = 0; q < NFQ; ++q) {
-                    double ff = ldg(&R.fw[q]) * ldg(&R.ephi[(e * NFQ + q) * MU + a]) *
-                                ldg(&R.ephi[(eo * NFQ + (NFQ - 1 - q)) * MU + b]);
-                    spen += ff;
-                    sadv += ff * (-0.5 * qsn[e * NFQ + q] + dup * fabs(qsn[e * NFQ + q]));
-                }
-                double F = alpha * nd * nd2 * spen + ((d == d2) ? g.h[e] * sadv : 0.0);
-                v = -c * F;
-            }
-            out[1 + e][i] = v;
-        }
+        D[i] = ((r == x) ? g.detJ : 0.0) - c * F;
     }
     tm.sync();
 }

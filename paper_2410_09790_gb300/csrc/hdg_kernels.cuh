@@ -7,8 +7,10 @@
 //    (the facet itself and the two other facets of each side cell):
 //        Sell[((b*NT + col) * nrows) + f*NT + row],  tcol[b*nfacets + f] (facet or -1);
 //    a warp reads 32 consecutive rows of one (b, col) slice: fully coalesced.
-//  * tentative-velocity operator M - cF in ELL form with 4 block columns per cell (the cell and
-//    its three neighbours): Bell[((b*NU + col) * nrowsQ) + cell*NU + row].
+//  * tentative-velocity operator M - cF: the diagonal blocks Dblk[col*nrowsQ + cell*NU + row];
+//    the neighbour coupling matrix-free from wq[(cell*3 + e)*NFQ + q] (hdg_cell.cuh,
+//    cell_fimpl_diag) and the cells' velocity values at their edge points,
+//    utr[((cell*3 + e)*NFQ + q)*2 + d].
 //  * block-Jacobi inverses: Dinv[col*nrows + f*NT + row], Binv[col*nrowsQ + cell*NU + row].
 // Reductions are deterministic: each block writes a partial, the last block to finish (atomic
 // ticket, no waiting) sums the partials in a fixed order and updates the solver scalars.
@@ -457,14 +459,16 @@ __global__ void k_bdm(RefDev R, MeshDev M, const double *Q, double *Qs) {
 template <int K>
 constexpr int fimpl_smem_doubles() {
     typedef Dims<K> Dm;
-    return 2 * Dm::NQ + 3 * Dm::NFQ + Dm::MU * Dm::MU + 4 * Dm::NU * Dm::NU + Dm::NU * Dm::NU + 2;
+    return 2 * Dm::NQ + 3 * Dm::NFQ + Dm::MU * Dm::MU + 2 * Dm::NU * Dm::NU + 3 * Dm::NFQ + 2;
 }
 
+// Step-I operator of one stage, one block per cell: diagonal block -> Dblk, neighbour weights
+// -> wq and (Binv non-null) the inverse of the diagonal block -> Binv.
 template <int K>
 __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c, double alpha,
-                                 double dup, double *Bell, double *Binv, int *status) {
+                                 double dup, double *Dblk, double *wq, double *Binv, int *status) {
     typedef Dims<K> Dm;
-    constexpr int NU = Dm::NU;
+    constexpr int NU = Dm::NU, NFQ = Dm::NFQ;
     extern __shared__ double sm[];
     const int cell = blockIdx.x;
     if (cell >= M.ncells) return;
@@ -477,20 +481,21 @@ __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c
         Qn[e] = o >= 0 ? Qs + (size_t)o * NU : nullptr;
         ne[e] = M.cell_nbr_edge[3 * cell + e];
     }
-    double *blk = sm + 2 * Dm::NQ + 3 * Dm::NFQ + Dm::MU * Dm::MU;
-    double *outp[4] = {blk, blk + NU * NU, blk + 2 * NU * NU, blk + 3 * NU * NU};
-    cell_fimpl_blocks<K>(tm, R, g, Qs + (size_t)cell * NU, Qn, ne, c, alpha, dup, sm, outp);
+    double *D = sm + 2 * Dm::NQ + 3 * NFQ + Dm::MU * Dm::MU;
+    double *wqs = D + NU * NU;
+    cell_fimpl_diag<K>(tm, R, g, Qs + (size_t)cell * NU, Qn, ne, c, alpha, dup, sm, D, wqs);
     const long long nrows = (long long)M.ncells * NU;
-    for (int b = 0; b < 4; ++b)
-        TFOR(i, NU * NU) {
-            int col = i / NU, row = i % NU;
-            Bell[((size_t)(b * NU + col)) * nrows + (size_t)cell * NU + row] = outp[b][row * NU + col];
-        }
+    TFOR(i, NU * NU) {
+        int col = i / NU, row = i % NU;
+        Dblk[(size_t)col * nrows + (size_t)cell * NU + row] = D[row * NU + col];
+    }
+    TFOR(i, 3 * NFQ) wq[(size_t)cell * 3 * NFQ + i] = wqs[i];
     tm.sync();
-    double *inv = blk + 4 * NU * NU;
+    if (!Binv) return;
+    double *inv = wqs + 3 * NFQ;
     int *piv = (int *)(inv + NU * NU);
-    // the diagonal block is consumed by the inversion (outp[0] in place)
-    bool ok = team_invert<NU>(tm, outp[0], inv, piv);
+    // the diagonal block is consumed by the inversion (in place)
+    bool ok = team_invert<NU>(tm, D, inv, piv);
     TFOR(i, NU * NU) {
         int col = i / NU, row = i % NU;
         Binv[(size_t)col * nrows + (size_t)cell * NU + row] = inv[row * NU + col];
@@ -498,24 +503,77 @@ __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c
     if (!ok && tm.tid == 0) atomicExch(status, 1);
 }
 
-// y = B x (ELL, 4 block columns)
+// ------------------------------------------------------------ matrix-free neighbour coupling
+// t[(e*NFQ + q)*2 + d] = pen_q n_d (n . u) + wq(e, q) u_d at the points of this cell's edges,
+// u = the neighbour's velocity at the matching point (its point NFQ-1-q on its edge), taken from
+// the table utr of the cells' own edge values, or evaluated from the coefficients x when utr is
+// null; pen_q = -c alpha fw_q (calpha = c alpha). Zero on walls.
 template <int K>
-__global__ void k_cell_apply(MeshDev M, const double *__restrict__ Bell, const double *__restrict__ x,
-                             double *__restrict__ y) {
-    constexpr int NU = Dims<K>::NU;
-    const long long nrows = (long long)M.ncells * NU;
-    GRID_STRIDE(g, nrows) {
-        int cell = (int)(g / NU);
-        double s = 0;
-        for (int b = 0; b < 4; ++b) {
-            int cc = b == 0 ? cell : __ldg(&M.cell_nbr[3 * cell + b - 1]);
-            if (cc < 0) continue;
-            const double *xc = x + (size_t)cc * NU;
-            const double *Bc = Bell + (size_t)(b * NU) * nrows + g;
-#pragma unroll 6
-            for (int j = 0; j < NU; ++j) s += __ldg(&Bc[(size_t)j * nrows]) * xc[j];
+__device__ __forceinline__ void team_nbr_flux(const Team &tm, const RefDev &R, const MeshDev &M, int cell,
+                                              const CellGeo &g, const double *__restrict__ wq, double calpha,
+                                              const double *utr, const double *x, double *t) {
+    typedef Dims<K> Dm;
+    constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
+    TFOR(i, 3 * NFQ) {
+        const int e = i / NFQ, q = i % NFQ;
+        const int o = __ldg(&M.cell_nbr[3 * cell + e]);
+        double tx = 0.0, ty = 0.0;
+        if (o >= 0) {
+            const int eo = __ldg(&M.cell_nbr_edge[3 * cell + e]), qo = NFQ - 1 - q;
+            double ux = 0.0, uy = 0.0;
+            if (utr) {
+                const double *u = utr + ((size_t)(o * 3 + eo) * NFQ + qo) * 2;
+                ux = u[0]; uy = u[1];
+            } else {
+                const double *ph = &R.ephi[(eo * NFQ + qo) * MU];
+                const double *xo = x + (size_t)o * NU;
+#pragma unroll 5
+                for (int b = 0; b < MU; ++b) {
+                    const double f = __ldg(ph + b);
+                    ux += f * xo[b]; uy += f * xo[MU + b];
+                }
+            }
+            const double nx = g.nx[e], ny = g.ny[e];
+            const double un = nx * ux + ny * uy, pen = -calpha * __ldg(&R.fw[q]);
+            const double w = __ldg(&wq[(size_t)cell * 3 * NFQ + i]);
+            tx = pen * nx * un + w * ux;
+            ty = pen * ny * un + w * uy;
         }
-        y[g] = s;
+        t[2 * i] = tx;
+        t[2 * i + 1] = ty;
+    }
+}
+
+// row (d, a) of the neighbour coupling: sum over the edge points of phi_a(e, q) t[(e, q), d]
+template <int K>
+__device__ __forceinline__ double nbr_row(const RefDev &R, const double *t, int d, int a) {
+    typedef Dims<K> Dm;
+    double s = 0.0;
+#pragma unroll 7
+    for (int i = 0; i < 3 * Dm::NFQ; ++i) s += __ldg(&R.ephi[i * Dm::MU + a]) * t[2 * i + d];
+    return s;
+}
+
+// y = (M - cF) x: diagonal block dense, neighbours matrix-free (team per cell)
+template <int K>
+__global__ void k_cell_apply_mf(RefDev R, MeshDev M, const double *__restrict__ Dblk, const double *__restrict__ wq,
+                                double calpha, const double *__restrict__ x, double *__restrict__ y) {
+    typedef Dims<K> Dm;
+    constexpr int MU = Dm::MU, NU = Dm::NU;
+    constexpr int SCR = 6 * Dm::NFQ;
+    CELL_TEAM(SCR)
+    double *t = mine;
+    const CellGeo g = M.geo[cell];
+    team_nbr_flux<K>(tm, R, M, cell, g, wq, calpha, nullptr, x, t);
+    tm.sync();
+    const long long nrows = (long long)M.ncells * NU;
+    const double *xK = x + (size_t)cell * NU;
+    TFOR(r, NU) {
+        const size_t gi = (size_t)cell * NU + r;
+        double s = nbr_row<K>(R, t, r / MU, r % MU);
+#pragma unroll 6
+        for (int j = 0; j < NU; ++j) s += __ldg(&Dblk[(size_t)j * nrows + gi]) * xK[j];
+        y[gi] = s;
     }
 }
 
@@ -629,27 +687,49 @@ __device__ bool multidot_rows(const RedBuf rb, const double *V, long long n, int
     return threadIdx.x == 0;
 }
 
-// start of a cycle: w = b - B x (x = 0 on the first cycle: w = b); beta = ||w||
-template <int K>
-__global__ void k_gm_start(MeshDev M, const double *__restrict__ Bell, const double *__restrict__ b,
-                           const double *__restrict__ x, double *w, int first, RedBuf rb, GmresState *gs,
-                           double rtol, int maxit) {
-    constexpr int NU = Dims<K>::NU;
-    const long long nrows = (long long)M.ncells * NU;
+// dots of w with V_0..V_{nvec-1} over the rows of the cell groups a team-per-cell kernel assigns
+// to this block (groups blockIdx.x, blockIdx.x + gridDim.x, ... of rows_per_group rows); w was
+// written by this block before the call (visible after __syncthreads)
+__device__ bool multidot_groups(const RedBuf rb, const double *V, const double *w, long long nrows,
+                                long long rows_per_group, int nvec, double *out) {
+    __shared__ double sh[1][32];
+    __shared__ int last;
+    __syncthreads();
+    for (int i = 0; i < nvec; ++i) {
+        double v[1] = {0.0};
+        const double *Vi = V + (size_t)i * nrows;
+        for (long long g0 = blockIdx.x * rows_per_group; g0 < nrows; g0 += gridDim.x * rows_per_group) {
+            const long long g1 = g0 + rows_per_group < nrows ? g0 + rows_per_group : nrows;
+            for (long long r = g0 + threadIdx.x; r < g1; r += blockDim.x) v[0] += Vi[r] * w[r];
+        }
+        block_sum<1>(v, sh);
+        if (threadIdx.x == 0) rb.partials[blockIdx.x * (GM_M + 2) + i] = v[0];
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned t = atomicAdd(rb.counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    for (int i = 0; i < nvec; ++i) {
+        double acc[1] = {0.0};
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc[0] += __ldcg(&rb.partials[b * (GM_M + 2) + i]);
+        block_sum<1>(acc, sh);
+        if (threadIdx.x == 0) out[i] = acc[0];
+    }
+    if (threadIdx.x == 0) *rb.counter = 0u;
+    return threadIdx.x == 0;
+}
+
+// start of a cycle: w = b - Bx (Bx = B x precomputed; null on the first cycle, x = 0: w = b);
+// beta = ||w||
+__global__ void k_gm_start(long long nrows, const double *__restrict__ b, const double *__restrict__ Bx,
+                           double *w, int first, RedBuf rb, GmresState *gs, double rtol, int maxit) {
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(g, nrows) {
-        double s = 0;
-        if (!first) {
-            int cell = (int)(g / NU);
-            for (int bb = 0; bb < 4; ++bb) {
-                int cc = bb == 0 ? cell : __ldg(&M.cell_nbr[3 * cell + bb - 1]);
-                if (cc < 0) continue;
-                const double *xc = x + (size_t)cc * NU;
-                const double *Bc = Bell + (size_t)(bb * NU) * nrows + g;
-                for (int j = 0; j < NU; ++j) s += __ldg(&Bc[(size_t)j * nrows]) * xc[j];
-            }
-        }
-        double r = b[g] - s;
+        double r = b[g] - (Bx ? Bx[g] : 0.0);
         w[g] = r;
         v[0] += r * r;
     }
@@ -673,50 +753,78 @@ __global__ void k_gm_start(MeshDev M, const double *__restrict__ Bell, const dou
     }
 }
 
-// v_j = w / h (h = beta for j = 0, H[j, j-1] otherwise); z = Binv v_j
+// v_j = w / h (h = beta for j = 0, H[j, j-1] otherwise) -> V_j; z = Binv v_j (cell-local) and z's
+// values at the cell's edge points -> utr (team per cell)
 template <int K>
-__global__ void k_gm_precond(const double *__restrict__ Binv, const double *__restrict__ w, double *V,
-                             double *z, long long ncells, const GmresState *gs) {
+__global__ void k_gm_precond_mf(RefDev R, MeshDev M, const double *__restrict__ Binv, const double *__restrict__ w,
+                                double *V, double *utr, const GmresState *gs) {
     if (gs->cycle_end) return;
-    constexpr int NU = Dims<K>::NU;
+    typedef Dims<K> Dm;
+    constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
+    constexpr int SCR = 2 * NU;
+    CELL_TEAM(SCR)
+    double *vK = mine, *zK = mine + NU;
     const int j = gs->j;
-    const double h = j == 0 ? gs->beta : gs->H[(j - 1) * (GM_M + 1) + j];
-    const double inv = 1.0 / h;
-    const long long nrows = ncells * NU;
+    const double inv = 1.0 / (j == 0 ? gs->beta : gs->H[(j - 1) * (GM_M + 1) + j]);
+    const long long nrows = (long long)M.ncells * NU;
     double *vj = V + (size_t)j * nrows;
-    GRID_STRIDE(g, nrows) {
-        long long base = (g / NU) * NU;
-        double acc = 0;
+    TFOR(r, NU) {
+        const size_t gi = (size_t)cell * NU + r;
+        const double v = w[gi] * inv;
+        vj[gi] = v;
+        vK[r] = v;
+    }
+    tm.sync();
+    TFOR(r, NU) {
+        const size_t gi = (size_t)cell * NU + r;
+        double acc = 0.0;
 #pragma unroll 6
-        for (int q = 0; q < NU; ++q) acc += __ldg(&Binv[(size_t)q * nrows + g]) * (w[base + q] * inv);
-        vj[g] = w[g] * inv;
-        z[g] = acc;
+        for (int q = 0; q < NU; ++q) acc += __ldg(&Binv[(size_t)q * nrows + gi]) * vK[q];
+        zK[r] = acc;
+    }
+    tm.sync();
+    TFOR(i, 3 * NFQ * 2) {
+        const int d = i & 1, p = i >> 1;            // p = e*NFQ + q
+        const double *ph = &R.ephi[p * MU];
+        double s = 0.0;
+#pragma unroll 5
+        for (int b = 0; b < MU; ++b) s += __ldg(ph + b) * zK[d * MU + b];
+        utr[(size_t)cell * 3 * NFQ * 2 + i] = s;
     }
 }
 
-// w = B z; hcol[i] = (V_i, w), i <= j
+// w = B z = v_j + (neighbour coupling) z for z = Binv v_j (the diagonal block returns v_j);
+// hcol[i] = (V_i, w), i <= j. Team per cell over groups of cells; grid <= MAX_RED_BLOCKS.
 template <int K>
-__global__ void k_gm_apply_dot(MeshDev M, const double *__restrict__ Bell, const double *__restrict__ z,
-                               double *__restrict__ w, const double *__restrict__ V, RedBuf rb, GmresState *gs) {
+__global__ void k_gm_apply_mf(RefDev R, MeshDev M, const double *__restrict__ wq, double calpha,
+                              const double *__restrict__ utr, double *w, const double *__restrict__ V, RedBuf rb,
+                              GmresState *gs) {
     if (gs->cycle_end) return;
-    constexpr int NU = Dims<K>::NU;
+    typedef Dims<K> Dm;
+    constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
+    extern __shared__ double sm[];
+    const int team = threadIdx.x / TEAM_LANES, tpb = blockDim.x / TEAM_LANES;
+    Team tm{(int)(threadIdx.x % TEAM_LANES), TEAM_LANES};
+    double *t = sm + team * (6 * NFQ);
     const long long nrows = (long long)M.ncells * NU;
-    GRID_STRIDE(g, nrows) {
-        int cell = (int)(g / NU);
-        double s = 0;
-        for (int bb = 0; bb < 4; ++bb) {
-            int cc = bb == 0 ? cell : __ldg(&M.cell_nbr[3 * cell + bb - 1]);
-            if (cc < 0) continue;
-            const double *zc = z + (size_t)cc * NU;
-            const double *Bc = Bell + (size_t)(bb * NU) * nrows + g;
-#pragma unroll 6
-            for (int q = 0; q < NU; ++q) s += __ldg(&Bc[(size_t)q * nrows]) * zc[q];
+    const int j = gs->j;
+    const double *vj = V + (size_t)j * nrows;
+    // cells come in pairs (2 n^2 triangles) and groups start at multiples of tpb: both teams of
+    // a warp are active or idle together
+    for (int base = blockIdx.x * tpb; base < M.ncells; base += gridDim.x * tpb) {
+        const int cell = base + team;
+        if (cell < M.ncells) {
+            const CellGeo g = M.geo[cell];
+            team_nbr_flux<K>(tm, R, M, cell, g, wq, calpha, utr, nullptr, t);
+            tm.sync();
+            TFOR(r, NU) {
+                const size_t gi = (size_t)cell * NU + r;
+                w[gi] = vj[gi] + nbr_row<K>(R, t, r / MU, r % MU);
+            }
+            tm.sync();
         }
-        w[g] = s;
     }
-    // w written by this thread only is read back by the same thread below (same g mapping)
-    const int nvec = gs->j + 1;
-    multidot_rows(rb, V, nrows, nvec, [&](long long g) { return w[g]; }, gs->hcol);
+    multidot_groups(rb, V, w, nrows, (long long)tpb * NU, j + 1, gs->hcol);
 }
 
 // w -= V hcol; h2 = (V_i, w)  (second Gram-Schmidt pass)
@@ -763,7 +871,7 @@ __global__ void k_gm_orth2(double *w, const double *__restrict__ V, long long nr
         gs->resid = fabs(gs->g[j + 1]);
         gs->total += 1;
         // keep H[j+1, j] (the norm) for the next v; stored separately in hcol[GM_M+1]
-        gs->H[j * (GM_M + 1) + j + 1] = hn;            // restored after the rotation (used by k_gm_precond)
+        gs->H[j * (GM_M + 1) + j + 1] = hn;            // restored after the rotation (used by k_gm_precond_mf)
         gs->hcol[GM_M + 1] = hn;
         gs->j = j + 1;
         if (!isfinite(gs->resid)) { gs->breakdown = 2; gs->cycle_end = 1; }

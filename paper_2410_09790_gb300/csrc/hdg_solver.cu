@@ -147,7 +147,8 @@ struct hdg_ctx {
     double (*phi)(double, void *) = nullptr;
     void *phi_user = nullptr;
     // Step I
-    double *Bell = nullptr, *Binv = nullptr;
+    double *Dblk = nullptr, *Binv = nullptr, *wq = nullptr, *utr = nullptr;
+    double calpha = 0.0;                                     // c alpha of the assembled operator
     int *dstatus = nullptr;
     // Step II
     double *vK = nullptr, *wK = nullptr, *tb = nullptr, *tx = nullptr, *tr = nullptr, *tz = nullptr,
@@ -712,19 +713,44 @@ struct Impl {
     }
 
     // ---------------------------------------------------------------- Step I operator
-    static void assemble_stepI(hdg_ctx *c, const double *Qs, double cc) {
+    // Step-I operator M - cc F(Qs): diagonal blocks, neighbour weights and (invert) the
+    // block-Jacobi inverses
+    static void assemble_stepI(hdg_ctx *c, const double *Qs, double cc, bool invert = true) {
         CompTimer tm_(c, &c->S.ms_assembly);
         size_t smem = sizeof(double) * fimpl_smem_doubles<K>();
         CK(cudaFuncSetAttribute(k_fimpl_assemble<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (!c->capturing) CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st));   // (graphs: once per launch)
         k_fimpl_assemble<K><<<(unsigned)c->ncells, 128, smem, c->st>>>(c->R, c->M, Qs, cc, c->P.alpha, c->P.delta_up,
-                                                                      c->Bell, c->Binv, c->dstatus);
+                                                                      c->Dblk, c->wq, invert ? c->Binv : nullptr,
+                                                                      c->dstatus);
         CKL();
+        c->calpha = cc * c->P.alpha;
     }
 
     static void cell_apply(hdg_ctx *c, const double *x, double *y) {
-        k_cell_apply<K><<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->M, c->Bell, x, y);
+        k_cell_apply_mf<K><<<cell_blocks(c), 128, sizeof(double) * TEAMS_PER_BLOCK * 6 * Dm::NFQ, c->st>>>(
+            c->R, c->M, c->Dblk, c->wq, c->calpha, x, y);
         CKL();
+    }
+
+    // one Arnoldi step of the Step-I GMRES: V_j, z = Binv V_j (edge values only), w = B z, dots
+    static void gmres_arnoldi(hdg_ctx *c) {
+        const long long n = c->nQ;
+        const int g = grid_for(n);
+        const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
+        const size_t sm_t = sizeof(double) * TEAMS_PER_BLOCK * 6 * Dm::NFQ;
+        k_gm_precond_mf<K><<<cb, 128, sizeof(double) * TEAMS_PER_BLOCK * 2 * NU, c->st>>>(c->R, c->M, c->Binv, c->gw,
+                                                                                          c->gV, c->utr, c->gs);
+        k_gm_apply_mf<K><<<ab, 128, sm_t, c->st>>>(c->R, c->M, c->wq, c->calpha, c->utr, c->gw, c->gV, c->rb(), c->gs);
+        k_gm_orth1<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
+        k_gm_orth2<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
+    }
+
+    // cycle start: w = b - B x (x = 0 on the first cycle)
+    static void gmres_start(hdg_ctx *c, int first) {
+        if (!first) cell_apply(c, c->gx, c->gz);
+        k_gm_start<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->nQ, c->gb, first ? nullptr : c->gz, c->gw, first,
+                                                              c->rb(), c->gs, -1.0, 0);
     }
 
     // Restarted GMRES(GM_M) on the assembled Step-I operator with right block-Jacobi
@@ -733,14 +759,9 @@ struct Impl {
     static void gmres_cycle(hdg_ctx *c, int first, int m) {
         const long long n = c->nQ;
         const int g = grid_for(n);
-        k_gm_start<K><<<g, VEC_THREADS, 0, c->st>>>(c->M, c->Bell, c->gb, c->gx, c->gw, first, c->rb(), c->gs, -1.0, 0);
+        gmres_start(c, first);
         k_gm_set_cycle<<<1, 1, 0, c->st>>>(c->gs, m);
-        for (int j = 0; j < m; ++j) {
-            k_gm_precond<K><<<g, VEC_THREADS, 0, c->st>>>(c->Binv, c->gw, c->gV, c->gz, c->ncells, c->gs);
-            k_gm_apply_dot<K><<<g, VEC_THREADS, 0, c->st>>>(c->M, c->Bell, c->gz, c->gw, c->gV, c->rb(), c->gs);
-            k_gm_orth1<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
-            k_gm_orth2<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
-        }
+        for (int j = 0; j < m; ++j) gmres_arnoldi(c);
         k_gm_solve<<<1, 32, 0, c->st>>>(c->gs, nullptr);
         k_gm_combine<<<g, VEC_THREADS, 0, c->st>>>(c->gV, c->gu, n, c->gs);
         k_gm_update_x<K><<<g, VEC_THREADS, 0, c->st>>>(c->Binv, c->gu, c->gx, c->ncells, first);
@@ -751,15 +772,12 @@ struct Impl {
     static void gmres_cycle_dev(hdg_ctx *c, int first, int m) {
         const long long n = c->nQ;
         const int g = grid_for(n);
-        k_gm_start<K><<<g, VEC_THREADS, 0, c->st>>>(c->M, c->Bell, c->gb, c->gx, c->gw, first, c->rb(), c->gs, -1.0, 0);
+        gmres_start(c, first);
         k_gm_set_cycle<<<1, 1, 0, c->st>>>(c->gs, m);
         capture_while(
             c, [&](LoopCtl L) { k_loop_init<<<1, 1, 0, c->st>>>(L, &c->gs->cycle_end); },
             [&](LoopCtl L) {
-                k_gm_precond<K><<<g, VEC_THREADS, 0, c->st>>>(c->Binv, c->gw, c->gV, c->gz, c->ncells, c->gs);
-                k_gm_apply_dot<K><<<g, VEC_THREADS, 0, c->st>>>(c->M, c->Bell, c->gz, c->gw, c->gV, c->rb(), c->gs);
-                k_gm_orth1<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
-                k_gm_orth2<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
+                gmres_arnoldi(c);
                 k_loop_ctl<<<1, 1, 0, c->st>>>(L, m + 1, &c->gs->cycle_end);
             });
         k_gm_solve<<<1, 32, 0, c->st>>>(c->gs, nullptr);
@@ -1058,7 +1076,7 @@ struct Impl {
 
     // f^impl(w, Q, P(Q)) + phi(t) (w.F) as a dual vector, using the Step-I buffers (c = 1)
     static void fimpl_dual(hdg_ctx *c, const double *Q, const double *Qs, double tt, double *out) {
-        assemble_stepI(c, Qs, 1.0);
+        assemble_stepI(c, Qs, 1.0, false);
         cell_apply(c, Q, c->q[6]);
         LinComb L{};
         L.nterms = 2;
@@ -1389,7 +1407,10 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
             c->ps.push_back(c->alloc<double>(nP)); c->ls.push_back(c->alloc<double>(nL));
         }
         c->Fload = c->alloc<double>(nQ);
-        c->Bell = c->alloc<double>((size_t)4 * c->NU * nQ);
+        const int nfq = (3 * c->K + 5) / 2;                      // facet points (Dims<K>::NFQ)
+        c->Dblk = c->alloc<double>((size_t)c->NU * nQ);
+        c->wq = c->alloc<double>((size_t)c->ncells * 3 * nfq);
+        c->utr = c->alloc<double>((size_t)c->ncells * 3 * nfq * 2);
         c->Binv = c->alloc<double>((size_t)c->NU * nQ);
         c->dstatus = c->alloc<int>(1);
         c->vK = c->alloc<double>((size_t)c->ncells * c->NL);
@@ -1779,15 +1800,10 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 for (int r = 0; r < reps; ++r) launch();
                 CK(cudaEventRecord(c->e1, c->st));
             } else {
-                long long nblk = 0;
-                for (long long cl = 0; cl < c->ncells; ++cl)
-                    for (int e = 0; e < 3; ++e) nblk += c->H.cell_nbr[3 * cl + e] >= 0;
-                nblk += c->ncells;
-                b = 8.0 * nblk * NU * NU + 4.0 * 3 * c->ncells + 8.0 * 2 * c->nQ;     // + x read; y written
-                const int g = grid_for(c->nQ);
-                auto launch = [&]() {
-                    k_cell_apply<I::K_><<<g, VEC_THREADS, 0, c->st>>>(c->M, c->Bell, c->gz, c->gw);
-                };
+                // diagonal blocks + neighbour weights + neighbour maps (2 ints x 3) + x read, y written
+                const int nfq = (3 * c->K + 5) / 2;
+                b = 8.0 * c->ncells * ((double)NU * NU + 3 * nfq) + 4.0 * 6 * c->ncells + 8.0 * 2 * c->nQ;
+                auto launch = [&]() { I::cell_apply(c, c->gz, c->gw); };
                 launch();
                 CKL();
                 CK(cudaEventRecord(c->e0, c->st));
