@@ -409,7 +409,16 @@ __host__ __device__ void cell_bdm(const Team &tm, const RefDev &R, const CellGeo
 // NU, with the volume advection) is formed densely; the neighbour coupling only needs, per edge
 // point, wq[e*NFQ + q] = -c fw_q h_e (-Q*.n_K/2 + delta |Q*.n_K|) (0 on walls) besides the
 // penalty -c alpha fw_q n n^T, and is applied matrix-free (k_cell_apply_mf and friends).
-// Scratch: 2*NQ + 3*NFQ + MU*MU doubles. D: row-major [row][col].
+// The sums are factored: the volume term through G[q][b] = w_q (beta(q) . grad phi_b(q)), the
+// facet terms through per-edge MU x MU matrices of the penalty mass and the weighted advective
+// mass, so that each D entry combines a handful of precomputed numbers.
+// Scratch: fimpl_diag_scratch<K>() doubles. D: row-major [row][col].
+template <int K>
+constexpr int fimpl_diag_scratch() {
+    typedef Dims<K> Dm;
+    return 2 * Dm::NQ + 3 * Dm::NFQ + Dm::MU * Dm::MU + Dm::NQ * Dm::MU + 6 * Dm::MU * Dm::MU;
+}
+
 template <int K>
 __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const CellGeo &g,
                                          const double *QsK, const double *const *Qsn,
@@ -420,6 +429,9 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
     double *beta = sm;               // NQ x 2: Jinv Q* at the volume points
     double *qsn = beta + 2 * NQ;     // 3 x NFQ: {Q*}.n_e
     double *adv = qsn + 3 * NFQ;     // MU x MU
+    double *G = adv + MU * MU;       // NQ x MU: w_q (beta(q) . grad phi_b(q))
+    double *Sp = G + NQ * MU;        // 3 x MU x MU: sum_q fw phi_a phi_b on edge e
+    double *Wa = Sp + 3 * MU * MU;   // 3 x MU x MU: the same weighted by Q*.n/2 - delta |Q*.n|
     TFOR(q, NQ) {
         double v0 = 0, v1 = 0;
         for (int a = 0; a < MU; ++a) {
@@ -447,17 +459,32 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
         qsn[i] = s;
     }
     tm.sync();
-    TFOR(i, MU * MU) {                  // -(w.(Q*.grad)Q)_K for one component
-        int a = i / MU, b = i % MU;
-        double s = 0;
-        for (int q = 0; q < NQ; ++q)
-            s += ldg(&R.qw[q]) * ldg(&R.phi[q * MU + a]) *
-                 (beta[2 * q] * ldg(&R.dphi[(q * MU + b) * 2]) + beta[2 * q + 1] * ldg(&R.dphi[(q * MU + b) * 2 + 1]));
-        adv[i] = -g.detJ * s;
+    TFOR(i, NQ * MU) {
+        int q = i / MU, b = i % MU;
+        G[i] = ldg(&R.qw[q]) * (beta[2 * q] * ldg(&R.dphi[(q * MU + b) * 2]) + beta[2 * q + 1] * ldg(&R.dphi[(q * MU + b) * 2 + 1]));
+    }
+    TFOR(i, 3 * MU * MU) {
+        int e = i / (MU * MU), a = (i / MU) % MU, b = i % MU;
+        double sp = 0, sa = 0;
+        const bool inter = Qsn[e] != nullptr;
+        for (int q = 0; q < NFQ; ++q) {
+            double ff = ldg(&R.fw[q]) * ldg(&R.ephi[(e * NFQ + q) * MU + a]) * ldg(&R.ephi[(e * NFQ + q) * MU + b]);
+            sp += ff;
+            if (inter) sa += ff * (0.5 * qsn[e * NFQ + q] - dup * fabs(qsn[e * NFQ + q]));
+        }
+        Sp[i] = sp;
+        Wa[i] = sa;
     }
     TFOR(i, 3 * NFQ) {
         int e = i / NFQ, q = i % NFQ;
         wq[i] = Qsn[e] ? -c * ldg(&R.fw[q]) * g.h[e] * (-0.5 * qsn[i] + dup * fabs(qsn[i])) : 0.0;
+    }
+    tm.sync();
+    TFOR(i, MU * MU) {                  // -(w.(Q*.grad)Q)_K for one component
+        int a = i / MU, b = i % MU;
+        double s = 0;
+        for (int q = 0; q < NQ; ++q) s += ldg(&R.phi[q * MU + a]) * G[q * MU + b];
+        adv[i] = -g.detJ * s;
     }
     tm.sync();
     TFOR(i, NU * NU) {                  // diagonal block
@@ -465,15 +492,8 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
         double F = (d == d2) ? adv[a * MU + b] : 0.0;
         for (int e = 0; e < 3; ++e) {
             double nd = d == 0 ? g.nx[e] : g.ny[e], nd2 = d2 == 0 ? g.nx[e] : g.ny[e];
-            double spen = 0, sadv = 0;
-            bool inter = Qsn[e] != nullptr;
-            for (int q = 0; q < NFQ; ++q) {
-                double ff = ldg(&R.fw[q]) * ldg(&R.ephi[(e * NFQ + q) * MU + a]) * ldg(&R.ephi[(e * NFQ + q) * MU + b]);
-                spen += ff;
-                if (inter) sadv += ff * (0.5 * qsn[e * NFQ + q] - dup * fabs(qsn[e * NFQ + q]));
-            }
-            F += -alpha * nd * nd2 * spen;
-            if (inter && d == d2) F += g.h[e] * sadv;
+            F += -alpha * nd * nd2 * Sp[(e * MU + a) * MU + b];
+            if (d == d2 && Qsn[e]) F += g.h[e] * Wa[(e * MU + a) * MU + b];
         }
         D[i] = ((r == x) ? g.detJ : 0.0) - c * F;
     }
@@ -481,43 +501,44 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
 }
 
 // In-place inverse of an n x n row-major matrix A (Gauss-Jordan, partial pivoting) with the
-// team; Inv receives the inverse. Scratch: 1 int (pivot). Returns false if singular.
-template <int N>
-__host__ __device__ bool team_invert(const Team &tm, double *A, double *Inv, int *piv_sm) {
-    TFOR(i, N * N) Inv[i] = (i / N == i % N) ? 1.0 : 0.0;
+// team, in the precision T; Inv receives the inverse. Scratch: 1 int (pivot). Returns false if
+// singular.
+template <int N, class T = double>
+__host__ __device__ bool team_invert(const Team &tm, T *A, T *Inv, int *piv_sm) {
+    TFOR(i, N * N) Inv[i] = (i / N == i % N) ? T(1) : T(0);
     tm.sync();
     bool ok = true;
     for (int col = 0; col < N; ++col) {
         if (tm.tid == 0) {
             int p = col;
-            double best = fabs(A[col * N + col]);
+            T best = fabs(A[col * N + col]);
             for (int r = col + 1; r < N; ++r)
                 if (fabs(A[r * N + col]) > best) { best = fabs(A[r * N + col]); p = r; }
-            *piv_sm = (best > 0.0) ? p : -1;
+            *piv_sm = (best > T(0)) ? p : -1;
         }
         tm.sync();
         int p = *piv_sm;
         if (p < 0) { ok = false; break; }
         if (p != col) {
             TFOR(j, N) {
-                double t = A[col * N + j]; A[col * N + j] = A[p * N + j]; A[p * N + j] = t;
+                T t = A[col * N + j]; A[col * N + j] = A[p * N + j]; A[p * N + j] = t;
                 t = Inv[col * N + j]; Inv[col * N + j] = Inv[p * N + j]; Inv[p * N + j] = t;
             }
             tm.sync();
         }
-        double inv_d = 1.0 / A[col * N + col];
+        T inv_d = T(1) / A[col * N + col];
         tm.sync();
         TFOR(j, N) { A[col * N + j] *= inv_d; Inv[col * N + j] *= inv_d; }
         tm.sync();
         TFOR(i, (N - 1) * N) {
             int r = i / N, j = i % N;
             if (r >= col) ++r;
-            double f = A[r * N + col];
+            T f = A[r * N + col];
             if (j != col) A[r * N + j] -= f * A[col * N + j];
             Inv[r * N + j] -= f * Inv[col * N + j];
         }
         tm.sync();
-        TFOR(r, N) if (r != col) A[r * N + col] = 0.0;
+        TFOR(r, N) if (r != col) A[r * N + col] = T(0);
         tm.sync();
     }
     return ok;

@@ -10,7 +10,8 @@
 //  * tentative-velocity operator M - cF: the diagonal blocks Dblk[col*nrowsQ + cell*NU + row];
 //    the neighbour coupling matrix-free from wq[(cell*3 + e)*NFQ + q] (hdg_cell.cuh,
 //    cell_fimpl_diag) and the cells' velocity values at their edge points,
-//    utr[((cell*3 + e)*NFQ + q)*2 + d].
+//    utr[((cell*3 + e)*NFQ + q)*2 + d]. The loose (inner) Step-I solves use FP32 copies
+//    (Binv32, wq32, utr32) and FP32 Krylov vectors.
 //  * block-Jacobi inverses: Dinv[col*nrows + f*NT + row], Binv[col*nrowsQ + cell*NU + row].
 // Reductions are deterministic: each block writes a partial, the last block to finish (atomic
 // ticket, no waiting) sums the partials in a fixed order and updates the solver scalars.
@@ -459,20 +460,27 @@ __global__ void k_bdm(RefDev R, MeshDev M, const double *Q, double *Qs) {
 template <int K>
 constexpr int fimpl_smem_doubles() {
     typedef Dims<K> Dm;
-    return 2 * Dm::NQ + 3 * Dm::NFQ + Dm::MU * Dm::MU + 2 * Dm::NU * Dm::NU + 3 * Dm::NFQ + 2;
+    return fimpl_diag_scratch<K>() + 3 * Dm::NU * Dm::NU + 3 * Dm::NFQ + 2;
 }
 
 // Step-I operator of one stage, one block per cell: diagonal block -> Dblk, neighbour weights
-// -> wq and (Binv non-null) the inverse of the diagonal block -> Binv.
+// -> wq (and wq32 in FP32), the penalty weights -> pen / pen32 (cell 0), and the inverse of the
+// diagonal block in FP64 -> Binv and/or in FP32 -> Binv32 (each when non-null).
 template <int K>
 __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c, double alpha,
-                                 double dup, double *Dblk, double *wq, double *Binv, int *status) {
+                                 double dup, double *Dblk, double *wq, float *wq32, double *pen, float *pen32,
+                                 double *Binv, float *Binv32, int *status) {
     typedef Dims<K> Dm;
     constexpr int NU = Dm::NU, NFQ = Dm::NFQ;
     extern __shared__ double sm[];
     const int cell = blockIdx.x;
     if (cell >= M.ncells) return;
     Team tm{(int)threadIdx.x, (int)blockDim.x};
+    if (cell == 0)
+        TFOR(q, NFQ) {
+            pen[q] = -c * alpha * ldg(&R.fw[q]);
+            pen32[q] = (float)pen[q];
+        }
     CellGeo g = M.geo[cell];
     const double *Qn[3];
     int ne[3];
@@ -481,7 +489,7 @@ __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c
         Qn[e] = o >= 0 ? Qs + (size_t)o * NU : nullptr;
         ne[e] = M.cell_nbr_edge[3 * cell + e];
     }
-    double *D = sm + 2 * Dm::NQ + 3 * NFQ + Dm::MU * Dm::MU;
+    double *D = sm + fimpl_diag_scratch<K>();
     double *wqs = D + NU * NU;
     cell_fimpl_diag<K>(tm, R, g, Qs + (size_t)cell * NU, Qn, ne, c, alpha, dup, sm, D, wqs);
     const long long nrows = (long long)M.ncells * NU;
@@ -489,53 +497,76 @@ __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c
         int col = i / NU, row = i % NU;
         Dblk[(size_t)col * nrows + (size_t)cell * NU + row] = D[row * NU + col];
     }
-    TFOR(i, 3 * NFQ) wq[(size_t)cell * 3 * NFQ + i] = wqs[i];
-    tm.sync();
-    if (!Binv) return;
-    double *inv = wqs + 3 * NFQ;
-    int *piv = (int *)(inv + NU * NU);
-    // the diagonal block is consumed by the inversion (in place)
-    bool ok = team_invert<NU>(tm, D, inv, piv);
-    TFOR(i, NU * NU) {
-        int col = i / NU, row = i % NU;
-        Binv[(size_t)col * nrows + (size_t)cell * NU + row] = inv[row * NU + col];
+    TFOR(i, 3 * NFQ) {
+        wq[(size_t)cell * 3 * NFQ + i] = wqs[i];
+        wq32[(size_t)cell * 3 * NFQ + i] = (float)wqs[i];
+    }
+    double *inv = wqs + 3 * NFQ;                    // NU^2 doubles, or 2 NU^2 floats
+    int *piv = (int *)(inv + 2 * NU * NU);
+    bool ok = true;
+    if (Binv32) {
+        float *A32 = reinterpret_cast<float *>(inv), *I32 = A32 + NU * NU;
+        TFOR(i, NU * NU) A32[i] = (float)D[i];
+        tm.sync();
+        ok = team_invert<NU, float>(tm, A32, I32, piv);
+        TFOR(i, NU * NU) {
+            int col = i / NU, row = i % NU;
+            Binv32[(size_t)col * nrows + (size_t)cell * NU + row] = I32[row * NU + col];
+        }
+        tm.sync();
+    }
+    if (Binv) {
+        // the diagonal block is consumed by the inversion (in place)
+        ok = team_invert<NU, double>(tm, D, inv, piv) && ok;
+        TFOR(i, NU * NU) {
+            int col = i / NU, row = i % NU;
+            Binv[(size_t)col * nrows + (size_t)cell * NU + row] = inv[row * NU + col];
+        }
     }
     if (!ok && tm.tid == 0) atomicExch(status, 1);
 }
 
 // ------------------------------------------------------------ matrix-free neighbour coupling
+// Tables the neighbour coupling needs, in the precision T of the solve: ephi (edge values of the
+// velocity basis, [e][q][a]) and pen (the penalty weights -c alpha fw_q of the assembled operator,
+// written by k_fimpl_assemble).
+template <class T>
+struct EdgeTab {
+    const T *ephi, *pen;
+};
+
 // t[(e*NFQ + q)*2 + d] = pen_q n_d (n . u) + wq(e, q) u_d at the points of this cell's edges,
 // u = the neighbour's velocity at the matching point (its point NFQ-1-q on its edge), taken from
 // the table utr of the cells' own edge values, or evaluated from the coefficients x when utr is
-// null; pen_q = -c alpha fw_q (calpha = c alpha). Zero on walls.
-template <int K>
-__device__ __forceinline__ void team_nbr_flux(const Team &tm, const RefDev &R, const MeshDev &M, int cell,
-                                              const CellGeo &g, const double *__restrict__ wq, double calpha,
-                                              const double *utr, const double *x, double *t) {
+// null. Zero on walls.
+template <int K, class T>
+__device__ __forceinline__ void team_nbr_flux(const Team &tm, const EdgeTab<T> &E, const MeshDev &M, int cell,
+                                              const T *__restrict__ wq, const T *utr, const T *x, T *t) {
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
+    const CellGeo *gp = M.geo + cell;
     TFOR(i, 3 * NFQ) {
         const int e = i / NFQ, q = i % NFQ;
         const int o = __ldg(&M.cell_nbr[3 * cell + e]);
-        double tx = 0.0, ty = 0.0;
+        T tx = 0, ty = 0;
         if (o >= 0) {
             const int eo = __ldg(&M.cell_nbr_edge[3 * cell + e]), qo = NFQ - 1 - q;
-            double ux = 0.0, uy = 0.0;
+            T ux = 0, uy = 0;
             if (utr) {
-                const double *u = utr + ((size_t)(o * 3 + eo) * NFQ + qo) * 2;
+                const T *u = utr + ((size_t)(o * 3 + eo) * NFQ + qo) * 2;
                 ux = u[0]; uy = u[1];
             } else {
-                const double *ph = &R.ephi[(eo * NFQ + qo) * MU];
-                const double *xo = x + (size_t)o * NU;
+                const T *ph = &E.ephi[(eo * NFQ + qo) * MU];
+                const T *xo = x + (size_t)o * NU;
 #pragma unroll 5
                 for (int b = 0; b < MU; ++b) {
-                    const double f = __ldg(ph + b);
+                    const T f = __ldg(ph + b);
                     ux += f * xo[b]; uy += f * xo[MU + b];
                 }
             }
-            const double nx = g.nx[e], ny = g.ny[e];
-            const double un = nx * ux + ny * uy, pen = -calpha * __ldg(&R.fw[q]);
-            const double w = __ldg(&wq[(size_t)cell * 3 * NFQ + i]);
+            const T nx = (T)gp->nx[e], ny = (T)gp->ny[e];
+            const T un = nx * ux + ny * uy, pen = E.pen[q];
+            const T w = __ldg(&wq[(size_t)cell * 3 * NFQ + i]);
             tx = pen * nx * un + w * ux;
             ty = pen * ny * un + w * uy;
         }
@@ -545,32 +576,31 @@ __device__ __forceinline__ void team_nbr_flux(const Team &tm, const RefDev &R, c
 }
 
 // row (d, a) of the neighbour coupling: sum over the edge points of phi_a(e, q) t[(e, q), d]
-template <int K>
-__device__ __forceinline__ double nbr_row(const RefDev &R, const double *t, int d, int a) {
+template <int K, class T>
+__device__ __forceinline__ T nbr_row(const EdgeTab<T> &E, const T *t, int d, int a) {
     typedef Dims<K> Dm;
-    double s = 0.0;
+    T s = 0;
 #pragma unroll 7
-    for (int i = 0; i < 3 * Dm::NFQ; ++i) s += __ldg(&R.ephi[i * Dm::MU + a]) * t[2 * i + d];
+    for (int i = 0; i < 3 * Dm::NFQ; ++i) s += __ldg(&E.ephi[i * Dm::MU + a]) * t[2 * i + d];
     return s;
 }
 
 // y = (M - cF) x: diagonal block dense, neighbours matrix-free (team per cell)
 template <int K>
-__global__ void k_cell_apply_mf(RefDev R, MeshDev M, const double *__restrict__ Dblk, const double *__restrict__ wq,
-                                double calpha, const double *__restrict__ x, double *__restrict__ y) {
+__global__ void k_cell_apply_mf(EdgeTab<double> E, MeshDev M, const double *__restrict__ Dblk,
+                                const double *__restrict__ wq, const double *__restrict__ x, double *__restrict__ y) {
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU;
     constexpr int SCR = 6 * Dm::NFQ;
     CELL_TEAM(SCR)
     double *t = mine;
-    const CellGeo g = M.geo[cell];
-    team_nbr_flux<K>(tm, R, M, cell, g, wq, calpha, nullptr, x, t);
+    team_nbr_flux<K, double>(tm, E, M, cell, wq, nullptr, x, t);
     tm.sync();
     const long long nrows = (long long)M.ncells * NU;
     const double *xK = x + (size_t)cell * NU;
     TFOR(r, NU) {
         const size_t gi = (size_t)cell * NU + r;
-        double s = nbr_row<K>(R, t, r / MU, r % MU);
+        double s = nbr_row<K, double>(E, t, r / MU, r % MU);
 #pragma unroll 6
         for (int j = 0; j < NU; ++j) s += __ldg(&Dblk[(size_t)j * nrows + gi]) * xK[j];
         y[gi] = s;
@@ -582,7 +612,6 @@ __global__ void k_cell_apply_mf(RefDev R, MeshDev M, const double *__restrict__ 
 // estimate live in device memory; the last block of each reduction does the small serial
 // updates, so one host read per restart cycle suffices.
 constexpr int GM_M = 30;        // restart length of the GMRES cycles
-constexpr int GM_SHORT = 8;     // restart length for loose (inner) tolerances
 struct GmresState {
     double H[(GM_M + 1) * GM_M];     // column-major: H[j*(GM_M+1) + i]
     double cs[GM_M], sn[GM_M], g[GM_M + 1], y[GM_M], hcol[GM_M + 2], h2[GM_M + 2];
@@ -658,80 +687,86 @@ __global__ void k_count_stage(DevCount *acc, const GmresState *fgs) {
     if (fgs->breakdown == 2) acc->breakdowns += 1;
 }
 
-// w (local row values) dotted with V_0..V_{nvec-1}: each thread holds its rows' w in a loop
-template <class WF>
-__device__ bool multidot_rows(const RedBuf rb, const double *V, long long n, int nvec, WF wfun, double *out) {
-    __shared__ double sh[1][32];
+// Dots out[i] = (V_i, w), i < nvec, over the rows a block owns: `ranges` calls f(r0, r1) for each
+// of the block's row ranges. Warp k of the block takes the vectors k, k + nwarps, ... (a warp reads
+// 32 consecutive rows of one vector: coalesced; w is re-read from L1), writes its block partials,
+// and the last block to arrive (atomic ticket, no waiting) adds the blocks' partials in a fixed
+// order, a warp per value. Deterministic; no per-thread accumulator arrays (registers stay few).
+// w must be visible to the whole block (written before a __syncthreads, or an input).
+template <class T, class Ranges>
+__device__ void block_multidot(const RedBuf rb, const T *V, const T *w, long long n, int nvec, Ranges ranges,
+                               double *out) {
     __shared__ int last;
-    for (int i = 0; i < nvec; ++i) {
-        double v[1] = {0.0};
-        GRID_STRIDE(g, n) v[0] += V[(size_t)i * n + g] * wfun(g);
-        block_sum<1>(v, sh);
-        if (threadIdx.x == 0) rb.partials[blockIdx.x * (GM_M + 2) + i] = v[0];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int i = warp; i < nvec; i += nw) {
+        const T *Vi = V + (size_t)i * n;
+        double a = 0.0;
+        ranges([&](long long r0, long long r1) {
+            for (long long g = r0 + lane; g < r1; g += 32) a += (double)Vi[g] * (double)w[g];
+        });
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) {
+            rb.partials[blockIdx.x * (GM_M + 2) + i] = a;
+            __threadfence();
+        }
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
         unsigned t = atomicAdd(rb.counter, 1u);
         last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (!last) return false;
+    if (!last) return;
     __threadfence();
-    for (int i = 0; i < nvec; ++i) {
-        double acc[1] = {0.0};
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc[0] += __ldcg(&rb.partials[b * (GM_M + 2) + i]);
-        block_sum<1>(acc, sh);
-        if (threadIdx.x == 0) out[i] = acc[0];
+    for (int i = warp; i < nvec; i += nw) {
+        double a = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) a += __ldcg(&rb.partials[b * (GM_M + 2) + i]);
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) out[i] = a;
     }
     if (threadIdx.x == 0) *rb.counter = 0u;
-    return threadIdx.x == 0;
 }
 
-// dots of w with V_0..V_{nvec-1} over the rows of the cell groups a team-per-cell kernel assigns
-// to this block (groups blockIdx.x, blockIdx.x + gridDim.x, ... of rows_per_group rows); w was
-// written by this block before the call (visible after __syncthreads)
-__device__ bool multidot_groups(const RedBuf rb, const double *V, const double *w, long long nrows,
-                                long long rows_per_group, int nvec, double *out) {
-    __shared__ double sh[1][32];
-    __shared__ int last;
+// the contiguous row chunk of this block for n rows split over the grid
+struct RowChunk {
+    long long r0, r1;
+    __device__ RowChunk(long long n) {
+        const long long ch = (n + gridDim.x - 1) / gridDim.x;
+        r0 = blockIdx.x * ch;
+        r1 = r0 + ch < n ? r0 + ch : n;
+    }
+};
+
+// out[i] = (V_i, w), i < nvec (rows split in contiguous chunks over the blocks)
+template <class T>
+__device__ void multidot_rows(const RedBuf rb, const T *V, const T *w, long long n, int nvec, double *out) {
+    const RowChunk ch(n);
+    block_multidot(rb, V, w, n, nvec, [&](auto f) { if (ch.r0 < ch.r1) f(ch.r0, ch.r1); }, out);
+}
+
+// the same over the rows of the cell groups a team-per-cell kernel assigns to this block (groups
+// blockIdx.x, blockIdx.x + gridDim.x, ... of rows_per_group rows); w was written by this block
+// before the call
+template <class T>
+__device__ void multidot_groups(const RedBuf rb, const T *V, const T *w, long long nrows, long long rows_per_group,
+                                int nvec, double *out) {
     __syncthreads();
-    for (int i = 0; i < nvec; ++i) {
-        double v[1] = {0.0};
-        const double *Vi = V + (size_t)i * nrows;
-        for (long long g0 = blockIdx.x * rows_per_group; g0 < nrows; g0 += gridDim.x * rows_per_group) {
-            const long long g1 = g0 + rows_per_group < nrows ? g0 + rows_per_group : nrows;
-            for (long long r = g0 + threadIdx.x; r < g1; r += blockDim.x) v[0] += Vi[r] * w[r];
-        }
-        block_sum<1>(v, sh);
-        if (threadIdx.x == 0) rb.partials[blockIdx.x * (GM_M + 2) + i] = v[0];
-    }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned t = atomicAdd(rb.counter, 1u);
-        last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    for (int i = 0; i < nvec; ++i) {
-        double acc[1] = {0.0};
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc[0] += __ldcg(&rb.partials[b * (GM_M + 2) + i]);
-        block_sum<1>(acc, sh);
-        if (threadIdx.x == 0) out[i] = acc[0];
-    }
-    if (threadIdx.x == 0) *rb.counter = 0u;
-    return threadIdx.x == 0;
+    block_multidot(rb, V, w, nrows, nvec, [&](auto f) {
+        for (long long g0 = blockIdx.x * rows_per_group; g0 < nrows; g0 += gridDim.x * rows_per_group)
+            f(g0, g0 + rows_per_group < nrows ? g0 + rows_per_group : nrows);
+    }, out);
 }
 
 // start of a cycle: w = b - Bx (Bx = B x precomputed; null on the first cycle, x = 0: w = b);
 // beta = ||w||
+template <class T>
 __global__ void k_gm_start(long long nrows, const double *__restrict__ b, const double *__restrict__ Bx,
-                           double *w, int first, RedBuf rb, GmresState *gs, double rtol, int maxit) {
+                           T *w, int first, RedBuf rb, GmresState *gs, double rtol, int maxit) {
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(g, nrows) {
-        double r = b[g] - (Bx ? Bx[g] : 0.0);
+        const T r = (T)(b[g] - (Bx ? Bx[g] : 0.0));
         w[g] = r;
-        v[0] += r * r;
+        v[0] += (double)r * (double)r;
     }
     if (grid_sum<1>(rb, v, tot)) {
         double beta = sqrt(tot[0]);
@@ -755,29 +790,34 @@ __global__ void k_gm_start(long long nrows, const double *__restrict__ b, const 
 
 // v_j = w / h (h = beta for j = 0, H[j, j-1] otherwise) -> V_j; z = Binv v_j (cell-local) and z's
 // values at the cell's edge points -> utr (team per cell)
-template <int K>
-__global__ void k_gm_precond_mf(RefDev R, MeshDev M, const double *__restrict__ Binv, const double *__restrict__ w,
-                                double *V, double *utr, const GmresState *gs) {
+template <int K, class T>
+__global__ void k_gm_precond_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ Binv, const T *__restrict__ w,
+                                T *V, T *utr, const GmresState *gs) {
     if (gs->cycle_end) return;
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
     constexpr int SCR = 2 * NU;
-    CELL_TEAM(SCR)
-    double *vK = mine, *zK = mine + NU;
+    extern __shared__ double smd[];
+    T *sm = reinterpret_cast<T *>(smd);
+    const int team = threadIdx.x / TEAM_LANES;
+    const int cell = (blockIdx.x * blockDim.x + threadIdx.x) / TEAM_LANES;
+    if (cell >= M.ncells) return;
+    Team tm{(int)(threadIdx.x % TEAM_LANES), TEAM_LANES};
+    T *vK = sm + team * SCR, *zK = vK + NU;
     const int j = gs->j;
-    const double inv = 1.0 / (j == 0 ? gs->beta : gs->H[(j - 1) * (GM_M + 1) + j]);
+    const T inv = (T)(1.0 / (j == 0 ? gs->beta : gs->H[(j - 1) * (GM_M + 1) + j]));
     const long long nrows = (long long)M.ncells * NU;
-    double *vj = V + (size_t)j * nrows;
+    T *vj = V + (size_t)j * nrows;
     TFOR(r, NU) {
         const size_t gi = (size_t)cell * NU + r;
-        const double v = w[gi] * inv;
+        const T v = w[gi] * inv;
         vj[gi] = v;
         vK[r] = v;
     }
     tm.sync();
     TFOR(r, NU) {
         const size_t gi = (size_t)cell * NU + r;
-        double acc = 0.0;
+        T acc = 0;
 #pragma unroll 6
         for (int q = 0; q < NU; ++q) acc += __ldg(&Binv[(size_t)q * nrows + gi]) * vK[q];
         zK[r] = acc;
@@ -785,8 +825,8 @@ __global__ void k_gm_precond_mf(RefDev R, MeshDev M, const double *__restrict__ 
     tm.sync();
     TFOR(i, 3 * NFQ * 2) {
         const int d = i & 1, p = i >> 1;            // p = e*NFQ + q
-        const double *ph = &R.ephi[p * MU];
-        double s = 0.0;
+        const T *ph = &E.ephi[p * MU];
+        T s = 0;
 #pragma unroll 5
         for (int b = 0; b < MU; ++b) s += __ldg(ph + b) * zK[d * MU + b];
         utr[(size_t)cell * 3 * NFQ * 2 + i] = s;
@@ -795,60 +835,69 @@ __global__ void k_gm_precond_mf(RefDev R, MeshDev M, const double *__restrict__ 
 
 // w = B z = v_j + (neighbour coupling) z for z = Binv v_j (the diagonal block returns v_j);
 // hcol[i] = (V_i, w), i <= j. Team per cell over groups of cells; grid <= MAX_RED_BLOCKS.
-template <int K>
-__global__ void k_gm_apply_mf(RefDev R, MeshDev M, const double *__restrict__ wq, double calpha,
-                              const double *__restrict__ utr, double *w, const double *__restrict__ V, RedBuf rb,
-                              GmresState *gs) {
+template <int K, class T>
+__global__ void k_gm_apply_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ wq, const T *__restrict__ utr, T *w,
+                              const T *__restrict__ V, RedBuf rb, GmresState *gs) {
     if (gs->cycle_end) return;
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
-    extern __shared__ double sm[];
+    extern __shared__ double smd[];
     const int team = threadIdx.x / TEAM_LANES, tpb = blockDim.x / TEAM_LANES;
     Team tm{(int)(threadIdx.x % TEAM_LANES), TEAM_LANES};
-    double *t = sm + team * (6 * NFQ);
+    T *t = reinterpret_cast<T *>(smd) + team * (6 * NFQ);
     const long long nrows = (long long)M.ncells * NU;
     const int j = gs->j;
-    const double *vj = V + (size_t)j * nrows;
+    const T *vj = V + (size_t)j * nrows;
     // cells come in pairs (2 n^2 triangles) and groups start at multiples of tpb: both teams of
     // a warp are active or idle together
     for (int base = blockIdx.x * tpb; base < M.ncells; base += gridDim.x * tpb) {
         const int cell = base + team;
         if (cell < M.ncells) {
-            const CellGeo g = M.geo[cell];
-            team_nbr_flux<K>(tm, R, M, cell, g, wq, calpha, utr, nullptr, t);
+            team_nbr_flux<K, T>(tm, E, M, cell, wq, utr, nullptr, t);
             tm.sync();
             TFOR(r, NU) {
                 const size_t gi = (size_t)cell * NU + r;
-                w[gi] = vj[gi] + nbr_row<K>(R, t, r / MU, r % MU);
+                w[gi] = vj[gi] + nbr_row<K, T>(E, t, r / MU, r % MU);
             }
             tm.sync();
         }
     }
-    multidot_groups(rb, V, w, nrows, (long long)tpb * NU, j + 1, gs->hcol);
+    multidot_groups(rb, V, (const T *)w, nrows, (long long)tpb * NU, j + 1, gs->hcol);
 }
 
-// w -= V hcol; h2 = (V_i, w)  (second Gram-Schmidt pass)
-__global__ void k_gm_orth1(double *w, const double *__restrict__ V, long long nrows, RedBuf rb, GmresState *gs) {
+// w -= V hcol; h2 = (V_i, w)  (second Gram-Schmidt pass); rows in contiguous chunks per block
+template <class T>
+__global__ void k_gm_orth1(T *w, const T *__restrict__ V, long long nrows, RedBuf rb, GmresState *gs) {
     if (gs->cycle_end) return;
     const int nvec = gs->j + 1;
-    GRID_STRIDE(g, nrows) {
+    __shared__ double h[GM_M + 1];
+    if ((int)threadIdx.x < nvec) h[threadIdx.x] = gs->hcol[threadIdx.x];
+    __syncthreads();
+    const RowChunk ch(nrows);
+    for (long long g = ch.r0 + threadIdx.x; g < ch.r1; g += blockDim.x) {
         double s = w[g];
-        for (int i = 0; i < nvec; ++i) s -= gs->hcol[i] * V[(size_t)i * nrows + g];
-        w[g] = s;
+        for (int i = 0; i < nvec; ++i) s -= h[i] * (double)V[(size_t)i * nrows + g];
+        w[g] = (T)s;
     }
-    multidot_rows(rb, V, nrows, nvec, [&](long long g) { return w[g]; }, gs->h2);
+    __syncthreads();
+    block_multidot(rb, V, (const T *)w, nrows, nvec, [&](auto f) { if (ch.r0 < ch.r1) f(ch.r0, ch.r1); }, gs->h2);
 }
 
 // w -= V h2; ||w|| -> H[j+1, j]; Givens rotations; residual estimate
-__global__ void k_gm_orth2(double *w, const double *__restrict__ V, long long nrows, RedBuf rb, GmresState *gs) {
+template <class T>
+__global__ void k_gm_orth2(T *w, const T *__restrict__ V, long long nrows, RedBuf rb, GmresState *gs) {
     if (gs->cycle_end) return;
     const int j = gs->j, nvec = j + 1;
+    __shared__ double h[GM_M + 1];
+    if ((int)threadIdx.x < nvec) h[threadIdx.x] = gs->h2[threadIdx.x];
+    __syncthreads();
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(g, nrows) {
         double s = w[g];
-        for (int i = 0; i < nvec; ++i) s -= gs->h2[i] * V[(size_t)i * nrows + g];
-        w[g] = s;
-        v[0] += s * s;
+        for (int i = 0; i < nvec; ++i) s -= h[i] * (double)V[(size_t)i * nrows + g];
+        const T st = (T)s;
+        w[g] = st;
+        v[0] += (double)st * (double)st;
     }
     if (grid_sum<1>(rb, v, tot)) {
         double *Hc = gs->H + j * (GM_M + 1);
@@ -893,23 +942,27 @@ __global__ void k_gm_solve(GmresState *gs, const double *Hdiag_unused) {
 }
 
 // u = V y (rows), then x += Binv u (cell-local)
-__global__ void k_gm_combine(const double *__restrict__ V, double *u, long long nrows, const GmresState *gs) {
+template <class T>
+__global__ void k_gm_combine(const T *__restrict__ V, T *u, long long nrows, const GmresState *gs) {
     const int m = gs->j;
+    __shared__ double y[GM_M];
+    if ((int)threadIdx.x < m) y[threadIdx.x] = gs->y[threadIdx.x];
+    __syncthreads();
     GRID_STRIDE(g, nrows) {
         double s = 0;
-        for (int i = 0; i < m; ++i) s += gs->y[i] * V[(size_t)i * nrows + g];
-        u[g] = s;
+        for (int i = 0; i < m; ++i) s += y[i] * (double)V[(size_t)i * nrows + g];
+        u[g] = (T)s;
     }
 }
 
-template <int K>
-__global__ void k_gm_update_x(const double *__restrict__ Binv, const double *__restrict__ u, double *x,
+template <int K, class T>
+__global__ void k_gm_update_x(const T *__restrict__ Binv, const T *__restrict__ u, double *x,
                               long long ncells, int first) {
     constexpr int NU = Dims<K>::NU;
     const long long nrows = ncells * NU;
     GRID_STRIDE(g, nrows) {
         long long base = (g / NU) * NU;
-        double acc = 0;
+        T acc = 0;
 #pragma unroll 6
         for (int q = 0; q < NU; ++q) acc += __ldg(&Binv[(size_t)q * nrows + g]) * u[base + q];
         x[g] = (first ? 0.0 : x[g]) + acc;
@@ -1016,7 +1069,7 @@ __global__ void k_vec_normalize(const double *__restrict__ w0, const double *__r
 __global__ void k_vec_dot(const double *__restrict__ w, const double *__restrict__ V, long long n, RedBuf rb,
                           GmresState *gs) {
     if (gs->cycle_end) return;
-    multidot_rows(rb, V, n, gs->j + 1, [&](long long g) { return w[g]; }, gs->hcol);
+    multidot_rows(rb, V, w, n, gs->j + 1, gs->hcol);
 }
 
 // x += u

@@ -148,7 +148,13 @@ struct hdg_ctx {
     void *phi_user = nullptr;
     // Step I
     double *Dblk = nullptr, *Binv = nullptr, *wq = nullptr, *utr = nullptr;
-    double calpha = 0.0;                                     // c alpha of the assembled operator
+    double *pen = nullptr;                                   // -c alpha fw_q of the assembled operator
+    int inv_ok = 0;                                          // inverses of the assembly: INV64 | INV32
+    // FP32 copies for the loose (inner) Step-I solves: tables, block inverses, weights, GMRES work
+    float *ephi32 = nullptr, *pen32 = nullptr, *Binv32 = nullptr, *wq32 = nullptr, *utr32 = nullptr;
+    float *gV32 = nullptr, *gw32 = nullptr, *gu32 = nullptr;
+    cudaGraphExec_t g_stepI32 = nullptr;                     // one loose Step-I solve (host-driven mode)
+    int stepI32_kernels = 0;
     int *dstatus = nullptr;
     // Step II
     double *vK = nullptr, *wK = nullptr, *tb = nullptr, *tx = nullptr, *tr = nullptr, *tz = nullptr,
@@ -189,7 +195,6 @@ struct hdg_ctx {
     cudaGraphExec_t g_step = nullptr;                        // one IMEX step (device-side loops)
     int step_kernels = 0;                                    // kernels of g_step outside its loops
     cudaGraphExec_t gm_first = nullptr, gm_restart = nullptr;   // captured GMRES(30) cycles
-    cudaGraphExec_t gms_first = nullptr, gms_restart = nullptr; // captured GMRES(GM_SHORT) cycles
     double *gb = nullptr, *gx = nullptr;                     // their fixed right-hand side / solution
     // running stats of the current call
     hdg_stats S{};
@@ -223,6 +228,19 @@ void read_scalars(hdg_ctx *c) {
 }
 
 int grid_for(long long n) { return red_grid(n); }
+
+// Krylov orthogonalisation kernels: at most four blocks per SM, several rows per thread
+int g_num_sms = 0;
+int grid_orth(long long n) {
+    if (!g_num_sms) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            g_num_sms = v;
+        if (g_num_sms <= 0) g_num_sms = 152;
+    }
+    const int g = red_grid(n);
+    return g < 4 * g_num_sms ? g : 4 * g_num_sms;
+}
 
 // per-cell team kernels: 128 threads = TEAMS_PER_BLOCK teams of TEAM_LANES lanes
 constexpr int TEAMS_PER_BLOCK = 128 / TEAM_LANES;
@@ -713,44 +731,76 @@ struct Impl {
     }
 
     // ---------------------------------------------------------------- Step I operator
-    // Step-I operator M - cc F(Qs): diagonal blocks, neighbour weights and (invert) the
-    // block-Jacobi inverses
-    static void assemble_stepI(hdg_ctx *c, const double *Qs, double cc, bool invert = true) {
+    // Step-I solves to loose tolerances (the inner solves of the stage preconditioner) run in FP32;
+    // tight ones in FP64. The assembly forms the block inverses the coming solves need.
+    static constexpr int INV64 = 1, INV32 = 2;
+    static bool loose(double rtol) { return rtol >= 1e-4; }
+    static int inv_for(double rtol) { return loose(rtol) ? INV32 : INV64; }
+
+    // Step-I operator M - cc F(Qs): diagonal blocks, neighbour and penalty weights, and the
+    // block-Jacobi inverses named by inv (INV64 | INV32)
+    static void assemble_stepI(hdg_ctx *c, const double *Qs, double cc, int inv) {
         CompTimer tm_(c, &c->S.ms_assembly);
         size_t smem = sizeof(double) * fimpl_smem_doubles<K>();
         CK(cudaFuncSetAttribute(k_fimpl_assemble<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (!c->capturing) CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st));   // (graphs: once per launch)
-        k_fimpl_assemble<K><<<(unsigned)c->ncells, 128, smem, c->st>>>(c->R, c->M, Qs, cc, c->P.alpha, c->P.delta_up,
-                                                                      c->Dblk, c->wq, invert ? c->Binv : nullptr,
-                                                                      c->dstatus);
+        k_fimpl_assemble<K><<<(unsigned)c->ncells, 128, smem, c->st>>>(
+            c->R, c->M, Qs, cc, c->P.alpha, c->P.delta_up, c->Dblk, c->wq, c->wq32, c->pen, c->pen32,
+            (inv & INV64) ? c->Binv : nullptr, (inv & INV32) ? c->Binv32 : nullptr, c->dstatus);
         CKL();
-        c->calpha = cc * c->P.alpha;
+        c->inv_ok = inv;
     }
 
     static void cell_apply(hdg_ctx *c, const double *x, double *y) {
         k_cell_apply_mf<K><<<cell_blocks(c), 128, sizeof(double) * TEAMS_PER_BLOCK * 6 * Dm::NFQ, c->st>>>(
-            c->R, c->M, c->Dblk, c->wq, c->calpha, x, y);
+            EdgeTab<double>{c->R.ephi, c->pen}, c->M, c->Dblk, c->wq, x, y);
         CKL();
     }
 
-    // one Arnoldi step of the Step-I GMRES: V_j, z = Binv V_j (edge values only), w = B z, dots
-    static void gmres_arnoldi(hdg_ctx *c) {
+    // one Arnoldi step of the Step-I GMRES in precision T: V_j, z = Binv V_j (edge values only),
+    // w = B z, dots
+    template <class T>
+    static void gmres_arnoldi(hdg_ctx *c, const EdgeTab<T> &E, const T *Binv, const T *wq, T *utr, T *w, T *V) {
+        const long long n = c->nQ;
+        const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
+        const int go = grid_orth(n);
+        k_gm_precond_mf<K, T><<<cb, 128, sizeof(T) * TEAMS_PER_BLOCK * 2 * NU, c->st>>>(E, c->M, Binv, w, V, utr, c->gs);
+        k_gm_apply_mf<K, T><<<ab, 128, sizeof(T) * TEAMS_PER_BLOCK * 6 * Dm::NFQ, c->st>>>(E, c->M, wq, utr, w, V,
+                                                                                          c->rb(), c->gs);
+        k_gm_orth1<T><<<go, VEC_THREADS, 0, c->st>>>(w, V, n, c->rb(), c->gs);
+        k_gm_orth2<T><<<go, VEC_THREADS, 0, c->st>>>(w, V, n, c->rb(), c->gs);
+    }
+    static void gmres_arnoldi64(hdg_ctx *c) {
+        gmres_arnoldi<double>(c, EdgeTab<double>{c->R.ephi, c->pen}, c->Binv, c->wq, c->utr, c->gw, c->gV);
+    }
+
+    // A loose Step-I solve in FP32, recorded into the current capture: one GMRES(GM_M) cycle from
+    // x = 0 with its Arnoldi steps as a device-side loop, stopping at the tolerance or after GM_M
+    // steps (an inexact solve is what the flexible outer iteration expects). b, x: FP64.
+    static void stepI32_record(hdg_ctx *c, const double *b, double *x) {
         const long long n = c->nQ;
         const int g = grid_for(n);
-        const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
-        const size_t sm_t = sizeof(double) * TEAMS_PER_BLOCK * 6 * Dm::NFQ;
-        k_gm_precond_mf<K><<<cb, 128, sizeof(double) * TEAMS_PER_BLOCK * 2 * NU, c->st>>>(c->R, c->M, c->Binv, c->gw,
-                                                                                          c->gV, c->utr, c->gs);
-        k_gm_apply_mf<K><<<ab, 128, sm_t, c->st>>>(c->R, c->M, c->wq, c->calpha, c->utr, c->gw, c->gV, c->rb(), c->gs);
-        k_gm_orth1<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
-        k_gm_orth2<<<g, VEC_THREADS, 0, c->st>>>(c->gw, c->gV, n, c->rb(), c->gs);
+        const EdgeTab<float> E{c->ephi32, c->pen32};
+        k_gm_start<float><<<g, VEC_THREADS, 0, c->st>>>(n, b, nullptr, c->gw32, 1, c->rb(), c->gs, -1.0, 0);
+        k_gm_set_cycle<<<1, 1, 0, c->st>>>(c->gs, GM_M);
+        capture_while(
+            c, [&](LoopCtl L) { k_loop_init<<<1, 1, 0, c->st>>>(L, &c->gs->cycle_end); },
+            [&](LoopCtl L) {
+                gmres_arnoldi<float>(c, E, c->Binv32, c->wq32, c->utr32, c->gw32, c->gV32);
+                k_loop_ctl<<<1, 1, 0, c->st>>>(L, GM_M + 1, &c->gs->cycle_end);
+            });
+        k_gm_solve<<<1, 32, 0, c->st>>>(c->gs, nullptr);
+        k_gm_combine<float><<<g, VEC_THREADS, 0, c->st>>>(c->gV32, c->gu32, n, c->gs);
+        k_gm_update_x<K, float><<<g, VEC_THREADS, 0, c->st>>>(c->Binv32, c->gu32, x, c->ncells, 1);
+        k_count_solve<<<1, 1, 0, c->st>>>(c->dcnt, c->gs, nullptr);
+        CKL();
     }
 
     // cycle start: w = b - B x (x = 0 on the first cycle)
     static void gmres_start(hdg_ctx *c, int first) {
         if (!first) cell_apply(c, c->gx, c->gz);
-        k_gm_start<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->nQ, c->gb, first ? nullptr : c->gz, c->gw, first,
-                                                              c->rb(), c->gs, -1.0, 0);
+        k_gm_start<double><<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->nQ, c->gb, first ? nullptr : c->gz, c->gw,
+                                                                      first, c->rb(), c->gs, -1.0, 0);
     }
 
     // Restarted GMRES(GM_M) on the assembled Step-I operator with right block-Jacobi
@@ -761,7 +811,7 @@ struct Impl {
         const int g = grid_for(n);
         gmres_start(c, first);
         k_gm_set_cycle<<<1, 1, 0, c->st>>>(c->gs, m);
-        for (int j = 0; j < m; ++j) gmres_arnoldi(c);
+        for (int j = 0; j < m; ++j) gmres_arnoldi64(c);
         k_gm_solve<<<1, 32, 0, c->st>>>(c->gs, nullptr);
         k_gm_combine<<<g, VEC_THREADS, 0, c->st>>>(c->gV, c->gu, n, c->gs);
         k_gm_update_x<K><<<g, VEC_THREADS, 0, c->st>>>(c->Binv, c->gu, c->gx, c->ncells, first);
@@ -777,7 +827,7 @@ struct Impl {
         capture_while(
             c, [&](LoopCtl L) { k_loop_init<<<1, 1, 0, c->st>>>(L, &c->gs->cycle_end); },
             [&](LoopCtl L) {
-                gmres_arnoldi(c);
+                gmres_arnoldi64(c);
                 k_loop_ctl<<<1, 1, 0, c->st>>>(L, m + 1, &c->gs->cycle_end);
             });
         k_gm_solve<<<1, 32, 0, c->st>>>(c->gs, nullptr);
@@ -789,13 +839,25 @@ struct Impl {
     static void stepI_solve(hdg_ctx *c, const double *b, double *x, double rtol = -1.0) {
         if (!(rtol > 0)) rtol = c->P.stepI_rtol;
         CompTimer tm_(c, &c->S.ms_stepI);
-        if (b != c->gb) CK(cudaMemcpyAsync(c->gb, b, 8 * c->nQ, cudaMemcpyDeviceToDevice, c->st));
+        if (!(c->inv_ok & inv_for(rtol))) throw std::logic_error("Step-I solve without the block inverses it needs");
         k_gm_set_tol<<<1, 1, 0, c->st>>>(c->gs, rtol, c->P.max_iters);
         CKL();
-        // loose tolerances (inner solves of the stage preconditioner) converge in a few
-        // iterations: a short cycle avoids launching a full 30-iteration cycle of idle kernels
-        const bool shortc = rtol >= 1e-4;
-        const int m = shortc ? GM_SHORT : GM_M;
+        if (loose(rtol)) {              // FP32, one cycle of at most GM_M steps
+            if (c->capturing) {
+                stepI32_record(c, b, x);
+                return;
+            }
+            if (b != c->gb) CK(cudaMemcpyAsync(c->gb, b, 8 * c->nQ, cudaMemcpyDeviceToDevice, c->st));
+            if (!c->g_stepI32)
+                c->g_stepI32 = capture_graph(c, [&]() { stepI32_record(c, c->gb, c->gx); }, &c->stepI32_kernels);
+            launch_counted(c, c->g_stepI32);
+            CK(cudaStreamSynchronize(c->st));
+            graph_stats(c, c->stepI32_kernels);
+            if (x != c->gx) CK(cudaMemcpyAsync(x, c->gx, 8 * c->nQ, cudaMemcpyDeviceToDevice, c->st));
+            return;
+        }
+        if (b != c->gb) CK(cudaMemcpyAsync(c->gb, b, 8 * c->nQ, cudaMemcpyDeviceToDevice, c->st));
+        const int m = GM_M;
         if (c->capturing) {             // restarts as a device-side loop
             gmres_cycle_dev(c, 1, m);
             const int limit = c->P.max_iters + 2;
@@ -810,7 +872,7 @@ struct Impl {
             CKL();
             return;
         }
-        cudaGraphExec_t &gf = shortc ? c->gms_first : c->gm_first, &gr = shortc ? c->gms_restart : c->gm_restart;
+        cudaGraphExec_t &gf = c->gm_first, &gr = c->gm_restart;
         if (!gf) {
             gf = capture_graph(c, [&]() { gmres_cycle(c, 1, m); });
             gr = capture_graph(c, [&]() { gmres_cycle(c, 0, m); });
@@ -839,7 +901,7 @@ struct Impl {
     // r: dual (modal); Qs: advecting velocity (modal); Q, p, lam: in/out (modal)
     static int richardson(hdg_ctx *c, double cc, const double *r, const double *Qsv, double *Q, double *p,
                           double *lam) {
-        assemble_stepI(c, Qsv, cc);
+        assemble_stepI(c, Qsv, cc, inv_for(c->P.stepI_rtol));
         int hstat = 0;
         CK(cudaMemcpyAsync(&hstat, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st));
         condense(c, cc);
@@ -937,9 +999,9 @@ struct Impl {
                         chorin_precond(c, cc, c->fv, c->fz);
                         k_slot_store<<<g, VEC_THREADS, 0, c->st>>>(c->fz, c->fZ, N, fgs);
                         stage_apply(c, cc, c->fz, w);
-                        k_vec_dot<<<g, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
-                        k_gm_orth1<<<g, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
-                        k_gm_orth2<<<g, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
+                        k_vec_dot<<<grid_orth(N), VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
+                        k_gm_orth1<<<grid_orth(N), VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
+                        k_gm_orth2<<<grid_orth(N), VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
                         k_loop_ctl<<<1, 1, 0, c->st>>>(L2, GM_M + 1, &fgs->cycle_end);
                         CKL();
                     });
@@ -977,7 +1039,7 @@ struct Impl {
     // the Chorin split (Alg. 2's preconditioner; plain Alg. 2 is its Richardson iteration).
     static int stage_fgmres(hdg_ctx *c, double cc, const double *r, const double *Qsv, double *Q, double *p,
                             double *lam) {
-        assemble_stepI(c, Qsv, cc);
+        assemble_stepI(c, Qsv, cc, inv_for(c->P.inner_stepI_rtol));
         CondCache &E = condense(c, cc);
         if (!c->capturing) {
             int hstat = 0;
@@ -1032,9 +1094,9 @@ struct Impl {
                 double *Vj = c->fV + (size_t)j * N, *Zj = c->fZ + (size_t)j * N;
                 chorin_precond(c, cc, Vj, Zj);
                 stage_apply(c, cc, Zj, w);
-                k_vec_dot<<<g, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), c->fgs);
-                k_gm_orth1<<<g, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), c->fgs);
-                k_gm_orth2<<<g, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), c->fgs);
+                k_vec_dot<<<grid_orth(N), VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), c->fgs);
+                k_gm_orth1<<<grid_orth(N), VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), c->fgs);
+                k_gm_orth2<<<grid_orth(N), VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), c->fgs);
                 CKL();
                 CK(cudaMemcpyAsync(c->hfgs, c->fgs, sizeof(GmresState), cudaMemcpyDeviceToHost, c->st));
                 CK(cudaStreamSynchronize(c->st));
@@ -1076,7 +1138,7 @@ struct Impl {
 
     // f^impl(w, Q, P(Q)) + phi(t) (w.F) as a dual vector, using the Step-I buffers (c = 1)
     static void fimpl_dual(hdg_ctx *c, const double *Q, const double *Qs, double tt, double *out) {
-        assemble_stepI(c, Qs, 1.0, false);
+        assemble_stepI(c, Qs, 1.0, 0);
         cell_apply(c, Q, c->q[6]);
         LinComb L{};
         L.nterms = 2;
@@ -1411,6 +1473,19 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         c->Dblk = c->alloc<double>((size_t)c->NU * nQ);
         c->wq = c->alloc<double>((size_t)c->ncells * 3 * nfq);
         c->utr = c->alloc<double>((size_t)c->ncells * 3 * nfq * 2);
+        c->pen = c->alloc<double>(nfq);
+        c->pen32 = c->alloc<float>(nfq);
+        c->Binv32 = c->alloc<float>((size_t)c->NU * nQ);
+        c->wq32 = c->alloc<float>((size_t)c->ncells * 3 * nfq);
+        c->utr32 = c->alloc<float>((size_t)c->ncells * 3 * nfq * 2);
+        c->gV32 = c->alloc<float>((size_t)(GM_M + 1) * nQ);
+        c->gw32 = c->alloc<float>(nQ);
+        c->gu32 = c->alloc<float>(nQ);
+        {
+            std::vector<float> e32(c->T.ephi.begin(), c->T.ephi.end());
+            c->ephi32 = c->alloc<float>(e32.size());
+            CK(cudaMemcpy(c->ephi32, e32.data(), e32.size() * sizeof(float), cudaMemcpyHostToDevice));
+        }
         c->Binv = c->alloc<double>((size_t)c->NU * nQ);
         c->dstatus = c->alloc<int>(1);
         c->vK = c->alloc<double>((size_t)c->ncells * c->NL);
@@ -1477,8 +1552,7 @@ void hdg_destroy(hdg_ctx *c) {
     }
     if (c->gm_first) cudaGraphExecDestroy(c->gm_first);
     if (c->gm_restart) cudaGraphExecDestroy(c->gm_restart);
-    if (c->gms_first) cudaGraphExecDestroy(c->gms_first);
-    if (c->gms_restart) cudaGraphExecDestroy(c->gms_restart);
+    if (c->g_stepI32) cudaGraphExecDestroy(c->g_stepI32);
     if (c->g_step) cudaGraphExecDestroy(c->g_step);
     if (c->cap) cudaStreamDestroy(c->cap);
     for (cudaStream_t s : c->capst)
@@ -1649,7 +1723,7 @@ hdg_status hdg_tentative_solve(hdg_ctx *c, double cc, const double *Qstar, const
             I::to_modal(c, Qstar, c->q[1], 0);
             I::to_modal(c, R, c->q[2], 0);
             I::mass(c, c->q[2], c->q[3], 0);
-            I::assemble_stepI(c, c->q[1], cc);
+            I::assemble_stepI(c, c->q[1], cc, I::inv_for(c->P.stepI_rtol));
             I::stepI_solve(c, c->q[3], c->q[4], c->P.stepI_rtol);
             I::to_nodal(c, c->q[4], Qbar, 0);
         });
@@ -1750,7 +1824,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
             DISPATCH(c, {
                 // operator of a stage at coefficient cc around the current state; v = (M Q, 0, 0)
                 I::bdm(c, c->Q, c->q[5]);
-                I::assemble_stepI(c, c->q[5], cc);
+                I::assemble_stepI(c, c->q[5], cc, I::inv_for(c->P.inner_stepI_rtol));
                 I::condense(c, cc);
                 I::mass(c, c->Q, c->fv, 0);
                 const long long N = c->nQ + c->nPv + c->nL;
