@@ -883,13 +883,15 @@ __global__ void k_gm_orth1(T *w, const T *__restrict__ V, long long nrows, RedBu
     block_multidot(rb, V, (const T *)w, nrows, nvec, [&](auto f) { if (ch.r0 < ch.r1) f(ch.r0, ch.r1); }, gs->h2);
 }
 
-// w -= V h2; ||w|| -> H[j+1, j]; Givens rotations; residual estimate
-template <class T>
+// w -= V h2; ||w|| -> H[j+1, j]; Givens rotations; residual estimate. CGS1: single classical
+// Gram-Schmidt pass (w -= V hcol straight after the first dots; no orth1), used by the FP32 inner
+// solves whose loose tolerance does not need the second pass.
+template <class T, bool CGS1 = false>
 __global__ void k_gm_orth2(T *w, const T *__restrict__ V, long long nrows, RedBuf rb, GmresState *gs) {
     if (gs->cycle_end) return;
     const int j = gs->j, nvec = j + 1;
     __shared__ double h[GM_M + 1];
-    if ((int)threadIdx.x < nvec) h[threadIdx.x] = gs->h2[threadIdx.x];
+    if ((int)threadIdx.x < nvec) h[threadIdx.x] = CGS1 ? gs->hcol[threadIdx.x] : gs->h2[threadIdx.x];
     __syncthreads();
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(g, nrows) {
@@ -901,7 +903,7 @@ __global__ void k_gm_orth2(T *w, const T *__restrict__ V, long long nrows, RedBu
     }
     if (grid_sum<1>(rb, v, tot)) {
         double *Hc = gs->H + j * (GM_M + 1);
-        for (int i = 0; i <= j; ++i) Hc[i] = gs->hcol[i] + gs->h2[i];
+        for (int i = 0; i <= j; ++i) Hc[i] = CGS1 ? gs->hcol[i] : gs->hcol[i] + gs->h2[i];
         double hn = sqrt(tot[0]);
         Hc[j + 1] = hn;
         for (int i = 0; i < j; ++i) {                     // previous rotations

@@ -758,7 +758,7 @@ struct Impl {
     }
 
     // one Arnoldi step of the Step-I GMRES in precision T: V_j, z = Binv V_j (edge values only),
-    // w = B z, dots
+    // w = B z, dots, orthogonalisation (classical Gram-Schmidt, twice in FP64, once in FP32)
     template <class T>
     static void gmres_arnoldi(hdg_ctx *c, const EdgeTab<T> &E, const T *Binv, const T *wq, T *utr, T *w, T *V) {
         const long long n = c->nQ;
@@ -767,8 +767,12 @@ struct Impl {
         k_gm_precond_mf<K, T><<<cb, 128, sizeof(T) * TEAMS_PER_BLOCK * 2 * NU, c->st>>>(E, c->M, Binv, w, V, utr, c->gs);
         k_gm_apply_mf<K, T><<<ab, 128, sizeof(T) * TEAMS_PER_BLOCK * 6 * Dm::NFQ, c->st>>>(E, c->M, wq, utr, w, V,
                                                                                           c->rb(), c->gs);
-        k_gm_orth1<T><<<go, VEC_THREADS, 0, c->st>>>(w, V, n, c->rb(), c->gs);
-        k_gm_orth2<T><<<go, VEC_THREADS, 0, c->st>>>(w, V, n, c->rb(), c->gs);
+        if (sizeof(T) == sizeof(double)) {        // tight FP64 solves: two Gram-Schmidt passes
+            k_gm_orth1<T><<<go, VEC_THREADS, 0, c->st>>>(w, V, n, c->rb(), c->gs);
+            k_gm_orth2<T><<<go, VEC_THREADS, 0, c->st>>>(w, V, n, c->rb(), c->gs);
+        } else {                                  // loose FP32 inner solves: one pass
+            k_gm_orth2<T, true><<<go, VEC_THREADS, 0, c->st>>>(w, V, n, c->rb(), c->gs);
+        }
     }
     static void gmres_arnoldi64(hdg_ctx *c) {
         gmres_arnoldi<double>(c, EdgeTab<double>{c->R.ephi, c->pen}, c->Binv, c->wq, c->utr, c->gw, c->gV);
