@@ -336,6 +336,12 @@ __global__ void k_gm_set_tol(GmresState *gs, double rtol, int maxit) {
     gs->maxit = maxit;
 }
 
+// instrumentation: put an Arnoldi step j of a live cycle in place (one kernel timed alone)
+__global__ void k_gm_set_step(GmresState *gs, int j) {
+    gs->j = j;
+    gs->cycle_end = 0;
+}
+
 }  // namespace hdg
 
 namespace hdg {

@@ -1820,10 +1820,47 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *c, hdg_stats *stats) {
 }
 
 hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *ms, double *bytes) {
-    if (!c || reps < 1 || !ms || !bytes || which < 0 || which > 5 || (which != 1 && !(cc > 0)))
+    if (!c || reps < 1 || !ms || !bytes || which < 0 || which > 6 || (which != 1 && !(cc > 0)))
         return HDG_ERR_INVALID_ARG;
     if (which >= 2 && !c->fv) return HDG_ERR_INVALID_ARG;
     try {
+        if (which == 6) {
+            DISPATCH(c, {
+                // one FP32 inner Step-I solve fills the basis and edge values; then the Arnoldi
+                // product of step j = 4 is launched alone
+                constexpr int J = 4;
+                I::bdm(c, c->Q, c->q[5]);
+                I::assemble_stepI(c, c->q[5], cc, I::INV32);
+                I::mass(c, c->Q, c->fv, 0);
+                k_gm_set_tol<<<1, 1, 0, c->st>>>(c->gs, 1e-30, J + 1);   // runs J + 1 steps
+                CKL();
+                cudaGraphExec_t ex = capture_graph(c, [&]() { I::stepI32_record(c, c->fv, c->q[2]); });
+                CK(cudaGraphLaunch(ex, c->st));
+                const EdgeTab<float> E{c->ephi32, c->pen32};
+                const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
+                const size_t sm = sizeof(float) * TEAMS_PER_BLOCK * 6 * I::Dm::NFQ;
+                auto launch = [&]() {
+                    k_gm_apply_mf<I::K_, float><<<ab, 128, sm, c->st>>>(E, c->M, c->wq32, c->utr32, c->gw32, c->gV32,
+                                                                        c->rb(), c->gs);
+                };
+                k_gm_set_step<<<1, 1, 0, c->st>>>(c->gs, J);
+                launch();
+                CKL();
+                CK(cudaEventRecord(c->e0, c->st));
+                for (int r = 0; r < reps; ++r) launch();
+                CK(cudaEventRecord(c->e1, c->st));
+                CK(cudaEventSynchronize(c->e1));
+                cudaGraphExecDestroy(ex);
+                const int nfq = I::Dm::NFQ;
+                // neighbour edge values (2 floats per point) + weights + v_j read + w written +
+                // the J + 1 basis vectors of the dots
+                *bytes = 4.0 * ((double)c->ncells * 3 * nfq * 3 + 2.0 * c->nQ + (J + 1.0) * c->nQ);
+            });
+            float t = 0;
+            CK(cudaEventElapsedTime(&t, c->e0, c->e1));
+            *ms = t / reps;
+            return HDG_OK;
+        }
         if (which >= 2) {
             DISPATCH(c, {
                 // operator of a stage at coefficient cc around the current state; v = (M Q, 0, 0)
