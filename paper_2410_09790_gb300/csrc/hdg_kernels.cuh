@@ -692,7 +692,9 @@ __global__ void k_count_stage(DevCount *acc, const GmresState *fgs) {
 // 32 consecutive rows of one vector: coalesced; w is re-read from L1), writes its block partials,
 // and the last block to arrive (atomic ticket, no waiting) adds the blocks' partials in a fixed
 // order, a warp per value. Deterministic; no per-thread accumulator arrays (registers stay few).
-// w must be visible to the whole block (written before a __syncthreads, or an input).
+// Lanes accumulate in T (FP32 for the inner solves: GB300's FP64 rate is low), warps and blocks
+// combine in FP64. w must be visible to the whole block (written before a __syncthreads, or an
+// input).
 template <class T, class Ranges>
 __device__ void block_multidot(const RedBuf rb, const T *V, const T *w, long long n, int nvec, Ranges ranges,
                                double *out) {
@@ -700,10 +702,11 @@ __device__ void block_multidot(const RedBuf rb, const T *V, const T *w, long lon
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     for (int i = warp; i < nvec; i += nw) {
         const T *Vi = V + (size_t)i * n;
-        double a = 0.0;
+        T at = 0;
         ranges([&](long long r0, long long r1) {
-            for (long long g = r0 + lane; g < r1; g += 32) a += (double)Vi[g] * (double)w[g];
+            for (long long g = r0 + lane; g < r1; g += 32) at += Vi[g] * w[g];
         });
+        double a = (double)at;
         for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
         if (lane == 0) {
             rb.partials[blockIdx.x * (GM_M + 2) + i] = a;
@@ -875,9 +878,9 @@ __global__ void k_gm_orth1(T *w, const T *__restrict__ V, long long nrows, RedBu
     __syncthreads();
     const RowChunk ch(nrows);
     for (long long g = ch.r0 + threadIdx.x; g < ch.r1; g += blockDim.x) {
-        double s = w[g];
-        for (int i = 0; i < nvec; ++i) s -= h[i] * (double)V[(size_t)i * nrows + g];
-        w[g] = (T)s;
+        T s = w[g];
+        for (int i = 0; i < nvec; ++i) s -= (T)h[i] * V[(size_t)i * nrows + g];
+        w[g] = s;
     }
     __syncthreads();
     block_multidot(rb, V, (const T *)w, nrows, nvec, [&](auto f) { if (ch.r0 < ch.r1) f(ch.r0, ch.r1); }, gs->h2);
@@ -894,13 +897,14 @@ __global__ void k_gm_orth2(T *w, const T *__restrict__ V, long long nrows, RedBu
     if ((int)threadIdx.x < nvec) h[threadIdx.x] = CGS1 ? gs->hcol[threadIdx.x] : gs->h2[threadIdx.x];
     __syncthreads();
     double v[1] = {0.0}, tot[1];
+    T vt = 0;
     GRID_STRIDE(g, nrows) {
-        double s = w[g];
-        for (int i = 0; i < nvec; ++i) s -= h[i] * (double)V[(size_t)i * nrows + g];
-        const T st = (T)s;
-        w[g] = st;
-        v[0] += (double)st * (double)st;
+        T s = w[g];
+        for (int i = 0; i < nvec; ++i) s -= (T)h[i] * V[(size_t)i * nrows + g];
+        w[g] = s;
+        vt += s * s;
     }
+    v[0] = (double)vt;
     if (grid_sum<1>(rb, v, tot)) {
         double *Hc = gs->H + j * (GM_M + 1);
         for (int i = 0; i <= j; ++i) Hc[i] = CGS1 ? gs->hcol[i] : gs->hcol[i] + gs->h2[i];
@@ -951,9 +955,9 @@ __global__ void k_gm_combine(const T *__restrict__ V, T *u, long long nrows, con
     if ((int)threadIdx.x < m) y[threadIdx.x] = gs->y[threadIdx.x];
     __syncthreads();
     GRID_STRIDE(g, nrows) {
-        double s = 0;
-        for (int i = 0; i < m; ++i) s += y[i] * (double)V[(size_t)i * nrows + g];
-        u[g] = (T)s;
+        T s = 0;
+        for (int i = 0; i < m; ++i) s += (T)y[i] * V[(size_t)i * nrows + g];
+        u[g] = s;
     }
 }
 
