@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(n=64, k=3, periodic_x=True, tableau='ARS343', dt=2e-3, n_richardson=0, stage_rtol=1e-10,
                 inner_stepI_rtol=1e-1, inner_trace_rtol=1e-1, trace_rtol=1e-12, stepI_rtol=1e-10,
-                init='shear_layer', width=0.05, amp=1e-3, noise=1e-4, seed=0)
+                inner_trace_vcycles=0, init='shear_layer', width=0.05, amp=1e-3, noise=1e-4, seed=0)
 STAGES = {'ARS343': 3, 'ARS222': 2, 'IMEX_EULER': 1}
 METRIC = 'IMEX stage solves/s (trace-DoF/s alongside)'
 
@@ -180,13 +180,16 @@ def run_gpu(args, rank, world, local_rank):
         w['inner_trace_rtol'] = args.inner_trace_rtol
     if args.inner_stepI_rtol:
         w['inner_stepI_rtol'] = args.inner_stepI_rtol
+    if args.inner_trace_vcycles is not None:
+        w['inner_trace_vcycles'] = args.inner_trace_vcycles
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         ctx = H.Context(w['n'], w['k'], periodic_x=w['periodic_x'], stream=stream, tableau=w['tableau'],
                         dt=w['dt'], n_richardson=w['n_richardson'], richardson_rtol=w['stage_rtol'],
                         richardson_max=600, stage_krylov=1, inner_stepI_rtol=w['inner_stepI_rtol'],
                         inner_trace_rtol=w['inner_trace_rtol'], trace_rtol=w['trace_rtol'],
-                        stepI_rtol=w['stepI_rtol'], device_loops=0 if args.host_loops else 1)
+                        stepI_rtol=w['stepI_rtol'], device_loops=0 if args.host_loops else 1,
+                        inner_trace_vcycles=w['inner_trace_vcycles'])
         Q0 = torch.from_numpy(initial_velocity(w, seed_offset=rank)).to(dev)
         ctx.hdg_set_state(Q0)
         ctx.hdg_div_free_project()
@@ -313,6 +316,8 @@ def main():
     ap.add_argument('--n', type=int, default=None, help='mesh size override (profiling runs only)')
     ap.add_argument('--inner-trace-rtol', type=float, default=None, help='tuning: inner Step II tolerance')
     ap.add_argument('--inner-stepI-rtol', type=float, default=None, help='tuning: inner Step I tolerance')
+    ap.add_argument('--inner-trace-vcycles', type=int, default=None,
+                    help='tuning: Step II inside the preconditioner as n V-cycles (0: CG to the inner tolerance)')
     ap.add_argument('--host-loops', action='store_true',
                     help='drive the Krylov loops from the host (fills the per-component timings)')
     ap.add_argument('--kernel-only', type=int, default=None,

@@ -284,6 +284,31 @@ __global__ void k_cg_setup_mg(const double *__restrict__ b, double *x, double *r
     }
 }
 
+// r = b - mean e0 - S x (stationary V-cycle iteration of the inner trace solves)
+template <int NT>
+__global__ void k_trace_resid(const double *__restrict__ Sell, const int *__restrict__ tcol,
+                              const double *__restrict__ b, const double *__restrict__ x, double *r, int nfacets,
+                              const Scalars *sc) {
+    const double mean = sc->bmean;
+    const long long nrows = (long long)nfacets * NT;
+    GRID_STRIDE(g, nrows) {
+        const int f = (int)(g / NT);
+        double s = b[g] - ((g % NT) == 0 ? mean : 0.0);
+        for (int bb = 0; bb < 5; ++bb) {
+            const int cf = __ldg(&tcol[bb * nfacets + f]);
+            if (cf < 0) continue;
+            for (int j = 0; j < NT; ++j)
+                s -= __ldg(&Sell[(size_t)(bb * NT + j) * nrows + g]) * x[(size_t)cf * NT + j];
+        }
+        r[g] = s;
+    }
+}
+
+// x += z (the V-cycle correction)
+__global__ void k_axpy_done(const double *__restrict__ z, double *x, long long n, const Scalars *sc) {
+    GRID_STRIDE(i, n) x[i] += z[i];
+}
+
 // x += alpha p; r -= alpha Ap
 __global__ void k_cg_update_nz(const double *__restrict__ p, const double *__restrict__ Ap, double *x, double *r,
                                long long n, const Scalars *sc) {

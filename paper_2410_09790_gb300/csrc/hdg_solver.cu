@@ -150,6 +150,7 @@ struct hdg_ctx {
     double *Dblk = nullptr, *Binv = nullptr, *wq = nullptr, *utr = nullptr;
     double *pen = nullptr;                                   // -c alpha fw_q of the assembled operator
     int inv_ok = 0;                                          // inverses of the assembly: INV64 | INV32
+    int trace_vcycles = 0;                                   // > 0: trace solves are that many V-cycles
     // FP32 copies for the loose (inner) Step-I solves: tables, block inverses, weights, GMRES work
     float *ephi32 = nullptr, *pen32 = nullptr, *Binv32 = nullptr, *wq32 = nullptr, *utr32 = nullptr;
     float *gV32 = nullptr, *gw32 = nullptr, *gu32 = nullptr;
@@ -636,6 +637,23 @@ struct Impl {
         if (b != c->tb) CK(cudaMemcpyAsync(c->tb, b, 8 * c->nL, cudaMemcpyDeviceToDevice, c->st));
         k_set_tol<<<1, 1, 0, c->st>>>(c->sc, rtol, c->P.max_iters);
         CKL();
+        if (c->trace_vcycles > 0) {     // a fixed number of V-cycles in place of the CG (inner solves)
+            k_trace_mean<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(c->tb, nf, c->rb(), c->sc);
+            k_cg_setup_mg<NT><<<gr, VEC_THREADS, 0, c->st>>>(c->tb, c->tx, c->tr, c->tp[0], nf, c->sc);
+            for (int v = 0; v < c->trace_vcycles; ++v) {
+                if (v > 0) {            // r = b - mean - S x
+                    k_trace_resid<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->tb, c->tx, c->tr, nf, c->sc);
+                }
+                vcycle(c, E, c->tr, c->tz, false, -1);
+                k_axpy_done<<<gr, VEC_THREADS, 0, c->st>>>(c->tz, c->tx, c->nL, c->sc);
+            }
+            CKL();
+            if (x != c->tx) CK(cudaMemcpyAsync(x, c->tx, 8 * c->nL, cudaMemcpyDeviceToDevice, c->st));
+            if (c->capturing) k_count_solve<<<1, 1, 0, c->st>>>(c->dcnt, nullptr, c->sc);
+            else c->S.trace_solves += 1;
+            CKL();
+            return;
+        }
         if (c->capturing) {             // device-side loop, two iterations per pass
             k_trace_mean<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(c->tb, nf, c->rb(), c->sc);
             k_cg_setup_mg<NT><<<gr, VEC_THREADS, 0, c->st>>>(c->tb, c->tx, c->tr, c->tp[0], nf, c->sc);
@@ -965,7 +983,14 @@ struct Impl {
         double *zQ = z, *zp = z + c->nQ, *zl = z + c->nQ + c->nPv;
         double *Qbar = c->q[2], *U = c->q[4];
         stepI_solve(c, vQ, Qbar, c->P.inner_stepI_rtol);
-        mixed_solve(c, cc, nullptr, Qbar, nullptr, nullptr, U, zp, zl, vp, vl, c->P.inner_trace_rtol);
+        c->trace_vcycles = c->P.inner_trace_vcycles;
+        try {
+            mixed_solve(c, cc, nullptr, Qbar, nullptr, nullptr, U, zp, zl, vp, vl, c->P.inner_trace_rtol);
+        } catch (...) {
+            c->trace_vcycles = 0;
+            throw;
+        }
+        c->trace_vcycles = 0;
         LinComb L{};
         L.nterms = 2; L.coef[0] = 1; L.vec[0] = Qbar; L.coef[1] = 1; L.vec[1] = U;
         k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, L, zQ, c->ncells);
@@ -1335,6 +1360,7 @@ void hdg_default_params(hdg_params *p) {
     p->inner_trace_rtol = 1e-1;
     p->trace_mg = 1;
     p->device_loops = 1;
+    p->inner_trace_vcycles = 0;
 }
 
 const char *hdg_status_string(hdg_status s) {
