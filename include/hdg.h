@@ -100,9 +100,9 @@ typedef struct {
      * an error there (the outer residual test decides). 0 = loops driven from the host (per-
      * component timings in hdg_stats are only filled in this mode). */
     int device_loops;
-    /* Step II inside the stage preconditioner (stage_krylov = 1, multigrid on): 0 (default) = trace
-     * CG to inner_trace_rtol; n > 0 = exactly n V-cycles of the trace multigrid (a fixed linear
-     * preconditioner; the flexible outer iteration decides the accuracy). */
+    /* Step II inside the stage preconditioner (stage_krylov = 1, multigrid on): n > 0 (default 1)
+     * = exactly n V-cycles of the trace multigrid (a fixed linear preconditioner; the flexible
+     * outer iteration decides the accuracy); 0 = trace CG to inner_trace_rtol. */
     int inner_trace_vcycles;
 } hdg_params;
 

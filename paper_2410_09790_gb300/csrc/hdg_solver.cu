@@ -1360,7 +1360,7 @@ void hdg_default_params(hdg_params *p) {
     p->inner_trace_rtol = 1e-1;
     p->trace_mg = 1;
     p->device_loops = 1;
-    p->inner_trace_vcycles = 0;
+    p->inner_trace_vcycles = 1;
 }
 
 const char *hdg_status_string(hdg_status s) {
