@@ -45,6 +45,18 @@ def measured_peaks():
         return 6800.0, 'fallback'
 
 
+def roofline_traffic():
+    """DRAM bytes per launch of the roofline kernel from its committed ncu summary (None if the
+    summary does not state them)."""
+    import re
+    try:
+        with open(os.path.join(ROOT, 'profiles', 'k_gm_apply_mf_fp32_c2.md')) as f:
+            m = re.search(r'^traffic_bytes_per_launch = (\d+)$', f.read(), re.M)
+        return int(m.group(1)) if m else None
+    except OSError:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons during the timed region."""
     Q = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
@@ -284,7 +296,7 @@ def run_gpu(args, rank, world, local_rank):
         'roofline': {'kernel': 'k_gm_apply_mf<float> (Arnoldi product of the FP32 inner Step-I GMRES, step j = 4)',
                      'bound': 'hbm',
                      'achieved': achieved, 'peak': peak, 'unit': 'GB/s', 'frac': achieved / peak,
-                     'peak_kind': peak_kind, 'traffic': None, 'ms_per_launch': a_ms,
+                     'peak_kind': peak_kind, 'traffic': roofline_traffic(), 'ms_per_launch': a_ms,
                      'algorithmic_bytes': a_bytes},
         'trace_apply': {'kernel': 'k_cg_apply', 'achieved_gbs': k_bytes / (k_ms * 1e-3) / 1e9, 'ms_per_launch': k_ms,
                         'bytes': k_bytes},
