@@ -5,9 +5,10 @@
  *
  * Discretisation (Sec. 2.2-2.4): on a structured triangulation of [0,Lx]x[0,Ly] (Sec. 3.2),
  * velocity Q in [DG_{k+1}]^2, pressure p in DG_k with (p)_Omega = 0, trace lambda in P_k on
- * every facet. Time stepping: the s-stage IMEX scheme of Alg. 1, each implicit stage solved by
- * the Chorin-preconditioned Richardson iteration of Alg. 2; Step II is condensed onto the
- * trace (Sec. 2.8) and solved by preconditioned CG on the GPU.
+ * every facet. Time stepping: the s-stage IMEX scheme of Alg. 1, each implicit stage solved
+ * either by the Chorin-split Richardson iteration of Alg. 2 (a fixed number of iterations, as
+ * printed, or to a tolerance) or to a tolerance by flexible GMRES preconditioned by that split;
+ * Step II is condensed onto the trace (Sec. 2.8) and solved by multigrid-preconditioned CG.
  *
  * Exchange format. Every array crossing this interface holds NODAL VALUES on the canonical
  * mesh (independent of the library's internal modal basis):
