@@ -422,6 +422,91 @@ __global__ void k_facet_gather(MeshDev M, const double *__restrict__ v, const do
     }
 }
 
+// ------------------------------------------------------------------ Step II inside the preconditioner
+// The stage preconditioner's Step II reads only (X, Rp_add) and the trace solution; its cell work
+// is linear in them, so per coefficient c the two per-cell maps are formed once (by applying the
+// FP64 cell routines to unit vectors) and stored in FP32:
+//   Lrhs: (X (NU), Rp_add (NP)) -> (v (NL, facet orientation), w (NP))
+//   Lbs:  (w (NP), lambda_local (NL)) -> (U (NU), p (NP))
+// layout L[(col * ncells + cell) * ROWS + row].
+template <int K>
+__global__ void k_build_pre_maps(RefDev R, MeshDev M, double c, double tau, const double *__restrict__ Zc,
+                                 const double *__restrict__ Ac, float *Lrhs, float *Lbs) {
+    typedef Dims<K> Dm;
+    constexpr int NU = Dm::NU, NP = Dm::NP, NL = Dm::NL, MU = Dm::MU;
+    constexpr int SCR = NU + NP + NL + NP + (NL + 4 * MU + NP + NL) + NU + NP + (NL + NP);
+    CELL_TEAM(SCR)
+    double *uin = mine;                 // NU + NP unit input (X, Rp_add)
+    double *vo = uin + NU + NP;         // NL + NP outputs (v, w)
+    double *scr = vo + NL + NP;         // scratch of cell_mixed_rhs
+    double *bo = scr + NL + 4 * MU + NP + NL;   // NU + NP outputs (U, p)
+    double *bscr = bo + NU + NP;        // scratch of cell_mixed_backsub
+    const CellGeo g = M.geo[cell];
+    int flip[3] = {M.cell_flip[3 * cell], M.cell_flip[3 * cell + 1], M.cell_flip[3 * cell + 2]};
+    const double *Z = Zc + (size_t)cell * NP * NL, *A = Ac + (size_t)cell * NP * NP;
+    constexpr int RR = NL + NP, RB = NU + NP;
+    for (int col = 0; col < NU + NP; ++col) {
+        TFOR(i, NU + NP) uin[i] = (i == col) ? 1.0 : 0.0;
+        tm.sync();
+        cell_mixed_rhs<K>(tm, R, g, flip, tau, nullptr, uin, nullptr, nullptr, uin + NU, Z, scr, vo, vo + NL);
+        TFOR(r, RR) Lrhs[((size_t)col * M.ncells + cell) * RR + r] = (float)vo[r];
+        tm.sync();
+    }
+    for (int col = 0; col < NP + NL; ++col) {
+        TFOR(i, NU + NP) uin[i] = (i == col) ? 1.0 : 0.0;     // w = uin[0..NP), lambda = uin[NP..NP+NL)
+        tm.sync();
+        cell_mixed_backsub<K>(tm, R, g, c, nullptr, uin, uin + NP, Z, A, bscr, bo, bo + NU);
+        TFOR(r, RB) Lbs[((size_t)col * M.ncells + cell) * RB + r] = (float)bo[r];
+        tm.sync();
+    }
+}
+
+// v, w of the preconditioner's Step II from X and Rp_add (FP32 map, FP64 in/out)
+template <int K>
+__global__ void k_pre_rhs(MeshDev M, const float *__restrict__ Lrhs, const double *__restrict__ X,
+                          const double *__restrict__ Rp_add, double *v, double *w) {
+    typedef Dims<K> Dm;
+    constexpr int NU = Dm::NU, NP = Dm::NP, NL = Dm::NL, RR = NL + NP;
+    constexpr int SCR = NU + NP;
+    CELL_TEAM(SCR)
+    float *in = reinterpret_cast<float *>(mine);
+    TFOR(i, NU + NP) in[i] = (float)(i < NU ? X[(size_t)cell * NU + i] : Rp_add[(size_t)cell * NP + i - NU]);
+    tm.sync();
+    TFOR(r, RR) {
+        float s = 0.f;
+        for (int col = 0; col < NU + NP; ++col) s += __ldg(&Lrhs[((size_t)col * M.ncells + cell) * RR + r]) * in[col];
+        if (r < NL) v[(size_t)cell * NL + r] = s;
+        else w[(size_t)cell * NP + r - NL] = s;
+    }
+}
+
+// U, p of the preconditioner's Step II from w and the trace solution (FP32 map, FP64 in/out)
+template <int K>
+__global__ void k_pre_backsub(MeshDev M, const float *__restrict__ Lbs, const double *__restrict__ w,
+                              const double *__restrict__ lam, double *U, double *p) {
+    typedef Dims<K> Dm;
+    constexpr int NU = Dm::NU, NP = Dm::NP, NL = Dm::NL, NT = Dm::NT, RB = NU + NP;
+    constexpr int SCR = NP + NL;
+    CELL_TEAM(SCR)
+    float *in = reinterpret_cast<float *>(mine);
+    TFOR(i, NP + NL) {
+        if (i < NP) {
+            in[i] = (float)w[(size_t)cell * NP + i];
+        } else {
+            const int q = i - NP, e = q / NT, j = q % NT;
+            const int f = M.cell_facet[3 * cell + e];
+            in[i] = (float)(tsign(M.cell_flip[3 * cell + e], j) * lam[(size_t)f * NT + j]);
+        }
+    }
+    tm.sync();
+    TFOR(r, RB) {
+        float s = 0.f;
+        for (int col = 0; col < NP + NL; ++col) s += __ldg(&Lbs[((size_t)col * M.ncells + cell) * RB + r]) * in[col];
+        if (r < NU) U[(size_t)cell * NU + r] = s;
+        else p[(size_t)cell * NP + r - NU] = s;
+    }
+}
+
 template <int K>
 __global__ void k_mixed_backsub(RefDev R, MeshDev M, double c, const double *Ru,
                                 const double *__restrict__ w, const double *lam,

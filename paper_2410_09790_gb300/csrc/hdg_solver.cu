@@ -104,6 +104,7 @@ struct CondCache {
     std::vector<MGLevel> lv;                  // lv[0] = level 1 (P1 on the mesh), ...
     double *Minv = nullptr;
     int Nc = 0;
+    float *Lrhs32 = nullptr, *Lbs32 = nullptr;             // preconditioner Step-II maps (FP32)
 };
 
 struct MGWork {                // per-level work vectors (shared by all coefficients)
@@ -740,6 +741,21 @@ struct Impl {
         CKL();
     }
 
+    // FP32 cell maps of the preconditioner's Step II for coefficient cc (formed once, outside
+    // graph captures)
+    static void ensure_pre_maps(hdg_ctx *c, double cc) {
+        CondCache &E = condense(c, cc);
+        if (E.Lrhs32 || c->capturing) return;
+        E.Lrhs32 = c->alloc<float>((size_t)c->ncells * (NU + NP) * (NL + NP));
+        E.Lbs32 = c->alloc<float>((size_t)c->ncells * (NP + NL) * (NU + NP));
+        constexpr int SCR = NU + NP + NL + NP + (NL + 4 * MU + NP + NL) + NU + NP + (NL + NP);
+        const size_t smem = sizeof(double) * TEAMS_PER_BLOCK * SCR;
+        CK(cudaFuncSetAttribute(k_build_pre_maps<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_build_pre_maps<K><<<cell_blocks(c), 128, smem, c->st>>>(c->R, c->M, cc, c->P.tau, E.Zc, E.Ac, E.Lrhs32,
+                                                                 E.Lbs32);
+        CKL();
+    }
+
     static void mean_shift(hdg_ctx *c, double *p, double *lam) {
         k_p_integral<K><<<grid_for(c->ncells), VEC_THREADS, 0, c->st>>>(c->M, p, c->rb(), c->sc);
         CKL();
@@ -985,7 +1001,21 @@ struct Impl {
         stepI_solve(c, vQ, Qbar, c->P.inner_stepI_rtol);
         c->trace_vcycles = c->P.inner_trace_vcycles;
         try {
-            mixed_solve(c, cc, nullptr, Qbar, nullptr, nullptr, U, zp, zl, vp, vl, c->P.inner_trace_rtol);
+            CondCache &E = condense(c, cc);
+            if (E.Lrhs32) {             // Step II from the precomputed FP32 cell maps
+                CompTimer tm_(c, &c->S.ms_trace);
+                const unsigned nb = cell_blocks(c);
+                k_pre_rhs<K><<<nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (NU + NP), c->st>>>(c->M, E.Lrhs32, Qbar, vp,
+                                                                                            c->vK, c->wK);
+                k_facet_gather<NT><<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(c->M, c->vK, vl, c->tb);
+                CKL();
+                trace_solve(c, E, c->tb, zl, c->P.inner_trace_rtol);
+                k_pre_backsub<K><<<nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (NP + NL), c->st>>>(c->M, E.Lbs32, c->wK,
+                                                                                                zl, U, zp);
+                CKL();
+            } else {
+                mixed_solve(c, cc, nullptr, Qbar, nullptr, nullptr, U, zp, zl, vp, vl, c->P.inner_trace_rtol);
+            }
         } catch (...) {
             c->trace_vcycles = 0;
             throw;
@@ -1069,6 +1099,7 @@ struct Impl {
     static int stage_fgmres(hdg_ctx *c, double cc, const double *r, const double *Qsv, double *Q, double *p,
                             double *lam) {
         assemble_stepI(c, Qsv, cc, inv_for(c->P.inner_stepI_rtol));
+        ensure_pre_maps(c, cc);
         CondCache &E = condense(c, cc);
         if (!c->capturing) {
             int hstat = 0;
@@ -1269,7 +1300,7 @@ struct Impl {
         }
         if (!c->g_step) {
             const Tab &T = c->tab;                      // condensations the step uses, built first
-            for (int i = 1; i < T.s; ++i) condense(c, T.Ai[i][i] * dt);
+            for (int i = 1; i < T.s; ++i) ensure_pre_maps(c, T.Ai[i][i] * dt);
             condense(c, dt * T.bi[T.s - 1]);
             condense(c, 1.0);
             c->g_step = capture_graph(c, [&]() { imex_step_body(c, t0); }, &c->step_kernels);
