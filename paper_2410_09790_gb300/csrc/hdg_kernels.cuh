@@ -692,6 +692,50 @@ __global__ void k_cell_apply_mf(EdgeTab<double> E, MeshDev M, const double *__re
     }
 }
 
+// ------------------------------------------------------------------ stage operator, fused
+// The stage operator A(c) applied to x = (Q, p, lambda) in one pass per cell: velocity rows
+// (M - cF)Q - c G(p, lambda) (diagonal block dense, neighbours matrix-free), constraint rows of
+// the cell (p-rows yp, the cell's lambda-row contributions v; summed per facet by k_facet_gather).
+template <int K>
+__global__ void k_stage_apply(RefDev R, EdgeTab<double> E, MeshDev M, const double *__restrict__ Dblk,
+                              const double *__restrict__ wq, double c, double tau, const double *Q,
+                              const double *p, const double *lam, double *yQ, double *yp, double *v) {
+    typedef Dims<K> Dm;
+    constexpr int MU = Dm::MU, NU = Dm::NU, NP = Dm::NP, NT = Dm::NT, NL = Dm::NL, NFQ = Dm::NFQ;
+    constexpr int SCR = 6 * NFQ + NL + 2 * MU;
+    CELL_TEAM(SCR)
+    double *t = mine, *lK = mine + 6 * NFQ, *cs = lK + NL;
+    team_nbr_flux<K, double>(tm, E, M, cell, wq, nullptr, Q, t);
+    gather_trace_local<K>(M, cell, lam, lK, tm);          // (ends with a team sync)
+    const CellGeo g = M.geo[cell];
+    const long long nrows = (long long)M.ncells * NU;
+    const double *QK = Q + (size_t)cell * NU, *pK = p + (size_t)cell * NP;
+    TFOR(x, NU) {
+        const int d = x / MU, a = x % MU;
+        const size_t gi = (size_t)cell * NU + x;
+        double bq = nbr_row<K, double>(E, t, d, a);
+#pragma unroll 6
+        for (int j = 0; j < NU; ++j) bq += __ldg(&Dblk[(size_t)j * nrows + gi]) * QK[j];
+        double et = 0;
+        for (int e = 0; e < 3; ++e) {
+            const double nd = d == 0 ? g.nx[e] : g.ny[e];
+            double s = 0;
+            for (int j = 0; j < NT; ++j) s += ldg(&R.Ehat[(e * NT + j) * MU + a]) * lK[e * NT + j];
+            et += g.h[e] * nd * s;
+        }
+        double dt = 0;
+        for (int rr = 0; rr < 2; ++rr) {
+            double s = 0;
+            for (int b = 0; b < NP; ++b) s += ldg(&R.Dhat[(rr * NP + b) * MU + a]) * pK[b];
+            dt += g.Jinv[rr * 2 + d] * s;
+        }
+        yQ[gi] = bq - c * (g.detJ * dt - et);
+    }
+    int flip[3] = {M.cell_flip[3 * cell], M.cell_flip[3 * cell + 1], M.cell_flip[3 * cell + 2]};
+    cell_constraint<K>(tm, R, g, flip, tau, QK, pK, lK, cs, yp + (size_t)cell * NP, v + (size_t)cell * NL);
+}
+
+
 // ------------------------------------------------------------------ restarted GMRES (right block-Jacobi)
 // Krylov basis V (GM_M+1 vectors of n), Hessenberg column / Givens rotations and the residual
 // estimate live in device memory; the last block of each reduction does the small serial
@@ -702,6 +746,7 @@ struct GmresState {
     double cs[GM_M], sn[GM_M], g[GM_M + 1], y[GM_M], hcol[GM_M + 2], h2[GM_M + 2];
     double bnorm, beta, resid, rtol;
     int j, cycle_end, converged, total, maxit, breakdown, m;   // m: restart length of this cycle
+    int reorth;                      // selective Gram-Schmidt: second pass needed for this step
 };
 
 __global__ void k_gm_set_cycle(GmresState *gs, int m) { gs->m = m; }
@@ -782,11 +827,12 @@ __global__ void k_count_stage(DevCount *acc, const GmresState *fgs) {
 // input).
 template <class T, class Ranges>
 __device__ void block_multidot(const RedBuf rb, const T *V, const T *w, long long n, int nvec, Ranges ranges,
-                               double *out) {
+                               double *out, const T *extra = nullptr) {
     __shared__ int last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (extra) ++nvec;                   // (extra, w) -> out[nvec - 1]
     for (int i = warp; i < nvec; i += nw) {
-        const T *Vi = V + (size_t)i * n;
+        const T *Vi = (extra && i == nvec - 1) ? extra : V + (size_t)i * n;
         T at = 0;
         ranges([&](long long r0, long long r1) {
             for (long long g = r0 + lane; g < r1; g += 32) at += Vi[g] * w[g];
@@ -825,11 +871,14 @@ struct RowChunk {
     }
 };
 
-// out[i] = (V_i, w), i < nvec (rows split in contiguous chunks over the blocks)
+// out[i] = (V_i, w), i < nvec (rows split in contiguous chunks over the blocks); with_norm:
+// also out[nvec] = (w, w)
 template <class T>
-__device__ void multidot_rows(const RedBuf rb, const T *V, const T *w, long long n, int nvec, double *out) {
+__device__ void multidot_rows(const RedBuf rb, const T *V, const T *w, long long n, int nvec, double *out,
+                              bool with_norm = false) {
     const RowChunk ch(n);
-    block_multidot(rb, V, w, n, nvec, [&](auto f) { if (ch.r0 < ch.r1) f(ch.r0, ch.r1); }, out);
+    block_multidot(rb, V, w, n, nvec, [&](auto f) { if (ch.r0 < ch.r1) f(ch.r0, ch.r1); }, out,
+                   with_norm ? w : nullptr);
 }
 
 // the same over the rows of the cell groups a team-per-cell kernel assigns to this block (groups
@@ -971,12 +1020,44 @@ __global__ void k_gm_orth1(T *w, const T *__restrict__ V, long long nrows, RedBu
     block_multidot(rb, V, (const T *)w, nrows, nvec, [&](auto f) { if (ch.r0 < ch.r1) f(ch.r0, ch.r1); }, gs->h2);
 }
 
+// Last block of an Arnoldi step: Hessenberg column (hcol, plus h2 after a second pass), norm
+// hn = ||w||, Givens rotations, residual estimate, step bookkeeping.
+__device__ void gm_finish_step(GmresState *gs, int j, double hn, bool with_h2) {
+    double *Hc = gs->H + j * (GM_M + 1);
+    for (int i = 0; i <= j; ++i) Hc[i] = with_h2 ? gs->hcol[i] + gs->h2[i] : gs->hcol[i];
+    Hc[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {                     // previous rotations
+        double a = Hc[i], b2 = Hc[i + 1];
+        Hc[i] = gs->cs[i] * a + gs->sn[i] * b2;
+        Hc[i + 1] = -gs->sn[i] * a + gs->cs[i] * b2;
+    }
+    double a = Hc[j], b2 = Hc[j + 1];
+    double r = sqrt(a * a + b2 * b2);
+    double c_ = r > 0 ? a / r : 1.0, s_ = r > 0 ? b2 / r : 0.0;
+    gs->cs[j] = c_; gs->sn[j] = s_;
+    Hc[j] = r;
+    Hc[j + 1] = 0.0;
+    gs->g[j + 1] = -s_ * gs->g[j];
+    gs->g[j] = c_ * gs->g[j];
+    gs->resid = fabs(gs->g[j + 1]);
+    gs->total += 1;
+    // keep H[j+1, j] (the norm) for the next v
+    gs->H[j * (GM_M + 1) + j + 1] = hn;            // restored after the rotation (used by k_gm_precond_mf)
+    gs->hcol[GM_M + 1] = hn;
+    gs->j = j + 1;
+    gs->reorth = 0;
+    if (!isfinite(gs->resid)) { gs->breakdown = 2; gs->cycle_end = 1; }
+    else if (gs->resid <= gs->rtol * gs->bnorm) { gs->converged = 1; gs->cycle_end = 1; }
+    else if (gs->j >= gs->m || gs->total >= gs->maxit || hn == 0.0) gs->cycle_end = 1;
+}
+
 // w -= V h2; ||w|| -> H[j+1, j]; Givens rotations; residual estimate. CGS1: single classical
 // Gram-Schmidt pass (w -= V hcol straight after the first dots; no orth1), used by the FP32 inner
-// solves whose loose tolerance does not need the second pass.
-template <class T, bool CGS1 = false>
+// solves whose loose tolerance does not need the second pass. SECOND: only when the selective
+// test of k_gm_orth_sel asked for a second pass.
+template <class T, bool CGS1 = false, bool SECOND = false>
 __global__ void k_gm_orth2(T *w, const T *__restrict__ V, long long nrows, RedBuf rb, GmresState *gs) {
-    if (gs->cycle_end) return;
+    if (gs->cycle_end || (SECOND && !gs->reorth)) return;
     const int j = gs->j, nvec = j + 1;
     __shared__ double h[GM_M + 1];
     if ((int)threadIdx.x < nvec) h[threadIdx.x] = CGS1 ? gs->hcol[threadIdx.x] : gs->h2[threadIdx.x];
@@ -990,34 +1071,41 @@ __global__ void k_gm_orth2(T *w, const T *__restrict__ V, long long nrows, RedBu
         vt += s * s;
     }
     v[0] = (double)vt;
-    if (grid_sum<1>(rb, v, tot)) {
-        double *Hc = gs->H + j * (GM_M + 1);
-        for (int i = 0; i <= j; ++i) Hc[i] = CGS1 ? gs->hcol[i] : gs->hcol[i] + gs->h2[i];
-        double hn = sqrt(tot[0]);
-        Hc[j + 1] = hn;
-        for (int i = 0; i < j; ++i) {                     // previous rotations
-            double a = Hc[i], b2 = Hc[i + 1];
-            Hc[i] = gs->cs[i] * a + gs->sn[i] * b2;
-            Hc[i + 1] = -gs->sn[i] * a + gs->cs[i] * b2;
-        }
-        double a = Hc[j], b2 = Hc[j + 1];
-        double r = sqrt(a * a + b2 * b2);
-        double c_ = r > 0 ? a / r : 1.0, s_ = r > 0 ? b2 / r : 0.0;
-        gs->cs[j] = c_; gs->sn[j] = s_;
-        Hc[j] = r;
-        Hc[j + 1] = 0.0;
-        gs->g[j + 1] = -s_ * gs->g[j];
-        gs->g[j] = c_ * gs->g[j];
-        gs->resid = fabs(gs->g[j + 1]);
-        gs->total += 1;
-        // keep H[j+1, j] (the norm) for the next v; stored separately in hcol[GM_M+1]
-        gs->H[j * (GM_M + 1) + j + 1] = hn;            // restored after the rotation (used by k_gm_precond_mf)
-        gs->hcol[GM_M + 1] = hn;
-        gs->j = j + 1;
-        if (!isfinite(gs->resid)) { gs->breakdown = 2; gs->cycle_end = 1; }
-        else if (gs->resid <= gs->rtol * gs->bnorm) { gs->converged = 1; gs->cycle_end = 1; }
-        else if (gs->j >= gs->m || gs->total >= gs->maxit || hn == 0.0) gs->cycle_end = 1;
+    if (grid_sum<1>(rb, v, tot)) gm_finish_step(gs, j, sqrt(tot[0]), !CGS1);
+}
+
+// Selective classical Gram-Schmidt (flexible GMRES on the stage system): k_vec_dot gave
+// hcol = V^T w and hcol[j+1] = ||w||^2; subtract, and accept the step when the norm kept at
+// least 1/sqrt(2) of its length (no cancellation); otherwise flag a second pass
+// (k_gm_orth_dots, then k_gm_orth2<T, false, true>).
+template <class T>
+__global__ void k_gm_orth_sel(T *w, const T *__restrict__ V, long long nrows, RedBuf rb, GmresState *gs) {
+    if (gs->cycle_end) return;
+    const int j = gs->j, nvec = j + 1;
+    __shared__ double h[GM_M + 1];
+    if ((int)threadIdx.x < nvec) h[threadIdx.x] = gs->hcol[threadIdx.x];
+    __syncthreads();
+    double v[1] = {0.0}, tot[1];
+    T vt = 0;
+    GRID_STRIDE(g, nrows) {
+        T s = w[g];
+        for (int i = 0; i < nvec; ++i) s -= (T)h[i] * V[(size_t)i * nrows + g];
+        w[g] = s;
+        vt += s * s;
     }
+    v[0] = (double)vt;
+    if (grid_sum<1>(rb, v, tot)) {
+        if (tot[0] >= 0.5 * gs->hcol[nvec] || !isfinite(tot[0])) gm_finish_step(gs, j, sqrt(tot[0]), false);
+        else gs->reorth = 1;
+    }
+}
+
+// second pass of the selective scheme: h2 = V^T w
+template <class T>
+__global__ void k_gm_orth_dots(const T *__restrict__ w, const T *__restrict__ V, long long n, RedBuf rb,
+                               GmresState *gs) {
+    if (gs->cycle_end || !gs->reorth) return;
+    multidot_rows(rb, V, w, n, gs->j + 1, gs->h2);
 }
 
 // y = R^{-1} g (upper triangular part of the rotated H, without the subdiagonal)
@@ -1158,9 +1246,9 @@ __global__ void k_vec_normalize(const double *__restrict__ w0, const double *__r
 
 // hcol = V^T w over V_0..V_j
 __global__ void k_vec_dot(const double *__restrict__ w, const double *__restrict__ V, long long n, RedBuf rb,
-                          GmresState *gs) {
+                          GmresState *gs, int with_norm) {
     if (gs->cycle_end) return;
-    multidot_rows(rb, V, w, n, gs->j + 1, gs->hcol);
+    multidot_rows(rb, V, w, n, gs->j + 1, gs->hcol, with_norm != 0);
 }
 
 // x += u

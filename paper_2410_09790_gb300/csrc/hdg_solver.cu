@@ -979,15 +979,13 @@ struct Impl {
     }
 
     // Stage operator y = A(c) x, x = (Q | p | lam) contiguous:
-    //   yQ = (M - cF) Q - c G (p, lam),  (yp | ylam) = B Q + C (p, lam)   (Step-I blocks assembled)
+    //   yQ = (M - cF) Q - c G (p, lam),  (yp | ylam) = B Q + C (p, lam)   (one fused cell pass)
     static void stage_apply(hdg_ctx *c, double cc, const double *x, double *y) {
         const double *Q = x, *p = x + c->nQ, *lam = x + c->nQ + c->nPv;
         double *yQ = y, *yp = y + c->nQ, *yl = y + c->nQ + c->nPv;
         unsigned nb = cell_blocks(c);
-        cell_apply(c, Q, c->q[6]);
-        k_rich_residual<K><<<nb, 128, sizeof(double) * TEAMS_PER_BLOCK * NL, c->st>>>(c->R, c->M, cc, nullptr, c->q[6], p, lam, yQ, -1.0);
-        CKL();
-        k_constraint<K><<<nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (NL + 2 * MU), c->st>>>(c->R, c->M, c->P.tau, Q, p, lam, yp, c->vK);
+        k_stage_apply<K><<<nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (6 * Dm::NFQ + NL + 2 * MU), c->st>>>(
+            c->R, EdgeTab<double>{c->R.ephi, c->pen}, c->M, c->Dblk, c->wq, cc, c->P.tau, Q, p, lam, yQ, yp, c->vK);
         CKL();
         k_facet_gather<NT><<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(c->M, c->vK, nullptr, yl);
         CKL();
@@ -1027,6 +1025,17 @@ struct Impl {
         CKL();
     }
 
+    // Orthogonalise w against the stage FGMRES basis: selective classical Gram-Schmidt (one pass
+    // unless the first pass cancels more than 1 - 1/sqrt(2) of w's norm, then a second pass).
+    static void fgmres_orth(hdg_ctx *c, double *w, long long N, GmresState *fgs) {
+        const int go = grid_orth(N);
+        k_vec_dot<<<go, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs, 1);
+        k_gm_orth_sel<double><<<go, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
+        k_gm_orth_dots<double><<<go, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
+        k_gm_orth2<double, false, true><<<go, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
+        CKL();
+    }
+
     // The flexible GMRES of a stage solve recorded into the current graph capture (x = c->fx,
     // b = c->fb): restart cycles, Arnoldi steps, and the inner Step-I GMRES and trace CG are
     // device-side while loops (conditional graph nodes), so a stage solve needs no host round trip.
@@ -1058,9 +1067,7 @@ struct Impl {
                         chorin_precond(c, cc, c->fv, c->fz);
                         k_slot_store<<<g, VEC_THREADS, 0, c->st>>>(c->fz, c->fZ, N, fgs);
                         stage_apply(c, cc, c->fz, w);
-                        k_vec_dot<<<grid_orth(N), VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
-                        k_gm_orth1<<<grid_orth(N), VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
-                        k_gm_orth2<<<grid_orth(N), VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
+                        fgmres_orth(c, w, N, fgs);
                         k_loop_ctl<<<1, 1, 0, c->st>>>(L2, GM_M + 1, &fgs->cycle_end);
                         CKL();
                     });
@@ -1154,9 +1161,7 @@ struct Impl {
                 double *Vj = c->fV + (size_t)j * N, *Zj = c->fZ + (size_t)j * N;
                 chorin_precond(c, cc, Vj, Zj);
                 stage_apply(c, cc, Zj, w);
-                k_vec_dot<<<grid_orth(N), VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), c->fgs);
-                k_gm_orth1<<<grid_orth(N), VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), c->fgs);
-                k_gm_orth2<<<grid_orth(N), VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), c->fgs);
+                fgmres_orth(c, w, N, c->fgs);
                 CKL();
                 CK(cudaMemcpyAsync(c->hfgs, c->fgs, sizeof(GmresState), cudaMemcpyDeviceToHost, c->st));
                 CK(cudaStreamSynchronize(c->st));
