@@ -746,7 +746,6 @@ struct GmresState {
     double cs[GM_M], sn[GM_M], g[GM_M + 1], y[GM_M], hcol[GM_M + 2], h2[GM_M + 2];
     double bnorm, beta, resid, rtol;
     int j, cycle_end, converged, total, maxit, breakdown, m;   // m: restart length of this cycle
-    int reorth;                      // selective Gram-Schmidt: second pass needed for this step
 };
 
 __global__ void k_gm_set_cycle(GmresState *gs, int m) { gs->m = m; }
@@ -1045,7 +1044,6 @@ __device__ void gm_finish_step(GmresState *gs, int j, double hn, bool with_h2) {
     gs->H[j * (GM_M + 1) + j + 1] = hn;            // restored after the rotation (used by k_gm_precond_mf)
     gs->hcol[GM_M + 1] = hn;
     gs->j = j + 1;
-    gs->reorth = 0;
     if (!isfinite(gs->resid)) { gs->breakdown = 2; gs->cycle_end = 1; }
     else if (gs->resid <= gs->rtol * gs->bnorm) { gs->converged = 1; gs->cycle_end = 1; }
     else if (gs->j >= gs->m || gs->total >= gs->maxit || hn == 0.0) gs->cycle_end = 1;
@@ -1053,11 +1051,10 @@ __device__ void gm_finish_step(GmresState *gs, int j, double hn, bool with_h2) {
 
 // w -= V h2; ||w|| -> H[j+1, j]; Givens rotations; residual estimate. CGS1: single classical
 // Gram-Schmidt pass (w -= V hcol straight after the first dots; no orth1), used by the FP32 inner
-// solves whose loose tolerance does not need the second pass. SECOND: only when the selective
-// test of k_gm_orth_sel asked for a second pass.
-template <class T, bool CGS1 = false, bool SECOND = false>
+// solves whose loose tolerance does not need the second pass.
+template <class T, bool CGS1 = false>
 __global__ void k_gm_orth2(T *w, const T *__restrict__ V, long long nrows, RedBuf rb, GmresState *gs) {
-    if (gs->cycle_end || (SECOND && !gs->reorth)) return;
+    if (gs->cycle_end) return;
     const int j = gs->j, nvec = j + 1;
     __shared__ double h[GM_M + 1];
     if ((int)threadIdx.x < nvec) h[threadIdx.x] = CGS1 ? gs->hcol[threadIdx.x] : gs->h2[threadIdx.x];
@@ -1072,40 +1069,6 @@ __global__ void k_gm_orth2(T *w, const T *__restrict__ V, long long nrows, RedBu
     }
     v[0] = (double)vt;
     if (grid_sum<1>(rb, v, tot)) gm_finish_step(gs, j, sqrt(tot[0]), !CGS1);
-}
-
-// Selective classical Gram-Schmidt (flexible GMRES on the stage system): k_vec_dot gave
-// hcol = V^T w and hcol[j+1] = ||w||^2; subtract, and accept the step when the norm kept at
-// least 1/sqrt(2) of its length (no cancellation); otherwise flag a second pass
-// (k_gm_orth_dots, then k_gm_orth2<T, false, true>).
-template <class T>
-__global__ void k_gm_orth_sel(T *w, const T *__restrict__ V, long long nrows, RedBuf rb, GmresState *gs) {
-    if (gs->cycle_end) return;
-    const int j = gs->j, nvec = j + 1;
-    __shared__ double h[GM_M + 1];
-    if ((int)threadIdx.x < nvec) h[threadIdx.x] = gs->hcol[threadIdx.x];
-    __syncthreads();
-    double v[1] = {0.0}, tot[1];
-    T vt = 0;
-    GRID_STRIDE(g, nrows) {
-        T s = w[g];
-        for (int i = 0; i < nvec; ++i) s -= (T)h[i] * V[(size_t)i * nrows + g];
-        w[g] = s;
-        vt += s * s;
-    }
-    v[0] = (double)vt;
-    if (grid_sum<1>(rb, v, tot)) {
-        if (tot[0] >= 0.5 * gs->hcol[nvec] || !isfinite(tot[0])) gm_finish_step(gs, j, sqrt(tot[0]), false);
-        else gs->reorth = 1;
-    }
-}
-
-// second pass of the selective scheme: h2 = V^T w
-template <class T>
-__global__ void k_gm_orth_dots(const T *__restrict__ w, const T *__restrict__ V, long long n, RedBuf rb,
-                               GmresState *gs) {
-    if (gs->cycle_end || !gs->reorth) return;
-    multidot_rows(rb, V, w, n, gs->j + 1, gs->h2);
 }
 
 // y = R^{-1} g (upper triangular part of the rotated H, without the subdiagonal)

@@ -1025,14 +1025,13 @@ struct Impl {
         CKL();
     }
 
-    // Orthogonalise w against the stage FGMRES basis: selective classical Gram-Schmidt (one pass
-    // unless the first pass cancels more than 1 - 1/sqrt(2) of w's norm, then a second pass).
+    // Orthogonalise w against the stage FGMRES basis: classical Gram-Schmidt, two passes (a
+    // selective second pass was tried: the first pass cancels most of w at every step here).
     static void fgmres_orth(hdg_ctx *c, double *w, long long N, GmresState *fgs) {
         const int go = grid_orth(N);
-        k_vec_dot<<<go, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs, 1);
-        k_gm_orth_sel<double><<<go, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
-        k_gm_orth_dots<double><<<go, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
-        k_gm_orth2<double, false, true><<<go, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
+        k_vec_dot<<<go, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs, 0);
+        k_gm_orth1<double><<<go, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
+        k_gm_orth2<double><<<go, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
         CKL();
     }
 
