@@ -1263,21 +1263,15 @@ struct Impl {
             k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, L, c->rs[i], c->ncells);
             CKL();
             bdm(c, c->Qs[i - 1], c->q[5]);                                       // Q*_{i-1}
-            if (c->P.n_richardson > 0) {     // Alg. 2 as printed: a fixed n_R from the previous stage
-                CK(cudaMemcpyAsync(c->Qs[i], c->Qs[i - 1], bq, cudaMemcpyDeviceToDevice, c->st));
-                CK(cudaMemcpyAsync(c->ps[i], c->ps[i - 1], sizeof(double) * c->nPv, cudaMemcpyDeviceToDevice, c->st));
-                CK(cudaMemcpyAsync(c->ls[i], c->ls[i - 1], sizeof(double) * c->nL, cudaMemcpyDeviceToDevice, c->st));
-            } else {
-                // solved to a tolerance: start from the previous stage plus the previous step's
-                // increment between these two stages (the previous stage alone after a new state)
-                k_extrapolate<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->Qs[i], c->Qs[i - 1], c->QP[i],
-                                                                         c->QP[i - 1], c->nQ, c->dprev);
-                k_extrapolate<<<grid_for(c->nPv), VEC_THREADS, 0, c->st>>>(c->ps[i], c->ps[i - 1], c->PP[i],
-                                                                          c->PP[i - 1], c->nPv, c->dprev);
-                k_extrapolate<<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(c->ls[i], c->ls[i - 1], c->LP[i],
-                                                                         c->LP[i - 1], c->nL, c->dprev);
-                CKL();
-            }
+            // initial guess: the previous stage plus the previous step's increment between
+            // these two stages (the previous stage alone after a change of state)
+            k_extrapolate<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->Qs[i], c->Qs[i - 1], c->QP[i], c->QP[i - 1],
+                                                                     c->nQ, c->dprev);
+            k_extrapolate<<<grid_for(c->nPv), VEC_THREADS, 0, c->st>>>(c->ps[i], c->ps[i - 1], c->PP[i], c->PP[i - 1],
+                                                                      c->nPv, c->dprev);
+            k_extrapolate<<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(c->ls[i], c->ls[i - 1], c->LP[i], c->LP[i - 1],
+                                                                     c->nL, c->dprev);
+            CKL();
             nc |= stage_solve(c, T.Ai[i][i] * dt, c->rs[i], c->q[5], c->Qs[i], c->ps[i], c->ls[i]);
         }
         // eq. final_residual and eq. final_update (coefficient b_{s-1}^im dt)
