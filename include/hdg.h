@@ -168,10 +168,7 @@ hdg_status hdg_get_state(hdg_ctx *ctx, double *Q, double *p, double *lam, double
 hdg_status hdg_set_forcing(hdg_ctx *ctx, const double *F, double (*phi)(double t, void *user), void *user);
 
 /* Alg. 1 x nsteps: s-1 stage solves (Alg. 2), final update (eq. final_update) and pressure
- * reconstruction (Sec. 2.7) per step, on the context's state. A stage solve starts from the
- * previous stage's solution plus the previous step's increment between the two stages (from the
- * previous stage alone on the first step after hdg_div_free_project or after setup); the start
- * changes the iteration count, not the tolerance the solve meets. */
+ * reconstruction (Sec. 2.7) per step, on the context's state. */
 hdg_status hdg_imex_step(hdg_ctx *ctx, int nsteps, hdg_stats *stats);
 
 /* One stage solve (Alg. 2): find (Q, p, lambda) with

@@ -1214,16 +1214,6 @@ __global__ void k_vec_dot(const double *__restrict__ w, const double *__restrict
     multidot_rows(rb, V, w, n, gs->j + 1, gs->hcol, with_norm != 0);
 }
 
-// initial guess of a stage: out = base + (a - b) when *valid, else base (a, b: the previous
-// step's solutions of this stage and of the stage before it)
-__global__ void k_extrapolate(double *out, const double *__restrict__ base, const double *__restrict__ a,
-                              const double *__restrict__ b, long long n, const int *valid) {
-    const bool use = *valid != 0;
-    GRID_STRIDE(i, n) out[i] = use ? base[i] + (a[i] - b[i]) : base[i];
-}
-
-__global__ void k_set_int(int *flag, int v) { *flag = v; }
-
 // x += u
 __global__ void k_vec_add(const double *__restrict__ u, double *x, long long n) {
     GRID_STRIDE(i, n) x[i] += u[i];

@@ -142,9 +142,6 @@ struct hdg_ctx {
     double t = 0.0;
     // IMEX stages
     std::vector<double *> Qs, rs, ps, ls;
-    // the previous step's Q^{n-1} (index 0) and stage solutions, for the stages' initial guesses
-    std::vector<double *> QP, PP, LP;
-    int *dprev = nullptr;                                    // device flag: QP.. hold a previous step
     // forcing
     double *Fload = nullptr;
     bool has_forcing = false;
@@ -1263,15 +1260,9 @@ struct Impl {
             k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, L, c->rs[i], c->ncells);
             CKL();
             bdm(c, c->Qs[i - 1], c->q[5]);                                       // Q*_{i-1}
-            // initial guess: the previous stage plus the previous step's increment between
-            // these two stages (the previous stage alone after a change of state)
-            k_extrapolate<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->Qs[i], c->Qs[i - 1], c->QP[i], c->QP[i - 1],
-                                                                     c->nQ, c->dprev);
-            k_extrapolate<<<grid_for(c->nPv), VEC_THREADS, 0, c->st>>>(c->ps[i], c->ps[i - 1], c->PP[i], c->PP[i - 1],
-                                                                      c->nPv, c->dprev);
-            k_extrapolate<<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(c->ls[i], c->ls[i - 1], c->LP[i], c->LP[i - 1],
-                                                                     c->nL, c->dprev);
-            CKL();
+            CK(cudaMemcpyAsync(c->Qs[i], c->Qs[i - 1], bq, cudaMemcpyDeviceToDevice, c->st));
+            CK(cudaMemcpyAsync(c->ps[i], c->ps[i - 1], sizeof(double) * c->nPv, cudaMemcpyDeviceToDevice, c->st));
+            CK(cudaMemcpyAsync(c->ls[i], c->ls[i - 1], sizeof(double) * c->nL, cudaMemcpyDeviceToDevice, c->st));
             nc |= stage_solve(c, T.Ai[i][i] * dt, c->rs[i], c->q[5], c->Qs[i], c->ps[i], c->ls[i]);
         }
         // eq. final_residual and eq. final_update (coefficient b_{s-1}^im dt)
@@ -1295,13 +1286,6 @@ struct Impl {
         CKL();
         mixed_solve(c, dt * T.bi[s - 1], rn, nullptr, nullptr, nullptr, c->Q, c->pp[1], c->ll[1]);
         reconstruct(c, c->Q, t0 + dt, c->p, c->lam);                            // Sec. 2.7
-        for (int i = 0; i < s; ++i) {                                           // for the next step
-            CK(cudaMemcpyAsync(c->QP[i], c->Qs[i], bq, cudaMemcpyDeviceToDevice, c->st));
-            CK(cudaMemcpyAsync(c->PP[i], c->ps[i], sizeof(double) * c->nPv, cudaMemcpyDeviceToDevice, c->st));
-            CK(cudaMemcpyAsync(c->LP[i], c->ls[i], sizeof(double) * c->nL, cudaMemcpyDeviceToDevice, c->st));
-        }
-        k_set_int<<<1, 1, 0, c->st>>>(c->dprev, 1);
-        CKL();
         return nc;
     }
 
@@ -1548,11 +1532,7 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         for (int i = 0; i < c->tab.s; ++i) {
             c->Qs.push_back(c->alloc<double>(nQ)); c->rs.push_back(c->alloc<double>(nQ));
             c->ps.push_back(c->alloc<double>(nP)); c->ls.push_back(c->alloc<double>(nL));
-            c->QP.push_back(c->alloc<double>(nQ)); c->PP.push_back(c->alloc<double>(nP));
-            c->LP.push_back(c->alloc<double>(nL));
         }
-        c->dprev = c->alloc<int>(1);
-        CK(cudaMemset(c->dprev, 0, sizeof(int)));
         c->Fload = c->alloc<double>(nQ);
         const int nfq = (3 * c->K + 5) / 2;                      // facet points (Dims<K>::NFQ)
         c->Dblk = c->alloc<double>((size_t)c->NU * nQ);
@@ -1874,7 +1854,6 @@ hdg_status hdg_div_free_project(hdg_ctx *c, hdg_stats *stats) {
             LinComb L{};
             L.nterms = 2; L.coef[0] = 1; L.vec[0] = c->Q; L.coef[1] = 1; L.vec[1] = c->q[0];
             k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, I::NU, L, c->Q, c->ncells);
-            k_set_int<<<1, 1, 0, c->st>>>(c->dprev, 0);      // a new initial field: no previous step
             CKL();
             I::reconstruct(c, c->Q, c->t, c->p, c->lam);
         });
