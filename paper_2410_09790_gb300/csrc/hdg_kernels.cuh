@@ -22,6 +22,12 @@
 
 namespace hdg {
 
+// Every kernel here is launched with programmatic dependent launch (launch_k in hdg_solver.cu):
+// its blocks may be scheduled while the previous kernel on the stream finishes, so that the launch
+// overlaps that kernel's tail. Each kernel first waits until the previous kernel has completed
+// and its writes are visible; only then does it touch memory.
+__device__ __forceinline__ void wait_prior_kernel() { cudaGridDependencySynchronize(); }
+
 constexpr int VEC_THREADS = 256;
 constexpr int MAX_RED_BLOCKS = 2048;
 
@@ -104,6 +110,7 @@ inline int red_grid(long long n) {
 // out[item][blk][a] = sum_n T[a][n] in[item][blk][n]  (T is n x n)
 __global__ void k_basis_change(const double *__restrict__ T, int n, const double *__restrict__ in,
                                double *__restrict__ out, long long nvec) {
+    wait_prior_kernel();
     GRID_STRIDE(i, nvec * n) {
         long long v = i / n;
         int a = (int)(i % n);
@@ -116,6 +123,7 @@ __global__ void k_basis_change(const double *__restrict__ T, int n, const double
 // dual <-> Riesz on V_Q: M = detJ I per cell. mode 0: out = detJ * in; mode 1: out = in / detJ.
 __global__ void k_mass_scale(const CellGeo *__restrict__ geo, int nu, const double *in, double *out,
                              long long ncells, int mode) {
+    wait_prior_kernel();
     GRID_STRIDE(i, ncells * nu) {
         double dj = geo[i / nu].detJ;
         out[i] = mode == 0 ? in[i] * dj : in[i] / dj;
@@ -126,6 +134,7 @@ __global__ void k_mass_scale(const CellGeo *__restrict__ geo, int nu, const doub
 __global__ void k_trace_riesz(const CellGeo *__restrict__ geo, const int *__restrict__ facet_cell,
                               const int *__restrict__ facet_edge, int nt, const double *in,
                               double *out, long long nfacets) {
+    wait_prior_kernel();
     GRID_STRIDE(i, nfacets * nt) {
         long long f = i / nt;
         int c = facet_cell[2 * f], e = facet_edge[2 * f];
@@ -142,6 +151,7 @@ struct LinComb {
     int mass[12];
 };
 __global__ void k_lincomb(const CellGeo *__restrict__ geo, int nu, LinComb L, double *out, long long ncells) {
+    wait_prior_kernel();
     GRID_STRIDE(i, ncells * nu) {
         double dj = geo[i / nu].detJ;
         double s = 0;
@@ -151,6 +161,7 @@ __global__ void k_lincomb(const CellGeo *__restrict__ geo, int nu, LinComb L, do
 }
 
 __global__ void k_axpby(double a, const double *x, double b, double *y, long long n) {
+    wait_prior_kernel();
     GRID_STRIDE(i, n) y[i] = a * x[i] + b * y[i];
 }
 
@@ -158,6 +169,7 @@ __global__ void k_axpby(double a, const double *x, double b, double *y, long lon
 template <int K>
 __global__ void k_condense(RefDev R, MeshDev M, double c, double tau, double *Scell, double *Zc,
                            double *Ac) {
+    wait_prior_kernel();
     typedef Dims<K> Dm;
     extern __shared__ double sm[];
     const int cell = blockIdx.x;
@@ -173,6 +185,7 @@ __global__ void k_condense(RefDev R, MeshDev M, double c, double tau, double *Sc
 template <int NT>
 __global__ void k_assemble_trace(MeshDev M, const double *__restrict__ Scell, double *Sell,
                                  int *tcol, double *Dinv) {
+    wait_prior_kernel();
     const int NL = 3 * NT;
     GRID_STRIDE(fl, M.nfacets) {
         int f = (int)fl;
@@ -225,6 +238,7 @@ __global__ void k_assemble_trace(MeshDev M, const double *__restrict__ Scell, do
 template <int NT>
 __global__ void k_trace_apply(const double *__restrict__ Sell, const int *__restrict__ tcol,
                               const double *__restrict__ x, double *__restrict__ y, int nfacets) {
+    wait_prior_kernel();
     long long nrows = (long long)nfacets * NT;
     GRID_STRIDE(g, nrows) {
         int f = (int)(g / NT);
@@ -244,6 +258,7 @@ __global__ void k_trace_apply(const double *__restrict__ Sell, const int *__rest
 // b -> sum of b_F[0] (constant-mode content), for the null-space projection
 template <int NT>
 __global__ void k_trace_mean(const double *__restrict__ b, int nfacets, RedBuf rb, Scalars *sc) {
+    wait_prior_kernel();
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(f, nfacets) v[0] += b[(size_t)f * NT];
     if (grid_sum<1>(rb, v, tot)) sc->bmean = tot[0] / nfacets;
@@ -254,6 +269,7 @@ template <int NT>
 __global__ void k_cg_setup(const double *__restrict__ b, const double *__restrict__ Dinv, double *x,
                            double *r, double *z, double *pold, int nfacets, RedBuf rb, Scalars *sc,
                            double rtol, int maxit) {
+    wait_prior_kernel();
     long long nrows = (long long)nfacets * NT;
     const double mean = sc->bmean;
     double v[3] = {0.0, 0.0, 0.0}, tot[3];
@@ -297,6 +313,7 @@ __global__ void k_cg_apply(const double *__restrict__ Sell, const int *__restric
                            const double *__restrict__ z, const double *__restrict__ pold,
                            double *__restrict__ pnew, double *__restrict__ Ap, int nfacets,
                            RedBuf rb, Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     const double beta = sc->beta, zm = sc->zmean;
     long long nrows = (long long)nfacets * NT;
@@ -331,6 +348,7 @@ template <int NT>
 __global__ void k_cg_update(const double *__restrict__ Dinv, const double *__restrict__ p,
                             const double *__restrict__ Ap, double *x, double *r, double *z,
                             int nfacets, RedBuf rb, Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     const double alpha = sc->alpha;
     long long nrows = (long long)nfacets * NT;
@@ -393,6 +411,7 @@ template <int K>
 __global__ void k_mixed_rhs(RefDev R, MeshDev M, double tau, const double *Ru, const double *X,
                             const double *p, const double *lam, const double *Rp_add,
                             const double *__restrict__ Zc, double *v, double *w) {
+    wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int SCR = Dm::NL + 4 * Dm::MU + Dm::NP + Dm::NL;
     CELL_TEAM(SCR)
@@ -410,6 +429,7 @@ __global__ void k_mixed_rhs(RefDev R, MeshDev M, double tau, const double *Ru, c
 // b_F = sum over the facet's cells of v_K (canonical rows of the facet's local edge) - sub_F
 template <int NT>
 __global__ void k_facet_gather(MeshDev M, const double *__restrict__ v, const double *sub, double *b) {
+    wait_prior_kernel();
     GRID_STRIDE(g, (long long)M.nfacets * NT) {
         int f = (int)(g / NT), j = (int)(g % NT);
         double s = sub ? -sub[g] : 0.0;
@@ -432,6 +452,7 @@ __global__ void k_facet_gather(MeshDev M, const double *__restrict__ v, const do
 template <int K>
 __global__ void k_build_pre_maps(RefDev R, MeshDev M, double c, double tau, const double *__restrict__ Zc,
                                  const double *__restrict__ Ac, float *Lrhs, float *Lbs) {
+    wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int NU = Dm::NU, NP = Dm::NP, NL = Dm::NL, MU = Dm::MU;
     constexpr int SCR = NU + NP + NL + NP + (NL + 4 * MU + NP + NL) + NU + NP + (NL + NP);
@@ -465,6 +486,7 @@ __global__ void k_build_pre_maps(RefDev R, MeshDev M, double c, double tau, cons
 template <int K>
 __global__ void k_pre_rhs(MeshDev M, const float *__restrict__ Lrhs, const double *__restrict__ X,
                           const double *__restrict__ Rp_add, double *v, double *w) {
+    wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int NU = Dm::NU, NP = Dm::NP, NL = Dm::NL, RR = NL + NP;
     constexpr int SCR = NU + NP;
@@ -484,6 +506,7 @@ __global__ void k_pre_rhs(MeshDev M, const float *__restrict__ Lrhs, const doubl
 template <int K>
 __global__ void k_pre_backsub(MeshDev M, const float *__restrict__ Lbs, const double *__restrict__ w,
                               const double *__restrict__ lam, double *U, double *p) {
+    wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int NU = Dm::NU, NP = Dm::NP, NL = Dm::NL, NT = Dm::NT, RB = NU + NP;
     constexpr int SCR = NP + NL;
@@ -512,6 +535,7 @@ __global__ void k_mixed_backsub(RefDev R, MeshDev M, double c, const double *Ru,
                                 const double *__restrict__ w, const double *lam,
                                 const double *__restrict__ Zc, const double *__restrict__ Ac,
                                 double *U, double *p) {
+    wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int SCR = Dm::NL + Dm::NP;
     CELL_TEAM(SCR)
@@ -527,6 +551,7 @@ __global__ void k_mixed_backsub(RefDev R, MeshDev M, double c, const double *Ru,
 // ------------------------------------------------------------------ BDM projection (warp / cell)
 template <int K>
 __global__ void k_bdm(RefDev R, MeshDev M, const double *Q, double *Qs) {
+    wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int SCR = 2 * Dm::NU;
     CELL_TEAM(SCR)
@@ -555,6 +580,7 @@ template <int K>
 __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c, double alpha,
                                  double dup, double *Dblk, double *wq, float *wq32, double *pen, float *pen32,
                                  double *Binv, float *Binv32, int *status) {
+    wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int NU = Dm::NU, NFQ = Dm::NFQ;
     extern __shared__ double sm[];
@@ -674,6 +700,7 @@ __device__ __forceinline__ T nbr_row(const EdgeTab<T> &E, const T *t, int d, int
 template <int K>
 __global__ void k_cell_apply_mf(EdgeTab<double> E, MeshDev M, const double *__restrict__ Dblk,
                                 const double *__restrict__ wq, const double *__restrict__ x, double *__restrict__ y) {
+    wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU;
     constexpr int SCR = 6 * Dm::NFQ;
@@ -700,6 +727,7 @@ template <int K>
 __global__ void k_stage_apply(RefDev R, EdgeTab<double> E, MeshDev M, const double *__restrict__ Dblk,
                               const double *__restrict__ wq, double c, double tau, const double *Q,
                               const double *p, const double *lam, double *yQ, double *yp, double *v) {
+    wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NP = Dm::NP, NT = Dm::NT, NL = Dm::NL, NFQ = Dm::NFQ;
     constexpr int SCR = 6 * NFQ + NL + 2 * MU;
@@ -748,7 +776,8 @@ struct GmresState {
     int j, cycle_end, converged, total, maxit, breakdown, m;   // m: restart length of this cycle
 };
 
-__global__ void k_gm_set_cycle(GmresState *gs, int m) { gs->m = m; }
+__global__ void k_gm_set_cycle(GmresState *gs, int m) {
+    wait_prior_kernel(); gs->m = m; }
 
 // ------------------------------------------------------------------ device-side loops
 // Control of a while loop that runs as a CUDA graph conditional node: one thread sets the
@@ -763,11 +792,13 @@ struct LoopCtl {
 };
 
 __global__ void k_loop_init(LoopCtl L, const int *stop) {
+    wait_prior_kernel();
     *L.guard = 0;
     cudaGraphSetConditional(L.h, *stop ? 0u : 1u);
 }
 
 __global__ void k_loop_ctl(LoopCtl L, int limit, const int *stop) {
+    wait_prior_kernel();
     const int gd = ++*L.guard;
     *L.launches += (unsigned long long)*L.nk;
     cudaGraphSetConditional(L.h, (!*stop && gd < limit) ? 1u : 0u);
@@ -775,6 +806,7 @@ __global__ void k_loop_ctl(LoopCtl L, int limit, const int *stop) {
 
 // restart loop of a GMRES: continue while not converged, finite and under the iteration cap
 __global__ void k_gm_loop_ctl(LoopCtl L, int limit, const GmresState *gs, int init) {
+    wait_prior_kernel();
     int gd = 0;
     if (init) *L.guard = 0;
     else {
@@ -787,6 +819,7 @@ __global__ void k_gm_loop_ctl(LoopCtl L, int limit, const GmresState *gs, int in
 
 // Z[j] = z with j = gs->j (basis slot of the current Arnoldi step)
 __global__ void k_slot_store(const double *__restrict__ z, double *Z, long long n, const GmresState *gs) {
+    wait_prior_kernel();
     if (gs->cycle_end) return;
     double *zj = Z + (size_t)gs->j * n;
     GRID_STRIDE(i, n) zj[i] = z[i];
@@ -801,6 +834,7 @@ struct DevCount {
 };
 
 __global__ void k_count_solve(DevCount *acc, const GmresState *gs, const Scalars *sc) {
+    wait_prior_kernel();
     if (gs) { acc->stepI_iters += gs->total; acc->stepI_solves += 1; }
     if (sc) {
         acc->trace_iters += sc->iters; acc->trace_solves += 1;
@@ -810,6 +844,7 @@ __global__ void k_count_solve(DevCount *acc, const GmresState *gs, const Scalars
 
 // after a stage solve by flexible GMRES
 __global__ void k_count_stage(DevCount *acc, const GmresState *fgs) {
+    wait_prior_kernel();
     acc->outer_iters += fgs->total;
     acc->stage_solves += 1;
     if (!fgs->converged) acc->stage_unconverged += 1;
@@ -898,6 +933,7 @@ __device__ void multidot_groups(const RedBuf rb, const T *V, const T *w, long lo
 template <class T>
 __global__ void k_gm_start(long long nrows, const double *__restrict__ b, const double *__restrict__ Bx,
                            T *w, int first, RedBuf rb, GmresState *gs, double rtol, int maxit) {
+    wait_prior_kernel();
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(g, nrows) {
         const T r = (T)(b[g] - (Bx ? Bx[g] : 0.0));
@@ -929,6 +965,7 @@ __global__ void k_gm_start(long long nrows, const double *__restrict__ b, const 
 template <int K, class T>
 __global__ void k_gm_precond_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ Binv, const T *__restrict__ w,
                                 T *V, T *utr, const GmresState *gs) {
+    wait_prior_kernel();
     if (gs->cycle_end) return;
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
@@ -974,6 +1011,7 @@ __global__ void k_gm_precond_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ B
 template <int K, class T>
 __global__ void k_gm_apply_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ wq, const T *__restrict__ utr, T *w,
                               const T *__restrict__ V, RedBuf rb, GmresState *gs) {
+    wait_prior_kernel();
     if (gs->cycle_end) return;
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
@@ -1004,6 +1042,7 @@ __global__ void k_gm_apply_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ wq,
 // w -= V hcol; h2 = (V_i, w)  (second Gram-Schmidt pass); rows in contiguous chunks per block
 template <class T>
 __global__ void k_gm_orth1(T *w, const T *__restrict__ V, long long nrows, RedBuf rb, GmresState *gs) {
+    wait_prior_kernel();
     if (gs->cycle_end) return;
     const int nvec = gs->j + 1;
     __shared__ double h[GM_M + 1];
@@ -1054,6 +1093,7 @@ __device__ void gm_finish_step(GmresState *gs, int j, double hn, bool with_h2) {
 // solves whose loose tolerance does not need the second pass.
 template <class T, bool CGS1 = false>
 __global__ void k_gm_orth2(T *w, const T *__restrict__ V, long long nrows, RedBuf rb, GmresState *gs) {
+    wait_prior_kernel();
     if (gs->cycle_end) return;
     const int j = gs->j, nvec = j + 1;
     __shared__ double h[GM_M + 1];
@@ -1073,6 +1113,7 @@ __global__ void k_gm_orth2(T *w, const T *__restrict__ V, long long nrows, RedBu
 
 // y = R^{-1} g (upper triangular part of the rotated H, without the subdiagonal)
 __global__ void k_gm_solve(GmresState *gs, const double *Hdiag_unused) {
+    wait_prior_kernel();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int m = gs->j;
     for (int i = m - 1; i >= 0; --i) {
@@ -1086,6 +1127,7 @@ __global__ void k_gm_solve(GmresState *gs, const double *Hdiag_unused) {
 // u = V y (rows), then x += Binv u (cell-local)
 template <class T>
 __global__ void k_gm_combine(const T *__restrict__ V, T *u, long long nrows, const GmresState *gs) {
+    wait_prior_kernel();
     const int m = gs->j;
     __shared__ double y[GM_M];
     if ((int)threadIdx.x < m) y[threadIdx.x] = gs->y[threadIdx.x];
@@ -1100,6 +1142,7 @@ __global__ void k_gm_combine(const T *__restrict__ V, T *u, long long nrows, con
 template <int K, class T>
 __global__ void k_gm_update_x(const T *__restrict__ Binv, const T *__restrict__ u, double *x,
                               long long ncells, int first) {
+    wait_prior_kernel();
     constexpr int NU = Dims<K>::NU;
     const long long nrows = ncells * NU;
     GRID_STRIDE(g, nrows) {
@@ -1116,6 +1159,7 @@ __global__ void k_gm_update_x(const T *__restrict__ Binv, const T *__restrict__ 
 template <int K>
 __global__ void k_rich_residual(RefDev R, MeshDev M, double c, const double *r, const double *BQ,
                                 const double *p, const double *lam, double *dr, double sgn) {
+    wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NP = Dm::NP, NT = Dm::NT, NL = Dm::NL;
     constexpr int SCR = NL;
@@ -1150,6 +1194,7 @@ __global__ void k_rich_residual(RefDev R, MeshDev M, double c, const double *r, 
 template <int K>
 __global__ void k_constraint(RefDev R, MeshDev M, double tau, const double *Q, const double *p,
                              const double *lam, double *yp, double *v) {
+    wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int SCR = Dm::NL + 2 * Dm::MU;
     CELL_TEAM(SCR)
@@ -1165,6 +1210,7 @@ __global__ void k_constraint(RefDev R, MeshDev M, double tau, const double *Q, c
 // beta = ||r||, g = beta e1 (cycle start on an already formed residual r)
 __global__ void k_vec_start(const double *__restrict__ r, long long n, int first, RedBuf rb, GmresState *gs,
                             double rtol, int maxit) {
+    wait_prior_kernel();
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(i, n) v[0] += r[i] * r[i];
     if (grid_sum<1>(rb, v, tot)) {
@@ -1185,6 +1231,7 @@ __global__ void k_vec_start(const double *__restrict__ r, long long n, int first
 }
 
 __global__ void k_vec_norm_into(const double *__restrict__ b, long long n, RedBuf rb, GmresState *gs) {
+    wait_prior_kernel();
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(i, n) v[0] += b[i] * b[i];
     if (grid_sum<1>(rb, v, tot)) gs->bnorm = sqrt(tot[0]);
@@ -1194,6 +1241,7 @@ __global__ void k_vec_norm_into(const double *__restrict__ b, long long n, RedBu
 // copy of V_j at a fixed address
 __global__ void k_vec_normalize(const double *__restrict__ w0, const double *__restrict__ w, double *V,
                                 double *vfix, long long n, const GmresState *gs) {
+    wait_prior_kernel();
     if (gs->cycle_end) return;
     const int j = gs->j;
     const double h = j == 0 ? gs->beta : gs->H[(j - 1) * (GM_M + 1) + j];
@@ -1210,12 +1258,14 @@ __global__ void k_vec_normalize(const double *__restrict__ w0, const double *__r
 // hcol = V^T w over V_0..V_j
 __global__ void k_vec_dot(const double *__restrict__ w, const double *__restrict__ V, long long n, RedBuf rb,
                           GmresState *gs, int with_norm) {
+    wait_prior_kernel();
     if (gs->cycle_end) return;
     multidot_rows(rb, V, w, n, gs->j + 1, gs->hcol, with_norm != 0);
 }
 
 // x += u
 __global__ void k_vec_add(const double *__restrict__ u, double *x, long long n) {
+    wait_prior_kernel();
     GRID_STRIDE(i, n) x[i] += u[i];
 }
 
@@ -1223,6 +1273,7 @@ __global__ void k_vec_add(const double *__restrict__ u, double *x, long long n) 
 template <int K>
 __global__ void k_rich_update(MeshDev M, double *Q, const double *Qbar, const double *U, double *p,
                               const double *dp, double *lam, const double *dl, RedBuf rb, Scalars *sc) {
+    wait_prior_kernel();
     typedef Dims<K> Dm;
     double v[2] = {0.0, 0.0}, tot[2];
     const long long nQ = (long long)M.ncells * Dm::NU;
@@ -1242,6 +1293,7 @@ __global__ void k_rich_update(MeshDev M, double *Q, const double *Qbar, const do
 // (p)_Omega: sum_K detJ p_K0 * int_T phi_0 = detJ p_K0 / sqrt(2)
 template <int K>
 __global__ void k_p_integral(MeshDev M, const double *p, RedBuf rb, Scalars *sc) {
+    wait_prior_kernel();
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(cl, M.ncells) v[0] += M.geo[cl].detJ * p[(size_t)cl * Dims<K>::NP] * 0.70710678118654752440;
     if (grid_sum<1>(rb, v, tot)) sc->red2 = tot[0];
@@ -1250,6 +1302,7 @@ __global__ void k_p_integral(MeshDev M, const double *p, RedBuf rb, Scalars *sc)
 // p -= m (constant), lam -= m, with m = (p)_Omega / area
 template <int K>
 __global__ void k_p_shift(MeshDev M, double area, double *p, double *lam, const Scalars *sc) {
+    wait_prior_kernel();
     const double m = sc->red2 / area;
     GRID_STRIDE(cl, M.ncells) p[(size_t)cl * Dims<K>::NP] -= m * 0.70710678118654752440;   // m = (m/sqrt2) phi_0
     if (lam) GRID_STRIDE(f, M.nfacets) lam[(size_t)f * Dims<K>::NT] -= m;

@@ -11,6 +11,7 @@ namespace hdg {
 template <int NT>
 __global__ void k_p1_cellop(const double *__restrict__ Scell, const int *__restrict__ cell_flip, int ncells,
                             double *cellA) {
+    wait_prior_kernel();
     GRID_STRIDE(c, ncells) {
         int flip[3] = {cell_flip[3 * c], cell_flip[3 * c + 1], cell_flip[3 * c + 2]};
         p1_cellop<NT>(Scell + (size_t)c * 9 * NT * NT, flip, cellA + 9 * c);
@@ -24,6 +25,7 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long *dst, double v
 
 __global__ void k_p1_assemble(P1Grid G, const double *__restrict__ cellA, const int *__restrict__ vert_cell,
                               const int *__restrict__ cell_vert, double *A, double *dinv, unsigned long long *lmax) {
+    wait_prior_kernel();
     GRID_STRIDE(v, G.nverts) {
         double row[P1_NS];
         p1_assemble_row((int)v, G, cellA, vert_cell, cell_vert, row);
@@ -36,6 +38,7 @@ __global__ void k_p1_assemble(P1Grid G, const double *__restrict__ cellA, const 
 
 __global__ void k_p1_coarsen(P1Grid Gc, P1Grid Gf, const double *__restrict__ Af, double *Ac, double *dinv,
                              unsigned long long *lmax) {
+    wait_prior_kernel();
     GRID_STRIDE(V, Gc.nverts) {
         double row[P1_NS];
         p1_galerkin_row((int)V, Gc, Gf, Af, row);
@@ -50,6 +53,7 @@ __global__ void k_p1_coarsen(P1Grid Gc, P1Grid Gf, const double *__restrict__ Af
 template <int NT>
 __global__ void k_trace_bound(const double *__restrict__ Sell, const int *__restrict__ tcol,
                               const double *__restrict__ Dinv, int nfacets, unsigned long long *lmax) {
+    wait_prior_kernel();
     const long long nrows = (long long)nfacets * NT;
     GRID_STRIDE(fl, nfacets) {
         int f = (int)fl;
@@ -75,6 +79,7 @@ __global__ void k_trace_bound(const double *__restrict__ Sell, const int *__rest
 
 // dense pseudo-inverse of the coarsest operator: Minv = (A + 1 1^T / N)^{-1} (one block)
 __global__ void k_coarse_inverse(P1Grid G, const double *__restrict__ A, double *B, double *Minv, int *status) {
+    wait_prior_kernel();
     const int N = G.nverts;
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
         B[i] = 1.0 / N;
@@ -129,6 +134,7 @@ __global__ void k_coarse_inverse(P1Grid G, const double *__restrict__ A, double 
 template <int NT>
 __global__ void k_tcheb0(const double *__restrict__ Dinv, const double *__restrict__ b, double *x, double *d,
                          double invth, int nfacets, const Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     const long long nrows = (long long)nfacets * NT;
     GRID_STRIDE(fl, nfacets) {
@@ -150,6 +156,7 @@ __global__ void k_tcheb(const double *__restrict__ Sell, const int *__restrict__
                         const double *__restrict__ Dinv, const double *__restrict__ b,
                         const double *__restrict__ xin, double *__restrict__ xout, double *d, double c1, double c2,
                         int nfacets, const Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     const long long nrows = (long long)nfacets * NT;
     GRID_STRIDE(fl, nfacets) {
@@ -178,6 +185,7 @@ __global__ void k_tcheb(const double *__restrict__ Sell, const int *__restrict__
 template <int NT>
 __global__ void k_tresid(const double *__restrict__ Sell, const int *__restrict__ tcol, const double *__restrict__ b,
                          const double *__restrict__ x, double *__restrict__ t, int nfacets, const Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     const long long nrows = (long long)nfacets * NT;
     GRID_STRIDE(g, nrows) {
@@ -195,6 +203,7 @@ __global__ void k_tresid(const double *__restrict__ Sell, const int *__restrict_
 template <int NT>
 __global__ void k_restrict_t(int nverts, const double *__restrict__ t, const int *__restrict__ vert_facet,
                              const int *__restrict__ vert_fsign, double *b1, const Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     GRID_STRIDE(v, nverts) b1[v] = restrict_trace<NT>((int)v, t, vert_facet, vert_fsign);
 }
@@ -202,6 +211,7 @@ __global__ void k_restrict_t(int nverts, const double *__restrict__ t, const int
 template <int NT>
 __global__ void k_prolong_t(const int *__restrict__ facet_vert, const double *__restrict__ e1, double *x, int nfacets,
                             const Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     const double s3 = 0.28867513459481288225;
     GRID_STRIDE(f, nfacets) {
@@ -214,6 +224,7 @@ __global__ void k_prolong_t(const int *__restrict__ facet_vert, const double *__
 // ---------------------------------------------------------------- V-cycle: P1 levels
 __global__ void k_pcheb0(const double *__restrict__ dinv, const double *__restrict__ b, double *x, double *d,
                          double invth, int n, const Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     GRID_STRIDE(v, n) {
         double s = dinv[v] * b[v] * invth;
@@ -225,6 +236,7 @@ __global__ void k_pcheb0(const double *__restrict__ dinv, const double *__restri
 __global__ void k_pcheb(P1Grid G, const double *__restrict__ A, const double *__restrict__ dinv,
                         const double *__restrict__ b, const double *__restrict__ xin, double *__restrict__ xout,
                         double *d, double c1, double c2, const Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     GRID_STRIDE(v, G.nverts) {
         double r = b[v] - p1_apply((int)v, G, A, xin);
@@ -236,16 +248,19 @@ __global__ void k_pcheb(P1Grid G, const double *__restrict__ A, const double *__
 
 __global__ void k_presid(P1Grid G, const double *__restrict__ A, const double *__restrict__ b,
                          const double *__restrict__ x, double *t, const Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     GRID_STRIDE(v, G.nverts) t[v] = b[v] - p1_apply((int)v, G, A, x);
 }
 
 __global__ void k_prestrict(P1Grid Gc, P1Grid Gf, const double *__restrict__ tf, double *bc, const Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     GRID_STRIDE(V, Gc.nverts) bc[V] = restrict_p1((int)V, Gc, Gf, tf);
 }
 
 __global__ void k_pprolong(P1Grid Gf, P1Grid Gc, const double *__restrict__ ec, double *x, const Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     GRID_STRIDE(a, Gf.nverts) x[a] += prolong_p1((int)a, Gf, Gc, ec);
 }
@@ -253,6 +268,7 @@ __global__ void k_pprolong(P1Grid Gf, P1Grid Gc, const double *__restrict__ ec, 
 // x = Minv (b - mean(b))   (one block)
 __global__ void k_coarse_solve(int N, const double *__restrict__ Minv, const double *__restrict__ b, double *x,
                                const Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     __shared__ double sh[1][32];
     __shared__ double mean;
@@ -273,6 +289,7 @@ __global__ void k_coarse_solve(int N, const double *__restrict__ Minv, const dou
 template <int NT>
 __global__ void k_cg_setup_mg(const double *__restrict__ b, double *x, double *r, double *pold, int nfacets,
                               Scalars *sc) {
+    wait_prior_kernel();
     const double mean = sc->bmean;
     GRID_STRIDE(g, (long long)nfacets * NT) {
         r[g] = b[g] - ((g % NT) == 0 ? mean : 0.0);
@@ -289,6 +306,7 @@ template <int NT>
 __global__ void k_trace_resid(const double *__restrict__ Sell, const int *__restrict__ tcol,
                               const double *__restrict__ b, const double *__restrict__ x, double *r, int nfacets,
                               const Scalars *sc) {
+    wait_prior_kernel();
     const double mean = sc->bmean;
     const long long nrows = (long long)nfacets * NT;
     GRID_STRIDE(g, nrows) {
@@ -306,12 +324,14 @@ __global__ void k_trace_resid(const double *__restrict__ Sell, const int *__rest
 
 // x += z (the V-cycle correction)
 __global__ void k_axpy_done(const double *__restrict__ z, double *x, long long n, const Scalars *sc) {
+    wait_prior_kernel();
     GRID_STRIDE(i, n) x[i] += z[i];
 }
 
 // x += alpha p; r -= alpha Ap
 __global__ void k_cg_update_nz(const double *__restrict__ p, const double *__restrict__ Ap, double *x, double *r,
                                long long n, const Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     const double alpha = sc->alpha;
     GRID_STRIDE(i, n) {
@@ -325,6 +345,7 @@ __global__ void k_cg_update_nz(const double *__restrict__ p, const double *__res
 template <int NT>
 __global__ void k_cg_rz(const double *__restrict__ r, const double *__restrict__ z, int nfacets, int first,
                         RedBuf rb, Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     double v[3] = {0.0, 0.0, 0.0}, tot[3];
     GRID_STRIDE(i, (long long)nfacets * NT) {
@@ -352,17 +373,20 @@ __global__ void k_cg_rz(const double *__restrict__ r, const double *__restrict__
 
 // tolerances of the next solve (kept out of the captured graphs, which serve every tolerance)
 __global__ void k_set_tol(Scalars *sc, double rtol, int maxit) {
+    wait_prior_kernel();
     sc->rtol = rtol;
     sc->maxit = maxit;
 }
 
 __global__ void k_gm_set_tol(GmresState *gs, double rtol, int maxit) {
+    wait_prior_kernel();
     gs->rtol = rtol;
     gs->maxit = maxit;
 }
 
 // instrumentation: put an Arnoldi step j of a live cycle in place (one kernel timed alone)
 __global__ void k_gm_set_step(GmresState *gs, int j) {
+    wait_prior_kernel();
     gs->j = j;
     gs->cycle_end = 0;
 }
@@ -392,6 +416,7 @@ struct MGTail {
 
 template <int NT>
 __global__ void __launch_bounds__(1024) k_mg_tail(MGTail T, const Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     const int tid = threadIdx.x, nth = blockDim.x;
     if (T.first == 0)
@@ -468,6 +493,7 @@ template <int NT>
 __global__ void k_cg_update_cheb0(const double *__restrict__ p, const double *__restrict__ Ap, double *x, double *r,
                                   const double *__restrict__ Dinv, double *z, double *d, double invth, int nfacets,
                                   const Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     const double alpha = sc->alpha;
     const long long nrows = (long long)nfacets * NT;
@@ -496,6 +522,7 @@ __global__ void k_tcheb_rz(const double *__restrict__ Sell, const int *__restric
                            const double *__restrict__ Dinv, const double *__restrict__ b,
                            const double *__restrict__ xin, double *__restrict__ xout, double *d, double c1, double c2,
                            int nfacets, int first, RedBuf rb, Scalars *sc) {
+    wait_prior_kernel();
     if (sc->done) return;
     const long long nrows = (long long)nfacets * NT;
     double v[3] = {0.0, 0.0, 0.0}, tot[3];

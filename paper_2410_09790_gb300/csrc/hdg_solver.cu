@@ -14,6 +14,7 @@
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/hdg.h"
@@ -231,6 +232,25 @@ void read_scalars(hdg_ctx *c) {
 
 int grid_for(long long n) { return red_grid(n); }
 
+// Kernel launch with programmatic stream serialisation (programmatic dependent launch): the
+// kernel may start while its predecessor on the stream drains; the kernel's first statement
+// (wait_prior_kernel) waits for the predecessor's completion. Works on plain streams and under
+// stream capture (graph edges become programmatic).
+template <class... KArgs, class... Args>
+void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args &&...args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
+
 // Krylov orthogonalisation kernels: at most four blocks per SM, several rows per thread
 int g_num_sms = 0;
 int grid_orth(long long n) {
@@ -388,18 +408,18 @@ struct Impl {
         const double *Tm = kind == 0 ? c->R.nod_u : kind == 1 ? c->R.nod_p : c->R.nod_t;
         int n = kind == 0 ? MU : kind == 1 ? NP : NT;
         long long nvec = kind == 0 ? 2 * c->ncells : kind == 1 ? c->ncells : c->nfacets;
-        k_basis_change<<<grid_for(nvec * n), VEC_THREADS, 0, c->st>>>(Tm, n, nodal, modal, nvec);
+        launch_k(k_basis_change, grid_for(nvec * n), VEC_THREADS, 0, c->st, Tm, n, nodal, modal, nvec);
         CKL();
     }
     static void to_nodal(hdg_ctx *c, const double *modal, double *nodal, int kind) {
         const double *Tm = kind == 0 ? c->R.mod_u : kind == 1 ? c->R.mod_p : c->R.mod_t;
         int n = kind == 0 ? MU : kind == 1 ? NP : NT;
         long long nvec = kind == 0 ? 2 * c->ncells : kind == 1 ? c->ncells : c->nfacets;
-        k_basis_change<<<grid_for(nvec * n), VEC_THREADS, 0, c->st>>>(Tm, n, modal, nodal, nvec);
+        launch_k(k_basis_change, grid_for(nvec * n), VEC_THREADS, 0, c->st, Tm, n, modal, nodal, nvec);
         CKL();
     }
     static void mass(hdg_ctx *c, const double *in, double *out, int mode) {
-        k_mass_scale<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, in, out, c->ncells, mode);
+        launch_k(k_mass_scale, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->geo, NU, in, out, c->ncells, mode);
         CKL();
     }
 
@@ -418,9 +438,9 @@ struct Impl {
         E.Dinv = c->alloc<double>((size_t)NT * c->nL);
         size_t smem = sizeof(double) * (NP * NU + NL * NU + 2 * NP * NP + 2 * NP * NL + NL * NL);
         CK(cudaFuncSetAttribute(k_condense<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_condense<K><<<(unsigned)c->ncells, 128, smem, c->st>>>(c->R, c->M, cc, c->P.tau, E.Scell, E.Zc, E.Ac);
+        launch_k(k_condense<K>, (unsigned)c->ncells, 128, smem, c->st, c->R, c->M, cc, c->P.tau, E.Scell, E.Zc, E.Ac);
         CKL();
-        k_assemble_trace<NT><<<grid_for(c->nfacets), VEC_THREADS, 0, c->st>>>(c->M, E.Scell, E.Sell, E.tcol, E.Dinv);
+        launch_k(k_assemble_trace<NT>, grid_for(c->nfacets), VEC_THREADS, 0, c->st, c->M, E.Scell, E.Sell, E.tcol, E.Dinv);
         CKL();
         if (c->P.trace_mg && c->H.p1_ok) build_mg(c, E);
         c->cache.push_back(E);
@@ -461,17 +481,17 @@ struct Impl {
         E.Minv = c->alloc<double>((size_t)Nc * Nc);
         E.Nc = Nc;
         CK(cudaMemsetAsync(c->dlmax, 0, 16 * sizeof(unsigned long long), c->st));
-        k_p1_cellop<NT><<<grid_for(c->ncells), VEC_THREADS, 0, c->st>>>(E.Scell, c->M.cell_flip, (int)c->ncells, c->cellA);
-        k_p1_assemble<<<grid_for(grids[0].nverts), VEC_THREADS, 0, c->st>>>(grids[0], c->cellA, c->M.vert_cell,
+        launch_k(k_p1_cellop<NT>, grid_for(c->ncells), VEC_THREADS, 0, c->st, E.Scell, c->M.cell_flip, (int)c->ncells, c->cellA);
+        launch_k(k_p1_assemble, grid_for(grids[0].nverts), VEC_THREADS, 0, c->st, grids[0], c->cellA, c->M.vert_cell,
                                                                          c->M.cell_vert, E.lv[0].A, E.lv[0].dinv,
                                                                          c->dlmax + 1);
         for (int l = 1; l < L; ++l)
-            k_p1_coarsen<<<grid_for(grids[l].nverts), VEC_THREADS, 0, c->st>>>(grids[l], grids[l - 1], E.lv[l - 1].A,
+            launch_k(k_p1_coarsen, grid_for(grids[l].nverts), VEC_THREADS, 0, c->st, grids[l], grids[l - 1], E.lv[l - 1].A,
                                                                              E.lv[l].A, E.lv[l].dinv, c->dlmax + 1 + l);
-        k_trace_bound<NT><<<grid_for(c->nfacets), VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, (int)c->nfacets,
+        launch_k(k_trace_bound<NT>, grid_for(c->nfacets), VEC_THREADS, 0, c->st, E.Sell, E.tcol, E.Dinv, (int)c->nfacets,
                                                                           c->dlmax);
         CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st));
-        k_coarse_inverse<<<1, 1024, 0, c->st>>>(grids[L - 1], E.lv[L - 1].A, c->mgB, E.Minv, c->dstatus);
+        launch_k(k_coarse_inverse, 1, 1024, 0, c->st, grids[L - 1], E.lv[L - 1].A, c->mgB, E.Minv, c->dstatus);
         CKL();
         unsigned long long bits[16];
         int st = 0;
@@ -527,30 +547,30 @@ struct Impl {
         int first = 0;
         while (first < L - 1 && E.lv[first].G.nverts > mg_fuse_max()) ++first;
         if (first > 0)
-            k_restrict_t<NT><<<grid_for(E.lv[0].G.nverts), VEC_THREADS, 0, c->st>>>(E.lv[0].G.nverts, c->tt,
+            launch_k(k_restrict_t<NT>, grid_for(E.lv[0].G.nverts), VEC_THREADS, 0, c->st, E.lv[0].G.nverts, c->tt,
                                                                                   c->M.vert_facet, c->M.vert_fsign,
                                                                                   c->mgw[0].b, sc);
         for (int l = 0; l < first; ++l) {
             const MGLevel &V = E.lv[l];
             const MGWork &W = c->mgw[l];
             const int g = grid_for(V.G.nverts);
-            k_pcheb0<<<g, VEC_THREADS, 0, c->st>>>(V.dinv, W.b, W.xa, W.d, V.invth, V.G.nverts, sc);
-            k_pcheb<<<g, VEC_THREADS, 0, c->st>>>(V.G, V.A, V.dinv, W.b, W.xa, W.xb, W.d, V.c1, V.c2, sc);
-            k_presid<<<g, VEC_THREADS, 0, c->st>>>(V.G, V.A, W.b, W.xb, W.t, sc);
-            k_prestrict<<<grid_for(E.lv[l + 1].G.nverts), VEC_THREADS, 0, c->st>>>(E.lv[l + 1].G, V.G, W.t,
+            launch_k(k_pcheb0, g, VEC_THREADS, 0, c->st, V.dinv, W.b, W.xa, W.d, V.invth, V.G.nverts, sc);
+            launch_k(k_pcheb, g, VEC_THREADS, 0, c->st, V.G, V.A, V.dinv, W.b, W.xa, W.xb, W.d, V.c1, V.c2, sc);
+            launch_k(k_presid, g, VEC_THREADS, 0, c->st, V.G, V.A, W.b, W.xb, W.t, sc);
+            launch_k(k_prestrict, grid_for(E.lv[l + 1].G.nverts), VEC_THREADS, 0, c->st, E.lv[l + 1].G, V.G, W.t,
                                                                                    c->mgw[l + 1].b, sc);
         }
-        k_mg_tail<NT><<<1, 1024, 0, c->st>>>(tail_params(c, E, first, c->tt, z0), sc);
+        launch_k(k_mg_tail<NT>, 1, 1024, 0, c->st, tail_params(c, E, first, c->tt, z0), sc);
         for (int l = first - 1; l >= 0; --l) {
             const MGLevel &V = E.lv[l];
             const MGWork &W = c->mgw[l];
             const int g = grid_for(V.G.nverts);
-            k_pprolong<<<g, VEC_THREADS, 0, c->st>>>(V.G, E.lv[l + 1].G, c->mgw[l + 1].xb, W.xb, sc);
-            k_pcheb<<<g, VEC_THREADS, 0, c->st>>>(V.G, V.A, V.dinv, W.b, W.xb, W.xa, W.d, 0.0, V.invth, sc);
-            k_pcheb<<<g, VEC_THREADS, 0, c->st>>>(V.G, V.A, V.dinv, W.b, W.xa, W.xb, W.d, V.c1, V.c2, sc);
+            launch_k(k_pprolong, g, VEC_THREADS, 0, c->st, V.G, E.lv[l + 1].G, c->mgw[l + 1].xb, W.xb, sc);
+            launch_k(k_pcheb, g, VEC_THREADS, 0, c->st, V.G, V.A, V.dinv, W.b, W.xb, W.xa, W.d, 0.0, V.invth, sc);
+            launch_k(k_pcheb, g, VEC_THREADS, 0, c->st, V.G, V.A, V.dinv, W.b, W.xa, W.xb, W.d, V.c1, V.c2, sc);
         }
         if (first > 0)
-            k_prolong_t<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(c->M.facet_vert, c->mgw[0].xb, z0, nf, sc);
+            launch_k(k_prolong_t<NT>, grid_for(nf), VEC_THREADS, 0, c->st, c->M.facet_vert, c->mgw[0].xb, z0, nf, sc);
     }
 
     // z0 = V-cycle(r0); with fused_start the first Chebyshev step (txa = d = Dinv r0 / theta) has
@@ -561,15 +581,15 @@ struct Impl {
         const int nf = (int)c->nfacets;
         const int gf = grid_facets(nf), gr = grid_for(c->nL);
         Scalars *sc = c->sc;
-        if (!fused_start) k_tcheb0<NT><<<gf, FACET_THREADS, 0, c->st>>>(E.Dinv, r0, c->txa, c->td, E.t_invth, nf, sc);
-        k_tcheb<NT><<<gf, FACET_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, r0, c->txa, z0, c->td, E.t_c1, E.t_c2, nf, sc);
-        k_tresid<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, r0, z0, c->tt, nf, sc);
+        if (!fused_start) launch_k(k_tcheb0<NT>, gf, FACET_THREADS, 0, c->st, E.Dinv, r0, c->txa, c->td, E.t_invth, nf, sc);
+        launch_k(k_tcheb<NT>, gf, FACET_THREADS, 0, c->st, E.Sell, E.tcol, E.Dinv, r0, c->txa, z0, c->td, E.t_c1, E.t_c2, nf, sc);
+        launch_k(k_tresid<NT>, gr, VEC_THREADS, 0, c->st, E.Sell, E.tcol, r0, z0, c->tt, nf, sc);
         vcycle_p1(c, E, z0);
-        k_tcheb<NT><<<gf, FACET_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, r0, z0, c->txa, c->td, 0.0, E.t_invth, nf, sc);
+        launch_k(k_tcheb<NT>, gf, FACET_THREADS, 0, c->st, E.Sell, E.tcol, E.Dinv, r0, z0, c->txa, c->td, 0.0, E.t_invth, nf, sc);
         if (rz_first < 0)
-            k_tcheb<NT><<<gf, FACET_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, r0, c->txa, z0, c->td, E.t_c1, E.t_c2, nf, sc);
+            launch_k(k_tcheb<NT>, gf, FACET_THREADS, 0, c->st, E.Sell, E.tcol, E.Dinv, r0, c->txa, z0, c->td, E.t_c1, E.t_c2, nf, sc);
         else
-            k_tcheb_rz<NT><<<gf, FACET_THREADS, 0, c->st>>>(E.Sell, E.tcol, E.Dinv, r0, c->txa, z0, c->td, E.t_c1, E.t_c2, nf,
+            launch_k(k_tcheb_rz<NT>, gf, FACET_THREADS, 0, c->st, E.Sell, E.tcol, E.Dinv, r0, c->txa, z0, c->td, E.t_c1, E.t_c2, nf,
                                                            rz_first, c->rb(), sc);
     }
 
@@ -577,26 +597,26 @@ struct Impl {
     static void trace_solve(hdg_ctx *c, CondCache &E, const double *b, double *x, double rtol) {
         const int nf = (int)c->nfacets;
         if (E.mg) { trace_solve_mg(c, E, b, x, rtol); return; }
-        k_trace_mean<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(b, nf, c->rb(), c->sc);
+        launch_k(k_trace_mean<NT>, grid_for(nf), VEC_THREADS, 0, c->st, b, nf, c->rb(), c->sc);
         CKL();
-        k_cg_setup<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(b, E.Dinv, x, c->tr, c->tz, c->tp[0], nf, c->rb(),
+        launch_k(k_cg_setup<NT>, grid_for(nf), VEC_THREADS, 0, c->st, b, E.Dinv, x, c->tr, c->tz, c->tp[0], nf, c->rb(),
                                                                c->sc, rtol, c->P.max_iters);
         CKL();
         const int gr = grid_for(c->nL), gf = grid_for(nf);
         if (c->capturing) {             // device-side loop, two iterations per pass
             capture_while(
-                c, [&](LoopCtl L) { k_loop_init<<<1, 1, 0, c->st>>>(L, &c->sc->done); },
+                c, [&](LoopCtl L) { launch_k(k_loop_init, 1, 1, 0, c->st, L, &c->sc->done); },
                 [&](LoopCtl L) {
                     for (int m = 0; m < 2; ++m) {
                         double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
-                        k_cg_apply<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
+                        launch_k(k_cg_apply<NT>, gr, VEC_THREADS, 0, c->st, E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
                                                                      c->rb(), c->sc);
-                        k_cg_update<NT><<<gf, VEC_THREADS, 0, c->st>>>(E.Dinv, pnew, c->tAp, x, c->tr, c->tz, nf,
+                        launch_k(k_cg_update<NT>, gf, VEC_THREADS, 0, c->st, E.Dinv, pnew, c->tAp, x, c->tr, c->tz, nf,
                                                                       c->rb(), c->sc);
                     }
-                    k_loop_ctl<<<1, 1, 0, c->st>>>(L, c->P.max_iters / 2 + 2, &c->sc->done);
+                    launch_k(k_loop_ctl, 1, 1, 0, c->st, L, c->P.max_iters / 2 + 2, &c->sc->done);
                 });
-            k_count_solve<<<1, 1, 0, c->st>>>(c->dcnt, nullptr, c->sc);
+            launch_k(k_count_solve, 1, 1, 0, c->st, c->dcnt, nullptr, c->sc);
             CKL();
             return;
         }
@@ -606,8 +626,8 @@ struct Impl {
                 throw std::length_error("trace CG: no convergence flag from the device");
             for (int m = 0; m < chunk; ++m) {
                 double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
-                k_cg_apply<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf, c->rb(), c->sc);
-                k_cg_update<NT><<<gf, VEC_THREADS, 0, c->st>>>(E.Dinv, pnew, c->tAp, x, c->tr, c->tz, nf, c->rb(), c->sc);
+                launch_k(k_cg_apply<NT>, gr, VEC_THREADS, 0, c->st, E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf, c->rb(), c->sc);
+                launch_k(k_cg_update<NT>, gf, VEC_THREADS, 0, c->st, E.Dinv, pnew, c->tAp, x, c->tr, c->tz, nf, c->rb(), c->sc);
             }
             CKL();
             read_scalars(c);
@@ -636,61 +656,61 @@ struct Impl {
         const int nf = (int)c->nfacets;
         const int gr = grid_for(c->nL);
         if (b != c->tb) CK(cudaMemcpyAsync(c->tb, b, 8 * c->nL, cudaMemcpyDeviceToDevice, c->st));
-        k_set_tol<<<1, 1, 0, c->st>>>(c->sc, rtol, c->P.max_iters);
+        launch_k(k_set_tol, 1, 1, 0, c->st, c->sc, rtol, c->P.max_iters);
         CKL();
         if (c->trace_vcycles > 0) {     // a fixed number of V-cycles in place of the CG (inner solves)
-            k_trace_mean<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(c->tb, nf, c->rb(), c->sc);
-            k_cg_setup_mg<NT><<<gr, VEC_THREADS, 0, c->st>>>(c->tb, c->tx, c->tr, c->tp[0], nf, c->sc);
+            launch_k(k_trace_mean<NT>, grid_for(nf), VEC_THREADS, 0, c->st, c->tb, nf, c->rb(), c->sc);
+            launch_k(k_cg_setup_mg<NT>, gr, VEC_THREADS, 0, c->st, c->tb, c->tx, c->tr, c->tp[0], nf, c->sc);
             for (int v = 0; v < c->trace_vcycles; ++v) {
                 if (v > 0) {            // r = b - mean - S x
-                    k_trace_resid<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->tb, c->tx, c->tr, nf, c->sc);
+                    launch_k(k_trace_resid<NT>, gr, VEC_THREADS, 0, c->st, E.Sell, E.tcol, c->tb, c->tx, c->tr, nf, c->sc);
                 }
                 vcycle(c, E, c->tr, c->tz, false, -1);
-                k_axpy_done<<<gr, VEC_THREADS, 0, c->st>>>(c->tz, c->tx, c->nL, c->sc);
+                launch_k(k_axpy_done, gr, VEC_THREADS, 0, c->st, c->tz, c->tx, c->nL, c->sc);
             }
             CKL();
             if (x != c->tx) CK(cudaMemcpyAsync(x, c->tx, 8 * c->nL, cudaMemcpyDeviceToDevice, c->st));
-            if (c->capturing) k_count_solve<<<1, 1, 0, c->st>>>(c->dcnt, nullptr, c->sc);
+            if (c->capturing) launch_k(k_count_solve, 1, 1, 0, c->st, c->dcnt, nullptr, c->sc);
             else c->S.trace_solves += 1;
             CKL();
             return;
         }
         if (c->capturing) {             // device-side loop, two iterations per pass
-            k_trace_mean<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(c->tb, nf, c->rb(), c->sc);
-            k_cg_setup_mg<NT><<<gr, VEC_THREADS, 0, c->st>>>(c->tb, c->tx, c->tr, c->tp[0], nf, c->sc);
+            launch_k(k_trace_mean<NT>, grid_for(nf), VEC_THREADS, 0, c->st, c->tb, nf, c->rb(), c->sc);
+            launch_k(k_cg_setup_mg<NT>, gr, VEC_THREADS, 0, c->st, c->tb, c->tx, c->tr, c->tp[0], nf, c->sc);
             vcycle(c, E, c->tr, c->tz, false, 1);
             capture_while(
-                c, [&](LoopCtl L) { k_loop_init<<<1, 1, 0, c->st>>>(L, &c->sc->done); },
+                c, [&](LoopCtl L) { launch_k(k_loop_init, 1, 1, 0, c->st, L, &c->sc->done); },
                 [&](LoopCtl L) {
                     for (int m = 0; m < 2; ++m) {
                         double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
-                        k_cg_apply<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
+                        launch_k(k_cg_apply<NT>, gr, VEC_THREADS, 0, c->st, E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
                                                                      c->rb(), c->sc);
-                        k_cg_update_cheb0<NT><<<grid_facets(nf), FACET_THREADS, 0, c->st>>>(
+                        launch_k(k_cg_update_cheb0<NT>, grid_facets(nf), FACET_THREADS, 0, c->st, 
                             pnew, c->tAp, c->tx, c->tr, E.Dinv, c->txa, c->td, E.t_invth, nf, c->sc);
                         vcycle(c, E, c->tr, c->tz, true, 0);
                     }
-                    k_loop_ctl<<<1, 1, 0, c->st>>>(L, c->P.max_iters / 2 + 2, &c->sc->done);
+                    launch_k(k_loop_ctl, 1, 1, 0, c->st, L, c->P.max_iters / 2 + 2, &c->sc->done);
                 });
             if (x != c->tx) CK(cudaMemcpyAsync(x, c->tx, 8 * c->nL, cudaMemcpyDeviceToDevice, c->st));
-            k_count_solve<<<1, 1, 0, c->st>>>(c->dcnt, nullptr, c->sc);
+            launch_k(k_count_solve, 1, 1, 0, c->st, c->dcnt, nullptr, c->sc);
             CKL();
             return;
         }
         const int chunk = trace_cg_enabled() ? 1 : 8;
         if (!E.g_setup) {
             E.g_setup = capture_graph(c, [&]() {
-                k_trace_mean<NT><<<grid_for(nf), VEC_THREADS, 0, c->st>>>(c->tb, nf, c->rb(), c->sc);
-                k_cg_setup_mg<NT><<<gr, VEC_THREADS, 0, c->st>>>(c->tb, c->tx, c->tr, c->tp[0], nf, c->sc);
+                launch_k(k_trace_mean<NT>, grid_for(nf), VEC_THREADS, 0, c->st, c->tb, nf, c->rb(), c->sc);
+                launch_k(k_cg_setup_mg<NT>, gr, VEC_THREADS, 0, c->st, c->tb, c->tx, c->tr, c->tp[0], nf, c->sc);
                 vcycle(c, E, c->tr, c->tz, false, 1);
                 CKL();
             });
             E.g_chunk = capture_graph(c, [&]() {
                 for (int m = 0; m < chunk; ++m) {
                     double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
-                    k_cg_apply<NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
+                    launch_k(k_cg_apply<NT>, gr, VEC_THREADS, 0, c->st, E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
                                                                  c->rb(), c->sc);
-                    k_cg_update_cheb0<NT><<<grid_facets(nf), FACET_THREADS, 0, c->st>>>(pnew, c->tAp, c->tx, c->tr, E.Dinv,
+                    launch_k(k_cg_update_cheb0<NT>, grid_facets(nf), FACET_THREADS, 0, c->st, pnew, c->tAp, c->tx, c->tr, E.Dinv,
                                                                                         c->txa, c->td, E.t_invth, nf, c->sc);
                     vcycle(c, E, c->tr, c->tz, true, 0);
                 }
@@ -731,13 +751,13 @@ struct Impl {
         CompTimer tm_(c, &c->S.ms_trace);
         size_t smem_rhs = sizeof(double) * TEAMS_PER_BLOCK * (NL + 4 * MU + NP + NL);
         unsigned nb = cell_blocks(c);
-        k_mixed_rhs<K><<<nb, 128, smem_rhs, c->st>>>(c->R, c->M, c->P.tau, Ru, X, p, lam, Rp_add, E.Zc, c->vK, c->wK);
+        launch_k(k_mixed_rhs<K>, nb, 128, smem_rhs, c->st, c->R, c->M, c->P.tau, Ru, X, p, lam, Rp_add, E.Zc, c->vK, c->wK);
         CKL();
-        k_facet_gather<NT><<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(c->M, c->vK, Rl_add, c->tb);
+        launch_k(k_facet_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, Rl_add, c->tb);
         CKL();
         trace_solve(c, E, c->tb, dl, rtol > 0 ? rtol : c->P.trace_rtol);
         size_t smem_bs = sizeof(double) * TEAMS_PER_BLOCK * (NL + NP);
-        k_mixed_backsub<K><<<nb, 128, smem_bs, c->st>>>(c->R, c->M, cc, Ru, c->wK, dl, E.Zc, E.Ac, U, dp);
+        launch_k(k_mixed_backsub<K>, nb, 128, smem_bs, c->st, c->R, c->M, cc, Ru, c->wK, dl, E.Zc, E.Ac, U, dp);
         CKL();
     }
 
@@ -751,15 +771,15 @@ struct Impl {
         constexpr int SCR = NU + NP + NL + NP + (NL + 4 * MU + NP + NL) + NU + NP + (NL + NP);
         const size_t smem = sizeof(double) * TEAMS_PER_BLOCK * SCR;
         CK(cudaFuncSetAttribute(k_build_pre_maps<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_build_pre_maps<K><<<cell_blocks(c), 128, smem, c->st>>>(c->R, c->M, cc, c->P.tau, E.Zc, E.Ac, E.Lrhs32,
+        launch_k(k_build_pre_maps<K>, cell_blocks(c), 128, smem, c->st, c->R, c->M, cc, c->P.tau, E.Zc, E.Ac, E.Lrhs32,
                                                                  E.Lbs32);
         CKL();
     }
 
     static void mean_shift(hdg_ctx *c, double *p, double *lam) {
-        k_p_integral<K><<<grid_for(c->ncells), VEC_THREADS, 0, c->st>>>(c->M, p, c->rb(), c->sc);
+        launch_k(k_p_integral<K>, grid_for(c->ncells), VEC_THREADS, 0, c->st, c->M, p, c->rb(), c->sc);
         CKL();
-        k_p_shift<K><<<grid_for(c->ncells > c->nfacets ? c->ncells : c->nfacets), VEC_THREADS, 0, c->st>>>(
+        launch_k(k_p_shift<K>, grid_for(c->ncells > c->nfacets ? c->ncells : c->nfacets), VEC_THREADS, 0, c->st, 
             c->M, c->area, p, lam, c->sc);
         CKL();
     }
@@ -778,7 +798,7 @@ struct Impl {
         size_t smem = sizeof(double) * fimpl_smem_doubles<K>();
         CK(cudaFuncSetAttribute(k_fimpl_assemble<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (!c->capturing) CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st));   // (graphs: once per launch)
-        k_fimpl_assemble<K><<<(unsigned)c->ncells, 128, smem, c->st>>>(
+        launch_k(k_fimpl_assemble<K>, (unsigned)c->ncells, 128, smem, c->st, 
             c->R, c->M, Qs, cc, c->P.alpha, c->P.delta_up, c->Dblk, c->wq, c->wq32, c->pen, c->pen32,
             (inv & INV64) ? c->Binv : nullptr, (inv & INV32) ? c->Binv32 : nullptr, c->dstatus);
         CKL();
@@ -786,7 +806,7 @@ struct Impl {
     }
 
     static void cell_apply(hdg_ctx *c, const double *x, double *y) {
-        k_cell_apply_mf<K><<<cell_blocks(c), 128, sizeof(double) * TEAMS_PER_BLOCK * 6 * Dm::NFQ, c->st>>>(
+        launch_k(k_cell_apply_mf<K>, cell_blocks(c), 128, sizeof(double) * TEAMS_PER_BLOCK * 6 * Dm::NFQ, c->st, 
             EdgeTab<double>{c->R.ephi, c->pen}, c->M, c->Dblk, c->wq, x, y);
         CKL();
     }
@@ -798,14 +818,14 @@ struct Impl {
         const long long n = c->nQ;
         const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
         const int go = grid_orth(n);
-        k_gm_precond_mf<K, T><<<cb, 128, sizeof(T) * TEAMS_PER_BLOCK * 2 * NU, c->st>>>(E, c->M, Binv, w, V, utr, c->gs);
-        k_gm_apply_mf<K, T><<<ab, 128, sizeof(T) * TEAMS_PER_BLOCK * 6 * Dm::NFQ, c->st>>>(E, c->M, wq, utr, w, V,
+        launch_k(k_gm_precond_mf<K, T>, cb, 128, sizeof(T) * TEAMS_PER_BLOCK * 2 * NU, c->st, E, c->M, Binv, w, V, utr, c->gs);
+        launch_k(k_gm_apply_mf<K, T>, ab, 128, sizeof(T) * TEAMS_PER_BLOCK * 6 * Dm::NFQ, c->st, E, c->M, wq, utr, w, V,
                                                                                           c->rb(), c->gs);
         if (sizeof(T) == sizeof(double)) {        // tight FP64 solves: two Gram-Schmidt passes
-            k_gm_orth1<T><<<go, VEC_THREADS, 0, c->st>>>(w, V, n, c->rb(), c->gs);
-            k_gm_orth2<T><<<go, VEC_THREADS, 0, c->st>>>(w, V, n, c->rb(), c->gs);
+            launch_k(k_gm_orth1<T>, go, VEC_THREADS, 0, c->st, w, V, n, c->rb(), c->gs);
+            launch_k(k_gm_orth2<T>, go, VEC_THREADS, 0, c->st, w, V, n, c->rb(), c->gs);
         } else {                                  // loose FP32 inner solves: one pass
-            k_gm_orth2<T, true><<<go, VEC_THREADS, 0, c->st>>>(w, V, n, c->rb(), c->gs);
+            launch_k(k_gm_orth2<T, true>, go, VEC_THREADS, 0, c->st, w, V, n, c->rb(), c->gs);
         }
     }
     static void gmres_arnoldi64(hdg_ctx *c) {
@@ -819,25 +839,25 @@ struct Impl {
         const long long n = c->nQ;
         const int g = grid_for(n);
         const EdgeTab<float> E{c->ephi32, c->pen32};
-        k_gm_start<float><<<g, VEC_THREADS, 0, c->st>>>(n, b, nullptr, c->gw32, 1, c->rb(), c->gs, -1.0, 0);
-        k_gm_set_cycle<<<1, 1, 0, c->st>>>(c->gs, GM_M);
+        launch_k(k_gm_start<float>, g, VEC_THREADS, 0, c->st, n, b, nullptr, c->gw32, 1, c->rb(), c->gs, -1.0, 0);
+        launch_k(k_gm_set_cycle, 1, 1, 0, c->st, c->gs, GM_M);
         capture_while(
-            c, [&](LoopCtl L) { k_loop_init<<<1, 1, 0, c->st>>>(L, &c->gs->cycle_end); },
+            c, [&](LoopCtl L) { launch_k(k_loop_init, 1, 1, 0, c->st, L, &c->gs->cycle_end); },
             [&](LoopCtl L) {
                 gmres_arnoldi<float>(c, E, c->Binv32, c->wq32, c->utr32, c->gw32, c->gV32);
-                k_loop_ctl<<<1, 1, 0, c->st>>>(L, GM_M + 1, &c->gs->cycle_end);
+                launch_k(k_loop_ctl, 1, 1, 0, c->st, L, GM_M + 1, &c->gs->cycle_end);
             });
-        k_gm_solve<<<1, 32, 0, c->st>>>(c->gs, nullptr);
-        k_gm_combine<float><<<g, VEC_THREADS, 0, c->st>>>(c->gV32, c->gu32, n, c->gs);
-        k_gm_update_x<K, float><<<g, VEC_THREADS, 0, c->st>>>(c->Binv32, c->gu32, x, c->ncells, 1);
-        k_count_solve<<<1, 1, 0, c->st>>>(c->dcnt, c->gs, nullptr);
+        launch_k(k_gm_solve, 1, 32, 0, c->st, c->gs, nullptr);
+        launch_k(k_gm_combine<float>, g, VEC_THREADS, 0, c->st, c->gV32, c->gu32, n, c->gs);
+        launch_k(k_gm_update_x<K, float>, g, VEC_THREADS, 0, c->st, c->Binv32, c->gu32, x, c->ncells, 1);
+        launch_k(k_count_solve, 1, 1, 0, c->st, c->dcnt, c->gs, nullptr);
         CKL();
     }
 
     // cycle start: w = b - B x (x = 0 on the first cycle)
     static void gmres_start(hdg_ctx *c, int first) {
         if (!first) cell_apply(c, c->gx, c->gz);
-        k_gm_start<double><<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->nQ, c->gb, first ? nullptr : c->gz, c->gw,
+        launch_k(k_gm_start<double>, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->nQ, c->gb, first ? nullptr : c->gz, c->gw,
                                                                       first, c->rb(), c->gs, -1.0, 0);
     }
 
@@ -848,11 +868,11 @@ struct Impl {
         const long long n = c->nQ;
         const int g = grid_for(n);
         gmres_start(c, first);
-        k_gm_set_cycle<<<1, 1, 0, c->st>>>(c->gs, m);
+        launch_k(k_gm_set_cycle, 1, 1, 0, c->st, c->gs, m);
         for (int j = 0; j < m; ++j) gmres_arnoldi64(c);
-        k_gm_solve<<<1, 32, 0, c->st>>>(c->gs, nullptr);
-        k_gm_combine<<<g, VEC_THREADS, 0, c->st>>>(c->gV, c->gu, n, c->gs);
-        k_gm_update_x<K><<<g, VEC_THREADS, 0, c->st>>>(c->Binv, c->gu, c->gx, c->ncells, first);
+        launch_k(k_gm_solve, 1, 32, 0, c->st, c->gs, nullptr);
+        launch_k(k_gm_combine<double>, g, VEC_THREADS, 0, c->st, c->gV, c->gu, n, c->gs);
+        launch_k(k_gm_update_x<K, double>, g, VEC_THREADS, 0, c->st, c->Binv, c->gu, c->gx, c->ncells, first);
         CKL();
     }
 
@@ -861,16 +881,16 @@ struct Impl {
         const long long n = c->nQ;
         const int g = grid_for(n);
         gmres_start(c, first);
-        k_gm_set_cycle<<<1, 1, 0, c->st>>>(c->gs, m);
+        launch_k(k_gm_set_cycle, 1, 1, 0, c->st, c->gs, m);
         capture_while(
-            c, [&](LoopCtl L) { k_loop_init<<<1, 1, 0, c->st>>>(L, &c->gs->cycle_end); },
+            c, [&](LoopCtl L) { launch_k(k_loop_init, 1, 1, 0, c->st, L, &c->gs->cycle_end); },
             [&](LoopCtl L) {
                 gmres_arnoldi64(c);
-                k_loop_ctl<<<1, 1, 0, c->st>>>(L, m + 1, &c->gs->cycle_end);
+                launch_k(k_loop_ctl, 1, 1, 0, c->st, L, m + 1, &c->gs->cycle_end);
             });
-        k_gm_solve<<<1, 32, 0, c->st>>>(c->gs, nullptr);
-        k_gm_combine<<<g, VEC_THREADS, 0, c->st>>>(c->gV, c->gu, n, c->gs);
-        k_gm_update_x<K><<<g, VEC_THREADS, 0, c->st>>>(c->Binv, c->gu, c->gx, c->ncells, first);
+        launch_k(k_gm_solve, 1, 32, 0, c->st, c->gs, nullptr);
+        launch_k(k_gm_combine<double>, g, VEC_THREADS, 0, c->st, c->gV, c->gu, n, c->gs);
+        launch_k(k_gm_update_x<K, double>, g, VEC_THREADS, 0, c->st, c->Binv, c->gu, c->gx, c->ncells, first);
         CKL();
     }
 
@@ -878,7 +898,7 @@ struct Impl {
         if (!(rtol > 0)) rtol = c->P.stepI_rtol;
         CompTimer tm_(c, &c->S.ms_stepI);
         if (!(c->inv_ok & inv_for(rtol))) throw std::logic_error("Step-I solve without the block inverses it needs");
-        k_gm_set_tol<<<1, 1, 0, c->st>>>(c->gs, rtol, c->P.max_iters);
+        launch_k(k_gm_set_tol, 1, 1, 0, c->st, c->gs, rtol, c->P.max_iters);
         CKL();
         if (loose(rtol)) {              // FP32, one cycle of at most GM_M steps
             if (c->capturing) {
@@ -900,13 +920,13 @@ struct Impl {
             gmres_cycle_dev(c, 1, m);
             const int limit = c->P.max_iters + 2;
             capture_while(
-                c, [&](LoopCtl L) { k_gm_loop_ctl<<<1, 1, 0, c->st>>>(L, limit, c->gs, 1); },
+                c, [&](LoopCtl L) { launch_k(k_gm_loop_ctl, 1, 1, 0, c->st, L, limit, c->gs, 1); },
                 [&](LoopCtl L) {
                     gmres_cycle_dev(c, 0, m);
-                    k_gm_loop_ctl<<<1, 1, 0, c->st>>>(L, limit, c->gs, 0);
+                    launch_k(k_gm_loop_ctl, 1, 1, 0, c->st, L, limit, c->gs, 0);
                 });
             if (x != c->gx) CK(cudaMemcpyAsync(x, c->gx, 8 * c->nQ, cudaMemcpyDeviceToDevice, c->st));
-            k_count_solve<<<1, 1, 0, c->st>>>(c->dcnt, c->gs, nullptr);
+            launch_k(k_count_solve, 1, 1, 0, c->st, c->dcnt, c->gs, nullptr);
             CKL();
             return;
         }
@@ -954,15 +974,15 @@ struct Impl {
         int it = 0;
         for (it = 0; it < nmax; ++it) {
             cell_apply(c, Q, BQ);
-            k_rich_residual<K><<<nb, 128, smem_res, c->st>>>(c->R, c->M, cc, r, BQ, p, lam, dr, 1.0);
+            launch_k(k_rich_residual<K>, nb, 128, smem_res, c->st, c->R, c->M, cc, r, BQ, p, lam, dr, 1.0);
             CKL();
             stepI_solve(c, dr, Qbar);                                            // Step I
             LinComb L{};
             L.nterms = 2; L.coef[0] = 1; L.vec[0] = Q; L.coef[1] = 1; L.vec[1] = Qbar;
-            k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, L, X, c->ncells);
+            launch_k(k_lincomb, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->geo, NU, L, X, c->ncells);
             CKL();
             mixed_solve(c, cc, nullptr, X, p, lam, U, dp, dl);                  // Step II
-            k_rich_update<K><<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->M, Q, Qbar, U, p, dp, lam, dl, c->rb(), c->sc);
+            launch_k(k_rich_update<K>, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->M, Q, Qbar, U, p, dp, lam, dl, c->rb(), c->sc);
             CKL();                                                               // Step III
             mean_shift(c, p, lam);
             read_scalars(c);
@@ -984,10 +1004,10 @@ struct Impl {
         const double *Q = x, *p = x + c->nQ, *lam = x + c->nQ + c->nPv;
         double *yQ = y, *yp = y + c->nQ, *yl = y + c->nQ + c->nPv;
         unsigned nb = cell_blocks(c);
-        k_stage_apply<K><<<nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (6 * Dm::NFQ + NL + 2 * MU), c->st>>>(
+        launch_k(k_stage_apply<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (6 * Dm::NFQ + NL + 2 * MU), c->st, 
             c->R, EdgeTab<double>{c->R.ephi, c->pen}, c->M, c->Dblk, c->wq, cc, c->P.tau, Q, p, lam, yQ, yp, c->vK);
         CKL();
-        k_facet_gather<NT><<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(c->M, c->vK, nullptr, yl);
+        launch_k(k_facet_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, nullptr, yl);
         CKL();
     }
 
@@ -1003,12 +1023,12 @@ struct Impl {
             if (E.Lrhs32) {             // Step II from the precomputed FP32 cell maps
                 CompTimer tm_(c, &c->S.ms_trace);
                 const unsigned nb = cell_blocks(c);
-                k_pre_rhs<K><<<nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (NU + NP), c->st>>>(c->M, E.Lrhs32, Qbar, vp,
+                launch_k(k_pre_rhs<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (NU + NP), c->st, c->M, E.Lrhs32, Qbar, vp,
                                                                                             c->vK, c->wK);
-                k_facet_gather<NT><<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(c->M, c->vK, vl, c->tb);
+                launch_k(k_facet_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, vl, c->tb);
                 CKL();
                 trace_solve(c, E, c->tb, zl, c->P.inner_trace_rtol);
-                k_pre_backsub<K><<<nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (NP + NL), c->st>>>(c->M, E.Lbs32, c->wK,
+                launch_k(k_pre_backsub<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (NP + NL), c->st, c->M, E.Lbs32, c->wK,
                                                                                                 zl, U, zp);
                 CKL();
             } else {
@@ -1021,7 +1041,7 @@ struct Impl {
         c->trace_vcycles = 0;
         LinComb L{};
         L.nterms = 2; L.coef[0] = 1; L.vec[0] = Qbar; L.coef[1] = 1; L.vec[1] = U;
-        k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, L, zQ, c->ncells);
+        launch_k(k_lincomb, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->geo, NU, L, zQ, c->ncells);
         CKL();
     }
 
@@ -1029,9 +1049,9 @@ struct Impl {
     // selective second pass was tried: the first pass cancels most of w at every step here).
     static void fgmres_orth(hdg_ctx *c, double *w, long long N, GmresState *fgs) {
         const int go = grid_orth(N);
-        k_vec_dot<<<go, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs, 0);
-        k_gm_orth1<double><<<go, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
-        k_gm_orth2<double><<<go, VEC_THREADS, 0, c->st>>>(w, c->fV, N, c->rb(), fgs);
+        launch_k(k_vec_dot, go, VEC_THREADS, 0, c->st, w, c->fV, N, c->rb(), fgs, 0);
+        launch_k(k_gm_orth1<double>, go, VEC_THREADS, 0, c->st, w, c->fV, N, c->rb(), fgs);
+        launch_k(k_gm_orth2<double>, go, VEC_THREADS, 0, c->st, w, c->fV, N, c->rb(), fgs);
         CKL();
     }
 
@@ -1048,36 +1068,36 @@ struct Impl {
         auto residual = [&](int first) {            // res = b - A x; cycle start
             stage_apply(c, cc, x, w);
             CK(cudaMemcpyAsync(res, b, 8 * N, cudaMemcpyDeviceToDevice, c->st));
-            k_axpby<<<g, VEC_THREADS, 0, c->st>>>(-1.0, w, 1.0, res, N);
-            k_vec_start<<<g, VEC_THREADS, 0, c->st>>>(res, N, first, c->rb(), fgs, rtol, maxit);
-            k_gm_set_cycle<<<1, 1, 0, c->st>>>(fgs, GM_M);
+            launch_k(k_axpby, g, VEC_THREADS, 0, c->st, -1.0, w, 1.0, res, N);
+            launch_k(k_vec_start, g, VEC_THREADS, 0, c->st, res, N, first, c->rb(), fgs, rtol, maxit);
+            launch_k(k_gm_set_cycle, 1, 1, 0, c->st, fgs, GM_M);
             CKL();
         };
-        k_vec_norm_into<<<g, VEC_THREADS, 0, c->st>>>(b, N, c->rb(), fgs);
+        launch_k(k_vec_norm_into, g, VEC_THREADS, 0, c->st, b, N, c->rb(), fgs);
         residual(2);
         capture_while(
-            c, [&](LoopCtl L) { k_gm_loop_ctl<<<1, 1, 0, c->st>>>(L, maxit + 2, fgs, 1); },
+            c, [&](LoopCtl L) { launch_k(k_gm_loop_ctl, 1, 1, 0, c->st, L, maxit + 2, fgs, 1); },
             [&](LoopCtl L) {
                 capture_while(
-                    c, [&](LoopCtl L2) { k_loop_init<<<1, 1, 0, c->st>>>(L2, &fgs->cycle_end); },
+                    c, [&](LoopCtl L2) { launch_k(k_loop_init, 1, 1, 0, c->st, L2, &fgs->cycle_end); },
                     [&](LoopCtl L2) {
-                        k_vec_normalize<<<g, VEC_THREADS, 0, c->st>>>(res, w, c->fV, c->fv, N, fgs);
+                        launch_k(k_vec_normalize, g, VEC_THREADS, 0, c->st, res, w, c->fV, c->fv, N, fgs);
                         CKL();
                         chorin_precond(c, cc, c->fv, c->fz);
-                        k_slot_store<<<g, VEC_THREADS, 0, c->st>>>(c->fz, c->fZ, N, fgs);
+                        launch_k(k_slot_store, g, VEC_THREADS, 0, c->st, c->fz, c->fZ, N, fgs);
                         stage_apply(c, cc, c->fz, w);
                         fgmres_orth(c, w, N, fgs);
-                        k_loop_ctl<<<1, 1, 0, c->st>>>(L2, GM_M + 1, &fgs->cycle_end);
+                        launch_k(k_loop_ctl, 1, 1, 0, c->st, L2, GM_M + 1, &fgs->cycle_end);
                         CKL();
                     });
-                k_gm_solve<<<1, 32, 0, c->st>>>(fgs, nullptr);
-                k_gm_combine<<<g, VEC_THREADS, 0, c->st>>>(c->fZ, u, N, fgs);
-                k_vec_add<<<g, VEC_THREADS, 0, c->st>>>(u, x, N);
+                launch_k(k_gm_solve, 1, 32, 0, c->st, fgs, nullptr);
+                launch_k(k_gm_combine<double>, g, VEC_THREADS, 0, c->st, c->fZ, u, N, fgs);
+                launch_k(k_vec_add, g, VEC_THREADS, 0, c->st, u, x, N);
                 residual(0);
-                k_gm_loop_ctl<<<1, 1, 0, c->st>>>(L, maxit + 2, fgs, 0);
+                launch_k(k_gm_loop_ctl, 1, 1, 0, c->st, L, maxit + 2, fgs, 0);
                 CKL();
             });
-        k_count_stage<<<1, 1, 0, c->st>>>(c->dcnt, fgs);
+        launch_k(k_count_stage, 1, 1, 0, c->st, c->dcnt, fgs);
         CKL();
     }
 
@@ -1139,23 +1159,23 @@ struct Impl {
             mean_shift(c, p, lam);
             return c->capturing ? 0 : (c->hfgs->converged ? 0 : 1);
         }
-        k_vec_norm_into<<<g, VEC_THREADS, 0, c->st>>>(b, N, c->rb(), c->fgs);
+        launch_k(k_vec_norm_into, g, VEC_THREADS, 0, c->st, b, N, c->rb(), c->fgs);
         CKL();
         int outer = 0, converged = 0;
         for (int cyc = 0; cyc < 1000; ++cyc) {
             stage_apply(c, cc, x, w);                                            // res = b - A x
             CK(cudaMemcpyAsync(res, b, 8 * N, cudaMemcpyDeviceToDevice, c->st));
-            k_axpby<<<g, VEC_THREADS, 0, c->st>>>(-1.0, w, 1.0, res, N);
-            k_vec_start<<<g, VEC_THREADS, 0, c->st>>>(res, N, cyc == 0 ? 2 : 0, c->rb(), c->fgs,
+            launch_k(k_axpby, g, VEC_THREADS, 0, c->st, -1.0, w, 1.0, res, N);
+            launch_k(k_vec_start, g, VEC_THREADS, 0, c->st, res, N, cyc == 0 ? 2 : 0, c->rb(), c->fgs,
                                                      c->P.richardson_rtol, c->P.richardson_max);
-            k_gm_set_cycle<<<1, 1, 0, c->st>>>(c->fgs, GM_M);
+            launch_k(k_gm_set_cycle, 1, 1, 0, c->st, c->fgs, GM_M);
             CKL();
             CK(cudaMemcpyAsync(c->hfgs, c->fgs, sizeof(GmresState), cudaMemcpyDeviceToHost, c->st));
             CK(cudaStreamSynchronize(c->st));
             if (c->hfgs->breakdown == 2) throw std::domain_error("stage FGMRES: non-finite residual");
             if (c->hfgs->converged) { converged = 1; break; }
             for (int j = 0; j < GM_M; ++j) {
-                k_vec_normalize<<<g, VEC_THREADS, 0, c->st>>>(res, w, c->fV, nullptr, N, c->fgs);
+                launch_k(k_vec_normalize, g, VEC_THREADS, 0, c->st, res, w, c->fV, nullptr, N, c->fgs);
                 CKL();
                 double *Vj = c->fV + (size_t)j * N, *Zj = c->fZ + (size_t)j * N;
                 chorin_precond(c, cc, Vj, Zj);
@@ -1168,9 +1188,9 @@ struct Impl {
                 if (c->hfgs->breakdown == 2) throw std::domain_error("stage FGMRES: non-finite residual");
                 if (c->hfgs->cycle_end) break;
             }
-            k_gm_solve<<<1, 32, 0, c->st>>>(c->fgs, nullptr);
-            k_gm_combine<<<g, VEC_THREADS, 0, c->st>>>(c->fZ, u, N, c->fgs);
-            k_vec_add<<<g, VEC_THREADS, 0, c->st>>>(u, x, N);
+            launch_k(k_gm_solve, 1, 32, 0, c->st, c->fgs, nullptr);
+            launch_k(k_gm_combine<double>, g, VEC_THREADS, 0, c->st, c->fZ, u, N, c->fgs);
+            launch_k(k_vec_add, g, VEC_THREADS, 0, c->st, u, x, N);
             CKL();
             if (c->hfgs->converged) { converged = 1; break; }
             if (outer >= c->P.richardson_max) break;
@@ -1196,7 +1216,7 @@ struct Impl {
     static void bdm(hdg_ctx *c, const double *Q, double *Qs) {
         CompTimer tm_(c, &c->S.ms_bdm);
         unsigned nb = cell_blocks(c);
-        k_bdm<K><<<nb, 128, sizeof(double) * TEAMS_PER_BLOCK * 2 * NU, c->st>>>(c->R, c->M, Q, Qs);
+        launch_k(k_bdm<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * 2 * NU, c->st, c->R, c->M, Q, Qs);
         CKL();
     }
 
@@ -1213,7 +1233,7 @@ struct Impl {
             L.coef[2] = c->phi ? c->phi(tt, c->phi_user) : 1.0;
             L.vec[2] = c->Fload;
         }
-        k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, L, out, c->ncells);
+        launch_k(k_lincomb, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->geo, NU, L, out, c->ncells);
         CKL();
     }
 
@@ -1257,7 +1277,7 @@ struct Impl {
                 if (f != 0.0) { L.coef[n] = f; L.vec[n] = c->Fload; L.mass[n] = 0; ++n; }
             }
             L.nterms = n;
-            k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, L, c->rs[i], c->ncells);
+            launch_k(k_lincomb, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->geo, NU, L, c->rs[i], c->ncells);
             CKL();
             bdm(c, c->Qs[i - 1], c->q[5]);                                       // Q*_{i-1}
             CK(cudaMemcpyAsync(c->Qs[i], c->Qs[i - 1], bq, cudaMemcpyDeviceToDevice, c->st));
@@ -1282,7 +1302,7 @@ struct Impl {
         }
         L.nterms = n;
         double *rn = c->q[7];
-        k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, NU, L, rn, c->ncells);
+        launch_k(k_lincomb, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->geo, NU, L, rn, c->ncells);
         CKL();
         mixed_solve(c, dt * T.bi[s - 1], rn, nullptr, nullptr, nullptr, c->Q, c->pp[1], c->ll[1]);
         reconstruct(c, c->Q, t0 + dt, c->p, c->lam);                            // Sec. 2.7
@@ -1831,9 +1851,9 @@ hdg_status hdg_trace_apply(hdg_ctx *c, double cc, const double *lam, double *out
         DISPATCH(c, {
             CondCache &E = I::condense(c, cc);
             I::to_modal(c, lam, c->ll[0], 2);
-            k_trace_apply<I::NT><<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->ll[0], c->ll[1], (int)c->nfacets);
+            launch_k(k_trace_apply<I::NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, E.Sell, E.tcol, c->ll[0], c->ll[1], (int)c->nfacets);
             CKL();
-            k_trace_riesz<<<grid_for(c->nL), VEC_THREADS, 0, c->st>>>(c->geo, c->M.facet_cell, c->M.facet_edge, I::NT,
+            launch_k(k_trace_riesz, grid_for(c->nL), VEC_THREADS, 0, c->st, c->geo, c->M.facet_cell, c->M.facet_edge, I::NT,
                                                                       c->ll[1], c->ll[2], c->nfacets);
             CKL();
             I::to_nodal(c, c->ll[2], out, 2);
@@ -1853,7 +1873,7 @@ hdg_status hdg_div_free_project(hdg_ctx *c, hdg_stats *stats) {
             I::mixed_solve(c, 1.0, nullptr, c->Q, nullptr, nullptr, c->q[0], c->pp[0], c->ll[0]);
             LinComb L{};
             L.nterms = 2; L.coef[0] = 1; L.vec[0] = c->Q; L.coef[1] = 1; L.vec[1] = c->q[0];
-            k_lincomb<<<grid_for(c->nQ), VEC_THREADS, 0, c->st>>>(c->geo, I::NU, L, c->Q, c->ncells);
+            launch_k(k_lincomb, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->geo, I::NU, L, c->Q, c->ncells);
             CKL();
             I::reconstruct(c, c->Q, c->t, c->p, c->lam);
         });
@@ -1893,7 +1913,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 I::bdm(c, c->Q, c->q[5]);
                 I::assemble_stepI(c, c->q[5], cc, I::INV32);
                 I::mass(c, c->Q, c->fv, 0);
-                k_gm_set_tol<<<1, 1, 0, c->st>>>(c->gs, 1e-30, J + 1);   // runs J + 1 steps
+                launch_k(k_gm_set_tol, 1, 1, 0, c->st, c->gs, 1e-30, J + 1);   // runs J + 1 steps
                 CKL();
                 cudaGraphExec_t ex = capture_graph(c, [&]() { I::stepI32_record(c, c->fv, c->q[2]); });
                 CK(cudaGraphLaunch(ex, c->st));
@@ -1901,10 +1921,10 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
                 const size_t sm = sizeof(float) * TEAMS_PER_BLOCK * 6 * I::Dm::NFQ;
                 auto launch = [&]() {
-                    k_gm_apply_mf<I::K_, float><<<ab, 128, sm, c->st>>>(E, c->M, c->wq32, c->utr32, c->gw32, c->gV32,
+                    launch_k(k_gm_apply_mf<I::K_, float>, ab, 128, sm, c->st, E, c->M, c->wq32, c->utr32, c->gw32, c->gV32,
                                                                         c->rb(), c->gs);
                 };
-                k_gm_set_step<<<1, 1, 0, c->st>>>(c->gs, J);
+                launch_k(k_gm_set_step, 1, 1, 0, c->st, c->gs, J);
                 launch();
                 CKL();
                 CK(cudaEventRecord(c->e0, c->st));
@@ -1967,7 +1987,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 CK(cudaMemcpyAsync(c->sc, &h, sizeof(Scalars), cudaMemcpyHostToDevice, c->st));
                 const int nf = (int)c->nfacets, gr = grid_for(c->nL);
                 auto launch = [&]() {
-                    k_cg_apply<I::NT><<<gr, VEC_THREADS, 0, c->st>>>(E.Sell, E.tcol, c->tz, c->tp[0], c->tp[1], c->tAp, nf,
+                    launch_k(k_cg_apply<I::NT>, gr, VEC_THREADS, 0, c->st, E.Sell, E.tcol, c->tz, c->tp[0], c->tp[1], c->tAp, nf,
                                                                     c->rb(), c->sc);
                 };
                 launch();
@@ -2015,6 +2035,7 @@ static double *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 template <int K>
 __global__ void k_condense_apply_cell(RefDev R, MeshDev M, double c, double tau, const double *__restrict__ lam,
                                       double *z) {
+    wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int NP = Dm::NP, NT = Dm::NT, NL = Dm::NL, NU = Dm::NU;
     extern __shared__ double sm[];
@@ -2044,18 +2065,18 @@ void trace_apply_noalloc_impl(hdg_ctx *c, double cc, const double *lam_nodal, do
     typedef Dims<K> Dm;
     constexpr int NP = Dm::NP, NT = Dm::NT, NL = Dm::NL, NU = Dm::NU;
     double *lm = scr, *ym = lm + c->nL, *yr = ym + c->nL, *z = yr + c->nL;
-    k_basis_change<<<red_grid(c->nL), VEC_THREADS, 0, c->st>>>(c->R.nod_t, NT, lam_nodal, lm, c->nfacets);
+    launch_k(k_basis_change, red_grid(c->nL), VEC_THREADS, 0, c->st, c->R.nod_t, NT, lam_nodal, lm, c->nfacets);
     CKL();
     size_t smem = sizeof(double) * (NP * NU + NL * NU + 2 * NP * NP + 2 * NP * NL + NL * NL + NL * NL + NP * NL +
                                     NP * NP + NL);
-    k_condense_apply_cell<K><<<(unsigned)c->ncells, 128, smem, c->st>>>(c->R, c->M, cc, c->P.tau, lm, z);
+    launch_k(k_condense_apply_cell<K>, (unsigned)c->ncells, 128, smem, c->st, c->R, c->M, cc, c->P.tau, lm, z);
     CKL();
-    k_facet_gather<NT><<<red_grid(c->nL), VEC_THREADS, 0, c->st>>>(c->M, z, nullptr, ym);
+    launch_k(k_facet_gather<NT>, red_grid(c->nL), VEC_THREADS, 0, c->st, c->M, z, nullptr, ym);
     CKL();
-    k_trace_riesz<<<red_grid(c->nL), VEC_THREADS, 0, c->st>>>(c->geo, c->M.facet_cell, c->M.facet_edge, NT, ym, yr,
+    launch_k(k_trace_riesz, red_grid(c->nL), VEC_THREADS, 0, c->st, c->geo, c->M.facet_cell, c->M.facet_edge, NT, ym, yr,
                                                               c->nfacets);
     CKL();
-    k_basis_change<<<red_grid(c->nL), VEC_THREADS, 0, c->st>>>(c->R.mod_t, NT, yr, out_nodal, c->nfacets);
+    launch_k(k_basis_change, red_grid(c->nL), VEC_THREADS, 0, c->st, c->R.mod_t, NT, yr, out_nodal, c->nfacets);
     CKL();
 }
 }  // namespace
