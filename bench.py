@@ -3,7 +3,7 @@
 Workload (the plain-FP64 GPU configuration): periodic-in-x channel [0,1]^2 with walls at
 y = 0, 1, 64 x 64 rectangles -> 8192 triangles, k = 3 (velocity P4, pressure/trace P3),
 ARS(3,4,3), dt = 2e-3; every stage solved to a relative stage residual of 1e-10 (flexible GMRES
-preconditioned by Alg. 2's Chorin split; inside it Step I by one FP32 GMRES cycle to 1e-1 and
+preconditioned by Alg. 2's Chorin split; inside it Step I by one FP32 GMRES cycle to 2e-2 and
 Step II by one trace multigrid V-cycle;
 the paper's fixed n_R = 2 is unstable on this flow); final update and pressure reconstruction
 trace CG rtol 1e-12; initial u = (tanh((y-1/2)/0.05), 1e-3 sin 2 pi x) + seeded N(0,1) 1e-4
@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(n=64, k=3, periodic_x=True, tableau='ARS343', dt=2e-3, n_richardson=0, stage_rtol=1e-10,
-                inner_stepI_rtol=1e-1, inner_trace_rtol=1e-1, trace_rtol=1e-12, stepI_rtol=1e-10,
+                inner_stepI_rtol=2e-2, inner_trace_rtol=1e-1, trace_rtol=1e-12, stepI_rtol=1e-10,
                 inner_trace_vcycles=1, init='shear_layer', width=0.05, amp=1e-3, noise=1e-4, seed=0)
 STAGES = {'ARS343': 3, 'ARS222': 2, 'IMEX_EULER': 1}
 METRIC = 'IMEX stage solves/s (trace-DoF/s alongside)'

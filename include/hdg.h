@@ -82,7 +82,7 @@ typedef struct {
     /* Stage solves to tolerance (n_richardson <= 0): stage_krylov = 0 iterates Alg. 2 until
      * ||dQ||_M <= richardson_rtol ||Q||_M; stage_krylov = 1 (default) runs flexible GMRES(30) on
      * the monolithic stage system with Alg. 2's Chorin split as the preconditioner (Step I and
-     * Step II solved to inner_stepI_rtol / inner_trace_rtol, defaults 1e-1 / 1e-1) until the
+     * Step II solved to inner_stepI_rtol / inner_trace_rtol, defaults 2e-2 / 1e-1) until the
      * stage residual is <= richardson_rtol times the right-hand side; richardson_max caps the
      * outer iterations. Both reach the same fixed point, the monolithic stage solution. */
     int stage_krylov;

@@ -1411,7 +1411,7 @@ void hdg_default_params(hdg_params *p) {
     p->stepI_rtol = 1e-10;
     p->max_iters = 5000;
     p->stage_krylov = 1;
-    p->inner_stepI_rtol = 1e-1;
+    p->inner_stepI_rtol = 2e-2;
     p->inner_trace_rtol = 1e-1;
     p->trace_mg = 1;
     p->device_loops = 1;
