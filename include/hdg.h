@@ -105,6 +105,9 @@ typedef struct {
      * = exactly n V-cycles of the trace multigrid (a fixed linear preconditioner; the flexible
      * outer iteration decides the accuracy); 0 = trace CG to inner_trace_rtol. */
     int inner_trace_vcycles;
+    /* Inner (FP32) Step-I solves: 1 (default) = one persistent cooperative kernel per solve with
+     * bounded grid-wide barriers; 0 = a sequence of kernels per Arnoldi step. Same algorithm. */
+    int persistent_stepI;
 } hdg_params;
 
 typedef struct {

@@ -20,6 +20,7 @@
 #include "../../include/hdg.h"
 #include "hdg_kernels.cuh"
 #include "hdg_mg_kernels.cuh"
+#include "hdg_stepI_persistent.cuh"
 #include "mesh.h"
 #include "refelem.h"
 
@@ -158,6 +159,8 @@ struct hdg_ctx {
     float *gV32 = nullptr, *gw32 = nullptr, *gu32 = nullptr;
     cudaGraphExec_t g_stepI32 = nullptr;                     // one loose Step-I solve (host-driven mode)
     int stepI32_kernels = 0;
+    GridBar *gbar = nullptr;                                 // barrier of the persistent Step-I kernel
+    int coop_grid = 0;                                       // its grid (all blocks co-resident)
     int *dstatus = nullptr;
     // Step II
     double *vK = nullptr, *wK = nullptr, *tb = nullptr, *tx = nullptr, *tr = nullptr, *tz = nullptr,
@@ -832,10 +835,47 @@ struct Impl {
         gmres_arnoldi<double>(c, EdgeTab<double>{c->R.ephi, c->pen}, c->Binv, c->wq, c->utr, c->gw, c->gV);
     }
 
+    // The same solve as one persistent cooperative kernel (hdg_stepI_persistent.cuh); a barrier
+    // that runs out of polls is reported as a breakdown through the device counters.
+    static void stepI32_persistent(hdg_ctx *c, const double *b, double *x) {
+        if (!c->coop_grid) {
+            int per_sm = 0, dev = 0, nsm = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stepI32_persistent<K>, 128, 0));
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+            const long long groups = (c->ncells + TEAMS_PER_BLOCK - 1) / TEAMS_PER_BLOCK;
+            long long g = (long long)per_sm * nsm;
+            if (g > groups) g = groups;
+            if (g > MAX_RED_BLOCKS) g = MAX_RED_BLOCKS;
+            if (g < 1) throw std::runtime_error("persistent Step-I kernel cannot be resident");
+            c->coop_grid = (int)g;
+        }
+        StepI32Args A{EdgeTab<float>{c->ephi32, c->pen32}, c->M, c->Binv32, c->wq32, c->gV32, c->utr32, c->gw32,
+                      b, x, c->partials, c->gbar, c->gs};
+        launch_k(k_bar_reset, 1, 1, 0, c->st, c->gbar);
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)c->coop_grid);
+        cfg.blockDim = dim3(128);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = c->st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelEx(&cfg, k_stepI32_persistent<K>, A));
+        launch_k(k_bar_check, 1, 1, 0, c->st, c->gbar, c->dcnt);
+        launch_k(k_count_solve, 1, 1, 0, c->st, c->dcnt, c->gs, (const Scalars *)nullptr);
+    }
+
     // A loose Step-I solve in FP32, recorded into the current capture: one GMRES(GM_M) cycle from
     // x = 0 with its Arnoldi steps as a device-side loop, stopping at the tolerance or after GM_M
     // steps (an inexact solve is what the flexible outer iteration expects). b, x: FP64.
     static void stepI32_record(hdg_ctx *c, const double *b, double *x) {
+        if (c->P.persistent_stepI) {
+            stepI32_persistent(c, b, x);
+            return;
+        }
         const long long n = c->nQ;
         const int g = grid_for(n);
         const EdgeTab<float> E{c->ephi32, c->pen32};
@@ -1416,6 +1456,7 @@ void hdg_default_params(hdg_params *p) {
     p->trace_mg = 1;
     p->device_loops = 1;
     p->inner_trace_vcycles = 1;
+    p->persistent_stepI = 1;
 }
 
 const char *hdg_status_string(hdg_status s) {
@@ -1564,6 +1605,8 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         c->wq32 = c->alloc<float>((size_t)c->ncells * 3 * nfq);
         c->utr32 = c->alloc<float>((size_t)c->ncells * 3 * nfq * 2);
         c->gV32 = c->alloc<float>((size_t)(GM_M + 1) * nQ);
+        c->gbar = c->alloc<GridBar>(1);
+        CK(cudaMemset(c->gbar, 0, sizeof(GridBar)));
         c->gw32 = c->alloc<float>(nQ);
         c->gu32 = c->alloc<float>(nQ);
         {

@@ -205,6 +205,27 @@ def test_device_loops_match_host_loops(mg):
         assert stats[0][key] == stats[1][key] > 0, key
 
 
+def test_persistent_inner_step_i_matches_kernel_sequence():
+    # the inner FP32 Step-I solve as one persistent cooperative kernel computes what the
+    # per-step kernel sequence computes (reduction orders differ: results agree to the stage
+    # tolerance, not bit for bit); both stage solves meet the same tolerance
+    n, k = 8, 3
+    Q0 = W.nodal_velocity(n, k, lambda x, y: W.shear_layer(x, y, width=0.1, amp=0.05), noise=1e-3, seed=6)
+    outs, stats = [], []
+    for ps in (0, 1):
+        ctx = H().Context(n, k, periodic_x=True, tableau='ARS343', dt=0.01, n_richardson=0, stage_krylov=1,
+                          richardson_rtol=1e-12, richardson_max=400, persistent_stepI=ps)
+        ctx.hdg_set_state(cuda(Q0))
+        ctx.hdg_reconstruct_pressure()
+        stats.append(ctx.hdg_imex_step(2))
+        outs.append([host(x) for x in ctx.hdg_get_state()[:3]])
+        ctx.close()
+    assert_close(outs[1][0], outs[0][0], 1e-10, 'Q')
+    assert_close(outs[1][1], outs[0][1], 1e-9, 'p')
+    for st in stats:
+        assert st['status'] == 0 and st['stepI_solves'] > 0 and st['stepI_iters'] >= st['stepI_solves']
+
+
 @pytest.mark.parametrize('n,px', [(16, True), (32, False)])
 def test_multigrid_iterations_mesh_robust(n, px):
     # the V-cycle preconditioner keeps the trace CG iteration count small and nearly independent
