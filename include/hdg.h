@@ -105,8 +105,10 @@ typedef struct {
      * = exactly n V-cycles of the trace multigrid (a fixed linear preconditioner; the flexible
      * outer iteration decides the accuracy); 0 = trace CG to inner_trace_rtol. */
     int inner_trace_vcycles;
-    /* Inner (FP32) Step-I solves: 1 (default) = one persistent cooperative kernel per solve with
-     * bounded grid-wide barriers; 0 = a sequence of kernels per Arnoldi step. Same algorithm. */
+    /* Inner (FP32) Step-I solves: 0 (default) = a sequence of kernels per Arnoldi step (launched
+     * with programmatic dependent launch); 1 = one persistent cooperative kernel per solve with
+     * bounded grid-wide barriers (same algorithm; slower on GB300 at the bench size: the barriers
+     * cost more than the kernel boundaries they replace). */
     int persistent_stepI;
 } hdg_params;
 

@@ -844,6 +844,14 @@ struct Impl {
             CK(cudaGetDevice(&dev));
             CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
             const long long groups = (c->ncells + TEAMS_PER_BLOCK - 1) / TEAMS_PER_BLOCK;
+            // few blocks per SM: every barrier is one atomic arrival per block
+            static int want = -1;
+            if (want < 0) {
+                const char *e = std::getenv("HDG_COOP_BLOCKS_PER_SM");
+                want = e ? std::atoi(e) : 4;
+                if (want < 1) want = 1;
+            }
+            if (per_sm > want) per_sm = want;
             long long g = (long long)per_sm * nsm;
             if (g > groups) g = groups;
             if (g > MAX_RED_BLOCKS) g = MAX_RED_BLOCKS;
@@ -1456,7 +1464,7 @@ void hdg_default_params(hdg_params *p) {
     p->trace_mg = 1;
     p->device_loops = 1;
     p->inner_trace_vcycles = 1;
-    p->persistent_stepI = 1;
+    p->persistent_stepI = 0;
 }
 
 const char *hdg_status_string(hdg_status s) {
