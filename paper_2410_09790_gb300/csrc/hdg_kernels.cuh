@@ -797,6 +797,37 @@ __global__ void k_loop_init(LoopCtl L, const int *stop) {
     cudaGraphSetConditional(L.h, *stop ? 0u : 1u);
 }
 
+// Last block of an Arnoldi step: Hessenberg column (hcol, plus h2 after a second pass), norm
+// hn = ||w||, Givens rotations, residual estimate, step bookkeeping.
+__device__ void gm_finish_step(GmresState *gs, int j, double hn, bool with_h2) {
+    double *Hc = gs->H + j * (GM_M + 1);
+    for (int i = 0; i <= j; ++i) Hc[i] = with_h2 ? gs->hcol[i] + gs->h2[i] : gs->hcol[i];
+    Hc[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {                     // previous rotations
+        double a = Hc[i], b2 = Hc[i + 1];
+        Hc[i] = gs->cs[i] * a + gs->sn[i] * b2;
+        Hc[i + 1] = -gs->sn[i] * a + gs->cs[i] * b2;
+    }
+    double a = Hc[j], b2 = Hc[j + 1];
+    double r = sqrt(a * a + b2 * b2);
+    double c_ = r > 0 ? a / r : 1.0, s_ = r > 0 ? b2 / r : 0.0;
+    gs->cs[j] = c_; gs->sn[j] = s_;
+    Hc[j] = r;
+    Hc[j + 1] = 0.0;
+    gs->g[j + 1] = -s_ * gs->g[j];
+    gs->g[j] = c_ * gs->g[j];
+    gs->resid = fabs(gs->g[j + 1]);
+    gs->total += 1;
+    // keep H[j+1, j] (the norm) for the next v
+    gs->H[j * (GM_M + 1) + j + 1] = hn;            // restored after the rotation (used by k_gm_precond_mf)
+    gs->hcol[GM_M + 1] = hn;
+    gs->j = j + 1;
+    if (!isfinite(gs->resid)) { gs->breakdown = 2; gs->cycle_end = 1; }
+    else if (gs->resid <= gs->rtol * gs->bnorm) { gs->converged = 1; gs->cycle_end = 1; }
+    else if (gs->j >= gs->m || gs->total >= gs->maxit || hn == 0.0) gs->cycle_end = 1;
+}
+
+
 __global__ void k_loop_ctl(LoopCtl L, int limit, const int *stop) {
     wait_prior_kernel();
     const int gd = ++*L.guard;
@@ -860,7 +891,7 @@ __global__ void k_count_stage(DevCount *acc, const GmresState *fgs) {
 // combine in FP64. w must be visible to the whole block (written before a __syncthreads, or an
 // input).
 template <class T, class Ranges>
-__device__ void block_multidot(const RedBuf rb, const T *V, const T *w, long long n, int nvec, Ranges ranges,
+__device__ bool block_multidot(const RedBuf rb, const T *V, const T *w, long long n, int nvec, Ranges ranges,
                                double *out, const T *extra = nullptr) {
     __shared__ int last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -884,7 +915,7 @@ __device__ void block_multidot(const RedBuf rb, const T *V, const T *w, long lon
         last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (!last) return;
+    if (!last) return false;
     __threadfence();
     for (int i = warp; i < nvec; i += nw) {
         double a = 0.0;
@@ -893,6 +924,7 @@ __device__ void block_multidot(const RedBuf rb, const T *V, const T *w, long lon
         if (lane == 0) out[i] = a;
     }
     if (threadIdx.x == 0) *rb.counter = 0u;
+    return true;
 }
 
 // the contiguous row chunk of this block for n rows split over the grid
@@ -919,13 +951,13 @@ __device__ void multidot_rows(const RedBuf rb, const T *V, const T *w, long long
 // blockIdx.x, blockIdx.x + gridDim.x, ... of rows_per_group rows); w was written by this block
 // before the call
 template <class T>
-__device__ void multidot_groups(const RedBuf rb, const T *V, const T *w, long long nrows, long long rows_per_group,
-                                int nvec, double *out) {
+__device__ bool multidot_groups(const RedBuf rb, const T *V, const T *w, long long nrows, long long rows_per_group,
+                                int nvec, double *out, bool with_norm = false) {
     __syncthreads();
-    block_multidot(rb, V, w, nrows, nvec, [&](auto f) {
+    return block_multidot(rb, V, w, nrows, nvec, [&](auto f) {
         for (long long g0 = blockIdx.x * rows_per_group; g0 < nrows; g0 += gridDim.x * rows_per_group)
             f(g0, g0 + rows_per_group < nrows ? g0 + rows_per_group : nrows);
-    }, out);
+    }, out, with_norm ? w : nullptr);
 }
 
 // start of a cycle: w = b - Bx (Bx = B x precomputed; null on the first cycle, x = 0: w = b);
@@ -962,7 +994,7 @@ __global__ void k_gm_start(long long nrows, const double *__restrict__ b, const 
 
 // v_j = w / h (h = beta for j = 0, H[j, j-1] otherwise) -> V_j; z = Binv v_j (cell-local) and z's
 // values at the cell's edge points -> utr (team per cell)
-template <int K, class T>
+template <int K, class T, bool FUSED = false>
 __global__ void k_gm_precond_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ Binv, const T *__restrict__ w,
                                 T *V, T *utr, const GmresState *gs) {
     wait_prior_kernel();
@@ -983,7 +1015,10 @@ __global__ void k_gm_precond_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ B
     T *vj = V + (size_t)j * nrows;
     TFOR(r, NU) {
         const size_t gi = (size_t)cell * NU + r;
-        const T v = w[gi] * inv;
+        T wv = w[gi];
+        if (FUSED)                      // w of step j-1 minus its projections (one Gram-Schmidt pass)
+            for (int i = 0; i < j; ++i) wv -= (T)gs->hcol[i] * V[(size_t)i * nrows + gi];
+        const T v = wv * inv;
         vj[gi] = v;
         vK[r] = v;
     }
@@ -1008,7 +1043,11 @@ __global__ void k_gm_precond_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ B
 
 // w = B z = v_j + (neighbour coupling) z for z = Binv v_j (the diagonal block returns v_j);
 // hcol[i] = (V_i, w), i <= j. Team per cell over groups of cells; grid <= MAX_RED_BLOCKS.
-template <int K, class T>
+// FUSED (FP32 inner solves): the same pass also gives ||w||^2, and the last block finishes the
+// Arnoldi step with the norm of w - V hcol from Pythagoras, ||w||^2 - sum hcol_i^2 (V orthonormal),
+// so that no separate orthogonalisation kernel runs; the next k_gm_precond_mf<.., true> subtracts
+// the projections while it normalises.
+template <int K, class T, bool FUSED = false>
 __global__ void k_gm_apply_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ wq, const T *__restrict__ utr, T *w,
                               const T *__restrict__ V, RedBuf rb, GmresState *gs) {
     wait_prior_kernel();
@@ -1036,7 +1075,18 @@ __global__ void k_gm_apply_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ wq,
             tm.sync();
         }
     }
-    multidot_groups(rb, V, (const T *)w, nrows, (long long)tpb * NU, j + 1, gs->hcol);
+    const bool last = multidot_groups(rb, V, (const T *)w, nrows, (long long)tpb * NU, j + 1, gs->hcol, FUSED);
+    if (FUSED && last) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double h2 = 0.0;
+            for (int i = 0; i <= j; ++i) h2 += gs->hcol[i] * gs->hcol[i];
+            const double ww = gs->hcol[j + 1];
+            const double hn2 = ww - h2;
+            // cancellation guard: a remainder below 1e-12 of ||w||^2 is taken as that floor
+            gm_finish_step(gs, j, sqrt(hn2 > 1e-12 * ww ? hn2 : 1e-12 * ww), false);
+        }
+    }
 }
 
 // w -= V hcol; h2 = (V_i, w)  (second Gram-Schmidt pass); rows in contiguous chunks per block
@@ -1056,36 +1106,6 @@ __global__ void k_gm_orth1(T *w, const T *__restrict__ V, long long nrows, RedBu
     }
     __syncthreads();
     block_multidot(rb, V, (const T *)w, nrows, nvec, [&](auto f) { if (ch.r0 < ch.r1) f(ch.r0, ch.r1); }, gs->h2);
-}
-
-// Last block of an Arnoldi step: Hessenberg column (hcol, plus h2 after a second pass), norm
-// hn = ||w||, Givens rotations, residual estimate, step bookkeeping.
-__device__ void gm_finish_step(GmresState *gs, int j, double hn, bool with_h2) {
-    double *Hc = gs->H + j * (GM_M + 1);
-    for (int i = 0; i <= j; ++i) Hc[i] = with_h2 ? gs->hcol[i] + gs->h2[i] : gs->hcol[i];
-    Hc[j + 1] = hn;
-    for (int i = 0; i < j; ++i) {                     // previous rotations
-        double a = Hc[i], b2 = Hc[i + 1];
-        Hc[i] = gs->cs[i] * a + gs->sn[i] * b2;
-        Hc[i + 1] = -gs->sn[i] * a + gs->cs[i] * b2;
-    }
-    double a = Hc[j], b2 = Hc[j + 1];
-    double r = sqrt(a * a + b2 * b2);
-    double c_ = r > 0 ? a / r : 1.0, s_ = r > 0 ? b2 / r : 0.0;
-    gs->cs[j] = c_; gs->sn[j] = s_;
-    Hc[j] = r;
-    Hc[j + 1] = 0.0;
-    gs->g[j + 1] = -s_ * gs->g[j];
-    gs->g[j] = c_ * gs->g[j];
-    gs->resid = fabs(gs->g[j + 1]);
-    gs->total += 1;
-    // keep H[j+1, j] (the norm) for the next v
-    gs->H[j * (GM_M + 1) + j + 1] = hn;            // restored after the rotation (used by k_gm_precond_mf)
-    gs->hcol[GM_M + 1] = hn;
-    gs->j = j + 1;
-    if (!isfinite(gs->resid)) { gs->breakdown = 2; gs->cycle_end = 1; }
-    else if (gs->resid <= gs->rtol * gs->bnorm) { gs->converged = 1; gs->cycle_end = 1; }
-    else if (gs->j >= gs->m || gs->total >= gs->maxit || hn == 0.0) gs->cycle_end = 1;
 }
 
 // w -= V h2; ||w|| -> H[j+1, j]; Givens rotations; residual estimate. CGS1: single classical

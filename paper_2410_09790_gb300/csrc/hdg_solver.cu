@@ -815,20 +815,22 @@ struct Impl {
     }
 
     // one Arnoldi step of the Step-I GMRES in precision T: V_j, z = Binv V_j (edge values only),
-    // w = B z, dots, orthogonalisation (classical Gram-Schmidt, twice in FP64, once in FP32)
+    // w = B z, dots, orthogonalisation. FP64 (tight solves): classical Gram-Schmidt twice, in two
+    // more kernels. FP32 (inner solves): one pass folded into the two kernels (the norm by
+    // Pythagoras in the product kernel, the subtraction in the next step's preconditioner kernel).
     template <class T>
     static void gmres_arnoldi(hdg_ctx *c, const EdgeTab<T> &E, const T *Binv, const T *wq, T *utr, T *w, T *V) {
         const long long n = c->nQ;
         const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
         const int go = grid_orth(n);
-        launch_k(k_gm_precond_mf<K, T>, cb, 128, sizeof(T) * TEAMS_PER_BLOCK * 2 * NU, c->st, E, c->M, Binv, w, V, utr, c->gs);
-        launch_k(k_gm_apply_mf<K, T>, ab, 128, sizeof(T) * TEAMS_PER_BLOCK * 6 * Dm::NFQ, c->st, E, c->M, wq, utr, w, V,
-                                                                                          c->rb(), c->gs);
-        if (sizeof(T) == sizeof(double)) {        // tight FP64 solves: two Gram-Schmidt passes
+        constexpr bool F = sizeof(T) == sizeof(float);
+        launch_k(k_gm_precond_mf<K, T, F>, cb, 128, sizeof(T) * TEAMS_PER_BLOCK * 2 * NU, c->st, E, c->M, Binv, w, V,
+                 utr, c->gs);
+        launch_k(k_gm_apply_mf<K, T, F>, ab, 128, sizeof(T) * TEAMS_PER_BLOCK * 6 * Dm::NFQ, c->st, E, c->M, wq, utr, w,
+                 V, c->rb(), c->gs);
+        if (!F) {
             launch_k(k_gm_orth1<T>, go, VEC_THREADS, 0, c->st, w, V, n, c->rb(), c->gs);
             launch_k(k_gm_orth2<T>, go, VEC_THREADS, 0, c->st, w, V, n, c->rb(), c->gs);
-        } else {                                  // loose FP32 inner solves: one pass
-            launch_k(k_gm_orth2<T, true>, go, VEC_THREADS, 0, c->st, w, V, n, c->rb(), c->gs);
         }
     }
     static void gmres_arnoldi64(hdg_ctx *c) {
