@@ -219,8 +219,10 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *ctx, hdg_stats *stats);
  * coefficient c around the current state and v = (M Q, 0, 0): 2 = Step-I solve to
  * inner_stepI_rtol, 3 = Step-II (mixed) solve to inner_trace_rtol, 4 = the whole Chorin-split
  * preconditioner, 5 = the stage operator apply. which = 6: the FP32 Arnoldi product of the inner
- * Step-I GMRES (neighbour coupling of B^-1 v_j plus the dots with the basis) at step j = 4,
- * launched alone after one inner solve has filled the basis; bytes = its algorithmic bytes. */
+ * Step-I GMRES (neighbour coupling of B^-1 v_j, the dots with the basis and ||w||, the Givens
+ * step) at step j = 4, launched alone after one inner solve has filled the basis (each launch
+ * after a one-thread kernel that resets the step, whose time is subtracted); bytes = its
+ * algorithmic bytes. */
 hdg_status hdg_time_kernel(hdg_ctx *ctx, int which, double c, int reps, double *ms_per_launch,
                            double *bytes_per_launch);
 
