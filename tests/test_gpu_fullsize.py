@@ -45,8 +45,8 @@ def c2():
     h = HDG(m, K)
     o = Oracle(h)
     ctx = _mod().Context(N, K, periodic_x=True, tableau='ARS343', dt=DT, n_richardson=0, stage_krylov=1,
-                         richardson_rtol=1e-10, richardson_max=600, inner_stepI_rtol=1e-1, inner_trace_rtol=1e-1,
-                         trace_rtol=1e-12, stepI_rtol=1e-10)
+                         richardson_rtol=1e-10, richardson_max=600, inner_stepI_rtol=2e-2, inner_trace_rtol=1e-1,
+                         inner_trace_vcycles=1, trace_rtol=1e-12, stepI_rtol=1e-10)
     Q0 = W.nodal_velocity(N, K, lambda x, y: W.shear_layer(x, y, 0.05, 1e-3), noise=1e-4, seed=0)
     ctx.hdg_set_state(_cuda(Q0))
     ctx.hdg_div_free_project()
