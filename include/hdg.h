@@ -110,6 +110,12 @@ typedef struct {
      * bounded grid-wide barriers (same algorithm; slower on GB300 at the bench size: the barriers
      * cost more than the kernel boundaries they replace). */
     int persistent_stepI;
+    /* The one-V-cycle Step II inside the stage preconditioner (inner_trace_vcycles = 1): 1
+     * (default) = the V-cycle in FP32 (operators rounded once per stage coefficient; the P1
+     * levels in one thread block), used when the P1 hierarchy fits that block's shared memory
+     * (vertices of all levels <= 12,800); 0 = the FP64 V-cycle. The outer iteration's tolerance
+     * is unchanged: this only alters the preconditioner. */
+    int inner_trace_fp32;
 } hdg_params;
 
 typedef struct {
@@ -222,7 +228,9 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *ctx, hdg_stats *stats);
  * Step-I GMRES (neighbour coupling of B^-1 v_j, the dots with the basis and ||w||, the Givens
  * step) at step j = 4, launched alone after one inner solve has filled the basis (each launch
  * after a one-thread kernel that resets the step, whose time is subtracted); bytes = its
- * algorithmic bytes. */
+ * algorithmic bytes. which = 7 (bytes = 0): the preconditioner's Step II as the stage solves run it
+ * (FP32 cell maps, then the inner trace solve: one V-cycle, in FP32 when inner_trace_fp32 is on),
+ * recorded and replayed like 2..5. */
 hdg_status hdg_time_kernel(hdg_ctx *ctx, int which, double c, int reps, double *ms_per_launch,
                            double *bytes_per_launch);
 

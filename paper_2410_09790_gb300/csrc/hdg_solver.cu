@@ -20,6 +20,7 @@
 #include "../../include/hdg.h"
 #include "hdg_kernels.cuh"
 #include "hdg_mg_kernels.cuh"
+#include "hdg_mg32.cuh"
 #include "hdg_stepI_persistent.cuh"
 #include "mesh.h"
 #include "refelem.h"
@@ -107,6 +108,11 @@ struct CondCache {
     double *Minv = nullptr;
     int Nc = 0;
     float *Lrhs32 = nullptr, *Lbs32 = nullptr;             // preconditioner Step-II maps (FP32)
+    // FP32 copy of the multigrid for the preconditioner's one-V-cycle Step II (hdg_mg32.cuh)
+    bool mg32 = false;
+    float *Sell32 = nullptr, *Dinv32 = nullptr, *Minv32 = nullptr;
+    std::vector<float *> A32, dinv32;
+    size_t tail32_smem = 0;
 };
 
 struct MGWork {                // per-level work vectors (shared by all coefficients)
@@ -179,6 +185,7 @@ struct hdg_ctx {
     // multigrid work
     std::vector<MGWork> mgw;
     double *txa = nullptr, *td = nullptr, *tt = nullptr, *cellA = nullptr, *mgB = nullptr;
+    float *tb32 = nullptr, *tr32 = nullptr, *tx32 = nullptr, *txa32 = nullptr, *td32 = nullptr, *tt32 = nullptr;
     unsigned long long *dlmax = nullptr;
     // reductions
     double *partials = nullptr;
@@ -766,9 +773,81 @@ struct Impl {
 
     // FP32 cell maps of the preconditioner's Step II for coefficient cc (formed once, outside
     // graph captures)
+    // FP32 copy of the trace multigrid of coefficient E.c for the one-V-cycle inner Step II; left
+    // out (FP64 V-cycle) when the P1 hierarchy's vectors do not fit one block's shared memory
+    static void build_mg32(hdg_ctx *c, CondCache &E) {
+        const int L = (int)E.lv.size();
+        if (L < 1 || L > MG_MAX_LEVELS) return;
+        P1Grid G[MG_MAX_LEVELS];
+        for (int l = 0; l < L; ++l) G[l] = E.lv[l].G;
+        const size_t smem = sizeof(float) * tail32_floats(G, L);
+        if (smem > (size_t)200 * 1024) return;
+        auto f32 = [&](const double *a, long long n) {
+            float *b = c->alloc<float>((size_t)n);
+            launch_k(k_f64_to_f32, grid_for(n), VEC_THREADS, 0, c->st, a, b, n);
+            return b;
+        };
+        E.Sell32 = f32(E.Sell, 5LL * NT * c->nL);
+        E.Dinv32 = f32(E.Dinv, (long long)NT * c->nL);
+        E.A32.resize(L);
+        E.dinv32.resize(L);
+        for (int l = 0; l < L; ++l) {
+            E.A32[l] = f32(E.lv[l].A, (long long)P1_NS * G[l].nverts);
+            E.dinv32[l] = f32(E.lv[l].dinv, G[l].nverts);
+        }
+        E.Minv32 = f32(E.Minv, (long long)E.Nc * E.Nc);
+        CKL();
+        if (!c->tb32) {
+            c->tb32 = c->alloc<float>(c->nL); c->tr32 = c->alloc<float>(c->nL); c->tx32 = c->alloc<float>(c->nL);
+            c->txa32 = c->alloc<float>(c->nL); c->td32 = c->alloc<float>(c->nL); c->tt32 = c->alloc<float>(c->nL);
+        }
+        CK(cudaFuncSetAttribute(k_tv_tail<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        E.tail32_smem = smem;
+        E.mg32 = true;
+    }
+
+    static Tail32 tail32_params(hdg_ctx *c, const CondCache &E) {
+        Tail32 T{};
+        T.L = (int)E.lv.size();
+        T.Nc = E.Nc;
+        T.nfacets = (int)c->nfacets;
+        int off = 0;
+        for (int l = 0; l < T.L; ++l) {
+            T.G[l] = E.lv[l].G; T.A[l] = E.A32[l]; T.dinv[l] = E.dinv32[l];
+            T.invth[l] = (float)E.lv[l].invth; T.c1[l] = (float)E.lv[l].c1; T.c2[l] = (float)E.lv[l].c2;
+            T.off[l] = off;
+            off += 4 * E.lv[l].G.nverts;
+        }
+        T.Minv = E.Minv32;
+        T.vert_facet = c->M.vert_facet; T.vert_fsign = c->M.vert_fsign; T.facet_vert = c->M.facet_vert;
+        T.tres = c->tt32;
+        T.z = c->tx32;
+        return T;
+    }
+
+    // Inner Step II's trace solve as one FP32 V-cycle: right-hand side gathered from the cells'
+    // lambda rows (c->vK) minus sub, result (FP64) in out
+    static void trace_vcycle32(hdg_ctx *c, const CondCache &E, const double *sub, double *out) {
+        const int nf = (int)c->nfacets;
+        const unsigned gb = tv_blocks(nf, TGrp<NT>::G);
+        const TraceOp32 T{E.Sell32, E.Dinv32, E.tcol, nf};
+        const float invth = (float)E.t_invth, c1 = (float)E.t_c1, c2 = (float)E.t_c2;
+        launch_k(k_tv_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, sub, c->tb32, c->rb(), c->sc,
+                                                                  c->capturing ? c->dcnt : nullptr);
+        launch_k(k_tv_cheb01<NT>, gb, 128, 0, c->st, T, c->tb32, c->sc, invth, c1, c2, c->tr32, c->tx32, c->td32);
+        launch_k(k_tv_resid<NT>, gb, 128, 0, c->st, T, c->tr32, c->tx32, c->tt32);
+        launch_k(k_tv_tail<NT>, 1, 1024, E.tail32_smem, c->st, tail32_params(c, E));
+        launch_k(k_tv_cheb<NT>, gb, 128, 0, c->st, T, c->tr32, c->tx32, c->txa32, c->td32, 0.f, invth, (double *)nullptr);
+        launch_k(k_tv_cheb<NT>, gb, 128, 0, c->st, T, c->tr32, c->txa32, (float *)nullptr, c->td32, c1, c2, out);
+        CKL();
+        if (!c->capturing) c->S.trace_solves += 1;
+    }
+
     static void ensure_pre_maps(hdg_ctx *c, double cc) {
         CondCache &E = condense(c, cc);
-        if (E.Lrhs32 || c->capturing) return;
+        if (c->capturing) return;
+        if (c->P.inner_trace_fp32 && E.mg && !E.mg32) build_mg32(c, E);
+        if (E.Lrhs32) return;
         E.Lrhs32 = c->alloc<float>((size_t)c->ncells * (NU + NP) * (NL + NP));
         E.Lbs32 = c->alloc<float>((size_t)c->ncells * (NP + NL) * (NU + NP));
         constexpr int SCR = NU + NP + NL + NP + (NL + 4 * MU + NP + NL) + NU + NP + (NL + NP);
@@ -1061,34 +1140,45 @@ struct Impl {
         CKL();
     }
 
-    // Chorin split as a preconditioner: z = P^{-1} v (Step I, then Step II on the constraint rows)
-    static void chorin_precond(hdg_ctx *c, double cc, const double *v, double *z) {
-        const double *vQ = v, *vp = v + c->nQ, *vl = v + c->nQ + c->nPv;
-        double *zQ = z, *zp = z + c->nQ, *zl = z + c->nQ + c->nPv;
-        double *Qbar = c->q[2], *U = c->q[4];
-        stepI_solve(c, vQ, Qbar, c->P.inner_stepI_rtol);
+    // Step II of the stage preconditioner: from the Step-I velocity X and the constraint rows
+    // (vp, vl) of the input, the velocity correction U and (zp, zl)
+    static void pre_step2(hdg_ctx *c, double cc, const double *X, const double *vp, const double *vl, double *U,
+                          double *zp, double *zl) {
         c->trace_vcycles = c->P.inner_trace_vcycles;
         try {
             CondCache &E = condense(c, cc);
             if (E.Lrhs32) {             // Step II from the precomputed FP32 cell maps
                 CompTimer tm_(c, &c->S.ms_trace);
                 const unsigned nb = cell_blocks(c);
-                launch_k(k_pre_rhs<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (NU + NP), c->st, c->M, E.Lrhs32, Qbar, vp,
+                launch_k(k_pre_rhs<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (NU + NP), c->st, c->M, E.Lrhs32, X, vp,
                                                                                             c->vK, c->wK);
-                launch_k(k_facet_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, vl, c->tb);
-                CKL();
-                trace_solve(c, E, c->tb, zl, c->P.inner_trace_rtol);
+                if (E.mg32 && c->P.inner_trace_fp32 && c->trace_vcycles == 1) {
+                    trace_vcycle32(c, E, vl, zl);
+                } else {
+                    launch_k(k_facet_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, vl, c->tb);
+                    CKL();
+                    trace_solve(c, E, c->tb, zl, c->P.inner_trace_rtol);
+                }
                 launch_k(k_pre_backsub<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (NP + NL), c->st, c->M, E.Lbs32, c->wK,
                                                                                                 zl, U, zp);
                 CKL();
             } else {
-                mixed_solve(c, cc, nullptr, Qbar, nullptr, nullptr, U, zp, zl, vp, vl, c->P.inner_trace_rtol);
+                mixed_solve(c, cc, nullptr, X, nullptr, nullptr, U, zp, zl, vp, vl, c->P.inner_trace_rtol);
             }
         } catch (...) {
             c->trace_vcycles = 0;
             throw;
         }
         c->trace_vcycles = 0;
+    }
+
+    // Chorin split as a preconditioner: z = P^{-1} v (Step I, then Step II on the constraint rows)
+    static void chorin_precond(hdg_ctx *c, double cc, const double *v, double *z) {
+        const double *vQ = v, *vp = v + c->nQ, *vl = v + c->nQ + c->nPv;
+        double *zQ = z, *zp = z + c->nQ, *zl = z + c->nQ + c->nPv;
+        double *Qbar = c->q[2], *U = c->q[4];
+        stepI_solve(c, vQ, Qbar, c->P.inner_stepI_rtol);
+        pre_step2(c, cc, Qbar, vp, vl, U, zp, zl);
         LinComb L{};
         L.nterms = 2; L.coef[0] = 1; L.vec[0] = Qbar; L.coef[1] = 1; L.vec[1] = U;
         launch_k(k_lincomb, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->geo, NU, L, zQ, c->ncells);
@@ -1467,6 +1557,7 @@ void hdg_default_params(hdg_params *p) {
     p->device_loops = 1;
     p->inner_trace_vcycles = 1;
     p->persistent_stepI = 0;
+    p->inner_trace_fp32 = 1;
 }
 
 const char *hdg_status_string(hdg_status s) {
@@ -1954,7 +2045,7 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *c, hdg_stats *stats) {
 }
 
 hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *ms, double *bytes) {
-    if (!c || reps < 1 || !ms || !bytes || which < 0 || which > 6 || (which != 1 && !(cc > 0)))
+    if (!c || reps < 1 || !ms || !bytes || which < 0 || which > 7 || (which != 1 && !(cc > 0)))
         return HDG_ERR_INVALID_ARG;
     if (which >= 2 && !c->fv) return HDG_ERR_INVALID_ARG;
     try {
@@ -2013,6 +2104,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 I::bdm(c, c->Q, c->q[5]);
                 I::assemble_stepI(c, c->q[5], cc, I::inv_for(c->P.inner_stepI_rtol));
                 I::condense(c, cc);
+                I::ensure_pre_maps(c, cc);
                 I::mass(c, c->Q, c->fv, 0);
                 const long long N = c->nQ + c->nPv + c->nL;
                 CK(cudaMemsetAsync(c->fv + c->nQ, 0, 8 * (N - c->nQ), c->st));
@@ -2022,6 +2114,9 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                         I::mixed_solve(c, cc, nullptr, c->fv, nullptr, nullptr, c->q[4], c->fz + c->nQ,
                                        c->fz + c->nQ + c->nPv, nullptr, nullptr, c->P.inner_trace_rtol);
                     else if (which == 4) I::chorin_precond(c, cc, c->fv, c->fz);
+                    else if (which == 7)
+                        I::pre_step2(c, cc, c->fv, c->fv + c->nQ, c->fv + c->nQ + c->nPv, c->q[4], c->fz + c->nQ,
+                                     c->fz + c->nQ + c->nPv);
                     else I::stage_apply(c, cc, c->fv, c->fw);
                 });
                 CK(cudaGraphLaunch(ex, c->st));

@@ -226,6 +226,30 @@ def test_persistent_inner_step_i_matches_kernel_sequence():
         assert st['status'] == 0 and st['stepI_solves'] > 0 and st['stepI_iters'] >= st['stepI_solves']
 
 
+@pytest.mark.parametrize('n,px,k', [(8, True, 1), (8, True, 2), (8, True, 3), (8, True, 4), (16, False, 3),
+                                    (3, True, 2)])
+def test_inner_trace_vcycle_fp32_matches_fp64(n, px, k):
+    # the preconditioner's one-V-cycle Step II in FP32 (group widths 2, 4, 4, 8 for k = 1..4; one to
+    # three P1 levels) changes only the preconditioner: both runs meet the same stage tolerance,
+    # agree to it, and need about as many outer iterations
+    Q0 = W.nodal_velocity(n, k, lambda x, y: W.shear_layer(x, y, width=0.1, amp=0.05), noise=1e-3, seed=8)
+    outs, stats = [], []
+    for f32 in (0, 1):
+        ctx = H().Context(n, k, periodic_x=px, tableau='ARS343', dt=0.01, n_richardson=0, stage_krylov=1,
+                          richardson_rtol=1e-12, richardson_max=400, inner_trace_fp32=f32)
+        ctx.hdg_set_state(cuda(Q0))
+        ctx.hdg_reconstruct_pressure()
+        stats.append(ctx.hdg_imex_step(2))
+        outs.append([host(x) for x in ctx.hdg_get_state()[:3]])
+        ctx.close()
+    assert_close(outs[1][0], outs[0][0], 1e-10, 'Q')
+    assert_close(outs[1][1], outs[0][1], 1e-9, 'p')
+    for st in stats:
+        assert st['status'] == 0 and st['trace_solves'] > 0
+    it64, it32 = stats[0]['richardson_iters'], stats[1]['richardson_iters']
+    assert it32 <= 1.1 * it64 + 3, (it32, it64)
+
+
 @pytest.mark.parametrize('n,px', [(16, True), (32, False)])
 def test_multigrid_iterations_mesh_robust(n, px):
     # the V-cycle preconditioner keeps the trace CG iteration count small and nearly independent
