@@ -113,7 +113,8 @@ typedef struct {
     /* The one-V-cycle Step II inside the stage preconditioner (inner_trace_vcycles = 1): 1
      * (default) = the V-cycle in FP32 (operators rounded once per stage coefficient; the P1
      * levels in one thread block), used when the P1 hierarchy fits that block's shared memory
-     * (vertices of all levels <= 12,800); 0 = the FP64 V-cycle. The outer iteration's tolerance
+     * (5 floats per vertex of the mesh, 12 per vertex of the coarser levels, <= 200 KiB in all:
+     * meshes up to 64 x 64 cells); 0 = the FP64 V-cycle. The outer iteration's tolerance
      * is unchanged: this only alters the preconditioner. */
     int inner_trace_fp32;
 } hdg_params;

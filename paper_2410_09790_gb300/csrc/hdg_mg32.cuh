@@ -156,35 +156,16 @@ __global__ void k_tv_cheb(TraceOp32 T, const float *__restrict__ r, const float 
 }
 
 // ---------------------------------------------------------------- P1 levels in one block
-// Neighbour of grid point (i, j) at offset (di, dj), |di|, |dj| <= 1: vertex id, or -1 outside
-// a non-periodic grid (no division: the offsets are one step)
-__device__ __forceinline__ int p1_nb32(const P1Grid &G, int i, int j, int di, int dj) {
-    i += di; j += dj;
-    if (i < 0) { if (!G.px) return -1; i += G.nvx; }
-    else if (i >= G.nvx) { if (!G.px) return -1; i -= G.nvx; }
-    if (j < 0) { if (!G.py) return -1; j += G.nvy; }
-    else if (j >= G.nvy) { if (!G.py) return -1; j -= G.nvy; }
-    return j * G.nvx + i;
-}
-
-// (A x)(v) for the 7-point stencil (entries of missing neighbours are zero)
-__device__ __forceinline__ float p1_apply32(const P1Grid &G, const float *__restrict__ A, int v, int i, int j,
-                                            const float *x) {
-    float s = 0.f;
-#pragma unroll
-    for (int o = 0; o < P1_NS; ++o) {
-        const int w = p1_nb32(G, i, j, p1_di(o), p1_dj(o));
-        if (w >= 0) s += __ldg(&A[P1_NS * v + o]) * x[w];
-    }
-    return s;
-}
-
+// Shared-memory layout of P1 level l (l = 0: the mesh vertices) at off[l]: b, xa, xb, d, dinv (nv
+// floats each), then for l >= 1 the stencil A (7 nv floats, by vertex); the stencil of level 0
+// is read from global memory. Threads take the points of a level as rows of nvx columns, so a
+// thread's column and its neighbours' columns are fixed and rows step without a division.
 struct Tail32 {
     int L, Nc, nfacets;
     P1Grid G[MG_MAX_LEVELS];
     const float *A[MG_MAX_LEVELS], *dinv[MG_MAX_LEVELS];
     float invth[MG_MAX_LEVELS], c1[MG_MAX_LEVELS], c2[MG_MAX_LEVELS];
-    int off[MG_MAX_LEVELS];        // shared-memory offset (floats) of the level's 4 vectors b, xa, xb, d
+    int off[MG_MAX_LEVELS];
     const float *Minv;             // coarsest grid: (A + 1 1^T / N)^{-1}, row-major
     const int *vert_facet, *vert_fsign, *facet_vert;
     const float *tres;             // trace residual t
@@ -194,20 +175,91 @@ struct Tail32 {
 // shared floats the tail needs for the grids G[0..L-1]
 inline size_t tail32_floats(const P1Grid *G, int L) {
     size_t n = 0;
-    for (int l = 0; l < L; ++l) n += 4 * (size_t)G[l].nverts;
+    for (int l = 0; l < L; ++l) n += (size_t)(l >= 1 ? 12 : 5) * G[l].nverts;
     return n;
 }
 
-#define TAIL_FOR(v_, n_) for (int v_ = threadIdx.x; v_ < (n_); v_ += blockDim.x)
+// index k + one step on a line of n points: wrapped when periodic, -1 outside otherwise
+__device__ __forceinline__ int step1(int k, int n, int per) {
+    return k < 0 ? (per ? k + n : -1) : (k >= n ? (per ? k - n : -1) : k);
+}
+
+// A level seen by the tail: vectors in shared memory, threads laid out as rows of nvx
+struct TLevel {
+    int nvx, nvy, px, py, nv;
+    float *b, *xa, *xb, *d, *dv;
+    const float *A;
+    float invth, c1, c2;
+};
+
+__device__ __forceinline__ TLevel tail_level(const Tail32 &T, float *tsm, int l) {
+    TLevel V;
+    const P1Grid &G = T.G[l];
+    V.nvx = G.nvx; V.nvy = G.nvy; V.px = G.px; V.py = G.py; V.nv = G.nverts;
+    V.b = tsm + T.off[l]; V.xa = V.b + V.nv; V.xb = V.xa + V.nv; V.d = V.xb + V.nv; V.dv = V.d + V.nv;
+    V.A = l >= 1 ? V.dv + V.nv : T.A[0];
+    V.invth = T.invth[l]; V.c1 = T.c1[l]; V.c2 = T.c2[l];
+    return V;
+}
+
+// the 7 stencil points of (i, j) in the order of P1_NS; absent neighbours (non-periodic edges)
+// are replaced by the point itself, whose stencil entry for that offset is zero
+struct Stencil {
+    int p[P1_NS];
+};
+
+__device__ __forceinline__ Stencil stencil(const TLevel &V, int i, int j, int ip, int im) {
+    const int jp = step1(j + 1, V.nvy, V.py), jm = step1(j - 1, V.nvy, V.py);
+    const int c = j * V.nvx + i;
+    Stencil S;
+    S.p[0] = c;
+    S.p[1] = ip >= 0 ? j * V.nvx + ip : c;
+    S.p[2] = im >= 0 ? j * V.nvx + im : c;
+    S.p[3] = jp >= 0 ? jp * V.nvx + i : c;
+    S.p[4] = jm >= 0 ? jm * V.nvx + i : c;
+    S.p[5] = ip >= 0 && jp >= 0 ? jp * V.nvx + ip : c;
+    S.p[6] = im >= 0 && jm >= 0 ? jm * V.nvx + im : c;
+    return S;
+}
+
+__device__ __forceinline__ float apply_st(const TLevel &V, const Stencil &S, const float *x, bool gA) {
+    const float *a = V.A + P1_NS * S.p[0];
+    float s = 0.f;
+#pragma unroll
+    for (int o = 0; o < P1_NS; ++o) s += (gA ? __ldg(a + o) : a[o]) * x[S.p[o]];
+    return s;
+}
+
+// loop over the level's points, threads as rows of nvx columns (nvx <= blockDim.x)
+#define TL_FOR(V, ...)                                                                       \
+    {                                                                                        \
+        const int rows_ = (int)blockDim.x / (V).nvx;                                         \
+        const int i = (int)threadIdx.x % (V).nvx, j0_ = (int)threadIdx.x / (V).nvx;          \
+        const int ip = step1(i + 1, (V).nvx, (V).px), im = step1(i - 1, (V).nvx, (V).px);    \
+        (void)ip; (void)im;                                                                  \
+        if (j0_ < rows_)                                                                     \
+            for (int j = j0_; j < (V).nvy; j += rows_) {                                     \
+                const int v = j * (V).nvx + i;                                               \
+                __VA_ARGS__                                                                  \
+            }                                                                                \
+    }
 
 template <int NT>
 __global__ void __launch_bounds__(1024) k_tv_tail(Tail32 T) {
     wait_prior_kernel();
     extern __shared__ float tsm[];
+    const int tid = threadIdx.x, nth = blockDim.x;
     const float s3 = 0.28867513459481288225f;              // 1 / (2 sqrt 3)
+    for (int l = 0; l < T.L; ++l) {                        // diagonals, and the stencils of l >= 1
+        const int nv = T.G[l].nverts;
+        float *dv = tsm + T.off[l] + 4 * nv;
+        for (int v = tid; v < nv; v += nth) dv[v] = __ldg(&T.dinv[l][v]);
+        if (l >= 1)
+            for (int q = tid; q < P1_NS * nv; q += nth) dv[nv + q] = __ldg(&T.A[l][q]);
+    }
     {   // b_1 = P^T t: a facet gives 0.5 t_0 +- t_1 / (2 sqrt 3) to each of its vertices
         float *b = tsm + T.off[0];
-        TAIL_FOR(v, T.G[0].nverts) {
+        for (int v = tid; v < T.G[0].nverts; v += nth) {
             float s = 0.f;
             for (int q = 0; q < 6; ++q) {
                 const int f = __ldg(&T.vert_facet[6 * v + q]);
@@ -219,98 +271,100 @@ __global__ void __launch_bounds__(1024) k_tv_tail(Tail32 T) {
         }
     }
     __syncthreads();
-    for (int l = 0; l < T.L - 1; ++l) {                    // down: two Chebyshev steps, restrict
-        const P1Grid G = T.G[l];
-        const float *A = T.A[l], *dv = T.dinv[l];
-        float *b = tsm + T.off[l], *xa = b + G.nverts, *xb = xa + G.nverts, *d = xb + G.nverts;
-        const float invth = T.invth[l], c1 = T.c1[l], c2 = T.c2[l];
-        TAIL_FOR(v, G.nverts) {
-            const float s = __ldg(&dv[v]) * b[v] * invth;
-            d[v] = s;
-            xa[v] = s;
-        }
-        __syncthreads();
-        TAIL_FOR(v, G.nverts) {
-            const int i = v % G.nvx, j = v / G.nvx;
-            const float dn = c1 * d[v] + c2 * __ldg(&dv[v]) * (b[v] - p1_apply32(G, A, v, i, j, xa));
-            d[v] = dn;
-            xb[v] = xa[v] + dn;
-        }
-        __syncthreads();
-        TAIL_FOR(v, G.nverts) {                             // residual into d (not needed again)
-            const int i = v % G.nvx, j = v / G.nvx;
-            d[v] = b[v] - p1_apply32(G, A, v, i, j, xb);
-        }
-        __syncthreads();
-        const P1Grid Gc = T.G[l + 1];
-        float *bc = tsm + T.off[l + 1];
-        TAIL_FOR(V, Gc.nverts) {                            // (I^T r)(V), I = linear interpolation
-            const int I = V % Gc.nvx, J = V / Gc.nvx;
-            float s = 0.f;
+    for (int l = 0; l < T.L - 1; ++l) {                    // down
+        const TLevel V = tail_level(T, tsm, l);
+        const bool gA = l == 0;
+        // two Chebyshev steps from 0: x0 = invth D^-1 b (formed at the stencil points), then
+        // d = c1 x0 + c2 D^-1 (b - A x0), xb = x0 + d
+        TL_FOR(V, {
+            const Stencil S = stencil(V, i, j, ip, im);
+            const float *a = V.A + P1_NS * v;
+            float ax = 0.f;
 #pragma unroll
             for (int o = 0; o < P1_NS; ++o) {
-                const int a = p1_nb32(G, 2 * I, 2 * J, p1_di(o), p1_dj(o));
-                if (a >= 0) s += (o == 0 ? 1.f : 0.5f) * d[a];
+                const int w = S.p[o];
+                ax += (gA ? __ldg(a + o) : a[o]) * (V.invth * V.dv[w] * V.b[w]);
             }
-            bc[V] = s;
-        }
+            const float x0 = V.invth * V.dv[v] * V.b[v];
+            const float dn = V.c1 * x0 + V.c2 * V.dv[v] * (V.b[v] - ax);
+            V.d[v] = dn;
+            V.xb[v] = x0 + dn;
+        })
+        __syncthreads();
+        TL_FOR(V, {                                        // residual, kept in xa
+            const Stencil S = stencil(V, i, j, ip, im);
+            V.xa[v] = V.b[v] - apply_st(V, S, V.xb, gA);
+        })
+        __syncthreads();
+        const TLevel C = tail_level(T, tsm, l + 1);
+        TL_FOR(C, {                                        // (I^T r)(V): fine points 2I + o
+            const int fi = 2 * i, fj = 2 * j;
+            const int fip = step1(fi + 1, V.nvx, V.px), fim = step1(fi - 1, V.nvx, V.px);
+            const Stencil S = stencil(V, fi, fj, fip, fim);
+            float s = V.xa[S.p[0]];
+            const int fjp = step1(fj + 1, V.nvy, V.py), fjm = step1(fj - 1, V.nvy, V.py);
+            const bool has[P1_NS] = {true, fip >= 0, fim >= 0, fjp >= 0, fjm >= 0, fip >= 0 && fjp >= 0,
+                                     fim >= 0 && fjm >= 0};
+#pragma unroll
+            for (int o = 1; o < P1_NS; ++o) s += has[o] ? 0.5f * V.xa[S.p[o]] : 0.f;
+            C.b[v] = s;
+        })
         __syncthreads();
     }
     {   // coarsest: x = Minv (b - mean b)
+        const TLevel V = tail_level(T, tsm, T.L - 1);
         const int N = T.Nc;
-        float *b = tsm + T.off[T.L - 1], *xb = b + 2 * N;
         __shared__ float part[32];
         __shared__ float mean;
         float s = 0.f;
-        TAIL_FOR(v, N) s += b[v];
+        for (int v = tid; v < N; v += nth) s += V.b[v];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+        if ((tid & 31) == 0) part[tid >> 5] = s;
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             float m = 0.f;
-            for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) m += part[w];
+            for (int w = 0; w < (nth + 31) / 32; ++w) m += part[w];
             mean = m / N;
         }
         __syncthreads();
-        TAIL_FOR(v, N) {
+        for (int v = tid; v < N; v += nth) {
             float acc = 0.f;
-            for (int c = 0; c < N; ++c) acc += __ldg(&T.Minv[(size_t)v * N + c]) * (b[c] - mean);
-            xb[v] = acc;
+            for (int c = 0; c < N; ++c) acc += __ldg(&T.Minv[(size_t)v * N + c]) * (V.b[c] - mean);
+            V.xb[v] = acc;
         }
         __syncthreads();
     }
-    for (int l = T.L - 2; l >= 0; --l) {                   // up: prolong, two Chebyshev steps
-        const P1Grid G = T.G[l], Gc = T.G[l + 1];
-        const float *A = T.A[l], *dv = T.dinv[l];
-        float *b = tsm + T.off[l], *xa = b + G.nverts, *xb = xa + G.nverts, *d = xb + G.nverts;
-        const float *ec = tsm + T.off[l + 1] + 2 * Gc.nverts;
-        const float invth = T.invth[l], c1 = T.c1[l], c2 = T.c2[l];
-        TAIL_FOR(a, G.nverts) {                             // xb += I e (linear interpolation)
-            const int i = a % G.nvx, j = a / G.nvx, i0 = i >> 1, j0 = j >> 1;
-            const int oi = i & 1, oj = j & 1;
-            float e = ec[p1_nb32(Gc, i0, j0, 0, 0)];
-            if (oi || oj) e = 0.5f * (e + ec[p1_nb32(Gc, i0, j0, oi, oj)]);
-            xb[a] += e;
-        }
+    for (int l = T.L - 2; l >= 0; --l) {                   // up
+        const TLevel V = tail_level(T, tsm, l), C = tail_level(T, tsm, l + 1);
+        const bool gA = l == 0;
+        TL_FOR(V, {                                        // xb += I e (linear interpolation)
+            const int i0 = i >> 1, j0 = j >> 1, oi = i & 1, oj = j & 1;
+            float e = C.xb[j0 * C.nvx + i0];
+            if (oi || oj) {
+                const int in = oi ? step1(i0 + 1, C.nvx, C.px) : i0, jn = oj ? step1(j0 + 1, C.nvy, C.py) : j0;
+                e = 0.5f * (e + C.xb[jn * C.nvx + in]);
+            }
+            V.xb[v] += e;
+        })
         __syncthreads();
-        TAIL_FOR(v, G.nverts) {
-            const int i = v % G.nvx, j = v / G.nvx;
-            const float dn = invth * __ldg(&dv[v]) * (b[v] - p1_apply32(G, A, v, i, j, xb));
-            d[v] = dn;
-            xa[v] = xb[v] + dn;
-        }
+        TL_FOR(V, {
+            const Stencil S = stencil(V, i, j, ip, im);
+            const float dn = V.invth * V.dv[v] * (V.b[v] - apply_st(V, S, V.xb, gA));
+            V.d[v] = dn;
+            V.xa[v] = V.xb[v] + dn;
+        })
         __syncthreads();
-        TAIL_FOR(v, G.nverts) {
-            const int i = v % G.nvx, j = v / G.nvx;
-            const float dn = c1 * d[v] + c2 * __ldg(&dv[v]) * (b[v] - p1_apply32(G, A, v, i, j, xa));
-            d[v] = dn;
-            xb[v] = xa[v] + dn;
-        }
+        TL_FOR(V, {
+            const Stencil S = stencil(V, i, j, ip, im);
+            const float dn = V.c1 * V.d[v] + V.c2 * V.dv[v] * (V.b[v] - apply_st(V, S, V.xa, gA));
+            V.d[v] = dn;
+            V.xb[v] = V.xa[v] + dn;
+        })
         __syncthreads();
     }
     {   // z += P e_1: components 0 and 1 of each facet from its two vertices
-        const float *e1 = tsm + T.off[0] + 2 * T.G[0].nverts;
-        TAIL_FOR(f, T.nfacets) {
+        const float *e1 = tail_level(T, tsm, 0).xb;
+        for (int f = tid; f < T.nfacets; f += nth) {
             const float a = e1[__ldg(&T.facet_vert[2 * f])], bb = e1[__ldg(&T.facet_vert[2 * f + 1])];
             T.z[(size_t)f * NT] += 0.5f * (a + bb);
             T.z[(size_t)f * NT + 1] += s3 * (bb - a);

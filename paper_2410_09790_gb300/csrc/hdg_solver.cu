@@ -782,6 +782,8 @@ struct Impl {
         for (int l = 0; l < L; ++l) G[l] = E.lv[l].G;
         const size_t smem = sizeof(float) * tail32_floats(G, L);
         if (smem > (size_t)200 * 1024) return;
+        for (int l = 0; l < L; ++l)
+            if (G[l].nvx > 1024) return;
         auto f32 = [&](const double *a, long long n) {
             float *b = c->alloc<float>((size_t)n);
             launch_k(k_f64_to_f32, grid_for(n), VEC_THREADS, 0, c->st, a, b, n);
@@ -816,7 +818,7 @@ struct Impl {
             T.G[l] = E.lv[l].G; T.A[l] = E.A32[l]; T.dinv[l] = E.dinv32[l];
             T.invth[l] = (float)E.lv[l].invth; T.c1[l] = (float)E.lv[l].c1; T.c2[l] = (float)E.lv[l].c2;
             T.off[l] = off;
-            off += 4 * E.lv[l].G.nverts;
+            off += (l >= 1 ? 12 : 5) * E.lv[l].G.nverts;
         }
         T.Minv = E.Minv32;
         T.vert_facet = c->M.vert_facet; T.vert_fsign = c->M.vert_fsign; T.facet_vert = c->M.facet_vert;
