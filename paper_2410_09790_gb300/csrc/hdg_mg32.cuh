@@ -5,9 +5,11 @@
 // the coarsest grid — with operators rounded to FP32 once per stage coefficient. In six kernels:
 //   k_tv_gather  : b = (sum of the cells' lambda-row contributions) - v_lambda, mean of b_0
 //   k_tv_cheb01  : r = b - mean e0; the first two Chebyshev steps from x = 0
-//   k_tv_resid   : t = r - S x
-//   k_tv_tail    : one block: t -> P1 level 1, the whole P1 hierarchy in shared memory, x += P e
-//   k_tv_cheb x2 : the two post-smoothing steps; the last writes the FP64 result
+//   k_tv_restrict: b_1 = P^T (r - S x) at the mesh vertices (rows 0 and 1 of the residual at
+//                  the vertex's facets, a 16-lane group per vertex)
+//   k_tv_tail    : one block: the whole P1 hierarchy in shared memory, e_1 out
+//   k_tv_cheb x2 : the two post-smoothing steps (the first from x + P e_1, formed on the fly;
+//                  the last writes the FP64 result)
 // A trace-level thread owns one row (facet f, component i) and works in a group of G lanes per
 // facet (G = NT rounded up to a power of two), so the facet block-Jacobi product is a
 // shuffle within the group. GB300's FP32 rate is 64x its FP64 rate: these kernels are bound by
@@ -128,27 +130,70 @@ __global__ void k_tv_cheb01(TraceOp32 T, const float *__restrict__ b, const Scal
     }
 }
 
-// t = r - S x
+// b_1(v) = sum over the facets f of vertex v of 0.5 t_f0 + sign(v, f) t_f1 / (2 sqrt 3), t = r - S x:
+// lane (q, row) of a vertex's 16-lane group forms row `row` of t at its q-th facet; the group sums
+// in a fixed tree (deterministic)
 template <int NT>
-__global__ void k_tv_resid(TraceOp32 T, const float *__restrict__ r, const float *__restrict__ x, float *t) {
+__global__ void k_tv_restrict(TraceOp32 T, const float *__restrict__ r, const float *__restrict__ x,
+                              const int *__restrict__ vert_facet, const int *__restrict__ vert_fsign, int nverts,
+                              float *b1) {
     wait_prior_kernel();
-    TV_ROW(NT)
-    (void)G;
-    const float s = __ldcg(&r[g]) - row_S<NT>(T, nrows, f, ic, x);
-    if (live) t[g] = s;
+    const float s3 = 0.28867513459481288225f;              // 1 / (2 sqrt 3)
+    const long long t_ = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = (int)(t_ & 15), q = lane >> 1, row = lane & 1;
+    int v = (int)(t_ >> 4);
+    const bool vlive = v < nverts;
+    if (!vlive) v = nverts - 1;
+    const long long nrows = (long long)T.nfacets * NT;
+    float c = 0.f;
+    const int f = q < 6 ? __ldg(&vert_facet[6 * v + q]) : -1;
+    if (f >= 0) {
+        const float t = __ldcg(&r[(size_t)f * NT + row]) - row_S<NT>(T, nrows, f, row, x);
+        c = row == 0 ? 0.5f * t : (float)__ldg(&vert_fsign[6 * v + q]) * s3 * t;
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o, 16);
+    if (vlive && lane == 0) b1[v] = c;
 }
 
-// d = c1 d + c2 D^{-1} (r - S xin); xout = xin + d (FP32), or out64 = xin + d when out64 is set
+// component j of x + P e_1 at facet cf (P e_1: the linear interpolant of the vertex values e_1,
+// components 0 and 1 of each facet)
 template <int NT>
-__global__ void k_tv_cheb(TraceOp32 T, const float *__restrict__ r, const float *__restrict__ xin, float *xout,
-                          float *d, float c1, float c2, double *out64) {
+__device__ __forceinline__ float x_plus_pe(const float *__restrict__ x, const float *__restrict__ e1,
+                                           const int *__restrict__ facet_vert, int cf, int j) {
+    float v = __ldcg(&x[(size_t)cf * NT + j]);
+    if (e1 && j < 2) {
+        const float a = __ldcg(&e1[__ldg(&facet_vert[2 * cf])]), b = __ldcg(&e1[__ldg(&facet_vert[2 * cf + 1])]);
+        v += j == 0 ? 0.5f * (a + b) : 0.28867513459481288225f * (b - a);
+    }
+    return v;
+}
+
+// d = c1 d + c2 D^{-1} (r - S xin); xout = xin + d (FP32), or out64 = xin + d when out64 is set;
+// xin = x + P e_1 when e1 is set
+template <int NT>
+__global__ void k_tv_cheb(TraceOp32 T, const float *__restrict__ r, const float *__restrict__ x,
+                          const float *__restrict__ e1, const int *__restrict__ facet_vert, float *xout, float *d,
+                          float c1, float c2, double *out64) {
     wait_prior_kernel();
     TV_ROW(NT)
     (void)G;
-    const float res = i < NT ? __ldcg(&r[g]) - row_S<NT>(T, nrows, f, ic, xin) : 0.f;
+    float res = 0.f;
+    if (i < NT) {
+        float s = 0.f;
+#pragma unroll
+        for (int bb = 0; bb < 5; ++bb) {
+            const int cf = __ldg(&T.tcol[bb * T.nfacets + f]);
+            if (cf < 0) continue;                              // uniform over the group
+#pragma unroll
+            for (int j = 0; j < NT; ++j)
+                s += __ldg(&T.Sell[(size_t)(bb * NT + j) * nrows + g]) * x_plus_pe<NT>(x, e1, facet_vert, cf, j);
+        }
+        res = __ldcg(&r[g]) - s;
+    }
     const float dn = (c1 != 0.f ? c1 * __ldcg(&d[g]) : 0.f) + c2 * grp_dinv<NT>(T.Dinv, nrows, f, ic, res);
     if (live) {
-        const float xo = __ldcg(&xin[g]) + dn;
+        const float xo = x_plus_pe<NT>(x, e1, facet_vert, f, ic) + dn;
         d[g] = dn;
         if (out64) out64[g] = (double)xo;
         else xout[g] = xo;
@@ -167,9 +212,8 @@ struct Tail32 {
     float invth[MG_MAX_LEVELS], c1[MG_MAX_LEVELS], c2[MG_MAX_LEVELS];
     int off[MG_MAX_LEVELS];
     const float *Minv;             // coarsest grid: (A + 1 1^T / N)^{-1}, row-major
-    const int *vert_facet, *vert_fsign, *facet_vert;
-    const float *tres;             // trace residual t
-    float *z;                      // trace iterate corrected by P e (components 0 and 1 of each facet)
+    const float *b1;               // right-hand side on level 0 (P^T of the trace residual)
+    float *e1;                     // correction on level 0 (out)
 };
 
 // shared floats the tail needs for the grids G[0..L-1]
@@ -249,7 +293,6 @@ __global__ void __launch_bounds__(1024) k_tv_tail(Tail32 T) {
     wait_prior_kernel();
     extern __shared__ float tsm[];
     const int tid = threadIdx.x, nth = blockDim.x;
-    const float s3 = 0.28867513459481288225f;              // 1 / (2 sqrt 3)
     for (int l = 0; l < T.L; ++l) {                        // diagonals, and the stencils of l >= 1
         const int nv = T.G[l].nverts;
         float *dv = tsm + T.off[l] + 4 * nv;
@@ -257,18 +300,9 @@ __global__ void __launch_bounds__(1024) k_tv_tail(Tail32 T) {
         if (l >= 1)
             for (int q = tid; q < P1_NS * nv; q += nth) dv[nv + q] = __ldg(&T.A[l][q]);
     }
-    {   // b_1 = P^T t: a facet gives 0.5 t_0 +- t_1 / (2 sqrt 3) to each of its vertices
+    {
         float *b = tsm + T.off[0];
-        for (int v = tid; v < T.G[0].nverts; v += nth) {
-            float s = 0.f;
-            for (int q = 0; q < 6; ++q) {
-                const int f = __ldg(&T.vert_facet[6 * v + q]);
-                if (f < 0) continue;
-                s += 0.5f * __ldcg(&T.tres[(size_t)f * NT]) +
-                     (float)__ldg(&T.vert_fsign[6 * v + q]) * s3 * __ldcg(&T.tres[(size_t)f * NT + 1]);
-            }
-            b[v] = s;
-        }
+        for (int v = tid; v < T.G[0].nverts; v += nth) b[v] = __ldcg(&T.b1[v]);
     }
     __syncthreads();
     for (int l = 0; l < T.L - 1; ++l) {                    // down
@@ -362,13 +396,9 @@ __global__ void __launch_bounds__(1024) k_tv_tail(Tail32 T) {
         })
         __syncthreads();
     }
-    {   // z += P e_1: components 0 and 1 of each facet from its two vertices
-        const float *e1 = tail_level(T, tsm, 0).xb;
-        for (int f = tid; f < T.nfacets; f += nth) {
-            const float a = e1[__ldg(&T.facet_vert[2 * f])], bb = e1[__ldg(&T.facet_vert[2 * f + 1])];
-            T.z[(size_t)f * NT] += 0.5f * (a + bb);
-            T.z[(size_t)f * NT + 1] += s3 * (bb - a);
-        }
+    {
+        const float *e = tail_level(T, tsm, 0).xb;
+        for (int v = tid; v < T.G[0].nverts; v += nth) T.e1[v] = e[v];
     }
 }
 

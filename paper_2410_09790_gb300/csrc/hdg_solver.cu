@@ -781,7 +781,7 @@ struct Impl {
         P1Grid G[MG_MAX_LEVELS];
         for (int l = 0; l < L; ++l) G[l] = E.lv[l].G;
         const size_t smem = sizeof(float) * tail32_floats(G, L);
-        if (smem > (size_t)200 * 1024) return;
+        if (smem > (size_t)200 * 1024 || 2LL * G[0].nverts > c->nL) return;   // b_1, e_1 share tt32
         for (int l = 0; l < L; ++l)
             if (G[l].nvx > 1024) return;
         auto f32 = [&](const double *a, long long n) {
@@ -821,9 +821,8 @@ struct Impl {
             off += (l >= 1 ? 12 : 5) * E.lv[l].G.nverts;
         }
         T.Minv = E.Minv32;
-        T.vert_facet = c->M.vert_facet; T.vert_fsign = c->M.vert_fsign; T.facet_vert = c->M.facet_vert;
-        T.tres = c->tt32;
-        T.z = c->tx32;
+        T.b1 = c->tt32;
+        T.e1 = c->tt32 + E.lv[0].G.nverts;
         return T;
     }
 
@@ -837,10 +836,15 @@ struct Impl {
         launch_k(k_tv_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, sub, c->tb32, c->rb(), c->sc,
                                                                   c->capturing ? c->dcnt : nullptr);
         launch_k(k_tv_cheb01<NT>, gb, 128, 0, c->st, T, c->tb32, c->sc, invth, c1, c2, c->tr32, c->tx32, c->td32);
-        launch_k(k_tv_resid<NT>, gb, 128, 0, c->st, T, c->tr32, c->tx32, c->tt32);
+        const int nv0 = E.lv[0].G.nverts;
+        float *b1 = c->tt32, *e1 = c->tt32 + nv0;
+        launch_k(k_tv_restrict<NT>, (unsigned)((16LL * nv0 + 127) / 128), 128, 0, c->st, T, c->tr32, c->tx32,
+                                                                   c->M.vert_facet, c->M.vert_fsign, nv0, b1);
         launch_k(k_tv_tail<NT>, 1, 1024, E.tail32_smem, c->st, tail32_params(c, E));
-        launch_k(k_tv_cheb<NT>, gb, 128, 0, c->st, T, c->tr32, c->tx32, c->txa32, c->td32, 0.f, invth, (double *)nullptr);
-        launch_k(k_tv_cheb<NT>, gb, 128, 0, c->st, T, c->tr32, c->txa32, (float *)nullptr, c->td32, c1, c2, out);
+        launch_k(k_tv_cheb<NT>, gb, 128, 0, c->st, T, c->tr32, c->tx32, e1, c->M.facet_vert, c->txa32, c->td32, 0.f, invth,
+                                                           (double *)nullptr);
+        launch_k(k_tv_cheb<NT>, gb, 128, 0, c->st, T, c->tr32, c->txa32, (const float *)nullptr, c->M.facet_vert,
+                                                           (float *)nullptr, c->td32, c1, c2, out);
         CKL();
         if (!c->capturing) c->S.trace_solves += 1;
     }
