@@ -65,8 +65,9 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[32]) {
     __syncthreads();
 }
 
-// Returns true in thread 0 of the last block, with the grid totals in tot.
-template <int NV>
+// Returns true in thread 0 of the last block (ALL: in every thread of the last block), with the
+// grid totals in tot (valid in thread 0).
+template <int NV, bool ALL = false>
 __device__ bool grid_sum(const RedBuf rb, double (&v)[NV], double (&tot)[NV]) {
     __shared__ double sh[NV][32];
     __shared__ int last;
@@ -94,7 +95,7 @@ __device__ bool grid_sum(const RedBuf rb, double (&v)[NV], double (&tot)[NV]) {
         for (int i = 0; i < NV; ++i) tot[i] = acc[i];
         return true;
     }
-    return false;
+    return ALL;
 }
 
 inline int red_grid(long long n) {
@@ -797,34 +798,58 @@ __global__ void k_loop_init(LoopCtl L, const int *stop) {
     cudaGraphSetConditional(L.h, *stop ? 0u : 1u);
 }
 
-// Last block of an Arnoldi step: Hessenberg column (hcol, plus h2 after a second pass), norm
-// hn = ||w||, Givens rotations, residual estimate, step bookkeeping.
-__device__ void gm_finish_step(GmresState *gs, int j, double hn, bool with_h2) {
-    double *Hc = gs->H + j * (GM_M + 1);
-    for (int i = 0; i <= j; ++i) Hc[i] = with_h2 ? gs->hcol[i] + gs->h2[i] : gs->hcol[i];
+// Last block of an Arnoldi step, called by all its threads: Hessenberg column (hcol, plus h2
+// after a second pass), norm hn = ||w|| (the value of thread 0; with pyth, thread 0 forms it as
+// sqrt(||w||^2 - sum h^2) from hcol[j+1] = ||w||^2, floored at 1e-12 ||w||^2 against
+// cancellation), Givens rotations, residual estimate, step bookkeeping. The state it reads is
+// first gathered into shared memory by the block in one round of independent loads; thread 0
+// then works on shared memory and only stores to the state.
+__device__ void gm_finish_step(GmresState *gs, int j, double hn, bool with_h2, bool pyth = false) {
+    __shared__ double Hc[GM_M + 2], cs[GM_M], sn[GM_M], dsc[4];
+    __shared__ int isc[3];
+    const int t = threadIdx.x;
+    if (t <= j + 1) Hc[t] = (with_h2 && t <= j) ? gs->hcol[t] + gs->h2[t] : gs->hcol[t];
+    if (t < j) { cs[t] = gs->cs[t]; sn[t] = gs->sn[t]; }
+    const int tl = (int)blockDim.x - 1;               // scalars: the block's last threads
+    if (t == tl) dsc[0] = gs->g[j];
+    if (t == tl - 1) dsc[1] = gs->rtol;
+    if (t == tl - 2) dsc[2] = gs->bnorm;
+    if (t == tl - 3) isc[0] = gs->m;
+    if (t == tl - 4) isc[1] = gs->total;
+    if (t == tl - 5) isc[2] = gs->maxit;
+    __syncthreads();
+    if (t != 0) return;
+    if (pyth) {
+        double h2 = 0.0;
+        for (int i = 0; i <= j; ++i) h2 += Hc[i] * Hc[i];
+        const double ww = Hc[j + 1], hn2 = ww - h2;
+        hn = sqrt(hn2 > 1e-12 * ww ? hn2 : 1e-12 * ww);
+    }
     Hc[j + 1] = hn;
     for (int i = 0; i < j; ++i) {                     // previous rotations
-        double a = Hc[i], b2 = Hc[i + 1];
-        Hc[i] = gs->cs[i] * a + gs->sn[i] * b2;
-        Hc[i + 1] = -gs->sn[i] * a + gs->cs[i] * b2;
+        const double a = Hc[i], b2 = Hc[i + 1];
+        Hc[i] = cs[i] * a + sn[i] * b2;
+        Hc[i + 1] = -sn[i] * a + cs[i] * b2;
     }
-    double a = Hc[j], b2 = Hc[j + 1];
-    double r = sqrt(a * a + b2 * b2);
-    double c_ = r > 0 ? a / r : 1.0, s_ = r > 0 ? b2 / r : 0.0;
+    const double a = Hc[j], b2 = Hc[j + 1];
+    const double r = sqrt(a * a + b2 * b2);
+    const double c_ = r > 0 ? a / r : 1.0, s_ = r > 0 ? b2 / r : 0.0;
+    double *H = gs->H + j * (GM_M + 1);
+    for (int i = 0; i < j; ++i) H[i] = Hc[i];
+    H[j] = r;
+    H[j + 1] = hn;                                    // the norm, kept for the next v (k_gm_precond_mf)
     gs->cs[j] = c_; gs->sn[j] = s_;
-    Hc[j] = r;
-    Hc[j + 1] = 0.0;
-    gs->g[j + 1] = -s_ * gs->g[j];
-    gs->g[j] = c_ * gs->g[j];
-    gs->resid = fabs(gs->g[j + 1]);
-    gs->total += 1;
-    // keep H[j+1, j] (the norm) for the next v
-    gs->H[j * (GM_M + 1) + j + 1] = hn;            // restored after the rotation (used by k_gm_precond_mf)
+    const double gj = dsc[0], resid = fabs(-s_ * gj);
+    gs->g[j + 1] = -s_ * gj;
+    gs->g[j] = c_ * gj;
+    gs->resid = resid;
+    const int total = isc[1] + 1;
+    gs->total = total;
     gs->hcol[GM_M + 1] = hn;
     gs->j = j + 1;
-    if (!isfinite(gs->resid)) { gs->breakdown = 2; gs->cycle_end = 1; }
-    else if (gs->resid <= gs->rtol * gs->bnorm) { gs->converged = 1; gs->cycle_end = 1; }
-    else if (gs->j >= gs->m || gs->total >= gs->maxit || hn == 0.0) gs->cycle_end = 1;
+    if (!isfinite(resid)) { gs->breakdown = 2; gs->cycle_end = 1; }
+    else if (resid <= dsc[1] * dsc[2]) { gs->converged = 1; gs->cycle_end = 1; }
+    else if (j + 1 >= isc[0] || total >= isc[2] || hn == 0.0) gs->cycle_end = 1;
 }
 
 
@@ -1078,14 +1103,7 @@ __global__ void k_gm_apply_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ wq,
     const bool last = multidot_groups(rb, V, (const T *)w, nrows, (long long)tpb * NU, j + 1, gs->hcol, FUSED);
     if (FUSED && last) {
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double h2 = 0.0;
-            for (int i = 0; i <= j; ++i) h2 += gs->hcol[i] * gs->hcol[i];
-            const double ww = gs->hcol[j + 1];
-            const double hn2 = ww - h2;
-            // cancellation guard: a remainder below 1e-12 of ||w||^2 is taken as that floor
-            gm_finish_step(gs, j, sqrt(hn2 > 1e-12 * ww ? hn2 : 1e-12 * ww), false);
-        }
+        gm_finish_step(gs, j, 0.0, false, true);     // hn by Pythagoras
     }
 }
 
@@ -1119,7 +1137,7 @@ __global__ void k_gm_orth2(T *w, const T *__restrict__ V, long long nrows, RedBu
     __shared__ double h[GM_M + 1];
     if ((int)threadIdx.x < nvec) h[threadIdx.x] = CGS1 ? gs->hcol[threadIdx.x] : gs->h2[threadIdx.x];
     __syncthreads();
-    double v[1] = {0.0}, tot[1];
+    double v[1] = {0.0}, tot[1] = {0.0};
     T vt = 0;
     GRID_STRIDE(g, nrows) {
         T s = w[g];
@@ -1128,19 +1146,29 @@ __global__ void k_gm_orth2(T *w, const T *__restrict__ V, long long nrows, RedBu
         vt += s * s;
     }
     v[0] = (double)vt;
-    if (grid_sum<1>(rb, v, tot)) gm_finish_step(gs, j, sqrt(tot[0]), !CGS1);
+    if (grid_sum<1, true>(rb, v, tot)) gm_finish_step(gs, j, sqrt(tot[0]), !CGS1);
 }
 
-// y = R^{-1} g (upper triangular part of the rotated H, without the subdiagonal)
+// y = R^{-1} g (upper triangular part of the rotated H, without the subdiagonal); R and g are
+// gathered into shared memory by the block first, then thread 0 substitutes
 __global__ void k_gm_solve(GmresState *gs, const double *Hdiag_unused) {
     wait_prior_kernel();
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int m = gs->j;
+    if (blockIdx.x != 0) return;
+    __shared__ double R[GM_M * (GM_M + 1)], g[GM_M], y[GM_M];
+    __shared__ int ms;
+    if (threadIdx.x == 0) ms = gs->j;
+    __syncthreads();
+    const int m = ms;
+    for (int q = threadIdx.x; q < m * (GM_M + 1); q += blockDim.x) R[q] = gs->H[q];
+    for (int q = threadIdx.x; q < m; q += blockDim.x) g[q] = gs->g[q];
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     for (int i = m - 1; i >= 0; --i) {
-        double s = gs->g[i];
-        for (int k = i + 1; k < m; ++k) s -= gs->H[k * (GM_M + 1) + i] * gs->y[k];
-        double d = gs->H[i * (GM_M + 1) + i];
-        gs->y[i] = d != 0.0 ? s / d : 0.0;
+        double s = g[i];
+        for (int k = i + 1; k < m; ++k) s -= R[k * (GM_M + 1) + i] * y[k];
+        const double d = R[i * (GM_M + 1) + i];
+        y[i] = d != 0.0 ? s / d : 0.0;
+        gs->y[i] = y[i];
     }
 }
 

@@ -982,7 +982,7 @@ struct Impl {
                 gmres_arnoldi<float>(c, E, c->Binv32, c->wq32, c->utr32, c->gw32, c->gV32);
                 launch_k(k_loop_ctl, 1, 1, 0, c->st, L, GM_M + 1, &c->gs->cycle_end);
             });
-        launch_k(k_gm_solve, 1, 32, 0, c->st, c->gs, nullptr);
+        launch_k(k_gm_solve, 1, 256, 0, c->st, c->gs, nullptr);
         launch_k(k_gm_combine<float>, g, VEC_THREADS, 0, c->st, c->gV32, c->gu32, n, c->gs);
         launch_k(k_gm_update_x<K, float>, g, VEC_THREADS, 0, c->st, c->Binv32, c->gu32, x, c->ncells, 1);
         launch_k(k_count_solve, 1, 1, 0, c->st, c->dcnt, c->gs, nullptr);
@@ -1005,7 +1005,7 @@ struct Impl {
         gmres_start(c, first);
         launch_k(k_gm_set_cycle, 1, 1, 0, c->st, c->gs, m);
         for (int j = 0; j < m; ++j) gmres_arnoldi64(c);
-        launch_k(k_gm_solve, 1, 32, 0, c->st, c->gs, nullptr);
+        launch_k(k_gm_solve, 1, 256, 0, c->st, c->gs, nullptr);
         launch_k(k_gm_combine<double>, g, VEC_THREADS, 0, c->st, c->gV, c->gu, n, c->gs);
         launch_k(k_gm_update_x<K, double>, g, VEC_THREADS, 0, c->st, c->Binv, c->gu, c->gx, c->ncells, first);
         CKL();
@@ -1023,7 +1023,7 @@ struct Impl {
                 gmres_arnoldi64(c);
                 launch_k(k_loop_ctl, 1, 1, 0, c->st, L, m + 1, &c->gs->cycle_end);
             });
-        launch_k(k_gm_solve, 1, 32, 0, c->st, c->gs, nullptr);
+        launch_k(k_gm_solve, 1, 256, 0, c->st, c->gs, nullptr);
         launch_k(k_gm_combine<double>, g, VEC_THREADS, 0, c->st, c->gV, c->gu, n, c->gs);
         launch_k(k_gm_update_x<K, double>, g, VEC_THREADS, 0, c->st, c->Binv, c->gu, c->gx, c->ncells, first);
         CKL();
@@ -1236,7 +1236,7 @@ struct Impl {
                         launch_k(k_loop_ctl, 1, 1, 0, c->st, L2, GM_M + 1, &fgs->cycle_end);
                         CKL();
                     });
-                launch_k(k_gm_solve, 1, 32, 0, c->st, fgs, nullptr);
+                launch_k(k_gm_solve, 1, 256, 0, c->st, fgs, nullptr);
                 launch_k(k_gm_combine<double>, g, VEC_THREADS, 0, c->st, c->fZ, u, N, fgs);
                 launch_k(k_vec_add, g, VEC_THREADS, 0, c->st, u, x, N);
                 residual(0);
@@ -1334,7 +1334,7 @@ struct Impl {
                 if (c->hfgs->breakdown == 2) throw std::domain_error("stage FGMRES: non-finite residual");
                 if (c->hfgs->cycle_end) break;
             }
-            launch_k(k_gm_solve, 1, 32, 0, c->st, c->fgs, nullptr);
+            launch_k(k_gm_solve, 1, 256, 0, c->st, c->fgs, nullptr);
             launch_k(k_gm_combine<double>, g, VEC_THREADS, 0, c->st, c->fZ, u, N, c->fgs);
             launch_k(k_vec_add, g, VEC_THREADS, 0, c->st, u, x, N);
             CKL();
