@@ -804,11 +804,21 @@ __global__ void k_loop_init(LoopCtl L, const int *stop) {
 // cancellation), Givens rotations, residual estimate, step bookkeeping. The state it reads is
 // first gathered into shared memory by the block in one round of independent loads; thread 0
 // then works on shared memory and only stores to the state.
-__device__ void gm_finish_step(GmresState *gs, int j, double hn, bool with_h2, bool pyth = false) {
+// hsrc (shared memory, optional): the column (V_i, w), i <= j, and ||w||^2 already summed by the
+// block, used in place of gs->hcol and stored there.
+__device__ void gm_finish_step(GmresState *gs, int j, double hn, bool with_h2, bool pyth = false,
+                               const double *hsrc = nullptr) {
     __shared__ double Hc[GM_M + 2], cs[GM_M], sn[GM_M], dsc[4];
     __shared__ int isc[3];
     const int t = threadIdx.x;
-    if (t <= j + 1) Hc[t] = (with_h2 && t <= j) ? gs->hcol[t] + gs->h2[t] : gs->hcol[t];
+    if (t <= j + 1) {
+        if (hsrc) {
+            Hc[t] = hsrc[t];
+            gs->hcol[t] = hsrc[t];
+        } else {
+            Hc[t] = (with_h2 && t <= j) ? gs->hcol[t] + gs->h2[t] : gs->hcol[t];
+        }
+    }
     if (t < j) { cs[t] = gs->cs[t]; sn[t] = gs->sn[t]; }
     const int tl = (int)blockDim.x - 1;               // scalars: the block's last threads
     if (t == tl) dsc[0] = gs->g[j];
@@ -915,12 +925,13 @@ __global__ void k_count_stage(DevCount *acc, const GmresState *fgs) {
 // Lanes accumulate in T (FP32 for the inner solves: GB300's FP64 rate is low), warps and blocks
 // combine in FP64. w must be visible to the whole block (written before a __syncthreads, or an
 // input).
+// The block's partials alone (no ticket): partials[block * (GM_M + 2) + i]; returns nvec (with
+// the extra vector counted). With fence, each partial is fenced for a last-block reduction.
 template <class T, class Ranges>
-__device__ bool block_multidot(const RedBuf rb, const T *V, const T *w, long long n, int nvec, Ranges ranges,
-                               double *out, const T *extra = nullptr) {
-    __shared__ int last;
+__device__ int block_dot_partials(const RedBuf rb, const T *V, const T *w, long long n, int nvec, Ranges ranges,
+                                  const T *extra, bool fence) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if (extra) ++nvec;                   // (extra, w) -> out[nvec - 1]
+    if (extra) ++nvec;                   // (extra, w) -> value nvec - 1
     for (int i = warp; i < nvec; i += nw) {
         const T *Vi = (extra && i == nvec - 1) ? extra : V + (size_t)i * n;
         T at = 0;
@@ -931,9 +942,18 @@ __device__ bool block_multidot(const RedBuf rb, const T *V, const T *w, long lon
         for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
         if (lane == 0) {
             rb.partials[blockIdx.x * (GM_M + 2) + i] = a;
-            __threadfence();
+            if (fence) __threadfence();
         }
     }
+    return nvec;
+}
+
+template <class T, class Ranges>
+__device__ bool block_multidot(const RedBuf rb, const T *V, const T *w, long long n, int nvec, Ranges ranges,
+                               double *out, const T *extra = nullptr) {
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    nvec = block_dot_partials(rb, V, w, n, nvec, ranges, extra, true);
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned t = atomicAdd(rb.counter, 1u);
@@ -983,6 +1003,17 @@ __device__ bool multidot_groups(const RedBuf rb, const T *V, const T *w, long lo
         for (long long g0 = blockIdx.x * rows_per_group; g0 < nrows; g0 += gridDim.x * rows_per_group)
             f(g0, g0 + rows_per_group < nrows ? g0 + rows_per_group : nrows);
     }, out, with_norm ? w : nullptr);
+}
+
+// the partials of multidot_groups only (reduced by k_gm_finish_ctl)
+template <class T>
+__device__ void multidot_groups_partials(const RedBuf rb, const T *V, const T *w, long long nrows,
+                                         long long rows_per_group, int nvec, bool with_norm) {
+    __syncthreads();
+    block_dot_partials(rb, V, w, nrows, nvec, [&](auto f) {
+        for (long long g0 = blockIdx.x * rows_per_group; g0 < nrows; g0 += gridDim.x * rows_per_group)
+            f(g0, g0 + rows_per_group < nrows ? g0 + rows_per_group : nrows);
+    }, with_norm ? w : nullptr, false);
 }
 
 // start of a cycle: w = b - Bx (Bx = B x precomputed; null on the first cycle, x = 0: w = b);
@@ -1068,7 +1099,8 @@ __global__ void k_gm_precond_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ B
 
 // w = B z = v_j + (neighbour coupling) z for z = Binv v_j (the diagonal block returns v_j);
 // hcol[i] = (V_i, w), i <= j. Team per cell over groups of cells; grid <= MAX_RED_BLOCKS.
-// FUSED (FP32 inner solves): the same pass also gives ||w||^2, and the last block finishes the
+// FUSED (FP32 inner solves): the same pass also gives ||w||^2; the blocks only write their
+// partials, which k_gm_finish_ctl (one block, next in the loop) sums before it finishes the
 // Arnoldi step with the norm of w - V hcol from Pythagoras, ||w||^2 - sum hcol_i^2 (V orthonormal),
 // so that no separate orthogonalisation kernel runs; the next k_gm_precond_mf<.., true> subtracts
 // the projections while it normalises.
@@ -1100,10 +1132,54 @@ __global__ void k_gm_apply_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ wq,
             tm.sync();
         }
     }
-    const bool last = multidot_groups(rb, V, (const T *)w, nrows, (long long)tpb * NU, j + 1, gs->hcol, FUSED);
-    if (FUSED && last) {
+    if (FUSED) multidot_groups_partials(rb, V, (const T *)w, nrows, (long long)tpb * NU, j + 1, true);
+    else multidot_groups(rb, V, (const T *)w, nrows, (long long)tpb * NU, j + 1, gs->hcol, false);
+}
+
+// Step bookkeeping of the FP32 inner Arnoldi loop, one block of 1024 threads after the FUSED
+// k_gm_apply_mf: sums the nblocks block partials of (V_i, w), i <= j, and ||w||^2 (each thread
+// its blocks' rows, then a fixed tree: deterministic), finishes the step (gm_finish_step: hn by
+// Pythagoras, Givens rotation, convergence) and sets the condition of the loop whose body it
+// ends: continue while the cycle has not ended and the pass guard is below limit.
+__global__ void __launch_bounds__(1024) k_gm_finish_ctl(LoopCtl L, int limit, RedBuf rb, int nblocks, GmresState *gs) {
+    wait_prior_kernel();
+    __shared__ double red[GM_M + 2][32];       // per value, per warp
+    __shared__ double hs[GM_M + 2];
+    __shared__ int s_end, s_j;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = (int)(blockDim.x >> 5);
+    if (t == 0) { s_end = gs->cycle_end; s_j = gs->j; }
+    __syncthreads();
+    if (!s_end) {
+        const int j = s_j, nvec = j + 2;
+        for (int i0 = 0; i0 < nvec; i0 += 8) {
+            double a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] = 0.0;
+            for (int b = t; b < nblocks; b += blockDim.x) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i0 + u < nvec) a[u] += __ldcg(&rb.partials[(size_t)b * (GM_M + 2) + i0 + u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                double x = a[u];
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                if (lane == 0 && i0 + u < nvec) red[i0 + u][warp] = x;
+            }
+        }
         __syncthreads();
-        gm_finish_step(gs, j, 0.0, false, true);     // hn by Pythagoras
+        if (t < nvec) {
+            double x = 0.0;
+            for (int w2 = 0; w2 < nw; ++w2) x += red[t][w2];
+            hs[t] = x;
+        }
+        __syncthreads();
+        gm_finish_step(gs, j, 0.0, false, true, hs);   // thread 0 writes the state
+    }
+    if (t == 0) {
+        const int gd = ++*L.guard;
+        *L.launches += (unsigned long long)*L.nk;
+        cudaGraphSetConditional(L.h, (!gs->cycle_end && gd < limit) ? 1u : 0u);
     }
 }
 
