@@ -1136,21 +1136,37 @@ __global__ void k_gm_apply_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ wq,
     else multidot_groups(rb, V, (const T *)w, nrows, (long long)tpb * NU, j + 1, gs->hcol, false);
 }
 
-// Step bookkeeping of the FP32 inner Arnoldi loop, one block of 1024 threads after the FUSED
-// k_gm_apply_mf: sums the nblocks block partials of (V_i, w), i <= j, and ||w||^2 (each thread
-// its blocks' rows, then a fixed tree: deterministic), finishes the step (gm_finish_step: hn by
-// Pythagoras, Givens rotation, convergence) and sets the condition of the loop whose body it
-// ends: continue while the cycle has not ended and the pass guard is below limit.
-__global__ void __launch_bounds__(1024) k_gm_finish_ctl(LoopCtl L, int limit, RedBuf rb, int nblocks, GmresState *gs) {
+// Step bookkeeping of the FP32 inner Arnoldi loop, one block (256 threads) after the FUSED
+// k_gm_apply_mf: reads all the loop state it may need in one round of independent loads, sums the
+// nblocks block partials of (V_i, w), i <= j, and ||w||^2 (each thread its blocks' rows, then a
+// fixed tree: deterministic), finishes the step on shared memory (hn by Pythagoras with the
+// 1e-12 ||w||^2 floor, previous rotations, new Givens rotation, residual estimate, convergence)
+// and sets the condition of the loop whose body it ends: continue while the cycle has not ended
+// and the pass guard is below limit.
+__global__ void __launch_bounds__(256) k_gm_finish_ctl(LoopCtl L, int limit, RedBuf rb, int nblocks, GmresState *gs) {
     wait_prior_kernel();
-    __shared__ double red[GM_M + 2][32];       // per value, per warp
-    __shared__ double hs[GM_M + 2];
-    __shared__ int s_end, s_j;
+    __shared__ double red[GM_M + 2][8];        // per value, per warp
+    __shared__ double Hc[GM_M + 2], cs[GM_M], sn[GM_M], gv[GM_M + 1], dsc[2];
+    __shared__ int isc[8];
+    __shared__ unsigned long long nlaunch;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = (int)(blockDim.x >> 5);
-    if (t == 0) { s_end = gs->cycle_end; s_j = gs->j; }
+    if (t < GM_M) { cs[t] = gs->cs[t]; sn[t] = gs->sn[t]; }
+    else if (t >= 32 && t < 32 + GM_M + 1) gv[t - 32] = gs->g[t - 32];
+    else if (t == 64) isc[0] = gs->cycle_end;
+    else if (t == 65) isc[1] = gs->j;
+    else if (t == 66) isc[2] = gs->m;
+    else if (t == 67) isc[3] = gs->total;
+    else if (t == 68) isc[4] = gs->maxit;
+    else if (t == 69) isc[5] = *L.guard;
+    else if (t == 70) isc[6] = *L.nk;
+    else if (t == 71) nlaunch = *L.launches;
+    else if (t == 72) dsc[0] = gs->rtol;
+    else if (t == 73) dsc[1] = gs->bnorm;
     __syncthreads();
-    if (!s_end) {
-        const int j = s_j, nvec = j + 2;
+    const int j = isc[1];
+    int end = isc[0];
+    if (!end) {
+        const int nvec = j + 2;
         for (int i0 = 0; i0 < nvec; i0 += 8) {
             double a[8];
 #pragma unroll
@@ -1171,15 +1187,48 @@ __global__ void __launch_bounds__(1024) k_gm_finish_ctl(LoopCtl L, int limit, Re
         if (t < nvec) {
             double x = 0.0;
             for (int w2 = 0; w2 < nw; ++w2) x += red[t][w2];
-            hs[t] = x;
+            Hc[t] = x;
+            gs->hcol[t] = x;                            // (V_i, w) for the next preconditioner pass
         }
         __syncthreads();
-        gm_finish_step(gs, j, 0.0, false, true, hs);   // thread 0 writes the state
+        if (t == 0) {
+            double h2 = 0.0;
+            for (int i = 0; i <= j; ++i) h2 += Hc[i] * Hc[i];
+            const double ww = Hc[j + 1], hn2 = ww - h2;
+            const double hn = sqrt(hn2 > 1e-12 * ww ? hn2 : 1e-12 * ww);
+            Hc[j + 1] = hn;
+            for (int i = 0; i < j; ++i) {              // previous rotations
+                const double p = Hc[i], q = Hc[i + 1];
+                Hc[i] = cs[i] * p + sn[i] * q;
+                Hc[i + 1] = -sn[i] * p + cs[i] * q;
+            }
+            const double p = Hc[j], q = Hc[j + 1];
+            const double r = sqrt(p * p + q * q);
+            const double c_ = r > 0 ? p / r : 1.0, s_ = r > 0 ? q / r : 0.0;
+            double *H = gs->H + j * (GM_M + 1);
+            for (int i = 0; i < j; ++i) H[i] = Hc[i];
+            H[j] = r;
+            H[j + 1] = hn;                              // the norm, kept for the next v
+            gs->cs[j] = c_; gs->sn[j] = s_;
+            const double gj = gv[j], resid = fabs(-s_ * gj);
+            gs->g[j + 1] = -s_ * gj;
+            gs->g[j] = c_ * gj;
+            gs->resid = resid;
+            const int total = isc[3] + 1;
+            gs->total = total;
+            gs->hcol[GM_M + 1] = hn;
+            gs->j = j + 1;
+            if (!isfinite(resid)) { gs->breakdown = 2; end = 1; }
+            else if (resid <= dsc[0] * dsc[1]) { gs->converged = 1; end = 1; }
+            else if (j + 1 >= isc[2] || total >= isc[4] || hn == 0.0) end = 1;
+            if (end) gs->cycle_end = 1;
+        }
     }
     if (t == 0) {
-        const int gd = ++*L.guard;
-        *L.launches += (unsigned long long)*L.nk;
-        cudaGraphSetConditional(L.h, (!gs->cycle_end && gd < limit) ? 1u : 0u);
+        const int gd = isc[5] + 1;
+        *L.guard = gd;
+        *L.launches = nlaunch + (unsigned long long)isc[6];
+        cudaGraphSetConditional(L.h, (!end && gd < limit) ? 1u : 0u);
     }
 }
 

@@ -981,7 +981,7 @@ struct Impl {
             [&](LoopCtl L) {
                 gmres_arnoldi<float>(c, E, c->Binv32, c->wq32, c->utr32, c->gw32, c->gV32);
                 const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
-                launch_k(k_gm_finish_ctl, 1, 1024, 0, c->st, L, GM_M + 1, c->rb(), (int)ab, c->gs);
+                launch_k(k_gm_finish_ctl, 1, 256, 0, c->st, L, GM_M + 1, c->rb(), (int)ab, c->gs);
             });
         launch_k(k_gm_solve, 1, 256, 0, c->st, c->gs, nullptr);
         launch_k(k_gm_combine<float>, g, VEC_THREADS, 0, c->st, c->gV32, c->gu32, n, c->gs);
