@@ -13,9 +13,11 @@ Alg. 1 (3 stage solves, final update, pressure reconstruction) through hdg_imex_
 Output: one JSON line (rank 0). value = stage solves/s (whole job); trace_dof_per_s = trace
 unknowns x trace solves / s. e2e: the same through the C-ABI with the state copied from pinned
 host memory to the device and back every step. roofline: the kernel with the largest share of a
-step, the Arnoldi product of the FP32 inner Step-I GMRES, timed alone with CUDA events on the
-context's stream (algorithmic bytes / time vs the measured HBM peak); trace_apply and
-stage_apply_fp64 report two more kernels of the path the same way.
+step, the fused FP64 stage-operator kernel (the flexible GMRES product), timed alone with CUDA
+events on the context's stream; it is bound by GB300's FP64 pipe, so achieved = algorithmic
+FP64 flops / time against the nominal FP64 rate. inner_stepI_fp32 (the two kernels of an inner
+Arnoldi step, bytes / time vs the measured HBM peak), trace_apply and stage_apply_fp64 report
+more kernels of the path the same way.
 cpu_baseline / --impl reference: the oracle (plain FP64 SciPy) on the host cores.
 """
 import argparse
@@ -45,12 +47,15 @@ def measured_peaks():
         return 6800.0, 'fallback'
 
 
-def roofline_traffic():
-    """DRAM bytes per launch of the roofline kernel from its committed ncu summary (None if the
-    summary does not state them)."""
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (vector pipe): 152 SMs x 2.07 GHz x 4 flops per clock
+
+
+def profile_traffic(name):
+    """DRAM bytes per launch of a kernel from its committed ncu summary profiles/<name> (None if
+    the summary does not state them)."""
     import re
     try:
-        with open(os.path.join(ROOT, 'profiles', 'k_gm_apply_mf_fp32_c2.md')) as f:
+        with open(os.path.join(ROOT, 'profiles', name)) as f:
             m = re.search(r'^traffic_bytes_per_launch = (\d+)$', f.read(), re.M)
         return int(m.group(1)) if m else None
     except OSError:
@@ -242,6 +247,8 @@ def run_gpu(args, rank, world, local_rank):
         k_ms, k_bytes = ctx.hdg_time_kernel(0, c_stage, 50)
         s_ms, s_bytes = ctx.hdg_time_kernel(1, 1.0, 20)
         a_ms, a_bytes = ctx.hdg_time_kernel(6, c_stage, 50)
+        p_ms, p_bytes = ctx.hdg_time_kernel(9, c_stage, 50)
+        st_ms, st_bytes = ctx.hdg_time_kernel(8, c_stage, 20)
         # end to end through the C-ABI with host buffers
         Qh, ph, lh, _ = ctx.hdg_get_state()
         Qh, ph, lh = Qh.cpu().pin_memory(), ph.cpu().pin_memory(), lh.cpu().pin_memory()
@@ -271,12 +278,19 @@ def run_gpu(args, rank, world, local_rank):
     trace_iters = sum(s['trace_iters'] for s in stats_all)
     stepI_iters = sum(s['stepI_iters'] for s in stats_all)
     peak, peak_kind = measured_peaks()
-    achieved = a_bytes / (a_ms * 1e-3) / 1e9
-    # FP64 stage-operator apply: FMAs per cell = dense diagonal block + neighbour evaluation +
+    # FP64 velocity-block apply: FMAs per cell = dense diagonal block + neighbour evaluation +
     # flux + test (interior edges; k = w['k'])
     mu = (w['k'] + 2) * (w['k'] + 3) // 2
     nu, nfq = 2 * mu, (3 * w['k'] + 5) // 2
-    s_flop = 2.0 * (nu * nu + 3 * nfq * 2 * mu + 3 * nfq * 8 + nu * 3 * nfq) * (ctx.nQ // nu)
+    npk, nt = (w['k'] + 1) * (w['k'] + 2) // 2, w['k'] + 1
+    ncells = ctx.nQ // nu
+    s_flop = 2.0 * (nu * nu + 3 * nfq * 2 * mu + 3 * nfq * 8 + nu * 3 * nfq) * ncells
+    # the fused stage operator: the velocity block above + the trace and pressure coupling of the
+    # velocity rows + the cell's constraint rows (pressure rows, trace rows)
+    st_flop = s_flop + ncells * (nu * (3 * (2 * nt + 3) + 2 * (2 * npk + 2) + 3) + 6 * mu +
+                                 npk * (4 * mu + 3 * (2 * npk + 2) + 3 * (2 * nt + 2) + 5) +
+                                 3 * nt * (5 * mu + 2 * npk + 5))
+    st_tflops = st_flop / (st_ms * 1e-3) / 1e12
     line = {
         'metric': METRIC, 'value': value, 'unit': 'stage_solves/s', 'n_gpus': world, 'steps': args.steps,
         'warmup': args.warmup, 'ms_per_step': ms_step, 'higher_is_better': True, 'scaling': 'weak',
@@ -296,11 +310,21 @@ def run_gpu(args, rank, world, local_rank):
                      'gmres_iters': stepI_iters / args.steps},
         'e2e': {'value': world * stages / (e2e_mean / 1e3), 'unit': 'stage_solves/s', 'h2d_bytes_per_step': h2d,
                 'd2h_bytes_per_step': h2d},
-        'roofline': {'kernel': 'k_gm_apply_mf<float> (Arnoldi product of the FP32 inner Step-I GMRES, step j = 4)',
-                     'bound': 'hbm',
-                     'achieved': achieved, 'peak': peak, 'unit': 'GB/s', 'frac': achieved / peak,
-                     'peak_kind': peak_kind, 'traffic': roofline_traffic(), 'ms_per_launch': a_ms,
-                     'algorithmic_bytes': a_bytes},
+        'roofline': {'kernel': 'k_stage_apply<3> (fused FP64 stage operator, the flexible GMRES product)',
+                     'bound': 'alu', 'achieved': st_tflops, 'peak': FP64_NOMINAL_TFLOPS, 'unit': 'TFLOP/s',
+                     'frac': st_tflops / FP64_NOMINAL_TFLOPS,
+                     'peak_kind': 'nominal FP64 vector rate (no measured FP64 peak exists for this pool)',
+                     'traffic': profile_traffic('k_stage_apply_fp64_c2.md'), 'ms_per_launch': st_ms,
+                     'algorithmic_flop': st_flop, 'algorithmic_bytes': st_bytes,
+                     'achieved_gbs': st_bytes / (st_ms * 1e-3) / 1e9},
+        'inner_stepI_fp32': {
+            'apply': {'kernel': 'k_gm_apply_mf<3, float, 1> (Arnoldi product, step j = 4)', 'ms_per_launch': a_ms,
+                      'bytes': a_bytes, 'achieved_gbs': a_bytes / (a_ms * 1e-3) / 1e9,
+                      'frac_of_hbm': a_bytes / (a_ms * 1e-3) / 1e9 / peak,
+                      'traffic': profile_traffic('k_gm_apply_mf_fp32_c2.md')},
+            'precond': {'kernel': 'k_gm_precond_mf<3, float, 1> (block inverse pass, step j = 4)',
+                        'ms_per_launch': p_ms, 'bytes': p_bytes, 'achieved_gbs': p_bytes / (p_ms * 1e-3) / 1e9,
+                        'frac_of_hbm': p_bytes / (p_ms * 1e-3) / 1e9 / peak, 'hbm_peak_kind': peak_kind}},
         'trace_apply': {'kernel': 'k_cg_apply', 'achieved_gbs': k_bytes / (k_ms * 1e-3) / 1e9, 'ms_per_launch': k_ms,
                         'bytes': k_bytes},
         'stage_apply_fp64': {'kernel': 'k_cell_apply_mf', 'achieved_gbs': s_bytes / (s_ms * 1e-3) / 1e9,

@@ -231,7 +231,11 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *ctx, hdg_stats *stats);
  * after a one-thread kernel that resets the step, whose time is subtracted); bytes = its
  * algorithmic bytes. which = 7 (bytes = 0): the preconditioner's Step II as the stage solves run it
  * (FP32 cell maps, then the inner trace solve: one V-cycle, in FP32 when inner_trace_fp32 is on),
- * recorded and replayed like 2..5. */
+ * recorded and replayed like 2..5. which = 8: the fused FP64 stage-operator kernel alone (the
+ * FGMRES matrix-vector product without the facet gather) on the operator last assembled, input
+ * the current state; bytes = its algorithmic bytes. which = 9: the FP32 preconditioner pass of
+ * the inner Step-I GMRES (v_j formed from w and the projections, z = B^-1 v_j, z's edge values) at
+ * step j = 4, launched like 6; bytes = its algorithmic bytes. */
 hdg_status hdg_time_kernel(hdg_ctx *ctx, int which, double c, int reps, double *ms_per_launch,
                            double *bytes_per_launch);
 

@@ -2052,11 +2052,11 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *c, hdg_stats *stats) {
 }
 
 hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *ms, double *bytes) {
-    if (!c || reps < 1 || !ms || !bytes || which < 0 || which > 7 || (which != 1 && !(cc > 0)))
+    if (!c || reps < 1 || !ms || !bytes || which < 0 || which > 9 || (which != 1 && !(cc > 0)))
         return HDG_ERR_INVALID_ARG;
-    if (which >= 2 && !c->fv) return HDG_ERR_INVALID_ARG;
+    if (which >= 2 && which != 8 && !c->fv) return HDG_ERR_INVALID_ARG;
     try {
-        if (which == 6) {
+        if (which == 6 || which == 9) {
             double t6_ms = 0.0;
             DISPATCH(c, {
                 // one FP32 inner Step-I solve fills the basis and edge values; then the Arnoldi
@@ -2072,14 +2072,18 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 const EdgeTab<float> E{c->ephi32, c->pen32};
                 const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
                 const size_t sm = sizeof(float) * TEAMS_PER_BLOCK * 6 * I::Dm::NFQ;
-                // the product as the solve runs it (with its norm and Givens step, which advance
-                // the step counter): each launch follows a one-thread kernel that puts step J back;
-                // that kernel's own time, measured alone, is subtracted
+                // the kernel as the solve runs it at step J: each launch follows a one-thread
+                // kernel that puts step J back (the solve above ended its cycle); that kernel's own
+                // time, measured alone, is subtracted
                 auto reset = [&]() { launch_k(k_gm_set_step, 1, 1, 0, c->st, c->gs, J); };
                 auto launch = [&]() {
                     reset();
-                    launch_k(k_gm_apply_mf<I::K_, float, true>, ab, 128, sm, c->st, E, c->M, c->wq32, c->utr32, c->gw32,
-                             c->gV32, c->rb(), c->gs);
+                    if (which == 6)
+                        launch_k(k_gm_apply_mf<I::K_, float, true>, ab, 128, sm, c->st, E, c->M, c->wq32, c->utr32,
+                                 c->gw32, c->gV32, c->rb(), c->gs);
+                    else
+                        launch_k(k_gm_precond_mf<I::K_, float, true>, cb, 128, sizeof(float) * TEAMS_PER_BLOCK * 2 * I::NU,
+                                 c->st, E, c->M, c->Binv32, c->gw32, c->gV32, c->utr32, c->gs);
                 };
                 launch();
                 CKL();
@@ -2098,9 +2102,13 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 t6_ms = (double)(t_pair - t_reset) / reps;
                 cudaGraphExecDestroy(ex);
                 const int nfq = I::Dm::NFQ;
-                // neighbour edge values (2 floats per point) + weights + v_j read + w written +
-                // the J + 1 basis vectors of the dots
-                *bytes = 4.0 * ((double)c->ncells * 3 * nfq * 3 + 2.0 * c->nQ + (J + 1.0) * c->nQ);
+                if (which == 6)   // neighbour edge values (2 floats per point) + weights + v_j read + w
+                                  // written + the J + 1 basis vectors of the dots
+                    *bytes = 4.0 * ((double)c->ncells * 3 * nfq * 3 + 2.0 * c->nQ + (J + 1.0) * c->nQ);
+                else              // block inverses + w read + V_0..V_{J-1} read (projections) + V_J
+                                  // written + edge values written (2 floats per point)
+                    *bytes = 4.0 * ((double)c->ncells * I::NU * I::NU + (J + 2.0) * c->nQ +
+                                    (double)c->ncells * 3 * nfq * 2);
             });
             *ms = t6_ms;
             return HDG_OK;
@@ -2156,6 +2164,24 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 auto launch = [&]() {
                     launch_k(k_cg_apply<I::NT>, gr, VEC_THREADS, 0, c->st, E.Sell, E.tcol, c->tz, c->tp[0], c->tp[1], c->tAp, nf,
                                                                     c->rb(), c->sc);
+                };
+                launch();
+                CKL();
+                CK(cudaEventRecord(c->e0, c->st));
+                for (int r = 0; r < reps; ++r) launch();
+                CK(cudaEventRecord(c->e1, c->st));
+            } else if (which == 8) {
+                // k_stage_apply alone on the operator last assembled (c scales the pressure and trace
+                // coupling), input the current state (Q, p, lambda); bytes: diagonal blocks +
+                // neighbour weights + neighbour maps + Q, p, lambda read + yQ, yp, v written
+                const int nfq = (3 * c->K + 5) / 2;
+                b = 8.0 * c->ncells * ((double)NU * NU + 3 * nfq) + 4.0 * 6 * c->ncells +
+                    8.0 * (2.0 * c->nQ + 2.0 * c->nPv + c->nL + (double)c->ncells * 3 * NT);
+                const unsigned nb = cell_blocks(c);
+                const size_t sm = sizeof(double) * TEAMS_PER_BLOCK * (6 * nfq + 3 * NT + 2 * I::MU);
+                auto launch = [&]() {
+                    launch_k(k_stage_apply<I::K_>, nb, 128, sm, c->st, c->R, EdgeTab<double>{c->R.ephi, c->pen}, c->M,
+                             c->Dblk, c->wq, cc, c->P.tau, c->Q, c->p, c->lam, c->q[6], c->pp[1], c->vK);
                 };
                 launch();
                 CKL();
