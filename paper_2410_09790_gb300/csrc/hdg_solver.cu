@@ -2113,7 +2113,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
             *ms = t6_ms;
             return HDG_OK;
         }
-        if (which >= 2) {
+        if (which >= 2 && which != 8) {
             DISPATCH(c, {
                 // operator of a stage at coefficient cc around the current state; v = (M Q, 0, 0)
                 I::bdm(c, c->Q, c->q[5]);
