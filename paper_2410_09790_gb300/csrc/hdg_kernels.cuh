@@ -645,6 +645,7 @@ __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c
 template <class T>
 struct EdgeTab {
     const T *ephi, *pen;
+    const T *nrm;           // optional: the cells' outward normals in T, nrm[6 cell + 2 e + d]
 };
 
 // t[(e*NFQ + q)*2 + d] = pen_q n_d (n . u) + wq(e, q) u_d at the points of this cell's edges,
@@ -676,7 +677,8 @@ __device__ __forceinline__ void team_nbr_flux(const Team &tm, const EdgeTab<T> &
                     ux += f * xo[b]; uy += f * xo[MU + b];
                 }
             }
-            const T nx = (T)gp->nx[e], ny = (T)gp->ny[e];
+            const T nx = E.nrm ? E.nrm[6 * cell + 2 * e] : (T)gp->nx[e];
+            const T ny = E.nrm ? E.nrm[6 * cell + 2 * e + 1] : (T)gp->ny[e];
             const T un = nx * ux + ny * uy, pen = E.pen[q];
             const T w = __ldg(&wq[(size_t)cell * 3 * NFQ + i]);
             tx = pen * nx * un + w * ux;
@@ -775,6 +777,8 @@ struct GmresState {
     double cs[GM_M], sn[GM_M], g[GM_M + 1], y[GM_M], hcol[GM_M + 2], h2[GM_M + 2];
     double bnorm, beta, resid, rtol;
     int j, cycle_end, converged, total, maxit, breakdown, m;   // m: restart length of this cycle
+    // FP32 copies for the FUSED inner kernels: 1 / (norm of the step's w) and the projections
+    float inv32, hcol32[GM_M + 2];
 };
 
 __global__ void k_gm_set_cycle(GmresState *gs, int m) {
@@ -938,10 +942,9 @@ __device__ int block_dot_partials(const RedBuf rb, const T *V, const T *w, long 
         ranges([&](long long r0, long long r1) {
             for (long long g = r0 + lane; g < r1; g += 32) at += Vi[g] * w[g];
         });
-        double a = (double)at;
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        for (int o = 16; o > 0; o >>= 1) at += __shfl_down_sync(0xffffffffu, at, o);
         if (lane == 0) {
-            rb.partials[blockIdx.x * (GM_M + 2) + i] = a;
+            rb.partials[blockIdx.x * (GM_M + 2) + i] = (double)at;
             if (fence) __threadfence();
         }
     }
@@ -1038,6 +1041,7 @@ __global__ void k_gm_start(long long nrows, const double *__restrict__ b, const 
             gs->breakdown = 0;
         }
         gs->beta = beta;
+        gs->inv32 = (float)(1.0 / beta);
         gs->resid = beta;
         for (int i = 0; i <= GM_M; ++i) gs->g[i] = 0.0;
         gs->g[0] = beta;
@@ -1060,20 +1064,25 @@ __global__ void k_gm_precond_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ B
     constexpr int SCR = 2 * NU;
     extern __shared__ double smd[];
     T *sm = reinterpret_cast<T *>(smd);
+    __shared__ float hproj[GM_M + 2];
     const int team = threadIdx.x / TEAM_LANES;
     const int cell = (blockIdx.x * blockDim.x + threadIdx.x) / TEAM_LANES;
+    const int j = gs->j;
+    if (FUSED) {                        // FP32 scalars of the step (no FP64 work in this kernel)
+        if ((int)threadIdx.x < j) hproj[threadIdx.x] = gs->hcol32[threadIdx.x];
+        __syncthreads();
+    }
     if (cell >= M.ncells) return;
     Team tm{(int)(threadIdx.x % TEAM_LANES), TEAM_LANES};
     T *vK = sm + team * SCR, *zK = vK + NU;
-    const int j = gs->j;
-    const T inv = (T)(1.0 / (j == 0 ? gs->beta : gs->H[(j - 1) * (GM_M + 1) + j]));
+    const T inv = FUSED ? (T)gs->inv32 : (T)(1.0 / (j == 0 ? gs->beta : gs->H[(j - 1) * (GM_M + 1) + j]));
     const long long nrows = (long long)M.ncells * NU;
     T *vj = V + (size_t)j * nrows;
     TFOR(r, NU) {
         const size_t gi = (size_t)cell * NU + r;
         T wv = w[gi];
         if (FUSED)                      // w of step j-1 minus its projections (one Gram-Schmidt pass)
-            for (int i = 0; i < j; ++i) wv -= (T)gs->hcol[i] * V[(size_t)i * nrows + gi];
+            for (int i = 0; i < j; ++i) wv -= (T)hproj[i] * V[(size_t)i * nrows + gi];
         const T v = wv * inv;
         vj[gi] = v;
         vK[r] = v;
@@ -1188,7 +1197,8 @@ __global__ void __launch_bounds__(256) k_gm_finish_ctl(LoopCtl L, int limit, Red
             double x = 0.0;
             for (int w2 = 0; w2 < nw; ++w2) x += red[t][w2];
             Hc[t] = x;
-            gs->hcol[t] = x;                            // (V_i, w) for the next preconditioner pass
+            gs->hcol[t] = x;
+            gs->hcol32[t] = (float)x;                   // projections for the next preconditioner pass
         }
         __syncthreads();
         if (t == 0) {
@@ -1209,6 +1219,7 @@ __global__ void __launch_bounds__(256) k_gm_finish_ctl(LoopCtl L, int limit, Red
             for (int i = 0; i < j; ++i) H[i] = Hc[i];
             H[j] = r;
             H[j + 1] = hn;                              // the norm, kept for the next v
+            gs->inv32 = (float)(1.0 / hn);
             gs->cs[j] = c_; gs->sn[j] = s_;
             const double gj = gv[j], resid = fabs(-s_ * gj);
             gs->g[j + 1] = -s_ * gj;
@@ -1393,6 +1404,7 @@ __global__ void k_vec_start(const double *__restrict__ r, long long n, int first
             if (first == 1) gs->bnorm = beta;           // first == 2: bnorm set by the caller
         }
         gs->beta = beta;
+        gs->inv32 = (float)(1.0 / beta);
         gs->resid = beta;
         for (int i = 0; i <= GM_M; ++i) gs->g[i] = 0.0;
         gs->g[0] = beta;

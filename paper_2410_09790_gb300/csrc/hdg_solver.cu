@@ -162,6 +162,7 @@ struct hdg_ctx {
     int trace_vcycles = 0;                                   // > 0: trace solves are that many V-cycles
     // FP32 copies for the loose (inner) Step-I solves: tables, block inverses, weights, GMRES work
     float *ephi32 = nullptr, *pen32 = nullptr, *Binv32 = nullptr, *wq32 = nullptr, *utr32 = nullptr;
+    float *nrm32 = nullptr;                                  // cell normals in FP32 [6 cell + 2 e + d]
     float *gV32 = nullptr, *gw32 = nullptr, *gu32 = nullptr;
     cudaGraphExec_t g_stepI32 = nullptr;                     // one loose Step-I solve (host-driven mode)
     int stepI32_kernels = 0;
@@ -945,7 +946,7 @@ struct Impl {
             if (g < 1) throw std::runtime_error("persistent Step-I kernel cannot be resident");
             c->coop_grid = (int)g;
         }
-        StepI32Args A{EdgeTab<float>{c->ephi32, c->pen32}, c->M, c->Binv32, c->wq32, c->gV32, c->utr32, c->gw32,
+        StepI32Args A{EdgeTab<float>{c->ephi32, c->pen32, c->nrm32}, c->M, c->Binv32, c->wq32, c->gV32, c->utr32, c->gw32,
                       b, x, c->partials, c->gbar, c->gs};
         launch_k(k_bar_reset, 1, 1, 0, c->st, c->gbar);
         cudaLaunchConfig_t cfg{};
@@ -973,7 +974,7 @@ struct Impl {
         }
         const long long n = c->nQ;
         const int g = grid_for(n);
-        const EdgeTab<float> E{c->ephi32, c->pen32};
+        const EdgeTab<float> E{c->ephi32, c->pen32, c->nrm32};
         launch_k(k_gm_start<float>, g, VEC_THREADS, 0, c->st, n, b, nullptr, c->gw32, 1, c->rb(), c->gs, -1.0, 0);
         launch_k(k_gm_set_cycle, 1, 1, 0, c->st, c->gs, GM_M);
         capture_while(
@@ -1721,6 +1722,14 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
             std::vector<float> e32(c->T.ephi.begin(), c->T.ephi.end());
             c->ephi32 = c->alloc<float>(e32.size());
             CK(cudaMemcpy(c->ephi32, e32.data(), e32.size() * sizeof(float), cudaMemcpyHostToDevice));
+            std::vector<float> n32((size_t)6 * c->ncells);
+            for (long long k = 0; k < c->ncells; ++k)
+                for (int e = 0; e < 3; ++e) {
+                    n32[6 * k + 2 * e] = (float)c->H.geo[k].nx[e];
+                    n32[6 * k + 2 * e + 1] = (float)c->H.geo[k].ny[e];
+                }
+            c->nrm32 = c->alloc<float>(n32.size());
+            CK(cudaMemcpy(c->nrm32, n32.data(), n32.size() * sizeof(float), cudaMemcpyHostToDevice));
         }
         c->Binv = c->alloc<double>((size_t)c->NU * nQ);
         c->dstatus = c->alloc<int>(1);
@@ -2069,7 +2078,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 CKL();
                 cudaGraphExec_t ex = capture_graph(c, [&]() { I::stepI32_record(c, c->fv, c->q[2]); });
                 CK(cudaGraphLaunch(ex, c->st));
-                const EdgeTab<float> E{c->ephi32, c->pen32};
+                const EdgeTab<float> E{c->ephi32, c->pen32, c->nrm32};
                 const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
                 const size_t sm = sizeof(float) * TEAMS_PER_BLOCK * 6 * I::Dm::NFQ;
                 // the kernel as the solve runs it at step J: each launch follows a one-thread
