@@ -1448,6 +1448,62 @@ __global__ void k_vec_dot(const double *__restrict__ w, const double *__restrict
     multidot_rows(rb, V, w, n, gs->j + 1, gs->hcol, with_norm != 0);
 }
 
+// Second classical Gram-Schmidt pass of the stage FGMRES, first half: w' = w - V hcol; h2 =
+// V^T w' and ||w'||^2 in the same sweep; the last block finishes the Arnoldi step with
+// hn = sqrt(||w'||^2 - ||h2||^2) (exact for the w'' = w' - V h2 the next kernel forms, V
+// orthonormal; no cancellation: h2 is small against w' after the first pass) and
+// H[:, j] = hcol + h2.
+__global__ void k_fgm_orth1(double *w, const double *__restrict__ V, long long nrows, RedBuf rb, GmresState *gs) {
+    wait_prior_kernel();
+    if (gs->cycle_end) return;
+    const int j = gs->j, nvec = j + 1;
+    __shared__ double h[GM_M + 1];
+    if ((int)threadIdx.x < nvec) h[threadIdx.x] = gs->hcol[threadIdx.x];
+    __syncthreads();
+    const RowChunk ch(nrows);
+    for (long long g = ch.r0 + threadIdx.x; g < ch.r1; g += blockDim.x) {
+        double s = w[g];
+        for (int i = 0; i < nvec; ++i) s -= h[i] * V[(size_t)i * nrows + g];
+        w[g] = s;
+    }
+    __syncthreads();
+    const bool last = block_multidot(rb, V, (const double *)w, nrows, nvec,
+                                     [&](auto f) { if (ch.r0 < ch.r1) f(ch.r0, ch.r1); }, gs->h2, (const double *)w);
+    if (!last) return;
+    __syncthreads();
+    __shared__ double hn_s;
+    if (threadIdx.x == 0) {
+        double q = 0.0;
+        for (int i = 0; i <= j; ++i) q += gs->h2[i] * gs->h2[i];
+        const double ww = gs->h2[j + 1], hn2 = ww - q;
+        hn_s = sqrt(hn2 > 1e-24 * ww ? hn2 : 1e-24 * ww);
+    }
+    __syncthreads();
+    gm_finish_step(gs, j, hn_s, true);
+}
+
+// Second half: v_{j+1} = (w' - V h2) / hn written to V_{j+1} (and vfix when set), for the step
+// the previous kernel finished (gs->j already advanced; nothing when the cycle ended)
+__global__ void k_fgm_orth2n(const double *__restrict__ w, double *V, double *vfix, long long nrows,
+                             const GmresState *gs) {
+    wait_prior_kernel();
+    if (gs->cycle_end) return;
+    const int jn = gs->j;                        // the new basis slot
+    __shared__ double h[GM_M + 1];
+    __shared__ double inv;
+    if ((int)threadIdx.x < jn) h[threadIdx.x] = gs->h2[threadIdx.x];
+    if (threadIdx.x == 0) inv = 1.0 / gs->H[(jn - 1) * (GM_M + 1) + jn];
+    __syncthreads();
+    double *vn = V + (size_t)jn * nrows;
+    GRID_STRIDE(g, nrows) {
+        double s = w[g];
+        for (int i = 0; i < jn; ++i) s -= h[i] * V[(size_t)i * nrows + g];
+        s *= inv;
+        vn[g] = s;
+        if (vfix) vfix[g] = s;
+    }
+}
+
 // x += u
 __global__ void k_vec_add(const double *__restrict__ u, double *x, long long n) {
     wait_prior_kernel();

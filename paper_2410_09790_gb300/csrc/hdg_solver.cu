@@ -1195,11 +1195,15 @@ struct Impl {
 
     // Orthogonalise w against the stage FGMRES basis: classical Gram-Schmidt, two passes (a
     // selective second pass was tried: the first pass cancels most of w at every step here).
-    static void fgmres_orth(hdg_ctx *c, double *w, long long N, GmresState *fgs) {
+    // The second pass's norm comes from Pythagoras with its own dots, so the last kernel only
+    // forms v_{j+1} = (w' - V h2) / hn in V (and in vfix when set): no reduction there, and the
+    // next Arnoldi step starts from V_{j+1} without a normalisation kernel.
+    static void fgmres_orth(hdg_ctx *c, double *w, long long N, GmresState *fgs, double *vfix) {
         const int go = grid_orth(N);
         launch_k(k_vec_dot, go, VEC_THREADS, 0, c->st, w, c->fV, N, c->rb(), fgs, 0);
-        launch_k(k_gm_orth1<double>, go, VEC_THREADS, 0, c->st, w, c->fV, N, c->rb(), fgs);
-        launch_k(k_gm_orth2<double>, go, VEC_THREADS, 0, c->st, w, c->fV, N, c->rb(), fgs);
+        launch_k(k_fgm_orth1, go, VEC_THREADS, 0, c->st, w, c->fV, N, c->rb(), fgs);
+        launch_k(k_fgm_orth2n, grid_for(N), VEC_THREADS, 0, c->st, (const double *)w, c->fV, vfix, N,
+                 (const GmresState *)fgs);
         CKL();
     }
 
@@ -1226,15 +1230,15 @@ struct Impl {
         capture_while(
             c, [&](LoopCtl L) { launch_k(k_gm_loop_ctl, 1, 1, 0, c->st, L, maxit + 2, fgs, 1); },
             [&](LoopCtl L) {
+                launch_k(k_vec_normalize, g, VEC_THREADS, 0, c->st, res, w, c->fV, c->fv, N, fgs);   // V_0
+                CKL();
                 capture_while(
                     c, [&](LoopCtl L2) { launch_k(k_loop_init, 1, 1, 0, c->st, L2, &fgs->cycle_end); },
                     [&](LoopCtl L2) {
-                        launch_k(k_vec_normalize, g, VEC_THREADS, 0, c->st, res, w, c->fV, c->fv, N, fgs);
-                        CKL();
                         chorin_precond(c, cc, c->fv, c->fz);
                         launch_k(k_slot_store, g, VEC_THREADS, 0, c->st, c->fz, c->fZ, N, fgs);
                         stage_apply(c, cc, c->fz, w);
-                        fgmres_orth(c, w, N, fgs);
+                        fgmres_orth(c, w, N, fgs, c->fv);
                         launch_k(k_loop_ctl, 1, 1, 0, c->st, L2, GM_M + 1, &fgs->cycle_end);
                         CKL();
                     });
@@ -1322,13 +1326,13 @@ struct Impl {
             CK(cudaStreamSynchronize(c->st));
             if (c->hfgs->breakdown == 2) throw std::domain_error("stage FGMRES: non-finite residual");
             if (c->hfgs->converged) { converged = 1; break; }
+            launch_k(k_vec_normalize, g, VEC_THREADS, 0, c->st, res, w, c->fV, nullptr, N, c->fgs);   // V_0
+            CKL();
             for (int j = 0; j < GM_M; ++j) {
-                launch_k(k_vec_normalize, g, VEC_THREADS, 0, c->st, res, w, c->fV, nullptr, N, c->fgs);
-                CKL();
                 double *Vj = c->fV + (size_t)j * N, *Zj = c->fZ + (size_t)j * N;
                 chorin_precond(c, cc, Vj, Zj);
                 stage_apply(c, cc, Zj, w);
-                fgmres_orth(c, w, N, c->fgs);
+                fgmres_orth(c, w, N, c->fgs, nullptr);
                 CKL();
                 CK(cudaMemcpyAsync(c->hfgs, c->fgs, sizeof(GmresState), cudaMemcpyDeviceToHost, c->st));
                 CK(cudaStreamSynchronize(c->st));
