@@ -506,7 +506,8 @@ __global__ void k_pre_rhs(MeshDev M, const float *__restrict__ Lrhs, const doubl
 // U, p of the preconditioner's Step II from w and the trace solution (FP32 map, FP64 in/out)
 template <int K>
 __global__ void k_pre_backsub(MeshDev M, const float *__restrict__ Lbs, const double *__restrict__ w,
-                              const double *__restrict__ lam, double *U, double *p) {
+                              const double *__restrict__ lam, double *U, double *p,
+                              const double *__restrict__ Qbar = nullptr) {
     wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int NU = Dm::NU, NP = Dm::NP, NL = Dm::NL, NT = Dm::NT, RB = NU + NP;
@@ -526,8 +527,12 @@ __global__ void k_pre_backsub(MeshDev M, const float *__restrict__ Lbs, const do
     TFOR(r, RB) {
         float s = 0.f;
         for (int col = 0; col < NP + NL; ++col) s += __ldg(&Lbs[((size_t)col * M.ncells + cell) * RB + r]) * in[col];
-        if (r < NU) U[(size_t)cell * NU + r] = s;
-        else p[(size_t)cell * NP + r - NU] = s;
+        if (r < NU) {                   // with Qbar: the preconditioner's velocity Qbar + U
+            const size_t gi = (size_t)cell * NU + r;
+            U[gi] = Qbar ? Qbar[gi] + (double)s : (double)s;
+        } else {
+            p[(size_t)cell * NP + r - NU] = s;
+        }
     }
 }
 
@@ -1023,7 +1028,7 @@ __device__ void multidot_groups_partials(const RedBuf rb, const T *V, const T *w
 // beta = ||w||
 template <class T>
 __global__ void k_gm_start(long long nrows, const double *__restrict__ b, const double *__restrict__ Bx,
-                           T *w, int first, RedBuf rb, GmresState *gs, double rtol, int maxit) {
+                           T *w, int first, RedBuf rb, GmresState *gs, double rtol, int maxit, int m = 0) {
     wait_prior_kernel();
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(g, nrows) {
@@ -1046,6 +1051,7 @@ __global__ void k_gm_start(long long nrows, const double *__restrict__ b, const 
         for (int i = 0; i <= GM_M; ++i) gs->g[i] = 0.0;
         gs->g[0] = beta;
         gs->j = 0;
+        if (m > 0) gs->m = m;           // restart length of this cycle (else set by k_gm_set_cycle)
         if (!isfinite(beta)) { gs->breakdown = 2; gs->cycle_end = 1; }
         else if (beta <= rtol * gs->bnorm || beta == 0.0) { gs->converged = 1; gs->cycle_end = 1; }
         else gs->cycle_end = 0;
@@ -1320,6 +1326,42 @@ __global__ void k_gm_combine(const T *__restrict__ V, T *u, long long nrows, con
         T s = 0;
         for (int i = 0; i < m; ++i) s += (T)y[i] * V[(size_t)i * nrows + g];
         u[g] = s;
+    }
+}
+
+// End of an inner cycle from x = 0, team per cell: u = V y on the cell's rows, x = Binv u
+// (cell-local), and the solve counted in acc (block 0). Replaces k_gm_combine + k_gm_update_x
+// (first cycle) + k_count_solve.
+template <int K, class T>
+__global__ void k_gm_combine_update(const T *__restrict__ V, const T *__restrict__ Binv, double *x, MeshDev M,
+                                    const GmresState *gs, DevCount *acc) {
+    wait_prior_kernel();
+    constexpr int NU = Dims<K>::NU;
+    __shared__ double ys[GM_M];
+    const int m = gs->j;
+    if ((int)threadIdx.x < m) ys[threadIdx.x] = gs->y[threadIdx.x];
+    if (acc && blockIdx.x == 0 && threadIdx.x == 0) { acc->stepI_iters += gs->total; acc->stepI_solves += 1; }
+    __syncthreads();
+    extern __shared__ double smd[];
+    const int team = threadIdx.x / TEAM_LANES;
+    const int cell = (blockIdx.x * blockDim.x + threadIdx.x) / TEAM_LANES;
+    if (cell >= M.ncells) return;
+    Team tm{(int)(threadIdx.x % TEAM_LANES), TEAM_LANES};
+    T *uK = reinterpret_cast<T *>(smd) + team * NU;
+    const long long nrows = (long long)M.ncells * NU;
+    TFOR(r, NU) {
+        const size_t gi = (size_t)cell * NU + r;
+        T s = 0;
+        for (int i = 0; i < m; ++i) s += (T)ys[i] * V[(size_t)i * nrows + gi];
+        uK[r] = s;
+    }
+    tm.sync();
+    TFOR(r, NU) {
+        const size_t gi = (size_t)cell * NU + r;
+        T a = 0;
+#pragma unroll 6
+        for (int q = 0; q < NU; ++q) a += __ldg(&Binv[(size_t)q * nrows + gi]) * uK[q];
+        x[gi] = (double)a;
     }
 }
 

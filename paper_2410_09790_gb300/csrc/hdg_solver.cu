@@ -975,8 +975,7 @@ struct Impl {
         const long long n = c->nQ;
         const int g = grid_for(n);
         const EdgeTab<float> E{c->ephi32, c->pen32, c->nrm32};
-        launch_k(k_gm_start<float>, g, VEC_THREADS, 0, c->st, n, b, nullptr, c->gw32, 1, c->rb(), c->gs, -1.0, 0);
-        launch_k(k_gm_set_cycle, 1, 1, 0, c->st, c->gs, GM_M);
+        launch_k(k_gm_start<float>, g, VEC_THREADS, 0, c->st, n, b, nullptr, c->gw32, 1, c->rb(), c->gs, -1.0, 0, GM_M);
         capture_while(
             c, [&](LoopCtl L) { launch_k(k_loop_init, 1, 1, 0, c->st, L, &c->gs->cycle_end); },
             [&](LoopCtl L) {
@@ -985,9 +984,8 @@ struct Impl {
                 launch_k(k_gm_finish_ctl, 1, 256, 0, c->st, L, GM_M + 1, c->rb(), (int)ab, c->gs);
             });
         launch_k(k_gm_solve, 1, 256, 0, c->st, c->gs, nullptr);
-        launch_k(k_gm_combine<float>, g, VEC_THREADS, 0, c->st, c->gV32, c->gu32, n, c->gs);
-        launch_k(k_gm_update_x<K, float>, g, VEC_THREADS, 0, c->st, c->Binv32, c->gu32, x, c->ncells, 1);
-        launch_k(k_count_solve, 1, 1, 0, c->st, c->dcnt, c->gs, nullptr);
+        launch_k(k_gm_combine_update<K, float>, cell_blocks(c), 128, sizeof(float) * TEAMS_PER_BLOCK * NU, c->st, c->gV32,
+                 c->Binv32, x, c->M, (const GmresState *)c->gs, c->dcnt);
         CKL();
     }
 
@@ -995,7 +993,7 @@ struct Impl {
     static void gmres_start(hdg_ctx *c, int first) {
         if (!first) cell_apply(c, c->gx, c->gz);
         launch_k(k_gm_start<double>, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->nQ, c->gb, first ? nullptr : c->gz, c->gw,
-                                                                      first, c->rb(), c->gs, -1.0, 0);
+                                                                      first, c->rb(), c->gs, -1.0, 0, 0);
     }
 
     // Restarted GMRES(GM_M) on the assembled Step-I operator with right block-Jacobi
@@ -1150,8 +1148,11 @@ struct Impl {
 
     // Step II of the stage preconditioner: from the Step-I velocity X and the constraint rows
     // (vp, vl) of the input, the velocity correction U and (zp, zl)
-    static void pre_step2(hdg_ctx *c, double cc, const double *X, const double *vp, const double *vl, double *U,
-                          double *zp, double *zl) {
+    // With Qbar and zQ set and the FP32 cell maps in use, zQ receives Qbar + U directly (U is not
+    // written) and the function returns true.
+    static bool pre_step2(hdg_ctx *c, double cc, const double *X, const double *vp, const double *vl, double *U,
+                          double *zp, double *zl, const double *Qbar = nullptr, double *zQ = nullptr) {
+        bool fused = false;
         c->trace_vcycles = c->P.inner_trace_vcycles;
         try {
             CondCache &E = condense(c, cc);
@@ -1167,8 +1168,10 @@ struct Impl {
                     CKL();
                     trace_solve(c, E, c->tb, zl, c->P.inner_trace_rtol);
                 }
+                fused = Qbar && zQ;
                 launch_k(k_pre_backsub<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (NP + NL), c->st, c->M, E.Lbs32, c->wK,
-                                                                                                zl, U, zp);
+                                                                                                zl, fused ? zQ : U, zp,
+                                                                                                fused ? Qbar : nullptr);
                 CKL();
             } else {
                 mixed_solve(c, cc, nullptr, X, nullptr, nullptr, U, zp, zl, vp, vl, c->P.inner_trace_rtol);
@@ -1178,6 +1181,7 @@ struct Impl {
             throw;
         }
         c->trace_vcycles = 0;
+        return fused;
     }
 
     // Chorin split as a preconditioner: z = P^{-1} v (Step I, then Step II on the constraint rows)
@@ -1186,7 +1190,7 @@ struct Impl {
         double *zQ = z, *zp = z + c->nQ, *zl = z + c->nQ + c->nPv;
         double *Qbar = c->q[2], *U = c->q[4];
         stepI_solve(c, vQ, Qbar, c->P.inner_stepI_rtol);
-        pre_step2(c, cc, Qbar, vp, vl, U, zp, zl);
+        if (pre_step2(c, cc, Qbar, vp, vl, U, zp, zl, Qbar, zQ)) return;    // zQ = Qbar + U written there
         LinComb L{};
         L.nterms = 2; L.coef[0] = 1; L.vec[0] = Qbar; L.coef[1] = 1; L.vec[1] = U;
         launch_k(k_lincomb, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->geo, NU, L, zQ, c->ncells);
