@@ -416,7 +416,7 @@ __host__ __device__ void cell_bdm(const Team &tm, const RefDev &R, const CellGeo
 template <int K>
 constexpr int fimpl_diag_scratch() {
     typedef Dims<K> Dm;
-    return 2 * Dm::NQ + 3 * Dm::NFQ + Dm::MU * Dm::MU + Dm::NQ * Dm::MU + 6 * Dm::MU * Dm::MU;
+    return 2 * Dm::NQ + 3 * Dm::NFQ + Dm::MU * Dm::MU + Dm::NQ * Dm::MU + 6 * Dm::MU * Dm::MU + 6 * Dm::NFQ * Dm::MU;
 }
 
 template <int K>
@@ -432,6 +432,8 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
     double *G = adv + MU * MU;       // NQ x MU: w_q (beta(q) . grad phi_b(q))
     double *Sp = G + NQ * MU;        // 3 x MU x MU: sum_q fw phi_a phi_b on edge e
     double *Wa = Sp + 3 * MU * MU;   // 3 x MU x MU: the same weighted by Q*.n/2 - delta |Q*.n|
+    double *T1 = Wa + 3 * MU * MU;   // 3 x NFQ x MU: fw_q phi_b(e, q)
+    double *T2 = T1 + 3 * NFQ * MU;  // 3 x NFQ x MU: the same times Q*.n/2 - delta |Q*.n| (0 on walls)
     TFOR(q, NQ) {
         double v0 = 0, v1 = 0;
         for (int a = 0; a < MU; ++a) {
@@ -463,17 +465,12 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
         int q = i / MU, b = i % MU;
         G[i] = ldg(&R.qw[q]) * (beta[2 * q] * ldg(&R.dphi[(q * MU + b) * 2]) + beta[2 * q + 1] * ldg(&R.dphi[(q * MU + b) * 2 + 1]));
     }
-    TFOR(i, 3 * MU * MU) {
-        int e = i / (MU * MU), a = (i / MU) % MU, b = i % MU;
-        double sp = 0, sa = 0;
-        const bool inter = Qsn[e] != nullptr;
-        for (int q = 0; q < NFQ; ++q) {
-            double ff = ldg(&R.fw[q]) * ldg(&R.ephi[(e * NFQ + q) * MU + a]) * ldg(&R.ephi[(e * NFQ + q) * MU + b]);
-            sp += ff;
-            if (inter) sa += ff * (0.5 * qsn[e * NFQ + q] - dup * fabs(qsn[e * NFQ + q]));
-        }
-        Sp[i] = sp;
-        Wa[i] = sa;
+    TFOR(i, 3 * NFQ * MU) {             // facet masses as E^T diag(weights) E: the weighted rows first
+        const int e = i / (NFQ * MU), q = (i / MU) % NFQ, b = i % MU;
+        const double f = ldg(&R.fw[q]) * ldg(&R.ephi[(e * NFQ + q) * MU + b]);
+        const double sq = qsn[e * NFQ + q];
+        T1[i] = f;
+        T2[i] = Qsn[e] ? f * (0.5 * sq - dup * fabs(sq)) : 0.0;
     }
     TFOR(i, 3 * NFQ) {
         int e = i / NFQ, q = i % NFQ;
@@ -485,6 +482,17 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
         double s = 0;
         for (int q = 0; q < NQ; ++q) s += ldg(&R.phi[q * MU + a]) * G[q * MU + b];
         adv[i] = -g.detJ * s;
+    }
+    TFOR(i, 3 * MU * MU) {              // Sp, Wa = sum_q phi_a(e, q) (T1, T2)[e][q][b]
+        const int e = i / (MU * MU), a = (i / MU) % MU, b = i % MU;
+        double sp = 0, sa = 0;
+        for (int q = 0; q < NFQ; ++q) {
+            const double pa = ldg(&R.ephi[(e * NFQ + q) * MU + a]);
+            sp += pa * T1[(e * NFQ + q) * MU + b];
+            sa += pa * T2[(e * NFQ + q) * MU + b];
+        }
+        Sp[i] = sp;
+        Wa[i] = sa;
     }
     tm.sync();
     TFOR(i, NU * NU) {                  // diagonal block

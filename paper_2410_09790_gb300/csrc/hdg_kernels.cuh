@@ -429,7 +429,7 @@ __global__ void k_mixed_rhs(RefDev R, MeshDev M, double tau, const double *Ru, c
 
 // b_F = sum over the facet's cells of v_K (canonical rows of the facet's local edge) - sub_F
 template <int NT>
-__global__ void k_facet_gather(MeshDev M, const double *__restrict__ v, const double *sub, double *b) {
+__global__ void k_facet_gather(MeshDev M, const double *__restrict__ v, const double *sub, double *b, float *b32) {
     wait_prior_kernel();
     GRID_STRIDE(g, (long long)M.nfacets * NT) {
         int f = (int)(g / NT), j = (int)(g % NT);
@@ -440,6 +440,7 @@ __global__ void k_facet_gather(MeshDev M, const double *__restrict__ v, const do
             s += v[(size_t)c * 3 * NT + M.facet_edge[2 * f + side] * NT + j];
         }
         b[g] = s;
+        if (b32) b32[g] = (float)s;
     }
 }
 
@@ -728,13 +729,15 @@ __global__ void k_cell_apply_mf(EdgeTab<double> E, MeshDev M, const double *__re
 }
 
 // ------------------------------------------------------------------ stage operator, fused
-// The stage operator A(c) applied to x = (Q, p, lambda) in one pass per cell: velocity rows
+// The stage operator A(c) applied to x = (Q, p, lambda) in one pass per cell (yQ32, yp32: FP32
+// copies of the output for the FGMRES first-pass dots, when set): velocity rows
 // (M - cF)Q - c G(p, lambda) (diagonal block dense, neighbours matrix-free), constraint rows of
 // the cell (p-rows yp, the cell's lambda-row contributions v; summed per facet by k_facet_gather).
 template <int K>
 __global__ void k_stage_apply(RefDev R, EdgeTab<double> E, MeshDev M, const double *__restrict__ Dblk,
                               const double *__restrict__ wq, double c, double tau, const double *Q,
-                              const double *p, const double *lam, double *yQ, double *yp, double *v) {
+                              const double *p, const double *lam, double *yQ, double *yp, double *v,
+                              float *yQ32, float *yp32) {
     wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NP = Dm::NP, NT = Dm::NT, NL = Dm::NL, NFQ = Dm::NFQ;
@@ -765,10 +768,13 @@ __global__ void k_stage_apply(RefDev R, EdgeTab<double> E, MeshDev M, const doub
             for (int b = 0; b < NP; ++b) s += ldg(&R.Dhat[(rr * NP + b) * MU + a]) * pK[b];
             dt += g.Jinv[rr * 2 + d] * s;
         }
-        yQ[gi] = bq - c * (g.detJ * dt - et);
+        const double yv = bq - c * (g.detJ * dt - et);
+        yQ[gi] = yv;
+        if (yQ32) yQ32[gi] = (float)yv;
     }
     int flip[3] = {M.cell_flip[3 * cell], M.cell_flip[3 * cell + 1], M.cell_flip[3 * cell + 2]};
     cell_constraint<K>(tm, R, g, flip, tau, QK, pK, lK, cs, yp + (size_t)cell * NP, v + (size_t)cell * NL);
+    if (yp32) TFOR(b, NP) yp32[(size_t)cell * NP + b] = (float)yp[(size_t)cell * NP + b];   // (team-synced)
 }
 
 
@@ -1467,7 +1473,7 @@ __global__ void k_vec_norm_into(const double *__restrict__ b, long long n, RedBu
 // V_j = w / h  (w = w0 and h = beta for j = 0, else w and H[j, j-1]); vfix (optional) gets a
 // copy of V_j at a fixed address
 __global__ void k_vec_normalize(const double *__restrict__ w0, const double *__restrict__ w, double *V,
-                                double *vfix, long long n, const GmresState *gs) {
+                                double *vfix, long long n, const GmresState *gs, float *V32) {
     wait_prior_kernel();
     if (gs->cycle_end) return;
     const int j = gs->j;
@@ -1475,11 +1481,23 @@ __global__ void k_vec_normalize(const double *__restrict__ w0, const double *__r
     const double inv = 1.0 / h;
     const double *src = j == 0 ? w0 : w;
     double *vj = V + (size_t)j * n;
+    float *vj32 = V32 ? V32 + (size_t)j * n : nullptr;
     GRID_STRIDE(i, n) {
         double v = src[i] * inv;
         vj[i] = v;
         if (vfix) vfix[i] = v;
+        if (vj32) vj32[i] = (float)v;
     }
+}
+
+// hcol = V32^T w32 over V_0..V_j in FP32 (FP32 shadows of the FGMRES basis and of w): the first
+// classical Gram-Schmidt pass of the stage FGMRES. Its error (1e-7 of |w|) is removed by the FP64
+// second pass, and H uses the same hcol as the update, so the Arnoldi relation stays FP64.
+__global__ void k_vec_dot32(const float *__restrict__ w32, const float *__restrict__ V32, long long n, RedBuf rb,
+                            GmresState *gs) {
+    wait_prior_kernel();
+    if (gs->cycle_end) return;
+    multidot_rows(rb, V32, w32, n, gs->j + 1, gs->hcol, false);
 }
 
 // hcol = V^T w over V_0..V_j
@@ -1527,7 +1545,7 @@ __global__ void k_fgm_orth1(double *w, const double *__restrict__ V, long long n
 // Second half: v_{j+1} = (w' - V h2) / hn written to V_{j+1} (and vfix when set), for the step
 // the previous kernel finished (gs->j already advanced; nothing when the cycle ended)
 __global__ void k_fgm_orth2n(const double *__restrict__ w, double *V, double *vfix, long long nrows,
-                             const GmresState *gs) {
+                             const GmresState *gs, float *V32) {
     wait_prior_kernel();
     if (gs->cycle_end) return;
     const int jn = gs->j;                        // the new basis slot
@@ -1537,12 +1555,14 @@ __global__ void k_fgm_orth2n(const double *__restrict__ w, double *V, double *vf
     if (threadIdx.x == 0) inv = 1.0 / gs->H[(jn - 1) * (GM_M + 1) + jn];
     __syncthreads();
     double *vn = V + (size_t)jn * nrows;
+    float *vn32 = V32 ? V32 + (size_t)jn * nrows : nullptr;
     GRID_STRIDE(g, nrows) {
         double s = w[g];
         for (int i = 0; i < jn; ++i) s -= h[i] * V[(size_t)i * nrows + g];
         s *= inv;
         vn[g] = s;
         if (vfix) vfix[g] = s;
+        if (vn32) vn32[g] = (float)s;
     }
 }
 

@@ -177,6 +177,7 @@ struct hdg_ctx {
     GmresState *gs = nullptr, *hgs = nullptr;
     // flexible GMRES on the stage system (vectors of nQ + np + nlambda)
     double *fV = nullptr, *fZ = nullptr, *fx = nullptr, *fb = nullptr, *fw = nullptr, *fr = nullptr, *fu = nullptr;
+    float *fV32 = nullptr, *fw32 = nullptr;                  // FP32 shadows of the basis and of w
     double *fv = nullptr, *fz = nullptr;                     // preconditioner input / output (fixed)
     GmresState *fgs = nullptr, *hfgs = nullptr;
     // temporaries
@@ -764,7 +765,7 @@ struct Impl {
         unsigned nb = cell_blocks(c);
         launch_k(k_mixed_rhs<K>, nb, 128, smem_rhs, c->st, c->R, c->M, c->P.tau, Ru, X, p, lam, Rp_add, E.Zc, c->vK, c->wK);
         CKL();
-        launch_k(k_facet_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, Rl_add, c->tb);
+        launch_k(k_facet_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, Rl_add, c->tb, (float *)nullptr);
         CKL();
         trace_solve(c, E, c->tb, dl, rtol > 0 ? rtol : c->P.trace_rtol);
         size_t smem_bs = sizeof(double) * TEAMS_PER_BLOCK * (NL + NP);
@@ -1135,14 +1136,17 @@ struct Impl {
 
     // Stage operator y = A(c) x, x = (Q | p | lam) contiguous:
     //   yQ = (M - cF) Q - c G (p, lam),  (yp | ylam) = B Q + C (p, lam)   (one fused cell pass)
-    static void stage_apply(hdg_ctx *c, double cc, const double *x, double *y) {
+    // y32 (optional): an FP32 copy of y
+    static void stage_apply(hdg_ctx *c, double cc, const double *x, double *y, float *y32 = nullptr) {
         const double *Q = x, *p = x + c->nQ, *lam = x + c->nQ + c->nPv;
         double *yQ = y, *yp = y + c->nQ, *yl = y + c->nQ + c->nPv;
+        float *yQ32 = y32, *yp32 = y32 ? y32 + c->nQ : nullptr, *yl32 = y32 ? y32 + c->nQ + c->nPv : nullptr;
         unsigned nb = cell_blocks(c);
         launch_k(k_stage_apply<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (6 * Dm::NFQ + NL + 2 * MU), c->st, 
-            c->R, EdgeTab<double>{c->R.ephi, c->pen}, c->M, c->Dblk, c->wq, cc, c->P.tau, Q, p, lam, yQ, yp, c->vK);
+            c->R, EdgeTab<double>{c->R.ephi, c->pen}, c->M, c->Dblk, c->wq, cc, c->P.tau, Q, p, lam, yQ, yp, c->vK,
+            yQ32, yp32);
         CKL();
-        launch_k(k_facet_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, nullptr, yl);
+        launch_k(k_facet_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, nullptr, yl, yl32);
         CKL();
     }
 
@@ -1164,7 +1168,7 @@ struct Impl {
                 if (E.mg32 && c->P.inner_trace_fp32 && c->trace_vcycles == 1) {
                     trace_vcycle32(c, E, vl, zl);
                 } else {
-                    launch_k(k_facet_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, vl, c->tb);
+                    launch_k(k_facet_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, vl, c->tb, (float *)nullptr);
                     CKL();
                     trace_solve(c, E, c->tb, zl, c->P.inner_trace_rtol);
                 }
@@ -1202,12 +1206,13 @@ struct Impl {
     // The second pass's norm comes from Pythagoras with its own dots, so the last kernel only
     // forms v_{j+1} = (w' - V h2) / hn in V (and in vfix when set): no reduction there, and the
     // next Arnoldi step starts from V_{j+1} without a normalisation kernel.
+    // The first pass's dots run in FP32 on the shadows (c->fw32 = FP32 w from the stage operator).
     static void fgmres_orth(hdg_ctx *c, double *w, long long N, GmresState *fgs, double *vfix) {
         const int go = grid_orth(N);
-        launch_k(k_vec_dot, go, VEC_THREADS, 0, c->st, w, c->fV, N, c->rb(), fgs, 0);
+        launch_k(k_vec_dot32, go, VEC_THREADS, 0, c->st, (const float *)c->fw32, (const float *)c->fV32, N, c->rb(), fgs);
         launch_k(k_fgm_orth1, go, VEC_THREADS, 0, c->st, w, c->fV, N, c->rb(), fgs);
         launch_k(k_fgm_orth2n, grid_for(N), VEC_THREADS, 0, c->st, (const double *)w, c->fV, vfix, N,
-                 (const GmresState *)fgs);
+                 (const GmresState *)fgs, c->fV32);
         CKL();
     }
 
@@ -1234,14 +1239,14 @@ struct Impl {
         capture_while(
             c, [&](LoopCtl L) { launch_k(k_gm_loop_ctl, 1, 1, 0, c->st, L, maxit + 2, fgs, 1); },
             [&](LoopCtl L) {
-                launch_k(k_vec_normalize, g, VEC_THREADS, 0, c->st, res, w, c->fV, c->fv, N, fgs);   // V_0
+                launch_k(k_vec_normalize, g, VEC_THREADS, 0, c->st, res, w, c->fV, c->fv, N, fgs, c->fV32);   // V_0
                 CKL();
                 capture_while(
                     c, [&](LoopCtl L2) { launch_k(k_loop_init, 1, 1, 0, c->st, L2, &fgs->cycle_end); },
                     [&](LoopCtl L2) {
                         chorin_precond(c, cc, c->fv, c->fz);
                         launch_k(k_slot_store, g, VEC_THREADS, 0, c->st, c->fz, c->fZ, N, fgs);
-                        stage_apply(c, cc, c->fz, w);
+                        stage_apply(c, cc, c->fz, w, c->fw32);
                         fgmres_orth(c, w, N, fgs, c->fv);
                         launch_k(k_loop_ctl, 1, 1, 0, c->st, L2, GM_M + 1, &fgs->cycle_end);
                         CKL();
@@ -1330,12 +1335,12 @@ struct Impl {
             CK(cudaStreamSynchronize(c->st));
             if (c->hfgs->breakdown == 2) throw std::domain_error("stage FGMRES: non-finite residual");
             if (c->hfgs->converged) { converged = 1; break; }
-            launch_k(k_vec_normalize, g, VEC_THREADS, 0, c->st, res, w, c->fV, nullptr, N, c->fgs);   // V_0
+            launch_k(k_vec_normalize, g, VEC_THREADS, 0, c->st, res, w, c->fV, nullptr, N, c->fgs, c->fV32);   // V_0
             CKL();
             for (int j = 0; j < GM_M; ++j) {
                 double *Vj = c->fV + (size_t)j * N, *Zj = c->fZ + (size_t)j * N;
                 chorin_precond(c, cc, Vj, Zj);
-                stage_apply(c, cc, Zj, w);
+                stage_apply(c, cc, Zj, w, c->fw32);
                 fgmres_orth(c, w, N, c->fgs, nullptr);
                 CKL();
                 CK(cudaMemcpyAsync(c->hfgs, c->fgs, sizeof(GmresState), cudaMemcpyDeviceToHost, c->st));
@@ -1755,6 +1760,8 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         if (params->n_richardson <= 0 && params->stage_krylov) {
             const size_t N = nQ + nP + nL;
             c->fV = c->alloc<double>((size_t)(GM_M + 1) * N);
+            c->fV32 = c->alloc<float>((size_t)(GM_M + 1) * N);
+            c->fw32 = c->alloc<float>(N);
             c->fZ = c->alloc<double>((size_t)GM_M * N);
             c->fx = c->alloc<double>(N); c->fb = c->alloc<double>(N); c->fw = c->alloc<double>(N);
             c->fr = c->alloc<double>(N); c->fu = c->alloc<double>(N);
@@ -2198,7 +2205,8 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 const size_t sm = sizeof(double) * TEAMS_PER_BLOCK * (6 * nfq + 3 * NT + 2 * I::MU);
                 auto launch = [&]() {
                     launch_k(k_stage_apply<I::K_>, nb, 128, sm, c->st, c->R, EdgeTab<double>{c->R.ephi, c->pen}, c->M,
-                             c->Dblk, c->wq, cc, c->P.tau, c->Q, c->p, c->lam, c->q[6], c->pp[1], c->vK);
+                             c->Dblk, c->wq, cc, c->P.tau, c->Q, c->p, c->lam, c->q[6], c->pp[1], c->vK,
+                             (float *)nullptr, (float *)nullptr);
                 };
                 launch();
                 CKL();
@@ -2281,7 +2289,7 @@ void trace_apply_noalloc_impl(hdg_ctx *c, double cc, const double *lam_nodal, do
                                     NP * NP + NL);
     launch_k(k_condense_apply_cell<K>, (unsigned)c->ncells, 128, smem, c->st, c->R, c->M, cc, c->P.tau, lm, z);
     CKL();
-    launch_k(k_facet_gather<NT>, red_grid(c->nL), VEC_THREADS, 0, c->st, c->M, z, nullptr, ym);
+    launch_k(k_facet_gather<NT>, red_grid(c->nL), VEC_THREADS, 0, c->st, c->M, z, nullptr, ym, (float *)nullptr);
     CKL();
     launch_k(k_trace_riesz, red_grid(c->nL), VEC_THREADS, 0, c->st, c->geo, c->M.facet_cell, c->M.facet_edge, NT, ym, yr,
                                                               c->nfacets);
