@@ -235,7 +235,9 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *ctx, hdg_stats *stats);
  * FGMRES matrix-vector product without the facet gather) on the operator last assembled, input
  * the current state; bytes = its algorithmic bytes. which = 9: the FP32 preconditioner pass of
  * the inner Step-I GMRES (v_j formed from w and the projections, z = B^-1 v_j, z's edge values) at
- * step j = 4, launched like 6; bytes = its algorithmic bytes. */
+ * step j = 4, launched like 6; bytes = its algorithmic bytes. which = 10 (bytes = 0): one inner FP32
+ * Arnoldi step as the solve runs it (preconditioner pass, product, finishing kernel), from 20 steps
+ * launched back to back after a cycle start, less the cycle start alone. */
 hdg_status hdg_time_kernel(hdg_ctx *ctx, int which, double c, int reps, double *ms_per_launch,
                            double *bytes_per_launch);
 

@@ -1164,7 +1164,10 @@ __global__ void k_gm_apply_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ wq,
 // 1e-12 ||w||^2 floor, previous rotations, new Givens rotation, residual estimate, convergence)
 // and sets the condition of the loop whose body it ends: continue while the cycle has not ended
 // and the pass guard is below limit.
-__global__ void __launch_bounds__(256) k_gm_finish_ctl(LoopCtl L, int limit, RedBuf rb, int nblocks, GmresState *gs) {
+// With ctl = 0 (an Arnoldi step inside an unrolled loop body, not its last) the loop's guard,
+// counter and condition are left alone.
+__global__ void __launch_bounds__(256) k_gm_finish_ctl(LoopCtl L, int limit, RedBuf rb, int nblocks, GmresState *gs,
+                                                       int ctl) {
     wait_prior_kernel();
     __shared__ double red[GM_M + 2][8];        // per value, per warp
     __shared__ double Hc[GM_M + 2], cs[GM_M], sn[GM_M], gv[GM_M + 1], dsc[2];
@@ -1178,9 +1181,9 @@ __global__ void __launch_bounds__(256) k_gm_finish_ctl(LoopCtl L, int limit, Red
     else if (t == 66) isc[2] = gs->m;
     else if (t == 67) isc[3] = gs->total;
     else if (t == 68) isc[4] = gs->maxit;
-    else if (t == 69) isc[5] = *L.guard;
-    else if (t == 70) isc[6] = *L.nk;
-    else if (t == 71) nlaunch = *L.launches;
+    else if (t == 69) isc[5] = ctl ? *L.guard : 0;           // (the loop state only when ctl)
+    else if (t == 70) isc[6] = ctl ? *L.nk : 0;
+    else if (t == 71) nlaunch = ctl ? *L.launches : 0ull;
     else if (t == 72) dsc[0] = gs->rtol;
     else if (t == 73) dsc[1] = gs->bnorm;
     __syncthreads();
@@ -1247,7 +1250,7 @@ __global__ void __launch_bounds__(256) k_gm_finish_ctl(LoopCtl L, int limit, Red
             if (end) gs->cycle_end = 1;
         }
     }
-    if (t == 0) {
+    if (t == 0 && ctl) {
         const int gd = isc[5] + 1;
         *L.guard = gd;
         *L.launches = nlaunch + (unsigned long long)isc[6];

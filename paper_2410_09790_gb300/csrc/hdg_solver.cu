@@ -965,6 +965,18 @@ struct Impl {
         launch_k(k_count_solve, 1, 1, 0, c->st, c->dcnt, c->gs, (const Scalars *)nullptr);
     }
 
+    // Arnoldi steps per pass of the inner FP32 loop (HDG_INNER_UNROLL overrides the default)
+    static int inner_unroll() {
+        static int v = -1;
+        if (v < 0) {
+            const char *e = std::getenv("HDG_INNER_UNROLL");
+            v = e ? std::atoi(e) : 4;
+            if (v < 1) v = 1;
+            if (v > 8) v = 8;
+        }
+        return v;
+    }
+
     // A loose Step-I solve in FP32, recorded into the current capture: one GMRES(GM_M) cycle from
     // x = 0 with its Arnoldi steps as a device-side loop, stopping at the tolerance or after GM_M
     // steps (an inexact solve is what the flexible outer iteration expects). b, x: FP64.
@@ -980,9 +992,12 @@ struct Impl {
         capture_while(
             c, [&](LoopCtl L) { launch_k(k_loop_init, 1, 1, 0, c->st, L, &c->gs->cycle_end); },
             [&](LoopCtl L) {
-                gmres_arnoldi<float>(c, E, c->Binv32, c->wq32, c->utr32, c->gw32, c->gV32);
                 const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
-                launch_k(k_gm_finish_ctl, 1, 256, 0, c->st, L, GM_M + 1, c->rb(), (int)ab, c->gs);
+                const int U = inner_unroll();
+                for (int u = 0; u < U; ++u) {
+                    gmres_arnoldi<float>(c, E, c->Binv32, c->wq32, c->utr32, c->gw32, c->gV32);
+                    launch_k(k_gm_finish_ctl, 1, 256, 0, c->st, L, GM_M / U + 2, c->rb(), (int)ab, c->gs, u == U - 1 ? 1 : 0);
+                }
             });
         launch_k(k_gm_solve, 1, 256, 0, c->st, c->gs, nullptr);
         launch_k(k_gm_combine_update<K, float>, cell_blocks(c), 128, sizeof(float) * TEAMS_PER_BLOCK * NU, c->st, c->gV32,
@@ -2076,10 +2091,53 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *c, hdg_stats *stats) {
 }
 
 hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *ms, double *bytes) {
-    if (!c || reps < 1 || !ms || !bytes || which < 0 || which > 9 || (which != 1 && !(cc > 0)))
+    if (!c || reps < 1 || !ms || !bytes || which < 0 || which > 10 || (which != 1 && !(cc > 0)))
         return HDG_ERR_INVALID_ARG;
     if (which >= 2 && which != 8 && !c->fv) return HDG_ERR_INVALID_ARG;
     try {
+        if (which == 10) {
+            double t10 = 0.0;
+            DISPATCH(c, {
+                // S inner FP32 Arnoldi steps (preconditioner pass, product, finishing kernel) launched
+                // back to back after a cycle start, minus the cycle start alone, per step
+                constexpr int S = 20;
+                I::bdm(c, c->Q, c->q[5]);
+                I::assemble_stepI(c, c->q[5], cc, I::INV32);
+                I::mass(c, c->Q, c->fv, 0);
+                const long long n = c->nQ;
+                const EdgeTab<float> E{c->ephi32, c->pen32, c->nrm32};
+                const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
+                auto start = [&]() {
+                    launch_k(k_gm_start<float>, grid_for(n), VEC_THREADS, 0, c->st, n, (const double *)c->fv,
+                             (const double *)nullptr, c->gw32, 1, c->rb(), c->gs, 1e-30, 1000, GM_M);
+                };
+                auto steps = [&]() {
+                    start();
+                    for (int k = 0; k < S; ++k) {
+                        I::template gmres_arnoldi<float>(c, E, c->Binv32, c->wq32, c->utr32, c->gw32, c->gV32);
+                        launch_k(k_gm_finish_ctl, 1, 256, 0, c->st, LoopCtl{}, 0, c->rb(), (int)ab, c->gs, 0);
+                    }
+                };
+                steps();
+                CKL();
+                CK(cudaEventRecord(c->e0, c->st));
+                for (int r = 0; r < reps; ++r) start();
+                CK(cudaEventRecord(c->e1, c->st));
+                CK(cudaEventSynchronize(c->e1));
+                float t_start = 0;
+                CK(cudaEventElapsedTime(&t_start, c->e0, c->e1));
+                CK(cudaEventRecord(c->e0, c->st));
+                for (int r = 0; r < reps; ++r) steps();
+                CK(cudaEventRecord(c->e1, c->st));
+                CK(cudaEventSynchronize(c->e1));
+                float t_all = 0;
+                CK(cudaEventElapsedTime(&t_all, c->e0, c->e1));
+                t10 = (double)(t_all - t_start) / reps / S;
+                *bytes = 0;
+            });
+            *ms = t10;
+            return HDG_OK;
+        }
         if (which == 6 || which == 9) {
             double t6_ms = 0.0;
             DISPATCH(c, {
