@@ -790,6 +790,9 @@ struct GmresState {
     int j, cycle_end, converged, total, maxit, breakdown, m;   // m: restart length of this cycle
     // FP32 copies for the FUSED inner kernels: 1 / (norm of the step's w) and the projections
     float inv32, hcol32[GM_M + 2];
+    // the FP32 inner solves keep their Hessenberg matrix, rotations, residual estimates and
+    // least-squares solution in FP32 (tol32 = rtol * bnorm)
+    float H32[(GM_M + 1) * GM_M], cs32[GM_M], sn32[GM_M], g32[GM_M + 1], y32[GM_M], tol32;
 };
 
 __global__ void k_gm_set_cycle(GmresState *gs, int m) {
@@ -944,7 +947,7 @@ __global__ void k_count_stage(DevCount *acc, const GmresState *fgs) {
 // the extra vector counted). With fence, each partial is fenced for a last-block reduction.
 template <class T, class Ranges>
 __device__ int block_dot_partials(const RedBuf rb, const T *V, const T *w, long long n, int nvec, Ranges ranges,
-                                  const T *extra, bool fence) {
+                                  const T *extra, bool fence, bool f32 = false) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     if (extra) ++nvec;                   // (extra, w) -> value nvec - 1
     for (int i = warp; i < nvec; i += nw) {
@@ -955,7 +958,8 @@ __device__ int block_dot_partials(const RedBuf rb, const T *V, const T *w, long 
         });
         for (int o = 16; o > 0; o >>= 1) at += __shfl_down_sync(0xffffffffu, at, o);
         if (lane == 0) {
-            rb.partials[blockIdx.x * (GM_M + 2) + i] = (double)at;
+            if (f32) reinterpret_cast<float *>(rb.partials)[blockIdx.x * (GM_M + 2) + i] = (float)at;
+            else rb.partials[blockIdx.x * (GM_M + 2) + i] = (double)at;
             if (fence) __threadfence();
         }
     }
@@ -1019,7 +1023,7 @@ __device__ bool multidot_groups(const RedBuf rb, const T *V, const T *w, long lo
     }, out, with_norm ? w : nullptr);
 }
 
-// the partials of multidot_groups only (reduced by k_gm_finish_ctl)
+// the partials of multidot_groups only, in FP32 (reduced by k_gm_finish_ctl)
 template <class T>
 __device__ void multidot_groups_partials(const RedBuf rb, const T *V, const T *w, long long nrows,
                                          long long rows_per_group, int nvec, bool with_norm) {
@@ -1027,7 +1031,7 @@ __device__ void multidot_groups_partials(const RedBuf rb, const T *V, const T *w
     block_dot_partials(rb, V, w, nrows, nvec, [&](auto f) {
         for (long long g0 = blockIdx.x * rows_per_group; g0 < nrows; g0 += gridDim.x * rows_per_group)
             f(g0, g0 + rows_per_group < nrows ? g0 + rows_per_group : nrows);
-    }, with_norm ? w : nullptr, false);
+    }, with_norm ? w : nullptr, false, true);
 }
 
 // start of a cycle: w = b - Bx (Bx = B x precomputed; null on the first cycle, x = 0: w = b);
@@ -1056,6 +1060,8 @@ __global__ void k_gm_start(long long nrows, const double *__restrict__ b, const 
         gs->resid = beta;
         for (int i = 0; i <= GM_M; ++i) gs->g[i] = 0.0;
         gs->g[0] = beta;
+        gs->g32[0] = (float)beta;
+        gs->tol32 = (float)(gs->rtol * gs->bnorm);
         gs->j = 0;
         if (m > 0) gs->m = m;           // restart length of this cycle (else set by k_gm_set_cycle)
         if (!isfinite(beta)) { gs->breakdown = 2; gs->cycle_end = 1; }
@@ -1169,13 +1175,13 @@ __global__ void k_gm_apply_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ wq,
 __global__ void __launch_bounds__(256) k_gm_finish_ctl(LoopCtl L, int limit, RedBuf rb, int nblocks, GmresState *gs,
                                                        int ctl) {
     wait_prior_kernel();
-    __shared__ double red[GM_M + 2][8];        // per value, per warp
-    __shared__ double Hc[GM_M + 2], cs[GM_M], sn[GM_M], gv[GM_M + 1], dsc[2];
+    __shared__ float red[GM_M + 2][8];         // per value, per warp
+    __shared__ float Hc[GM_M + 2], cs[GM_M], sn[GM_M], gv[GM_M + 1], tol;
     __shared__ int isc[8];
     __shared__ unsigned long long nlaunch;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = (int)(blockDim.x >> 5);
-    if (t < GM_M) { cs[t] = gs->cs[t]; sn[t] = gs->sn[t]; }
-    else if (t >= 32 && t < 32 + GM_M + 1) gv[t - 32] = gs->g[t - 32];
+    if (t < GM_M) { cs[t] = gs->cs32[t]; sn[t] = gs->sn32[t]; }
+    else if (t >= 32 && t < 32 + GM_M + 1) gv[t - 32] = gs->g32[t - 32];
     else if (t == 64) isc[0] = gs->cycle_end;
     else if (t == 65) isc[1] = gs->j;
     else if (t == 66) isc[2] = gs->m;
@@ -1184,69 +1190,65 @@ __global__ void __launch_bounds__(256) k_gm_finish_ctl(LoopCtl L, int limit, Red
     else if (t == 69) isc[5] = ctl ? *L.guard : 0;           // (the loop state only when ctl)
     else if (t == 70) isc[6] = ctl ? *L.nk : 0;
     else if (t == 71) nlaunch = ctl ? *L.launches : 0ull;
-    else if (t == 72) dsc[0] = gs->rtol;
-    else if (t == 73) dsc[1] = gs->bnorm;
+    else if (t == 72) tol = gs->tol32;
     __syncthreads();
     const int j = isc[1];
     int end = isc[0];
     if (!end) {
         const int nvec = j + 2;
+        const float *pf = reinterpret_cast<const float *>(rb.partials);
         for (int i0 = 0; i0 < nvec; i0 += 8) {
-            double a[8];
+            float a[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) a[u] = 0.0;
+            for (int u = 0; u < 8; ++u) a[u] = 0.f;
             for (int b = t; b < nblocks; b += blockDim.x) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
-                    if (i0 + u < nvec) a[u] += __ldcg(&rb.partials[(size_t)b * (GM_M + 2) + i0 + u]);
+                    if (i0 + u < nvec) a[u] += __ldcg(&pf[(size_t)b * (GM_M + 2) + i0 + u]);
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                double x = a[u];
+                float x = a[u];
                 for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
                 if (lane == 0 && i0 + u < nvec) red[i0 + u][warp] = x;
             }
         }
         __syncthreads();
         if (t < nvec) {
-            double x = 0.0;
+            float x = 0.f;
             for (int w2 = 0; w2 < nw; ++w2) x += red[t][w2];
             Hc[t] = x;
-            gs->hcol[t] = x;
-            gs->hcol32[t] = (float)x;                   // projections for the next preconditioner pass
+            gs->hcol32[t] = x;                          // projections for the next preconditioner pass
         }
         __syncthreads();
-        if (t == 0) {
-            double h2 = 0.0;
+        if (t == 0) {                                   // FP32 throughout: GB300's FP64 pipe makes a
+            float h2 = 0.f;                             // serial FP64 chain cost ~10 us here
             for (int i = 0; i <= j; ++i) h2 += Hc[i] * Hc[i];
-            const double ww = Hc[j + 1], hn2 = ww - h2;
-            const double hn = sqrt(hn2 > 1e-12 * ww ? hn2 : 1e-12 * ww);
+            const float ww = Hc[j + 1], hn2 = ww - h2;
+            const float hn = sqrtf(hn2 > 1e-10f * ww ? hn2 : 1e-10f * ww);
             Hc[j + 1] = hn;
             for (int i = 0; i < j; ++i) {              // previous rotations
-                const double p = Hc[i], q = Hc[i + 1];
+                const float p = Hc[i], q = Hc[i + 1];
                 Hc[i] = cs[i] * p + sn[i] * q;
                 Hc[i + 1] = -sn[i] * p + cs[i] * q;
             }
-            const double p = Hc[j], q = Hc[j + 1];
-            const double r = sqrt(p * p + q * q);
-            const double c_ = r > 0 ? p / r : 1.0, s_ = r > 0 ? q / r : 0.0;
-            double *H = gs->H + j * (GM_M + 1);
+            const float p = Hc[j], q = Hc[j + 1];
+            const float r = sqrtf(p * p + q * q);
+            const float c_ = r > 0.f ? p / r : 1.f, s_ = r > 0.f ? q / r : 0.f;
+            float *H = gs->H32 + j * (GM_M + 1);
             for (int i = 0; i < j; ++i) H[i] = Hc[i];
             H[j] = r;
-            H[j + 1] = hn;                              // the norm, kept for the next v
-            gs->inv32 = (float)(1.0 / hn);
-            gs->cs[j] = c_; gs->sn[j] = s_;
-            const double gj = gv[j], resid = fabs(-s_ * gj);
-            gs->g[j + 1] = -s_ * gj;
-            gs->g[j] = c_ * gj;
-            gs->resid = resid;
+            gs->inv32 = 1.f / hn;
+            gs->cs32[j] = c_; gs->sn32[j] = s_;
+            const float gj = gv[j], resid = fabsf(s_ * gj);
+            gs->g32[j + 1] = -s_ * gj;
+            gs->g32[j] = c_ * gj;
             const int total = isc[3] + 1;
             gs->total = total;
-            gs->hcol[GM_M + 1] = hn;
             gs->j = j + 1;
             if (!isfinite(resid)) { gs->breakdown = 2; end = 1; }
-            else if (resid <= dsc[0] * dsc[1]) { gs->converged = 1; end = 1; }
-            else if (j + 1 >= isc[2] || total >= isc[4] || hn == 0.0) end = 1;
+            else if (resid <= tol) { gs->converged = 1; end = 1; }
+            else if (j + 1 >= isc[2] || total >= isc[4] || hn == 0.f) end = 1;
             if (end) gs->cycle_end = 1;
         }
     }
@@ -1323,6 +1325,29 @@ __global__ void k_gm_solve(GmresState *gs, const double *Hdiag_unused) {
     }
 }
 
+// FP32 back substitution of an inner FP32 cycle: y32 = R^{-1} g32 (block 0; thread 0 substitutes
+// after the block has gathered R and g into shared memory)
+__global__ void k_gm_solve32(GmresState *gs) {
+    wait_prior_kernel();
+    if (blockIdx.x != 0) return;
+    __shared__ float R[GM_M * (GM_M + 1)], g[GM_M], y[GM_M];
+    __shared__ int ms;
+    if (threadIdx.x == 0) ms = gs->j;
+    __syncthreads();
+    const int m = ms;
+    for (int q = threadIdx.x; q < m * (GM_M + 1); q += blockDim.x) R[q] = gs->H32[q];
+    for (int q = threadIdx.x; q < m; q += blockDim.x) g[q] = gs->g32[q];
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int i = m - 1; i >= 0; --i) {
+        float s = g[i];
+        for (int k = i + 1; k < m; ++k) s -= R[k * (GM_M + 1) + i] * y[k];
+        const float d = R[i * (GM_M + 1) + i];
+        y[i] = d != 0.f ? s / d : 0.f;
+        gs->y32[i] = y[i];
+    }
+}
+
 // u = V y (rows), then x += Binv u (cell-local)
 template <class T>
 __global__ void k_gm_combine(const T *__restrict__ V, T *u, long long nrows, const GmresState *gs) {
@@ -1346,9 +1371,9 @@ __global__ void k_gm_combine_update(const T *__restrict__ V, const T *__restrict
                                     const GmresState *gs, DevCount *acc) {
     wait_prior_kernel();
     constexpr int NU = Dims<K>::NU;
-    __shared__ double ys[GM_M];
+    __shared__ float ys[GM_M];
     const int m = gs->j;
-    if ((int)threadIdx.x < m) ys[threadIdx.x] = gs->y[threadIdx.x];
+    if ((int)threadIdx.x < m) ys[threadIdx.x] = gs->y32[threadIdx.x];
     if (acc && blockIdx.x == 0 && threadIdx.x == 0) { acc->stepI_iters += gs->total; acc->stepI_solves += 1; }
     __syncthreads();
     extern __shared__ double smd[];

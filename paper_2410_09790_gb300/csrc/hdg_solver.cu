@@ -999,7 +999,7 @@ struct Impl {
                     launch_k(k_gm_finish_ctl, 1, 256, 0, c->st, L, GM_M / U + 2, c->rb(), (int)ab, c->gs, u == U - 1 ? 1 : 0);
                 }
             });
-        launch_k(k_gm_solve, 1, 256, 0, c->st, c->gs, nullptr);
+        launch_k(k_gm_solve32, 1, 256, 0, c->st, c->gs);
         launch_k(k_gm_combine_update<K, float>, cell_blocks(c), 128, sizeof(float) * TEAMS_PER_BLOCK * NU, c->st, c->gV32,
                  c->Binv32, x, c->M, (const GmresState *)c->gs, c->dcnt);
         CKL();
