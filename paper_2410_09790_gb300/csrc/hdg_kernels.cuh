@@ -1163,19 +1163,10 @@ __global__ void k_gm_apply_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ wq,
     else multidot_groups(rb, V, (const T *)w, nrows, (long long)tpb * NU, j + 1, gs->hcol, false);
 }
 
-// Step bookkeeping of the FP32 inner Arnoldi loop, one block (256 threads) after the FUSED
-// k_gm_apply_mf: reads all the loop state it may need in one round of independent loads, sums the
-// nblocks block partials of (V_i, w), i <= j, and ||w||^2 (each thread its blocks' rows, then a
-// fixed tree: deterministic), finishes the step on shared memory (hn by Pythagoras with the
-// 1e-12 ||w||^2 floor, previous rotations, new Givens rotation, residual estimate, convergence)
-// and sets the condition of the loop whose body it ends: continue while the cycle has not ended
-// and the pass guard is below limit.
-// With ctl = 0 (an Arnoldi step inside an unrolled loop body, not its last) the loop's guard,
-// counter and condition are left alone.
-__global__ void __launch_bounds__(256) k_gm_finish_ctl(LoopCtl L, int limit, RedBuf rb, int nblocks, GmresState *gs,
-                                                       int ctl) {
-    wait_prior_kernel();
-    __shared__ float red[GM_M + 2][8];         // per value, per warp
+// The finishing work of an FP32 inner Arnoldi step for one whole block (see k_gm_finish_ctl);
+// pf: the FP32 block partials of the product (nblocks rows of GM_M + 2).
+__device__ void finish32_block(LoopCtl L, int limit, const float *pf, int nblocks, GmresState *gs, int ctl) {
+    __shared__ float red[GM_M + 2][32];        // per value, per warp
     __shared__ float Hc[GM_M + 2], cs[GM_M], sn[GM_M], gv[GM_M + 1], tol;
     __shared__ int isc[8];
     __shared__ unsigned long long nlaunch;
@@ -1196,7 +1187,6 @@ __global__ void __launch_bounds__(256) k_gm_finish_ctl(LoopCtl L, int limit, Red
     int end = isc[0];
     if (!end) {
         const int nvec = j + 2;
-        const float *pf = reinterpret_cast<const float *>(rb.partials);
         for (int i0 = 0; i0 < nvec; i0 += 8) {
             float a[8];
 #pragma unroll
@@ -1258,6 +1248,78 @@ __global__ void __launch_bounds__(256) k_gm_finish_ctl(LoopCtl L, int limit, Red
         *L.launches = nlaunch + (unsigned long long)isc[6];
         cudaGraphSetConditional(L.h, (!end && gd < limit) ? 1u : 0u);
     }
+}
+
+// Step bookkeeping of the FP32 inner Arnoldi loop, one block (256 threads) after the FUSED
+// k_gm_apply_mf: reads all the loop state it may need in one round of independent loads, sums the
+// nblocks block partials of (V_i, w), i <= j, and ||w||^2 (each thread its blocks' rows, then a
+// fixed tree: deterministic), finishes the step on shared memory (hn by Pythagoras with the
+// 1e-10 ||w||^2 floor, all in FP32, previous rotations, new Givens rotation, residual estimate, convergence)
+// and sets the condition of the loop whose body it ends: continue while the cycle has not ended
+// and the pass guard is below limit.
+// With ctl = 0 (an Arnoldi step inside an unrolled loop body, not its last) the loop's guard,
+// counter and condition are left alone.
+__global__ void __launch_bounds__(256) k_gm_finish_ctl(LoopCtl L, int limit, RedBuf rb, int nblocks, GmresState *gs,
+                                                       int ctl) {
+    wait_prior_kernel();
+    finish32_block(L, limit, reinterpret_cast<const float *>(rb.partials), nblocks, gs, ctl);
+}
+
+// The FUSED FP32 Arnoldi product with the step finished by its last block (atomic ticket, no
+// waiting) instead of a separate k_gm_finish_ctl: one kernel boundary fewer per step. When the
+// cycle has already ended it only keeps the loop state (ctl).
+template <int K>
+__global__ void k_gm_apply_fin(EdgeTab<float> E, MeshDev M, const float *__restrict__ wq, const float *__restrict__ utr,
+                               float *w, const float *__restrict__ V, RedBuf rb, GmresState *gs, LoopCtl L, int limit,
+                               int ctl) {
+    wait_prior_kernel();
+    if (gs->cycle_end) {
+        if (ctl && blockIdx.x == 0 && threadIdx.x == 0) {
+            const int gd = *L.guard + 1;
+            *L.guard = gd;
+            *L.launches += (unsigned long long)*L.nk;
+            cudaGraphSetConditional(L.h, 0u);
+        }
+        return;
+    }
+    typedef Dims<K> Dm;
+    constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
+    extern __shared__ double smd[];
+    __shared__ int last;
+    const int team = threadIdx.x / TEAM_LANES, tpb = blockDim.x / TEAM_LANES;
+    Team tm{(int)(threadIdx.x % TEAM_LANES), TEAM_LANES};
+    float *t = reinterpret_cast<float *>(smd) + team * (6 * NFQ);
+    const long long nrows = (long long)M.ncells * NU;
+    const int j = gs->j;
+    const float *vj = V + (size_t)j * nrows;
+    for (int base = blockIdx.x * tpb; base < M.ncells; base += gridDim.x * tpb) {
+        const int cell = base + team;
+        if (cell < M.ncells) {
+            team_nbr_flux<K, float>(tm, E, M, cell, wq, utr, nullptr, t);
+            tm.sync();
+            TFOR(r, NU) {
+                const size_t gi = (size_t)cell * NU + r;
+                w[gi] = vj[gi] + nbr_row<K, float>(E, t, r / MU, r % MU);
+            }
+            tm.sync();
+        }
+    }
+    __syncthreads();
+    const long long rpg = (long long)tpb * NU;
+    block_dot_partials(rb, V, (const float *)w, nrows, j + 1, [&](auto f) {
+        for (long long g0 = blockIdx.x * rpg; g0 < nrows; g0 += gridDim.x * rpg)
+            f(g0, g0 + rpg < nrows ? g0 + rpg : nrows);
+    }, (const float *)w, true, true);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned tk = atomicAdd(rb.counter, 1u);
+        last = (tk == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    finish32_block(L, limit, reinterpret_cast<const float *>(rb.partials), (int)gridDim.x, gs, ctl);
+    if (threadIdx.x == 0) *rb.counter = 0u;
 }
 
 // w -= V hcol; h2 = (V_i, w)  (second Gram-Schmidt pass); rows in contiguous chunks per block
