@@ -1265,63 +1265,6 @@ __global__ void __launch_bounds__(256) k_gm_finish_ctl(LoopCtl L, int limit, Red
     finish32_block(L, limit, reinterpret_cast<const float *>(rb.partials), nblocks, gs, ctl);
 }
 
-// The FUSED FP32 Arnoldi product with the step finished by its last block (atomic ticket, no
-// waiting) instead of a separate k_gm_finish_ctl: one kernel boundary fewer per step. When the
-// cycle has already ended it only keeps the loop state (ctl).
-template <int K>
-__global__ void k_gm_apply_fin(EdgeTab<float> E, MeshDev M, const float *__restrict__ wq, const float *__restrict__ utr,
-                               float *w, const float *__restrict__ V, RedBuf rb, GmresState *gs, LoopCtl L, int limit,
-                               int ctl) {
-    wait_prior_kernel();
-    if (gs->cycle_end) {
-        if (ctl && blockIdx.x == 0 && threadIdx.x == 0) {
-            const int gd = *L.guard + 1;
-            *L.guard = gd;
-            *L.launches += (unsigned long long)*L.nk;
-            cudaGraphSetConditional(L.h, 0u);
-        }
-        return;
-    }
-    typedef Dims<K> Dm;
-    constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
-    extern __shared__ double smd[];
-    __shared__ int last;
-    const int team = threadIdx.x / TEAM_LANES, tpb = blockDim.x / TEAM_LANES;
-    Team tm{(int)(threadIdx.x % TEAM_LANES), TEAM_LANES};
-    float *t = reinterpret_cast<float *>(smd) + team * (6 * NFQ);
-    const long long nrows = (long long)M.ncells * NU;
-    const int j = gs->j;
-    const float *vj = V + (size_t)j * nrows;
-    for (int base = blockIdx.x * tpb; base < M.ncells; base += gridDim.x * tpb) {
-        const int cell = base + team;
-        if (cell < M.ncells) {
-            team_nbr_flux<K, float>(tm, E, M, cell, wq, utr, nullptr, t);
-            tm.sync();
-            TFOR(r, NU) {
-                const size_t gi = (size_t)cell * NU + r;
-                w[gi] = vj[gi] + nbr_row<K, float>(E, t, r / MU, r % MU);
-            }
-            tm.sync();
-        }
-    }
-    __syncthreads();
-    const long long rpg = (long long)tpb * NU;
-    block_dot_partials(rb, V, (const float *)w, nrows, j + 1, [&](auto f) {
-        for (long long g0 = blockIdx.x * rpg; g0 < nrows; g0 += gridDim.x * rpg)
-            f(g0, g0 + rpg < nrows ? g0 + rpg : nrows);
-    }, (const float *)w, true, true);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned tk = atomicAdd(rb.counter, 1u);
-        last = (tk == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    finish32_block(L, limit, reinterpret_cast<const float *>(rb.partials), (int)gridDim.x, gs, ctl);
-    if (threadIdx.x == 0) *rb.counter = 0u;
-}
-
 // w -= V hcol; h2 = (V_i, w)  (second Gram-Schmidt pass); rows in contiguous chunks per block
 template <class T>
 __global__ void k_gm_orth1(T *w, const T *__restrict__ V, long long nrows, RedBuf rb, GmresState *gs) {

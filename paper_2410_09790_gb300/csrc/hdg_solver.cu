@@ -977,17 +977,6 @@ struct Impl {
         return v;
     }
 
-    // 1: the inner FP32 Arnoldi step is finished by the product kernel's last block; 0: by a
-    // separate one-block kernel (HDG_FINISH_IN_PRODUCT overrides the default)
-    static int finish_in_product() {
-        static int v = -1;
-        if (v < 0) {
-            const char *e = std::getenv("HDG_FINISH_IN_PRODUCT");
-            v = e ? (std::atoi(e) != 0) : 0;
-        }
-        return v;
-    }
-
     // A loose Step-I solve in FP32, recorded into the current capture: one GMRES(GM_M) cycle from
     // x = 0 with its Arnoldi steps as a device-side loop, stopping at the tolerance or after GM_M
     // steps (an inexact solve is what the flexible outer iteration expects). b, x: FP64.
@@ -1006,18 +995,8 @@ struct Impl {
                 const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
                 const int U = inner_unroll();
                 for (int u = 0; u < U; ++u) {
-                    if (finish_in_product()) {
-                        launch_k(k_gm_precond_mf<K, float, true>, cb, 128, sizeof(float) * TEAMS_PER_BLOCK * 2 * NU, c->st, E,
-                                 c->M, (const float *)c->Binv32, (const float *)c->gw32, c->gV32, c->utr32,
-                                 (const GmresState *)c->gs);
-                        launch_k(k_gm_apply_fin<K>, ab, 128, sizeof(float) * TEAMS_PER_BLOCK * 6 * Dm::NFQ, c->st, E, c->M,
-                                 (const float *)c->wq32, (const float *)c->utr32, c->gw32, (const float *)c->gV32, c->rb(),
-                                 c->gs, L, GM_M / U + 2, u == U - 1 ? 1 : 0);
-                    } else {
-                        gmres_arnoldi<float>(c, E, c->Binv32, c->wq32, c->utr32, c->gw32, c->gV32);
-                        launch_k(k_gm_finish_ctl, 1, 256, 0, c->st, L, GM_M / U + 2, c->rb(), (int)ab, c->gs,
-                                 u == U - 1 ? 1 : 0);
-                    }
+                    gmres_arnoldi<float>(c, E, c->Binv32, c->wq32, c->utr32, c->gw32, c->gV32);
+                    launch_k(k_gm_finish_ctl, 1, 256, 0, c->st, L, GM_M / U + 2, c->rb(), (int)ab, c->gs, u == U - 1 ? 1 : 0);
                 }
             });
         launch_k(k_gm_solve32, 1, 256, 0, c->st, c->gs);
