@@ -117,6 +117,13 @@ typedef struct {
      * meshes up to 64 x 64 cells); 0 = the FP64 V-cycle. The outer iteration's tolerance
      * is unchanged: this only alters the preconditioner. */
     int inner_trace_fp32;
+    /* Trace CG with the multigrid (tight solves: final update, pressure reconstruction, mixed
+     * solves): 1 (default) = preconditioned by the same V-cycle in FP32 (when the hierarchy fits
+     * one block, as for inner_trace_fp32), with the flexible (Polak-Ribiere) CG update since the
+     * FP32 V-cycle is not exactly one fixed symmetric map; everything else of the CG (operator,
+     * residual, iterate, dot products, the tolerance on sqrt(r.z / r0.z0)) stays FP64. 0 = the
+     * FP64 V-cycle with plain preconditioned CG. */
+    int trace_fp32_vcycle;
 } hdg_params;
 
 typedef struct {

@@ -36,6 +36,7 @@ struct Scalars {
     double bmean, red0, red1, red2, zmean;
     int done, iters, breakdown, maxit;
     double rtol, relres;
+    double zmean_old;       // flexible CG: the mean removed from the previous z
 };
 
 struct RedBuf {

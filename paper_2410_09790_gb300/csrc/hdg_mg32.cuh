@@ -98,19 +98,21 @@ __global__ void k_tv_gather(MeshDev M, const double *__restrict__ v, const doubl
 
 // r = b - mean e0; x0 = d0 = invth D^{-1} r; r1 = r - S x0 (x0 of the neighbours formed here from
 // their b); d1 = c1 d0 + c2 D^{-1} r1; x1 = x0 + d1.  Writes r, x1, d1.
+// b64 (when set, in place of b): an FP64 right-hand side; sc null: no mean removed.
 template <int NT>
-__global__ void k_tv_cheb01(TraceOp32 T, const float *__restrict__ b, const Scalars *sc, float invth, float c1,
-                            float c2, float *r, float *x, float *d) {
+__global__ void k_tv_cheb01(TraceOp32 T, const float *__restrict__ b, const double *__restrict__ b64,
+                            const Scalars *sc, float invth, float c1, float c2, float *r, float *x, float *d) {
     wait_prior_kernel();
     TV_ROW(NT)
-    const float mean = (float)sc->bmean;
-    const float rown = i < NT ? __ldcg(&b[g]) - (i == 0 ? mean : 0.f) : 0.f;
+    const float mean = sc ? (float)sc->bmean : 0.f;
+    auto bv = [&](size_t k) { return b64 ? (float)__ldcg(&b64[k]) : __ldcg(&b[k]); };
+    const float rown = i < NT ? bv(g) - (i == 0 ? mean : 0.f) : 0.f;
     float sx = 0.f;
 #pragma unroll
     for (int bb = 0; bb < 5; ++bb) {
         const int cf = __ldg(&T.tcol[bb * T.nfacets + f]);
         const int cfc = cf >= 0 ? cf : f;
-        const float rn = i < NT ? __ldcg(&b[(size_t)cfc * NT + ic]) - (i == 0 ? mean : 0.f) : 0.f;
+        const float rn = i < NT ? bv((size_t)cfc * NT + ic) - (i == 0 ? mean : 0.f) : 0.f;
         float xn = invth * grp_dinv<NT>(T.Dinv, nrows, cfc, ic, rn);
         if (cf < 0) xn = 0.f;
         float s = 0.f;
@@ -399,6 +401,58 @@ __global__ void __launch_bounds__(1024) k_tv_tail(Tail32 T) {
     {
         const float *e = tail_level(T, tsm, 0).xb;
         for (int v = tid; v < T.G[0].nverts; v += nth) T.e1[v] = e[v];
+    }
+}
+
+// ---------------------------------------------------------------- flexible CG with the FP32 V-cycle
+// x += alpha p; r -= alpha Ap (the preconditioner follows as separate kernels)
+template <int NT>
+__global__ void k_cg_update_xr(const double *__restrict__ p, const double *__restrict__ Ap, double *x, double *r,
+                               int nfacets, const Scalars *sc) {
+    wait_prior_kernel();
+    if (sc->done) return;
+    const double alpha = sc->alpha;
+    GRID_STRIDE(g, (long long)nfacets * NT) {
+        x[g] += alpha * p[g];
+        r[g] -= alpha * Ap[g];
+    }
+}
+
+// Reduction of flexible CG (Polak-Ribiere beta; the FP32 V-cycle is not exactly the same linear
+// map twice): z is taken off the constant mode, z - zmean e0; rz = (r, z - zmean e0);
+// beta = (r, (z - zmean e0) - (zold - zmean_old e0)) / rz_old; zold = z. first: rz0. Convergence
+// on sqrt(rz / rz0), as the CG with the FP64 V-cycle.
+template <int NT>
+__global__ void k_fcg_rz(const double *__restrict__ r, const double *__restrict__ z, double *zold, int nfacets,
+                         int first, RedBuf rb, Scalars *sc) {
+    wait_prior_kernel();
+    if (sc->done) return;
+    double v[4] = {0.0, 0.0, 0.0, 0.0}, tot[4];
+    GRID_STRIDE(g, (long long)nfacets * NT) {
+        const double rg = r[g], zg = z[g];
+        v[0] += rg * zg;
+        if (g % NT == 0) { v[1] += zg; v[2] += rg; }
+        if (!first) v[3] += rg * zold[g];
+        zold[g] = zg;
+    }
+    if (grid_sum<4>(rb, v, tot)) {
+        const double zm = tot[1] / nfacets, rz = tot[0] - zm * tot[2];
+        if (first) {
+            sc->rz = rz; sc->rz0 = rz; sc->relres = rz > 0 ? 1.0 : 0.0;
+            if (!isfinite(rz)) { sc->done = 1; sc->breakdown = 2; }
+            else if (!(rz > 0.0)) sc->done = 1;
+        } else {
+            const double rzo = tot[3] - sc->zmean_old * tot[2];
+            sc->beta = (rz - rzo) / sc->rz;
+            sc->rz = rz;
+            sc->iters += 1;
+            const double rel = sc->rz0 > 0 ? sqrt(fmax(rz, 0.0) / sc->rz0) : 0.0;
+            sc->relres = rel;
+            if (!isfinite(rz)) { sc->done = 1; sc->breakdown = 2; }
+            else if (rel <= sc->rtol || sc->iters >= sc->maxit) sc->done = 1;
+        }
+        sc->zmean = zm;
+        sc->zmean_old = zm;
     }
 }
 

@@ -188,6 +188,7 @@ struct hdg_ctx {
     std::vector<MGWork> mgw;
     double *txa = nullptr, *td = nullptr, *tt = nullptr, *cellA = nullptr, *mgB = nullptr;
     float *tb32 = nullptr, *tr32 = nullptr, *tx32 = nullptr, *txa32 = nullptr, *td32 = nullptr, *tt32 = nullptr;
+    double *tzold = nullptr;                                 // flexible CG: the previous z
     unsigned long long *dlmax = nullptr;
     // reductions
     double *partials = nullptr;
@@ -455,6 +456,7 @@ struct Impl {
         launch_k(k_assemble_trace<NT>, grid_for(c->nfacets), VEC_THREADS, 0, c->st, c->M, E.Scell, E.Sell, E.tcol, E.Dinv);
         CKL();
         if (c->P.trace_mg && c->H.p1_ok) build_mg(c, E);
+        if (E.mg && (c->P.inner_trace_fp32 || c->P.trace_fp32_vcycle)) build_mg32(c, E);
         c->cache.push_back(E);
         return c->cache.back();
     }
@@ -688,9 +690,11 @@ struct Impl {
             return;
         }
         if (c->capturing) {             // device-side loop, two iterations per pass
+            const bool f32 = fcg32(c, E);
             launch_k(k_trace_mean<NT>, grid_for(nf), VEC_THREADS, 0, c->st, c->tb, nf, c->rb(), c->sc);
             launch_k(k_cg_setup_mg<NT>, gr, VEC_THREADS, 0, c->st, c->tb, c->tx, c->tr, c->tp[0], nf, c->sc);
-            vcycle(c, E, c->tr, c->tz, false, 1);
+            if (f32) cg_vcycle32(c, E, 1);
+            else vcycle(c, E, c->tr, c->tz, false, 1);
             capture_while(
                 c, [&](LoopCtl L) { launch_k(k_loop_init, 1, 1, 0, c->st, L, &c->sc->done); },
                 [&](LoopCtl L) {
@@ -698,6 +702,12 @@ struct Impl {
                         double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
                         launch_k(k_cg_apply<NT>, gr, VEC_THREADS, 0, c->st, E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
                                                                      c->rb(), c->sc);
+                        if (f32) {
+                            launch_k(k_cg_update_xr<NT>, gr, VEC_THREADS, 0, c->st, (const double *)pnew,
+                                     (const double *)c->tAp, c->tx, c->tr, nf, (const Scalars *)c->sc);
+                            cg_vcycle32(c, E, 0);
+                            continue;
+                        }
                         launch_k(k_cg_update_cheb0<NT>, grid_facets(nf), FACET_THREADS, 0, c->st, 
                             pnew, c->tAp, c->tx, c->tr, E.Dinv, c->txa, c->td, E.t_invth, nf, c->sc);
                         vcycle(c, E, c->tr, c->tz, true, 0);
@@ -711,10 +721,12 @@ struct Impl {
         }
         const int chunk = trace_cg_enabled() ? 1 : 8;
         if (!E.g_setup) {
+            const bool f32 = fcg32(c, E);
             E.g_setup = capture_graph(c, [&]() {
                 launch_k(k_trace_mean<NT>, grid_for(nf), VEC_THREADS, 0, c->st, c->tb, nf, c->rb(), c->sc);
                 launch_k(k_cg_setup_mg<NT>, gr, VEC_THREADS, 0, c->st, c->tb, c->tx, c->tr, c->tp[0], nf, c->sc);
-                vcycle(c, E, c->tr, c->tz, false, 1);
+                if (f32) cg_vcycle32(c, E, 1);
+                else vcycle(c, E, c->tr, c->tz, false, 1);
                 CKL();
             });
             E.g_chunk = capture_graph(c, [&]() {
@@ -722,6 +734,12 @@ struct Impl {
                     double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
                     launch_k(k_cg_apply<NT>, gr, VEC_THREADS, 0, c->st, E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
                                                                  c->rb(), c->sc);
+                    if (f32) {
+                        launch_k(k_cg_update_xr<NT>, gr, VEC_THREADS, 0, c->st, (const double *)pnew, (const double *)c->tAp,
+                                 c->tx, c->tr, nf, (const Scalars *)c->sc);
+                        cg_vcycle32(c, E, 0);
+                        continue;
+                    }
                     launch_k(k_cg_update_cheb0<NT>, grid_facets(nf), FACET_THREADS, 0, c->st, pnew, c->tAp, c->tx, c->tr, E.Dinv,
                                                                                         c->txa, c->td, E.t_invth, nf, c->sc);
                     vcycle(c, E, c->tr, c->tz, true, 0);
@@ -804,6 +822,7 @@ struct Impl {
         if (!c->tb32) {
             c->tb32 = c->alloc<float>(c->nL); c->tr32 = c->alloc<float>(c->nL); c->tx32 = c->alloc<float>(c->nL);
             c->txa32 = c->alloc<float>(c->nL); c->td32 = c->alloc<float>(c->nL); c->tt32 = c->alloc<float>(c->nL);
+            c->tzold = c->alloc<double>(c->nL);
         }
         CK(cudaFuncSetAttribute(k_tv_tail<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         E.tail32_smem = smem;
@@ -837,7 +856,8 @@ struct Impl {
         const float invth = (float)E.t_invth, c1 = (float)E.t_c1, c2 = (float)E.t_c2;
         launch_k(k_tv_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, sub, c->tb32, c->rb(), c->sc,
                                                                   c->capturing ? c->dcnt : nullptr);
-        launch_k(k_tv_cheb01<NT>, gb, 128, 0, c->st, T, c->tb32, c->sc, invth, c1, c2, c->tr32, c->tx32, c->td32);
+        launch_k(k_tv_cheb01<NT>, gb, 128, 0, c->st, T, (const float *)c->tb32, (const double *)nullptr, (const Scalars *)c->sc,
+                 invth, c1, c2, c->tr32, c->tx32, c->td32);
         const int nv0 = E.lv[0].G.nverts;
         float *b1 = c->tt32, *e1 = c->tt32 + nv0;
         launch_k(k_tv_restrict<NT>, (unsigned)((16LL * nv0 + 127) / 128), 128, 0, c->st, T, c->tr32, c->tx32,
@@ -849,6 +869,29 @@ struct Impl {
                                                            (float *)nullptr, c->td32, c1, c2, out);
         CKL();
         if (!c->capturing) c->S.trace_solves += 1;
+    }
+
+    // The trace CG's preconditioner as the FP32 V-cycle (flexible CG): z = V(r) for r = c->tr
+    // (FP64, off the constant mode), then the flexible CG reduction (first: rz0).
+    static bool fcg32(const hdg_ctx *c, const CondCache &E) { return E.mg32 && c->P.trace_fp32_vcycle; }
+    static void cg_vcycle32(hdg_ctx *c, const CondCache &E, int first) {
+        const int nf = (int)c->nfacets;
+        const unsigned gb = tv_blocks(nf, TGrp<NT>::G);
+        const TraceOp32 T{E.Sell32, E.Dinv32, E.tcol, nf};
+        const float invth = (float)E.t_invth, c1 = (float)E.t_c1, c2 = (float)E.t_c2;
+        const int nv0 = E.lv[0].G.nverts;
+        float *b1 = c->tt32, *e1 = c->tt32 + nv0;
+        launch_k(k_tv_cheb01<NT>, gb, 128, 0, c->st, T, (const float *)nullptr, (const double *)c->tr,
+                 (const Scalars *)nullptr, invth, c1, c2, c->tr32, c->tx32, c->td32);
+        launch_k(k_tv_restrict<NT>, (unsigned)((16LL * nv0 + 127) / 128), 128, 0, c->st, T, c->tr32, c->tx32,
+                                                                   c->M.vert_facet, c->M.vert_fsign, nv0, b1);
+        launch_k(k_tv_tail<NT>, 1, 1024, E.tail32_smem, c->st, tail32_params(c, E));
+        launch_k(k_tv_cheb<NT>, gb, 128, 0, c->st, T, c->tr32, c->tx32, e1, c->M.facet_vert, c->txa32, c->td32, 0.f, invth,
+                                                           (double *)nullptr);
+        launch_k(k_tv_cheb<NT>, gb, 128, 0, c->st, T, c->tr32, c->txa32, (const float *)nullptr, c->M.facet_vert,
+                                                           (float *)nullptr, c->td32, c1, c2, c->tz);
+        launch_k(k_fcg_rz<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, (const double *)c->tr, (const double *)c->tz,
+                 c->tzold, nf, first, c->rb(), c->sc);
     }
 
     static void ensure_pre_maps(hdg_ctx *c, double cc) {
@@ -1594,6 +1637,7 @@ void hdg_default_params(hdg_params *p) {
     p->inner_trace_vcycles = 1;
     p->persistent_stepI = 0;
     p->inner_trace_fp32 = 1;
+    p->trace_fp32_vcycle = 1;
 }
 
 const char *hdg_status_string(hdg_status s) {

@@ -40,7 +40,8 @@ class hdg_params(ctypes.Structure):
                 ('stage_krylov', ctypes.c_int), ('inner_stepI_rtol', ctypes.c_double),
                 ('inner_trace_rtol', ctypes.c_double), ('trace_mg', ctypes.c_int),
                 ('device_loops', ctypes.c_int), ('inner_trace_vcycles', ctypes.c_int),
-                ('persistent_stepI', ctypes.c_int), ('inner_trace_fp32', ctypes.c_int)]
+                ('persistent_stepI', ctypes.c_int), ('inner_trace_fp32', ctypes.c_int),
+                ('trace_fp32_vcycle', ctypes.c_int)]
 
 
 class hdg_stats(ctypes.Structure):

@@ -250,6 +250,25 @@ def test_inner_trace_vcycle_fp32_matches_fp64(n, px, k):
     assert it32 <= 1.1 * it64 + 3, (it32, it64)
 
 
+@pytest.mark.parametrize('n,px,k', [(8, True, 2), (16, False, 3), (16, True, 4)])
+def test_trace_cg_fp32_vcycle_matches_fp64(n, px, k):
+    # the tight trace solves with the FP32 V-cycle inside flexible CG reach the same tolerance as
+    # plain CG with the FP64 V-cycle, give the same solution to it, in about as many iterations
+    rng = np.random.default_rng(71)
+    R = rng.standard_normal((2 * n * n, 2, (k + 2) * (k + 3) // 2))
+    outs, its = [], []
+    for f32 in (0, 1):
+        ctx = H().Context(n, k, periodic_x=px, trace_rtol=1e-12, max_iters=20000, trace_mg=1, trace_fp32_vcycle=f32)
+        U, dp, dl, st = ctx.hdg_mixed_solve(1.0, cuda(R))
+        outs.append([host(U), host(dp), host(dl)])
+        its.append(st['trace_iters'])
+        assert st['last_trace_relres'] <= 1e-12
+        ctx.close()
+    for a, b, name in zip(outs[1], outs[0], ('U', 'dp', 'dl')):
+        assert_close(a, b, 1e-9, name)
+    assert its[1] <= 1.5 * its[0] + 3, its
+
+
 @pytest.mark.parametrize('n,px', [(16, True), (32, False)])
 def test_multigrid_iterations_mesh_robust(n, px):
     # the V-cycle preconditioner keeps the trace CG iteration count small and nearly independent
