@@ -33,7 +33,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(n=64, k=3, periodic_x=True, tableau='ARS343', dt=2e-3, n_richardson=0, stage_rtol=1e-10,
                 inner_stepI_rtol=2e-2, inner_trace_rtol=1e-1, trace_rtol=1e-12, stepI_rtol=1e-10,
-                inner_trace_vcycles=1, inner_trace_fp32=1, trace_fp32_vcycle=1, init='shear_layer', width=0.05, amp=1e-3, noise=1e-4, seed=0)
+                inner_trace_vcycles=1, inner_trace_fp32=1, trace_fp32_vcycle=1, inner_gs=1,
+                init='shear_layer', width=0.05, amp=1e-3, noise=1e-4, seed=0)
 STAGES = {'ARS343': 3, 'ARS222': 2, 'IMEX_EULER': 1}
 METRIC = 'IMEX stage solves/s (trace-DoF/s alongside)'
 
@@ -204,6 +205,8 @@ def run_gpu(args, rank, world, local_rank):
         w['inner_trace_fp32'] = args.inner_trace_fp32
     if args.trace_fp32_vcycle is not None:
         w['trace_fp32_vcycle'] = args.trace_fp32_vcycle
+    if args.inner_gs is not None:
+        w['inner_gs'] = args.inner_gs
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         ctx = H.Context(w['n'], w['k'], periodic_x=w['periodic_x'], stream=stream, tableau=w['tableau'],
@@ -212,7 +215,7 @@ def run_gpu(args, rank, world, local_rank):
                         inner_trace_rtol=w['inner_trace_rtol'], trace_rtol=w['trace_rtol'],
                         stepI_rtol=w['stepI_rtol'], device_loops=0 if args.host_loops else 1,
                         inner_trace_vcycles=w['inner_trace_vcycles'], inner_trace_fp32=w['inner_trace_fp32'],
-                        trace_fp32_vcycle=w['trace_fp32_vcycle'])
+                        trace_fp32_vcycle=w['trace_fp32_vcycle'], inner_gs=w['inner_gs'])
         Q0 = torch.from_numpy(initial_velocity(w, seed_offset=rank)).to(dev)
         ctx.hdg_set_state(Q0)
         ctx.hdg_div_free_project()
@@ -365,6 +368,8 @@ def main():
                     help='tuning: the one-V-cycle Step II inside the preconditioner in FP32 (1) or FP64 (0)')
     ap.add_argument('--trace-fp32-vcycle', type=int, default=None,
                     help='tuning: the tight trace CG preconditioned by the FP32 V-cycle (1) or the FP64 one (0)')
+    ap.add_argument('--inner-gs', type=int, default=None,
+                    help='tuning: inner Step-I preconditioner red-black block Gauss-Seidel (1) or block Jacobi (0)')
     ap.add_argument('--host-loops', action='store_true',
                     help='drive the Krylov loops from the host (fills the per-component timings)')
     ap.add_argument('--kernel-only', type=int, default=None,

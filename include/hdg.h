@@ -124,6 +124,11 @@ typedef struct {
      * residual, iterate, dot products, the tolerance on sqrt(r.z / r0.z0)) stays FP64. 0 = the
      * FP64 V-cycle with plain preconditioned CG. */
     int trace_fp32_vcycle;
+    /* Right preconditioner of the inner FP32 Step-I GMRES: 1 (default) = red-black block
+     * Gauss-Seidel on the cells' diagonal blocks (the structured triangulation's cells are
+     * two-coloured by index parity; checked at setup, else block Jacobi): about half the Arnoldi
+     * steps for one more kernel per step; 0 = block Jacobi. */
+    int inner_gs;
 } hdg_params;
 
 typedef struct {
@@ -243,7 +248,7 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *ctx, hdg_stats *stats);
  * the current state; bytes = its algorithmic bytes. which = 9: the FP32 preconditioner pass of
  * the inner Step-I GMRES (v_j formed from w and the projections, z = B^-1 v_j, z's edge values) at
  * step j = 4, launched like 6; bytes = its algorithmic bytes. which = 10 (bytes = 0): one inner FP32
- * Arnoldi step as the solve runs it (preconditioner pass, product, finishing kernel), from 20 steps
+ * Arnoldi step as the solve runs it (preconditioner passes, product, finishing kernel), from 20 steps
  * launched back to back after a cycle start, less the cycle start alone. */
 hdg_status hdg_time_kernel(hdg_ctx *ctx, int which, double c, int reps, double *ms_per_launch,
                            double *bytes_per_launch);

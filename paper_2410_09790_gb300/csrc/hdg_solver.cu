@@ -21,6 +21,7 @@
 #include "hdg_kernels.cuh"
 #include "hdg_mg_kernels.cuh"
 #include "hdg_mg32.cuh"
+#include "hdg_gs32.cuh"
 #include "hdg_stepI_persistent.cuh"
 #include "mesh.h"
 #include "refelem.h"
@@ -163,6 +164,7 @@ struct hdg_ctx {
     // FP32 copies for the loose (inner) Step-I solves: tables, block inverses, weights, GMRES work
     float *ephi32 = nullptr, *pen32 = nullptr, *Binv32 = nullptr, *wq32 = nullptr, *utr32 = nullptr;
     float *nrm32 = nullptr;                                  // cell normals in FP32 [6 cell + 2 e + d]
+    bool gs_ok = false;                                      // cells 2-coloured by index parity (hdg_gs32.cuh)
     float *gV32 = nullptr, *gw32 = nullptr, *gu32 = nullptr;
     cudaGraphExec_t g_stepI32 = nullptr;                     // one loose Step-I solve (host-driven mode)
     int stepI32_kernels = 0;
@@ -1020,6 +1022,30 @@ struct Impl {
         return v;
     }
 
+    static bool use_gs(const hdg_ctx *c) { return c->gs_ok && c->P.inner_gs; }
+    static unsigned gs_blocks(const hdg_ctx *c) {
+        return (unsigned)(((c->ncells + 1) / 2 + TEAMS_PER_BLOCK - 1) / TEAMS_PER_BLOCK);
+    }
+
+    // One Arnoldi step of the inner FP32 solve: the preconditioner (block Jacobi, or red-black block
+    // Gauss-Seidel, hdg_gs32.cuh), the product with the block partials of its dots, and the
+    // finishing kernel (ctl: it also keeps the loop L's state; limit: the loop's pass guard)
+    static void inner_step32(hdg_ctx *c, LoopCtl L, int limit, int ctl) {
+        const EdgeTab<float> E{c->ephi32, c->pen32, c->nrm32};
+        const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
+        if (use_gs(c)) {
+            const size_t smg = sizeof(float) * TEAMS_PER_BLOCK * (2 * NU + 6 * Dm::NFQ);
+            for (int col = 0; col < 2; ++col)
+                launch_k(k_gs_diag<K>, gs_blocks(c), 128, smg, c->st, E, c->M, (const float *)c->Binv32, (const float *)c->gw32,
+                         c->gV32, c->utr32, (const float *)c->wq32, (const GmresState *)c->gs, col);
+            launch_k(k_gs_apply<K>, ab, 128, sizeof(float) * TEAMS_PER_BLOCK * 6 * Dm::NFQ, c->st, E, c->M,
+                     (const float *)c->wq32, (const float *)c->utr32, c->gw32, (const float *)c->gV32, c->rb(), c->gs);
+        } else {
+            gmres_arnoldi<float>(c, E, c->Binv32, c->wq32, c->utr32, c->gw32, c->gV32);
+        }
+        launch_k(k_gm_finish_ctl, 1, 256, 0, c->st, L, limit, c->rb(), (int)ab, c->gs, ctl);
+    }
+
     // A loose Step-I solve in FP32, recorded into the current capture: one GMRES(GM_M) cycle from
     // x = 0 with its Arnoldi steps as a device-side loop, stopping at the tolerance or after GM_M
     // steps (an inexact solve is what the flexible outer iteration expects). b, x: FP64.
@@ -1035,16 +1061,20 @@ struct Impl {
         capture_while(
             c, [&](LoopCtl L) { launch_k(k_loop_init, 1, 1, 0, c->st, L, &c->gs->cycle_end); },
             [&](LoopCtl L) {
-                const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
                 const int U = inner_unroll();
-                for (int u = 0; u < U; ++u) {
-                    gmres_arnoldi<float>(c, E, c->Binv32, c->wq32, c->utr32, c->gw32, c->gV32);
-                    launch_k(k_gm_finish_ctl, 1, 256, 0, c->st, L, GM_M / U + 2, c->rb(), (int)ab, c->gs, u == U - 1 ? 1 : 0);
-                }
+                for (int u = 0; u < U; ++u) inner_step32(c, L, GM_M / U + 2, u == U - 1 ? 1 : 0);
             });
         launch_k(k_gm_solve32, 1, 256, 0, c->st, c->gs);
-        launch_k(k_gm_combine_update<K, float>, cell_blocks(c), 128, sizeof(float) * TEAMS_PER_BLOCK * NU, c->st, c->gV32,
-                 c->Binv32, x, c->M, (const GmresState *)c->gs, c->dcnt);
+        if (use_gs(c)) {
+            const EdgeTab<float> E32{c->ephi32, c->pen32, c->nrm32};
+            for (int col = 0; col < 2; ++col)
+                launch_k(k_gs_combine<K>, gs_blocks(c), 128, sizeof(float) * TEAMS_PER_BLOCK * (2 * NU + 6 * Dm::NFQ), c->st,
+                         E32, c->M, (const float *)c->gV32, (const float *)c->Binv32, (const float *)c->wq32, c->utr32, x,
+                         (const GmresState *)c->gs, col == 1 ? c->dcnt : (DevCount *)nullptr, col);
+        } else {
+            launch_k(k_gm_combine_update<K, float>, cell_blocks(c), 128, sizeof(float) * TEAMS_PER_BLOCK * NU, c->st, c->gV32,
+                     c->Binv32, x, c->M, (const GmresState *)c->gs, c->dcnt);
+        }
         CKL();
     }
 
@@ -1638,6 +1668,7 @@ void hdg_default_params(hdg_params *p) {
     p->persistent_stepI = 0;
     p->inner_trace_fp32 = 1;
     p->trace_fp32_vcycle = 1;
+    p->inner_gs = 1;
 }
 
 const char *hdg_status_string(hdg_status s) {
@@ -1717,6 +1748,12 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         c->tab = make_tableau(params->tableau);
         c->T = build_tables(params->k);
         c->H = build_mesh(mesh->n, mesh->Lx, mesh->Ly, mesh->periodic_x != 0, mesh->periodic_y != 0);
+        c->gs_ok = c->H.ncells % 2 == 0;                         // every neighbour of the other parity?
+        for (int k = 0; k < c->H.ncells && c->gs_ok; ++k)
+            for (int e = 0; e < 3; ++e) {
+                const int o = c->H.cell_nbr[3 * k + e];
+                if (o >= 0 && (o & 1) == (k & 1)) { c->gs_ok = false; break; }
+            }
         c->K = params->k;
         c->MU = c->T.mu; c->NU = 2 * c->T.mu; c->NP = c->T.np; c->NT = c->T.nt; c->NL = 3 * c->T.nt;
         c->ncells = c->H.ncells;
@@ -2157,10 +2194,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 };
                 auto steps = [&]() {
                     start();
-                    for (int k = 0; k < S; ++k) {
-                        I::template gmres_arnoldi<float>(c, E, c->Binv32, c->wq32, c->utr32, c->gw32, c->gV32);
-                        launch_k(k_gm_finish_ctl, 1, 256, 0, c->st, LoopCtl{}, 0, c->rb(), (int)ab, c->gs, 0);
-                    }
+                    for (int k = 0; k < S; ++k) I::inner_step32(c, LoopCtl{}, 0, 0);
                 };
                 steps();
                 CKL();

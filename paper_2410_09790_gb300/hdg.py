@@ -41,7 +41,7 @@ class hdg_params(ctypes.Structure):
                 ('inner_trace_rtol', ctypes.c_double), ('trace_mg', ctypes.c_int),
                 ('device_loops', ctypes.c_int), ('inner_trace_vcycles', ctypes.c_int),
                 ('persistent_stepI', ctypes.c_int), ('inner_trace_fp32', ctypes.c_int),
-                ('trace_fp32_vcycle', ctypes.c_int)]
+                ('trace_fp32_vcycle', ctypes.c_int), ('inner_gs', ctypes.c_int)]
 
 
 class hdg_stats(ctypes.Structure):

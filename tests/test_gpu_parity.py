@@ -250,6 +250,29 @@ def test_inner_trace_vcycle_fp32_matches_fp64(n, px, k):
     assert it32 <= 1.1 * it64 + 3, (it32, it64)
 
 
+@pytest.mark.parametrize('n,px,k', [(8, True, 1), (8, True, 2), (8, True, 3), (8, True, 4), (16, False, 3)])
+def test_inner_gauss_seidel_matches_jacobi(n, px, k):
+    # the red-black block Gauss-Seidel preconditioner of the inner Step-I solves changes only the
+    # preconditioner: both runs meet the stage tolerance, agree to it, need about as many outer
+    # iterations, and Gauss-Seidel fewer inner Arnoldi steps
+    Q0 = W.nodal_velocity(n, k, lambda x, y: W.shear_layer(x, y, width=0.1, amp=0.05), noise=1e-3, seed=9)
+    outs, stats = [], []
+    for gsp in (0, 1):
+        ctx = H().Context(n, k, periodic_x=px, tableau='ARS343', dt=0.01, n_richardson=0, stage_krylov=1,
+                          richardson_rtol=1e-12, richardson_max=400, inner_gs=gsp)
+        ctx.hdg_set_state(cuda(Q0))
+        ctx.hdg_reconstruct_pressure()
+        stats.append(ctx.hdg_imex_step(2))
+        outs.append([host(x) for x in ctx.hdg_get_state()[:3]])
+        ctx.close()
+    assert_close(outs[1][0], outs[0][0], 1e-10, 'Q')
+    assert_close(outs[1][1], outs[0][1], 1e-9, 'p')
+    for st in stats:
+        assert st['status'] == 0 and st['stepI_solves'] > 0
+    assert stats[1]['richardson_iters'] <= 1.15 * stats[0]['richardson_iters'] + 3, stats
+    assert stats[1]['stepI_iters'] < stats[0]['stepI_iters'], stats
+
+
 @pytest.mark.parametrize('n,px,k', [(8, True, 2), (16, False, 3), (16, True, 4)])
 def test_trace_cg_fp32_vcycle_matches_fp64(n, px, k):
     # the tight trace solves with the FP32 V-cycle inside flexible CG reach the same tolerance as
