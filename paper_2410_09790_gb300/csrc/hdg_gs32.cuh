@@ -17,7 +17,8 @@
 namespace hdg {
 
 // the cell of colour col handled by this team: teams of a block take consecutive same-colour
-// cells, so a warp's two teams follow the same path
+// cells, so a warp's two teams follow the same path (the cell count is a multiple of 4, so they
+// are in range together)
 #define GS_CELL(COL)                                                                 \
     const int team = threadIdx.x / TEAM_LANES, tpb = blockDim.x / TEAM_LANES;        \
     const int cell = 2 * (blockIdx.x * tpb + team) + (COL);                          \
@@ -107,18 +108,14 @@ __global__ void k_gs_apply(EdgeTab<float> E, MeshDev M, const float *__restrict_
     for (int base = blockIdx.x * tpb; base < M.ncells; base += gridDim.x * tpb) {
         const int cell = base + team;
         if (cell < M.ncells) {
-            if ((cell & 1) == 0) {
-                team_nbr_flux<K, float>(tm, E, M, cell, wq, utr, nullptr, t);
-                tm.sync();
-                TFOR(r, NU) {
-                    const size_t gi = (size_t)cell * NU + r;
-                    w[gi] = vj[gi] + nbr_row<K, float>(E, t, r / MU, r % MU);
-                }
-            } else {
-                TFOR(r, NU) {
-                    const size_t gi = (size_t)cell * NU + r;
-                    w[gi] = vj[gi];
-                }
+            // a warp holds one red and one black team: both execute the same barriers (a team
+            // sync is a whole-warp __syncwarp)
+            const bool red = (cell & 1) == 0;
+            if (red) team_nbr_flux<K, float>(tm, E, M, cell, wq, utr, nullptr, t);
+            tm.sync();
+            TFOR(r, NU) {
+                const size_t gi = (size_t)cell * NU + r;
+                w[gi] = red ? vj[gi] + nbr_row<K, float>(E, t, r / MU, r % MU) : vj[gi];
             }
             tm.sync();
         }

@@ -1748,7 +1748,9 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         c->tab = make_tableau(params->tableau);
         c->T = build_tables(params->k);
         c->H = build_mesh(mesh->n, mesh->Lx, mesh->Ly, mesh->periodic_x != 0, mesh->periodic_y != 0);
-        c->gs_ok = c->H.ncells % 2 == 0;                         // every neighbour of the other parity?
+        // every neighbour of the other parity? (and cells in fours, so that the two teams of a warp in
+        // the colour kernels are both in range or both out: their team syncs are whole-warp)
+        c->gs_ok = c->H.ncells % 4 == 0;
         for (int k = 0; k < c->H.ncells && c->gs_ok; ++k)
             for (int e = 0; e < 3; ++e) {
                 const int o = c->H.cell_nbr[3 * k + e];
