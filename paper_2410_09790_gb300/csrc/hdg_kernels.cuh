@@ -817,27 +817,16 @@ __global__ void k_loop_init(LoopCtl L, const int *stop) {
     cudaGraphSetConditional(L.h, *stop ? 0u : 1u);
 }
 
-// Last block of an Arnoldi step, called by all its threads: Hessenberg column (hcol, plus h2
-// after a second pass), norm hn = ||w|| (the value of thread 0; with pyth, thread 0 forms it as
-// sqrt(||w||^2 - sum h^2) from hcol[j+1] = ||w||^2, floored at 1e-12 ||w||^2 against
-// cancellation), Givens rotations, residual estimate, step bookkeeping. The state it reads is
-// first gathered into shared memory by the block in one round of independent loads; thread 0
-// then works on shared memory and only stores to the state.
-// hsrc (shared memory, optional): the column (V_i, w), i <= j, and ||w||^2 already summed by the
-// block, used in place of gs->hcol and stored there.
-__device__ void gm_finish_step(GmresState *gs, int j, double hn, bool with_h2, bool pyth = false,
-                               const double *hsrc = nullptr) {
+// Last block of an FP64 Arnoldi step, called by all its threads: Hessenberg column (hcol, plus
+// h2 after a second pass), norm hn = ||w|| (the value of thread 0), Givens rotations, residual
+// estimate, step bookkeeping. The state it reads is first gathered into shared memory by the
+// block in one round of independent loads; thread 0 then works on shared memory and only stores
+// to the state.
+__device__ void gm_finish_step(GmresState *gs, int j, double hn, bool with_h2) {
     __shared__ double Hc[GM_M + 2], cs[GM_M], sn[GM_M], dsc[4];
     __shared__ int isc[3];
     const int t = threadIdx.x;
-    if (t <= j + 1) {
-        if (hsrc) {
-            Hc[t] = hsrc[t];
-            gs->hcol[t] = hsrc[t];
-        } else {
-            Hc[t] = (with_h2 && t <= j) ? gs->hcol[t] + gs->h2[t] : gs->hcol[t];
-        }
-    }
+    if (t <= j) Hc[t] = with_h2 ? gs->hcol[t] + gs->h2[t] : gs->hcol[t];
     if (t < j) { cs[t] = gs->cs[t]; sn[t] = gs->sn[t]; }
     const int tl = (int)blockDim.x - 1;               // scalars: the block's last threads
     if (t == tl) dsc[0] = gs->g[j];
@@ -848,12 +837,6 @@ __device__ void gm_finish_step(GmresState *gs, int j, double hn, bool with_h2, b
     if (t == tl - 5) isc[2] = gs->maxit;
     __syncthreads();
     if (t != 0) return;
-    if (pyth) {
-        double h2 = 0.0;
-        for (int i = 0; i <= j; ++i) h2 += Hc[i] * Hc[i];
-        const double ww = Hc[j + 1], hn2 = ww - h2;
-        hn = sqrt(hn2 > 1e-12 * ww ? hn2 : 1e-12 * ww);
-    }
     Hc[j + 1] = hn;
     for (int i = 0; i < j; ++i) {                     // previous rotations
         const double a = Hc[i], b2 = Hc[i + 1];
@@ -1532,14 +1515,6 @@ __global__ void k_vec_dot32(const float *__restrict__ w32, const float *__restri
     wait_prior_kernel();
     if (gs->cycle_end) return;
     multidot_rows(rb, V32, w32, n, gs->j + 1, gs->hcol, false);
-}
-
-// hcol = V^T w over V_0..V_j
-__global__ void k_vec_dot(const double *__restrict__ w, const double *__restrict__ V, long long n, RedBuf rb,
-                          GmresState *gs, int with_norm) {
-    wait_prior_kernel();
-    if (gs->cycle_end) return;
-    multidot_rows(rb, V, w, n, gs->j + 1, gs->hcol, with_norm != 0);
 }
 
 // Second classical Gram-Schmidt pass of the stage FGMRES, first half: w' = w - V hcol; h2 =
