@@ -27,6 +27,37 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
 
 
+def struct_fields(name):
+    """Field names, in order, of `typedef struct { ... } name;` in include/hdg.h."""
+    src = open(os.path.join(ROOT, 'include', 'hdg.h')).read()
+    src = re.sub(r'/\*.*?\*/', '', src, flags=re.S)
+    body = re.search(r'typedef struct \{([^{}]*)\}\s*' + name + r'\s*;', src).group(1)
+    out = []
+    for decl in body.split(';'):
+        decl = decl.strip()
+        if decl:
+            parts = decl.split(',')           # "type a, b": a is the last word of the first part
+            names = [parts[0].split()[-1]] + [q.strip() for q in parts[1:]]
+            out += [v.lstrip('*').split('[')[0] for v in names]
+    return out
+
+
+@pytest.mark.parametrize('name', ['hdg_params', 'hdg_stats', 'hdg_mesh_desc'])
+def test_ctypes_mirrors_match_header(name):
+    # the binding's ctypes structures list the header's fields in the header's order
+    assert [f[0] for f in getattr(H.hdg, name)._fields_] == struct_fields(name)
+
+
+def test_default_params():
+    # hdg_default_params (host code) fills the documented defaults, the GB300 options on
+    p = H.hdg.hdg_default_params()
+    assert p.alpha == 1.0 and p.tau == 1.0 and p.delta_up == 1.0 and p.n_richardson == 2
+    assert p.trace_rtol == 1e-12 and p.stepI_rtol == 1e-10
+    assert (p.stage_krylov, p.trace_mg, p.device_loops, p.inner_trace_vcycles) == (1, 1, 1, 1)
+    assert (p.inner_trace_fp32, p.trace_fp32_vcycle, p.inner_gs, p.persistent_stepI) == (1, 1, 1, 0)
+    assert p.inner_stepI_rtol == 2e-2 and p.inner_trace_rtol == 1e-1
+
+
 def test_status_strings():
     lib = H.load()
     for s in range(7):
