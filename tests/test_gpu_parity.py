@@ -292,6 +292,25 @@ def test_trace_cg_fp32_vcycle_matches_fp64(n, px, k):
     assert its[1] <= 1.5 * its[0] + 3, its
 
 
+def test_large_mesh_uses_fp64_vcycle_and_converges():
+    # 128 x 128: the P1 hierarchy no longer fits one block's shared memory, so the FP32 V-cycles
+    # (inner Step II and tight trace CG) fall back to the FP64 V-cycle; the stage solves still
+    # reach their tolerance, and both settings of the FP32 options run the same path
+    n, k = 128, 1
+    Q0 = W.nodal_velocity(n, k, lambda x, y: W.shear_layer(x, y, width=0.05, amp=1e-3), noise=1e-4, seed=3)
+    outs = []
+    for f32 in (1, 0):
+        ctx = H().Context(n, k, periodic_x=True, tableau='ARS222', dt=1e-3, n_richardson=0, stage_krylov=1,
+                          richardson_rtol=1e-10, richardson_max=400, inner_trace_fp32=f32, trace_fp32_vcycle=f32)
+        ctx.hdg_set_state(cuda(Q0))
+        ctx.hdg_div_free_project()
+        st = ctx.hdg_imex_step(1)
+        assert st['status'] == 0 and st['stage_solves'] >= 2 and st['richardson_iters'] > 0, st
+        outs.append([host(x) for x in ctx.hdg_get_state()[:2]])
+        ctx.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
 @pytest.mark.parametrize('n,px', [(16, True), (32, False)])
 def test_multigrid_iterations_mesh_robust(n, px):
     # the V-cycle preconditioner keeps the trace CG iteration count small and nearly independent
