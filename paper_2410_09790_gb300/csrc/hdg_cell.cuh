@@ -495,14 +495,23 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
         Wa[i] = sa;
     }
     tm.sync();
+    // per edge: -alpha n_d n_d2 for (d, d2) = (x, x), (x, y) = (y, x), (y, y); upwind weight h_e on
+    // interior edges
+    double pxx[3], pxy[3], pyy[3], hw[3];
+    for (int e = 0; e < 3; ++e) {
+        pxx[e] = -alpha * g.nx[e] * g.nx[e];
+        pxy[e] = -alpha * g.nx[e] * g.ny[e];
+        pyy[e] = -alpha * g.ny[e] * g.ny[e];
+        hw[e] = Qsn[e] ? g.h[e] : 0.0;
+    }
     TFOR(i, NU * NU) {                  // diagonal block
-        int r = i / NU, x = i % NU, d = r / MU, a = r % MU, d2 = x / MU, b = x % MU;
-        double F = (d == d2) ? adv[a * MU + b] : 0.0;
-        for (int e = 0; e < 3; ++e) {
-            double nd = d == 0 ? g.nx[e] : g.ny[e], nd2 = d2 == 0 ? g.nx[e] : g.ny[e];
-            F += -alpha * nd * nd2 * Sp[(e * MU + a) * MU + b];
-            if (d == d2 && Qsn[e]) F += g.h[e] * Wa[(e * MU + a) * MU + b];
-        }
+        const int r = i / NU, x = i % NU, d = r / MU, a = r % MU, d2 = x / MU, b = x % MU;
+        const int ab = a * MU + b, k = d + d2;
+        const double p0 = k == 0 ? pxx[0] : (k == 1 ? pxy[0] : pyy[0]);
+        const double p1 = k == 0 ? pxx[1] : (k == 1 ? pxy[1] : pyy[1]);
+        const double p2 = k == 0 ? pxx[2] : (k == 1 ? pxy[2] : pyy[2]);
+        double F = p0 * Sp[ab] + p1 * Sp[MU * MU + ab] + p2 * Sp[2 * MU * MU + ab];
+        if (d == d2) F += adv[ab] + hw[0] * Wa[ab] + hw[1] * Wa[MU * MU + ab] + hw[2] * Wa[2 * MU * MU + ab];
         D[i] = ((r == x) ? g.detJ : 0.0) - c * F;
     }
     tm.sync();
