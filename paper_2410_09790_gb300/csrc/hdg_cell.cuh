@@ -561,63 +561,4 @@ __host__ __device__ bool team_invert(const Team &tm, T *A, T *Inv, int *piv_sm) 
     return ok;
 }
 
-#ifdef __CUDACC__
-// The same inverse (Gauss-Jordan, partial pivoting with the first largest |pivot|) for a team of
-// at least 32 threads that syncs as a block: warp 0 finds the pivot with shuffles, and each column
-// takes three barriers (pivot, pivot row and factors, update) plus one when rows are swapped,
-// against six with the serial search above.
-template <int N, class T>
-__device__ bool team_invert_fast(const Team &tm, T *A, T *Inv, int *piv_sm) {
-    __shared__ T fac[N], prow[2 * N];
-    TFOR(i, N * N) Inv[i] = (i / N == i % N) ? T(1) : T(0);
-    tm.sync();
-    for (int col = 0; col < N; ++col) {
-        if (tm.tid < 32) {
-            T best = T(-1);
-            int p = col;
-            for (int r = col + tm.tid; r < N; r += 32) {
-                const T v = fabs(A[r * N + col]);
-                if (v > best) { best = v; p = r; }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const T ob = __shfl_down_sync(0xffffffffu, best, o);
-                const int op = __shfl_down_sync(0xffffffffu, p, o);
-                if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
-            }
-            if (tm.tid == 0) *piv_sm = best > T(0) ? p : -1;
-        }
-        tm.sync();
-        const int p = *piv_sm;
-        if (p < 0) return false;                      // (uniform)
-        if (p != col) {
-            TFOR(j, N) {
-                T t = A[col * N + j]; A[col * N + j] = A[p * N + j]; A[p * N + j] = t;
-                t = Inv[col * N + j]; Inv[col * N + j] = Inv[p * N + j]; Inv[p * N + j] = t;
-            }
-            tm.sync();
-        }
-        TFOR(i, N) {
-            fac[i] = A[i * N + col];
-            prow[i] = A[col * N + i];
-            prow[N + i] = Inv[col * N + i];
-        }
-        tm.sync();
-        const T inv_d = T(1) / prow[col];
-        TFOR(i, N * N) {
-            const int r = i / N, j = i % N;
-            if (r == col) {
-                A[i] = prow[j] * inv_d;
-                Inv[i] = prow[N + j] * inv_d;
-            } else {
-                const T f = fac[r] * inv_d;
-                A[i] = j == col ? T(0) : A[i] - f * prow[j];
-                Inv[i] -= f * prow[N + j];
-            }
-        }
-        tm.sync();
-    }
-    return true;
-}
-#endif
-
 }  // namespace hdg

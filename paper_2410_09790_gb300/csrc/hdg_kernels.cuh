@@ -627,7 +627,7 @@ __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c
         float *A32 = reinterpret_cast<float *>(inv), *I32 = A32 + NU * NU;
         TFOR(i, NU * NU) A32[i] = (float)D[i];
         tm.sync();
-        ok = team_invert_fast<NU, float>(tm, A32, I32, piv);
+        ok = team_invert<NU, float>(tm, A32, I32, piv);
         TFOR(i, NU * NU) {
             int col = i / NU, row = i % NU;
             Binv32[(size_t)col * nrows + (size_t)cell * NU + row] = I32[row * NU + col];
@@ -636,7 +636,7 @@ __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c
     }
     if (Binv) {
         // the diagonal block is consumed by the inversion (in place)
-        ok = team_invert_fast<NU, double>(tm, D, inv, piv) && ok;
+        ok = team_invert<NU, double>(tm, D, inv, piv) && ok;
         TFOR(i, NU * NU) {
             int col = i / NU, row = i % NU;
             Binv[(size_t)col * nrows + (size_t)cell * NU + row] = inv[row * NU + col];
