@@ -107,7 +107,7 @@ typedef struct {
     int inner_trace_vcycles;
     /* Inner (FP32) Step-I solves: 0 (default) = a sequence of kernels per Arnoldi step (launched
      * with programmatic dependent launch); 1 = one persistent cooperative kernel per solve with
-     * bounded grid-wide barriers (same algorithm; slower on GB300 at the bench size: the barriers
+     * bounded grid-wide barriers (same algorithm; slower on GB300 on a 64 x 64, k = 3 mesh: the barriers
      * cost more than the kernel boundaries they replace). */
     int persistent_stepI;
     /* The one-V-cycle Step II inside the stage preconditioner (inner_trace_vcycles = 1): 1
