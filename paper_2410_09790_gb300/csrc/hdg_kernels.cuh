@@ -731,14 +731,15 @@ __global__ void k_cell_apply_mf(EdgeTab<double> E, MeshDev M, const double *__re
 
 // ------------------------------------------------------------------ stage operator, fused
 // The stage operator A(c) applied to x = (Q, p, lambda) in one pass per cell (yQ32, yp32: FP32
-// copies of the output for the FGMRES first-pass dots, when set): velocity rows
+// copies of the output for the FGMRES first-pass dots, when set; zslot: x also copied to slot
+// *zslot_j (the FGMRES step) of the FGMRES's preconditioned vectors, when set): velocity rows
 // (M - cF)Q - c G(p, lambda) (diagonal block dense, neighbours matrix-free), constraint rows of
 // the cell (p-rows yp, the cell's lambda-row contributions v; summed per facet by k_facet_gather).
 template <int K>
 __global__ void k_stage_apply(RefDev R, EdgeTab<double> E, MeshDev M, const double *__restrict__ Dblk,
                               const double *__restrict__ wq, double c, double tau, const double *Q,
                               const double *p, const double *lam, double *yQ, double *yp, double *v,
-                              float *yQ32, float *yp32) {
+                              float *yQ32, float *yp32, double *zslot, const int *zslot_j) {
     wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NP = Dm::NP, NT = Dm::NT, NL = Dm::NL, NFQ = Dm::NFQ;
@@ -776,6 +777,16 @@ __global__ void k_stage_apply(RefDev R, EdgeTab<double> E, MeshDev M, const doub
     int flip[3] = {M.cell_flip[3 * cell], M.cell_flip[3 * cell + 1], M.cell_flip[3 * cell + 2]};
     cell_constraint<K>(tm, R, g, flip, tau, QK, pK, lK, cs, yp + (size_t)cell * NP, v + (size_t)cell * NL);
     if (yp32) TFOR(b, NP) yp32[(size_t)cell * NP + b] = (float)yp[(size_t)cell * NP + b];   // (team-synced)
+    if (zslot) {                        // the input x also stored as slot gs->j of the FGMRES's Z
+        const long long nQ = (long long)M.ncells * NU, nPv = (long long)M.ncells * NP;
+        double *zj = zslot + (size_t)*zslot_j * (size_t)(nQ + nPv + (long long)M.nfacets * NT);
+        TFOR(x, NU) zj[(size_t)cell * NU + x] = QK[x];
+        TFOR(b, NP) zj[nQ + (size_t)cell * NP + b] = pK[b];
+        TFOR(i, 3 * NT) {               // each facet's values once, by its first cell
+            const int f = M.cell_facet[3 * cell + i / NT];
+            if (M.facet_cell[2 * f] == cell) zj[nQ + nPv + (size_t)f * NT + i % NT] = lam[(size_t)f * NT + i % NT];
+        }
+    }
 }
 
 
@@ -883,14 +894,6 @@ __global__ void k_gm_loop_ctl(LoopCtl L, int limit, const GmresState *gs, int in
     }
     const bool more = !gs->converged && gs->breakdown != 2 && gs->total < gs->maxit && gd < limit;
     cudaGraphSetConditional(L.h, more ? 1u : 0u);
-}
-
-// Z[j] = z with j = gs->j (basis slot of the current Arnoldi step)
-__global__ void k_slot_store(const double *__restrict__ z, double *Z, long long n, const GmresState *gs) {
-    wait_prior_kernel();
-    if (gs->cycle_end) return;
-    double *zj = Z + (size_t)gs->j * n;
-    GRID_STRIDE(i, n) zj[i] = z[i];
 }
 
 // Solve counters kept on the device (DevCount fields: see the struct)

@@ -1225,14 +1225,15 @@ struct Impl {
     // Stage operator y = A(c) x, x = (Q | p | lam) contiguous:
     //   yQ = (M - cF) Q - c G (p, lam),  (yp | ylam) = B Q + C (p, lam)   (one fused cell pass)
     // y32 (optional): an FP32 copy of y
-    static void stage_apply(hdg_ctx *c, double cc, const double *x, double *y, float *y32 = nullptr) {
+    static void stage_apply(hdg_ctx *c, double cc, const double *x, double *y, float *y32 = nullptr,
+                            double *zslot = nullptr, const GmresState *zgs = nullptr) {
         const double *Q = x, *p = x + c->nQ, *lam = x + c->nQ + c->nPv;
         double *yQ = y, *yp = y + c->nQ, *yl = y + c->nQ + c->nPv;
         float *yQ32 = y32, *yp32 = y32 ? y32 + c->nQ : nullptr, *yl32 = y32 ? y32 + c->nQ + c->nPv : nullptr;
         unsigned nb = cell_blocks(c);
         launch_k(k_stage_apply<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (6 * Dm::NFQ + NL + 2 * MU), c->st, 
             c->R, EdgeTab<double>{c->R.ephi, c->pen}, c->M, c->Dblk, c->wq, cc, c->P.tau, Q, p, lam, yQ, yp, c->vK,
-            yQ32, yp32);
+            yQ32, yp32, zslot, zgs ? &zgs->j : (const int *)nullptr);
         CKL();
         launch_k(k_facet_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, nullptr, yl, yl32);
         CKL();
@@ -1333,8 +1334,7 @@ struct Impl {
                     c, [&](LoopCtl L2) { launch_k(k_loop_init, 1, 1, 0, c->st, L2, &fgs->cycle_end); },
                     [&](LoopCtl L2) {
                         chorin_precond(c, cc, c->fv, c->fz);
-                        launch_k(k_slot_store, g, VEC_THREADS, 0, c->st, c->fz, c->fZ, N, fgs);
-                        stage_apply(c, cc, c->fz, w, c->fw32);
+                        stage_apply(c, cc, c->fz, w, c->fw32, c->fZ, fgs);      // also Z_j = fz
                         fgmres_orth(c, w, N, fgs, c->fv);
                         launch_k(k_loop_ctl, 1, 1, 0, c->st, L2, GM_M + 1, &fgs->cycle_end);
                         CKL();
@@ -2344,7 +2344,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 auto launch = [&]() {
                     launch_k(k_stage_apply<I::K_>, nb, 128, sm, c->st, c->R, EdgeTab<double>{c->R.ephi, c->pen}, c->M,
                              c->Dblk, c->wq, cc, c->P.tau, c->Q, c->p, c->lam, c->q[6], c->pp[1], c->vK,
-                             (float *)nullptr, (float *)nullptr);
+                             (float *)nullptr, (float *)nullptr, (double *)nullptr, (const int *)nullptr);
                 };
                 launch();
                 CKL();
