@@ -164,7 +164,8 @@ def test_solve_stage_tolerance_reaches_monolithic():
     assert_close(host(p), pd, 1e-9, 'p')
 
 
-@pytest.mark.parametrize('n,k,c', [(4, 2, 0.003), (16, 2, 3.6 / 256), (8, 3, 0.9 / 64)])
+@pytest.mark.parametrize('n,k,c', [(4, 2, 0.003), (16, 2, 3.6 / 256), (8, 3, 0.9 / 64), (8, 1, 0.9 / 64),
+                                   (8, 4, 0.9 / 64)])
 def test_solve_stage_krylov_reaches_monolithic(n, k, c):
     # Alg. 2's preconditioner inside flexible GMRES, including the stiff regime c/h^2 = 3.6 where
     # the plain Richardson iteration contracts slowly
