@@ -423,3 +423,28 @@ def test_invalid_inputs_rejected_on_device():
         ctx.hdg_mixed_solve(-1.0)
     with pytest.raises(ValueError):
         ctx.hdg_set_state(torch.zeros(3, device='cuda'))          # wrong dtype
+
+
+def test_time_kernel_modes_and_algorithmic_bytes():
+    # the instrumentation bench.py builds its roofline on: every mode runs, and modes 6, 8 and 9
+    # report the algorithmic bytes their documentation states
+    n, k = 8, 3
+    Q0 = W.nodal_velocity(n, k, lambda x, y: W.shear_layer(x, y, width=0.1, amp=0.05), noise=1e-3, seed=12)
+    ctx = H().Context(n, k, periodic_x=True, tableau='ARS343', dt=0.01, n_richardson=0, stage_krylov=1,
+                      richardson_rtol=1e-10, richardson_max=400)
+    ctx.hdg_set_state(cuda(Q0))
+    ctx.hdg_reconstruct_pressure()
+    ctx.hdg_imex_step(1)
+    cstage = 0.43586652150845899942 * 0.01
+    mu, npk, nt = (k + 2) * (k + 3) // 2, (k + 1) * (k + 2) // 2, k + 1
+    nu, nfq = 2 * mu, (3 * k + 5) // 2
+    nc = ctx.nQ // nu
+    res = {}
+    for which in range(11):
+        ms, b = ctx.hdg_time_kernel(which, 1.0 if which == 1 else cstage, 3)
+        assert ms > 0.0 and np.isfinite(ms), (which, ms)
+        res[which] = b
+    assert res[6] == 4.0 * (nc * 3 * nfq * 3 + 2 * ctx.nQ + 5 * ctx.nQ)
+    assert res[9] == 4.0 * (nc * nu * nu + 6 * ctx.nQ + nc * 3 * nfq * 2)
+    assert res[8] == 8.0 * nc * (nu * nu + 3 * nfq) + 4.0 * 6 * nc + 8.0 * (2 * ctx.nQ + 2 * ctx.nP + ctx.nL + nc * 3 * nt)
+    ctx.close()
