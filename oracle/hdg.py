@@ -210,6 +210,28 @@ class HDG:
                                      (self.nQ, self.nQ))
         return F.tocsr()
 
+    # ----------------------------------------------------------------- L2 projection
+    def l2_project(self, fun, field, npts=None):
+        """L2 projection, cell by cell, of fun(x, y) onto V_Q (field 0; fun returns the pair of
+        components) or V_p (field 1): the coefficients c of each cell solve
+        (phi_a, phi_b)_K c_b = (f, phi_a)_K, the integrals taken by the collapsed Gauss rule with
+        npts x npts points (default k + 4: exact to degree 2k + 7, i.e. the degree 2(k+1)+4 that
+        non-polynomial data is projected with). Returns the nodal coefficients in the exchange
+        layout ([cell][2][mu] or [cell][n_p], flattened)."""
+        m = self.mesh
+        qp, qw = triangle_quadrature(npts or self.k + 4)
+        X = m.cell_points(np.arange(m.ncells), qp)                 # (c, nq, 2)
+        V = self.Vu if field == 0 else self.Vp
+        B = V.values(qp)                                           # (nq, nb)
+        mass = np.einsum('q,qa,qb->ab', qw, B, B)                  # detJ cancels on both sides
+        if field == 0:
+            fx, fy = fun(X[..., 0], X[..., 1])
+            f = np.stack([fx, fy], axis=1)                         # (c, 2, nq)
+            rhs = np.einsum('q,qa,cdq->cda', qw, B, f)
+        else:
+            rhs = np.einsum('q,qa,cq->ca', qw, B, fun(X[..., 0], X[..., 1]))
+        return np.linalg.solve(mass, rhs[..., None])[..., 0].reshape(-1)
+
     # ----------------------------------------------------------------- helpers on fields
     def mean_p(self, p):
         """(p)_Omega / |Omega| (the reference triangle has area 1/2)."""

@@ -161,3 +161,46 @@ def test_trace_schur_complement_semidefinite_with_constant_kernel():
                 ev = np.linalg.eigvalsh(-S)        # the mu-row sign makes S negative semidefinite
                 assert abs(ev[0]) < 1e-10 * ev[-1] and ev[1] > 1e-8 * ev[-1]
                 assert np.abs(S @ np.ones(h.nL)).max() < 1e-11 * np.abs(S).max()
+
+
+def _const_field(h, cell, vec):
+    """Nodal velocity that is the constant vector vec on one cell and zero elsewhere."""
+    Q = np.zeros((h.mesh.ncells, 2, h.mu))
+    Q[cell, 0, :], Q[cell, 1, :] = vec
+    return Q.reshape(-1)
+
+
+@pytest.mark.parametrize('per', MESHES)
+@pytest.mark.parametrize('k', [1, 3])
+def test_fimpl_penalty_and_upwind_weights_closed_form(per, k):
+    # eq. f_impl with Q, w constant on single cells and a constant advecting velocity u: the volume
+    # term vanishes and each facet integral is its constant integrand times |F| = h_F, so
+    #   penalty  -alpha h_F^-1 <[[Q.n]][[w.n]]>  -> -alpha [[Q.n]][[w.n]]        (no h left)
+    #   central  <(u.n+)(Q+ - Q-).{w}>           ->  h_F (u.n+)(Q+ - Q-).{w}
+    #   upwind   -delta <|u.n+|(Q+ - Q-).(w+ - w-)> -> -delta h_F |u.n+|(Q+ - Q-).(w+ - w-)
+    # For Q = a on K1, w = b on its neighbour K2 across F (n1 = outward normal of K1 on F):
+    #   w^T F Q = alpha (a.n1)(b.n1) + h_F (u.n1)(a.b)/2 + delta h_F |u.n1| (a.b)
+    # and for w = b on K1 itself (sum over K1's facets e, walls included in the penalty only):
+    #   w^T F Q = -alpha sum_e (a.n_e)(b.n_e) + sum_{e interior} h_e ((u.n_e)/2 - delta |u.n_e|)(a.b)
+    m = Mesh(3, Lx=2.0, Ly=1.0, periodic_x=per[0], periodic_y=per[1])   # facets of three lengths
+    a, b, u = np.array([0.7, -1.3]), np.array([-0.4, 0.9]), np.array([1.1, 0.35])
+    for alpha, delta in ((1.0, 0.0), (0.0, 1.0), (2.5, 0.6)):
+        h = HDG(m, k, alpha=alpha, delta_up=delta)
+        Qs = np.tile(np.repeat(u, h.mu), m.ncells)             # constant advecting velocity
+        F = h.fimpl(Qs)
+        for f in np.nonzero(m.interior)[0][::3]:
+            K1, K2 = m.f_cell[f]
+            n1, hf = m.f_normal[f], m.f_h[f]                   # outward from side 0 = K1
+            got = _const_field(h, K2, b) @ (F @ _const_field(h, K1, a))
+            want = alpha * (a @ n1) * (b @ n1) + hf * (u @ n1) * (a @ b) / 2 + delta * hf * abs(u @ n1) * (a @ b)
+            assert abs(got - want) < 1e-12 * (1 + abs(want)), (f, got, want)
+        for K1 in range(0, m.ncells, 5):
+            want = 0.0
+            for e in range(3):
+                f = m.cell_facet[K1, e]
+                ne = m.f_normal[f] * (1 if m.cell_side[K1, e] == 0 else -1)
+                want -= alpha * (a @ ne) * (b @ ne)
+                if m.interior[f]:
+                    want += m.f_h[f] * ((u @ ne) / 2 - delta * abs(u @ ne)) * (a @ b)
+            got = _const_field(h, K1, b) @ (F @ _const_field(h, K1, a))
+            assert abs(got - want) < 1e-12 * (1 + abs(want)), (K1, got, want)
