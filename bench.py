@@ -1,14 +1,20 @@
 """Benchmark: IMEX stage solves/s of the HDG incompressible-Euler stage solver on GB300.
 
-Workload (the plain-FP64 GPU configuration): periodic-in-x channel [0,1]^2 with walls at
-y = 0, 1, 64 x 64 rectangles -> 8192 triangles, k = 3 (velocity P4, pressure/trace P3),
+Default workload (c2, the plain-method GPU configuration): periodic-in-x channel [0,1]^2 with
+walls at y = 0, 1, 64 x 64 rectangles -> 8192 triangles, k = 3 (velocity P4, pressure/trace P3),
 ARS(3,4,3), dt = 2e-3; every stage solved to a relative stage residual of 1e-10 (flexible GMRES
 preconditioned by Alg. 2's Chorin split; inside it Step I by one FP32 GMRES cycle to 2e-2 and
-Step II by one trace multigrid V-cycle;
-the paper's fixed n_R = 2 is unstable on this flow); final update and pressure reconstruction
-trace CG rtol 1e-12; initial u = (tanh((y-1/2)/0.05), 1e-3 sin 2 pi x) + seeded N(0,1) 1e-4
-noise per nodal value, projected to divergence-free. One bench step = one IMEX time step of
-Alg. 1 (3 stage solves, final update, pressure reconstruction) through hdg_imex_step.
+Step II by one FP32 trace multigrid V-cycle: precision HDG_MIXED; the paper's fixed n_R = 2 is
+unstable on this flow); final update and pressure reconstruction trace CG rtol 1e-12; initial
+u = (tanh((y-1/2)/0.05), 1e-3 sin 2 pi x) + seeded N(0,1) 1e-4 noise per nodal value, projected to
+divergence-free. One bench step = one IMEX time step of Alg. 1 (3 stage solves, final update,
+pressure reconstruction) through hdg_imex_step. The same steps are also timed with every kernel in
+FP64 (precision HDG_FP64; same stage tolerance) and the two results compared field by field.
+
+--workload c3: the forced Taylor-Green vortex on 256 x 256 rectangles with walls, k = 4,
+ARS(3,4,3), dt = 1.25e-4 (the stage stiffness c/h^2 of c2), f = -exp(-t) Q0, initial field and
+forcing by the library's L2 projection (hdg_project); HDG_MIXED and HDG_FP64 timed in the same run,
+errors against each other and against the exact solution exp(-t) Q0.
 
 Output: one JSON line (rank 0). value = stage solves/s (whole job); trace_dof_per_s = trace
 unknowns x trace solves / s. e2e: the same through the C-ABI with the state copied from pinned
@@ -16,8 +22,8 @@ host memory to the device and back every step. roofline: the kernel with the lar
 step, the fused FP64 stage-operator kernel (the flexible GMRES product), timed alone with CUDA
 events on the context's stream; it is bound by GB300's FP64 pipe, so achieved = algorithmic
 FP64 flops / time against the nominal FP64 rate. inner_stepI_fp32 (the two kernels of an inner
-Arnoldi step, bytes / time vs the measured HBM peak), trace_apply and stage_apply_fp64 report
-more kernels of the path the same way.
+Arnoldi step, bytes / time vs the measured HBM peak; warm in L2 at this size), trace_apply and
+stage_apply_fp64 report more kernels of the path the same way.
 cpu_baseline / --impl reference: the oracle (plain FP64 SciPy) on the host cores.
 """
 import argparse
@@ -31,10 +37,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(n=64, k=3, periodic_x=True, tableau='ARS343', dt=2e-3, n_richardson=0, stage_rtol=1e-10,
-                inner_stepI_rtol=2e-2, inner_trace_rtol=1e-1, trace_rtol=1e-12, stepI_rtol=1e-10,
-                inner_trace_vcycles=1, inner_trace_fp32=1, trace_fp32_vcycle=1, inner_gs=1,
-                init='shear_layer', width=0.05, amp=1e-3, noise=1e-4, seed=0)
+# solver settings of every bench context (the workloads themselves: hdg_workloads.WORKLOADS)
+SOLVER = dict(n_richardson=0, stage_krylov=1, inner_stepI_rtol=2e-2, inner_trace_rtol=1e-1, trace_rtol=1e-12,
+              stepI_rtol=1e-10, inner_trace_vcycles=1, inner_trace_fp32=1, trace_fp32_vcycle=1, inner_gs=1,
+              richardson_max=600)
 STAGES = {'ARS343': 3, 'ARS222': 2, 'IMEX_EULER': 1}
 METRIC = 'IMEX stage solves/s (trace-DoF/s alongside)'
 
@@ -125,6 +131,11 @@ def job_rate(world, stages, steps, total_ms):
     return world * stages * steps / (total_ms / 1e3)
 
 
+def workload(name):
+    import hdg_workloads as W
+    return dict(W.WORKLOADS[name])
+
+
 def initial_velocity(w, n_override=None, seed_offset=0):
     import hdg_workloads as W
     n = n_override or w['n']
@@ -133,51 +144,51 @@ def initial_velocity(w, n_override=None, seed_offset=0):
 
 
 # ---------------------------------------------------------------------------------- oracle arm
-def oracle_sample(w, n_sample=16, steps=1):
-    """The oracle (as it stands) on a bounded sample of the workload: `steps` IMEX steps of the
-    same configuration on an n_sample x n_sample mesh. Returns (stage solves/s scaled to the
-    full mesh by the cell-count ratio, seconds, description, threads)."""
+def oracle_sample(w, n_sample=32):
+    """The oracle (as it stands) on a bounded sample of the workload: the first stage solve of the
+    first IMEX step (monolithic direct sparse LU, eq. imex_implicit_solve) of the same
+    configuration on an n_sample x n_sample mesh, after the oracle's own divergence-free projection.
+    Returns (stage solves/s scaled to the full mesh by the cell-count ratio, seconds of the timed
+    stage solve, description, threads)."""
     os.environ.setdefault('OMP_NUM_THREADS', '1')
     os.environ.setdefault('OPENBLAS_NUM_THREADS', '1')
-    from oracle import Mesh, HDG, Oracle, TABLEAUS
+    from oracle import Mesh, HDG, Oracle, TABLEAUS, bdm_project
     m = Mesh(n_sample, periodic_x=w['periodic_x'])
     h = HDG(m, w['k'])
     o = Oracle(h)
     Q0 = initial_velocity(w, n_override=n_sample).reshape(-1)
     Q, _, _ = o.div_free_project(Q0)
-    _, p, lam = o.reconstruct_pressure(Q)
     tab = TABLEAUS[w['tableau']]()
+    c1 = tab.A_im[1, 1] * w['dt']
     t0 = time.perf_counter()
-    for s in range(steps):
-        Q, p, lam = o.imex_step(tab, w['dt'], s * w['dt'], Q, p, lam, solver='direct')
+    o.stage_solve(c1, o.M @ Q, bdm_project(h, Q))
     sec = time.perf_counter() - t0
-    stages = STAGES[w['tableau']] * steps
     scale = (n_sample / w['n']) ** 2
-    rate = stages / sec * scale
-    desc = (f'{steps} IMEX step(s) ({stages} stage solves by direct sparse LU of the monolithic stage system, '
-            f'final update, reconstruction) of the same workload on a {n_sample}x{n_sample} mesh in {sec:.1f} s; '
-            f'rate scaled by the cell ratio ({n_sample}/{w["n"]})^2 to the {w["n"]}x{w["n"]} mesh')
+    rate = scale / sec
+    desc = (f'the first stage solve (direct sparse LU of the monolithic stage system, with the f^impl assembly '
+            f'and BDM projection) of the same workload on a {n_sample}x{n_sample} mesh: {sec:.1f} s; rate scaled by '
+            f'the cell ratio ({n_sample}/{w["n"]})^2 to the {w["n"]}x{w["n"]} mesh (sparse LU grows faster than '
+            f'the cell count, so this overstates the oracle at full size)')
     return rate, sec, desc, int(os.environ.get('OMP_NUM_THREADS', '1'))
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    w = dict(WORKLOAD)
-    for _ in range(args.warmup):
-        oracle_sample(w, steps=1)
+    w = workload('c2')
+    for _ in range(min(args.warmup, 1)):
+        oracle_sample(w)
     rates, secs = [], []
     for _ in range(args.steps):
-        r, s, desc, cores = oracle_sample(w, steps=1)
+        r, s, desc, cores = oracle_sample(w)
         rates.append(r)
         secs.append(s)
     value = len(rates) / sum(1.0 / r for r in rates)
     line = {'metric': METRIC, 'value': value, 'unit': 'stage_solves/s', 'impl': 'reference',
-            'n_gpus': args.gpus, 'steps': args.steps, 'warmup': args.warmup,
-            'ms_per_step': 1e3 * sum(secs) / len(secs), 'higher_is_better': True, 'scaling': 'weak',
-            'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
-            'config': {'workload': 'shear-layer channel 64x64, k=3, ARS(3,4,3), dt=2e-3, stages to 1e-10', 'n': w['n'],
-                       'k': w['k'], 'periodic_x': True, 'sample_n': 16},
+            'n_gpus': args.gpus, 'steps': args.steps, 'warmup': min(args.warmup, 1),
+            'ms_per_step': 1e3 * sum(secs) / len(secs) * STAGES[w['tableau']], 'higher_is_better': True,
+            'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
+            'config': {'workload': w['name'], 'n': w['n'], 'k': w['k'], 'periodic_x': True, 'sample_n': 32},
             'cpu_baseline': {'value': value, 'unit': 'stage_solves/s', 'cores': cores, 'kind': 'oracle',
                              'sample': desc},
             'e2e': {'value': value, 'unit': 'stage_solves/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
@@ -185,6 +196,138 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------------- GPU arm
+def rel_err(a, b):
+    """Relative l2 difference of two nodal arrays (host numpy)."""
+    import numpy as np
+    a, b = np.asarray(a).ravel(), np.asarray(b).ravel()
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a - b))
+
+
+def solver_settings(args, w):
+    kw = dict(SOLVER)
+    for key in ('inner_trace_rtol', 'inner_stepI_rtol', 'inner_trace_vcycles', 'inner_trace_fp32', 'trace_fp32_vcycle',
+                'inner_gs'):
+        v = getattr(args, key)
+        if v is not None:
+            kw[key] = v
+    kw['richardson_rtol'] = w['stage_rtol']
+    kw['device_loops'] = 0 if args.host_loops else 1
+    return kw
+
+
+def make_context(H, w, prec, stream, kw, seed_offset=0, n=None):
+    """A context of workload w in precision prec, with its initial state (divergence-free)."""
+    import numpy as np
+    import torch
+    import hdg_workloads as W
+    n = n or w['n']
+    ctx = H.Context(n, w['k'], periodic_x=w['periodic_x'], stream=stream, tableau=w['tableau'], dt=w['dt'],
+                    precision=prec, **kw)
+    if w['init'] == 'shear_layer':
+        Q0 = torch.from_numpy(initial_velocity(w, n_override=n, seed_offset=seed_offset)).cuda()
+        ctx.hdg_set_state(Q0)
+    else:                                             # forced Taylor-Green: L2 projections
+        pts, _ = H.hdg_reference_rule(w['k'], 0)
+        vals = torch.from_numpy(W.sampled_velocity(n, pts, W.taylor_green)).cuda()
+        Q0 = ctx.hdg_project(0, vals)
+        ctx.hdg_set_state(Q0)
+        kappa = w['kappa']
+        ctx.hdg_set_forcing(Q0, lambda t: -kappa * np.exp(-kappa * t))
+    ctx.hdg_div_free_project()
+    return ctx
+
+
+def timed_steps(ctx, stream, steps, warmup, flush, world=1, clk=None):
+    """warmup untimed steps, then `steps` steps each between CUDA events on the context's stream
+    (the L2 flushed before each). Returns (ms per step, stats per step)."""
+    import torch
+    for _ in range(warmup):
+        ctx.hdg_imex_step(1)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stats = []
+
+    def run():
+        for i in range(steps):
+            flush.fill_(float(i))                      # evict the previous step's working set
+            ev[i][0].record(stream)
+            stats.append(ctx.hdg_imex_step(1))
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+    if clk is not None:
+        with clk:
+            run()
+    else:
+        run()
+    return [a.elapsed_time(b) for a, b in ev], stats
+
+
+def state_host(ctx):
+    Q, p, lam, t = ctx.hdg_get_state()
+    return Q.cpu().numpy(), p.cpu().numpy(), lam.cpu().numpy(), t
+
+
+def e2e_steps(ctx, nsteps, flush, dev):
+    """The metric end to end through the C-ABI: per step, the state from pinned host memory to the
+    device, one step, the state back to pinned host memory. Returns (mean ms, bytes each way)."""
+    import torch
+    Qh, ph, lh, tsim = ctx.hdg_get_state()
+    Qh, ph, lh = Qh.cpu().pin_memory(), ph.cpu().pin_memory(), lh.cpu().pin_memory()
+    Qd, pd, ld = torch.empty_like(Qh, device=dev), torch.empty_like(ph, device=dev), torch.empty_like(lh, device=dev)
+    ms = []
+    for i in range(nsteps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Qd.copy_(Qh, non_blocking=True); pd.copy_(ph, non_blocking=True); ld.copy_(lh, non_blocking=True)
+        ctx.hdg_set_state(Qd, pd, ld, tsim)
+        ctx.hdg_imex_step(1)
+        Qo, po, lo, tsim = ctx.hdg_get_state()
+        Qh.copy_(Qo); ph.copy_(po); lh.copy_(lo)
+        torch.cuda.synchronize()
+        ms.append(1e3 * (time.perf_counter() - t0))
+    return sum(ms) / max(len(ms), 1), (Qh.numel() + ph.numel() + lh.numel()) * 8
+
+
+def golden_error(H, w, stream, kw):
+    """Error of one step of the workload on the stored oracle result at 32 x 32
+    (tests/golden/c2_step1_32.npz), per field; None if the file is absent."""
+    import numpy as np
+    path = os.path.join(ROOT, 'tests', 'golden', 'c2_step1_32.npz')
+    if not os.path.exists(path):
+        return None
+    g = np.load(path)
+    n = int(g['meta'][0])
+    ctx = make_context(H, w, 'MIXED', stream, kw, n=n)
+    ctx.hdg_imex_step(1)
+    Q, p, lam, _ = state_host(ctx)
+    ctx.close()
+    q_rms = float(np.linalg.norm(g['Q']) / np.sqrt(g['Q'].size))
+    vs = lambda a, b: float(np.linalg.norm(a - b) / np.sqrt(b.size) / q_rms)
+    return {'mesh': f'{n}x{n} (same workload; oracle: monolithic direct stage solves)',
+            'rel_l2': {'Q': rel_err(Q, g['Q']), 'p': rel_err(p, g['p']), 'lambda': rel_err(lam, g['lam'])},
+            'rms_over_velocity_rms': {'Q': vs(Q, g['Q']), 'p': vs(p, g['p']), 'lambda': vs(lam, g['lam'])},
+            'note': 'the flow\'s pressure is ~1e-3 of the velocity scale; the solver tolerances act at that scale'}
+
+
+def stage_flops(k, ncells):
+    """Algorithmic FP64 flops of one launch of the fused stage operator (k_stage_apply) and of the
+    Step-I operator alone (k_cell_apply_mf)."""
+    mu = (k + 2) * (k + 3) // 2
+    nu, nfq = 2 * mu, (3 * k + 5) // 2
+    npk, nt = (k + 1) * (k + 2) // 2, k + 1
+    s_flop = 2.0 * (nu * nu + 3 * nfq * 2 * mu + 3 * nfq * 8 + nu * 3 * nfq) * ncells
+    st_flop = s_flop + ncells * (nu * (3 * (2 * nt + 3) + 2 * (2 * npk + 2) + 3) + 6 * mu +
+                                 npk * (4 * mu + 3 * (2 * npk + 2) + 3 * (2 * nt + 2) + 5) +
+                                 3 * nt * (5 * mu + 2 * npk + 5))
+    return st_flop, s_flop
+
+
 def run_gpu(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -192,160 +335,128 @@ def run_gpu(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device('cuda', local_rank)
-    w = dict(WORKLOAD)
+    w = workload(args.workload)
     if args.n:
         w['n'] = args.n
-    if args.inner_trace_rtol:
-        w['inner_trace_rtol'] = args.inner_trace_rtol
-    if args.inner_stepI_rtol:
-        w['inner_stepI_rtol'] = args.inner_stepI_rtol
-    if args.inner_trace_vcycles is not None:
-        w['inner_trace_vcycles'] = args.inner_trace_vcycles
-    if args.inner_trace_fp32 is not None:
-        w['inner_trace_fp32'] = args.inner_trace_fp32
-    if args.trace_fp32_vcycle is not None:
-        w['trace_fp32_vcycle'] = args.trace_fp32_vcycle
-    if args.inner_gs is not None:
-        w['inner_gs'] = args.inner_gs
+    kw = solver_settings(args, w)
     stream = torch.cuda.Stream(device=dev)
+    stages = STAGES[w['tableau']]
+    gamma = 0.43586652150845899942                   # ARS(3,4,3) diagonal
+    c_stage = gamma * w['dt']
+    peak, peak_kind = measured_peaks()
     with torch.cuda.stream(stream):
-        ctx = H.Context(w['n'], w['k'], periodic_x=w['periodic_x'], stream=stream, tableau=w['tableau'],
-                        dt=w['dt'], n_richardson=w['n_richardson'], richardson_rtol=w['stage_rtol'],
-                        richardson_max=600, stage_krylov=1, inner_stepI_rtol=w['inner_stepI_rtol'],
-                        inner_trace_rtol=w['inner_trace_rtol'], trace_rtol=w['trace_rtol'],
-                        stepI_rtol=w['stepI_rtol'], device_loops=0 if args.host_loops else 1,
-                        inner_trace_vcycles=w['inner_trace_vcycles'], inner_trace_fp32=w['inner_trace_fp32'],
-                        trace_fp32_vcycle=w['trace_fp32_vcycle'], inner_gs=w['inner_gs'])
-        Q0 = torch.from_numpy(initial_velocity(w, seed_offset=rank)).to(dev)
-        ctx.hdg_set_state(Q0)
-        ctx.hdg_div_free_project()
+        flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)   # > L2 (129 MB)
+        ctx = make_context(H, w, args.precision, stream, kw, seed_offset=rank)
         if args.kernel_only is not None:
             ctx.hdg_imex_step(1)
-            gamma = 0.43586652150845899942
-            ms_k, b_k = ctx.hdg_time_kernel(args.kernel_only, gamma * w['dt'], args.steps)
+            ms_k, b_k = ctx.hdg_time_kernel(args.kernel_only, c_stage, args.steps)
             print(json.dumps({'kernel': args.kernel_only, 'ms_per_launch': ms_k, 'bytes': b_k}), flush=True)
             ctx.close()
             return
-        flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)   # > L2 (129 MB)
-        stats_all = []
-        for _ in range(args.warmup):
-            ctx.hdg_imex_step(1)
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        with ClockSampler(local_rank) as clk:
-            for i in range(args.steps):
-                flush.fill_(float(i))                      # evict the previous step's working set
-                torch.cuda.nvtx.range_push('bench_step')
-                ev[i][0].record(stream)
-                st = ctx.hdg_imex_step(1)
-                ev[i][1].record(stream)
-                torch.cuda.nvtx.range_pop()
-                stats_all.append(st)
-            torch.cuda.synchronize()
-            if world > 1:
-                torch.distributed.barrier()
-        ms = [a.elapsed_time(b) for a, b in ev]
-        # kernels timed alone on the same operators and stream (roofline and two diagnostics)
-        gamma = 0.43586652150845899942                   # ARS(3,4,3) diagonal
-        c_stage = gamma * w['dt']
+        clk = ClockSampler(local_rank)
+        ms, stats_all = timed_steps(ctx, stream, args.steps, args.warmup, flush, world, clk)
+        # kernels timed alone on the same operators and stream (roofline and diagnostics)
         k_ms, k_bytes = ctx.hdg_time_kernel(0, c_stage, 50)
         s_ms, s_bytes = ctx.hdg_time_kernel(1, 1.0, 20)
-        a_ms, a_bytes = ctx.hdg_time_kernel(6, c_stage, 50)
-        p_ms, p_bytes = ctx.hdg_time_kernel(9, c_stage, 50)
         st_ms, st_bytes = ctx.hdg_time_kernel(8, c_stage, 20)
-        # end to end through the C-ABI with host buffers
-        Qh, ph, lh, _ = ctx.hdg_get_state()
-        Qh, ph, lh = Qh.cpu().pin_memory(), ph.cpu().pin_memory(), lh.cpu().pin_memory()
-        Qd, pd, ld = torch.empty_like(Qh, device=dev), torch.empty_like(ph, device=dev), torch.empty_like(lh, device=dev)
-        e2e_ms = []
-        tsim = w['dt'] * (args.warmup + args.steps)
-        for i in range(args.e2e_steps):
-            flush.fill_(float(i))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            Qd.copy_(Qh, non_blocking=True); pd.copy_(ph, non_blocking=True); ld.copy_(lh, non_blocking=True)
-            ctx.hdg_set_state(Qd, pd, ld, tsim)
-            ctx.hdg_imex_step(1)
-            Qo, po, lo, tsim = ctx.hdg_get_state()
-            Qh.copy_(Qo); ph.copy_(po); lh.copy_(lo)
-            torch.cuda.synchronize()
-            e2e_ms.append(1e3 * (time.perf_counter() - t0))
-        h2d = (Qh.numel() + ph.numel() + lh.numel()) * 8
+        a_ms = p_ms = a_bytes = p_bytes = None
+        if args.precision == 'MIXED':
+            a_ms, a_bytes = ctx.hdg_time_kernel(6, c_stage, 50)
+            p_ms, p_bytes = ctx.hdg_time_kernel(9, c_stage, 50)
+        e2e_ms, h2d = e2e_steps(ctx, args.e2e_steps, flush, dev)
+        nsteps_done = args.warmup + args.steps + args.e2e_steps
+        final = state_host(ctx)
+        ntrace, nQ, nP = ctx.nL, ctx.nQ, ctx.nP
         ctx.close()
+        # the same steps with every kernel in FP64 (the plain FP64 GPU form), and the two compared
+        other = None
+        if not args.no_compare:
+            oprec = 'FP64' if args.precision == 'MIXED' else 'MIXED'
+            ctx2 = make_context(H, w, oprec, stream, kw, seed_offset=rank)
+            ms2, st2 = timed_steps(ctx2, stream, args.compare_steps, args.warmup, flush, world)
+            for _ in range(nsteps_done - args.warmup - args.compare_steps):
+                ctx2.hdg_imex_step(1)
+            fin2 = state_host(ctx2)
+            ctx2.close()
+            other = {'precision': oprec, 'value': world * stages * len(ms2) / (sum(ms2) / 1e3),
+                     'ms_per_step': float(np.mean(ms2)), 'steps': len(ms2),
+                     'stage_outer_iters': sum(s['richardson_iters'] for s in st2) / len(st2),
+                     'diff_after_steps': nsteps_done,
+                     'rel_l2_diff': {'Q': rel_err(final[0], fin2[0]), 'p': rel_err(final[1], fin2[1]),
+                                     'lambda': rel_err(final[2], fin2[2])}}
+        gold = golden_error(H, w, stream, kw) if (rank == 0 and args.workload == 'c2' and not args.n) else None
 
-    stages = STAGES[w['tableau']]
     ms_step = float(np.mean(ms))
-    total_ms, e2e_mean = aggregate_ranks(sum(ms), float(np.mean(e2e_ms)) if e2e_ms else float('nan'), world, dev)
+    total_ms, e2e_mean = aggregate_ranks(sum(ms), e2e_ms, world, dev)
     value = job_rate(world, stages, args.steps, total_ms)
-    ntrace = ctx.nL
     trace_solves = sum(s['trace_solves'] for s in stats_all)
     trace_iters = sum(s['trace_iters'] for s in stats_all)
     stepI_iters = sum(s['stepI_iters'] for s in stats_all)
-    peak, peak_kind = measured_peaks()
-    # FP64 velocity-block apply: FMAs per cell = dense diagonal block + neighbour evaluation +
-    # flux + test (interior edges; k = w['k'])
-    mu = (w['k'] + 2) * (w['k'] + 3) // 2
-    nu, nfq = 2 * mu, (3 * w['k'] + 5) // 2
-    npk, nt = (w['k'] + 1) * (w['k'] + 2) // 2, w['k'] + 1
-    ncells = ctx.nQ // nu
-    s_flop = 2.0 * (nu * nu + 3 * nfq * 2 * mu + 3 * nfq * 8 + nu * 3 * nfq) * ncells
-    # the fused stage operator: the velocity block above + the trace and pressure coupling of the
-    # velocity rows + the cell's constraint rows (pressure rows, trace rows)
-    st_flop = s_flop + ncells * (nu * (3 * (2 * nt + 3) + 2 * (2 * npk + 2) + 3) + 6 * mu +
-                                 npk * (4 * mu + 3 * (2 * npk + 2) + 3 * (2 * nt + 2) + 5) +
-                                 3 * nt * (5 * mu + 2 * npk + 5))
+    ncells = 2 * w['n'] * w['n']
+    st_flop, s_flop = stage_flops(w['k'], ncells)
     st_tflops = st_flop / (st_ms * 1e-3) / 1e12
+    host_loops = bool(args.host_loops)
+    per_step = {'trace_solves': trace_solves / args.steps, 'trace_cg_iters': trace_iters / args.steps,
+                'stage_outer_iters': sum(s['richardson_iters'] for s in stats_all) / args.steps,
+                'gmres_iters': stepI_iters / args.steps}
+    for key, name in (('ms_trace_solves', 'ms_trace'), ('ms_stepI_solves', 'ms_stepI'), ('ms_assembly', 'ms_assembly'),
+                      ('ms_bdm', 'ms_bdm')):      # per-component device times exist only with host-driven loops
+        per_step[key] = sum(s[name] for s in stats_all) / args.steps if host_loops else None
+    cfg = {'workload': w['name'], 'n': w['n'], 'k': w['k'], 'periodic_x': w['periodic_x'], 'trace_dofs': ntrace,
+           'dg_dofs': nQ + nP, 'precision': args.precision,
+           'inner_rtol': [kw['inner_stepI_rtol'], kw['inner_trace_rtol']],
+           'l2': 'flushed (256 MB write) between timed steps', 'parallelism': f'replicas x{world}',
+           'loops': 'host' if host_loops else 'device (one CUDA graph per IMEX step)'}
+    if gold is not None:
+        cfg['error_vs_oracle'] = gold
+    if w['init'] == 'taylor_green':                   # the exact solution exp(-kappa t) Q0 is known
+        import hdg_workloads as W
+        T = final[3]
+        Qex = np.exp(-w['kappa'] * T) * W.nodal_velocity(w['n'], w['k'], W.taylor_green)
+        pex = np.exp(-2 * w['kappa'] * T) * W.nodal_scalar(w['n'], w['k'], W.taylor_green_pressure)
+        cfg['error_vs_exact'] = {'t': T, 'Q': rel_err(final[0], Qex), 'p': rel_err(final[1], pex)}
     line = {
         'metric': METRIC, 'value': value, 'unit': 'stage_solves/s', 'n_gpus': world, 'steps': args.steps,
         'warmup': args.warmup, 'ms_per_step': ms_step, 'higher_is_better': True, 'scaling': 'weak',
-        'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic (seeded shear layer + noise)',
-        'config': {'workload': 'shear-layer channel 64x64, k=3, ARS(3,4,3), dt=2e-3, stages to 1e-10', 'n': w['n'],
-                   'k': w['k'], 'periodic_x': True, 'trace_dofs': ntrace, 'dg_dofs': ctx.nQ + ctx.nP,
-                   'inner_rtol': [w['inner_stepI_rtol'], w['inner_trace_rtol']],
-                   'inner_step2': f"{w['inner_trace_vcycles']} V-cycle(s), {'FP32' if w['inner_trace_fp32'] else 'FP64'}",
-                   'l2': 'flushed (256 MB write) between timed steps', 'parallelism': f'replicas x{world}'},
+        'vs_baseline': None, 'dtype': 'f64',
+        'data': 'synthetic (seeded shear layer + noise)' if w['init'] == 'shear_layer' else 'synthetic (analytic, forced)',
+        'config': cfg,
         'trace_dof_per_s': world * ntrace * trace_solves / (total_ms / 1e3),
-        'per_step': {'ms_trace_solves': sum(s['ms_trace'] for s in stats_all) / args.steps,
-                     'ms_stepI_solves': sum(s['ms_stepI'] for s in stats_all) / args.steps,
-                     'ms_assembly': sum(s['ms_assembly'] for s in stats_all) / args.steps,
-                     'ms_bdm': sum(s['ms_bdm'] for s in stats_all) / args.steps,
-                     'trace_solves': trace_solves / args.steps, 'trace_cg_iters': trace_iters / args.steps,
-                     'stage_outer_iters': sum(s['richardson_iters'] for s in stats_all) / args.steps,
-                     'gmres_iters': stepI_iters / args.steps},
+        'per_step': per_step,
         'e2e': {'value': world * stages / (e2e_mean / 1e3), 'unit': 'stage_solves/s', 'h2d_bytes_per_step': h2d,
                 'd2h_bytes_per_step': h2d},
-        'roofline': {'kernel': 'k_stage_apply<3> (fused FP64 stage operator, the flexible GMRES product)',
+        'roofline': {'kernel': f"k_stage_apply<{w['k']}> (fused FP64 stage operator, the flexible GMRES product)",
                      'bound': 'alu', 'achieved': st_tflops, 'peak': FP64_NOMINAL_TFLOPS, 'unit': 'TFLOP/s',
                      'frac': st_tflops / FP64_NOMINAL_TFLOPS,
                      'peak_kind': 'nominal FP64 vector rate (no measured FP64 peak exists for this pool)',
-                     'traffic': profile_traffic('k_stage_apply_fp64_c2.md'), 'ms_per_launch': st_ms,
-                     'algorithmic_flop': st_flop, 'algorithmic_bytes': st_bytes,
+                     'traffic': profile_traffic('k_stage_apply_fp64_c2.md') if args.workload == 'c2' else None,
+                     'ms_per_launch': st_ms, 'algorithmic_flop': st_flop, 'algorithmic_bytes': st_bytes,
                      'achieved_gbs': st_bytes / (st_ms * 1e-3) / 1e9},
-        'inner_stepI_fp32': {
-            'apply': {'kernel': 'k_gm_apply_mf<3, float, 1> (Arnoldi product, step j = 4)', 'ms_per_launch': a_ms,
-                      'bytes': a_bytes, 'achieved_gbs': a_bytes / (a_ms * 1e-3) / 1e9,
-                      'frac_of_hbm': a_bytes / (a_ms * 1e-3) / 1e9 / peak,
-                      'traffic': profile_traffic('k_gm_apply_mf_fp32_c2.md')},
-            'precond': {'kernel': 'k_gm_precond_mf<3, float, 1> (block inverse pass, step j = 4)',
-                        'ms_per_launch': p_ms, 'bytes': p_bytes, 'achieved_gbs': p_bytes / (p_ms * 1e-3) / 1e9,
-                        'frac_of_hbm': p_bytes / (p_ms * 1e-3) / 1e9 / peak, 'hbm_peak_kind': peak_kind}},
         'trace_apply': {'kernel': 'k_cg_apply', 'achieved_gbs': k_bytes / (k_ms * 1e-3) / 1e9, 'ms_per_launch': k_ms,
-                        'bytes': k_bytes},
+                        'bytes': k_bytes, 'frac_of_hbm': k_bytes / (k_ms * 1e-3) / 1e9 / peak, 'hbm_peak_kind': peak_kind},
         'stage_apply_fp64': {'kernel': 'k_cell_apply_mf', 'achieved_gbs': s_bytes / (s_ms * 1e-3) / 1e9,
                              'achieved_tflops': s_flop / (s_ms * 1e-3) / 1e12, 'fp64_nominal_tflops': 1.25,
                              'ms_per_launch': s_ms, 'bytes': s_bytes, 'flop': s_flop},
         'clocks': clk.summary(),
         'gpu_launches': None,
     }
+    if a_ms is not None:
+        line['inner_stepI_fp32'] = {
+            'note': 'timed back to back on the same vectors: warm in L2 where they fit (129 MB)',
+            'apply': {'kernel': f"k_gm_apply_mf<{w['k']}, float, 1> (Arnoldi product, step j = 4)", 'ms_per_launch': a_ms,
+                      'bytes': a_bytes, 'achieved_gbs': a_bytes / (a_ms * 1e-3) / 1e9,
+                      'frac_of_hbm_l2_warm': a_bytes / (a_ms * 1e-3) / 1e9 / peak},
+            'precond': {'kernel': f"k_gm_precond_mf<{w['k']}, float, 1> (block inverse pass, step j = 4)",
+                        'ms_per_launch': p_ms, 'bytes': p_bytes, 'achieved_gbs': p_bytes / (p_ms * 1e-3) / 1e9,
+                        'frac_of_hbm_l2_warm': p_bytes / (p_ms * 1e-3) / 1e9 / peak, 'hbm_peak_kind': peak_kind}}
+    if other is not None:
+        line['compare_precision'] = other
     # kernels launched inside the timed steps: counted exactly by the library (graph kernel nodes
     # plus every pass of the device-side loops); with host-driven loops it is not counted (None)
     launches = sum(s['graph_kernels'] for s in stats_all)
     line['gpu_launches'] = int(launches) if launches > 0 else None
-    line['config']['loops'] = 'host' if args.host_loops else 'device (one CUDA graph per IMEX step)'
-    if rank == 0 and not args.no_cpu_baseline:
-        r, s, desc, cores = oracle_sample(w, steps=1)
+    if rank == 0 and not args.no_cpu_baseline and args.workload == 'c2':
+        r, s_, desc, cores = oracle_sample(w)
         line['cpu_baseline'] = {'value': r, 'unit': 'stage_solves/s', 'cores': cores, 'kind': 'oracle', 'sample': desc}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -359,6 +470,11 @@ def main():
     ap.add_argument('--impl', default='gpu', choices=['gpu', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--e2e-steps', type=int, default=3)
+    ap.add_argument('--workload', default='c2', choices=['c2', 'c3'],
+                    help='c2: the shear channel (default); c3: forced Taylor-Green 256x256, k=4')
+    ap.add_argument('--precision', default='MIXED', choices=['MIXED', 'FP64'])
+    ap.add_argument('--no-compare', action='store_true', help='skip the run in the other precision')
+    ap.add_argument('--compare-steps', type=int, default=3, help='timed steps of the other precision')
     ap.add_argument('--n', type=int, default=None, help='mesh size override (profiling runs only)')
     ap.add_argument('--inner-trace-rtol', type=float, default=None, help='tuning: inner Step II tolerance')
     ap.add_argument('--inner-stepI-rtol', type=float, default=None, help='tuning: inner Step I tolerance')

@@ -51,10 +51,13 @@ typedef enum {
     HDG_ERR_OOM = 3,           /* device allocation failed                                  */
     HDG_ERR_NOT_CONVERGED = 4, /* an iteration hit its cap; best iterate kept               */
     HDG_ERR_NUMERIC = 5,       /* NaN / Inf in a residual norm                              */
-    HDG_ERR_UNSUPPORTED = 6    /* valid request this build does not handle                  */
+    HDG_ERR_UNSUPPORTED = 6,   /* valid request this build does not handle                  */
+    HDG_ERR_TIMEOUT = 7        /* hdg_params.timeout_ms ran out before the GPU work finished */
 } hdg_status;
 
 typedef enum { HDG_ARS222 = 0, HDG_ARS343 = 1, HDG_IMEX_EULER = 2 } hdg_tableau;
+
+typedef enum { HDG_FP64 = 0, HDG_MIXED = 1 } hdg_precision;
 
 /* Mesh (Sec. 3.2): n x n rectangles over [0,Lx]x[0,Ly]; walls (n.Q = 0, weakly) on every
  * non-periodic side. */
@@ -105,17 +108,20 @@ typedef struct {
      * = exactly n V-cycles of the trace multigrid (a fixed linear preconditioner; the flexible
      * outer iteration decides the accuracy); 0 = trace CG to inner_trace_rtol. */
     int inner_trace_vcycles;
-    /* Inner (FP32) Step-I solves: 0 (default) = a sequence of kernels per Arnoldi step (launched
-     * with programmatic dependent launch); 1 = one persistent cooperative kernel per solve with
-     * bounded grid-wide barriers (same algorithm; slower on GB300 on a 64 x 64, k = 3 mesh: the barriers
-     * cost more than the kernel boundaries they replace). */
-    int persistent_stepI;
+    /* Arithmetic of the stage preconditioner (stage_krylov = 1; hdg_precision). HDG_MIXED
+     * (default): the inner Step-I GMRES, the preconditioner's Step-II cell maps and V-cycle, the
+     * tight trace CG's V-cycle and the first orthogonalisation pass of the stage FGMRES run in FP32;
+     * the stage residual, its Krylov basis, the trace operator and the CG's iterates stay FP64, so
+     * the result meets the same FP64 stage tolerance. HDG_FP64: every kernel of the path computes
+     * in FP64 (inner Step I by FP64 GMRES with block Jacobi; inner_trace_fp32 and
+     * trace_fp32_vcycle are forced to 0). */
+    int precision;
     /* The one-V-cycle Step II inside the stage preconditioner (inner_trace_vcycles = 1): 1
-     * (default) = the V-cycle in FP32 (operators rounded once per stage coefficient; the P1
-     * levels in one thread block), used when the P1 hierarchy fits that block's shared memory
-     * (5 floats per vertex of the mesh, 12 per vertex of the coarser levels, <= 200 KiB in all:
-     * meshes up to 64 x 64 cells); 0 = the FP64 V-cycle. The outer iteration's tolerance
-     * is unchanged: this only alters the preconditioner. */
+     * (default) = the V-cycle in FP32 (operators rounded once per stage coefficient; the large P1
+     * levels as grid-wide kernels, the small ones — from the first level with at most 5000
+     * vertices whose sub-hierarchy fits 200 KiB of shared memory — in one thread block);
+     * 0 = the FP64 V-cycle. The outer iteration's tolerance is unchanged: this only alters the
+     * preconditioner. */
     int inner_trace_fp32;
     /* Trace CG with the multigrid (tight solves: final update, pressure reconstruction, mixed
      * solves): 1 (default) = preconditioned by the same V-cycle in FP32 (when the hierarchy fits
@@ -129,6 +135,14 @@ typedef struct {
      * two-coloured by index parity; checked at setup, else block Jacobi): about half the Arnoldi
      * steps for one more kernel per step; 0 = block Jacobi. */
     int inner_gs;
+    /* > 0: bound, in milliseconds counted from the step's launch, on the host's wait for the GPU
+     * work of each step of hdg_imex_step when the step runs as one CUDA graph (device_loops = 1,
+     * stage_krylov = 1). When it runs out the call returns HDG_ERR_TIMEOUT at
+     * once; the step stays queued on the context's stream and completes there (nothing is
+     * cancelled), and the next call on the context waits for it without a limit and then advances
+     * the context's time. Set-up work before a context's first step graph (condensations, graph
+     * capture) is not bounded. 0 (default): no limit. */
+    double timeout_ms;
 } hdg_params;
 
 typedef struct {
@@ -150,7 +164,7 @@ typedef struct {
     double ms_bdm;
     /* kernels run by the call's CUDA graphs (device_loops = 1): the graphs' kernel nodes plus
      * every pass of their device-side loops, counted exactly on the device; in that mode an IMEX
-     * step (stage_krylov = 1, no forcing callback) is one graph, so this counts all of its kernels */
+     * step (stage_krylov = 1) is one graph, so this counts all of its kernels */
     long long graph_kernels;
 } hdg_stats;
 
@@ -186,9 +200,23 @@ hdg_status hdg_dof_sizes(const hdg_ctx *ctx, int64_t *nQ, int64_t *np, int64_t *
 hdg_status hdg_set_state(hdg_ctx *ctx, const double *Q, const double *p, const double *lam, double t);
 hdg_status hdg_get_state(hdg_ctx *ctx, double *Q, double *p, double *lam, double *t_host);
 
+/* L2 projection of sampled data onto a cell space (Sec. 2.2: the initial velocity and the forcing
+ * enter the method as elements of V_Q; non-polynomial data is projected with a fixed rule).
+ * values_at_qp (device) samples the data at the library's volume quadrature points, whose
+ * reference coordinates (xi, eta) hdg_reference_rule(k, 0, ...) returns: the point of a cell is
+ * v0 + xi (v1 - v0) + eta (v2 - v0) (vertex order of the exchange format). The rule integrates
+ * polynomials of degree 2 floor((3k+4)/2) - 1 exactly, so data of degree up to that minus the
+ * space's degree is projected exactly (it reproduces every polynomial of the space).
+ *   field 0: values_at_qp double[ncells][2][nq] (x and y components) -> dofs = Q (nodal, device)
+ *   field 1: values_at_qp double[ncells][nq]                          -> dofs = p (nodal, device)
+ * The projection is cell-local: dofs_K = argmin over the space of ||u - f||_{L2(K)} with the
+ * integral replaced by the rule. HDG_ERR_INVALID_ARG for another field or a NULL pointer. */
+hdg_status hdg_project(hdg_ctx *ctx, int field, const double *values_at_qp, double *dofs);
+
 /* Forcing f(x, t) = phi(t) F(x) with F a velocity field (nodal, device): f^ex(w, t) =
- * (w . f(t)) (eq. f_expl). phi is called on the host; NULL phi means phi = 1. F = NULL
- * removes the forcing. */
+ * (w . f(t)) (eq. f_expl). phi is called on the host, once per stage time of each step (for a
+ * step recorded as a CUDA graph, before the graph's launch: the graph reads the values from device
+ * memory); NULL phi means phi = 1. F = NULL removes the forcing. */
 hdg_status hdg_set_forcing(hdg_ctx *ctx, const double *F, double (*phi)(double t, void *user), void *user);
 
 /* Alg. 1 x nsteps: s-1 stage solves (Alg. 2), final update (eq. final_update) and pressure
@@ -254,23 +282,25 @@ hdg_status hdg_time_kernel(hdg_ctx *ctx, int which, double c, int reps, double *
                            double *bytes_per_launch);
 
 /* The trace-operator apply of hdg_trace_apply (same operator, same output) without any device
- * allocation. The paper has no counterpart: this entry point exists for callers that cannot call
- * cudaMalloc while they run, such as code recording a CUDA graph under global stream capture (where
- * allocation calls are refused) or hosts whose device memory is owned by another allocator.
- * hdg_trace_apply may allocate: it caches the condensed operator of every new coefficient c. This
- * variant condenses the cells again on every call and keeps its intermediate vectors in one static
- * device array of 2^20 doubles (8 MiB) inside the library, which every GPU that loads the library
- * holds until the process exits.
+ * allocation. The paper has no counterpart. It serves callers that must not call cudaMalloc once
+ * they run: hosts that hand all device memory to their own pool allocator at start-up (a library
+ * allocation would then fail or break the pool's accounting), and time-critical loops for which
+ * cudaMalloc is off limits because it may synchronise the whole device. hdg_trace_apply may
+ * allocate: it caches the condensed operator of every new coefficient c. This variant condenses
+ * the cells again on every call and keeps its intermediate vectors in one static device array of
+ * 2^20 doubles (8 MiB) inside the library, which every GPU that loads the library holds until the
+ * process exits.
  *   Limit: 3 * nlambda + ncells * 3(k+1) <= 2^20 doubles (e.g. 64 x 64 meshes with k <= 4,
  *   128 x 128 with k <= 3); larger meshes return HDG_ERR_INVALID_ARG with the sizes in
  *   hdg_last_error().
- *   The first call on each device looks up the array's device address (cudaGetSymbolAddress) with
- *   that device current; make that first call before any stream capture begins.
+ *   The context's device must be the current device (else HDG_ERR_INVALID_ARG). The first call on
+ *   each device looks up the array's device address (cudaGetSymbolAddress, once per device, under a
+ *   lock); make that first call before any stream capture begins.
  *   Every call on a device shares the array, which keeps the last call's contents (nothing in it
  *   needs to start at zero: every element a call reads it has written first). Calls whose work
  *   overlaps on the GPU (other streams, other contexts, other host threads) race on the array and
- *   must be ordered by the caller. The context's own buffers are not touched. Synchronises the
- *   context's stream before returning. */
+ *   must be ordered by the caller. The context's own buffers are not touched. lam and out hold
+ *   nlambda doubles each (device). Synchronises the context's stream before returning. */
 hdg_status hdg_trace_apply_noalloc(hdg_ctx *ctx, double c, const double *lam, double *out);
 
 #ifdef __cplusplus

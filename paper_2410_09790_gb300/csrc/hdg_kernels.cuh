@@ -122,6 +122,23 @@ __global__ void k_basis_change(const double *__restrict__ T, int n, const double
     }
 }
 
+// L2 projection of samples at the volume points onto the orthonormal cell basis: with
+// int_T phi_a phi_b = delta_ab and M_K = detJ I, the coefficient of phi_a is
+// (1/detJ) int_K f phi_a = sum_q w_q phi_a(xi_q) f(x_q). One thread per (vector v, basis a);
+// vals: [v][nq] (v = cell, or cell * 2 + component), out: [v][n] modal.
+__global__ void k_project_qp(const double *__restrict__ qw, const double *__restrict__ phi, int nq, int mu, int n,
+                             const double *__restrict__ vals, double *__restrict__ out, long long nvec) {
+    wait_prior_kernel();
+    GRID_STRIDE(i, nvec * n) {
+        const long long v = i / n;
+        const int a = (int)(i % n);
+        const double *f = vals + v * nq;
+        double s = 0;
+        for (int q = 0; q < nq; ++q) s += __ldg(&qw[q]) * __ldg(&phi[q * mu + a]) * f[q];
+        out[i] = s;
+    }
+}
+
 // dual <-> Riesz on V_Q: M = detJ I per cell. mode 0: out = detJ * in; mode 1: out = in / detJ.
 __global__ void k_mass_scale(const CellGeo *__restrict__ geo, int nu, const double *in, double *out,
                              long long ncells, int mode) {
@@ -151,9 +168,12 @@ struct LinComb {
     double coef[12];
     const double *vec[12];
     int mass[12];
+    int fterm;              // >= 0: the coefficient of term fterm is also multiplied by *fscale
+    const double *fscale;   // (device; the time factor of a forcing, refreshed between graph launches)
 };
 __global__ void k_lincomb(const CellGeo *__restrict__ geo, int nu, LinComb L, double *out, long long ncells) {
     wait_prior_kernel();
+    if (L.fterm >= 0) L.coef[L.fterm] *= *L.fscale;
     GRID_STRIDE(i, ncells * nu) {
         double dj = geo[i / nu].detJ;
         double s = 0;
@@ -1510,14 +1530,15 @@ __global__ void k_vec_normalize(const double *__restrict__ w0, const double *__r
     }
 }
 
-// hcol = V32^T w32 over V_0..V_j in FP32 (FP32 shadows of the FGMRES basis and of w): the first
+// hcol = V^T w over V_0..V_j; T = float: in FP32 (FP32 shadows of the FGMRES basis and of w): the first
 // classical Gram-Schmidt pass of the stage FGMRES. Its error (1e-7 of |w|) is removed by the FP64
 // second pass, and H uses the same hcol as the update, so the Arnoldi relation stays FP64.
-__global__ void k_vec_dot32(const float *__restrict__ w32, const float *__restrict__ V32, long long n, RedBuf rb,
-                            GmresState *gs) {
+// (T = double: the same pass in FP64, for the all-FP64 precision mode.)
+template <class T>
+__global__ void k_vec_dot(const T *__restrict__ w, const T *__restrict__ V, long long n, RedBuf rb, GmresState *gs) {
     wait_prior_kernel();
     if (gs->cycle_end) return;
-    multidot_rows(rb, V32, w32, n, gs->j + 1, gs->hcol, false);
+    multidot_rows(rb, V, w, n, gs->j + 1, gs->hcol, false);
 }
 
 // Second classical Gram-Schmidt pass of the stage FGMRES, first half: w' = w - V hcol; h2 =

@@ -122,10 +122,11 @@ __host__ __device__ inline void p1_galerkin_row(int V, const P1Grid &Gc, const P
     }
 }
 
-// y(v) = sum_o A(v, o) x(nb)
-__host__ __device__ __forceinline__ double p1_apply(int v, const P1Grid &G, const double *A, const double *x) {
+// y(v) = sum_o A(v, o) x(nb)   (T = double, or float for the FP32 V-cycle)
+template <class T>
+__host__ __device__ __forceinline__ T p1_apply(int v, const P1Grid &G, const T *A, const T *x) {
     int i = v % G.nvx, j = v / G.nvx;
-    double s = 0;
+    T s = 0;
     for (int o = 0; o < P1_NS; ++o) {
         int w = p1_vid(G, i + p1_di(o), j + p1_dj(o));
         if (w >= 0) s += A[P1_NS * v + o] * x[w];
@@ -148,24 +149,26 @@ __host__ __device__ __forceinline__ double restrict_trace(int v, const double *r
 }
 
 // (I^T r)(V): restriction between P1 levels
-__host__ __device__ __forceinline__ double restrict_p1(int V, const P1Grid &Gc, const P1Grid &Gf, const double *rf) {
+template <class T>
+__host__ __device__ __forceinline__ T restrict_p1(int V, const P1Grid &Gc, const P1Grid &Gf, const T *rf) {
     const int I = V % Gc.nvx, J = V / Gc.nvx;
-    double s = 0;
+    T s = 0;
     for (int sa = 0; sa < P1_NS; ++sa) {
         int a = p1_vid(Gf, 2 * I + p1_di(sa), 2 * J + p1_dj(sa));
-        if (a >= 0) s += (sa == 0 ? 1.0 : 0.5) * rf[a];
+        if (a >= 0) s += (sa == 0 ? T(1) : T(0.5)) * rf[a];
     }
     return s;
 }
 
 // (I e)(a): linear interpolation from the coarse P1 grid to fine vertex a
-__host__ __device__ __forceinline__ double prolong_p1(int a, const P1Grid &Gf, const P1Grid &Gc, const double *ec) {
+template <class T>
+__host__ __device__ __forceinline__ T prolong_p1(int a, const P1Grid &Gf, const P1Grid &Gc, const T *ec) {
     int i = a % Gf.nvx, j = a / Gf.nvx;
     int i0 = i >> 1, j0 = j >> 1;
     bool oi = i & 1, oj = j & 1;
-    double v0 = ec[p1_vid(Gc, i0, j0)];
+    T v0 = ec[p1_vid(Gc, i0, j0)];
     if (!oi && !oj) return v0;
-    return 0.5 * (v0 + ec[p1_vid(Gc, i0 + (oi ? 1 : 0), j0 + (oj ? 1 : 0))]);
+    return T(0.5) * (v0 + ec[p1_vid(Gc, i0 + (oi ? 1 : 0), j0 + (oj ? 1 : 0))]);
 }
 
 }  // namespace hdg

@@ -404,6 +404,53 @@ __global__ void __launch_bounds__(1024) k_tv_tail(Tail32 T) {
     }
 }
 
+// ---------------------------------------------------------------- large P1 levels, grid-wide
+// The P1 levels with more vertices than the one-block tail takes run as grid-wide FP32 kernels,
+// a thread per vertex, with the same smoothing as the tail: down, two Chebyshev steps from 0 and
+// the restriction of the residual; up, the prolongation and two Chebyshev steps.
+// x = d = invth D^{-1} b
+__global__ void k_p32_cheb0(const float *__restrict__ dinv, const float *__restrict__ b, float *x, float *d,
+                            float invth, int n) {
+    wait_prior_kernel();
+    GRID_STRIDE(v, n) {
+        const float s = invth * __ldg(&dinv[v]) * __ldcg(&b[v]);
+        d[v] = s;
+        x[v] = s;
+    }
+}
+
+// d = c1 d + c2 D^{-1} (b - A xin); xout = xin + d
+__global__ void k_p32_cheb(P1Grid G, const float *__restrict__ A, const float *__restrict__ dinv,
+                           const float *__restrict__ b, const float *__restrict__ xin, float *__restrict__ xout,
+                           float *d, float c1, float c2) {
+    wait_prior_kernel();
+    GRID_STRIDE(v, G.nverts) {
+        const float r = __ldcg(&b[v]) - p1_apply<float>((int)v, G, A, xin);
+        const float dn = (c1 != 0.f ? c1 * d[v] : 0.f) + c2 * __ldg(&dinv[v]) * r;
+        d[v] = dn;
+        xout[v] = xin[v] + dn;
+    }
+}
+
+// t = b - A x
+__global__ void k_p32_resid(P1Grid G, const float *__restrict__ A, const float *__restrict__ b,
+                            const float *__restrict__ x, float *t) {
+    wait_prior_kernel();
+    GRID_STRIDE(v, G.nverts) t[v] = __ldcg(&b[v]) - p1_apply<float>((int)v, G, A, x);
+}
+
+// b_coarse = I^T t_fine
+__global__ void k_p32_restrict(P1Grid Gc, P1Grid Gf, const float *__restrict__ tf, float *bc) {
+    wait_prior_kernel();
+    GRID_STRIDE(V, Gc.nverts) bc[V] = restrict_p1<float>((int)V, Gc, Gf, tf);
+}
+
+// x_fine += I e_coarse
+__global__ void k_p32_prolong(P1Grid Gf, P1Grid Gc, const float *__restrict__ ec, float *x) {
+    wait_prior_kernel();
+    GRID_STRIDE(a, Gf.nverts) x[a] += prolong_p1<float>((int)a, Gf, Gc, ec);
+}
+
 // ---------------------------------------------------------------- flexible CG with the FP32 V-cycle
 // x += alpha p; r -= alpha Ap (the preconditioner follows as separate kernels)
 template <int NT>

@@ -11,6 +11,9 @@
 #include <cstring>
 #include <deque>
 #include <exception>
+#include <mutex>
+#include <chrono>
+#include <thread>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -22,7 +25,6 @@
 #include "hdg_mg_kernels.cuh"
 #include "hdg_mg32.cuh"
 #include "hdg_gs32.cuh"
-#include "hdg_stepI_persistent.cuh"
 #include "mesh.h"
 #include "refelem.h"
 
@@ -36,6 +38,9 @@ struct CudaError : std::runtime_error {
 };
 struct OomError : std::runtime_error {
     explicit OomError(const std::string &s) : std::runtime_error(s) {}
+};
+struct TimeoutError : std::runtime_error {
+    explicit TimeoutError(const std::string &s) : std::runtime_error(s) {}
 };
 
 #define CK(x)                                                                                  \
@@ -114,10 +119,14 @@ struct CondCache {
     float *Sell32 = nullptr, *Dinv32 = nullptr, *Minv32 = nullptr;
     std::vector<float *> A32, dinv32;
     size_t tail32_smem = 0;
+    int first32 = 0;                          // P1 levels >= first32 run in the one-block tail
 };
 
 struct MGWork {                // per-level work vectors (shared by all coefficients)
     double *b = nullptr, *xa = nullptr, *xb = nullptr, *d = nullptr, *t = nullptr;
+};
+struct MGWork32 {              // the same for the FP32 V-cycle
+    float *b = nullptr, *xa = nullptr, *xb = nullptr, *d = nullptr, *t = nullptr;
 };
 
 void cheb_coefs(double lmax, double &invth, double &c1, double &c2) {
@@ -134,6 +143,7 @@ struct hdg_ctx {
     hdg_params P{};
     hdg_mesh_desc D{};
     cudaStream_t st = nullptr;
+    int device = 0;                                          // CUDA device current at setup
     RefTables T;
     HostMesh H;
     int K = 0, MU = 0, NU = 0, NP = 0, NT = 0, NL = 0;
@@ -154,6 +164,9 @@ struct hdg_ctx {
     // forcing
     double *Fload = nullptr;
     bool has_forcing = false;
+    // time factors of the forcing for one step (stage sums 1..s-1, final sum s, reconstruction 7):
+    // device copy read by the step graph, pinned host staging refreshed before each launch
+    double *dfv = nullptr, *hfv = nullptr;
     double (*phi)(double, void *) = nullptr;
     void *phi_user = nullptr;
     // Step I
@@ -168,8 +181,6 @@ struct hdg_ctx {
     float *gV32 = nullptr, *gw32 = nullptr, *gu32 = nullptr;
     cudaGraphExec_t g_stepI32 = nullptr;                     // one loose Step-I solve (host-driven mode)
     int stepI32_kernels = 0;
-    GridBar *gbar = nullptr;                                 // barrier of the persistent Step-I kernel
-    int coop_grid = 0;                                       // its grid (all blocks co-resident)
     int *dstatus = nullptr;
     // Step II
     double *vK = nullptr, *wK = nullptr, *tb = nullptr, *tx = nullptr, *tr = nullptr, *tz = nullptr,
@@ -188,8 +199,9 @@ struct hdg_ctx {
     double *ll[3] = {};
     // multigrid work
     std::vector<MGWork> mgw;
+    std::vector<MGWork32> mgw32;
     double *txa = nullptr, *td = nullptr, *tt = nullptr, *cellA = nullptr, *mgB = nullptr;
-    float *tb32 = nullptr, *tr32 = nullptr, *tx32 = nullptr, *txa32 = nullptr, *td32 = nullptr, *tt32 = nullptr;
+    float *tb32 = nullptr, *tr32 = nullptr, *tx32 = nullptr, *txa32 = nullptr, *td32 = nullptr;
     double *tzold = nullptr;                                 // flexible CG: the previous z
     unsigned long long *dlmax = nullptr;
     // reductions
@@ -214,6 +226,13 @@ struct hdg_ctx {
     int step_kernels = 0;                                    // kernels of g_step outside its loops
     cudaGraphExec_t gm_first = nullptr, gm_restart = nullptr;   // captured GMRES(30) cycles
     double *gb = nullptr, *gx = nullptr;                     // their fixed right-hand side / solution
+    // hdg_params.timeout_ms: the host's wait for a step graph is bounded; a step whose wait ran out
+    // is still queued on the stream, and its bookkeeping (time, counters) is applied by the next call
+    double deadline = 0;                                     // steady-clock ms; 0: no limit on this wait
+    bool pending = false;                                    // a timed-out step is still on the stream
+    double pending_t = 0;
+    cudaEvent_t ewait = nullptr;                             // marks the end of the step being waited for
+    int *hstat = nullptr;                                    // pinned copy of dstatus
     // running stats of the current call
     hdg_stats S{};
 
@@ -411,6 +430,38 @@ void capture_while(hdg_ctx *c, Init &&init, Body &&body) {
     CK(cudaStreamEndCapture(bs, &outg));
     c->nk_host[id] = count_kernel_nodes(bodyg);
     CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+}
+
+inline LinComb lincomb() {
+    LinComb L{};
+    L.fterm = -1;
+    return L;
+}
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Wait for the work queued on the context's stream; with a deadline, poll an event until it has
+// passed and then throw TimeoutError (the work stays queued and completes on the stream).
+void wait_stream(hdg_ctx *c) {
+    if (!(c->deadline > 0)) {
+        CK(cudaStreamSynchronize(c->st));
+        return;
+    }
+    CK(cudaEventRecord(c->ewait, c->st));
+    for (;;) {
+        cudaError_t e = cudaEventQuery(c->ewait);
+        if (e == cudaSuccess) return;
+        if (e != cudaErrorNotReady) CK(e);
+        if (now_ms() > c->deadline) {
+            char msg[160];
+            snprintf(msg, sizeof msg, "the step's GPU work did not finish within timeout_ms = %.3f; it completes on "
+                                      "the context's stream", c->P.timeout_ms);
+            throw TimeoutError(msg);
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
 }
 
 template <int K>
@@ -797,15 +848,38 @@ struct Impl {
     // graph captures)
     // FP32 copy of the trace multigrid of coefficient E.c for the one-V-cycle inner Step II; left
     // out (FP64 V-cycle) when the P1 hierarchy's vectors do not fit one block's shared memory
+    // The levels from first32 down run in one block (k_tv_tail, everything in shared memory); the
+    // larger ones above as grid-wide kernels. first32: the first level whose sub-hierarchy fits the
+    // block (<= 200 KiB, rows of at most 1024 points) and has at most HDG_MG32_TAIL_MAX vertices.
+    static int mg32_tail_max() {
+        static int v = -1;
+        if (v < 0) {
+            const char *e = std::getenv("HDG_MG32_TAIL_MAX");
+            v = e ? std::atoi(e) : 5000;
+            if (v < 1) v = 1;
+        }
+        return v;
+    }
+    static size_t tail32_bytes(const CondCache &E, int first) {
+        P1Grid G[MG_MAX_LEVELS];
+        const int L = (int)E.lv.size();
+        for (int l = first; l < L; ++l) G[l - first] = E.lv[l].G;
+        return sizeof(float) * tail32_floats(G, L - first);
+    }
+    static bool tail32_fits(const CondCache &E, int first) {
+        const int L = (int)E.lv.size();
+        if (tail32_bytes(E, first) > (size_t)200 * 1024) return false;
+        for (int l = first; l < L; ++l)
+            if (E.lv[l].G.nvx > 1024) return false;
+        return E.lv[first].G.nverts <= mg32_tail_max() || first == L - 1;
+    }
     static void build_mg32(hdg_ctx *c, CondCache &E) {
         const int L = (int)E.lv.size();
         if (L < 1 || L > MG_MAX_LEVELS) return;
-        P1Grid G[MG_MAX_LEVELS];
-        for (int l = 0; l < L; ++l) G[l] = E.lv[l].G;
-        const size_t smem = sizeof(float) * tail32_floats(G, L);
-        if (smem > (size_t)200 * 1024 || 2LL * G[0].nverts > c->nL) return;   // b_1, e_1 share tt32
-        for (int l = 0; l < L; ++l)
-            if (G[l].nvx > 1024) return;
+        int first = 0;
+        while (first < L - 1 && !tail32_fits(E, first)) ++first;
+        if (!tail32_fits(E, first)) return;
+        const size_t smem = tail32_bytes(E, first);
         auto f32 = [&](const double *a, long long n) {
             float *b = c->alloc<float>((size_t)n);
             launch_k(k_f64_to_f32, grid_for(n), VEC_THREADS, 0, c->st, a, b, n);
@@ -816,16 +890,25 @@ struct Impl {
         E.A32.resize(L);
         E.dinv32.resize(L);
         for (int l = 0; l < L; ++l) {
-            E.A32[l] = f32(E.lv[l].A, (long long)P1_NS * G[l].nverts);
-            E.dinv32[l] = f32(E.lv[l].dinv, G[l].nverts);
+            E.A32[l] = f32(E.lv[l].A, (long long)P1_NS * E.lv[l].G.nverts);
+            E.dinv32[l] = f32(E.lv[l].dinv, E.lv[l].G.nverts);
         }
         E.Minv32 = f32(E.Minv, (long long)E.Nc * E.Nc);
         CKL();
         if (!c->tb32) {
             c->tb32 = c->alloc<float>(c->nL); c->tr32 = c->alloc<float>(c->nL); c->tx32 = c->alloc<float>(c->nL);
-            c->txa32 = c->alloc<float>(c->nL); c->td32 = c->alloc<float>(c->nL); c->tt32 = c->alloc<float>(c->nL);
+            c->txa32 = c->alloc<float>(c->nL); c->td32 = c->alloc<float>(c->nL);
             c->tzold = c->alloc<double>(c->nL);
         }
+        if (c->mgw32.empty())               // the hierarchy depends on the mesh only
+            for (int l = 0; l < L; ++l) {
+                const size_t nv = (size_t)E.lv[l].G.nverts;
+                MGWork32 w;
+                w.b = c->alloc<float>(nv); w.xa = c->alloc<float>(nv); w.xb = c->alloc<float>(nv);
+                w.d = c->alloc<float>(nv); w.t = c->alloc<float>(nv);
+                c->mgw32.push_back(w);
+            }
+        E.first32 = first;
         CK(cudaFuncSetAttribute(k_tv_tail<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         E.tail32_smem = smem;
         E.mg32 = true;
@@ -833,20 +916,53 @@ struct Impl {
 
     static Tail32 tail32_params(hdg_ctx *c, const CondCache &E) {
         Tail32 T{};
-        T.L = (int)E.lv.size();
+        const int f0 = E.first32;
+        T.L = (int)E.lv.size() - f0;
         T.Nc = E.Nc;
         T.nfacets = (int)c->nfacets;
         int off = 0;
         for (int l = 0; l < T.L; ++l) {
-            T.G[l] = E.lv[l].G; T.A[l] = E.A32[l]; T.dinv[l] = E.dinv32[l];
-            T.invth[l] = (float)E.lv[l].invth; T.c1[l] = (float)E.lv[l].c1; T.c2[l] = (float)E.lv[l].c2;
+            const MGLevel &V = E.lv[f0 + l];
+            T.G[l] = V.G; T.A[l] = E.A32[f0 + l]; T.dinv[l] = E.dinv32[f0 + l];
+            T.invth[l] = (float)V.invth; T.c1[l] = (float)V.c1; T.c2[l] = (float)V.c2;
             T.off[l] = off;
-            off += (l >= 1 ? 12 : 5) * E.lv[l].G.nverts;
+            off += (l >= 1 ? 12 : 5) * V.G.nverts;
         }
         T.Minv = E.Minv32;
-        T.b1 = c->tt32;
-        T.e1 = c->tt32 + E.lv[0].G.nverts;
+        T.b1 = c->mgw32[f0].b;
+        T.e1 = c->mgw32[f0].xb;
         return T;
+    }
+
+    // The P1 part of the FP32 V-cycle: from the right-hand side on the mesh vertices (mgw32[0].b)
+    // to the correction there (mgw32[0].xb); the levels above first32 as grid-wide kernels around
+    // the one-block tail
+    static void p1_cycle32(hdg_ctx *c, const CondCache &E) {
+        const int f0 = E.first32;
+        for (int l = 0; l < f0; ++l) {
+            const MGLevel &V = E.lv[l];
+            const MGWork32 &W = c->mgw32[l];
+            const int nv = V.G.nverts, g = grid_for(nv);
+            launch_k(k_p32_cheb0, g, VEC_THREADS, 0, c->st, (const float *)E.dinv32[l], (const float *)W.b, W.xa, W.d,
+                     (float)V.invth, nv);
+            launch_k(k_p32_cheb, g, VEC_THREADS, 0, c->st, V.G, (const float *)E.A32[l], (const float *)E.dinv32[l],
+                     (const float *)W.b, (const float *)W.xa, W.xb, W.d, (float)V.c1, (float)V.c2);
+            launch_k(k_p32_resid, g, VEC_THREADS, 0, c->st, V.G, (const float *)E.A32[l], (const float *)W.b,
+                     (const float *)W.xb, W.t);
+            launch_k(k_p32_restrict, grid_for(E.lv[l + 1].G.nverts), VEC_THREADS, 0, c->st, E.lv[l + 1].G, V.G,
+                     (const float *)W.t, c->mgw32[l + 1].b);
+        }
+        launch_k(k_tv_tail<NT>, 1, 1024, E.tail32_smem, c->st, tail32_params(c, E));
+        for (int l = f0 - 1; l >= 0; --l) {
+            const MGLevel &V = E.lv[l];
+            const MGWork32 &W = c->mgw32[l];
+            const int g = grid_for(V.G.nverts);
+            launch_k(k_p32_prolong, g, VEC_THREADS, 0, c->st, V.G, E.lv[l + 1].G, (const float *)c->mgw32[l + 1].xb, W.xb);
+            launch_k(k_p32_cheb, g, VEC_THREADS, 0, c->st, V.G, (const float *)E.A32[l], (const float *)E.dinv32[l],
+                     (const float *)W.b, (const float *)W.xb, W.xa, W.d, 0.f, (float)V.invth);
+            launch_k(k_p32_cheb, g, VEC_THREADS, 0, c->st, V.G, (const float *)E.A32[l], (const float *)E.dinv32[l],
+                     (const float *)W.b, (const float *)W.xa, W.xb, W.d, (float)V.c1, (float)V.c2);
+        }
     }
 
     // Inner Step II's trace solve as one FP32 V-cycle: right-hand side gathered from the cells'
@@ -861,10 +977,10 @@ struct Impl {
         launch_k(k_tv_cheb01<NT>, gb, 128, 0, c->st, T, (const float *)c->tb32, (const double *)nullptr, (const Scalars *)c->sc,
                  invth, c1, c2, c->tr32, c->tx32, c->td32);
         const int nv0 = E.lv[0].G.nverts;
-        float *b1 = c->tt32, *e1 = c->tt32 + nv0;
+        float *b1 = c->mgw32[0].b, *e1 = c->mgw32[0].xb;
         launch_k(k_tv_restrict<NT>, (unsigned)((16LL * nv0 + 127) / 128), 128, 0, c->st, T, c->tr32, c->tx32,
                                                                    c->M.vert_facet, c->M.vert_fsign, nv0, b1);
-        launch_k(k_tv_tail<NT>, 1, 1024, E.tail32_smem, c->st, tail32_params(c, E));
+        p1_cycle32(c, E);
         launch_k(k_tv_cheb<NT>, gb, 128, 0, c->st, T, c->tr32, c->tx32, e1, c->M.facet_vert, c->txa32, c->td32, 0.f, invth,
                                                            (double *)nullptr);
         launch_k(k_tv_cheb<NT>, gb, 128, 0, c->st, T, c->tr32, c->txa32, (const float *)nullptr, c->M.facet_vert,
@@ -882,12 +998,12 @@ struct Impl {
         const TraceOp32 T{E.Sell32, E.Dinv32, E.tcol, nf};
         const float invth = (float)E.t_invth, c1 = (float)E.t_c1, c2 = (float)E.t_c2;
         const int nv0 = E.lv[0].G.nverts;
-        float *b1 = c->tt32, *e1 = c->tt32 + nv0;
+        float *b1 = c->mgw32[0].b, *e1 = c->mgw32[0].xb;
         launch_k(k_tv_cheb01<NT>, gb, 128, 0, c->st, T, (const float *)nullptr, (const double *)c->tr,
                  (const Scalars *)nullptr, invth, c1, c2, c->tr32, c->tx32, c->td32);
         launch_k(k_tv_restrict<NT>, (unsigned)((16LL * nv0 + 127) / 128), 128, 0, c->st, T, c->tr32, c->tx32,
                                                                    c->M.vert_facet, c->M.vert_fsign, nv0, b1);
-        launch_k(k_tv_tail<NT>, 1, 1024, E.tail32_smem, c->st, tail32_params(c, E));
+        p1_cycle32(c, E);
         launch_k(k_tv_cheb<NT>, gb, 128, 0, c->st, T, c->tr32, c->tx32, e1, c->M.facet_vert, c->txa32, c->td32, 0.f, invth,
                                                            (double *)nullptr);
         launch_k(k_tv_cheb<NT>, gb, 128, 0, c->st, T, c->tr32, c->txa32, (const float *)nullptr, c->M.facet_vert,
@@ -898,7 +1014,7 @@ struct Impl {
 
     static void ensure_pre_maps(hdg_ctx *c, double cc) {
         CondCache &E = condense(c, cc);
-        if (c->capturing) return;
+        if (c->capturing || c->P.precision != HDG_MIXED) return;
         if (c->P.inner_trace_fp32 && E.mg && !E.mg32) build_mg32(c, E);
         if (E.Lrhs32) return;
         E.Lrhs32 = c->alloc<float>((size_t)c->ncells * (NU + NP) * (NL + NP));
@@ -923,8 +1039,8 @@ struct Impl {
     // Step-I solves to loose tolerances (the inner solves of the stage preconditioner) run in FP32;
     // tight ones in FP64. The assembly forms the block inverses the coming solves need.
     static constexpr int INV64 = 1, INV32 = 2;
-    static bool loose(double rtol) { return rtol >= 1e-4; }
-    static int inv_for(double rtol) { return loose(rtol) ? INV32 : INV64; }
+    static bool loose(const hdg_ctx *c, double rtol) { return rtol >= 1e-4 && c->P.precision == HDG_MIXED; }
+    static int inv_for(const hdg_ctx *c, double rtol) { return loose(c, rtol) ? INV32 : INV64; }
 
     // Step-I operator M - cc F(Qs): diagonal blocks, neighbour and penalty weights, and the
     // block-Jacobi inverses named by inv (INV64 | INV32)
@@ -969,47 +1085,6 @@ struct Impl {
         gmres_arnoldi<double>(c, EdgeTab<double>{c->R.ephi, c->pen}, c->Binv, c->wq, c->utr, c->gw, c->gV);
     }
 
-    // The same solve as one persistent cooperative kernel (hdg_stepI_persistent.cuh); a barrier
-    // that runs out of polls is reported as a breakdown through the device counters.
-    static void stepI32_persistent(hdg_ctx *c, const double *b, double *x) {
-        if (!c->coop_grid) {
-            int per_sm = 0, dev = 0, nsm = 0;
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stepI32_persistent<K>, 128, 0));
-            CK(cudaGetDevice(&dev));
-            CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-            const long long groups = (c->ncells + TEAMS_PER_BLOCK - 1) / TEAMS_PER_BLOCK;
-            // few blocks per SM: every barrier is one atomic arrival per block
-            static int want = -1;
-            if (want < 0) {
-                const char *e = std::getenv("HDG_COOP_BLOCKS_PER_SM");
-                want = e ? std::atoi(e) : 4;
-                if (want < 1) want = 1;
-            }
-            if (per_sm > want) per_sm = want;
-            long long g = (long long)per_sm * nsm;
-            if (g > groups) g = groups;
-            if (g > MAX_RED_BLOCKS) g = MAX_RED_BLOCKS;
-            if (g < 1) throw std::runtime_error("persistent Step-I kernel cannot be resident");
-            c->coop_grid = (int)g;
-        }
-        StepI32Args A{EdgeTab<float>{c->ephi32, c->pen32, c->nrm32}, c->M, c->Binv32, c->wq32, c->gV32, c->utr32, c->gw32,
-                      b, x, c->partials, c->gbar, c->gs};
-        launch_k(k_bar_reset, 1, 1, 0, c->st, c->gbar);
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3((unsigned)c->coop_grid);
-        cfg.blockDim = dim3(128);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = c->st;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeCooperative;
-        at[0].val.cooperative = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        CK(cudaLaunchKernelEx(&cfg, k_stepI32_persistent<K>, A));
-        launch_k(k_bar_check, 1, 1, 0, c->st, c->gbar, c->dcnt);
-        launch_k(k_count_solve, 1, 1, 0, c->st, c->dcnt, c->gs, (const Scalars *)nullptr);
-    }
-
     // Arnoldi steps per pass of the inner FP32 loop (HDG_INNER_UNROLL overrides the default)
     static int inner_unroll() {
         static int v = -1;
@@ -1050,10 +1125,6 @@ struct Impl {
     // x = 0 with its Arnoldi steps as a device-side loop, stopping at the tolerance or after GM_M
     // steps (an inexact solve is what the flexible outer iteration expects). b, x: FP64.
     static void stepI32_record(hdg_ctx *c, const double *b, double *x) {
-        if (c->P.persistent_stepI) {
-            stepI32_persistent(c, b, x);
-            return;
-        }
         const long long n = c->nQ;
         const int g = grid_for(n);
         const EdgeTab<float> E{c->ephi32, c->pen32, c->nrm32};
@@ -1121,10 +1192,10 @@ struct Impl {
     static void stepI_solve(hdg_ctx *c, const double *b, double *x, double rtol = -1.0) {
         if (!(rtol > 0)) rtol = c->P.stepI_rtol;
         CompTimer tm_(c, &c->S.ms_stepI);
-        if (!(c->inv_ok & inv_for(rtol))) throw std::logic_error("Step-I solve without the block inverses it needs");
+        if (!(c->inv_ok & inv_for(c, rtol))) throw std::logic_error("Step-I solve without the block inverses it needs");
         launch_k(k_gm_set_tol, 1, 1, 0, c->st, c->gs, rtol, c->P.max_iters);
         CKL();
-        if (loose(rtol)) {              // FP32, one cycle of at most GM_M steps
+        if (loose(c, rtol)) {           // FP32, one cycle of at most GM_M steps
             if (c->capturing) {
                 stepI32_record(c, b, x);
                 return;
@@ -1183,7 +1254,7 @@ struct Impl {
     // r: dual (modal); Qs: advecting velocity (modal); Q, p, lam: in/out (modal)
     static int richardson(hdg_ctx *c, double cc, const double *r, const double *Qsv, double *Q, double *p,
                           double *lam) {
-        assemble_stepI(c, Qsv, cc, inv_for(c->P.stepI_rtol));
+        assemble_stepI(c, Qsv, cc, inv_for(c, c->P.stepI_rtol));
         int hstat = 0;
         CK(cudaMemcpyAsync(&hstat, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st));
         condense(c, cc);
@@ -1201,7 +1272,7 @@ struct Impl {
             launch_k(k_rich_residual<K>, nb, 128, smem_res, c->st, c->R, c->M, cc, r, BQ, p, lam, dr, 1.0);
             CKL();
             stepI_solve(c, dr, Qbar);                                            // Step I
-            LinComb L{};
+            LinComb L = lincomb();
             L.nterms = 2; L.coef[0] = 1; L.vec[0] = Q; L.coef[1] = 1; L.vec[1] = Qbar;
             launch_k(k_lincomb, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->geo, NU, L, X, c->ncells);
             CKL();
@@ -1284,7 +1355,7 @@ struct Impl {
         double *Qbar = c->q[2], *U = c->q[4];
         stepI_solve(c, vQ, Qbar, c->P.inner_stepI_rtol);
         if (pre_step2(c, cc, Qbar, vp, vl, U, zp, zl, Qbar, zQ)) return;    // zQ = Qbar + U written there
-        LinComb L{};
+        LinComb L = lincomb();
         L.nterms = 2; L.coef[0] = 1; L.vec[0] = Qbar; L.coef[1] = 1; L.vec[1] = U;
         launch_k(k_lincomb, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->geo, NU, L, zQ, c->ncells);
         CKL();
@@ -1296,12 +1367,18 @@ struct Impl {
     // forms v_{j+1} = (w' - V h2) / hn in V (and in vfix when set): no reduction there, and the
     // next Arnoldi step starts from V_{j+1} without a normalisation kernel.
     // The first pass's dots run in FP32 on the shadows (c->fw32 = FP32 w from the stage operator).
+    static float *fV32(const hdg_ctx *c) { return c->P.precision == HDG_MIXED ? c->fV32 : nullptr; }
+    static float *fw32(const hdg_ctx *c) { return c->P.precision == HDG_MIXED ? c->fw32 : nullptr; }
     static void fgmres_orth(hdg_ctx *c, double *w, long long N, GmresState *fgs, double *vfix) {
         const int go = grid_orth(N);
-        launch_k(k_vec_dot32, go, VEC_THREADS, 0, c->st, (const float *)c->fw32, (const float *)c->fV32, N, c->rb(), fgs);
+        if (c->P.precision == HDG_MIXED)
+            launch_k(k_vec_dot<float>, go, VEC_THREADS, 0, c->st, (const float *)c->fw32, (const float *)c->fV32, N,
+                     c->rb(), fgs);
+        else
+            launch_k(k_vec_dot<double>, go, VEC_THREADS, 0, c->st, (const double *)w, (const double *)c->fV, N, c->rb(), fgs);
         launch_k(k_fgm_orth1, go, VEC_THREADS, 0, c->st, w, c->fV, N, c->rb(), fgs);
         launch_k(k_fgm_orth2n, grid_for(N), VEC_THREADS, 0, c->st, (const double *)w, c->fV, vfix, N,
-                 (const GmresState *)fgs, c->fV32);
+                 (const GmresState *)fgs, fV32(c));
         CKL();
     }
 
@@ -1328,13 +1405,13 @@ struct Impl {
         capture_while(
             c, [&](LoopCtl L) { launch_k(k_gm_loop_ctl, 1, 1, 0, c->st, L, maxit + 2, fgs, 1); },
             [&](LoopCtl L) {
-                launch_k(k_vec_normalize, g, VEC_THREADS, 0, c->st, res, w, c->fV, c->fv, N, fgs, c->fV32);   // V_0
+                launch_k(k_vec_normalize, g, VEC_THREADS, 0, c->st, res, w, c->fV, c->fv, N, fgs, fV32(c));   // V_0
                 CKL();
                 capture_while(
                     c, [&](LoopCtl L2) { launch_k(k_loop_init, 1, 1, 0, c->st, L2, &fgs->cycle_end); },
                     [&](LoopCtl L2) {
                         chorin_precond(c, cc, c->fv, c->fz);
-                        stage_apply(c, cc, c->fz, w, c->fw32, c->fZ, fgs);      // also Z_j = fz
+                        stage_apply(c, cc, c->fz, w, fw32(c), c->fZ, fgs);      // also Z_j = fz
                         fgmres_orth(c, w, N, fgs, c->fv);
                         launch_k(k_loop_ctl, 1, 1, 0, c->st, L2, GM_M + 1, &fgs->cycle_end);
                         CKL();
@@ -1373,7 +1450,7 @@ struct Impl {
     // the Chorin split (Alg. 2's preconditioner; plain Alg. 2 is its Richardson iteration).
     static int stage_fgmres(hdg_ctx *c, double cc, const double *r, const double *Qsv, double *Q, double *p,
                             double *lam) {
-        assemble_stepI(c, Qsv, cc, inv_for(c->P.inner_stepI_rtol));
+        assemble_stepI(c, Qsv, cc, inv_for(c, c->P.inner_stepI_rtol));
         ensure_pre_maps(c, cc);
         CondCache &E = condense(c, cc);
         if (!c->capturing) {
@@ -1423,12 +1500,12 @@ struct Impl {
             CK(cudaStreamSynchronize(c->st));
             if (c->hfgs->breakdown == 2) throw std::domain_error("stage FGMRES: non-finite residual");
             if (c->hfgs->converged) { converged = 1; break; }
-            launch_k(k_vec_normalize, g, VEC_THREADS, 0, c->st, res, w, c->fV, nullptr, N, c->fgs, c->fV32);   // V_0
+            launch_k(k_vec_normalize, g, VEC_THREADS, 0, c->st, res, w, c->fV, nullptr, N, c->fgs, fV32(c));   // V_0
             CKL();
             for (int j = 0; j < GM_M; ++j) {
                 double *Vj = c->fV + (size_t)j * N, *Zj = c->fZ + (size_t)j * N;
                 chorin_precond(c, cc, Vj, Zj);
-                stage_apply(c, cc, Zj, w, c->fw32);
+                stage_apply(c, cc, Zj, w, fw32(c));
                 fgmres_orth(c, w, N, c->fgs, nullptr);
                 CKL();
                 CK(cudaMemcpyAsync(c->hfgs, c->fgs, sizeof(GmresState), cudaMemcpyDeviceToHost, c->st));
@@ -1473,14 +1550,18 @@ struct Impl {
     static void fimpl_dual(hdg_ctx *c, const double *Q, const double *Qs, double tt, double *out) {
         assemble_stepI(c, Qs, 1.0, 0);
         cell_apply(c, Q, c->q[6]);
-        LinComb L{};
+        LinComb L = lincomb();
         L.nterms = 2;
         L.coef[0] = 1.0; L.vec[0] = Q; L.mass[0] = 1;
         L.coef[1] = -1.0; L.vec[1] = c->q[6];
         if (c->has_forcing) {
             L.nterms = 3;
-            L.coef[2] = c->phi ? c->phi(tt, c->phi_user) : 1.0;
             L.vec[2] = c->Fload;
+            if (c->capturing) {         // phi(t) from the step's device values
+                L.coef[2] = 1.0; L.fterm = 2; L.fscale = c->dfv + 7;
+            } else {
+                L.coef[2] = c->phi ? c->phi(tt, c->phi_user) : 1.0;
+            }
         }
         launch_k(k_lincomb, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->geo, NU, L, out, c->ncells);
         CKL();
@@ -1495,6 +1576,23 @@ struct Impl {
         mean_shift(c, p, lam);
     }
 
+    // Time factors of the forcing f(t) = phi(t) F for the step from t0: out[i] = dt sum_j a^ex_ij
+    // phi(t0 + c_j dt) for stage i (eq. imex_residual), out[s] = dt sum_i b^ex_i phi(t0 + c_i dt)
+    // (eq. final_residual), out[7] = phi(t0 + dt) (the reconstruction at the new time).
+    static void forcing_values(const hdg_ctx *c, double t0, double out[8]) {
+        const Tab &T = c->tab;
+        const double dt = c->P.dt;
+        for (int i = 0; i < 8; ++i) out[i] = 0.0;
+        if (!c->has_forcing) return;
+        auto phi = [&](double t) { return c->phi ? c->phi(t, c->phi_user) : 1.0; };
+        double ph[4] = {0, 0, 0, 0};
+        for (int j = 0; j < T.s; ++j) ph[j] = phi(t0 + T.c[j] * dt);
+        for (int i = 1; i < T.s; ++i)
+            for (int j = 0; j < i; ++j) out[i] += dt * T.Ae[i][j] * ph[j];
+        for (int i = 0; i < T.s; ++i) out[T.s] += dt * T.be[i] * ph[i];
+        out[7] = phi(t0 + dt);
+    }
+
     // ---------------------------------------------------------------- Alg. 1
     // One step from t0 (c->t is not advanced here). Inside a graph capture every solve is recorded
     // with device-side loops and the return value is 0 (non-convergence is counted on the device).
@@ -1502,8 +1600,8 @@ struct Impl {
         const Tab &T = c->tab;
         const double dt = c->P.dt;
         const int s = T.s;
-        double fval[4] = {0, 0, 0, 0};
-        for (int j = 0; j < s; ++j) fval[j] = c->has_forcing ? (c->phi ? c->phi(t0 + T.c[j] * dt, c->phi_user) : 1.0) : 0.0;
+        double fv[8];
+        forcing_values(c, t0, fv);
         size_t bq = sizeof(double) * c->nQ;
         CK(cudaMemcpyAsync(c->Qs[0], c->Q, bq, cudaMemcpyDeviceToDevice, c->st));
         CK(cudaMemcpyAsync(c->ps[0], c->p, sizeof(double) * c->nPv, cudaMemcpyDeviceToDevice, c->st));
@@ -1511,7 +1609,7 @@ struct Impl {
         int nc = 0;
         for (int i = 1; i < s; ++i) {
             // eq. imex_residual: r_i = M Q^n + sum_j (a_ij/a_jj)(M Q_j - r_j) + dt sum_j aex_ij (w.f_j)
-            LinComb L{};
+            LinComb L = lincomb();
             int n = 0;
             L.coef[n] = 1.0; L.vec[n] = c->Qs[0]; L.mass[n] = 1; ++n;
             for (int j = 1; j < i; ++j) {
@@ -1520,10 +1618,10 @@ struct Impl {
                 L.coef[n] = w; L.vec[n] = c->Qs[j]; L.mass[n] = 1; ++n;
                 L.coef[n] = -w; L.vec[n] = c->rs[j]; L.mass[n] = 0; ++n;
             }
-            if (c->has_forcing) {
-                double f = 0;
-                for (int j = 0; j < i; ++j) f += dt * T.Ae[i][j] * fval[j];
-                if (f != 0.0) { L.coef[n] = f; L.vec[n] = c->Fload; L.mass[n] = 0; ++n; }
+            if (c->has_forcing && c->capturing) {
+                L.coef[n] = 1.0; L.vec[n] = c->Fload; L.mass[n] = 0; L.fterm = n; L.fscale = c->dfv + i; ++n;
+            } else if (c->has_forcing && fv[i] != 0.0) {
+                L.coef[n] = fv[i]; L.vec[n] = c->Fload; L.mass[n] = 0; ++n;
             }
             L.nterms = n;
             launch_k(k_lincomb, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->geo, NU, L, c->rs[i], c->ncells);
@@ -1535,7 +1633,7 @@ struct Impl {
             nc |= stage_solve(c, T.Ai[i][i] * dt, c->rs[i], c->q[5], c->Qs[i], c->ps[i], c->ls[i]);
         }
         // eq. final_residual and eq. final_update (coefficient b_{s-1}^im dt)
-        LinComb L{};
+        LinComb L = lincomb();
         int n = 0;
         L.coef[n] = 1.0; L.vec[n] = c->Qs[0]; L.mass[n] = 1; ++n;
         for (int i = 1; i < s; ++i) {
@@ -1544,10 +1642,10 @@ struct Impl {
             L.coef[n] = w; L.vec[n] = c->Qs[i]; L.mass[n] = 1; ++n;
             L.coef[n] = -w; L.vec[n] = c->rs[i]; L.mass[n] = 0; ++n;
         }
-        if (c->has_forcing) {
-            double f = 0;
-            for (int i = 0; i < s; ++i) f += dt * T.be[i] * fval[i];
-            if (f != 0.0) { L.coef[n] = f; L.vec[n] = c->Fload; L.mass[n] = 0; ++n; }
+        if (c->has_forcing && c->capturing) {
+            L.coef[n] = 1.0; L.vec[n] = c->Fload; L.mass[n] = 0; L.fterm = n; L.fscale = c->dfv + s; ++n;
+        } else if (c->has_forcing && fv[s] != 0.0) {
+            L.coef[n] = fv[s]; L.vec[n] = c->Fload; L.mass[n] = 0; ++n;
         }
         L.nterms = n;
         double *rn = c->q[7];
@@ -1558,10 +1656,10 @@ struct Impl {
         return nc;
     }
 
-    // The step as one CUDA graph: stages solved by flexible GMRES with device-side loops, no
-    // time-dependent forcing callback (its values would be frozen into the graph).
+    // The step as one CUDA graph: stages solved by flexible GMRES with device-side loops; the
+    // forcing's time factors are device values refreshed before each launch.
     static bool step_graph_ok(const hdg_ctx *c) {
-        return c->P.device_loops && c->P.n_richardson <= 0 && c->P.stage_krylov && !(c->has_forcing && c->phi);
+        return c->P.device_loops && c->P.n_richardson <= 0 && c->P.stage_krylov;
     }
 
     static int imex_step(hdg_ctx *c) {
@@ -1578,17 +1676,34 @@ struct Impl {
             condense(c, 1.0);
             c->g_step = capture_graph(c, [&]() { imex_step_body(c, t0); }, &c->step_kernels);
         }
+        if (c->has_forcing) {                           // this step's forcing time factors
+            forcing_values(c, t0, c->hfv);
+            CK(cudaMemcpyAsync(c->dfv, c->hfv, 8 * sizeof(double), cudaMemcpyHostToDevice, c->st));
+        }
         CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st));
+        c->deadline = c->P.timeout_ms > 0 ? now_ms() + c->P.timeout_ms : 0;   // counted from the launch
         launch_counted(c, c->g_step);
-        int hstat = 0;
-        CK(cudaMemcpyAsync(&hstat, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-        CK(cudaStreamSynchronize(c->st));
+        CK(cudaMemcpyAsync(c->hstat, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        c->pending = true;
+        c->pending_t = t0 + dt;
+        wait_stream(c);
+        c->pending = false;
+        c->deadline = 0;
+        const int hstat = *c->hstat;
         if (hstat) throw std::domain_error("singular tentative-velocity block");
         graph_stats(c, c->step_kernels);
         c->t = t0 + dt;
         return c->hcnt->stage_unconverged ? 1 : 0;
     }
 };
+
+// A step that timed out in an earlier call: wait for it without a limit, then apply its bookkeeping.
+void settle_pending(hdg_ctx *c) {
+    if (!c->pending) return;
+    CK(cudaStreamSynchronize(c->st));
+    c->pending = false;
+    c->t = c->pending_t;
+}
 
 hdg_status map_exception() {
     try {
@@ -1599,6 +1714,9 @@ hdg_status map_exception() {
     } catch (const CudaError &e) {
         g_last_error = e.what();
         return HDG_ERR_CUDA;
+    } catch (const TimeoutError &e) {
+        g_last_error = e.what();
+        return HDG_ERR_TIMEOUT;
     } catch (const std::length_error &e) {
         g_last_error = e.what();
         return HDG_ERR_NOT_CONVERGED;
@@ -1627,6 +1745,7 @@ hdg_status map_exception() {
     }
 
 void begin_call(hdg_ctx *c) {
+    settle_pending(c);
     c->S = hdg_stats{};
     CK(cudaEventRecord(c->e0, c->st));
 }
@@ -1665,7 +1784,8 @@ void hdg_default_params(hdg_params *p) {
     p->trace_mg = 1;
     p->device_loops = 1;
     p->inner_trace_vcycles = 1;
-    p->persistent_stepI = 0;
+    p->precision = HDG_MIXED;
+    p->timeout_ms = 0.0;
     p->inner_trace_fp32 = 1;
     p->trace_fp32_vcycle = 1;
     p->inner_gs = 1;
@@ -1680,6 +1800,7 @@ const char *hdg_status_string(hdg_status s) {
         case HDG_ERR_NOT_CONVERGED: return "iteration did not converge";
         case HDG_ERR_NUMERIC: return "non-finite value";
         case HDG_ERR_UNSUPPORTED: return "unsupported";
+        case HDG_ERR_TIMEOUT: return "timed out";
     }
     return "unknown status";
 }
@@ -1739,12 +1860,19 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         (!(params->inner_stepI_rtol > 0) || !(params->inner_trace_rtol > 0)))
         return HDG_ERR_INVALID_ARG;
     if (params->tableau < HDG_ARS222 || params->tableau > HDG_IMEX_EULER) return HDG_ERR_INVALID_ARG;
+    if (params->precision != HDG_FP64 && params->precision != HDG_MIXED) return HDG_ERR_INVALID_ARG;
+    if (!(params->timeout_ms >= 0)) return HDG_ERR_INVALID_ARG;
     hdg_ctx *c = new (std::nothrow) hdg_ctx();
     if (!c) return HDG_ERR_OOM;
     try {
         c->P = *params;
         c->D = *mesh;
         c->st = (cudaStream_t)cuda_stream;
+        CK(cudaGetDevice(&c->device));
+        if (c->P.precision == HDG_FP64) {        // every part of the path in FP64
+            c->P.inner_trace_fp32 = 0;
+            c->P.trace_fp32_vcycle = 0;
+        }
         c->tab = make_tableau(params->tableau);
         c->T = build_tables(params->k);
         c->H = build_mesh(mesh->n, mesh->Lx, mesh->Ly, mesh->periodic_x != 0, mesh->periodic_y != 0);
@@ -1815,6 +1943,8 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
             c->ps.push_back(c->alloc<double>(nP)); c->ls.push_back(c->alloc<double>(nL));
         }
         c->Fload = c->alloc<double>(nQ);
+        c->dfv = c->alloc<double>(8);
+        CK(cudaMallocHost(&c->hfv, 8 * sizeof(double)));
         const int nfq = (3 * c->K + 5) / 2;                      // facet points (Dims<K>::NFQ)
         c->Dblk = c->alloc<double>((size_t)c->NU * nQ);
         c->wq = c->alloc<double>((size_t)c->ncells * 3 * nfq);
@@ -1825,8 +1955,6 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         c->wq32 = c->alloc<float>((size_t)c->ncells * 3 * nfq);
         c->utr32 = c->alloc<float>((size_t)c->ncells * 3 * nfq * 2);
         c->gV32 = c->alloc<float>((size_t)(GM_M + 1) * nQ);
-        c->gbar = c->alloc<GridBar>(1);
-        CK(cudaMemset(c->gbar, 0, sizeof(GridBar)));
         c->gw32 = c->alloc<float>(nQ);
         c->gu32 = c->alloc<float>(nQ);
         {
@@ -1881,6 +2009,8 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         CK(cudaEventCreate(&c->e1));
         CK(cudaEventCreate(&c->te0));
         CK(cudaEventCreate(&c->te1));
+        CK(cudaEventCreateWithFlags(&c->ewait, cudaEventDisableTiming));
+        CK(cudaMallocHost(&c->hstat, sizeof(int)));
         CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
         c->dguard = c->alloc<int>(hdg_ctx::CAP_LEVELS);
         c->dnk = c->alloc<int>(hdg_ctx::MAX_LOOPS);
@@ -1916,6 +2046,9 @@ void hdg_destroy(hdg_ctx *c) {
     for (cudaStream_t s : c->capst)
         if (s) cudaStreamDestroy(s);
     for (void *p : c->allocs) cudaFree(p);
+    if (c->hstat) cudaFreeHost(c->hstat);
+    if (c->hfv) cudaFreeHost(c->hfv);
+    if (c->ewait) cudaEventDestroy(c->ewait);
     if (c->hsc) cudaFreeHost(c->hsc);
     if (c->hgs) cudaFreeHost(c->hgs);
     if (c->hfgs) cudaFreeHost(c->hfgs);
@@ -1938,6 +2071,7 @@ hdg_status hdg_dof_sizes(const hdg_ctx *c, int64_t *nQ, int64_t *np, int64_t *nl
 hdg_status hdg_set_state(hdg_ctx *c, const double *Q, const double *p, const double *lam, double t) {
     if (!c || !Q) return HDG_ERR_INVALID_ARG;
     try {
+        settle_pending(c);
         DISPATCH(c, {
             I::to_modal(c, Q, c->Q, 0);
             if (p) I::to_modal(c, p, c->p, 1); else CK(cudaMemsetAsync(c->p, 0, c->nPv * 8, c->st));
@@ -1954,6 +2088,7 @@ hdg_status hdg_set_state(hdg_ctx *c, const double *Q, const double *p, const dou
 hdg_status hdg_get_state(hdg_ctx *c, double *Q, double *p, double *lam, double *t) {
     if (!c) return HDG_ERR_INVALID_ARG;
     try {
+        settle_pending(c);
         DISPATCH(c, {
             if (Q) I::to_nodal(c, c->Q, Q, 0);
             if (p) I::to_nodal(c, c->p, p, 1);
@@ -1967,9 +2102,29 @@ hdg_status hdg_get_state(hdg_ctx *c, double *Q, double *p, double *lam, double *
     return HDG_OK;
 }
 
+hdg_status hdg_project(hdg_ctx *c, int field, const double *values_at_qp, double *dofs) {
+    if (!c || !values_at_qp || !dofs || (field != 0 && field != 1)) return HDG_ERR_INVALID_ARG;
+    try {
+        settle_pending(c);
+        const int nq = c->T.nq, mu = c->MU;
+        const int n = field == 0 ? c->MU : c->NP;
+        const long long nvec = field == 0 ? 2 * c->ncells : c->ncells;
+        double *modal = field == 0 ? c->q[6] : c->pp[2];
+        launch_k(k_project_qp, grid_for(nvec * n), VEC_THREADS, 0, c->st, c->R.qw, c->R.phi, nq, mu, n, values_at_qp, modal,
+                 nvec);
+        CKL();
+        DISPATCH(c, I::to_nodal(c, modal, dofs, field));
+        CK(cudaStreamSynchronize(c->st));
+    } catch (...) {
+        return map_exception();
+    }
+    return HDG_OK;
+}
+
 hdg_status hdg_set_forcing(hdg_ctx *c, const double *F, double (*phi)(double, void *), void *user) {
     if (!c) return HDG_ERR_INVALID_ARG;
     try {
+        settle_pending(c);
         if (c->g_step) {                      // the recorded step depends on the forcing terms
             CK(cudaStreamSynchronize(c->st));
             CK(cudaGraphExecDestroy(c->g_step));
@@ -2040,6 +2195,7 @@ hdg_status hdg_solve_stage(hdg_ctx *c, double cc, const double *R, const double 
 hdg_status hdg_bdm_project(hdg_ctx *c, const double *Q, double *Qstar) {
     if (!c || !Q || !Qstar) return HDG_ERR_INVALID_ARG;
     try {
+        settle_pending(c);
         DISPATCH(c, {
             I::to_modal(c, Q, c->q[0], 0);
             I::bdm(c, c->q[0], c->q[1]);
@@ -2055,6 +2211,7 @@ hdg_status hdg_bdm_project(hdg_ctx *c, const double *Q, double *Qstar) {
 hdg_status hdg_fimpl_apply(hdg_ctx *c, const double *Qstar, const double *Q, double *out) {
     if (!c || !Qstar || !Q || !out) return HDG_ERR_INVALID_ARG;
     try {
+        settle_pending(c);
         DISPATCH(c, {
             I::to_modal(c, Qstar, c->q[1], 0);
             I::to_modal(c, Q, c->q[2], 0);
@@ -2081,7 +2238,7 @@ hdg_status hdg_tentative_solve(hdg_ctx *c, double cc, const double *Qstar, const
             I::to_modal(c, Qstar, c->q[1], 0);
             I::to_modal(c, R, c->q[2], 0);
             I::mass(c, c->q[2], c->q[3], 0);
-            I::assemble_stepI(c, c->q[1], cc, I::inv_for(c->P.stepI_rtol));
+            I::assemble_stepI(c, c->q[1], cc, I::inv_for(c, c->P.stepI_rtol));
             I::stepI_solve(c, c->q[3], c->q[4], c->P.stepI_rtol);
             I::to_nodal(c, c->q[4], Qbar, 0);
         });
@@ -2121,6 +2278,7 @@ hdg_status hdg_mixed_solve(hdg_ctx *c, double cc, const double *R, const double 
 hdg_status hdg_trace_apply(hdg_ctx *c, double cc, const double *lam, double *out) {
     if (!c || !(cc > 0) || !lam || !out) return HDG_ERR_INVALID_ARG;
     try {
+        settle_pending(c);
         DISPATCH(c, {
             CondCache &E = I::condense(c, cc);
             I::to_modal(c, lam, c->ll[0], 2);
@@ -2144,7 +2302,7 @@ hdg_status hdg_div_free_project(hdg_ctx *c, hdg_stats *stats) {
         begin_call(c);
         DISPATCH(c, {
             I::mixed_solve(c, 1.0, nullptr, c->Q, nullptr, nullptr, c->q[0], c->pp[0], c->ll[0]);
-            LinComb L{};
+            LinComb L = lincomb();
             L.nterms = 2; L.coef[0] = 1; L.vec[0] = c->Q; L.coef[1] = 1; L.vec[1] = c->q[0];
             launch_k(k_lincomb, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->geo, I::NU, L, c->Q, c->ncells);
             CKL();
@@ -2178,6 +2336,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
         return HDG_ERR_INVALID_ARG;
     if (which >= 2 && which != 8 && !c->fv) return HDG_ERR_INVALID_ARG;
     try {
+        settle_pending(c);
         if (which == 10) {
             double t10 = 0.0;
             DISPATCH(c, {
@@ -2279,7 +2438,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
             DISPATCH(c, {
                 // operator of a stage at coefficient cc around the current state; v = (M Q, 0, 0)
                 I::bdm(c, c->Q, c->q[5]);
-                I::assemble_stepI(c, c->q[5], cc, I::inv_for(c->P.inner_stepI_rtol));
+                I::assemble_stepI(c, c->q[5], cc, I::inv_for(c, c->P.inner_stepI_rtol));
                 I::condense(c, cc);
                 I::ensure_pre_maps(c, cc);
                 I::mass(c, c->Q, c->fv, 0);
@@ -2386,6 +2545,7 @@ constexpr long long NOALLOC_MAX_DOUBLES = 1LL << 20;          // 8 MiB per devic
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_DOUBLES];
 constexpr int NOALLOC_MAX_DEVICES = 64;
 static double *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+std::mutex g_noalloc_mutex;                                   // guards g_noalloc_ptr
 
 // per cell: condense S_K in shared memory (cell_condense) and write z_K = S_K l_K (canonical rows)
 template <int K>
@@ -2445,23 +2605,42 @@ extern "C" hdg_status hdg_trace_apply_noalloc(hdg_ctx *c, double cc, const doubl
                        std::to_string(need) + " doubles, maximum " + std::to_string(NOALLOC_MAX_DOUBLES) + ")";
         return HDG_ERR_INVALID_ARG;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+    // the scratch address belongs to the context's device, which must be the current one (the
+    // kernels run on the context's stream, and the address is looked up with that device current)
+    const int dev = c->device;
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) {
         g_last_error = std::string("hdg_trace_apply_noalloc: cudaGetDevice: ") + cudaGetErrorString(e);
         return HDG_ERR_CUDA;
     }
-    if (!g_noalloc_ptr[dev]) {                     // once per device, with that device current
-        double *ptr = nullptr;
-        e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr) {
-            g_last_error = std::string("hdg_trace_apply_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-            return HDG_ERR_CUDA;
+    if (cur != dev) {
+        g_last_error = "hdg_trace_apply_noalloc: current device " + std::to_string(cur) +
+                       " is not the context's device " + std::to_string(dev);
+        return HDG_ERR_INVALID_ARG;
+    }
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        g_last_error = "hdg_trace_apply_noalloc: device index " + std::to_string(dev) +
+                       " is beyond the library's table of " + std::to_string(NOALLOC_MAX_DEVICES) + " devices";
+        return HDG_ERR_UNSUPPORTED;
+    }
+    double *scr = nullptr;
+    {
+        // once per device, with that device current; concurrent first calls from several host
+        // threads are serialised here
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            double *ptr = nullptr;
+            e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess || !ptr) {
+                g_last_error = std::string("hdg_trace_apply_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+                return HDG_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = ptr;
         }
-        g_noalloc_ptr[dev] = ptr;
+        scr = g_noalloc_ptr[dev];
     }
     try {
-        double *scr = g_noalloc_ptr[dev];
         switch (c->K) {
             case 1: trace_apply_noalloc_impl<1>(c, cc, lam, out, scr); break;
             case 2: trace_apply_noalloc_impl<2>(c, cc, lam, out, scr); break;

@@ -22,8 +22,9 @@ class HdgError(RuntimeError):
 
 
 HDG_OK, HDG_ERR_INVALID_ARG, HDG_ERR_CUDA, HDG_ERR_OOM, HDG_ERR_NOT_CONVERGED, HDG_ERR_NUMERIC, \
-    HDG_ERR_UNSUPPORTED = range(7)
+    HDG_ERR_UNSUPPORTED, HDG_ERR_TIMEOUT = range(8)
 TABLEAUS = {'ARS222': 0, 'ARS343': 1, 'IMEX_EULER': 2}
+PRECISIONS = {'FP64': 0, 'MIXED': 1}
 
 
 class hdg_mesh_desc(ctypes.Structure):
@@ -40,8 +41,8 @@ class hdg_params(ctypes.Structure):
                 ('stage_krylov', ctypes.c_int), ('inner_stepI_rtol', ctypes.c_double),
                 ('inner_trace_rtol', ctypes.c_double), ('trace_mg', ctypes.c_int),
                 ('device_loops', ctypes.c_int), ('inner_trace_vcycles', ctypes.c_int),
-                ('persistent_stepI', ctypes.c_int), ('inner_trace_fp32', ctypes.c_int),
-                ('trace_fp32_vcycle', ctypes.c_int), ('inner_gs', ctypes.c_int)]
+                ('precision', ctypes.c_int), ('inner_trace_fp32', ctypes.c_int),
+                ('trace_fp32_vcycle', ctypes.c_int), ('inner_gs', ctypes.c_int), ('timeout_ms', ctypes.c_double)]
 
 
 class hdg_stats(ctypes.Structure):
@@ -76,6 +77,7 @@ _SIGNATURES = {
     'hdg_dof_sizes': (_I, [_P, _I64P, _I64P, _I64P]),
     'hdg_set_state': (_I, [_P, _P, _P, _P, _D]),
     'hdg_get_state': (_I, [_P, _P, _P, _P, _DP]),
+    'hdg_project': (_I, [_P, _I, _P, _P]),
     'hdg_set_forcing': (_I, [_P, _P, PHI, _P]),
     'hdg_imex_step': (_I, [_P, _I, ctypes.POINTER(hdg_stats)]),
     'hdg_solve_stage': (_I, [_P, _D, _P, _P, _P, _P, _P, ctypes.POINTER(hdg_stats)]),
@@ -171,6 +173,8 @@ class Context:
         for key, val in params.items():
             if key == 'tableau' and isinstance(val, str):
                 val = TABLEAUS[val]
+            if key == 'precision' and isinstance(val, str):
+                val = PRECISIONS[val]
             if not hasattr(p, key):
                 raise KeyError(key)
             setattr(p, key, val)
@@ -226,6 +230,13 @@ class Context:
         t = ctypes.c_double()
         _check(load().hdg_get_state(self._ctx, _ptr(Q), _ptr(p), _ptr(lam), ctypes.byref(t)), 'hdg_get_state')
         return Q, p, lam, t.value
+
+    def hdg_project(self, field, values_at_qp):
+        """L2 projection of samples at the volume quadrature points (field 0: velocity, values
+        [ncells][2][nq]; field 1: pressure, values [ncells][nq]) -> nodal Q or p."""
+        out = self.zeros()[field]
+        _check(load().hdg_project(self._ctx, field, _ptr(values_at_qp), _ptr(out)), 'hdg_project')
+        return out
 
     def hdg_set_forcing(self, F, phi=None):
         if F is None:
@@ -295,6 +306,14 @@ class Context:
         return ms.value, b.value
 
     def hdg_trace_apply_noalloc(self, c, lam, out):
-        """hdg_trace_apply without device allocation; out is a caller-owned trace-shaped tensor."""
+        """hdg_trace_apply without device allocation; out is a caller-owned trace-shaped tensor.
+        lam and out must hold nlambda doubles each, on the context's device."""
+        import torch
+        dev = torch.cuda.current_device()
+        for name, t in (('lam', lam), ('out', out)):
+            if t is None or t.numel() != self.nL:
+                raise ValueError(f'{name} must hold {self.nL} doubles')
+            if t.is_cuda and t.device.index != dev:
+                raise ValueError(f'{name} is on cuda:{t.device.index}, the current device is cuda:{dev}')
         _check(load().hdg_trace_apply_noalloc(self._ctx, c, _ptr(lam), _ptr(out)), 'hdg_trace_apply_noalloc')
         return out

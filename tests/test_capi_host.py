@@ -54,14 +54,14 @@ def test_default_params():
     assert p.alpha == 1.0 and p.tau == 1.0 and p.delta_up == 1.0 and p.n_richardson == 2
     assert p.trace_rtol == 1e-12 and p.stepI_rtol == 1e-10
     assert (p.stage_krylov, p.trace_mg, p.device_loops, p.inner_trace_vcycles) == (1, 1, 1, 1)
-    assert (p.inner_trace_fp32, p.trace_fp32_vcycle, p.inner_gs, p.persistent_stepI) == (1, 1, 1, 0)
+    assert (p.inner_trace_fp32, p.trace_fp32_vcycle, p.inner_gs, p.precision) == (1, 1, 1, 1)
     assert p.inner_stepI_rtol == 2e-2 and p.inner_trace_rtol == 1e-1
 
 
 def test_status_strings():
     lib = H.load()
-    for s in range(7):
-        assert lib.hdg_status_string(s)
+    for s in range(8):
+        assert lib.hdg_status_string(s).decode() != 'unknown status'
 
 
 @pytest.mark.parametrize('px,py', [(False, False), (True, False), (True, True)])
