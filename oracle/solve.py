@@ -45,14 +45,29 @@ class Oracle:
     def split(self, x):
         return x[:self.nQ], x[self.nQ:self.nQ + self.nP], x[self.nQ + self.nP:self.nQ + self.nY]
 
+    REFINE = 2          # steps of iterative refinement after each direct solve
+
     def _pinned_factor(self, A):
-        """LU of A without its last row and column (the last trace equation / unknown)."""
+        """LU of A without its last row and column (the last trace equation / unknown); the
+        reduced matrix is kept for the refinement steps."""
         n = A.shape[0] - 1
-        return spla.splu(sp.csc_matrix(A)[:n, :n])
+        Ar = sp.csc_matrix(A)[:n, :n]
+        lu = spla.splu(Ar)
+        return lu, Ar
 
     def _pinned_solve(self, lu, rhs):
+        """Solve with the pinned factorisation, then REFINE steps of iterative refinement
+        (x += LU^{-1}(b - A x) with the residual in FP64): the stage and mixed solutions are
+        defined as the exact solutions of their linear systems (eq. imex_implicit_solve), and the
+        LU's backward error in the Lagrange basis leaves relative residuals ~1e-11 that the
+        refinement removes (to ~1e-13)."""
+        lu, Ar = lu
+        b = rhs[:-1]
+        y = lu.solve(b)
+        for _ in range(self.REFINE):
+            y = y + lu.solve(b - Ar @ y)
         x = np.zeros(len(rhs))
-        x[:-1] = lu.solve(rhs[:-1])
+        x[:-1] = y
         Q, p, lam = self.split(x)
         shift = self.hdg.mean_p(p)
         return Q, p - shift, lam - shift
@@ -98,6 +113,8 @@ class Oracle:
             dr = r - self.M @ Q + c * (F @ Q + self.G @ y)
             rho = -(self.B @ Q + self.C @ y)
             Qbar = lu1.solve(dr)                                    # Step I
+            for _ in range(self.REFINE):
+                Qbar = Qbar + lu1.solve(dr - Ms @ Qbar)
             U, dp, dl = self.mixed_solve(c, np.zeros(self.nQ), rho - self.B @ Qbar)  # Step II
             dQ = Qbar + U                                           # Step III
             Q = Q + dQ
@@ -158,31 +175,51 @@ class Oracle:
                   richardson_kw=None, stats=None):
         """One step of Alg. 1. forcing(t) returns the dual vector (w . f(t)) or None.
         solver='direct' solves each stage system monolithically (the definition);
-        'richardson' uses Alg. 2 with the keyword arguments richardson_kw."""
+        'richardson' uses Alg. 2 with the keyword arguments richardson_kw.
+
+        Alg. 1 assumes an explicit first stage (a_00 = a_i0 = b_0 = 0, Q_0 = Q^n). The paper's
+        SSP2(3,3,2) and SSP3(4,3,3) tableaus (App. A) have an implicit first stage (a_00 != 0);
+        they are run with the same recursion extended to it: every stage i with a_ii != 0 is
+        solved with coefficient a_ii dt (stage 0 advected by P(Q^n)), and the sums of
+        eq. imex_residual and eq. final_residual run over every implicit stage j < i (or i),
+        j = 0 included. For a_00 = 0 this is Alg. 1 exactly."""
         hdg, M = self.hdg, self.M
         A, Ae, b, be, cc, s = tab.A_im, tab.A_ex, tab.b_im, tab.b_ex, tab.c, tab.s
         fl = (lambda tt: forcing(tt)) if forcing is not None else (lambda tt: 0.0)
+        MQn = M @ Q
         Qs, ps, ls, rs = [Q], [p], [lam], [None]
-        for i in range(1, s):
-            r = M @ Q
-            for j in range(1, i):
-                r = r + (A[i, j] / A[j, j]) * (M @ Qs[j] - rs[j])
+        implicit = [A[i, i] != 0.0 for i in range(s)]
+        if not implicit[0]:
+            assert np.all(A[:, 0] == 0.0) and b[0] == 0.0, 'explicit first stage needs a_i0 = b_0 = 0'
+        for i in range(s):
+            if i == 0 and not implicit[0]:
+                continue                                            # Q_0 = Q^n
+            assert implicit[i], 'only the first stage may be explicit'
+            r = MQn.copy()
+            for j in range(i):
+                if implicit[j] and A[i, j] != 0.0:
+                    r = r + (A[i, j] / A[j, j]) * (M @ Qs[j] - rs[j])
             for j in range(0, i):
                 if Ae[i, j] != 0.0:
                     r = r + dt * Ae[i, j] * fl(t + cc[j] * dt)
-            Qstar = bdm_project(hdg, Qs[i - 1])
+            Qprev, pprev, lprev = (Qs[i - 1], ps[i - 1], ls[i - 1]) if i > 0 else (Q, p, lam)
+            Qstar = bdm_project(hdg, Qprev)
             ci = A[i, i] * dt
             if solver == 'direct':
                 Qi, pi, li = self.stage_solve(ci, r, Qstar)
             else:
-                Qi, pi, li, nit = self.richardson(ci, r, Qstar, Qs[i - 1], ps[i - 1], ls[i - 1],
+                Qi, pi, li, nit = self.richardson(ci, r, Qstar, Qprev, pprev, lprev,
                                                   **(richardson_kw or {}))
                 if stats is not None:
                     stats.setdefault('richardson', []).append(nit)
-            Qs.append(Qi); ps.append(pi); ls.append(li); rs.append(r)
-        rn = M @ Q
-        for i in range(1, s):
-            rn = rn + (b[i] / A[i, i]) * (M @ Qs[i] - rs[i])
+            if i == 0:
+                Qs[0], ps[0], ls[0], rs[0] = Qi, pi, li, r
+            else:
+                Qs.append(Qi); ps.append(pi); ls.append(li); rs.append(r)
+        rn = MQn.copy()
+        for i in range(s):
+            if implicit[i] and b[i] != 0.0:
+                rn = rn + (b[i] / A[i, i]) * (M @ Qs[i] - rs[i])
         for i in range(0, s):
             if be[i] != 0.0:
                 rn = rn + dt * be[i] * fl(t + cc[i] * dt)
