@@ -423,8 +423,8 @@ def run_gpu(args, rank, world, local_rank):
         'config': cfg,
         'trace_dof_per_s': world * ntrace * trace_solves / (total_ms / 1e3),
         'per_step': per_step,
-        'e2e': {'value': world * stages / (e2e_mean / 1e3), 'unit': 'stage_solves/s', 'h2d_bytes_per_step': h2d,
-                'd2h_bytes_per_step': h2d},
+        'e2e': {'value': world * stages / (e2e_mean / 1e3) if e2e_mean > 0 else None, 'unit': 'stage_solves/s',
+                'h2d_bytes_per_step': h2d, 'd2h_bytes_per_step': h2d},
         'roofline': {'kernel': f"k_stage_apply<{w['k']}> (fused FP64 stage operator, the flexible GMRES product)",
                      'bound': 'alu', 'achieved': st_tflops, 'peak': FP64_NOMINAL_TFLOPS, 'unit': 'TFLOP/s',
                      'frac': st_tflops / FP64_NOMINAL_TFLOPS,

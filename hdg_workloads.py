@@ -55,6 +55,13 @@ def shear_layer(x, y, width=0.05, amp=1e-3):
     return np.tanh((y - 0.5) / width), amp * np.sin(2 * np.pi * x)
 
 
+def double_shear_layer(x, y, rho=np.pi / 15, delta=0.05):
+    """The doubly periodic double shear layer on [0, 2 pi]^2: u = tanh((y - pi/2)/rho) for
+    y <= pi, tanh((3 pi/2 - y)/rho) above; v = delta sin x."""
+    u = np.where(y <= np.pi, np.tanh((y - 0.5 * np.pi) / rho), np.tanh((1.5 * np.pi - y) / rho))
+    return u, delta * np.sin(x)
+
+
 def stream_function_modes(seed, n_modes=8, kmax=4):
     """(m1, m2, a) for psi = sum a sin(m1 pi x) sin(m2 pi y), a ~ N(0,1)/|m|^2."""
     rng = np.random.default_rng(seed)

@@ -55,7 +55,12 @@ typedef enum {
     HDG_ERR_TIMEOUT = 7        /* hdg_params.timeout_ms ran out before the GPU work finished */
 } hdg_status;
 
-typedef enum { HDG_ARS222 = 0, HDG_ARS343 = 1, HDG_IMEX_EULER = 2 } hdg_tableau;
+/* IMEX tableaus: ARS(2,2,2) and ARS(3,4,3) (Ascher, Ruuth and Spiteri 1997), and App. A's IMEX
+ * Euler, SSP2(3,3,2) (explicit abscissae read as (0, 1/2, 1)) and SSP3(4,3,3). The SSP tableaus
+ * have an implicit first stage (a_00 != 0), outside Alg. 1's assumed form: every stage with
+ * a_ii != 0 is solved (the first advected by P(Q^n)) and the sums of eq. imex_residual and
+ * eq. final_residual run over all implicit stages. */
+typedef enum { HDG_ARS222 = 0, HDG_ARS343 = 1, HDG_IMEX_EULER = 2, HDG_SSP2_332 = 3, HDG_SSP3_433 = 4 } hdg_tableau;
 
 typedef enum { HDG_FP64 = 0, HDG_MIXED = 1 } hdg_precision;
 

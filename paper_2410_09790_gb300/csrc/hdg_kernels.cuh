@@ -329,40 +329,67 @@ __global__ void k_cg_setup(const double *__restrict__ b, const double *__restric
 
 // pnew = z' + beta pold with z' = z - zmean e0 (z projected off the constant trace mode, the
 // kernel of S; without it the direction can drift into the kernel and p^T S p lose its sign);
-// Ap = S pnew; pAp -> alpha = rz / pAp
+// Ap = S pnew; pAp -> alpha = rz / pAp.
+// A facet is handled by a group of NT lanes (32 / NT facets per warp; lane i of a group owns row
+// i): for each of the facet's five block columns the group reads the neighbour facet's NT
+// direction entries once (lane j forms p_j from z and pold) and passes them to every row by warp
+// shuffles, so each row streams its 5 NT operator entries (consecutive rows at consecutive
+// addresses: coalesced) and no vector entry is read twice by a group. Grid: cg_apply_grid.
 template <int NT>
-__global__ void k_cg_apply(const double *__restrict__ Sell, const int *__restrict__ tcol,
-                           const double *__restrict__ z, const double *__restrict__ pold,
-                           double *__restrict__ pnew, double *__restrict__ Ap, int nfacets,
-                           RedBuf rb, Scalars *sc) {
+__global__ void __launch_bounds__(128) k_cg_apply(const double *__restrict__ Sell, const int *__restrict__ tcol,
+                                                  const double *__restrict__ z, const double *__restrict__ pold,
+                                                  double *__restrict__ pnew, double *__restrict__ Ap, int nfacets,
+                                                  RedBuf rb, Scalars *sc) {
     wait_prior_kernel();
     if (sc->done) return;
+    constexpr int GPW = 32 / NT;                       // facets per warp
     const double beta = sc->beta, zm = sc->zmean;
-    long long nrows = (long long)nfacets * NT;
+    const long long nrows = (long long)nfacets * NT;
+    const int lane = (int)(threadIdx.x & 31), q = lane / NT, i = lane - q * NT, base = q * NT;
+    const long long wpb = blockDim.x >> 5, nw = (long long)gridDim.x * wpb;
     double v[1] = {0.0}, tot[1];
-    GRID_STRIDE(g, nrows) {
-        int f = (int)(g / NT);
-        double s = 0;
+    for (long long w = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); w * GPW < nfacets; w += nw) {
+        const long long f0 = w * GPW + q;
+        const bool live = q < GPW && f0 < nfacets;
+        const int f = live ? (int)f0 : 0;              // dead lanes read row 0 and store nothing
+        const size_t g = (size_t)f * NT + i;
+        double s = 0.0, pn = 0.0;
 #pragma unroll
         for (int b = 0; b < 5; ++b) {
-            int cf = __ldg(&tcol[b * nfacets + f]);
-            if (cf < 0) continue;
+            const int cf = __ldg(&tcol[b * nfacets + f]);
+            double pv = 0.0;
+            if (cf >= 0) {
+                const size_t k = (size_t)cf * NT + i;
+                pv = z[k] - (i == 0 ? zm : 0.0) + beta * pold[k];
+            }
+            if (b == 0) pn = pv;                       // block 0 is the facet itself
 #pragma unroll
             for (int j = 0; j < NT; ++j) {
-                size_t k = (size_t)cf * NT + j;
-                s += __ldg(&Sell[(size_t)(b * NT + j) * nrows + g]) * (z[k] - (j == 0 ? zm : 0.0) + beta * pold[k]);
+                const double pj = __shfl_sync(0xffffffffu, pv, base + j);
+                if (cf >= 0) s += __ldg(&Sell[(size_t)(b * NT + j) * nrows + g]) * pj;
             }
         }
-        double pn = z[g] - ((g % NT) == 0 ? zm : 0.0) + beta * pold[g];
-        pnew[g] = pn;
-        Ap[g] = s;
-        v[0] += pn * s;
+        if (live) {
+            pnew[g] = pn;
+            Ap[g] = s;
+            v[0] += pn * s;
+        }
     }
     if (grid_sum<1>(rb, v, tot)) {
         sc->pAp = tot[0];
         if (tot[0] > 0.0 && isfinite(tot[0])) sc->alpha = sc->rz / tot[0];
         else { sc->alpha = 0.0; sc->done = 1; sc->breakdown = isfinite(tot[0]) ? 1 : 2; }
     }
+}
+
+// blocks of 128 threads for k_cg_apply: a warp per 32 / NT facets, at most MAX_RED_BLOCKS
+template <int NT>
+inline int cg_apply_grid(long long nfacets) {
+    const long long warps = (nfacets + 32 / NT - 1) / (32 / NT);
+    long long g = (warps + 3) / 4;
+    if (g < 1) g = 1;
+    if (g > MAX_RED_BLOCKS) g = MAX_RED_BLOCKS;
+    return (int)g;
 }
 
 // x += alpha p; r -= alpha Ap; z = Dinv r; rz_new -> beta, convergence

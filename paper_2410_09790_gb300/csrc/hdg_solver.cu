@@ -53,7 +53,8 @@ struct TimeoutError : std::runtime_error {
     } while (0)
 #define CKL() CK(cudaGetLastError())
 
-// IMEX tableaus (Alg. 1 form: stage 0 explicit, a_im[i][0] = b_im[0] = 0).
+// IMEX tableaus (Alg. 1 form: stage 0 explicit, a_im[i][0] = b_im[0] = 0; the SSP tableaus of
+// App. A have an implicit stage 0, see imex_step_body).
 struct Tab {
     int s = 0;
     double Ae[4][4] = {}, Ai[4][4] = {}, be[4] = {}, bi[4] = {}, c[4] = {};
@@ -88,6 +89,24 @@ Tab make_tableau(int which) {
         T.Ai[1][1] = 1.0; T.Ae[1][0] = 1.0;
         T.bi[1] = 1.0; T.be[0] = 1.0;
         T.c[1] = 1.0;
+    } else if (which == HDG_SSP2_332) {     // App. A, SSP2(3,3,2); explicit abscissae (0, 1/2, 1)
+        T.s = 3;
+        T.Ai[0][0] = 0.25; T.Ai[1][1] = 0.25;
+        T.Ai[2][0] = T.Ai[2][1] = T.Ai[2][2] = 1.0 / 3.0;
+        T.Ae[1][0] = 0.5; T.Ae[2][0] = 0.5; T.Ae[2][1] = 0.5;
+        for (int i = 0; i < 3; ++i) T.bi[i] = T.be[i] = 1.0 / 3.0;
+        T.c[1] = 0.5; T.c[2] = 1.0;
+    } else if (which == HDG_SSP3_433) {     // App. A, SSP3(4,3,3)
+        const double al = 0.24169426078821, be = 0.06042356519705, et = 0.12915286960590;
+        const double de = 0.5 - al - be - et;
+        T.s = 4;
+        T.Ai[0][0] = al;
+        T.Ai[1][0] = -al; T.Ai[1][1] = al;
+        T.Ai[2][1] = 1.0 - al; T.Ai[2][2] = al;
+        T.Ai[3][0] = be; T.Ai[3][1] = et; T.Ai[3][2] = de; T.Ai[3][3] = al;
+        T.Ae[2][1] = 1.0; T.Ae[3][1] = 0.25; T.Ae[3][2] = 0.25;
+        T.bi[1] = T.be[1] = 1.0 / 6.0; T.bi[2] = T.be[2] = 1.0 / 6.0; T.bi[3] = T.be[3] = 2.0 / 3.0;
+        T.c[2] = 1.0; T.c[3] = 0.5;
     } else {
         throw std::invalid_argument("unknown tableau");
     }
@@ -676,7 +695,7 @@ struct Impl {
                 [&](LoopCtl L) {
                     for (int m = 0; m < 2; ++m) {
                         double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
-                        launch_k(k_cg_apply<NT>, gr, VEC_THREADS, 0, c->st, E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
+                        launch_k(k_cg_apply<NT>, cg_apply_grid<NT>(nf), 128, 0, c->st, E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
                                                                      c->rb(), c->sc);
                         launch_k(k_cg_update<NT>, gf, VEC_THREADS, 0, c->st, E.Dinv, pnew, c->tAp, x, c->tr, c->tz, nf,
                                                                       c->rb(), c->sc);
@@ -693,7 +712,7 @@ struct Impl {
                 throw std::length_error("trace CG: no convergence flag from the device");
             for (int m = 0; m < chunk; ++m) {
                 double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
-                launch_k(k_cg_apply<NT>, gr, VEC_THREADS, 0, c->st, E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf, c->rb(), c->sc);
+                launch_k(k_cg_apply<NT>, cg_apply_grid<NT>(nf), 128, 0, c->st, E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf, c->rb(), c->sc);
                 launch_k(k_cg_update<NT>, gf, VEC_THREADS, 0, c->st, E.Dinv, pnew, c->tAp, x, c->tr, c->tz, nf, c->rb(), c->sc);
             }
             CKL();
@@ -753,7 +772,7 @@ struct Impl {
                 [&](LoopCtl L) {
                     for (int m = 0; m < 2; ++m) {
                         double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
-                        launch_k(k_cg_apply<NT>, gr, VEC_THREADS, 0, c->st, E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
+                        launch_k(k_cg_apply<NT>, cg_apply_grid<NT>(nf), 128, 0, c->st, E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
                                                                      c->rb(), c->sc);
                         if (f32) {
                             launch_k(k_cg_update_xr<NT>, gr, VEC_THREADS, 0, c->st, (const double *)pnew,
@@ -785,7 +804,7 @@ struct Impl {
             E.g_chunk = capture_graph(c, [&]() {
                 for (int m = 0; m < chunk; ++m) {
                     double *pold = c->tp[m & 1], *pnew = c->tp[(m + 1) & 1];
-                    launch_k(k_cg_apply<NT>, gr, VEC_THREADS, 0, c->st, E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
+                    launch_k(k_cg_apply<NT>, cg_apply_grid<NT>(nf), 128, 0, c->st, E.Sell, E.tcol, c->tz, pold, pnew, c->tAp, nf,
                                                                  c->rb(), c->sc);
                     if (f32) {
                         launch_k(k_cg_update_xr<NT>, gr, VEC_THREADS, 0, c->st, (const double *)pnew, (const double *)c->tAp,
@@ -1607,12 +1626,17 @@ struct Impl {
         CK(cudaMemcpyAsync(c->ps[0], c->p, sizeof(double) * c->nPv, cudaMemcpyDeviceToDevice, c->st));
         CK(cudaMemcpyAsync(c->ls[0], c->lam, sizeof(double) * c->nL, cudaMemcpyDeviceToDevice, c->st));
         int nc = 0;
-        for (int i = 1; i < s; ++i) {
+        // stages with a_ii != 0 are solved; the first stage is explicit (Q_0 = Q^n, Alg. 1) unless
+        // the tableau has a_00 != 0 (SSP2(3,3,2), SSP3(4,3,3)): then it is solved too, advected by
+        // P(Q^n), and every sum below runs over all implicit stages. M Q^n is read from the state,
+        // which the step overwrites only in the final update.
+        const int i0 = T.Ai[0][0] != 0.0 ? 0 : 1;
+        for (int i = i0; i < s; ++i) {
             // eq. imex_residual: r_i = M Q^n + sum_j (a_ij/a_jj)(M Q_j - r_j) + dt sum_j aex_ij (w.f_j)
             LinComb L = lincomb();
             int n = 0;
-            L.coef[n] = 1.0; L.vec[n] = c->Qs[0]; L.mass[n] = 1; ++n;
-            for (int j = 1; j < i; ++j) {
+            L.coef[n] = 1.0; L.vec[n] = c->Q; L.mass[n] = 1; ++n;
+            for (int j = i0; j < i; ++j) {
                 double w = T.Ai[i][j] / T.Ai[j][j];
                 if (w == 0.0) continue;
                 L.coef[n] = w; L.vec[n] = c->Qs[j]; L.mass[n] = 1; ++n;
@@ -1626,17 +1650,21 @@ struct Impl {
             L.nterms = n;
             launch_k(k_lincomb, grid_for(c->nQ), VEC_THREADS, 0, c->st, c->geo, NU, L, c->rs[i], c->ncells);
             CKL();
-            bdm(c, c->Qs[i - 1], c->q[5]);                                       // Q*_{i-1}
-            CK(cudaMemcpyAsync(c->Qs[i], c->Qs[i - 1], bq, cudaMemcpyDeviceToDevice, c->st));
-            CK(cudaMemcpyAsync(c->ps[i], c->ps[i - 1], sizeof(double) * c->nPv, cudaMemcpyDeviceToDevice, c->st));
-            CK(cudaMemcpyAsync(c->ls[i], c->ls[i - 1], sizeof(double) * c->nL, cudaMemcpyDeviceToDevice, c->st));
+            if (i > 0) {
+                bdm(c, c->Qs[i - 1], c->q[5]);                                   // Q*_{i-1}
+                CK(cudaMemcpyAsync(c->Qs[i], c->Qs[i - 1], bq, cudaMemcpyDeviceToDevice, c->st));
+                CK(cudaMemcpyAsync(c->ps[i], c->ps[i - 1], sizeof(double) * c->nPv, cudaMemcpyDeviceToDevice, c->st));
+                CK(cudaMemcpyAsync(c->ls[i], c->ls[i - 1], sizeof(double) * c->nL, cudaMemcpyDeviceToDevice, c->st));
+            } else {
+                bdm(c, c->Q, c->q[5]);                                           // P(Q^n); Q_0 starts at Q^n
+            }
             nc |= stage_solve(c, T.Ai[i][i] * dt, c->rs[i], c->q[5], c->Qs[i], c->ps[i], c->ls[i]);
         }
         // eq. final_residual and eq. final_update (coefficient b_{s-1}^im dt)
         LinComb L = lincomb();
         int n = 0;
-        L.coef[n] = 1.0; L.vec[n] = c->Qs[0]; L.mass[n] = 1; ++n;
-        for (int i = 1; i < s; ++i) {
+        L.coef[n] = 1.0; L.vec[n] = c->Q; L.mass[n] = 1; ++n;
+        for (int i = i0; i < s; ++i) {
             double w = T.bi[i] / T.Ai[i][i];
             if (w == 0.0) continue;
             L.coef[n] = w; L.vec[n] = c->Qs[i]; L.mass[n] = 1; ++n;
@@ -1671,7 +1699,8 @@ struct Impl {
         }
         if (!c->g_step) {
             const Tab &T = c->tab;                      // condensations the step uses, built first
-            for (int i = 1; i < T.s; ++i) ensure_pre_maps(c, T.Ai[i][i] * dt);
+            for (int i = 0; i < T.s; ++i)
+                if (T.Ai[i][i] != 0.0) ensure_pre_maps(c, T.Ai[i][i] * dt);
             condense(c, dt * T.bi[T.s - 1]);
             condense(c, 1.0);
             c->g_step = capture_graph(c, [&]() { imex_step_body(c, t0); }, &c->step_kernels);
@@ -1859,7 +1888,7 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
     if (params->n_richardson <= 0 && params->stage_krylov &&
         (!(params->inner_stepI_rtol > 0) || !(params->inner_trace_rtol > 0)))
         return HDG_ERR_INVALID_ARG;
-    if (params->tableau < HDG_ARS222 || params->tableau > HDG_IMEX_EULER) return HDG_ERR_INVALID_ARG;
+    if (params->tableau < HDG_ARS222 || params->tableau > HDG_SSP3_433) return HDG_ERR_INVALID_ARG;
     if (params->precision != HDG_FP64 && params->precision != HDG_MIXED) return HDG_ERR_INVALID_ARG;
     if (!(params->timeout_ms >= 0)) return HDG_ERR_INVALID_ARG;
     hdg_ctx *c = new (std::nothrow) hdg_ctx();
@@ -2481,9 +2510,9 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 Scalars h{};
                 h.done = 0; h.beta = 0.5; h.rz = 1.0; h.zmean = 0.0;
                 CK(cudaMemcpyAsync(c->sc, &h, sizeof(Scalars), cudaMemcpyHostToDevice, c->st));
-                const int nf = (int)c->nfacets, gr = grid_for(c->nL);
+                const int nf = (int)c->nfacets;
                 auto launch = [&]() {
-                    launch_k(k_cg_apply<I::NT>, gr, VEC_THREADS, 0, c->st, E.Sell, E.tcol, c->tz, c->tp[0], c->tp[1], c->tAp, nf,
+                    launch_k(k_cg_apply<I::NT>, cg_apply_grid<I::NT>(nf), 128, 0, c->st, E.Sell, E.tcol, c->tz, c->tp[0], c->tp[1], c->tAp, nf,
                                                                     c->rb(), c->sc);
                 };
                 launch();

@@ -23,7 +23,7 @@ class HdgError(RuntimeError):
 
 HDG_OK, HDG_ERR_INVALID_ARG, HDG_ERR_CUDA, HDG_ERR_OOM, HDG_ERR_NOT_CONVERGED, HDG_ERR_NUMERIC, \
     HDG_ERR_UNSUPPORTED, HDG_ERR_TIMEOUT = range(8)
-TABLEAUS = {'ARS222': 0, 'ARS343': 1, 'IMEX_EULER': 2}
+TABLEAUS = {'ARS222': 0, 'ARS343': 1, 'IMEX_EULER': 2, 'SSP2_332': 3, 'SSP3_433': 4}
 PRECISIONS = {'FP64': 0, 'MIXED': 1}
 
 
