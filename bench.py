@@ -295,11 +295,17 @@ def e2e_steps(ctx, nsteps, flush, dev):
 
 
 def golden_error(H, w, stream, kw):
-    """Error of one step of the workload on the stored oracle result at 32 x 32
-    (tests/golden/c2_step1_32.npz), per field; None if the file is absent."""
+    """Error of one step of the workload against the oracle's step stored by
+    tests/golden/make_c2_golden.py (on the workload's own mesh, else 32 x 32), per field; None if
+    no file is stored."""
     import numpy as np
-    path = os.path.join(ROOT, 'tests', 'golden', 'c2_step1_32.npz')
-    if not os.path.exists(path):
+    path = None
+    for n in (w['n'], 32):                            # the workload's own mesh when stored
+        cand = os.path.join(ROOT, 'tests', 'golden', f'c2_step1_{n}.npz')
+        if os.path.exists(cand):
+            path = cand
+            break
+    if path is None:
         return None
     g = np.load(path)
     n = int(g['meta'][0])

@@ -224,6 +224,24 @@ hdg_status hdg_project(hdg_ctx *ctx, int field, const double *values_at_qp, doub
  * memory); NULL phi means phi = 1. F = NULL removes the forcing. */
 hdg_status hdg_set_forcing(hdg_ctx *ctx, const double *F, double (*phi)(double t, void *user), void *user);
 
+/* Passive tracer (App. B): q in DG_k (nodal, device, the pressure layout double[ncells][(k+1)(k+2)/2])
+ * advected explicitly by every hdg_imex_step with the explicit tableau of the IMEX method:
+ *   q_i = q^n + dt sum_{j<i} a^ex_ij d_j,  q^{n+1} = q^n + dt sum_i b^ex_i d_i,
+ *   d_i = M^-1 a(., q_i, P_CG(Q_i)),  a(chi, q, U) = (q, div(chi U)) - sum over interior facets
+ *   <q^up [[chi U.n]]>  (q^up: the upwind value; U.n at a facet point averaged over its sides)
+ * (eq. advection_update_stages, eq. advection_update_final; the printed final sum starts at i = 1,
+ * which would leave IMEX Euler's tracer (b^ex = (1, 0)) unchanged: it is read from i = 0). Q_i are
+ * the step's stage velocities (Q_0 = Q^n for an explicit first stage). P_CG is the L2 projection
+ * onto the continuous space CG_{k+1} (Jacobi-preconditioned CG on the device, to 1e-13). Walls
+ * carry no tracer flux. q = NULL removes the tracer. */
+hdg_status hdg_set_tracer(hdg_ctx *ctx, const double *q);
+hdg_status hdg_get_tracer(hdg_ctx *ctx, double *q);
+/* Component entry points of the tracer: Qcg = P_CG(Q) (nodal DG velocities in and out; the output
+ * takes one value per lattice point shared by several cells), and dq = M^-1 a(., q, U) (nodal DG_k
+ * in and out) for a continuous velocity U (e.g. the output of hdg_cg_project). */
+hdg_status hdg_cg_project(hdg_ctx *ctx, const double *Q, double *Qcg);
+hdg_status hdg_tracer_rhs(hdg_ctx *ctx, const double *q, const double *U, double *dq);
+
 /* Alg. 1 x nsteps: s-1 stage solves (Alg. 2), final update (eq. final_update) and pressure
  * reconstruction (Sec. 2.7) per step, on the context's state. */
 hdg_status hdg_imex_step(hdg_ctx *ctx, int nsteps, hdg_stats *stats);

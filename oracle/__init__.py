@@ -10,3 +10,4 @@ from .hdg import HDG
 from .bdm import bdm_project
 from .tableaus import TABLEAUS, Tableau
 from .solve import Oracle
+from .tracer import Tracer

@@ -172,7 +172,7 @@ class Oracle:
 
     # ------------------------------------------------------------------ Alg. 1
     def imex_step(self, tab, dt, t, Q, p, lam, forcing=None, solver='direct',
-                  richardson_kw=None, stats=None):
+                  richardson_kw=None, stats=None, stages=None):
         """One step of Alg. 1. forcing(t) returns the dual vector (w . f(t)) or None.
         solver='direct' solves each stage system monolithically (the definition);
         'richardson' uses Alg. 2 with the keyword arguments richardson_kw.
@@ -182,7 +182,8 @@ class Oracle:
         they are run with the same recursion extended to it: every stage i with a_ii != 0 is
         solved with coefficient a_ii dt (stage 0 advected by P(Q^n)), and the sums of
         eq. imex_residual and eq. final_residual run over every implicit stage j < i (or i),
-        j = 0 included. For a_00 = 0 this is Alg. 1 exactly."""
+        j = 0 included. For a_00 = 0 this is Alg. 1 exactly. stages (a list, optional) receives the
+        stage velocities Q_0 .. Q_{s-1} (Q_0 = Q^n when the first stage is explicit)."""
         hdg, M = self.hdg, self.M
         A, Ae, b, be, cc, s = tab.A_im, tab.A_ex, tab.b_im, tab.b_ex, tab.c, tab.s
         fl = (lambda tt: forcing(tt)) if forcing is not None else (lambda tt: 0.0)
@@ -216,6 +217,8 @@ class Oracle:
                 Qs[0], ps[0], ls[0], rs[0] = Qi, pi, li, r
             else:
                 Qs.append(Qi); ps.append(pi); ls.append(li); rs.append(r)
+        if stages is not None:
+            stages.extend(Qs)
         rn = MQn.copy()
         for i in range(s):
             if implicit[i] and b[i] != 0.0:

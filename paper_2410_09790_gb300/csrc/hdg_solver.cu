@@ -25,6 +25,7 @@
 #include "hdg_mg_kernels.cuh"
 #include "hdg_mg32.cuh"
 #include "hdg_gs32.cuh"
+#include "hdg_tracer.cuh"
 #include "mesh.h"
 #include "refelem.h"
 
@@ -188,6 +189,13 @@ struct hdg_ctx {
     double *dfv = nullptr, *hfv = nullptr;
     double (*phi)(double, void *) = nullptr;
     void *phi_user = nullptr;
+    // passive tracer (App. B): state (modal DG_k), stage values / derivatives, advecting velocity
+    bool has_tracer = false;
+    double *qtr = nullptr, *tr_q = nullptr, *tr_dq[4] = {}, *tr_U = nullptr;
+    // continuous space CG_{k+1} for P_CG: numbering, Jacobi diagonal, Krylov vectors ([d][point])
+    CGMap cgm{};
+    double *cg_b = nullptr, *cg_u = nullptr, *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_Ap = nullptr,
+           *cg_w = nullptr;
     // Step I
     double *Dblk = nullptr, *Binv = nullptr, *wq = nullptr, *utr = nullptr;
     double *pen = nullptr;                                   // -c alpha fw_q of the assembled operator
@@ -481,6 +489,49 @@ void wait_stream(hdg_ctx *c) {
         }
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+}
+
+// The continuous space of P_CG (App. B), set up on first use (outside graph captures)
+void ensure_cg(hdg_ctx *c) {
+    if (c->cg_b) return;
+    if (c->capturing) throw std::logic_error("continuous space set up inside a graph capture");
+    const CGNumbering N = build_cg_numbering(c->H, c->K + 1);
+    const int nl = N.nl;
+    std::vector<double> dinv(N.npts, 0.0);
+    for (int pt = 0; pt < N.npts; ++pt) {
+        double dsum = 0.0;
+        for (int e = N.node_ptr[pt]; e < N.node_ptr[pt + 1]; ++e) {
+            const int ent = N.node_list[e], cell = ent / nl, l = ent % nl;
+            double s = 0.0;
+            for (int a = 0; a < nl; ++a) s += c->T.nod_u[a * nl + l] * c->T.nod_u[a * nl + l];
+            dsum += c->H.geo[cell].detJ * s;
+        }
+        dinv[pt] = 1.0 / dsum;
+    }
+    int *gid = c->alloc<int>(N.cell_gid.size()), *ptr = c->alloc<int>(N.node_ptr.size()),
+        *lst = c->alloc<int>(N.node_list.size());
+    double *dv = c->alloc<double>(N.npts);
+    CK(cudaMemcpy(gid, N.cell_gid.data(), N.cell_gid.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ptr, N.node_ptr.data(), N.node_ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(lst, N.node_list.data(), N.node_list.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dv, dinv.data(), dinv.size() * sizeof(double), cudaMemcpyHostToDevice));
+    c->cgm = CGMap{gid, ptr, lst, dv, N.npts, nl, (int)c->ncells};
+    const size_t n2 = 2 * (size_t)N.npts;
+    c->cg_u = c->alloc<double>(n2); c->cg_r = c->alloc<double>(n2); c->cg_z = c->alloc<double>(n2);
+    c->cg_p = c->alloc<double>(n2); c->cg_Ap = c->alloc<double>(n2);
+    c->cg_w = c->alloc<double>((size_t)c->ncells * 2 * nl);
+    c->cg_b = c->alloc<double>(n2);
+    CK(cudaMemset(c->cg_p, 0, n2 * sizeof(double)));
+}
+
+// Buffers of the tracer (one DG_k field and its stage values)
+void ensure_tracer_buffers(hdg_ctx *c) {
+    ensure_cg(c);
+    if (c->qtr) return;
+    c->qtr = c->alloc<double>(c->nPv);
+    c->tr_q = c->alloc<double>(c->nPv);
+    for (auto &x : c->tr_dq) x = c->alloc<double>(c->nPv);
+    c->tr_U = c->alloc<double>(c->nQ);
 }
 
 template <int K>
@@ -1595,6 +1646,91 @@ struct Impl {
         mean_shift(c, p, lam);
     }
 
+    // ---------------------------------------------------------------- tracer (App. B)
+    // U = P_CG(Q) in each cell's modal basis (Q modal): Jacobi-preconditioned CG to 1e-13 on the
+    // continuous space, a device-side loop when recording a graph
+    static void cg_project(hdg_ctx *c, const double *Qm, double *Um) {
+        const CGMap &C = c->cgm;
+        const long long n2 = 2LL * C.npts;
+        const int g = grid_for(n2);
+        const unsigned cb = cell_blocks(c);
+        const size_t smem = sizeof(double) * TEAMS_PER_BLOCK * 4 * MU;
+        launch_k(k_cgp_rhs, grid_for(n2), VEC_THREADS, 0, c->st, c->geo, c->R.nod_u, C, Qm, c->cg_b);
+        launch_k(k_cgp_start, g, VEC_THREADS, 0, c->st, C, (const double *)c->cg_b, c->cg_u, c->cg_r, c->cg_z, c->rb(),
+                 c->sc, 1e-13, 400);
+        auto iteration = [&]() {
+            launch_k(k_cgp_cell<K>, cb, 128, smem, c->st, c->M, c->R.nod_u, C, (const double *)c->cg_z,
+                     (const double *)c->cg_p, c->cg_w, (const Scalars *)c->sc);
+            launch_k(k_cgp_gather, g, VEC_THREADS, 0, c->st, C, (const double *)c->cg_w, (const double *)c->cg_z, c->cg_p,
+                     c->cg_Ap, c->rb(), c->sc);
+            launch_k(k_cgp_update, g, VEC_THREADS, 0, c->st, C, (const double *)c->cg_p, (const double *)c->cg_Ap,
+                     c->cg_u, c->cg_r, c->cg_z, c->rb(), c->sc);
+        };
+        if (c->capturing) {
+            capture_while(
+                c, [&](LoopCtl L) { launch_k(k_loop_init, 1, 1, 0, c->st, L, &c->sc->done); },
+                [&](LoopCtl L) {
+                    iteration();
+                    iteration();
+                    launch_k(k_loop_ctl, 1, 1, 0, c->st, L, 400 / 2 + 2, &c->sc->done);
+                });
+        } else {
+            for (int chunk = 0;; ++chunk) {
+                if (chunk > 400 / 8 + 2) throw std::length_error("P_CG: no convergence flag from the device");
+                for (int it = 0; it < 8; ++it) iteration();
+                CKL();
+                read_scalars(c);
+                if (c->hsc->done) break;
+            }
+            if (c->hsc->breakdown == 2) throw std::domain_error("P_CG: non-finite residual");
+        }
+        launch_k(k_cgp_to_modal<K>, grid_for((long long)c->ncells * 2 * MU), VEC_THREADS, 0, c->st, c->R.nod_u, C,
+                 (const double *)c->cg_u, Um);
+        CKL();
+    }
+
+    static void tracer_rhs(hdg_ctx *c, const double *q, const double *Um, double *out) {
+        launch_k(k_tracer_rhs<K>, cell_blocks(c), 128, sizeof(double) * TEAMS_PER_BLOCK * (3 * Dm::NQ + 3 * Dm::NFQ),
+                 c->st, c->R, c->M, q, Um, out);
+        CKL();
+    }
+
+    // eq. advection_update_stages / eq. advection_update_final with the explicit tableau, advected
+    // by P_CG of the step's stage velocities (Q_0 = Q^n for an explicit first stage); the final sum
+    // includes i = 0 (see hdg.h)
+    static void tracer_step(hdg_ctx *c) {
+        const Tab &T = c->tab;
+        const double dt = c->P.dt;
+        const int s = T.s;
+        for (int i = 0; i < s; ++i) {
+            bool need = T.be[i] != 0.0;
+            for (int r = i + 1; r < s; ++r) need = need || T.Ae[r][i] != 0.0;
+            const double *qi = c->qtr;
+            LinComb L = lincomb();
+            int n = 0;
+            L.coef[n] = 1.0; L.vec[n] = c->qtr; L.mass[n] = 0; ++n;
+            for (int j = 0; j < i; ++j)
+                if (T.Ae[i][j] != 0.0) { L.coef[n] = dt * T.Ae[i][j]; L.vec[n] = c->tr_dq[j]; L.mass[n] = 0; ++n; }
+            if (n > 1 && need) {
+                L.nterms = n;
+                launch_k(k_lincomb, grid_for(c->nPv), VEC_THREADS, 0, c->st, c->geo, NP, L, c->tr_q, c->ncells);
+                CKL();
+                qi = c->tr_q;
+            }
+            if (!need) continue;
+            cg_project(c, c->Qs[i], c->tr_U);
+            tracer_rhs(c, qi, c->tr_U, c->tr_dq[i]);
+        }
+        LinComb L = lincomb();
+        int n = 0;
+        L.coef[n] = 1.0; L.vec[n] = c->qtr; L.mass[n] = 0; ++n;
+        for (int i = 0; i < s; ++i)
+            if (T.be[i] != 0.0) { L.coef[n] = dt * T.be[i]; L.vec[n] = c->tr_dq[i]; L.mass[n] = 0; ++n; }
+        L.nterms = n;
+        launch_k(k_lincomb, grid_for(c->nPv), VEC_THREADS, 0, c->st, c->geo, NP, L, c->qtr, c->ncells);
+        CKL();
+    }
+
     // Time factors of the forcing f(t) = phi(t) F for the step from t0: out[i] = dt sum_j a^ex_ij
     // phi(t0 + c_j dt) for stage i (eq. imex_residual), out[s] = dt sum_i b^ex_i phi(t0 + c_i dt)
     // (eq. final_residual), out[7] = phi(t0 + dt) (the reconstruction at the new time).
@@ -1681,6 +1817,7 @@ struct Impl {
         CKL();
         mixed_solve(c, dt * T.bi[s - 1], rn, nullptr, nullptr, nullptr, c->Q, c->pp[1], c->ll[1]);
         reconstruct(c, c->Q, t0 + dt, c->p, c->lam);                            // Sec. 2.7
+        if (c->has_tracer) tracer_step(c);                                       // App. B
         return nc;
     }
 
@@ -2143,6 +2280,79 @@ hdg_status hdg_project(hdg_ctx *c, int field, const double *values_at_qp, double
                  nvec);
         CKL();
         DISPATCH(c, I::to_nodal(c, modal, dofs, field));
+        CK(cudaStreamSynchronize(c->st));
+    } catch (...) {
+        return map_exception();
+    }
+    return HDG_OK;
+}
+
+hdg_status hdg_set_tracer(hdg_ctx *c, const double *q) {
+    if (!c) return HDG_ERR_INVALID_ARG;
+    try {
+        settle_pending(c);
+        if (c->g_step) {                      // the recorded step depends on the tracer
+            CK(cudaStreamSynchronize(c->st));
+            CK(cudaGraphExecDestroy(c->g_step));
+            c->g_step = nullptr;
+        }
+        if (!q) {
+            c->has_tracer = false;
+            return HDG_OK;
+        }
+        ensure_tracer_buffers(c);
+        DISPATCH(c, I::to_modal(c, q, c->qtr, 1));
+        c->has_tracer = true;
+        CK(cudaStreamSynchronize(c->st));
+    } catch (...) {
+        return map_exception();
+    }
+    return HDG_OK;
+}
+
+hdg_status hdg_get_tracer(hdg_ctx *c, double *q) {
+    if (!c || !q) return HDG_ERR_INVALID_ARG;
+    if (!c->has_tracer) {
+        g_last_error = "hdg_get_tracer: no tracer set";
+        return HDG_ERR_INVALID_ARG;
+    }
+    try {
+        settle_pending(c);
+        DISPATCH(c, I::to_nodal(c, c->qtr, q, 1));
+        CK(cudaStreamSynchronize(c->st));
+    } catch (...) {
+        return map_exception();
+    }
+    return HDG_OK;
+}
+
+hdg_status hdg_cg_project(hdg_ctx *c, const double *Q, double *Qcg) {
+    if (!c || !Q || !Qcg) return HDG_ERR_INVALID_ARG;
+    try {
+        settle_pending(c);
+        ensure_tracer_buffers(c);
+        DISPATCH(c, {
+            I::to_modal(c, Q, c->q[0], 0);
+            I::cg_project(c, c->q[0], c->q[1]);
+            I::to_nodal(c, c->q[1], Qcg, 0);
+        });
+        CK(cudaStreamSynchronize(c->st));
+    } catch (...) {
+        return map_exception();
+    }
+    return HDG_OK;
+}
+
+hdg_status hdg_tracer_rhs(hdg_ctx *c, const double *q, const double *U, double *dq) {
+    if (!c || !q || !U || !dq) return HDG_ERR_INVALID_ARG;
+    try {
+        settle_pending(c);
+        DISPATCH(c, {
+            I::to_modal(c, q, c->pp[0], 1);
+            I::to_modal(c, U, c->q[0], 0);
+            I::tracer_rhs(c, c->pp[0], c->q[0], c->pp[1]);
+            I::to_nodal(c, c->pp[1], dq, 1);
+        });
         CK(cudaStreamSynchronize(c->st));
     } catch (...) {
         return map_exception();

@@ -146,4 +146,37 @@ HostMesh build_mesh(int n, double Lx, double Ly, bool px, bool py) {
     return M;
 }
 
+CGNumbering build_cg_numbering(const HostMesh &M, int m) {
+    if (m < 1) throw std::runtime_error("CG degree must be >= 1");
+    CGNumbering C;
+    const int n = M.n, nm = n * m;
+    const int NX = M.px ? nm : nm + 1, NY = M.py ? nm : nm + 1;
+    C.m = m;
+    C.nl = (m + 1) * (m + 2) / 2;
+    C.npts = NX * NY;
+    C.cell_gid.resize((size_t)M.ncells * C.nl);
+    for (int cj = 0; cj < n; ++cj)
+        for (int ci = 0; ci < n; ++ci)
+            for (int t = 0; t < 2; ++t) {
+                const int c = 2 * (cj * n + ci) + t;
+                int l = 0;
+                for (int j = 0; j <= m; ++j)
+                    for (int i = 0; i + j <= m; ++i, ++l) {
+                        // lower cell (A, B, C): A + h ((i + j)/m, j/m); upper (A, C, D): A + h (i/m, (i + j)/m)
+                        int I = m * ci + (t == 0 ? i + j : i), J = m * cj + (t == 0 ? j : i + j);
+                        if (M.px) I %= NX;
+                        if (M.py) J %= NY;
+                        C.cell_gid[(size_t)c * C.nl + l] = J * NX + I;
+                    }
+            }
+    std::vector<int> count(C.npts + 1, 0);
+    for (int g : C.cell_gid) ++count[g + 1];
+    for (int p = 0; p < C.npts; ++p) count[p + 1] += count[p];
+    C.node_ptr = count;
+    C.node_list.resize(C.cell_gid.size());
+    std::vector<int> fill(count.begin(), count.end() - 1);
+    for (size_t e = 0; e < C.cell_gid.size(); ++e) C.node_list[fill[C.cell_gid[e]]++] = (int)e;
+    return C;
+}
+
 }  // namespace hdg

@@ -43,4 +43,15 @@ struct HostMesh {
 int64_t mesh_facet_count(int n, bool px, bool py);
 HostMesh build_mesh(int n, double Lx, double Ly, bool px, bool py);
 
+// The continuous space CG_m on the mesh (App. B: the tracer's advecting velocity). The points of
+// the cells' equispaced degree-m lattices lie on the grid of spacing (Lx, Ly) / (n m); a point is
+// numbered J * NX + I (periodic directions wrapped, NX = n m or n m + 1). cell_gid[c][l]: the
+// point of lattice node l of cell c (nodes j outer, i inner, i + j <= m); node_ptr / node_list:
+// for every point the entries c * nl + l that share it (CSR, ascending).
+struct CGNumbering {
+    int m = 0, nl = 0, npts = 0;
+    std::vector<int> cell_gid, node_ptr, node_list;
+};
+CGNumbering build_cg_numbering(const HostMesh &M, int m);
+
 }  // namespace hdg

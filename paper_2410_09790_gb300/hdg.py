@@ -78,6 +78,10 @@ _SIGNATURES = {
     'hdg_set_state': (_I, [_P, _P, _P, _P, _D]),
     'hdg_get_state': (_I, [_P, _P, _P, _P, _DP]),
     'hdg_project': (_I, [_P, _I, _P, _P]),
+    'hdg_set_tracer': (_I, [_P, _P]),
+    'hdg_get_tracer': (_I, [_P, _P]),
+    'hdg_cg_project': (_I, [_P, _P, _P]),
+    'hdg_tracer_rhs': (_I, [_P, _P, _P, _P]),
     'hdg_set_forcing': (_I, [_P, _P, PHI, _P]),
     'hdg_imex_step': (_I, [_P, _I, ctypes.POINTER(hdg_stats)]),
     'hdg_solve_stage': (_I, [_P, _D, _P, _P, _P, _P, _P, ctypes.POINTER(hdg_stats)]),
@@ -236,6 +240,24 @@ class Context:
         [ncells][2][nq]; field 1: pressure, values [ncells][nq]) -> nodal Q or p."""
         out = self.zeros()[field]
         _check(load().hdg_project(self._ctx, field, _ptr(values_at_qp), _ptr(out)), 'hdg_project')
+        return out
+
+    def hdg_set_tracer(self, q):
+        _check(load().hdg_set_tracer(self._ctx, _ptr(q)), 'hdg_set_tracer')
+
+    def hdg_get_tracer(self):
+        out = self.zeros()[1]
+        _check(load().hdg_get_tracer(self._ctx, _ptr(out)), 'hdg_get_tracer')
+        return out
+
+    def hdg_cg_project(self, Q):
+        out = self.zeros()[0]
+        _check(load().hdg_cg_project(self._ctx, _ptr(Q), _ptr(out)), 'hdg_cg_project')
+        return out
+
+    def hdg_tracer_rhs(self, q, U):
+        out = self.zeros()[1]
+        _check(load().hdg_tracer_rhs(self._ctx, _ptr(q), _ptr(U), _ptr(out)), 'hdg_tracer_rhs')
         return out
 
     def hdg_set_forcing(self, F, phi=None):

@@ -6,8 +6,8 @@ The oracle's direct stage solve takes minutes at this size, so the stage solve i
 through a property that holds at any size: the oracle's own stage matrix applied to the GPU
 result leaves a residual at the level the outer tolerance allows. The cell-local rows (BDM
 projection, f^impl) are compared element by element over every cell. A whole IMEX step of the
-same workload is compared element by element on 32 x 32 against the oracle's step stored by
-tests/golden/make_c2_golden.py.
+workload is compared element by element, on 32 x 32 and on the full 64 x 64 mesh, against the
+oracle's steps stored by tests/golden/make_c2_golden.py.
 """
 import os
 
@@ -95,7 +95,7 @@ def test_full_size_stage_solve_oracle_residual(c2):
     assert abs(h.p_integral_vector() @ _host(pd)) <= 1e-12 * max(1.0, np.abs(_host(pd)).max())
 
 
-GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), 'golden', 'c2_step1_32.npz')
+GOLDEN_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), 'golden')
 
 
 # (stage rtol, trace and Step-I rtol, bars). The bench's settings: stages to 1e-10 on the stage
@@ -115,11 +115,13 @@ CASES = [(1e-10, 1e-12, {'Q': ('velocity-scale', 1e-9), 'p': ('velocity-scale', 
 
 @pytest.mark.parametrize('stage_rtol,inner_rtol,bars', CASES)
 @pytest.mark.parametrize('prec', ['MIXED', 'FP64'])
-def test_one_step_of_the_workload_against_stored_oracle_step(stage_rtol, inner_rtol, bars, prec):
-    # the bench's workload on 32 x 32 (tests/golden/make_c2_golden.py: the oracle's divergence-free
-    # projection, pressure reconstruction and one IMEX step with monolithic direct stage solves),
-    # compared element by element with the GPU step launched as the bench launches it
-    g = np.load(GOLDEN)
+@pytest.mark.parametrize('nmesh', [32, 64])
+def test_one_step_of_the_workload_against_stored_oracle_step(stage_rtol, inner_rtol, bars, prec, nmesh):
+    # the bench's workload on 32 x 32 and on its own 64 x 64 mesh (tests/golden/make_c2_golden.py:
+    # the oracle's divergence-free projection, pressure reconstruction and one IMEX step with
+    # monolithic direct stage solves), compared element by element with the GPU step launched as
+    # the bench launches it
+    g = np.load(os.path.join(GOLDEN_DIR, f'c2_step1_{nmesh}.npz'))
     n, k, dt, width, amp, noise, seed = g['meta']
     n, k, seed = int(n), int(k), int(seed)
     ctx = _mod().Context(n, k, periodic_x=True, tableau='ARS343', dt=float(dt), n_richardson=0, stage_krylov=1,
