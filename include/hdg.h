@@ -36,6 +36,7 @@
 #ifndef HDG_GB300_H
 #define HDG_GB300_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -223,6 +224,55 @@ hdg_status hdg_project(hdg_ctx *ctx, int field, const double *values_at_qp, doub
  * step recorded as a CUDA graph, before the graph's launch: the graph reads the values from device
  * memory); NULL phi means phi = 1. F = NULL removes the forcing. */
 hdg_status hdg_set_forcing(hdg_ctx *ctx, const double *F, double (*phi)(double t, void *user), void *user);
+
+/* Several contexts advanced together: nsteps steps of Alg. 1 for each context. Per step, every
+ * context's step (recorded as one CUDA graph, see device_loops) is enqueued on its own stream
+ * before any is waited for, so independent instances of different mesh sizes and degrees run on
+ * the GPU at the same time; contexts whose steps cannot be one graph take theirs synchronously in
+ * turn. Each result is the one hdg_imex_step gives for that context alone (bitwise: the kernels
+ * are deterministic and the contexts share no buffers). Contexts should have distinct streams
+ * (shared streams serialise their work). stats: n entries or NULL. The paper has no counterpart
+ * (it times one run at a time). Returns the first error met; HDG_ERR_NOT_CONVERGED if any context's
+ * stage solves stopped at their cap. */
+hdg_status hdg_batch_step(hdg_ctx *const *ctxs, int n, int nsteps, hdg_stats *stats);
+/* Device bytes the context has allocated so far (host query). */
+size_t hdg_ctx_bytes(const hdg_ctx *ctx);
+/* Upper estimate (bytes) of the device memory of a context with this mesh and these parameters
+ * once it has taken IMEX steps (host-only; 0 for invalid arguments). */
+double hdg_estimate_bytes(const hdg_mesh_desc *mesh, const hdg_params *params);
+
+/* Serving runtime: independent Euler runs ("requests": a mesh, parameters, an initial velocity
+ * and a number of IMEX steps) of different sizes and degrees, admitted in arrival order while the
+ * device-memory budget (hdg_estimate_bytes of the request's configuration, plus the bytes every
+ * context holds) and the slot limit allow, and advanced together with continuous batching: each
+ * call of hdg_server_progress admits what fits, takes one step of every active request at once
+ * (hdg_batch_step) and retires the requests that have taken their steps. Contexts stay resident
+ * on the device with their condensed operators and recorded step graphs: a retired request's
+ * context is kept idle and reused by the next request with the same configuration (mesh and
+ * parameters), and idle contexts are released, least recently used first, when an admission
+ * needs their memory. Each request's result equals the result of running it alone. One host
+ * thread at a time per server. The paper has no counterpart. */
+typedef struct hdg_server hdg_server;
+typedef struct {
+    int submitted, admitted, completed, active, queued;
+    int contexts_created, contexts_reused, contexts_released;
+    double bytes_in_use;        /* device bytes held by the server's contexts (active and idle) */
+    long long steps;            /* IMEX steps taken over all requests */
+    long long stage_solves;     /* stage solves over all requests */
+} hdg_server_stats;
+hdg_status hdg_server_create(hdg_server **out, int device, double mem_budget_bytes, int max_active);
+/* Q0_host: the request's initial velocity (host, nodal, the Q layout); it is copied. The initial
+ * state is (Q0, p = 0, lambda = 0) projected to be divergence-free with its pressure reconstructed
+ * (hdg_div_free_project) before the first step. id: the request's number. */
+hdg_status hdg_server_submit(hdg_server *srv, const hdg_mesh_desc *mesh, const hdg_params *params,
+                             const double *Q0_host, int nsteps, long long *id);
+hdg_status hdg_server_progress(hdg_server *srv, hdg_server_stats *stats);
+/* A completed request's result (host arrays in the exchange layouts, any may be NULL) and its
+ * latency from submission to completion in ms (host clock); releases the result. HDG_ERR_INVALID_ARG
+ * if the request is unknown or not complete. */
+hdg_status hdg_server_result(hdg_server *srv, long long id, double *Q_host, double *p_host, double *lam_host,
+                             double *latency_ms);
+void hdg_server_destroy(hdg_server *srv);
 
 /* Passive tracer (App. B): q in DG_k (nodal, device, the pressure layout double[ncells][(k+1)(k+2)/2])
  * advected explicitly by every hdg_imex_step with the explicit tableau of the IMEX method:

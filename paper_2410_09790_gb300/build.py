@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, 'csrc')
 LIB = os.path.join(HERE, 'libhdg_gb300.so')
 BUILD = os.path.join(HERE, '_build')
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
-SOURCES = ['hdg_solver.cu', 'refelem.cpp', 'mesh.cpp']
+SOURCES = ['hdg_solver.cu', 'refelem.cpp', 'mesh.cpp', 'hdg_server.cpp']
 
 
 def _nvcc():

@@ -12,6 +12,7 @@
 #include <deque>
 #include <exception>
 #include <mutex>
+#include <algorithm>
 #include <chrono>
 #include <thread>
 #include <new>
@@ -266,10 +267,13 @@ struct hdg_ctx {
     template <class T_>
     T_ *alloc(size_t n) {
         void *p_ = nullptr;
-        CK(cudaMalloc(&p_, n * sizeof(T_) > 0 ? n * sizeof(T_) : 16));
+        const size_t b_ = n * sizeof(T_) > 0 ? n * sizeof(T_) : 16;
+        CK(cudaMalloc(&p_, b_));
         allocs.push_back(p_);
+        bytes += b_;
         return (T_ *)p_;
     }
+    size_t bytes = 0;                                        // device bytes allocated by alloc()
     RedBuf rb() const { return RedBuf{partials, counter}; }
 };
 
@@ -1827,13 +1831,10 @@ struct Impl {
         return c->P.device_loops && c->P.n_richardson <= 0 && c->P.stage_krylov;
     }
 
-    static int imex_step(hdg_ctx *c) {
+    // One step as the graph: prepare (first call: condensations and capture) and enqueue it on the
+    // context's stream without waiting; step_finish waits for it and does the bookkeeping.
+    static void step_enqueue(hdg_ctx *c) {
         const double t0 = c->t, dt = c->P.dt;
-        if (!step_graph_ok(c)) {
-            int nc = imex_step_body(c, t0);
-            c->t = t0 + dt;
-            return nc;
-        }
         if (!c->g_step) {
             const Tab &T = c->tab;                      // condensations the step uses, built first
             for (int i = 0; i < T.s; ++i)
@@ -1852,14 +1853,28 @@ struct Impl {
         CK(cudaMemcpyAsync(c->hstat, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st));
         c->pending = true;
         c->pending_t = t0 + dt;
+    }
+
+    static int step_finish(hdg_ctx *c) {
         wait_stream(c);
         c->pending = false;
         c->deadline = 0;
         const int hstat = *c->hstat;
         if (hstat) throw std::domain_error("singular tentative-velocity block");
         graph_stats(c, c->step_kernels);
-        c->t = t0 + dt;
+        c->t = c->pending_t;
         return c->hcnt->stage_unconverged ? 1 : 0;
+    }
+
+    static int imex_step(hdg_ctx *c) {
+        const double t0 = c->t, dt = c->P.dt;
+        if (!step_graph_ok(c)) {
+            int nc = imex_step_body(c, t0);
+            c->t = t0 + dt;
+            return nc;
+        }
+        step_enqueue(c);
+        return step_finish(c);
     }
 };
 
@@ -2401,6 +2416,101 @@ hdg_status hdg_imex_step(hdg_ctx *c, int nsteps, hdg_stats *stats) {
         return s;
     }
     return nc ? HDG_ERR_NOT_CONVERGED : HDG_OK;
+}
+
+hdg_status hdg_batch_step(hdg_ctx *const *ctxs, int n, int nsteps, hdg_stats *stats) {
+    if (!ctxs || n < 0 || nsteps < 0) return HDG_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i]) return HDG_ERR_INVALID_ARG;
+    std::vector<int> nc(n, 0), graph(n, 0);
+    hdg_status first_err = HDG_OK;
+    auto fail = [&](int i) {
+        hdg_status s = map_exception();
+        if (stats) stats[i] = ctxs[i]->S;
+        if (first_err == HDG_OK) first_err = s;
+    };
+    for (int i = 0; i < n; ++i) {
+        try {
+            begin_call(ctxs[i]);
+            DISPATCH(ctxs[i], graph[i] = I::step_graph_ok(ctxs[i]) ? 1 : 0);
+        } catch (...) {
+            fail(i);
+            return first_err;
+        }
+    }
+    for (int s = 0; s < nsteps && first_err == HDG_OK; ++s) {
+        // enqueue every context's step graph (each on its own stream), then wait for them in turn;
+        // contexts whose steps cannot be one graph run their step synchronously here
+        for (int i = 0; i < n && first_err == HDG_OK; ++i) {
+            try {
+                if (graph[i]) {
+                    DISPATCH(ctxs[i], I::step_enqueue(ctxs[i]));
+                } else {
+                    DISPATCH(ctxs[i], nc[i] |= I::imex_step(ctxs[i]));
+                }
+            } catch (...) {
+                fail(i);
+            }
+        }
+        for (int i = 0; i < n; ++i) {
+            if (!graph[i] || !ctxs[i]->pending) continue;
+            try {
+                DISPATCH(ctxs[i], nc[i] |= I::step_finish(ctxs[i]));
+            } catch (...) {
+                fail(i);
+            }
+        }
+    }
+    if (first_err != HDG_OK) return first_err;
+    int any = 0;
+    for (int i = 0; i < n; ++i) {
+        try {
+            end_call(ctxs[i], stats ? &stats[i] : nullptr);
+        } catch (...) {
+            fail(i);
+            return first_err;
+        }
+        any |= nc[i];
+    }
+    return any ? HDG_ERR_NOT_CONVERGED : HDG_OK;
+}
+
+size_t hdg_ctx_bytes(const hdg_ctx *c) { return c ? c->bytes : 0; }
+
+// Upper estimate of a context's device memory once it has taken IMEX steps: the buffers allocated
+// at set-up plus the per-coefficient operators (one condensation per distinct implicit diagonal,
+// the final update and the reconstruction; FP32 cell maps and multigrid copies for the stage
+// coefficients), with 15 % for the small tables and work vectors not counted term by term.
+double hdg_estimate_bytes(const hdg_mesh_desc *mesh, const hdg_params *params) {
+    if (!mesh || !params || mesh->n < 1 || params->k < 1 || params->k > 4) return 0.0;
+    const double k = params->k, n = mesh->n;
+    const double MU = (k + 2) * (k + 3) / 2, NU = 2 * MU, NP = (k + 1) * (k + 2) / 2, NT = k + 1, NL = 3 * NT;
+    const double nc = 2 * n * n, nf = (double)mesh_facet_count(mesh->n, mesh->periodic_x != 0, mesh->periodic_y != 0);
+    const double nQ = nc * NU, nP = nc * NP, nL = nf * NT, N = nQ + nP + nL;
+    const double nfq = std::floor((3 * k + 5) / 2);
+    Tab T;
+    try {
+        T = make_tableau(params->tableau);
+    } catch (...) {
+        return 0.0;
+    }
+    std::vector<double> cs;
+    for (int i = 0; i < T.s; ++i)
+        if (T.Ai[i][i] != 0.0 && std::find(cs.begin(), cs.end(), T.Ai[i][i]) == cs.end()) cs.push_back(T.Ai[i][i]);
+    const double nstage_c = (double)cs.size(), ncond = nstage_c + 2;
+    double b = 0;
+    b += 8 * ((T.s + 1) * (nQ + nP + nL) + T.s * nQ + nQ);                 // state, stages, forcing
+    b += 8 * 2 * NU * nQ + 4 * NU * nQ;                                    // Dblk, Binv, Binv32
+    b += 8 * 3 * nc * 3 * nfq * 2 + 4 * 3 * nc * 3 * nfq * 2;             // weights, edge values
+    b += 4 * (32 + 2) * nQ + 8 * (32 + 5) * nQ;                            // Step-I Krylov (FP32, FP64)
+    if (params->n_richardson <= 0 && params->stage_krylov)
+        b += 8 * (31 + 30 + 7) * N + 4 * 32 * N;                           // stage FGMRES
+    b += 8 * (8 * nQ + 3 * nP + 3 * nL + nc * NL + 10 * nL);               // temporaries, trace work
+    b += ncond * 8 * (nc * (NL * NL + NP * NL + NP * NP) + 6 * NT * nL) + ncond * 4 * 5 * nf;
+    if (params->precision == HDG_MIXED)
+        b += nstage_c * 4 * (2 * nc * (NU + NP) * (NL + NP) + 6 * NT * nL);
+    b += 8 * 40 * (n + 1) * (n + 1);                                       // P1 multigrid
+    return 1.15 * b + (1 << 20);
 }
 
 hdg_status hdg_solve_stage(hdg_ctx *c, double cc, const double *R, const double *Qstar, double *Q,

@@ -58,6 +58,16 @@ class hdg_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class hdg_server_stats(ctypes.Structure):
+    _fields_ = [('submitted', ctypes.c_int), ('admitted', ctypes.c_int), ('completed', ctypes.c_int),
+                ('active', ctypes.c_int), ('queued', ctypes.c_int), ('contexts_created', ctypes.c_int),
+                ('contexts_reused', ctypes.c_int), ('contexts_released', ctypes.c_int),
+                ('bytes_in_use', ctypes.c_double), ('steps', ctypes.c_longlong), ('stage_solves', ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 PHI = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_double, ctypes.c_void_p)
 _P = ctypes.c_void_p
 _D = ctypes.c_double
@@ -78,6 +88,15 @@ _SIGNATURES = {
     'hdg_set_state': (_I, [_P, _P, _P, _P, _D]),
     'hdg_get_state': (_I, [_P, _P, _P, _P, _DP]),
     'hdg_project': (_I, [_P, _I, _P, _P]),
+    'hdg_batch_step': (_I, [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(hdg_stats)]),
+    'hdg_ctx_bytes': (ctypes.c_size_t, [_P]),
+    'hdg_estimate_bytes': (ctypes.c_double, [ctypes.POINTER(hdg_mesh_desc), ctypes.POINTER(hdg_params)]),
+    'hdg_server_create': (_I, [ctypes.POINTER(_P), _I, _D, _I]),
+    'hdg_server_submit': (_I, [_P, ctypes.POINTER(hdg_mesh_desc), ctypes.POINTER(hdg_params), _DP, _I,
+                              ctypes.POINTER(ctypes.c_longlong)]),
+    'hdg_server_progress': (_I, [_P, ctypes.POINTER(hdg_server_stats)]),
+    'hdg_server_result': (_I, [_P, ctypes.c_longlong, _DP, _DP, _DP, _DP]),
+    'hdg_server_destroy': (None, [_P]),
     'hdg_set_tracer': (_I, [_P, _P]),
     'hdg_get_tracer': (_I, [_P, _P]),
     'hdg_cg_project': (_I, [_P, _P, _P]),
@@ -339,3 +358,94 @@ class Context:
                 raise ValueError(f'{name} is on cuda:{t.device.index}, the current device is cuda:{dev}')
         _check(load().hdg_trace_apply_noalloc(self._ctx, c, _ptr(lam), _ptr(out)), 'hdg_trace_apply_noalloc')
         return out
+
+    def hdg_ctx_bytes(self):
+        return int(load().hdg_ctx_bytes(self._ctx))
+
+
+def make_params(k, **params):
+    """hdg_params with the library's defaults, degree k and the given fields."""
+    p = hdg_default_params()
+    p.k = k
+    for key, val in params.items():
+        if key == 'tableau' and isinstance(val, str):
+            val = TABLEAUS[val]
+        if key == 'precision' and isinstance(val, str):
+            val = PRECISIONS[val]
+        if not hasattr(p, key):
+            raise KeyError(key)
+        setattr(p, key, val)
+    return p
+
+
+def hdg_batch_step(contexts, nsteps=1, check=True):
+    """hdg_batch_step over Context objects: every context's step enqueued before any is waited for."""
+    n = len(contexts)
+    arr = (_P * n)(*[c._ctx.value for c in contexts])
+    st = (hdg_stats * n)()
+    s = load().hdg_batch_step(arr, n, nsteps, st)
+    if check:
+        _check(s, 'hdg_batch_step')
+    return [x.as_dict() for x in st], s
+
+
+def hdg_estimate_bytes(n, k, periodic_x=False, periodic_y=False, Lx=1.0, Ly=1.0, **params):
+    d = hdg_mesh_desc(n, Lx, Ly, int(periodic_x), int(periodic_y))
+    p = make_params(k, **params)
+    return float(load().hdg_estimate_bytes(ctypes.byref(d), ctypes.byref(p)))
+
+
+class Server:
+    """An hdg_server: requests (mesh, parameters, initial velocity, steps) served with admission by
+    device-memory budget and continuous batching."""
+
+    def __init__(self, mem_budget_bytes, max_active, device=None):
+        import torch
+        lib = load()
+        self._srv = ctypes.c_void_p()
+        dev = torch.cuda.current_device() if device is None else device
+        _check(lib.hdg_server_create(ctypes.byref(self._srv), dev, float(mem_budget_bytes), int(max_active)),
+               'hdg_server_create')
+        self._sizes = {}
+
+    def submit(self, n, k, Q0, nsteps, periodic_x=False, periodic_y=False, Lx=1.0, Ly=1.0, **params):
+        """Q0: host numpy array of the initial nodal velocity ((ncells, 2, mu) or flat). Returns the id."""
+        import numpy as np
+        d = hdg_mesh_desc(n, Lx, Ly, int(periodic_x), int(periodic_y))
+        p = make_params(k, **params)
+        q = np.ascontiguousarray(Q0, dtype=np.float64).reshape(-1)
+        rid = ctypes.c_longlong()
+        _check(load().hdg_server_submit(self._srv, ctypes.byref(d), ctypes.byref(p), q.ctypes.data_as(_DP), int(nsteps),
+                                        ctypes.byref(rid)), 'hdg_server_submit')
+        nc, nf = hdg_mesh_counts(n, k, periodic_x, periodic_y, Lx, Ly)
+        mu, npn = (k + 2) * (k + 3) // 2, (k + 1) * (k + 2) // 2
+        self._sizes[rid.value] = (nc * 2 * mu, nc * npn, nf * (k + 1))
+        return rid.value
+
+    def progress(self):
+        st = hdg_server_stats()
+        _check(load().hdg_server_progress(self._srv, ctypes.byref(st)), 'hdg_server_progress')
+        return st.as_dict()
+
+    def result(self, rid):
+        """(Q, p, lambda, latency_ms) of a completed request (host numpy), or None if not complete."""
+        import numpy as np
+        nQ, nP, nL = self._sizes[rid]
+        Q, p, lam, lat = np.empty(nQ), np.empty(nP), np.empty(nL), ctypes.c_double()
+        s = load().hdg_server_result(self._srv, rid, Q.ctypes.data_as(_DP), p.ctypes.data_as(_DP),
+                                     lam.ctypes.data_as(_DP), ctypes.byref(lat))
+        if s != HDG_OK:
+            return None
+        del self._sizes[rid]
+        return Q, p, lam, lat.value
+
+    def close(self):
+        if self._srv:
+            load().hdg_server_destroy(self._srv)
+            self._srv = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
