@@ -195,6 +195,180 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------------- batched / served
+def c4_instances(count=64, seed=4):
+    """The batching workload: `count` independent instances, mesh sizes from {16, 32, 64, 128}^2 and
+    degrees from {1, 2, 3, 4} drawn with a seed, walls, ARS(3,4,3) with dt keeping the stage
+    stiffness c/h^2 of the channel workload (dt = 2e-3 (64/n)^2), random divergence-free initial
+    fields from a stream function of 8 Fourier modes (amplitudes N(0,1)/|m|^2)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    ns = rng.choice([16, 32, 64, 128], size=count)
+    ks = rng.integers(1, 5, size=count)
+    return [dict(n=int(n), k=int(k), dt=2e-3 * (64.0 / n) ** 2, seed=1000 + i) for i, (n, k) in enumerate(zip(ns, ks))]
+
+
+def c5_requests(count, seed=5, rate=200.0, nmax=96, smax=30):
+    """The serving workload: Poisson arrivals (mean `rate` per s), mesh sizes uniform over
+    32..nmax, degrees from {2, 3, 4}, 10..smax steps each, the instances of c4_instances otherwise."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    ns = rng.integers(32, nmax + 1, size=count)
+    ks = rng.integers(2, 5, size=count)
+    steps = rng.integers(10, smax + 1, size=count)
+    return [dict(t=float(ti), n=int(n), k=int(k), steps=int(st_), dt=2e-3 * (64.0 / n) ** 2, seed=2000 + i)
+            for i, (ti, n, k, st_) in enumerate(zip(t, ns, ks, steps))]
+
+
+def instance_field(inst):
+    import hdg_workloads as W
+    modes = W.stream_function_modes(inst['seed'])
+    return W.nodal_velocity(inst['n'], inst['k'], lambda x, y: W.stream_velocity(x, y, modes))
+
+
+def instance_context(H, inst, prec, kw):
+    import torch
+    ctx = H.Context(inst['n'], inst['k'], stream=torch.cuda.Stream(), tableau='ARS343', dt=inst['dt'],
+                    precision=prec, **kw)
+    ctx.hdg_set_state(torch.from_numpy(instance_field(inst)).cuda())
+    ctx.hdg_div_free_project()
+    return ctx
+
+
+def run_batched(args, rank, world, local_rank):
+    """c4: all instances advanced together (hdg_batch_step, HDG_MIXED) against the same instances
+    stepped one at a time (HDG_MIXED, and every kernel in FP64: the plain GPU form)."""
+    import numpy as np
+    import torch
+    import paper_2410_09790_gb300 as H
+    torch.cuda.set_device(local_rank)
+    insts = c4_instances(args.instances)
+    kw = dict(SOLVER, richardson_rtol=1e-10)
+    K = args.steps
+    stages = STAGES['ARS343']
+
+    def sync_time(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    out = {}
+    # plain FP64 form, one instance at a time
+    ctxs = [instance_context(H, inst, 'FP64', kw) for inst in insts]
+    for c in ctxs:
+        c.hdg_imex_step(1)
+    sec64 = sync_time(lambda: [c.hdg_imex_step(K) for c in ctxs])
+    for c in ctxs:
+        c.close()
+    # mixed precision: one at a time, then all together
+    ctxs = [instance_context(H, inst, 'MIXED', kw) for inst in insts]
+    H.hdg_batch_step(ctxs, 1)
+    seqm = sync_time(lambda: [c.hdg_imex_step(K) for c in ctxs])
+    with ClockSampler(local_rank) as clk:
+        bat = sync_time(lambda: H.hdg_batch_step(ctxs, K))
+    launches = sum(s['graph_kernels'] for s in H.hdg_batch_step(ctxs, 1)[0])
+    for c in ctxs:
+        c.close()
+    n_stage = len(insts) * stages * K
+    value = n_stage / bat
+    line = {'metric': METRIC, 'value': value, 'unit': 'stage_solves/s', 'n_gpus': world, 'steps': K,
+            'warmup': 1, 'ms_per_step': 1e3 * bat / K, 'higher_is_better': True, 'scaling': 'weak',
+            'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic (seeded stream-function fields)',
+            'config': {'workload': f'{len(insts)} instances, n from {{16,32,64,128}}^2, k from 1..4, walls, ARS(3,4,3), '
+                                   f'dt = 2e-3 (64/n)^2, stages to 1e-10, HDG_MIXED, hdg_batch_step',
+                       'instances': [[i['n'], i['k']] for i in insts], 'parallelism': 'one stream per instance',
+                       'l2': 'inputs larger than L2 in total'},
+            'sequential_mixed': {'value': n_stage / seqm, 'seconds': seqm},
+            'sequential_fp64': {'value': n_stage / sec64, 'seconds': sec64,
+                                'note': 'every kernel in FP64 (HDG_FP64), instances one at a time: the plain GPU form'},
+            'speedup_vs_sequential_fp64': sec64 / bat, 'speedup_vs_sequential_mixed': seqm / bat,
+            'gpu_launches': int(launches * K), 'clocks': clk.summary(),
+            'e2e': {'value': None, 'unit': 'stage_solves/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_served(args, rank, world, local_rank):
+    """c5: a Poisson stream of requests served by hdg_server (HDG_MIXED, continuous batching,
+    admission by device memory) against the plain per-request loop (HDG_FP64, one request at a time,
+    a new context each); latency = completion - arrival on the host clock."""
+    import numpy as np
+    import torch
+    import paper_2410_09790_gb300 as H
+    torch.cuda.set_device(local_rank)
+    reqs = c5_requests(args.requests)
+    kw = dict(SOLVER, richardson_rtol=1e-10)
+    stages = STAGES['ARS343']
+    fields = [instance_field(r) for r in reqs]
+    free = torch.cuda.mem_get_info()[0]
+    # served
+    srv = H.Server(0.7 * free, max_active=args.max_active)
+    ids, lat, done_t = {}, {}, {}
+    t0 = time.perf_counter()
+    nxt = 0
+    with ClockSampler(local_rank) as clk:
+        while len(lat) < len(reqs):
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and reqs[nxt]['t'] <= now:
+                r = reqs[nxt]
+                ids[srv.submit(r['n'], r['k'], fields[nxt], r['steps'], tableau='ARS343', dt=r['dt'], precision='MIXED',
+                               **kw)] = nxt
+                nxt += 1
+            if not ids or all(i in lat for i in ids.values()):
+                if nxt < len(reqs):
+                    time.sleep(max(0.0, reqs[nxt]['t'] - (time.perf_counter() - t0)))
+                continue
+            st = srv.progress()
+            tnow = time.perf_counter() - t0
+            for rid, i in list(ids.items()):
+                if i in lat:
+                    continue
+                res = srv.result(rid)
+                if res is not None:
+                    lat[i] = tnow - reqs[i]['t']
+                    done_t[i] = res[0]
+    span = time.perf_counter() - t0
+    sst = srv.progress()
+    srv.close()
+    # the plain per-request loop
+    lat64, fin64 = {}, {}
+    t0 = time.perf_counter()
+    for i, r in enumerate(reqs):
+        now = time.perf_counter() - t0
+        if now < r['t']:
+            time.sleep(r['t'] - now)
+        ctx = instance_context(H, r, 'FP64', kw)
+        ctx.hdg_imex_step(r['steps'])
+        fin64[i] = ctx.hdg_get_state()[0].cpu().numpy().reshape(-1)
+        ctx.close()
+        torch.cuda.synchronize()
+        lat64[i] = time.perf_counter() - t0 - r['t']
+    span64 = time.perf_counter() - t0
+    n_stage = sum(r['steps'] for r in reqs) * stages
+    diff = max(float(np.linalg.norm(done_t[i] - fin64[i]) / np.linalg.norm(fin64[i])) for i in range(len(reqs)))
+    pct = lambda d, q: 1e3 * float(np.percentile(np.array(list(d.values())), q))
+    line = {'metric': METRIC, 'value': n_stage / span, 'unit': 'stage_solves/s', 'n_gpus': world,
+            'steps': int(sum(r['steps'] for r in reqs)), 'warmup': 0, 'ms_per_step': None, 'higher_is_better': True,
+            'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic (seeded request stream)',
+            'config': {'workload': f'{len(reqs)} requests, Poisson arrivals 200/s, n ~ U{{32..96}}, k in {{2,3,4}}, '
+                                   f'10..30 steps, walls, ARS(3,4,3), dt = 2e-3 (64/n)^2, stages to 1e-10; '
+                                   f'served by hdg_server (HDG_MIXED, continuous batching, admission by device memory)',
+                       'scaled_down_from': '2,000 requests, n ~ U{32..256}, k in {2,3,4}, 10..100 steps',
+                       'max_active': args.max_active, 'mem_budget_bytes': 0.7 * free},
+            'latency_ms': {'p50': pct(lat, 50), 'p99': pct(lat, 99)},
+            'server': sst,
+            'plain_fp64_loop': {'value': n_stage / span64, 'latency_ms': {'p50': pct(lat64, 50), 'p99': pct(lat64, 99)},
+                                'note': 'one request at a time in arrival order, a new HDG_FP64 context each'},
+            'max_rel_diff_vs_plain_fp64': diff, 'clocks': clk.summary(), 'gpu_launches': None,
+            'e2e': {'value': n_stage / span, 'unit': 'stage_solves/s', 'h2d_bytes_per_step': None,
+                    'd2h_bytes_per_step': None}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------------- GPU arm
 def rel_err(a, b):
     """Relative l2 difference of two nodal arrays (host numpy)."""
@@ -314,7 +488,7 @@ def golden_error(H, w, stream, kw):
     Q, p, lam, _ = state_host(ctx)
     ctx.close()
     q_rms = float(np.linalg.norm(g['Q']) / np.sqrt(g['Q'].size))
-    vs = lambda a, b: float(np.linalg.norm(a - b) / np.sqrt(b.size) / q_rms)
+    vs = lambda a, b: float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.sqrt(b.size) / q_rms)
     return {'mesh': f'{n}x{n} (same workload; oracle: monolithic direct stage solves)',
             'rel_l2': {'Q': rel_err(Q, g['Q']), 'p': rel_err(p, g['p']), 'lambda': rel_err(lam, g['lam'])},
             'rms_over_velocity_rms': {'Q': vs(Q, g['Q']), 'p': vs(p, g['p']), 'lambda': vs(lam, g['lam'])},
@@ -476,8 +650,12 @@ def main():
     ap.add_argument('--impl', default='gpu', choices=['gpu', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--e2e-steps', type=int, default=3)
-    ap.add_argument('--workload', default='c2', choices=['c2', 'c3'],
-                    help='c2: the shear channel (default); c3: forced Taylor-Green 256x256, k=4')
+    ap.add_argument('--workload', default='c2', choices=['c2', 'c3', 'c4', 'c5'],
+                    help='c2: the shear channel (default); c3: forced Taylor-Green 256x256, k=4; '
+                         'c4: batched instances; c5: served request stream')
+    ap.add_argument('--instances', type=int, default=64, help='c4: number of instances')
+    ap.add_argument('--requests', type=int, default=48, help='c5: number of requests')
+    ap.add_argument('--max-active', type=int, default=64, help='c5: server slot limit')
     ap.add_argument('--precision', default='MIXED', choices=['MIXED', 'FP64'])
     ap.add_argument('--no-compare', action='store_true', help='skip the run in the other precision')
     ap.add_argument('--compare-steps', type=int, default=3, help='timed steps of the other precision')
@@ -510,6 +688,10 @@ def main():
         dist.init_process_group(backend)
     if args.impl == 'reference':
         run_reference(args, rank, world)
+    elif args.workload == 'c4':
+        run_batched(args, rank, world, local_rank)
+    elif args.workload == 'c5':
+        run_served(args, rank, world, local_rank)
     else:
         run_gpu(args, rank, world, local_rank)
     if world > 1:
