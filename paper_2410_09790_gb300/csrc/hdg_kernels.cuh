@@ -692,6 +692,61 @@ __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c
     if (!ok && tm.tid == 0) atomicExch(status, 1);
 }
 
+// FP32 inverses of the Step-I diagonal blocks for the inner (preconditioner) solves, one warp per
+// cell with the block in registers: lane l holds rows l and l + 32 (< NU), Gauss-Jordan in place
+// without pivoting, row k reaching the other lanes by shuffles. No pivoting is needed: the block
+// M_K - c F_K has a positive definite symmetric part (mass plus the dissipative penalty and upwind
+// terms; the advection's symmetric part is c (div Q*)/2 |Q|^2, far below the mass), so every
+// leading block is nonsingular. A zero or non-finite pivot sets *status (singular block).
+// Dblk and Binv32 in the column-slice layout [col * nrows + cell * NU + row].
+template <int K>
+__global__ void __launch_bounds__(128) k_block_inv32(const double *__restrict__ Dblk, float *__restrict__ Binv32,
+                                                     long long ncells, int *status) {
+    wait_prior_kernel();
+    constexpr int N = Dims<K>::NU;
+    constexpr int R = (N + 31) / 32;
+    const int lane = (int)(threadIdx.x & 31);
+    const long long cell = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // uniform per warp
+    if (cell >= ncells) return;
+    const long long nrows = ncells * N;
+    float a[R][N];
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+        const int r = lane + 32 * s;
+#pragma unroll
+        for (int j = 0; j < N; ++j) a[s][j] = r < N ? (float)__ldg(&Dblk[(size_t)j * nrows + (size_t)cell * N + r]) : 0.f;
+    }
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const int owner = k & 31, ks = k >> 5;
+        const float piv = __shfl_sync(0xffffffffu, a[ks][k], owner);
+        ok = ok && isfinite(piv) && piv != 0.f;
+        const float inv = 1.f / piv;
+        float f[R];
+#pragma unroll
+        for (int s = 0; s < R; ++s) f[s] = a[s][k];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const float rkj = __shfl_sync(0xffffffffu, a[ks][j], owner) * inv;   // row k, normalised
+#pragma unroll
+            for (int s = 0; s < R; ++s) {
+                const bool pivot_row = lane + 32 * s == k;
+                if (j == k) a[s][j] = pivot_row ? inv : -f[s] * inv;
+                else a[s][j] = pivot_row ? rkj : a[s][j] - f[s] * rkj;
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+        const int r = lane + 32 * s;
+        if (r < N)
+#pragma unroll
+            for (int j = 0; j < N; ++j) Binv32[(size_t)j * nrows + (size_t)cell * N + r] = a[s][j];
+    }
+    if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicExch(status, 1);
+}
+
 // ------------------------------------------------------------ matrix-free neighbour coupling
 // Tables the neighbour coupling needs, in the precision T of the solve: ephi (edge values of the
 // velocity basis, [e][q][a]) and pen (the penalty weights -c alpha fw_q of the assembled operator,

@@ -1125,8 +1125,13 @@ struct Impl {
         if (!c->capturing) CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st));   // (graphs: once per launch)
         launch_k(k_fimpl_assemble<K>, (unsigned)c->ncells, 128, smem, c->st, 
             c->R, c->M, Qs, cc, c->P.alpha, c->P.delta_up, c->Dblk, c->wq, c->wq32, c->pen, c->pen32,
-            (inv & INV64) ? c->Binv : nullptr, (inv & INV32) ? c->Binv32 : nullptr, c->dstatus);
+            (inv & INV64) ? c->Binv : nullptr, (float *)nullptr, c->dstatus);
         CKL();
+        if (inv & INV32) {              // FP32 inverses: a warp per cell, the block in registers
+            launch_k(k_block_inv32<K>, (unsigned)((c->ncells * 32 + 127) / 128), 128, 0, c->st, (const double *)c->Dblk,
+                     c->Binv32, c->ncells, c->dstatus);
+            CKL();
+        }
         c->inv_ok = inv;
     }
 
