@@ -124,7 +124,7 @@ typedef struct {
     int precision;
     /* The one-V-cycle Step II inside the stage preconditioner (inner_trace_vcycles = 1): 1
      * (default) = the V-cycle in FP32 (operators rounded once per stage coefficient; the large P1
-     * levels as grid-wide kernels, the small ones — from the first level with at most 5000
+     * levels as grid-wide kernels, the small ones — from the first level with at most 1200
      * vertices whose sub-hierarchy fits 200 KiB of shared memory — in one thread block);
      * 0 = the FP64 V-cycle. The outer iteration's tolerance is unchanged: this only alters the
      * preconditioner. */

@@ -627,14 +627,20 @@ constexpr int fimpl_smem_doubles() {
     typedef Dims<K> Dm;
     return fimpl_diag_scratch<K>() + 3 * Dm::NU * Dm::NU + 3 * Dm::NFQ + 2;
 }
+template <int K>
+constexpr int fimpl_smem_noinv_doubles() {
+    typedef Dims<K> Dm;
+    return fimpl_diag_scratch<K>() + Dm::NU * Dm::NU + 3 * Dm::NFQ;
+}
 
 // Step-I operator of one stage, one block per cell: diagonal block -> Dblk, neighbour weights
 // -> wq (and wq32 in FP32), the penalty weights -> pen / pen32 (cell 0), and the inverse of the
-// diagonal block in FP64 -> Binv and/or in FP32 -> Binv32 (each when non-null).
+// diagonal block in FP64 -> Binv when non-null (dynamic shared memory: fimpl_smem_doubles, or
+// fimpl_smem_noinv_doubles without Binv). The FP32 inverses come from k_block_inv32.
 template <int K>
 __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c, double alpha,
                                  double dup, double *Dblk, double *wq, float *wq32, double *pen, float *pen32,
-                                 double *Binv, float *Binv32, int *status) {
+                                 double *Binv, int *status) {
     wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int NU = Dm::NU, NFQ = Dm::NFQ;
@@ -667,20 +673,9 @@ __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c
         wq[(size_t)cell * 3 * NFQ + i] = wqs[i];
         wq32[(size_t)cell * 3 * NFQ + i] = (float)wqs[i];
     }
-    double *inv = wqs + 3 * NFQ;                    // NU^2 doubles, or 2 NU^2 floats
+    double *inv = wqs + 3 * NFQ;                    // NU^2 doubles (FP64 inverse only)
     int *piv = (int *)(inv + 2 * NU * NU);
     bool ok = true;
-    if (Binv32) {
-        float *A32 = reinterpret_cast<float *>(inv), *I32 = A32 + NU * NU;
-        TFOR(i, NU * NU) A32[i] = (float)D[i];
-        tm.sync();
-        ok = team_invert<NU, float>(tm, A32, I32, piv);
-        TFOR(i, NU * NU) {
-            int col = i / NU, row = i % NU;
-            Binv32[(size_t)col * nrows + (size_t)cell * NU + row] = I32[row * NU + col];
-        }
-        tm.sync();
-    }
     if (Binv) {
         // the diagonal block is consumed by the inversion (in place)
         ok = team_invert<NU, double>(tm, D, inv, piv) && ok;

@@ -924,12 +924,13 @@ struct Impl {
     // out (FP64 V-cycle) when the P1 hierarchy's vectors do not fit one block's shared memory
     // The levels from first32 down run in one block (k_tv_tail, everything in shared memory); the
     // larger ones above as grid-wide kernels. first32: the first level whose sub-hierarchy fits the
-    // block (<= 200 KiB, rows of at most 1024 points) and has at most HDG_MG32_TAIL_MAX vertices.
+    // block (<= 200 KiB, rows of at most 1024 points) and has at most HDG_MG32_TAIL_MAX (default
+    // 1200) vertices: one block serves the small levels, the large ones keep all SMs busy.
     static int mg32_tail_max() {
         static int v = -1;
         if (v < 0) {
             const char *e = std::getenv("HDG_MG32_TAIL_MAX");
-            v = e ? std::atoi(e) : 5000;
+            v = e ? std::atoi(e) : 1200;
             if (v < 1) v = 1;
         }
         return v;
@@ -1120,12 +1121,13 @@ struct Impl {
     // block-Jacobi inverses named by inv (INV64 | INV32)
     static void assemble_stepI(hdg_ctx *c, const double *Qs, double cc, int inv) {
         CompTimer tm_(c, &c->S.ms_assembly);
-        size_t smem = sizeof(double) * fimpl_smem_doubles<K>();
-        CK(cudaFuncSetAttribute(k_fimpl_assemble<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const size_t smem = sizeof(double) * ((inv & INV64) ? fimpl_smem_doubles<K>() : fimpl_smem_noinv_doubles<K>());
+        CK(cudaFuncSetAttribute(k_fimpl_assemble<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(double) * fimpl_smem_doubles<K>())));
         if (!c->capturing) CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st));   // (graphs: once per launch)
         launch_k(k_fimpl_assemble<K>, (unsigned)c->ncells, 128, smem, c->st, 
             c->R, c->M, Qs, cc, c->P.alpha, c->P.delta_up, c->Dblk, c->wq, c->wq32, c->pen, c->pen32,
-            (inv & INV64) ? c->Binv : nullptr, (float *)nullptr, c->dstatus);
+            (inv & INV64) ? c->Binv : nullptr, c->dstatus);
         CKL();
         if (inv & INV32) {              // FP32 inverses: a warp per cell, the block in registers
             launch_k(k_block_inv32<K>, (unsigned)((c->ncells * 32 + 127) / 128), 128, 0, c->st, (const double *)c->Dblk,
