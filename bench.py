@@ -18,12 +18,13 @@ errors against each other and against the exact solution exp(-t) Q0.
 
 Output: one JSON line (rank 0). value = stage solves/s (whole job); trace_dof_per_s = trace
 unknowns x trace solves / s. e2e: the same through the C-ABI with the state copied from pinned
-host memory to the device and back every step. roofline: the kernel with the largest share of a
-step, the fused FP64 stage-operator kernel (the flexible GMRES product), timed alone with CUDA
-events on the context's stream; it is bound by GB300's FP64 pipe, so achieved = algorithmic
-FP64 flops / time against the nominal FP64 rate. inner_stepI_fp32 (the two kernels of an inner
-Arnoldi step, bytes / time vs the measured HBM peak; warm in L2 at this size), trace_apply and
-stage_apply_fp64 report more kernels of the path the same way.
+host memory to the device and back every step. kernels: the path's main kernels, each timed
+alone with CUDA events on the context's stream (time per launch), with launches per step from the
+solver's own counters; roofline: the one of them with the largest device time per step. FP64
+kernels are bound by GB300's FP64 pipe (achieved = algorithmic FP64 flops / time against the
+nominal FP64 rate), FP32 ones by memory (algorithmic bytes / time against the measured HBM peak;
+their data stays in L2 where it fits, 129 MB). trace_apply, condensation and stage_apply_fp64
+report more kernels the same way.
 cpu_baseline / --impl reference: the oracle (plain FP64 SciPy) on the host cores.
 """
 import argparse
@@ -387,6 +388,8 @@ def solver_settings(args, w):
             kw[key] = v
     kw['richardson_rtol'] = w['stage_rtol']
     kw['device_loops'] = 0 if args.host_loops else 1
+    if getattr(args, 'relax_eta', None) is not None:
+        kw['relax_eta'] = args.relax_eta
     return kw
 
 
@@ -508,6 +511,17 @@ def stage_flops(k, ncells):
     return st_flop, s_flop
 
 
+def condense_flops(k, ncells):
+    """Algorithmic FP64 flops of one launch of the per-cell condensation (k_condense): D and E
+    formed, A = (c/detJ) D D^T + tau T_pp, H = (c/detJ) D E^T + tau E_hat^T, the Cholesky factor of
+    A and its inverse, Z = A^-1 H, S_K = (c/detJ) E E^T + tau T_ll - H^T Z (an FMA counts two)."""
+    mu = (k + 2) * (k + 3) // 2
+    nu, npk, nl = 2 * mu, (k + 1) * (k + 2) // 2, 3 * (k + 1)
+    per = (4 * npk * nu + 2 * nl * nu + npk * npk * (2 * nu + 8) + npk * nl * (2 * nu + 3) + 2 * npk ** 3 / 3
+           + 2 * npk ** 3 + 2 * npk * npk * nl + nl * nl * (2 * nu + 2 * npk + 4))
+    return per * ncells
+
+
 def run_gpu(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -539,10 +553,14 @@ def run_gpu(args, rank, world, local_rank):
         k_ms, k_bytes = ctx.hdg_time_kernel(0, c_stage, 50)
         s_ms, s_bytes = ctx.hdg_time_kernel(1, 1.0, 20)
         st_ms, st_bytes = ctx.hdg_time_kernel(8, c_stage, 20)
-        a_ms = p_ms = a_bytes = p_bytes = None
+        cd_ms, cd_bytes = ctx.hdg_time_kernel(11, c_stage, 3)
+        s32_ms = s32_bytes = gd_ms = gd_bytes = ga_ms = ga_bytes = None
         if args.precision == 'MIXED':
-            a_ms, a_bytes = ctx.hdg_time_kernel(6, c_stage, 50)
-            p_ms, p_bytes = ctx.hdg_time_kernel(9, c_stage, 50)
+            if kw.get('relax_eta', 1e-4) > 0:
+                s32_ms, s32_bytes = ctx.hdg_time_kernel(12, c_stage, 20)
+            if kw.get('inner_gs', 1):
+                gd_ms, gd_bytes = ctx.hdg_time_kernel(13, c_stage, 50)
+                ga_ms, ga_bytes = ctx.hdg_time_kernel(14, c_stage, 50)
         e2e_ms, h2d = e2e_steps(ctx, args.e2e_steps, flush, dev)
         nsteps_done = args.warmup + args.steps + args.e2e_steps
         final = state_host(ctx)
@@ -574,10 +592,58 @@ def run_gpu(args, rank, world, local_rank):
     stepI_iters = sum(s['stepI_iters'] for s in stats_all)
     ncells = 2 * w['n'] * w['n']
     st_flop, s_flop = stage_flops(w['k'], ncells)
-    st_tflops = st_flop / (st_ms * 1e-3) / 1e12
     host_loops = bool(args.host_loops)
+    # the path's main kernels: time per launch alone (CUDA events, after the timed steps), launches
+    # per step from the solver's counters, and the device time per step that gives; the roofline
+    # object reports the kernel with the largest share
+    outer = sum(s['richardson_iters'] for s in stats_all) / args.steps
+    p32 = sum(s['stage_products32'] for s in stats_all) / args.steps
+    inner = stepI_iters / args.steps
+    kernels = {
+        f"k_stage_apply<{w['k']}>": {'what': 'FP64 stage operator (FGMRES products, restart residuals)',
+                                     'ms_per_launch': st_ms, 'launches_per_step': outer - p32 + 2 * stages,
+                                     'bytes': st_bytes, 'flop': st_flop, 'bound': 'alu'},
+        f"k_cg_apply<{w['k'] + 1}>": {'what': 'FP64 trace operator apply (tight trace CG)', 'ms_per_launch': k_ms,
+                                      'launches_per_step': trace_iters / args.steps, 'bytes': k_bytes, 'bound': 'hbm'}}
+    if s32_ms is not None:
+        kernels[f"k_stage_apply32<{w['k']}>"] = {'what': 'FP32 stage operator (relaxed FGMRES products)',
+                                                 'ms_per_launch': s32_ms, 'launches_per_step': p32,
+                                                 'bytes': s32_bytes, 'bound': 'hbm'}
+    if gd_ms is not None:
+        kernels[f"k_gs_diag<{w['k']}>"] = {'what': 'inner FP32 Step-I GMRES: red-black block Gauss-Seidel colour '
+                                                   'pass (FP32 block inverses)', 'ms_per_launch': gd_ms,
+                                           'launches_per_step': 2 * inner, 'bytes': gd_bytes, 'bound': 'hbm'}
+        kernels[f"k_gs_apply<{w['k']}>"] = {'what': 'inner FP32 Step-I GMRES: Arnoldi product and dots',
+                                            'ms_per_launch': ga_ms, 'launches_per_step': inner, 'bytes': ga_bytes,
+                                            'bound': 'hbm'}
+    for name, kd in kernels.items():
+        kd['ms_per_step_est'] = kd['ms_per_launch'] * kd['launches_per_step']
+        kd['share_of_step_est'] = kd['ms_per_step_est'] / float(np.mean(ms))
+        kd['achieved_gbs'] = kd['bytes'] / (kd['ms_per_launch'] * 1e-3) / 1e9
+        if kd['bound'] == 'hbm':
+            kd['frac_of_hbm'] = kd['achieved_gbs'] / peak
+        else:
+            kd['achieved_tflops'] = kd['flop'] / (kd['ms_per_launch'] * 1e-3) / 1e12
+            kd['frac_of_fp64_nominal'] = kd['achieved_tflops'] / FP64_NOMINAL_TFLOPS
+    top = max(kernels, key=lambda n: kernels[n]['ms_per_step_est'])
+    kt = kernels[top]
+    traffic_file = {f"k_stage_apply<{w['k']}>": 'k_stage_apply_fp64_c2.md'}.get(top) if args.workload == 'c2' else None
+    if kt['bound'] == 'alu':
+        roofline = {'kernel': f"{top} ({kt['what']})", 'bound': 'alu', 'achieved': kt['achieved_tflops'],
+                    'peak': FP64_NOMINAL_TFLOPS, 'unit': 'TFLOP/s', 'frac': kt['frac_of_fp64_nominal'],
+                    'peak_kind': 'nominal FP64 vector rate (no measured FP64 peak exists for this pool)',
+                    'algorithmic_flop': kt['flop']}
+    else:
+        roofline = {'kernel': f"{top} ({kt['what']})", 'bound': 'hbm', 'achieved': kt['achieved_gbs'], 'peak': peak,
+                    'unit': 'GB/s', 'frac': kt['frac_of_hbm'], 'peak_kind': peak_kind}
+    roofline.update({'traffic': profile_traffic(traffic_file) if traffic_file else None,
+                     'ms_per_launch': kt['ms_per_launch'], 'algorithmic_bytes': kt['bytes'],
+                     'launches_per_step': kt['launches_per_step'], 'share_of_step_est': kt['share_of_step_est'],
+                     'note': 'the kernel with the largest estimated device time per step (time per launch alone x '
+                             'launches per step from the solver counters)'})
     per_step = {'trace_solves': trace_solves / args.steps, 'trace_cg_iters': trace_iters / args.steps,
                 'stage_outer_iters': sum(s['richardson_iters'] for s in stats_all) / args.steps,
+                'stage_products_fp32': sum(s['stage_products32'] for s in stats_all) / args.steps,
                 'gmres_iters': stepI_iters / args.steps}
     for key, name in (('ms_trace_solves', 'ms_trace'), ('ms_stepI_solves', 'ms_stepI'), ('ms_assembly', 'ms_assembly'),
                       ('ms_bdm', 'ms_bdm')):      # per-component device times exist only with host-driven loops
@@ -605,30 +671,22 @@ def run_gpu(args, rank, world, local_rank):
         'per_step': per_step,
         'e2e': {'value': world * stages / (e2e_mean / 1e3) if e2e_mean > 0 else None, 'unit': 'stage_solves/s',
                 'h2d_bytes_per_step': h2d, 'd2h_bytes_per_step': h2d},
-        'roofline': {'kernel': f"k_stage_apply<{w['k']}> (fused FP64 stage operator, the flexible GMRES product)",
-                     'bound': 'alu', 'achieved': st_tflops, 'peak': FP64_NOMINAL_TFLOPS, 'unit': 'TFLOP/s',
-                     'frac': st_tflops / FP64_NOMINAL_TFLOPS,
-                     'peak_kind': 'nominal FP64 vector rate (no measured FP64 peak exists for this pool)',
-                     'traffic': profile_traffic('k_stage_apply_fp64_c2.md') if args.workload == 'c2' else None,
-                     'ms_per_launch': st_ms, 'algorithmic_flop': st_flop, 'algorithmic_bytes': st_bytes,
-                     'achieved_gbs': st_bytes / (st_ms * 1e-3) / 1e9},
+        'roofline': roofline,
+        'kernels': kernels,
         'trace_apply': {'kernel': 'k_cg_apply', 'achieved_gbs': k_bytes / (k_ms * 1e-3) / 1e9, 'ms_per_launch': k_ms,
                         'bytes': k_bytes, 'frac_of_hbm': k_bytes / (k_ms * 1e-3) / 1e9 / peak, 'hbm_peak_kind': peak_kind},
+        'condensation': {'kernel': f"k_condense<{w['k']}>", 'ms_per_launch': cd_ms,
+                         'algorithmic_flop': condense_flops(w['k'], ncells), 'bytes': cd_bytes,
+                         'achieved_tflops': condense_flops(w['k'], ncells) / (cd_ms * 1e-3) / 1e12,
+                         'frac_of_fp64_nominal': condense_flops(w['k'], ncells) / (cd_ms * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS,
+                         'achieved_gbs': cd_bytes / (cd_ms * 1e-3) / 1e9, 'frac_of_hbm': cd_bytes / (cd_ms * 1e-3) / 1e9 / peak,
+                         'note': 'once per stage coefficient (setup); FP64, one block per cell, serial Cholesky'},
         'stage_apply_fp64': {'kernel': 'k_cell_apply_mf', 'achieved_gbs': s_bytes / (s_ms * 1e-3) / 1e9,
                              'achieved_tflops': s_flop / (s_ms * 1e-3) / 1e12, 'fp64_nominal_tflops': 1.25,
                              'ms_per_launch': s_ms, 'bytes': s_bytes, 'flop': s_flop},
         'clocks': clk.summary(),
         'gpu_launches': None,
     }
-    if a_ms is not None:
-        line['inner_stepI_fp32'] = {
-            'note': 'timed back to back on the same vectors: warm in L2 where they fit (129 MB)',
-            'apply': {'kernel': f"k_gm_apply_mf<{w['k']}, float, 1> (Arnoldi product, step j = 4)", 'ms_per_launch': a_ms,
-                      'bytes': a_bytes, 'achieved_gbs': a_bytes / (a_ms * 1e-3) / 1e9,
-                      'frac_of_hbm_l2_warm': a_bytes / (a_ms * 1e-3) / 1e9 / peak},
-            'precond': {'kernel': f"k_gm_precond_mf<{w['k']}, float, 1> (block inverse pass, step j = 4)",
-                        'ms_per_launch': p_ms, 'bytes': p_bytes, 'achieved_gbs': p_bytes / (p_ms * 1e-3) / 1e9,
-                        'frac_of_hbm_l2_warm': p_bytes / (p_ms * 1e-3) / 1e9 / peak, 'hbm_peak_kind': peak_kind}}
     if other is not None:
         line['compare_precision'] = other
     # kernels launched inside the timed steps: counted exactly by the library (graph kernel nodes
@@ -668,6 +726,9 @@ def main():
                     help='tuning: the one-V-cycle Step II inside the preconditioner in FP32 (1) or FP64 (0)')
     ap.add_argument('--trace-fp32-vcycle', type=int, default=None,
                     help='tuning: the tight trace CG preconditioned by the FP32 V-cycle (1) or the FP64 one (0)')
+    ap.add_argument('--relax-eta', type=float, default=None,
+                    help='tuning: relaxed FP32 stage-operator products once the FGMRES residual times this is '
+                         'below the tolerance (0: all FP64; default: the library default)')
     ap.add_argument('--inner-gs', type=int, default=None,
                     help='tuning: inner Step-I preconditioner red-black block Gauss-Seidel (1) or block Jacobi (0)')
     ap.add_argument('--host-loops', action='store_true',

@@ -149,6 +149,14 @@ typedef struct {
      * the context's time. Set-up work before a context's first step graph (condensations, graph
      * capture) is not bounded. 0 (default): no limit. */
     double timeout_ms;
+    /* Relaxed stage-operator products (HDG_MIXED with stage_krylov only). The stage FGMRES takes
+     * an Arnoldi product A(c) z_j in FP32 once its residual estimate r_j satisfies
+     * r_j * relax_eta <= richardson_rtol * ||b||: by the inexact-Krylov bound (Simoncini and
+     * Szyld 2003) a product error of relative size relax_eta then moves the final residual by
+     * about the tolerance at most, and every restart (and the final check) forms b - A x in FP64,
+     * so the stage tolerance holds regardless. relax_eta is the relative error assumed for an
+     * FP32 product. 0: every product in FP64. Default 1e-5. */
+    double relax_eta;
 } hdg_params;
 
 typedef struct {
@@ -172,11 +180,15 @@ typedef struct {
      * every pass of their device-side loops, counted exactly on the device; in that mode an IMEX
      * step (stage_krylov = 1) is one graph, so this counts all of its kernels */
     long long graph_kernels;
+    /* stage-operator products the stage FGMRES took in FP32 (relax_eta), summed over the call */
+    long long stage_products32;
 } hdg_stats;
 
 void hdg_default_params(hdg_params *p);
 const char *hdg_status_string(hdg_status s);
-/* Text of the last CUDA error seen by any context (host string, valid until the next call). */
+/* Message of the last call on this thread that failed (a CUDA error's text, the reason for
+ * HDG_ERR_INVALID_ARG where one is known, the solve that did not converge). Calls that run solver
+ * work on a context clear it when they start. Host string, valid until the next call. */
 const char *hdg_last_error(void);
 
 /* Host-only queries (no GPU needed). Sizes of the exchange arrays for a mesh and degree. */
@@ -350,7 +362,15 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *ctx, hdg_stats *stats);
  * the inner Step-I GMRES (v_j formed from w and the projections, z = B^-1 v_j, z's edge values) at
  * step j = 4, launched like 6; bytes = its algorithmic bytes. which = 10 (bytes = 0): one inner FP32
  * Arnoldi step as the solve runs it (preconditioner passes, product, finishing kernel), from 20 steps
- * launched back to back after a cycle start, less the cycle start alone. */
+ * launched back to back after a cycle start, less the cycle start alone. which = 11: the per-cell
+ * condensation (k_condense, Sec. 2.8) for coefficient c alone; bytes = geometry read + S_K, Z_K and
+ * A_K^-1 written. which = 12: the FP32 stage-operator kernel (the relaxed FGMRES product, see
+ * relax_eta) alone, like 8, on the FP32 copy of the diagonal blocks of the last stage assembly
+ * (needs HDG_MIXED with stage_krylov and relax_eta > 0, and a stage solve run first); bytes =
+ * its algorithmic bytes. which = 13, 14 (inner_gs on): the red-black Gauss-Seidel kernels of the
+ * inner FP32 Step-I GMRES at step j = 4, launched like 6: 13 = the colour pass (k_gs_diag; both
+ * colours launched, time and bytes per launch), 14 = the Arnoldi product with its dots
+ * (k_gs_apply); bytes = their algorithmic bytes. */
 hdg_status hdg_time_kernel(hdg_ctx *ctx, int which, double c, int reps, double *ms_per_launch,
                            double *bytes_per_launch);
 

@@ -51,6 +51,7 @@ struct Dims {
 struct RefDev {
     const double *qw, *phi, *dphi, *fw, *ephi, *leg, *Dhat, *Ehat, *Tpp, *bdm_inv, *Iv;
     const double *nod_u, *nod_p, *mod_u, *mod_p, *nod_t, *mod_t;
+    const double *Sfac, *Tadv;
 };
 
 struct MeshDev {
@@ -409,14 +410,16 @@ __host__ __device__ void cell_bdm(const Team &tm, const RefDev &R, const CellGeo
 // NU, with the volume advection) is formed densely; the neighbour coupling only needs, per edge
 // point, wq[e*NFQ + q] = -c fw_q h_e (-Q*.n_K/2 + delta |Q*.n_K|) (0 on walls) besides the
 // penalty -c alpha fw_q n n^T, and is applied matrix-free (k_cell_apply_mf and friends).
-// The sums are factored: the volume term through G[q][b] = w_q (beta(q) . grad phi_b(q)), the
-// facet terms through per-edge MU x MU matrices of the penalty mass and the weighted advective
-// mass, so that each D entry combines a handful of precomputed numbers.
+// The sums are factored: the volume advection through the reference tensor Tadv (the block is
+// sum_{r,c} g_rc Tadv[r][c] with g_rc the coefficients of (J^-1 Q*)_r: the quadrature sum over
+// the volume points regrouped, 2 MU multiply-adds per entry), the penalty through the reference
+// facet masses Sfac, and the central/upwind facet term through per-edge MU x MU weighted facet
+// masses, so that each D entry combines a handful of precomputed numbers.
 // Scratch: fimpl_diag_scratch<K>() doubles. D: row-major [row][col].
 template <int K>
 constexpr int fimpl_diag_scratch() {
     typedef Dims<K> Dm;
-    return 2 * Dm::NQ + 3 * Dm::NFQ + Dm::MU * Dm::MU + Dm::NQ * Dm::MU + 6 * Dm::MU * Dm::MU + 6 * Dm::NFQ * Dm::MU;
+    return 2 * Dm::MU + 3 * Dm::NFQ + Dm::MU * Dm::MU + 3 * Dm::MU * Dm::MU + 3 * Dm::NFQ * Dm::MU;
 }
 
 template <int K>
@@ -425,23 +428,15 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
                                          const int *nbr_edge, double c, double alpha,
                                          double dup, double *sm, double *D, double *wq) {
     typedef Dims<K> Dm;
-    constexpr int MU = Dm::MU, NU = Dm::NU, NQ = Dm::NQ, NFQ = Dm::NFQ;
-    double *beta = sm;               // NQ x 2: Jinv Q* at the volume points
-    double *qsn = beta + 2 * NQ;     // 3 x NFQ: {Q*}.n_e
+    constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
+    double *gc = sm;                 // 2 x MU: coefficients of (J^-1 Q*)_r
+    double *qsn = gc + 2 * MU;       // 3 x NFQ: {Q*}.n_e
     double *adv = qsn + 3 * NFQ;     // MU x MU
-    double *G = adv + MU * MU;       // NQ x MU: w_q (beta(q) . grad phi_b(q))
-    double *Sp = G + NQ * MU;        // 3 x MU x MU: sum_q fw phi_a phi_b on edge e
-    double *Wa = Sp + 3 * MU * MU;   // 3 x MU x MU: the same weighted by Q*.n/2 - delta |Q*.n|
-    double *T1 = Wa + 3 * MU * MU;   // 3 x NFQ x MU: fw_q phi_b(e, q)
-    double *T2 = T1 + 3 * NFQ * MU;  // 3 x NFQ x MU: the same times Q*.n/2 - delta |Q*.n| (0 on walls)
-    TFOR(q, NQ) {
-        double v0 = 0, v1 = 0;
-        for (int a = 0; a < MU; ++a) {
-            double f = ldg(&R.phi[q * MU + a]);
-            v0 += f * QsK[a]; v1 += f * QsK[MU + a];
-        }
-        beta[2 * q] = g.Jinv[0] * v0 + g.Jinv[1] * v1;
-        beta[2 * q + 1] = g.Jinv[2] * v0 + g.Jinv[3] * v1;
+    double *Wa = adv + MU * MU;      // 3 x MU x MU: sum_q fw phi_a phi_b (Q*.n/2 - delta |Q*.n|) on edge e
+    double *T2 = Wa + 3 * MU * MU;   // 3 x NFQ x MU: fw_q phi_b(e, q) (Q*.n/2 - delta |Q*.n|) (0 on walls)
+    TFOR(i, 2 * MU) {
+        const int r = i / MU, b = i % MU;
+        gc[i] = g.Jinv[2 * r] * QsK[b] + g.Jinv[2 * r + 1] * QsK[MU + b];
     }
     TFOR(i, 3 * NFQ) {
         int e = i / NFQ, q = i % NFQ;
@@ -461,37 +456,26 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
         qsn[i] = s;
     }
     tm.sync();
-    TFOR(i, NQ * MU) {
-        int q = i / MU, b = i % MU;
-        G[i] = ldg(&R.qw[q]) * (beta[2 * q] * ldg(&R.dphi[(q * MU + b) * 2]) + beta[2 * q + 1] * ldg(&R.dphi[(q * MU + b) * 2 + 1]));
-    }
     TFOR(i, 3 * NFQ * MU) {             // facet masses as E^T diag(weights) E: the weighted rows first
         const int e = i / (NFQ * MU), q = (i / MU) % NFQ, b = i % MU;
-        const double f = ldg(&R.fw[q]) * ldg(&R.ephi[(e * NFQ + q) * MU + b]);
         const double sq = qsn[e * NFQ + q];
-        T1[i] = f;
-        T2[i] = Qsn[e] ? f * (0.5 * sq - dup * fabs(sq)) : 0.0;
+        T2[i] = Qsn[e] ? ldg(&R.fw[q]) * ldg(&R.ephi[(e * NFQ + q) * MU + b]) * (0.5 * sq - dup * fabs(sq)) : 0.0;
     }
     TFOR(i, 3 * NFQ) {
         int e = i / NFQ, q = i % NFQ;
         wq[i] = Qsn[e] ? -c * ldg(&R.fw[q]) * g.h[e] * (-0.5 * qsn[i] + dup * fabs(qsn[i])) : 0.0;
     }
-    tm.sync();
     TFOR(i, MU * MU) {                  // -(w.(Q*.grad)Q)_K for one component
-        int a = i / MU, b = i % MU;
         double s = 0;
-        for (int q = 0; q < NQ; ++q) s += ldg(&R.phi[q * MU + a]) * G[q * MU + b];
+#pragma unroll 6
+        for (int rc = 0; rc < 2 * MU; ++rc) s += gc[rc] * ldg(&R.Tadv[(size_t)rc * MU * MU + i]);
         adv[i] = -g.detJ * s;
     }
-    TFOR(i, 3 * MU * MU) {              // Sp, Wa = sum_q phi_a(e, q) (T1, T2)[e][q][b]
+    tm.sync();
+    TFOR(i, 3 * MU * MU) {              // Wa = sum_q phi_a(e, q) T2[e][q][b]
         const int e = i / (MU * MU), a = (i / MU) % MU, b = i % MU;
-        double sp = 0, sa = 0;
-        for (int q = 0; q < NFQ; ++q) {
-            const double pa = ldg(&R.ephi[(e * NFQ + q) * MU + a]);
-            sp += pa * T1[(e * NFQ + q) * MU + b];
-            sa += pa * T2[(e * NFQ + q) * MU + b];
-        }
-        Sp[i] = sp;
+        double sa = 0;
+        for (int q = 0; q < NFQ; ++q) sa += ldg(&R.ephi[(e * NFQ + q) * MU + a]) * T2[(e * NFQ + q) * MU + b];
         Wa[i] = sa;
     }
     tm.sync();
@@ -510,7 +494,7 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
         const double p0 = k == 0 ? pxx[0] : (k == 1 ? pxy[0] : pyy[0]);
         const double p1 = k == 0 ? pxx[1] : (k == 1 ? pxy[1] : pyy[1]);
         const double p2 = k == 0 ? pxx[2] : (k == 1 ? pxy[2] : pyy[2]);
-        double F = p0 * Sp[ab] + p1 * Sp[MU * MU + ab] + p2 * Sp[2 * MU * MU + ab];
+        double F = p0 * ldg(&R.Sfac[ab]) + p1 * ldg(&R.Sfac[MU * MU + ab]) + p2 * ldg(&R.Sfac[2 * MU * MU + ab]);
         if (d == d2) F += adv[ab] + hw[0] * Wa[ab] + hw[1] * Wa[MU * MU + ab] + hw[2] * Wa[2 * MU * MU + ab];
         D[i] = ((r == x) ? g.detJ : 0.0) - c * F;
     }

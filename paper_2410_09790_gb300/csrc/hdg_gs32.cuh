@@ -1,4 +1,5 @@
-// Red-black block Gauss-Seidel right preconditioner for the FP32 inner Step-I GMRES.
+// Red-black block Gauss-Seidel right preconditioner for the FP32 inner Step-I GMRES. The block
+// inverses are stored colour-major (gs_slot), so each colour pass reads a contiguous half.
 //
 // On the structured triangulation every cell's three neighbours have the other index parity
 // (each square's lower and upper triangle; checked on the host before use), so the even cells
@@ -77,11 +78,11 @@ __global__ void k_gs_diag(EdgeTab<float> E, MeshDev M, const float *__restrict__
         TFOR(r, NU) vK[r] -= nbr_row<K, float>(E, t, r / MU, r % MU);
     }
     tm.sync();
+    const size_t bslot = (size_t)gs_slot(cell, M.ncells) * NU;     // the colour-major inverses
     TFOR(r, NU) {
-        const size_t gi = (size_t)cell * NU + r;
         float acc = 0.f;
 #pragma unroll 6
-        for (int q = 0; q < NU; ++q) acc += __ldg(&Binv[(size_t)q * nrows + gi]) * vK[q];
+        for (int q = 0; q < NU; ++q) acc += __ldg(&Binv[(size_t)q * nrows + bslot + r]) * vK[q];
         zK[r] = acc;
     }
     tm.sync();
@@ -156,13 +157,13 @@ __global__ void k_gs_combine(EdgeTab<float> E, MeshDev M, const float *__restric
         TFOR(r, NU) uK[r] -= nbr_row<K, float>(E, t, r / MU, r % MU);
     }
     tm.sync();
+    const size_t bslot = (size_t)gs_slot(cell, M.ncells) * NU;     // the colour-major inverses
     TFOR(r, NU) {
-        const size_t gi = (size_t)cell * NU + r;
         float a = 0.f;
 #pragma unroll 6
-        for (int q = 0; q < NU; ++q) a += __ldg(&Binv[(size_t)q * nrows + gi]) * uK[q];
+        for (int q = 0; q < NU; ++q) a += __ldg(&Binv[(size_t)q * nrows + bslot + r]) * uK[q];
         xK[r] = a;
-        x[gi] = (double)a;
+        x[(size_t)cell * NU + r] = (double)a;
     }
     if (col == 0) {
         tm.sync();

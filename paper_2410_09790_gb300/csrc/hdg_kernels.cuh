@@ -687,16 +687,26 @@ __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c
     if (!ok && tm.tid == 0) atomicExch(status, 1);
 }
 
+// storage slot of a cell's FP32 block inverse in the colour-major order of the red-black passes:
+// even (red) cells first, then odd (black) cells (ncells is even)
+__host__ __device__ __forceinline__ long long gs_slot(long long cell, long long ncells) {
+    return (cell & 1) * (ncells >> 1) + (cell >> 1);
+}
+
 // FP32 inverses of the Step-I diagonal blocks for the inner (preconditioner) solves, one warp per
 // cell with the block in registers: lane l holds rows l and l + 32 (< NU), Gauss-Jordan in place
 // without pivoting, row k reaching the other lanes by shuffles. No pivoting is needed: the block
 // M_K - c F_K has a positive definite symmetric part (mass plus the dissipative penalty and upwind
 // terms; the advection's symmetric part is c (div Q*)/2 |Q|^2, far below the mass), so every
 // leading block is nonsingular. A zero or non-finite pivot sets *status (singular block).
-// Dblk and Binv32 in the column-slice layout [col * nrows + cell * NU + row].
+// Dblk32 (optional) receives the block itself rounded to FP32 (the relaxed stage products).
+// Dblk, Dblk32 and Binv32 in the column-slice layout [col * nrows + slot * NU + row] with slot =
+// cell, or for Binv32 with by_colour set slot = gs_slot(cell) (the red-black Gauss-Seidel passes:
+// each colour's inverses contiguous, so a colour pass reads only its own half).
 template <int K>
 __global__ void __launch_bounds__(128) k_block_inv32(const double *__restrict__ Dblk, float *__restrict__ Binv32,
-                                                     long long ncells, int *status) {
+                                                     float *__restrict__ Dblk32, long long ncells, int by_colour,
+                                                     int *status) {
     wait_prior_kernel();
     constexpr int N = Dims<K>::NU;
     constexpr int R = (N + 31) / 32;
@@ -710,6 +720,15 @@ __global__ void __launch_bounds__(128) k_block_inv32(const double *__restrict__ 
         const int r = lane + 32 * s;
 #pragma unroll
         for (int j = 0; j < N; ++j) a[s][j] = r < N ? (float)__ldg(&Dblk[(size_t)j * nrows + (size_t)cell * N + r]) : 0.f;
+    }
+    if (Dblk32) {
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+            const int r = lane + 32 * s;
+            if (r < N)
+#pragma unroll
+                for (int j = 0; j < N; ++j) Dblk32[(size_t)j * nrows + (size_t)cell * N + r] = a[s][j];
+        }
     }
     bool ok = true;
 #pragma unroll
@@ -732,12 +751,13 @@ __global__ void __launch_bounds__(128) k_block_inv32(const double *__restrict__ 
             }
         }
     }
+    const long long slot = by_colour ? gs_slot(cell, ncells) : cell;
 #pragma unroll
     for (int s = 0; s < R; ++s) {
         const int r = lane + 32 * s;
         if (r < N)
 #pragma unroll
-            for (int j = 0; j < N; ++j) Binv32[(size_t)j * nrows + (size_t)cell * N + r] = a[s][j];
+            for (int j = 0; j < N; ++j) Binv32[(size_t)j * nrows + (size_t)slot * N + r] = a[s][j];
     }
     if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicExch(status, 1);
 }
@@ -832,12 +852,14 @@ __global__ void k_cell_apply_mf(EdgeTab<double> E, MeshDev M, const double *__re
 // *zslot_j (the FGMRES step) of the FGMRES's preconditioned vectors, when set): velocity rows
 // (M - cF)Q - c G(p, lambda) (diagonal block dense, neighbours matrix-free), constraint rows of
 // the cell (p-rows yp, the cell's lambda-row contributions v; summed per facet by k_facet_gather).
+// skip (optional): return at once when *skip is set (k_stage_apply32 takes that product in FP32).
 template <int K>
 __global__ void k_stage_apply(RefDev R, EdgeTab<double> E, MeshDev M, const double *__restrict__ Dblk,
                               const double *__restrict__ wq, double c, double tau, const double *Q,
                               const double *p, const double *lam, double *yQ, double *yp, double *v,
-                              float *yQ32, float *yp32, double *zslot, const int *zslot_j) {
+                              float *yQ32, float *yp32, double *zslot, const int *zslot_j, const int *skip) {
     wait_prior_kernel();
+    if (skip && *skip) return;
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NP = Dm::NP, NT = Dm::NT, NL = Dm::NL, NFQ = Dm::NFQ;
     constexpr int SCR = 6 * NFQ + NL + 2 * MU;
@@ -902,6 +924,11 @@ struct GmresState {
     // the FP32 inner solves keep their Hessenberg matrix, rotations, residual estimates and
     // least-squares solution in FP32 (tol32 = rtol * bnorm)
     float H32[(GM_M + 1) * GM_M], cs32[GM_M], sn32[GM_M], g32[GM_M + 1], y32[GM_M], tol32;
+    // relaxed products (stage FGMRES, HDG_MIXED): the next Arnoldi product may be taken in FP32
+    // (lowprec) once resid * relax <= rtol * bnorm; relax = 0: never. used32: the current cycle
+    // took an FP32 product (set by k_stage_apply32)
+    double relax;
+    int lowprec, used32;
 };
 
 __global__ void k_gm_set_cycle(GmresState *gs, int m) {
@@ -943,6 +970,7 @@ __device__ void gm_finish_step(GmresState *gs, int j, double hn, bool with_h2) {
     if (t == tl - 3) isc[0] = gs->m;
     if (t == tl - 4) isc[1] = gs->total;
     if (t == tl - 5) isc[2] = gs->maxit;
+    if (t == tl - 6) dsc[3] = gs->relax;
     __syncthreads();
     if (t != 0) return;
     Hc[j + 1] = hn;
@@ -963,6 +991,7 @@ __device__ void gm_finish_step(GmresState *gs, int j, double hn, bool with_h2) {
     gs->g[j + 1] = -s_ * gj;
     gs->g[j] = c_ * gj;
     gs->resid = resid;
+    gs->lowprec = (dsc[3] > 0.0 && resid * dsc[3] <= dsc[1] * dsc[2]) ? 1 : 0;
     const int total = isc[1] + 1;
     gs->total = total;
     gs->hcol[GM_M + 1] = hn;
@@ -998,7 +1027,8 @@ struct DevCount {
     long long stepI_iters, stepI_solves, trace_iters, trace_solves;
     long long outer_iters, stage_solves, stage_unconverged, breakdowns;
     unsigned long long launches;      // kernels run inside device-side loops
-    long long pad[7];
+    long long products32;             // stage-operator products taken in FP32 (k_stage_apply32)
+    long long pad[6];
 };
 
 __global__ void k_count_solve(DevCount *acc, const GmresState *gs, const Scalars *sc) {
@@ -1558,25 +1588,39 @@ __global__ void k_constraint(RefDev R, MeshDev M, double tau, const double *Q, c
 // --------------------------------------------------------------- generic (flexible) GMRES pieces
 // beta = ||r||, g = beta e1 (cycle start on an already formed residual r)
 __global__ void k_vec_start(const double *__restrict__ r, long long n, int first, RedBuf rb, GmresState *gs,
-                            double rtol, int maxit) {
+                            double rtol, int maxit, double relax) {
     wait_prior_kernel();
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(i, n) v[0] += r[i] * r[i];
     if (grid_sum<1>(rb, v, tot)) {
         double beta = sqrt(tot[0]);
+        const bool relaxed = !first && gs->used32;   // the cycle that just ended took FP32 products
         if (first) {
             gs->total = 0; gs->rtol = rtol; gs->maxit = maxit; gs->converged = 0; gs->breakdown = 0;
+            gs->relax = relax;
             if (first == 1) gs->bnorm = beta;           // first == 2: bnorm set by the caller
+        } else if (relaxed && !(beta < 0.5 * gs->beta)) {
+            // a cycle with relaxed products that did not halve the FP64 residual: the products'
+            // error is too large for this system, so the rest of the solve takes FP64 products
+            gs->relax = 0.0;
         }
+        gs->used32 = 0;
+        gs->lowprec = (gs->relax > 0.0 && beta * gs->relax <= gs->rtol * gs->bnorm) ? 1 : 0;
         gs->beta = beta;
         gs->inv32 = (float)(1.0 / beta);
         gs->resid = beta;
         for (int i = 0; i <= GM_M; ++i) gs->g[i] = 0.0;
         gs->g[0] = beta;
         gs->j = 0;
+        // convergence: the residual formed here in FP64 meets the tolerance, or the cycle that just
+        // ended took FP64 products only and its estimate met it (the estimate is then exact up to
+        // rounding, and an FP64 residual at the attainable-accuracy floor stays accepted); a cycle
+        // with relaxed FP32 products is judged on the FP64 residual alone, its estimate can be
+        // optimistic by the products' error
         if (!isfinite(beta)) { gs->breakdown = 2; gs->cycle_end = 1; }
         else if (beta <= gs->rtol * gs->bnorm || beta == 0.0) { gs->converged = 1; gs->cycle_end = 1; }
-        else gs->cycle_end = 0;
+        else if (!relaxed && gs->converged) gs->cycle_end = 1;
+        else { gs->converged = 0; gs->cycle_end = 0; }
     }
 }
 

@@ -28,11 +28,12 @@ double now_ms() {
 std::string config_key(const hdg_mesh_desc &m, const hdg_params &p) {
     char b[1024];
     snprintf(b, sizeof b,
-             "%d %a %a %d %d | %d %a %a %a %d %a %d %a %d %a %a %d %d %a %a %d %d %d %d %d %d %d %a",
+             "%d %a %a %d %d | %d %a %a %a %d %a %d %a %d %a %a %d %d %a %a %d %d %d %d %d %d %d %a %a",
              m.n, m.Lx, m.Ly, m.periodic_x, m.periodic_y, p.k, p.alpha, p.tau, p.delta_up, p.tableau, p.dt,
              p.n_richardson, p.richardson_rtol, p.richardson_max, p.trace_rtol, p.stepI_rtol, p.max_iters,
              p.stage_krylov, p.inner_stepI_rtol, p.inner_trace_rtol, p.trace_mg, p.device_loops, p.inner_trace_vcycles,
-             p.precision, p.inner_trace_fp32, p.trace_fp32_vcycle, p.inner_gs, p.timeout_ms);
+             p.precision, p.inner_trace_fp32, p.trace_fp32_vcycle, p.inner_gs, p.timeout_ms,
+             p.relax_eta);
     return b;
 }
 

@@ -26,6 +26,7 @@
 #include "hdg_mg_kernels.cuh"
 #include "hdg_mg32.cuh"
 #include "hdg_gs32.cuh"
+#include "hdg_stage32.cuh"
 #include "hdg_tracer.cuh"
 #include "mesh.h"
 #include "refelem.h"
@@ -205,6 +206,8 @@ struct hdg_ctx {
     // FP32 copies for the loose (inner) Step-I solves: tables, block inverses, weights, GMRES work
     float *ephi32 = nullptr, *pen32 = nullptr, *Binv32 = nullptr, *wq32 = nullptr, *utr32 = nullptr;
     float *nrm32 = nullptr;                                  // cell normals in FP32 [6 cell + 2 e + d]
+    // relaxed (FP32) stage-operator products: diagonal blocks, geometry, reference tables
+    float *Dblk32 = nullptr, *geo32 = nullptr, *Dhat32 = nullptr, *Ehat32 = nullptr;
     bool gs_ok = false;                                      // cells 2-coloured by index parity (hdg_gs32.cuh)
     float *gV32 = nullptr, *gw32 = nullptr, *gu32 = nullptr;
     cudaGraphExec_t g_stepI32 = nullptr;                     // one loose Step-I solve (host-driven mode)
@@ -1113,12 +1116,12 @@ struct Impl {
     // ---------------------------------------------------------------- Step I operator
     // Step-I solves to loose tolerances (the inner solves of the stage preconditioner) run in FP32;
     // tight ones in FP64. The assembly forms the block inverses the coming solves need.
-    static constexpr int INV64 = 1, INV32 = 2;
+    static constexpr int INV64 = 1, INV32 = 2, BLK32 = 4;     // BLK32: FP32 copy of the blocks (Dblk32)
     static bool loose(const hdg_ctx *c, double rtol) { return rtol >= 1e-4 && c->P.precision == HDG_MIXED; }
     static int inv_for(const hdg_ctx *c, double rtol) { return loose(c, rtol) ? INV32 : INV64; }
 
     // Step-I operator M - cc F(Qs): diagonal blocks, neighbour and penalty weights, and the
-    // block-Jacobi inverses named by inv (INV64 | INV32)
+    // block-Jacobi inverses named by inv (INV64 | INV32; with BLK32 also the blocks in FP32)
     static void assemble_stepI(hdg_ctx *c, const double *Qs, double cc, int inv) {
         CompTimer tm_(c, &c->S.ms_assembly);
         const size_t smem = sizeof(double) * ((inv & INV64) ? fimpl_smem_doubles<K>() : fimpl_smem_noinv_doubles<K>());
@@ -1129,9 +1132,14 @@ struct Impl {
             c->R, c->M, Qs, cc, c->P.alpha, c->P.delta_up, c->Dblk, c->wq, c->wq32, c->pen, c->pen32,
             (inv & INV64) ? c->Binv : nullptr, c->dstatus);
         CKL();
+        float *blk32 = (inv & BLK32) ? c->Dblk32 : nullptr;
         if (inv & INV32) {              // FP32 inverses: a warp per cell, the block in registers
             launch_k(k_block_inv32<K>, (unsigned)((c->ncells * 32 + 127) / 128), 128, 0, c->st, (const double *)c->Dblk,
-                     c->Binv32, c->ncells, c->dstatus);
+                     c->Binv32, blk32, c->ncells, use_gs(c) ? 1 : 0, c->dstatus);
+            CKL();
+        } else if (blk32) {
+            launch_k(k_to_f32, grid_for((long long)NU * c->nQ), VEC_THREADS, 0, c->st, (const double *)c->Dblk, blk32,
+                     (long long)NU * c->nQ);
             CKL();
         }
         c->inv_ok = inv;
@@ -1377,16 +1385,43 @@ struct Impl {
     // Stage operator y = A(c) x, x = (Q | p | lam) contiguous:
     //   yQ = (M - cF) Q - c G (p, lam),  (yp | ylam) = B Q + C (p, lam)   (one fused cell pass)
     // y32 (optional): an FP32 copy of y
+    // relaxed products in use: HDG_MIXED, relax_eta > 0 and the FP32 blocks allocated
+    static bool relax_on(const hdg_ctx *c) {
+        return c->P.precision == HDG_MIXED && c->P.relax_eta > 0 && c->Dblk32 != nullptr;
+    }
+    static double relax_of(const hdg_ctx *c) { return relax_on(c) ? c->P.relax_eta : 0.0; }
+
+    // the FP32 stage-operator kernel (runs when gs->lowprec is set)
+    static void stage_apply32(hdg_ctx *c, double cc, const double *Q, const double *p, const double *lam, double *yQ,
+                              double *yp, float *yQ32, float *yp32, double *zslot, const int *zslot_j,
+                              GmresState *gs, DevCount *acc) {
+        launch_k(k_stage_apply32<K>, cell_blocks(c), 128,
+                 sizeof(double) * TEAMS_PER_BLOCK * ((stage32_scratch_floats<K>() + 1) / 2), c->st, c->R,
+                 Ref32{c->Dhat32, c->Ehat32}, EdgeTab<float>{c->ephi32, c->pen32, c->nrm32}, c->M,
+                 (const float *)c->geo32, (const float *)c->Dblk32, (const float *)c->wq32, (float)cc, (float)c->P.tau, Q,
+                 p, lam, yQ, yp, c->vK, yQ32, yp32, zslot, zslot_j, gs, acc);
+    }
+
+    // y = A(c) x (the stage operator). relax_gs (optional, with relaxed products in use): the
+    // product is taken by the FP32 kernel when relax_gs->lowprec is set, else by the FP64 one
+    // (both are launched; the other returns at once).
     static void stage_apply(hdg_ctx *c, double cc, const double *x, double *y, float *y32 = nullptr,
-                            double *zslot = nullptr, const GmresState *zgs = nullptr) {
+                            double *zslot = nullptr, const GmresState *zgs = nullptr,
+                            GmresState *relax_gs = nullptr) {
         const double *Q = x, *p = x + c->nQ, *lam = x + c->nQ + c->nPv;
         double *yQ = y, *yp = y + c->nQ, *yl = y + c->nQ + c->nPv;
         float *yQ32 = y32, *yp32 = y32 ? y32 + c->nQ : nullptr, *yl32 = y32 ? y32 + c->nQ + c->nPv : nullptr;
+        const int *lowprec = relax_gs && relax_on(c) ? &relax_gs->lowprec : nullptr;
+        const int *zj = zgs ? &zgs->j : (const int *)nullptr;
         unsigned nb = cell_blocks(c);
         launch_k(k_stage_apply<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (6 * Dm::NFQ + NL + 2 * MU), c->st, 
             c->R, EdgeTab<double>{c->R.ephi, c->pen}, c->M, c->Dblk, c->wq, cc, c->P.tau, Q, p, lam, yQ, yp, c->vK,
-            yQ32, yp32, zslot, zgs ? &zgs->j : (const int *)nullptr);
+            yQ32, yp32, zslot, zj, lowprec);
         CKL();
+        if (lowprec) {
+            stage_apply32(c, cc, Q, p, lam, yQ, yp, yQ32, yp32, zslot, zj, relax_gs, c->capturing ? c->dcnt : nullptr);
+            CKL();
+        }
         launch_k(k_facet_gather<NT>, grid_for(c->nL), VEC_THREADS, 0, c->st, c->M, c->vK, nullptr, yl, yl32);
         CKL();
     }
@@ -1477,7 +1512,7 @@ struct Impl {
             stage_apply(c, cc, x, w);
             CK(cudaMemcpyAsync(res, b, 8 * N, cudaMemcpyDeviceToDevice, c->st));
             launch_k(k_axpby, g, VEC_THREADS, 0, c->st, -1.0, w, 1.0, res, N);
-            launch_k(k_vec_start, g, VEC_THREADS, 0, c->st, res, N, first, c->rb(), fgs, rtol, maxit);
+            launch_k(k_vec_start, g, VEC_THREADS, 0, c->st, res, N, first, c->rb(), fgs, rtol, maxit, relax_of(c));
             launch_k(k_gm_set_cycle, 1, 1, 0, c->st, fgs, GM_M);
             CKL();
         };
@@ -1492,7 +1527,7 @@ struct Impl {
                     c, [&](LoopCtl L2) { launch_k(k_loop_init, 1, 1, 0, c->st, L2, &fgs->cycle_end); },
                     [&](LoopCtl L2) {
                         chorin_precond(c, cc, c->fv, c->fz);
-                        stage_apply(c, cc, c->fz, w, fw32(c), c->fZ, fgs);      // also Z_j = fz
+                        stage_apply(c, cc, c->fz, w, fw32(c), c->fZ, fgs, fgs);   // also Z_j = fz
                         fgmres_orth(c, w, N, fgs, c->fv);
                         launch_k(k_loop_ctl, 1, 1, 0, c->st, L2, GM_M + 1, &fgs->cycle_end);
                         CKL();
@@ -1518,6 +1553,7 @@ struct Impl {
         c->S.richardson_iters += (int)D.outer_iters;
         c->S.stage_solves += (int)D.stage_solves;
         c->S.graph_kernels += (long long)static_kernels + (long long)D.launches;
+        c->S.stage_products32 += D.products32;
         if (D.breakdowns) throw std::domain_error("device-side solve: non-finite residual");
     }
 
@@ -1531,7 +1567,7 @@ struct Impl {
     // the Chorin split (Alg. 2's preconditioner; plain Alg. 2 is its Richardson iteration).
     static int stage_fgmres(hdg_ctx *c, double cc, const double *r, const double *Qsv, double *Q, double *p,
                             double *lam) {
-        assemble_stepI(c, Qsv, cc, inv_for(c, c->P.inner_stepI_rtol));
+        assemble_stepI(c, Qsv, cc, inv_for(c, c->P.inner_stepI_rtol) | (relax_on(c) ? BLK32 : 0));
         ensure_pre_maps(c, cc);
         CondCache &E = condense(c, cc);
         if (!c->capturing) {
@@ -1574,7 +1610,7 @@ struct Impl {
             CK(cudaMemcpyAsync(res, b, 8 * N, cudaMemcpyDeviceToDevice, c->st));
             launch_k(k_axpby, g, VEC_THREADS, 0, c->st, -1.0, w, 1.0, res, N);
             launch_k(k_vec_start, g, VEC_THREADS, 0, c->st, res, N, cyc == 0 ? 2 : 0, c->rb(), c->fgs,
-                                                     c->P.richardson_rtol, c->P.richardson_max);
+                                                     c->P.richardson_rtol, c->P.richardson_max, relax_of(c));
             launch_k(k_gm_set_cycle, 1, 1, 0, c->st, c->fgs, GM_M);
             CKL();
             CK(cudaMemcpyAsync(c->hfgs, c->fgs, sizeof(GmresState), cudaMemcpyDeviceToHost, c->st));
@@ -1586,7 +1622,8 @@ struct Impl {
             for (int j = 0; j < GM_M; ++j) {
                 double *Vj = c->fV + (size_t)j * N, *Zj = c->fZ + (size_t)j * N;
                 chorin_precond(c, cc, Vj, Zj);
-                stage_apply(c, cc, Zj, w, fw32(c));
+                if (relax_on(c) && c->hfgs->lowprec) c->S.stage_products32 += 1;    // the state read last
+                stage_apply(c, cc, Zj, w, fw32(c), nullptr, nullptr, c->fgs);
                 fgmres_orth(c, w, N, c->fgs, nullptr);
                 CKL();
                 CK(cudaMemcpyAsync(c->hfgs, c->fgs, sizeof(GmresState), cudaMemcpyDeviceToHost, c->st));
@@ -1599,7 +1636,7 @@ struct Impl {
             launch_k(k_gm_combine<double>, g, VEC_THREADS, 0, c->st, c->fZ, u, N, c->fgs);
             launch_k(k_vec_add, g, VEC_THREADS, 0, c->st, u, x, N);
             CKL();
-            if (c->hfgs->converged) { converged = 1; break; }
+            // the next pass forms the residual in FP64 and decides convergence on it
             if (outer >= c->P.richardson_max) break;
         }
         CK(cudaMemcpyAsync(Q, x, 8 * c->nQ, cudaMemcpyDeviceToDevice, c->st));
@@ -1933,9 +1970,15 @@ hdg_status map_exception() {
     }
 
 void begin_call(hdg_ctx *c) {
+    g_last_error.clear();
     settle_pending(c);
     c->S = hdg_stats{};
     CK(cudaEventRecord(c->e0, c->st));
+}
+// HDG_ERR_NOT_CONVERGED with its message (the state keeps the last iterate)
+hdg_status not_converged(const char *where) {
+    g_last_error = std::string(where) + ": a stage solve did not reach richardson_rtol within richardson_max iterations";
+    return HDG_ERR_NOT_CONVERGED;
 }
 void end_call(hdg_ctx *c, hdg_stats *out) {
     CK(cudaEventRecord(c->e1, c->st));
@@ -1974,6 +2017,7 @@ void hdg_default_params(hdg_params *p) {
     p->inner_trace_vcycles = 1;
     p->precision = HDG_MIXED;
     p->timeout_ms = 0.0;
+    p->relax_eta = 1e-5;
     p->inner_trace_fp32 = 1;
     p->trace_fp32_vcycle = 1;
     p->inner_gs = 1;
@@ -2050,6 +2094,7 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
     if (params->tableau < HDG_ARS222 || params->tableau > HDG_SSP3_433) return HDG_ERR_INVALID_ARG;
     if (params->precision != HDG_FP64 && params->precision != HDG_MIXED) return HDG_ERR_INVALID_ARG;
     if (!(params->timeout_ms >= 0)) return HDG_ERR_INVALID_ARG;
+    if (!(params->relax_eta >= 0) || !std::isfinite(params->relax_eta)) return HDG_ERR_INVALID_ARG;
     hdg_ctx *c = new (std::nothrow) hdg_ctx();
     if (!c) return HDG_ERR_OOM;
     try {
@@ -2084,7 +2129,8 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         const RefTables &T = c->T;
         std::vector<const std::vector<double> *> tabs = {&T.qw, &T.phi, &T.dphi, &T.fw, &T.ephi, &T.leg,
                                                          &T.Dhat, &T.Ehat, &T.Tpp, &T.bdm_inv, &T.Iv, &T.nod_u,
-                                                         &T.nod_p, &T.mod_u, &T.mod_p, &T.nod_t, &T.mod_t};
+                                                         &T.nod_p, &T.mod_u, &T.mod_p, &T.nod_t, &T.mod_t,
+                                                         &T.Sfac, &T.Tadv};
         size_t tot = 0;
         for (auto *v : tabs) tot += v->size();
         std::vector<double> hbuf;
@@ -2095,7 +2141,7 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         CK(cudaMemcpy(c->dref, hbuf.data(), tot * sizeof(double), cudaMemcpyHostToDevice));
         const double **dst[] = {&c->R.qw, &c->R.phi, &c->R.dphi, &c->R.fw, &c->R.ephi, &c->R.leg, &c->R.Dhat,
                                 &c->R.Ehat, &c->R.Tpp, &c->R.bdm_inv, &c->R.Iv, &c->R.nod_u, &c->R.nod_p,
-                                &c->R.mod_u, &c->R.mod_p, &c->R.nod_t, &c->R.mod_t};
+                                &c->R.mod_u, &c->R.mod_p, &c->R.nod_t, &c->R.mod_t, &c->R.Sfac, &c->R.Tadv};
         for (size_t i = 0; i < tabs.size(); ++i) *dst[i] = c->dref + offs[i];
         // mesh
         c->geo = c->alloc<CellGeo>(c->ncells);
@@ -2183,6 +2229,27 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
             c->fgs = c->alloc<GmresState>(1);
             CK(cudaMemset(c->fgs, 0, sizeof(GmresState)));
             CK(cudaMallocHost(&c->hfgs, sizeof(GmresState)));
+            if (params->precision == HDG_MIXED && params->relax_eta > 0) {
+                c->Dblk32 = c->alloc<float>((size_t)c->NU * nQ);
+                std::vector<float> g32((size_t)GEO32 * c->ncells);
+                for (long long k = 0; k < c->ncells; ++k) {
+                    const CellGeo &G = c->H.geo[k];
+                    float *o = &g32[(size_t)GEO32 * k];
+                    for (int i = 0; i < 4; ++i) o[i] = (float)G.Jinv[i];
+                    o[4] = (float)G.detJ;
+                    for (int e = 0; e < 3; ++e) o[5 + e] = (float)G.h[e];
+                }
+                auto up32 = [&](const std::vector<double> &v) {
+                    std::vector<float> f(v.begin(), v.end());
+                    float *d = c->alloc<float>(f.size());
+                    CK(cudaMemcpy(d, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+                    return d;
+                };
+                c->geo32 = c->alloc<float>(g32.size());
+                CK(cudaMemcpy(c->geo32, g32.data(), g32.size() * sizeof(float), cudaMemcpyHostToDevice));
+                c->Dhat32 = up32(c->T.Dhat);
+                c->Ehat32 = up32(c->T.Ehat);
+            }
         }
         for (auto &x : c->q) x = c->alloc<double>(nQ);
         for (auto &x : c->pp) x = c->alloc<double>(nP);
@@ -2422,7 +2489,7 @@ hdg_status hdg_imex_step(hdg_ctx *c, int nsteps, hdg_stats *stats) {
         if (stats) *stats = c->S;
         return s;
     }
-    return nc ? HDG_ERR_NOT_CONVERGED : HDG_OK;
+    return nc ? not_converged("hdg_imex_step") : HDG_OK;
 }
 
 hdg_status hdg_batch_step(hdg_ctx *const *ctxs, int n, int nsteps, hdg_stats *stats) {
@@ -2479,7 +2546,7 @@ hdg_status hdg_batch_step(hdg_ctx *const *ctxs, int n, int nsteps, hdg_stats *st
         }
         any |= nc[i];
     }
-    return any ? HDG_ERR_NOT_CONVERGED : HDG_OK;
+    return any ? not_converged("hdg_batch_step") : HDG_OK;
 }
 
 size_t hdg_ctx_bytes(const hdg_ctx *c) { return c ? c->bytes : 0; }
@@ -2510,8 +2577,11 @@ double hdg_estimate_bytes(const hdg_mesh_desc *mesh, const hdg_params *params) {
     b += 8 * 2 * NU * nQ + 4 * NU * nQ;                                    // Dblk, Binv, Binv32
     b += 8 * 3 * nc * 3 * nfq * 2 + 4 * 3 * nc * 3 * nfq * 2;             // weights, edge values
     b += 4 * (32 + 2) * nQ + 8 * (32 + 5) * nQ;                            // Step-I Krylov (FP32, FP64)
-    if (params->n_richardson <= 0 && params->stage_krylov)
+    if (params->n_richardson <= 0 && params->stage_krylov) {
         b += 8 * (31 + 30 + 7) * N + 4 * 32 * N;                           // stage FGMRES
+        if (params->precision == HDG_MIXED && params->relax_eta > 0)
+            b += 4 * NU * nQ + 4 * 8 * nc;                                 // FP32 blocks, geometry
+    }
     b += 8 * (8 * nQ + 3 * nP + 3 * nL + nc * NL + 10 * nL);               // temporaries, trace work
     b += ncond * 8 * (nc * (NL * NL + NP * NL + NP * NP) + 6 * NT * nL) + ncond * 4 * 5 * nf;
     if (params->precision == HDG_MIXED)
@@ -2545,7 +2615,7 @@ hdg_status hdg_solve_stage(hdg_ctx *c, double cc, const double *R, const double 
         if (stats) *stats = c->S;
         return s;
     }
-    return nc ? HDG_ERR_NOT_CONVERGED : HDG_OK;
+    return nc ? not_converged("hdg_solve_stage") : HDG_OK;
 }
 
 hdg_status hdg_bdm_project(hdg_ctx *c, const double *Q, double *Qstar) {
@@ -2688,9 +2758,10 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *c, hdg_stats *stats) {
 }
 
 hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *ms, double *bytes) {
-    if (!c || reps < 1 || !ms || !bytes || which < 0 || which > 10 || (which != 1 && !(cc > 0)))
+    if (!c || reps < 1 || !ms || !bytes || which < 0 || which > 14 || (which != 1 && !(cc > 0)))
         return HDG_ERR_INVALID_ARG;
-    if (which >= 2 && which != 8 && !c->fv) return HDG_ERR_INVALID_ARG;
+    if (which == 12 && !(c->Dblk32 && c->P.precision == HDG_MIXED && c->P.relax_eta > 0)) return HDG_ERR_INVALID_ARG;
+    if (which >= 2 && which != 8 && which != 11 && which != 12 && !c->fv) return HDG_ERR_INVALID_ARG;
     try {
         settle_pending(c);
         if (which == 10) {
@@ -2733,9 +2804,11 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
             *ms = t10;
             return HDG_OK;
         }
-        if (which == 6 || which == 9) {
+        if (which == 6 || which == 9 || which == 13 || which == 14) {
             double t6_ms = 0.0;
             DISPATCH(c, {
+                if (which >= 13 && !I::use_gs(c)) throw std::invalid_argument("hdg_time_kernel: modes 13, 14 time the "
+                                                                              "red-black Gauss-Seidel inner kernels (inner_gs)");
                 // one FP32 inner Step-I solve fills the basis and edge values; then the Arnoldi
                 // product of step j = 4 is launched alone
                 constexpr int J = 4;
@@ -2753,14 +2826,23 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 // kernel that puts step J back (the solve above ended its cycle); that kernel's own
                 // time, measured alone, is subtracted
                 auto reset = [&]() { launch_k(k_gm_set_step, 1, 1, 0, c->st, c->gs, J); };
+                const size_t smg = sizeof(float) * TEAMS_PER_BLOCK * (2 * I::NU + 6 * I::Dm::NFQ);
                 auto launch = [&]() {
                     reset();
                     if (which == 6)
                         launch_k(k_gm_apply_mf<I::K_, float, true>, ab, 128, sm, c->st, E, c->M, c->wq32, c->utr32,
                                  c->gw32, c->gV32, c->rb(), c->gs);
-                    else
+                    else if (which == 9)
                         launch_k(k_gm_precond_mf<I::K_, float, true>, cb, 128, sizeof(float) * TEAMS_PER_BLOCK * 2 * I::NU,
                                  c->st, E, c->M, c->Binv32, c->gw32, c->gV32, c->utr32, c->gs);
+                    else if (which == 13)       // both colours (the time per launch is half the pair's)
+                        for (int col = 0; col < 2; ++col)
+                            launch_k(k_gs_diag<I::K_>, I::gs_blocks(c), 128, smg, c->st, E, c->M, (const float *)c->Binv32,
+                                     (const float *)c->gw32, c->gV32, c->utr32, (const float *)c->wq32,
+                                     (const GmresState *)c->gs, col);
+                    else
+                        launch_k(k_gs_apply<I::K_>, ab, 128, sm, c->st, E, c->M, (const float *)c->wq32,
+                                 (const float *)c->utr32, c->gw32, (const float *)c->gV32, c->rb(), c->gs);
                 };
                 launch();
                 CKL();
@@ -2779,18 +2861,27 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 t6_ms = (double)(t_pair - t_reset) / reps;
                 cudaGraphExecDestroy(ex);
                 const int nfq = I::Dm::NFQ;
+                const double nc = (double)c->ncells;
                 if (which == 6)   // neighbour edge values (2 floats per point) + weights + v_j read + w
                                   // written + the J + 1 basis vectors of the dots
-                    *bytes = 4.0 * ((double)c->ncells * 3 * nfq * 3 + 2.0 * c->nQ + (J + 1.0) * c->nQ);
-                else              // block inverses + w read + V_0..V_{J-1} read (projections) + V_J
-                                  // written + edge values written (2 floats per point)
-                    *bytes = 4.0 * ((double)c->ncells * I::NU * I::NU + (J + 2.0) * c->nQ +
-                                    (double)c->ncells * 3 * nfq * 2);
+                    *bytes = 4.0 * (nc * 3 * nfq * 3 + 2.0 * c->nQ + (J + 1.0) * c->nQ);
+                else if (which == 9)   // block inverses + w read + V_0..V_{J-1} read (projections) + V_J
+                                       // written + edge values written (2 floats per point)
+                    *bytes = 4.0 * (nc * I::NU * I::NU + (J + 2.0) * c->nQ + nc * 3 * nfq * 2);
+                else if (which == 13) {   // per launch (one colour, half the cells): the colour's block
+                                          // inverses, w, V_0..V_{J-1} read, V_J and edge values written;
+                                          // black also reads its red neighbours' edge values and weights
+                    *bytes = 0.5 * 4.0 * (nc * I::NU * I::NU + (J + 2.0) * c->nQ + nc * 3 * nfq * 2 +
+                                          0.5 * nc * 3 * nfq * 3);
+                    t6_ms *= 0.5;
+                } else                // red cells' neighbour edge values and weights, v_j read, w written,
+                                      // the J + 1 basis vectors of the dots
+                    *bytes = 4.0 * (0.5 * nc * 3 * nfq * 3 + 2.0 * c->nQ + (J + 1.0) * c->nQ);
             });
             *ms = t6_ms;
             return HDG_OK;
         }
-        if (which >= 2 && which != 8) {
+        if (which >= 2 && which != 8 && which != 11 && which != 12 && which != 13 && which != 14) {
             DISPATCH(c, {
                 // operator of a stage at coefficient cc around the current state; v = (M Q, 0, 0)
                 I::bdm(c, c->Q, c->q[5]);
@@ -2847,6 +2938,39 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 CK(cudaEventRecord(c->e0, c->st));
                 for (int r = 0; r < reps; ++r) launch();
                 CK(cudaEventRecord(c->e1, c->st));
+            } else if (which == 11) {
+                // k_condense alone for coefficient cc (rewrites the cached factors with the same
+                // values); bytes: geometry and flip read + S_K, Z_K, A_K^-1 written
+                CondCache &E = I::condense(c, cc);
+                const int NP = I::NP, NL = I::NL;
+                const size_t smem = sizeof(double) * (NP * NU + NL * NU + 2 * NP * NP + 2 * NP * NL + NL * NL);
+                b = (double)c->ncells * (sizeof(CellGeo) + 3 * sizeof(int) + 8.0 * (NL * NL + NP * NL + NP * NP));
+                auto launch = [&]() {
+                    launch_k(k_condense<I::K_>, (unsigned)c->ncells, 128, smem, c->st, c->R, c->M, cc, c->P.tau, E.Scell,
+                             E.Zc, E.Ac);
+                };
+                launch();
+                CKL();
+                CK(cudaEventRecord(c->e0, c->st));
+                for (int r = 0; r < reps; ++r) launch();
+                CK(cudaEventRecord(c->e1, c->st));
+            } else if (which == 12) {
+                // k_stage_apply32 alone (its flag forced on), like 8; bytes: FP32 diagonal blocks,
+                // weights, geometry and normals + neighbour maps + Q, p, lambda read + yQ, yp, v written
+                const int nfq = (3 * c->K + 5) / 2;
+                b = 4.0 * c->ncells * ((double)NU * NU + 3 * nfq + GEO32 + 6) + 4.0 * 6 * c->ncells +
+                    8.0 * (2.0 * c->nQ + 2.0 * c->nPv + c->nL + (double)c->ncells * 3 * NT);
+                const int one = 1;
+                CK(cudaMemcpyAsync(&c->fgs->lowprec, &one, sizeof(int), cudaMemcpyHostToDevice, c->st));
+                auto launch = [&]() {
+                    I::stage_apply32(c, cc, c->Q, c->p, c->lam, c->q[6], c->pp[1], (float *)nullptr, (float *)nullptr,
+                                     (double *)nullptr, (const int *)nullptr, c->fgs, (DevCount *)nullptr);
+                };
+                launch();
+                CKL();
+                CK(cudaEventRecord(c->e0, c->st));
+                for (int r = 0; r < reps; ++r) launch();
+                CK(cudaEventRecord(c->e1, c->st));
             } else if (which == 8) {
                 // k_stage_apply alone on the operator last assembled (c scales the pressure and trace
                 // coupling), input the current state (Q, p, lambda); bytes: diagonal blocks +
@@ -2859,7 +2983,8 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 auto launch = [&]() {
                     launch_k(k_stage_apply<I::K_>, nb, 128, sm, c->st, c->R, EdgeTab<double>{c->R.ephi, c->pen}, c->M,
                              c->Dblk, c->wq, cc, c->P.tau, c->Q, c->p, c->lam, c->q[6], c->pp[1], c->vK,
-                             (float *)nullptr, (float *)nullptr, (double *)nullptr, (const int *)nullptr);
+                             (float *)nullptr, (float *)nullptr, (double *)nullptr, (const int *)nullptr,
+                             (const int *)nullptr);
                 };
                 launch();
                 CKL();

@@ -247,6 +247,28 @@ RefTables build_tables(int k) {
                 T.Tpp[(e * np + b) * np + c] = (double)s;
             }
     }
+    // facet mass of each reference edge (the penalty term's matrices) and the volume advection
+    // tensor: the advection block of a cell is sum_{r,c} g_rc Tadv[r][c] with g_rc the
+    // coefficients of (J^-1 Q*)_r, the same quadrature sum regrouped (exact in exact arithmetic)
+    T.Sfac.assign(3 * mu * mu, 0.0);
+    for (int e = 0; e < 3; ++e)
+        for (int a = 0; a < mu; ++a)
+            for (int b = 0; b < mu; ++b) {
+                ld s = 0;
+                for (int q = 0; q < T.nfq; ++q)
+                    s += fwL[q] * ephiL[(e * T.nfq + q) * mu + a] * ephiL[(e * T.nfq + q) * mu + b];
+                T.Sfac[(e * mu + a) * mu + b] = (double)s;
+            }
+    T.Tadv.assign(2 * mu * mu * mu, 0.0);
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < mu; ++c)
+            for (int a = 0; a < mu; ++a)
+                for (int b = 0; b < mu; ++b) {
+                    ld s = 0;
+                    for (int q = 0; q < T.nq; ++q)
+                        s += (ld)T.qw[q] * phiL[q * mu + a] * phiL[q * mu + c] * dphiL[(q * mu + b) * 2 + r];
+                    T.Tadv[((r * mu + c) * mu + a) * mu + b] = (double)s;
+                }
     // interior BDM moments against the first-kind Nedelec space N_k on T:
     // [P_{k-1}]^2 (monomials x^i y^j) and (-y, x) * homogeneous degree k-1
     const int nv = T.nv;

@@ -31,6 +31,8 @@ struct RefTables {
     std::vector<double> Dhat;             // [r][b][a]        2 x np x mu  = int psi_b d_r phi_a
     std::vector<double> Ehat;             // [e][j][a]        3 x nt x mu  = int_0^1 phi_a(x_e(s)) L_j(s) ds
     std::vector<double> Tpp;              // [e][b][c]        3 x np x np  = int_0^1 psi_b psi_c ds
+    std::vector<double> Sfac;             // [e][a][b]        3 x mu x mu  = sum_q fw_q phi_a(e,q) phi_b(e,q)
+    std::vector<double> Tadv;             // [r][c][a][b]     2 x mu^3     = sum_q w_q phi_a phi_c d_r phi_b
     std::vector<double> bdm_inv;          // [(d,a)][dof]     nu x nu      inverse BDM moment matrix
     std::vector<double> Iv;               // [a][v][d]        mu x nv x 2  = int_T phi_a v_d (Nedelec N_k)
     std::vector<double> nod_u, nod_p;     // nodal -> modal: [a][node]

@@ -42,7 +42,8 @@ class hdg_params(ctypes.Structure):
                 ('inner_trace_rtol', ctypes.c_double), ('trace_mg', ctypes.c_int),
                 ('device_loops', ctypes.c_int), ('inner_trace_vcycles', ctypes.c_int),
                 ('precision', ctypes.c_int), ('inner_trace_fp32', ctypes.c_int),
-                ('trace_fp32_vcycle', ctypes.c_int), ('inner_gs', ctypes.c_int), ('timeout_ms', ctypes.c_double)]
+                ('trace_fp32_vcycle', ctypes.c_int), ('inner_gs', ctypes.c_int), ('timeout_ms', ctypes.c_double),
+                ('relax_eta', ctypes.c_double)]
 
 
 class hdg_stats(ctypes.Structure):
@@ -52,7 +53,7 @@ class hdg_stats(ctypes.Structure):
                 ('last_update_norm', ctypes.c_double), ('last_trace_relres', ctypes.c_double),
                 ('ms_total', ctypes.c_double), ('ms_trace', ctypes.c_double), ('ms_stepI', ctypes.c_double),
                 ('ms_assembly', ctypes.c_double), ('ms_bdm', ctypes.c_double),
-                ('graph_kernels', ctypes.c_longlong)]
+                ('graph_kernels', ctypes.c_longlong), ('stage_products32', ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

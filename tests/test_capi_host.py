@@ -56,6 +56,7 @@ def test_default_params():
     assert (p.stage_krylov, p.trace_mg, p.device_loops, p.inner_trace_vcycles) == (1, 1, 1, 1)
     assert (p.inner_trace_fp32, p.trace_fp32_vcycle, p.inner_gs, p.precision) == (1, 1, 1, 1)
     assert p.inner_stepI_rtol == 2e-2 and p.inner_trace_rtol == 1e-1
+    assert p.timeout_ms == 0.0 and p.relax_eta == 1e-5
 
 
 def test_status_strings():
@@ -114,3 +115,19 @@ def test_reference_basis_orthonormal_and_hierarchical(m):
     mono = np.stack([pts[:, 0] ** a * pts[:, 1] ** (d - a) for d in range(m + 1) for a in range(d + 1)], 1)
     coef = np.linalg.lstsq(V, mono, rcond=None)[0]
     assert np.abs(V @ coef - mono).max() < 1e-12
+
+
+def test_memory_estimate_host_only():
+    # hdg_estimate_bytes (host code, used by the server's admission): positive, growing with the
+    # mesh and the degree, the stage FGMRES bases counted only when stages are solved to tolerance,
+    # the FP32 cell maps only in mixed precision; 0 for an invalid degree
+    est = lambda n, k, **kw: H.hdg_estimate_bytes(n, k, tableau='ARS343', **kw)
+    assert est(16, 2) > 0
+    assert est(32, 2) > 3.5 * est(16, 2) and est(32, 3) > est(32, 2) > est(32, 1)
+    assert est(32, 3, n_richardson=0, stage_krylov=1) > est(32, 3, n_richardson=2)
+    assert est(32, 3, n_richardson=0, precision='MIXED') > est(32, 3, n_richardson=0, precision='FP64')
+    # the FP32 copy of the diagonal blocks (relaxed products): 4 NU^2 bytes per cell and more
+    nu, nc = 2 * 10, 2 * 32 * 32
+    d = est(32, 3, n_richardson=0, precision='MIXED') - est(32, 3, n_richardson=0, precision='MIXED', relax_eta=0.0)
+    assert d >= 4 * nu * nu * nc
+    assert H.hdg_estimate_bytes(16, 5) == 0.0

@@ -203,7 +203,8 @@ def test_device_loops_match_host_loops(mg):
         ctx.close()
     for a, b in zip(*outs):
         assert np.array_equal(a, b)
-    for key in ('richardson_iters', 'stepI_solves', 'stepI_iters', 'trace_solves', 'trace_iters'):
+    for key in ('richardson_iters', 'stepI_solves', 'stepI_iters', 'trace_solves', 'trace_iters',
+                'stage_products32'):
         assert stats[0][key] == stats[1][key] > 0, key
 
 
@@ -228,6 +229,38 @@ def test_precision_fp64_and_mixed_reach_the_same_stage_solutions(k):
     assert_close(outs[1][2], outs[0][2], 1e-10, 'lambda')
     for st in stats:
         assert st['status'] == 0 and st['stepI_solves'] > 0 and st['stepI_iters'] >= st['stepI_solves']
+
+
+@pytest.mark.parametrize('n,px,k', [(8, True, 1), (8, True, 2), (8, True, 3), (8, True, 4), (16, False, 4),
+                                    (3, True, 2)])
+def test_relaxed_fp32_products_keep_the_stage_tolerance(n, px, k):
+    # HDG_MIXED takes the late Arnoldi products of the stage FGMRES in FP32 (relax_eta): the
+    # restart and final checks form the residual in FP64, so every eta meets the same stage
+    # tolerance and the results agree to it; eta = 0 takes no FP32 product, the default some, and
+    # a deliberately reckless eta = 1e-13 (the FP32 product assumed exact: FP32 products from the
+    # first step on) still converges: a cycle that does not halve the FP64 residual switches the
+    # rest of its solve to FP64 products
+    Q0 = W.nodal_velocity(n, k, lambda x, y: W.shear_layer(x, y, width=0.1, amp=0.05), noise=1e-3, seed=9)
+    outs, stats = [], []
+    for eta in (0.0, 1e-4, 1e-13):
+        ctx = H().Context(n, k, periodic_x=px, tableau='ARS343', dt=0.01, n_richardson=0, stage_krylov=1,
+                          richardson_rtol=1e-12, richardson_max=400, relax_eta=eta)
+        ctx.hdg_set_state(cuda(Q0))
+        ctx.hdg_reconstruct_pressure()
+        stats.append(ctx.hdg_imex_step(2))
+        outs.append([host(x) for x in ctx.hdg_get_state()[:3]])
+        ctx.close()
+    for i in (1, 2):
+        assert_close(outs[i][0], outs[0][0], 1e-10, 'Q')
+        assert_close(outs[i][1], outs[0][1], 1e-10, 'p')
+        assert_close(outs[i][2], outs[0][2], 1e-10, 'lambda')
+    for st in stats:
+        assert st['status'] == 0
+    assert stats[0]['stage_products32'] == 0
+    assert 0 < stats[1]['stage_products32'] < stats[1]['richardson_iters']
+    assert stats[2]['stage_products32'] > 0
+    assert stats[1]['richardson_iters'] <= stats[0]['richardson_iters'] + 2 * stats[0]['stage_solves'], \
+        (stats[1]['richardson_iters'], stats[0]['richardson_iters'])
 
 
 @pytest.mark.parametrize('n,px,k', [(8, True, 1), (8, True, 2), (8, True, 3), (8, True, 4), (16, False, 3),
@@ -448,7 +481,7 @@ def test_time_kernel_modes_and_algorithmic_bytes():
     nu, nfq = 2 * mu, (3 * k + 5) // 2
     nc = ctx.nQ // nu
     res = {}
-    for which in range(11):
+    for which in range(12):
         ms, b = ctx.hdg_time_kernel(which, 1.0 if which == 1 else cstage, 3)
         assert ms > 0.0 and np.isfinite(ms), (which, ms)
         res[which] = b
