@@ -1,5 +1,12 @@
-// Red-black block Gauss-Seidel right preconditioner for the FP32 inner Step-I GMRES. The block
-// inverses are stored colour-major (gs_slot), so each colour pass reads a contiguous half.
+// Red-black block Gauss-Seidel right preconditioner for the FP32 inner Step-I GMRES.
+//
+// The colour passes are bound by reading the FP32 block inverses (NU x NU per cell, 7 KB at
+// k = 4). They are stored for these passes as one contiguous block per cell (GsBlk: column-major,
+// rows padded to a multiple of 4, blocks padded to 128 bytes) in colour-major order (gs_slot),
+// and a warp applies its cell's block with 16-byte loads: lane s*G + g holds row group g (rows
+// 4g..4g+3) of the columns q = s, s + S, ..., so each load instruction of the warp covers
+// consecutive columns of one block (352 contiguous bytes at k = 4), and the S partial sums of a
+// row group are added by shuffles in a fixed order.
 //
 // On the structured triangulation every cell's three neighbours have the other index parity
 // (each square's lower and upper triangle; checked on the host before use), so the even cells
@@ -17,13 +24,46 @@
 
 namespace hdg {
 
-// the cell of colour col handled by this team: teams of a block take consecutive same-colour
-// cells, so a warp's two teams follow the same path (the cell count is a multiple of 4, so they
-// are in range together)
+// the cell of colour col handled by this warp: the warps of a block take consecutive same-colour
+// cells
 #define GS_CELL(COL)                                                                 \
-    const int team = threadIdx.x / TEAM_LANES, tpb = blockDim.x / TEAM_LANES;        \
+    const int team = threadIdx.x >> 5, tpb = blockDim.x >> 5;                        \
     const int cell = 2 * (blockIdx.x * tpb + team) + (COL);                          \
-    Team tm{(int)(threadIdx.x % TEAM_LANES), TEAM_LANES};
+    Team tm{(int)(threadIdx.x & 31), 32};
+
+// z = B v for the block B of storage slot `slot` (a warp; v in shared memory, NU entries; z's NU
+// entries written to shared memory)
+template <int K>
+__device__ __forceinline__ void warp_block_apply(const float *__restrict__ Binv, long long slot, const float *v,
+                                                 float *z) {
+    typedef GsBlk<K> B;
+    const int lane = (int)(threadIdx.x & 31), g = lane % B::G, s = lane / B::G;
+    const float4 *blk = reinterpret_cast<const float4 *>(Binv + (size_t)slot * B::SIZE);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    if (s < B::S) {
+#pragma unroll 4
+        for (int q = s; q < B::NU; q += B::S) {
+            const float4 b = __ldg(blk + q * (B::NUP / 4) + g);
+            const float vq = v[q];
+            a0 = fmaf(b.x, vq, a0); a1 = fmaf(b.y, vq, a1);
+            a2 = fmaf(b.z, vq, a2); a3 = fmaf(b.w, vq, a3);
+        }
+    }
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+#pragma unroll
+    for (int s2 = 0; s2 < B::S; ++s2) {             // the subsets' partial sums, in order
+        const int src = s2 * B::G + g;
+        t0 += __shfl_sync(0xffffffffu, a0, src); t1 += __shfl_sync(0xffffffffu, a1, src);
+        t2 += __shfl_sync(0xffffffffu, a2, src); t3 += __shfl_sync(0xffffffffu, a3, src);
+    }
+    if (s == 0) {
+        const int r = 4 * g;
+        if (r < B::NU) z[r] = t0;
+        if (r + 1 < B::NU) z[r + 1] = t1;
+        if (r + 2 < B::NU) z[r + 2] = t2;
+        if (r + 3 < B::NU) z[r + 3] = t3;
+    }
+}
 
 // edge values of the cell's z (zK: its NU coefficients in shared memory) -> utr
 template <int K>
@@ -78,13 +118,7 @@ __global__ void k_gs_diag(EdgeTab<float> E, MeshDev M, const float *__restrict__
         TFOR(r, NU) vK[r] -= nbr_row<K, float>(E, t, r / MU, r % MU);
     }
     tm.sync();
-    const size_t bslot = (size_t)gs_slot(cell, M.ncells) * NU;     // the colour-major inverses
-    TFOR(r, NU) {
-        float acc = 0.f;
-#pragma unroll 6
-        for (int q = 0; q < NU; ++q) acc += __ldg(&Binv[(size_t)q * nrows + bslot + r]) * vK[q];
-        zK[r] = acc;
-    }
+    warp_block_apply<K>(Binv, gs_slot(cell, M.ncells), vK, zK);
     tm.sync();
     team_edge_values<K>(tm, E, cell, zK, utr);
 }
@@ -157,14 +191,9 @@ __global__ void k_gs_combine(EdgeTab<float> E, MeshDev M, const float *__restric
         TFOR(r, NU) uK[r] -= nbr_row<K, float>(E, t, r / MU, r % MU);
     }
     tm.sync();
-    const size_t bslot = (size_t)gs_slot(cell, M.ncells) * NU;     // the colour-major inverses
-    TFOR(r, NU) {
-        float a = 0.f;
-#pragma unroll 6
-        for (int q = 0; q < NU; ++q) a += __ldg(&Binv[(size_t)q * nrows + bslot + r]) * uK[q];
-        xK[r] = a;
-        x[(size_t)cell * NU + r] = (double)a;
-    }
+    warp_block_apply<K>(Binv, gs_slot(cell, M.ncells), uK, xK);
+    tm.sync();
+    TFOR(r, NU) x[(size_t)cell * NU + r] = (double)xK[r];
     if (col == 0) {
         tm.sync();
         team_edge_values<K>(tm, E, cell, xK, utr);

@@ -693,6 +693,18 @@ __host__ __device__ __forceinline__ long long gs_slot(long long cell, long long 
     return (cell & 1) * (ncells >> 1) + (cell >> 1);
 }
 
+// per-cell block layout of the FP32 inverses for the red-black passes (hdg_gs32.cuh): the block
+// of slot s at [s * SIZE], column-major with the rows padded to NUP (zeros), SIZE a multiple of
+// 32 floats; G groups of 4 rows, S column subsets for a warp's lanes s * G + g
+template <int K>
+struct GsBlk {
+    static constexpr int NU = Dims<K>::NU;
+    static constexpr int NUP = (NU + 3) / 4 * 4;
+    static constexpr int SIZE = (NU * NUP + 31) / 32 * 32;
+    static constexpr int G = NUP / 4;
+    static constexpr int S = 32 / G;
+};
+
 // FP32 inverses of the Step-I diagonal blocks for the inner (preconditioner) solves, one warp per
 // cell with the block in registers: lane l holds rows l and l + 32 (< NU), Gauss-Jordan in place
 // without pivoting, row k reaching the other lanes by shuffles. No pivoting is needed: the block
@@ -700,9 +712,8 @@ __host__ __device__ __forceinline__ long long gs_slot(long long cell, long long 
 // terms; the advection's symmetric part is c (div Q*)/2 |Q|^2, far below the mass), so every
 // leading block is nonsingular. A zero or non-finite pivot sets *status (singular block).
 // Dblk32 (optional) receives the block itself rounded to FP32 (the relaxed stage products).
-// Dblk, Dblk32 and Binv32 in the column-slice layout [col * nrows + slot * NU + row] with slot =
-// cell, or for Binv32 with by_colour set slot = gs_slot(cell) (the red-black Gauss-Seidel passes:
-// each colour's inverses contiguous, so a colour pass reads only its own half).
+// Dblk, Dblk32 and Binv32 in the column-slice layout [col * nrows + cell * NU + row], or with
+// by_colour set Binv32 in the red-black passes' layout (GsBlk, slot gs_slot(cell)).
 template <int K>
 __global__ void __launch_bounds__(128) k_block_inv32(const double *__restrict__ Dblk, float *__restrict__ Binv32,
                                                      float *__restrict__ Dblk32, long long ncells, int by_colour,
@@ -751,13 +762,25 @@ __global__ void __launch_bounds__(128) k_block_inv32(const double *__restrict__ 
             }
         }
     }
-    const long long slot = by_colour ? gs_slot(cell, ncells) : cell;
+    if (by_colour) {
+        typedef GsBlk<K> B;
+        float *blk = Binv32 + (size_t)gs_slot(cell, ncells) * B::SIZE;
 #pragma unroll
-    for (int s = 0; s < R; ++s) {
-        const int r = lane + 32 * s;
-        if (r < N)
+        for (int s = 0; s < R; ++s) {
+            const int r = lane + 32 * s;
+            if (r < B::NUP)
 #pragma unroll
-            for (int j = 0; j < N; ++j) Binv32[(size_t)j * nrows + (size_t)slot * N + r] = a[s][j];
+                for (int j = 0; j < N; ++j) blk[j * B::NUP + r] = r < N ? a[s][j] : 0.f;
+        }
+        for (int i = N * B::NUP + lane; i < B::SIZE; i += 32) blk[i] = 0.f;
+    } else {
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+            const int r = lane + 32 * s;
+            if (r < N)
+#pragma unroll
+                for (int j = 0; j < N; ++j) Binv32[(size_t)j * nrows + (size_t)cell * N + r] = a[s][j];
+        }
     }
     if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicExch(status, 1);
 }

@@ -1187,8 +1187,10 @@ struct Impl {
     }
 
     static bool use_gs(const hdg_ctx *c) { return c->gs_ok && c->P.inner_gs; }
+    // the colour kernels run a warp per cell, four warps per 128-thread block
+    static constexpr int GS_WARPS = 4;
     static unsigned gs_blocks(const hdg_ctx *c) {
-        return (unsigned)(((c->ncells + 1) / 2 + TEAMS_PER_BLOCK - 1) / TEAMS_PER_BLOCK);
+        return (unsigned)(((c->ncells + 1) / 2 + GS_WARPS - 1) / GS_WARPS);
     }
 
     // One Arnoldi step of the inner FP32 solve: the preconditioner (block Jacobi, or red-black block
@@ -1198,7 +1200,7 @@ struct Impl {
         const EdgeTab<float> E{c->ephi32, c->pen32, c->nrm32};
         const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
         if (use_gs(c)) {
-            const size_t smg = sizeof(float) * TEAMS_PER_BLOCK * (2 * NU + 6 * Dm::NFQ);
+            const size_t smg = sizeof(float) * GS_WARPS * (2 * NU + 6 * Dm::NFQ);
             for (int col = 0; col < 2; ++col)
                 launch_k(k_gs_diag<K>, gs_blocks(c), 128, smg, c->st, E, c->M, (const float *)c->Binv32, (const float *)c->gw32,
                          c->gV32, c->utr32, (const float *)c->wq32, (const GmresState *)c->gs, col);
@@ -1228,7 +1230,7 @@ struct Impl {
         if (use_gs(c)) {
             const EdgeTab<float> E32{c->ephi32, c->pen32, c->nrm32};
             for (int col = 0; col < 2; ++col)
-                launch_k(k_gs_combine<K>, gs_blocks(c), 128, sizeof(float) * TEAMS_PER_BLOCK * (2 * NU + 6 * Dm::NFQ), c->st,
+                launch_k(k_gs_combine<K>, gs_blocks(c), 128, sizeof(float) * GS_WARPS * (2 * NU + 6 * Dm::NFQ), c->st,
                          E32, c->M, (const float *)c->gV32, (const float *)c->Binv32, (const float *)c->wq32, c->utr32, x,
                          (const GmresState *)c->gs, col == 1 ? c->dcnt : (DevCount *)nullptr, col);
         } else {
@@ -2185,7 +2187,11 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         c->utr = c->alloc<double>((size_t)c->ncells * 3 * nfq * 2);
         c->pen = c->alloc<double>(nfq);
         c->pen32 = c->alloc<float>(nfq);
-        c->Binv32 = c->alloc<float>((size_t)c->NU * nQ);
+        {
+            // the column-slice layout (block Jacobi) or the per-cell blocks of the red-black passes
+            const size_t nup = (size_t)(c->NU + 3) / 4 * 4, blk = ((size_t)c->NU * nup + 31) / 32 * 32;
+            c->Binv32 = c->alloc<float>(std::max((size_t)c->NU * nQ, blk * (size_t)c->ncells));
+        }
         c->wq32 = c->alloc<float>((size_t)c->ncells * 3 * nfq);
         c->utr32 = c->alloc<float>((size_t)c->ncells * 3 * nfq * 2);
         c->gV32 = c->alloc<float>((size_t)(GM_M + 1) * nQ);
@@ -2574,7 +2580,7 @@ double hdg_estimate_bytes(const hdg_mesh_desc *mesh, const hdg_params *params) {
     const double nstage_c = (double)cs.size(), ncond = nstage_c + 2;
     double b = 0;
     b += 8 * ((T.s + 1) * (nQ + nP + nL) + T.s * nQ + nQ);                 // state, stages, forcing
-    b += 8 * 2 * NU * nQ + 4 * NU * nQ;                                    // Dblk, Binv, Binv32
+    b += 8 * 2 * NU * nQ + 4 * nc * std::ceil(NU * 4 * std::ceil(NU / 4) / 32) * 32;   // Dblk, Binv, Binv32
     b += 8 * 3 * nc * 3 * nfq * 2 + 4 * 3 * nc * 3 * nfq * 2;             // weights, edge values
     b += 4 * (32 + 2) * nQ + 8 * (32 + 5) * nQ;                            // Step-I Krylov (FP32, FP64)
     if (params->n_richardson <= 0 && params->stage_krylov) {
@@ -2826,7 +2832,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 // kernel that puts step J back (the solve above ended its cycle); that kernel's own
                 // time, measured alone, is subtracted
                 auto reset = [&]() { launch_k(k_gm_set_step, 1, 1, 0, c->st, c->gs, J); };
-                const size_t smg = sizeof(float) * TEAMS_PER_BLOCK * (2 * I::NU + 6 * I::Dm::NFQ);
+                const size_t smg = sizeof(float) * I::GS_WARPS * (2 * I::NU + 6 * I::Dm::NFQ);
                 auto launch = [&]() {
                     reset();
                     if (which == 6)
@@ -2871,7 +2877,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 else if (which == 13) {   // per launch (one colour, half the cells): the colour's block
                                           // inverses, w, V_0..V_{J-1} read, V_J and edge values written;
                                           // black also reads its red neighbours' edge values and weights
-                    *bytes = 0.5 * 4.0 * (nc * I::NU * I::NU + (J + 2.0) * c->nQ + nc * 3 * nfq * 2 +
+                    *bytes = 0.5 * 4.0 * (nc * GsBlk<I::K_>::SIZE + (J + 2.0) * c->nQ + nc * 3 * nfq * 2 +
                                           0.5 * nc * 3 * nfq * 3);
                     t6_ms *= 0.5;
                 } else                // red cells' neighbour edge values and weights, v_j read, w written,
