@@ -31,40 +31,6 @@ namespace hdg {
     const int cell = 2 * (blockIdx.x * tpb + team) + (COL);                          \
     Team tm{(int)(threadIdx.x & 31), 32};
 
-// z = B v for the block B of storage slot `slot` (a warp; v in shared memory, NU entries; z's NU
-// entries written to shared memory)
-template <int K>
-__device__ __forceinline__ void warp_block_apply(const float *__restrict__ Binv, long long slot, const float *v,
-                                                 float *z) {
-    typedef GsBlk<K> B;
-    const int lane = (int)(threadIdx.x & 31), g = lane % B::G, s = lane / B::G;
-    const float4 *blk = reinterpret_cast<const float4 *>(Binv + (size_t)slot * B::SIZE);
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    if (s < B::S) {
-#pragma unroll 4
-        for (int q = s; q < B::NU; q += B::S) {
-            const float4 b = __ldg(blk + q * (B::NUP / 4) + g);
-            const float vq = v[q];
-            a0 = fmaf(b.x, vq, a0); a1 = fmaf(b.y, vq, a1);
-            a2 = fmaf(b.z, vq, a2); a3 = fmaf(b.w, vq, a3);
-        }
-    }
-    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
-#pragma unroll
-    for (int s2 = 0; s2 < B::S; ++s2) {             // the subsets' partial sums, in order
-        const int src = s2 * B::G + g;
-        t0 += __shfl_sync(0xffffffffu, a0, src); t1 += __shfl_sync(0xffffffffu, a1, src);
-        t2 += __shfl_sync(0xffffffffu, a2, src); t3 += __shfl_sync(0xffffffffu, a3, src);
-    }
-    if (s == 0) {
-        const int r = 4 * g;
-        if (r < B::NU) z[r] = t0;
-        if (r + 1 < B::NU) z[r + 1] = t1;
-        if (r + 2 < B::NU) z[r + 2] = t2;
-        if (r + 3 < B::NU) z[r + 3] = t3;
-    }
-}
-
 // edge values of the cell's z (zK: its NU coefficients in shared memory) -> utr
 template <int K>
 __device__ __forceinline__ void team_edge_values(const Team &tm, const EdgeTab<float> &E, int cell, const float *zK,

@@ -705,15 +705,50 @@ struct GsBlk {
     static constexpr int S = 32 / G;
 };
 
+// z = B v for the block B of storage slot `slot` (a warp; v in shared memory, NU entries; z's NU
+// entries written to shared memory)
+template <int K>
+__device__ __forceinline__ void warp_block_apply(const float *__restrict__ Binv, long long slot, const float *v,
+                                                 float *z) {
+    typedef GsBlk<K> B;
+    const int lane = (int)(threadIdx.x & 31), g = lane % B::G, s = lane / B::G;
+    const float4 *blk = reinterpret_cast<const float4 *>(Binv + (size_t)slot * B::SIZE);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    if (s < B::S) {
+#pragma unroll 4
+        for (int q = s; q < B::NU; q += B::S) {
+            const float4 b = __ldg(blk + q * (B::NUP / 4) + g);
+            const float vq = v[q];
+            a0 = fmaf(b.x, vq, a0); a1 = fmaf(b.y, vq, a1);
+            a2 = fmaf(b.z, vq, a2); a3 = fmaf(b.w, vq, a3);
+        }
+    }
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+#pragma unroll
+    for (int s2 = 0; s2 < B::S; ++s2) {             // the subsets' partial sums, in order
+        const int src = s2 * B::G + g;
+        t0 += __shfl_sync(0xffffffffu, a0, src); t1 += __shfl_sync(0xffffffffu, a1, src);
+        t2 += __shfl_sync(0xffffffffu, a2, src); t3 += __shfl_sync(0xffffffffu, a3, src);
+    }
+    if (s == 0) {
+        const int r = 4 * g;
+        if (r < B::NU) z[r] = t0;
+        if (r + 1 < B::NU) z[r + 1] = t1;
+        if (r + 2 < B::NU) z[r + 2] = t2;
+        if (r + 3 < B::NU) z[r + 3] = t3;
+    }
+}
+
 // FP32 inverses of the Step-I diagonal blocks for the inner (preconditioner) solves, one warp per
 // cell with the block in registers: lane l holds rows l and l + 32 (< NU), Gauss-Jordan in place
 // without pivoting, row k reaching the other lanes by shuffles. No pivoting is needed: the block
 // M_K - c F_K has a positive definite symmetric part (mass plus the dissipative penalty and upwind
 // terms; the advection's symmetric part is c (div Q*)/2 |Q|^2, far below the mass), so every
 // leading block is nonsingular. A zero or non-finite pivot sets *status (singular block).
-// Dblk32 (optional) receives the block itself rounded to FP32 (the relaxed stage products).
-// Dblk, Dblk32 and Binv32 in the column-slice layout [col * nrows + cell * NU + row], or with
-// by_colour set Binv32 in the red-black passes' layout (GsBlk, slot gs_slot(cell)).
+// Dblk32 (optional) receives the block itself rounded to FP32 for the relaxed stage products, in
+// the per-cell block layout GsBlk (slot = cell). Dblk and Binv32 in the column-slice layout
+// [col * nrows + cell * NU + row], or with by_colour set Binv32 in the red-black passes' layout
+// (GsBlk, slot gs_slot(cell)).
 template <int K>
 __global__ void __launch_bounds__(128) k_block_inv32(const double *__restrict__ Dblk, float *__restrict__ Binv32,
                                                      float *__restrict__ Dblk32, long long ncells, int by_colour,
@@ -733,13 +768,16 @@ __global__ void __launch_bounds__(128) k_block_inv32(const double *__restrict__ 
         for (int j = 0; j < N; ++j) a[s][j] = r < N ? (float)__ldg(&Dblk[(size_t)j * nrows + (size_t)cell * N + r]) : 0.f;
     }
     if (Dblk32) {
+        typedef GsBlk<K> B;
+        float *blk = Dblk32 + (size_t)cell * B::SIZE;
 #pragma unroll
         for (int s = 0; s < R; ++s) {
             const int r = lane + 32 * s;
-            if (r < N)
+            if (r < B::NUP)
 #pragma unroll
-                for (int j = 0; j < N; ++j) Dblk32[(size_t)j * nrows + (size_t)cell * N + r] = a[s][j];
+                for (int j = 0; j < N; ++j) blk[j * B::NUP + r] = r < N ? a[s][j] : 0.f;
         }
+        for (int i = N * B::NUP + lane; i < B::SIZE; i += 32) blk[i] = 0.f;
     }
     bool ok = true;
 #pragma unroll

@@ -1138,8 +1138,8 @@ struct Impl {
                      c->Binv32, blk32, c->ncells, use_gs(c) ? 1 : 0, c->dstatus);
             CKL();
         } else if (blk32) {
-            launch_k(k_to_f32, grid_for((long long)NU * c->nQ), VEC_THREADS, 0, c->st, (const double *)c->Dblk, blk32,
-                     (long long)NU * c->nQ);
+            launch_k(k_blocks_to_f32<K>, grid_for((long long)GsBlk<K>::SIZE * c->ncells), VEC_THREADS, 0, c->st,
+                     (const double *)c->Dblk, blk32, (long long)c->ncells);
             CKL();
         }
         c->inv_ok = inv;
@@ -1397,8 +1397,8 @@ struct Impl {
     static void stage_apply32(hdg_ctx *c, double cc, const double *Q, const double *p, const double *lam, double *yQ,
                               double *yp, float *yQ32, float *yp32, double *zslot, const int *zslot_j,
                               GmresState *gs, DevCount *acc) {
-        launch_k(k_stage_apply32<K>, cell_blocks(c), 128,
-                 sizeof(double) * TEAMS_PER_BLOCK * ((stage32_scratch_floats<K>() + 1) / 2), c->st, c->R,
+        launch_k(k_stage_apply32<K>, (unsigned)((c->ncells + STAGE32_WARPS - 1) / STAGE32_WARPS), 32 * STAGE32_WARPS,
+                 sizeof(double) * STAGE32_WARPS * ((stage32_scratch_floats<K>() + 1) / 2), c->st, c->R,
                  Ref32{c->Dhat32, c->Ehat32}, EdgeTab<float>{c->ephi32, c->pen32, c->nrm32}, c->M,
                  (const float *)c->geo32, (const float *)c->Dblk32, (const float *)c->wq32, (float)cc, (float)c->P.tau, Q,
                  p, lam, yQ, yp, c->vK, yQ32, yp32, zslot, zslot_j, gs, acc);
@@ -2236,7 +2236,8 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
             CK(cudaMemset(c->fgs, 0, sizeof(GmresState)));
             CK(cudaMallocHost(&c->hfgs, sizeof(GmresState)));
             if (params->precision == HDG_MIXED && params->relax_eta > 0) {
-                c->Dblk32 = c->alloc<float>((size_t)c->NU * nQ);
+                const size_t nup = (size_t)(c->NU + 3) / 4 * 4;       // the per-cell layout GsBlk
+                c->Dblk32 = c->alloc<float>(((size_t)c->NU * nup + 31) / 32 * 32 * (size_t)c->ncells);
                 std::vector<float> g32((size_t)GEO32 * c->ncells);
                 for (long long k = 0; k < c->ncells; ++k) {
                     const CellGeo &G = c->H.geo[k];
@@ -2586,7 +2587,7 @@ double hdg_estimate_bytes(const hdg_mesh_desc *mesh, const hdg_params *params) {
     if (params->n_richardson <= 0 && params->stage_krylov) {
         b += 8 * (31 + 30 + 7) * N + 4 * 32 * N;                           // stage FGMRES
         if (params->precision == HDG_MIXED && params->relax_eta > 0)
-            b += 4 * NU * nQ + 4 * 8 * nc;                                 // FP32 blocks, geometry
+            b += 4 * nc * std::ceil(NU * 4 * std::ceil(NU / 4) / 32) * 32 + 4 * 8 * nc;   // FP32 blocks, geometry
     }
     b += 8 * (8 * nQ + 3 * nP + 3 * nL + nc * NL + 10 * nL);               // temporaries, trace work
     b += ncond * 8 * (nc * (NL * NL + NP * NL + NP * NP) + 6 * NT * nL) + ncond * 4 * 5 * nf;
@@ -2964,7 +2965,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 // k_stage_apply32 alone (its flag forced on), like 8; bytes: FP32 diagonal blocks,
                 // weights, geometry and normals + neighbour maps + Q, p, lambda read + yQ, yp, v written
                 const int nfq = (3 * c->K + 5) / 2;
-                b = 4.0 * c->ncells * ((double)NU * NU + 3 * nfq + GEO32 + 6) + 4.0 * 6 * c->ncells +
+                b = 4.0 * c->ncells * ((double)GsBlk<I::K_>::SIZE + 3 * nfq + GEO32 + 6) + 4.0 * 6 * c->ncells +
                     8.0 * (2.0 * c->nQ + 2.0 * c->nPv + c->nL + (double)c->ncells * 3 * NT);
                 const int one = 1;
                 CK(cudaMemcpyAsync(&c->fgs->lowprec, &one, sizeof(int), cudaMemcpyHostToDevice, c->st));

@@ -36,10 +36,19 @@ struct Ref32 {
     const float *Dhat, *Ehat;
 };
 
-// y = x rounded to FP32 (the diagonal blocks when no FP32 inverses are formed)
-__global__ void k_to_f32(const double *__restrict__ x, float *__restrict__ y, long long n) {
+// the diagonal blocks rounded to FP32 in the per-cell layout GsBlk (when no FP32 inverses are
+// formed; else k_block_inv32 writes them): Dblk in the column-slice layout [col * nrows + cell *
+// NU + row]
+template <int K>
+__global__ void k_blocks_to_f32(const double *__restrict__ Dblk, float *__restrict__ Dblk32, long long ncells) {
     wait_prior_kernel();
-    GRID_STRIDE(i, n) y[i] = (float)x[i];
+    typedef GsBlk<K> B;
+    const long long nrows = ncells * B::NU;
+    GRID_STRIDE(i, ncells * B::SIZE) {
+        const long long cell = i / B::SIZE;
+        const int o = (int)(i % B::SIZE), q = o / B::NUP, r = o % B::NUP;
+        Dblk32[i] = (q < B::NU && r < B::NU) ? (float)Dblk[(size_t)q * nrows + (size_t)cell * B::NU + r] : 0.f;
+    }
 }
 
 // per-cell geometry in FP32: Jinv[4], detJ, h[3]
@@ -48,13 +57,18 @@ constexpr int GEO32 = 8;
 template <int K>
 constexpr int stage32_scratch_floats() {
     typedef Dims<K> Dm;
-    return 2 * (Dm::NP + Dm::NL) + 4 * Dm::NU + Dm::NP + Dm::NL + 6 * Dm::NFQ + 2 * Dm::MU + GEO32 + Dm::NL;
+    return 2 * (Dm::NP + Dm::NL) + 5 * Dm::NU + Dm::NP + Dm::NL + 6 * Dm::NFQ + 2 * Dm::MU + GEO32 + Dm::NL;
 }
+
+// a warp per cell, four cells per 128-thread block
+constexpr int STAGE32_WARPS = 4;
 
 // y = A(c) x with x = (Q, p, lambda) in FP64 memory, arithmetic in FP32; same outputs as
 // k_stage_apply (yQ, yp, the cell's lambda-row contributions v, the FP32 shadows yQ32 / yp32,
 // and the copy of x into the FGMRES's preconditioned-vector slot *zslot_j when set). Runs only
-// when *lowprec is set; counts its launches in acc->products32 (when acc is set).
+// when gs->lowprec is set; counts its launches in acc->products32 (when acc is set). A warp per
+// cell: the diagonal block (Dblk, per-cell layout GsBlk) is applied by warp_block_apply with
+// 16-byte loads of contiguous memory.
 template <int K>
 __global__ void __launch_bounds__(128) k_stage_apply32(RefDev R64, Ref32 R, EdgeTab<float> E, MeshDev M,
                                                        const float *__restrict__ geo32, const float *__restrict__ Dblk,
@@ -70,15 +84,18 @@ __global__ void __launch_bounds__(128) k_stage_apply32(RefDev R64, Ref32 R, Edge
     }
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NP = Dm::NP, NT = Dm::NT, NL = Dm::NL, NFQ = Dm::NFQ;
-    constexpr int SCRF = stage32_scratch_floats<K>();
-    constexpr int SCR = (SCRF + 1) / 2;                      // in doubles, for CELL_TEAM
-    CELL_TEAM(SCR)
-    double *pD = mine, *lD = pD + NP;                        // p and lambda (local orientation) in FP64
+    constexpr int SCR = (stage32_scratch_floats<K>() + 1) / 2;   // in doubles
+    extern __shared__ double sm[];
+    const int team = threadIdx.x >> 5;
+    const int cell = blockIdx.x * STAGE32_WARPS + team;
+    if (cell >= M.ncells) return;
+    Team tm{(int)(threadIdx.x & 31), 32};
+    double *pD = sm + team * SCR, *lD = pD + NP;             // p and lambda (local orientation) in FP64
     float *xK = reinterpret_cast<float *>(lD + NL);          // own Q (NU)
     float *xn = xK + NU;                                     // neighbours' Q (3 x NU)
     float *pK = xn + 3 * NU, *lK = pK + NP, *t = lK + NL, *xr = t + 6 * NFQ, *gg = xr + 2 * MU;
     float *jmp = gg + GEO32;                                 // J_ej = (L_j, p)_e - lambda_ej (NL)
-    const long long nrows = (long long)M.ncells * NU;
+    float *dq = jmp + NL;                                    // the diagonal block times Q (NU)
     const int *nbr = M.cell_nbr + 3 * cell;
     TFOR(i, NU) xK[i] = (float)Q[(size_t)cell * NU + i];
     TFOR(i, 3 * NU) {
@@ -135,15 +152,15 @@ __global__ void __launch_bounds__(128) k_stage_apply32(RefDev R64, Ref32 R, Edge
         xr[MU + a] = gg[2] * xK[a] + gg[3] * xK[MU + a];
     }
     tm.sync();
+    warp_block_apply<K>(Dblk, cell, xK, dq);
+    tm.sync();
     const float detJ = gg[4];
     // velocity rows: (M - cF) Q (diagonal block dense, neighbours from t) - c (detJ Jinv-mapped
     // Dhat^T p - sum_e h_e n_e Ehat^T lambda)
     TFOR(x, NU) {
         const int d = x / MU, a = x % MU;
         const size_t gi = (size_t)cell * NU + x;
-        float bq = nbr_row<K, float>(E, t, d, a);
-#pragma unroll 6
-        for (int j = 0; j < NU; ++j) bq = fmaf(__ldg(&Dblk[(size_t)j * nrows + gi]), xK[j], bq);
+        const float bq = nbr_row<K, float>(E, t, d, a) + dq[x];
         float et = 0.f;
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
