@@ -511,6 +511,28 @@ def stage_flops(k, ncells):
     return st_flop, s_flop
 
 
+def assembly_flops(k, ncells):
+    """Algorithmic FP64 flops of one launch of the Step-I assembly (k_fimpl_assemble, stage form):
+    the coefficients of J^-1 Q*, {Q*}.n at the facet points (own and neighbour traces), the
+    weighted facet rows, the volume advection block through the reference tensor (2 MU products per
+    entry), the three weighted facet masses, and the NU x NU block entries (an FMA counts two)."""
+    mu = (k + 2) * (k + 3) // 2
+    nu, nfq = 2 * mu, (3 * k + 5) // 2
+    fma = 4 * mu + 3 * nfq * 4 * mu + 3 * nfq * mu * 2 + 3 * nfq * 3 + mu * mu * 2 * mu + 3 * mu * mu * nfq + nu * nu * 5
+    return 2.0 * fma * ncells
+
+
+def bdm_flops(k, ncells):
+    """Algorithmic FP64 flops of one launch of the BDM projection (k_bdm): the normal average at the
+    facet points (own and neighbour traces), the edge moments against L_j, the interior Nedelec
+    moments, the NU x NU local solve through the precomputed inverse moment matrix and the Piola
+    map back (an FMA counts two)."""
+    mu = (k + 2) * (k + 3) // 2
+    nu, nfq, nb, nv = 2 * mu, (3 * k + 5) // 2, k + 2, k * (k + 2)
+    fma = 3 * nfq * 4 * mu + 3 * nb * nfq + nv * mu * 4 + nu * nu + 2 * nu
+    return 2.0 * fma * ncells
+
+
 def condense_flops(k, ncells):
     """Algorithmic FP64 flops of one launch of the per-cell condensation (k_condense): D and E
     formed, A = (c/detJ) D D^T + tau T_pp, H = (c/detJ) D E^T + tau E_hat^T, the Cholesky factor of
@@ -554,6 +576,8 @@ def run_gpu(args, rank, world, local_rank):
         s_ms, s_bytes = ctx.hdg_time_kernel(1, 1.0, 20)
         st_ms, st_bytes = ctx.hdg_time_kernel(8, c_stage, 20)
         cd_ms, cd_bytes = ctx.hdg_time_kernel(11, c_stage, 3)
+        as_ms, as_bytes = ctx.hdg_time_kernel(15, c_stage, 5)
+        bd_ms, bd_bytes = ctx.hdg_time_kernel(16, c_stage, 10)
         s32_ms = s32_bytes = gd_ms = gd_bytes = ga_ms = ga_bytes = None
         if args.precision == 'MIXED':
             if kw.get('relax_eta', 1e-4) > 0:
@@ -604,7 +628,13 @@ def run_gpu(args, rank, world, local_rank):
                                      'ms_per_launch': st_ms, 'launches_per_step': outer - p32 + 2 * stages,
                                      'bytes': st_bytes, 'flop': st_flop, 'bound': 'alu'},
         f"k_cg_apply<{w['k'] + 1}>": {'what': 'FP64 trace operator apply (tight trace CG)', 'ms_per_launch': k_ms,
-                                      'launches_per_step': trace_iters / args.steps, 'bytes': k_bytes, 'bound': 'hbm'}}
+                                      'launches_per_step': trace_iters / args.steps, 'bytes': k_bytes, 'bound': 'hbm'},
+        f"k_fimpl_assemble<{w['k']}>": {'what': 'FP64 Step-I assembly (stage solves and the reconstruction f^impl)',
+                                        'ms_per_launch': as_ms, 'launches_per_step': stages + 1, 'bytes': as_bytes,
+                                        'flop': assembly_flops(w['k'], ncells), 'bound': 'alu'},
+        f"k_bdm<{w['k']}>": {'what': 'FP64 BDM projection (stage advecting velocities and the reconstruction)',
+                             'ms_per_launch': bd_ms, 'launches_per_step': stages + 1, 'bytes': bd_bytes,
+                             'flop': bdm_flops(w['k'], ncells), 'bound': 'alu'}}
     if s32_ms is not None:
         kernels[f"k_stage_apply32<{w['k']}>"] = {'what': 'FP32 stage operator (relaxed FGMRES products)',
                                                  'ms_per_launch': s32_ms, 'launches_per_step': p32,
@@ -627,7 +657,12 @@ def run_gpu(args, rank, world, local_rank):
             kd['frac_of_fp64_nominal'] = kd['achieved_tflops'] / FP64_NOMINAL_TFLOPS
     top = max(kernels, key=lambda n: kernels[n]['ms_per_step_est'])
     kt = kernels[top]
-    traffic_file = {f"k_stage_apply<{w['k']}>": 'k_stage_apply_fp64_c2.md'}.get(top) if args.workload == 'c2' else None
+    # DRAM bytes per launch from a committed ncu summary of the same kernel: C2 captured at its own
+    # size; C3's colour pass captured at 128x128 (the size rule for a full capture) and scaled by
+    # the cell ratio (its traffic is proportional to the cells: one block inverse per cell)
+    traffic_src = {('c2', 'k_stage_apply<3>'): ('k_stage_apply_fp64_c2.md', 1.0),
+                   ('c2', 'k_gs_diag<3>'): ('k_gs_diag_fp32_c2.md', 1.0),
+                   ('c3', 'k_gs_diag<4>'): ('k_gs_diag_fp32_tg128_k4.md', (w['n'] / 128.0) ** 2)}.get((args.workload, top))
     if kt['bound'] == 'alu':
         roofline = {'kernel': f"{top} ({kt['what']})", 'bound': 'alu', 'achieved': kt['achieved_tflops'],
                     'peak': FP64_NOMINAL_TFLOPS, 'unit': 'TFLOP/s', 'frac': kt['frac_of_fp64_nominal'],
@@ -636,7 +671,8 @@ def run_gpu(args, rank, world, local_rank):
     else:
         roofline = {'kernel': f"{top} ({kt['what']})", 'bound': 'hbm', 'achieved': kt['achieved_gbs'], 'peak': peak,
                     'unit': 'GB/s', 'frac': kt['frac_of_hbm'], 'peak_kind': peak_kind}
-    roofline.update({'traffic': profile_traffic(traffic_file) if traffic_file else None,
+    traffic = profile_traffic(traffic_src[0]) if traffic_src else None
+    roofline.update({'traffic': traffic * traffic_src[1] if traffic is not None else None,
                      'ms_per_launch': kt['ms_per_launch'], 'algorithmic_bytes': kt['bytes'],
                      'launches_per_step': kt['launches_per_step'], 'share_of_step_est': kt['share_of_step_est'],
                      'note': 'the kernel with the largest estimated device time per step (time per launch alone x '

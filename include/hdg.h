@@ -370,7 +370,11 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *ctx, hdg_stats *stats);
  * its algorithmic bytes. which = 13, 14 (inner_gs on): the red-black Gauss-Seidel kernels of the
  * inner FP32 Step-I GMRES at step j = 4, launched like 6: 13 = the colour pass (k_gs_diag; both
  * colours launched, time and bytes per launch), 14 = the Arnoldi product with its dots
- * (k_gs_apply); bytes = their algorithmic bytes. */
+ * (k_gs_apply); bytes = their algorithmic bytes. which = 15: the Step-I assembly kernel alone
+ * (k_fimpl_assemble in the stage solves' form: block and weights, no FP64 inverse) for coefficient
+ * c around the current state's BDM projection (the context's Step-I operator is overwritten; the
+ * next stage solve assembles its own); which = 16: the BDM projection kernel alone on the current
+ * state; bytes = their algorithmic bytes. */
 hdg_status hdg_time_kernel(hdg_ctx *ctx, int which, double c, int reps, double *ms_per_launch,
                            double *bytes_per_launch);
 

@@ -345,7 +345,11 @@ __host__ __device__ void cell_mixed_backsub(const Team &tm, const RefDev &R, con
 // BDM^0_{k+1} projection of one cell (Sec. 2.3, canonical interpolant): edge normal moments of
 // the average {Q}.n (0 on walls) against L_j, j < k+2; interior moments against N_k; solved on
 // the reference cell through the Piola map. QK, Qnbr[e] (null on walls): modal velocities.
-// Scratch: NU (moments) + NU doubles.
+// The normal average is evaluated once per facet point, then integrated against every L_j.
+// Scratch: bdm_scratch<K>() doubles (moments, reference coefficients, the facet-point values).
+template <int K>
+constexpr int bdm_scratch() { return 2 * Dims<K>::NU + 3 * Dims<K>::NFQ; }
+
 template <int K>
 __host__ __device__ void cell_bdm(const Team &tm, const RefDev &R, const CellGeo &g,
                                   const double *QK, const double *const *Qnbr, const int *nbr_edge,
@@ -354,26 +358,29 @@ __host__ __device__ void cell_bdm(const Team &tm, const RefDev &R, const CellGeo
     constexpr int MU = Dm::MU, NU = Dm::NU, NB = Dm::NB, NV = Dm::NV, NFQ = Dm::NFQ;
     double *m = sm;                 // NU moments
     double *qh = m + NU;            // NU reference coefficients
-    TFOR(i, 3 * NB) {
-        int e = i / NB, j = i % NB;
+    double *an = qh + NU;           // 3 x NFQ: h_e fw_q {Q}.n at the facet points (0 on walls)
+    TFOR(i, 3 * NFQ) {
+        const int e = i / NFQ, q = i % NFQ;
         double s = 0;
         if (Qnbr[e]) {
             const double *Qo = Qnbr[e];
-            int eo = nbr_edge[e];
-            for (int q = 0; q < NFQ; ++q) {
-                const double *pk = &R.ephi[(e * NFQ + q) * MU];
-                const double *po = &R.ephi[(eo * NFQ + (NFQ - 1 - q)) * MU];
-                double k0 = 0, k1 = 0, o0 = 0, o1 = 0;
-                for (int a = 0; a < MU; ++a) {
-                    double fk = ldg(pk + a), fo = ldg(po + a);
-                    k0 += fk * QK[a]; k1 += fk * QK[MU + a];
-                    o0 += fo * Qo[a]; o1 += fo * Qo[MU + a];
-                }
-                double an = 0.5 * ((k0 + o0) * g.nx[e] + (k1 + o1) * g.ny[e]);
-                s += ldg(&R.fw[q]) * an * ldg(&R.leg[q * NB + j]);
+            const double *pk = &R.ephi[(e * NFQ + q) * MU];
+            const double *po = &R.ephi[(nbr_edge[e] * NFQ + (NFQ - 1 - q)) * MU];
+            double k0 = 0, k1 = 0, o0 = 0, o1 = 0;
+            for (int a = 0; a < MU; ++a) {
+                double fk = ldg(pk + a), fo = ldg(po + a);
+                k0 += fk * QK[a]; k1 += fk * QK[MU + a];
+                o0 += fo * Qo[a]; o1 += fo * Qo[MU + a];
             }
-            s *= g.h[e];
+            s = g.h[e] * ldg(&R.fw[q]) * 0.5 * ((k0 + o0) * g.nx[e] + (k1 + o1) * g.ny[e]);
         }
+        an[i] = s;
+    }
+    tm.sync();
+    TFOR(i, 3 * NB) {               // edge moments against the Legendre polynomials
+        const int e = i / NB, j = i % NB;
+        double s = 0;
+        for (int q = 0; q < NFQ; ++q) s += an[e * NFQ + q] * ldg(&R.leg[q * NB + j]);
         m[i] = s;
     }
     TFOR(v, NV) {

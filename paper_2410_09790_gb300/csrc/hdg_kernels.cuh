@@ -608,7 +608,7 @@ template <int K>
 __global__ void k_bdm(RefDev R, MeshDev M, const double *Q, double *Qs) {
     wait_prior_kernel();
     typedef Dims<K> Dm;
-    constexpr int SCR = 2 * Dm::NU;
+    constexpr int SCR = bdm_scratch<K>();
     CELL_TEAM(SCR)
     CellGeo g = M.geo[cell];
     const double *Qn[3];
@@ -1207,6 +1207,55 @@ __device__ void multidot_groups_partials(const RedBuf rb, const T *V, const T *w
         for (long long g0 = blockIdx.x * rows_per_group; g0 < nrows; g0 += gridDim.x * rows_per_group)
             f(g0, g0 + rows_per_group < nrows ? g0 + rows_per_group : nrows);
     }, with_norm ? w : nullptr, false, true);
+}
+
+// FP32 form (the inner solves' products): one pass over the block's rows with 16-byte loads, w
+// read once and the nvec (+ 1) partial sums kept in registers, the block's sums added in a fixed
+// order. Rows in groups of rows_per_group (a multiple of 4, as is nrows; V, w 16-byte aligned);
+// group g belongs to block g mod gridDim. w may have been written by this block before the call.
+template <>
+__device__ void multidot_groups_partials<float>(const RedBuf rb, const float *V, const float *w, long long nrows,
+                                                long long rows_per_group, int nvec, bool with_norm) {
+    constexpr int NV = GM_M + 1;                 // V_0..V_j, j <= GM_M
+    __shared__ float red[GM_M + 2][32];          // per value, per warp
+    __syncthreads();
+    float acc[NV], an = 0.f;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.f;
+    const long long q4 = rows_per_group / 4;
+    const long long ngroups = (nrows + rows_per_group - 1) / rows_per_group;
+    const long long mine = (long long)blockIdx.x < ngroups ? (ngroups - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    for (long long it = threadIdx.x; it < mine * q4; it += blockDim.x) {
+        const long long r = (blockIdx.x + (it / q4) * gridDim.x) * rows_per_group + 4 * (it % q4);
+        if (r >= nrows) continue;
+        const float4 wv = *reinterpret_cast<const float4 *>(w + r);
+        if (with_norm) an = fmaf(wv.x, wv.x, fmaf(wv.y, wv.y, fmaf(wv.z, wv.z, fmaf(wv.w, wv.w, an))));
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i < nvec) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(V + (size_t)i * nrows + r));
+                acc[i] = fmaf(v.x, wv.x, fmaf(v.y, wv.y, fmaf(v.z, wv.z, fmaf(v.w, wv.w, acc[i]))));
+            }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+        if (i < nvec) {
+            float a = acc[i];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) red[i][warp] = a;
+        }
+    if (with_norm) {
+        float a = an;
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) red[nvec][warp] = a;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nvec + (with_norm ? 1 : 0)) {
+        float sum = 0.f;
+        for (int k = 0; k < nw; ++k) sum += red[threadIdx.x][k];
+        reinterpret_cast<float *>(rb.partials)[blockIdx.x * (GM_M + 2) + threadIdx.x] = sum;
+    }
 }
 
 // start of a cycle: w = b - Bx (Bx = B x precomputed; null on the first cycle, x = 0: w = b);

@@ -1662,7 +1662,7 @@ struct Impl {
     static void bdm(hdg_ctx *c, const double *Q, double *Qs) {
         CompTimer tm_(c, &c->S.ms_bdm);
         unsigned nb = cell_blocks(c);
-        launch_k(k_bdm<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * 2 * NU, c->st, c->R, c->M, Q, Qs);
+        launch_k(k_bdm<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * bdm_scratch<K_>(), c->st, c->R, c->M, Q, Qs);
         CKL();
     }
 
@@ -2765,7 +2765,7 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *c, hdg_stats *stats) {
 }
 
 hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *ms, double *bytes) {
-    if (!c || reps < 1 || !ms || !bytes || which < 0 || which > 14 || (which != 1 && !(cc > 0)))
+    if (!c || reps < 1 || !ms || !bytes || which < 0 || which > 16 || (which != 1 && !(cc > 0)))
         return HDG_ERR_INVALID_ARG;
     if (which == 12 && !(c->Dblk32 && c->P.precision == HDG_MIXED && c->P.relax_eta > 0)) return HDG_ERR_INVALID_ARG;
     if (which >= 2 && which != 8 && which != 11 && which != 12 && !c->fv) return HDG_ERR_INVALID_ARG;
@@ -2888,7 +2888,8 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
             *ms = t6_ms;
             return HDG_OK;
         }
-        if (which >= 2 && which != 8 && which != 11 && which != 12 && which != 13 && which != 14) {
+        if (which >= 2 && which != 8 && which != 11 && which != 12 && which != 13 && which != 14 && which != 15 &&
+            which != 16) {
             DISPATCH(c, {
                 // operator of a stage at coefficient cc around the current state; v = (M Q, 0, 0)
                 I::bdm(c, c->Q, c->q[5]);
@@ -2939,6 +2940,32 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 auto launch = [&]() {
                     launch_k(k_cg_apply<I::NT>, cg_apply_grid<I::NT>(nf), 128, 0, c->st, E.Sell, E.tcol, c->tz, c->tp[0], c->tp[1], c->tAp, nf,
                                                                     c->rb(), c->sc);
+                };
+                launch();
+                CKL();
+                CK(cudaEventRecord(c->e0, c->st));
+                for (int r = 0; r < reps; ++r) launch();
+                CK(cudaEventRecord(c->e1, c->st));
+            } else if (which == 15 || which == 16) {
+                // 15: k_fimpl_assemble alone (the stage solves' form: block, weights, no FP64
+                // inverse) for coefficient cc around the current state's P(Q); bytes: Q* of the cell
+                // and its neighbours read, the block and weights written (FP64 and FP32 weights).
+                // 16: k_bdm alone on the current state; bytes: Q read, P(Q) written
+                const int nfq = (3 * c->K + 5) / 2;
+                I::bdm(c, c->Q, c->q[5]);
+                const size_t smem = sizeof(double) * fimpl_smem_noinv_doubles<I::K_>();
+                if (which == 15)
+                    b = (double)c->ncells * (8.0 * 4 * NU + 8.0 * NU * NU + 12.0 * 3 * nfq + 4.0 * 6);
+                else
+                    b = 16.0 * c->nQ;
+                auto launch = [&]() {
+                    if (which == 15)
+                        launch_k(k_fimpl_assemble<I::K_>, (unsigned)c->ncells, 128, smem, c->st, c->R, c->M,
+                                 (const double *)c->q[5], cc, c->P.alpha, c->P.delta_up, c->Dblk, c->wq, c->wq32, c->pen,
+                                 c->pen32, (double *)nullptr, c->dstatus);
+                    else
+                        launch_k(k_bdm<I::K_>, cell_blocks(c), 128, sizeof(double) * TEAMS_PER_BLOCK * bdm_scratch<I::K_>(), c->st,
+                                 c->R, c->M, (const double *)c->Q, c->q[5]);
                 };
                 launch();
                 CKL();
