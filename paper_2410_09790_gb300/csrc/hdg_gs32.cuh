@@ -121,7 +121,9 @@ __global__ void k_gs_apply(EdgeTab<float> E, MeshDev M, const float *__restrict_
             tm.sync();
         }
     }
-    multidot_groups_partials(rb, V, (const float *)w, nrows, (long long)tpb * NU, j + 1, true);
+    constexpr int RPG = (128 / TEAM_LANES) * NU;                 // the rows of a 128-thread block's cells
+    if (tpb * NU == RPG) multidot_groups_partials_f32<RPG>(rb, V, (const float *)w, nrows, j + 1, true);
+    else multidot_groups_partials(rb, V, (const float *)w, nrows, (long long)tpb * NU, j + 1, true);
 }
 
 // End of an inner cycle, colour col: u = V y on the colour's cells; col 0: x = D^-1 u, x's edge

@@ -862,8 +862,14 @@ __device__ __forceinline__ void team_nbr_flux(const Team &tm, const EdgeTab<T> &
                     ux += f * xo[b]; uy += f * xo[MU + b];
                 }
             }
-            const T nx = E.nrm ? E.nrm[6 * cell + 2 * e] : (T)gp->nx[e];
-            const T ny = E.nrm ? E.nrm[6 * cell + 2 * e + 1] : (T)gp->ny[e];
+            T nx, ny;
+            if constexpr (sizeof(T) == 4) {     // FP32 tables: the normals always come in FP32
+                nx = E.nrm[6 * cell + 2 * e];
+                ny = E.nrm[6 * cell + 2 * e + 1];
+            } else {
+                nx = E.nrm ? E.nrm[6 * cell + 2 * e] : gp->nx[e];
+                ny = E.nrm ? E.nrm[6 * cell + 2 * e + 1] : gp->ny[e];
+            }
             const T un = nx * ux + ny * uy, pen = E.pen[q];
             const T w = __ldg(&wq[(size_t)cell * 3 * NFQ + i]);
             tx = pen * nx * un + w * ux;
@@ -1211,22 +1217,22 @@ __device__ void multidot_groups_partials(const RedBuf rb, const T *V, const T *w
 
 // FP32 form (the inner solves' products): one pass over the block's rows with 16-byte loads, w
 // read once and the nvec (+ 1) partial sums kept in registers, the block's sums added in a fixed
-// order. Rows in groups of rows_per_group (a multiple of 4, as is nrows; V, w 16-byte aligned);
+// order. Rows in groups of RPG (a compile-time multiple of 4, as is nrows; V, w 16-byte aligned);
 // group g belongs to block g mod gridDim. w may have been written by this block before the call.
-template <>
-__device__ void multidot_groups_partials<float>(const RedBuf rb, const float *V, const float *w, long long nrows,
-                                                long long rows_per_group, int nvec, bool with_norm) {
+template <int RPG>
+__device__ void multidot_groups_partials_f32(const RedBuf rb, const float *V, const float *w, long long nrows,
+                                             int nvec, bool with_norm) {
     constexpr int NV = GM_M + 1;                 // V_0..V_j, j <= GM_M
+    constexpr int Q4 = RPG / 4;
     __shared__ float red[GM_M + 2][32];          // per value, per warp
     __syncthreads();
     float acc[NV], an = 0.f;
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.f;
-    const long long q4 = rows_per_group / 4;
-    const long long ngroups = (nrows + rows_per_group - 1) / rows_per_group;
-    const long long mine = (long long)blockIdx.x < ngroups ? (ngroups - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    for (long long it = threadIdx.x; it < mine * q4; it += blockDim.x) {
-        const long long r = (blockIdx.x + (it / q4) * gridDim.x) * rows_per_group + 4 * (it % q4);
+    const long long ngroups = (nrows + RPG - 1) / RPG;
+    const int mine = (long long)blockIdx.x < ngroups ? (int)((ngroups - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
+    for (int it = threadIdx.x; it < mine * Q4; it += blockDim.x) {
+        const long long r = ((long long)blockIdx.x + (long long)(it / Q4) * gridDim.x) * RPG + 4 * (it % Q4);
         if (r >= nrows) continue;
         const float4 wv = *reinterpret_cast<const float4 *>(w + r);
         if (with_norm) an = fmaf(wv.x, wv.x, fmaf(wv.y, wv.y, fmaf(wv.z, wv.z, fmaf(wv.w, wv.w, an))));
@@ -1383,7 +1389,11 @@ __global__ void k_gm_apply_mf(EdgeTab<T> E, MeshDev M, const T *__restrict__ wq,
             tm.sync();
         }
     }
-    if (FUSED) multidot_groups_partials(rb, V, (const T *)w, nrows, (long long)tpb * NU, j + 1, true);
+    constexpr int RPG = (128 / TEAM_LANES) * NU;                 // the rows of a 128-thread block's cells
+    if constexpr (FUSED && sizeof(T) == 4) {
+        if (tpb * NU == RPG) multidot_groups_partials_f32<RPG>(rb, V, (const float *)w, nrows, j + 1, true);
+        else multidot_groups_partials(rb, V, (const T *)w, nrows, (long long)tpb * NU, j + 1, true);
+    } else if (FUSED) multidot_groups_partials(rb, V, (const T *)w, nrows, (long long)tpb * NU, j + 1, true);
     else multidot_groups(rb, V, (const T *)w, nrows, (long long)tpb * NU, j + 1, gs->hcol, false);
 }
 

@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(1024) k_tv_tail(Tail32 T) {
             const Stencil S = stencil(V, i, j, ip, im);
             const float *a = V.A + P1_NS * v;
             float ax = 0.f;
-#pragma unroll
+_Pragma("unroll")
             for (int o = 0; o < P1_NS; ++o) {
                 const int w = S.p[o];
                 ax += (gA ? __ldg(a + o) : a[o]) * (V.invth * V.dv[w] * V.b[w]);
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(1024) k_tv_tail(Tail32 T) {
             const int fjp = step1(fj + 1, V.nvy, V.py), fjm = step1(fj - 1, V.nvy, V.py);
             const bool has[P1_NS] = {true, fip >= 0, fim >= 0, fjp >= 0, fjm >= 0, fip >= 0 && fjp >= 0,
                                      fim >= 0 && fjm >= 0};
-#pragma unroll
+_Pragma("unroll")
             for (int o = 1; o < P1_NS; ++o) s += has[o] ? 0.5f * V.xa[S.p[o]] : 0.f;
             C.b[v] = s;
         })

@@ -2781,8 +2781,6 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 I::assemble_stepI(c, c->q[5], cc, I::INV32);
                 I::mass(c, c->Q, c->fv, 0);
                 const long long n = c->nQ;
-                const EdgeTab<float> E{c->ephi32, c->pen32, c->nrm32};
-                const unsigned cb = cell_blocks(c), ab = cb < (unsigned)MAX_RED_BLOCKS ? cb : (unsigned)MAX_RED_BLOCKS;
                 auto start = [&]() {
                     launch_k(k_gm_start<float>, grid_for(n), VEC_THREADS, 0, c->st, n, (const double *)c->fv,
                              (const double *)nullptr, c->gw32, 1, c->rb(), c->gs, 1e-30, 1000, GM_M);
