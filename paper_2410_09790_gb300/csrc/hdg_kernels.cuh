@@ -187,6 +187,87 @@ __global__ void k_axpby(double a, const double *x, double b, double *y, long lon
     GRID_STRIDE(i, n) y[i] = a * x[i] + b * y[i];
 }
 
+// Initial guesses of a step's stage solves from the previous step (one field: velocity, pressure
+// or trace). With *hist set, stage k's guess is its solution in the previous step shifted by the
+// state's change over that step, guess_k = H_k + (x - xprev): both are first-order accurate in
+// time, so the guess is off by O(dt^2) where the previous stage's solution (the guess without
+// history) is off by O(dt). S: dst_k the stage guesses, src_k the kept solutions. xprev is then
+// set to x for the next step.
+struct StageVecs {
+    double *dst[8];
+    const double *src[8];
+    double *aux[8];
+    int n;
+};
+__global__ void k_stage_guess(const int *hist, const double *x, double *xprev, StageVecs S, long long n) {
+    wait_prior_kernel();
+    const bool h = *hist != 0;
+    GRID_STRIDE(i, n) {
+        const double xv = x[i];
+        if (h) {
+            const double d = xv - xprev[i];
+            for (int k = 0; k < S.n; ++k) S.dst[k][i] = S.src[k][i] + d;
+        }
+        xprev[i] = xv;
+    }
+}
+
+// out[0] = max |a - b|, out[1] = max |b| (non-negative doubles compared by their bit patterns, whose
+// order is theirs); out zeroed before the launch
+__global__ void k_max_diff(const double *a, const double *b, long long n, unsigned long long *out) {
+    wait_prior_kernel();
+    double d = 0.0, m = 0.0;
+    GRID_STRIDE(i, n) {
+        const double bv = b[i];
+        d = fmax(d, fabs(a[i] - bv));
+        m = fmax(m, fabs(bv));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        d = fmax(d, __shfl_down_sync(0xffffffffu, d, o));
+        m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&out[0], (unsigned long long)__double_as_longlong(d));
+        atomicMax(&out[1], (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// the stage history is cleared unless out[0] <= rtol out[1] (see k_max_diff)
+__global__ void k_keep_if_close(const unsigned long long *out, double rtol, int *hist) {
+    wait_prior_kernel();
+    const double d = __longlong_as_double((long long)out[0]), m = __longlong_as_double((long long)out[1]);
+    if (!(d <= rtol * m)) *hist = 0;
+}
+
+// dst = src unless *hist is set (the stage guess without history: the previous stage's solution)
+__global__ void k_copy_unless(const int *hist, const double *src, double *dst, long long n) {
+    wait_prior_kernel();
+    if (*hist) return;
+    GRID_STRIDE(i, n) dst[i] = src[i];
+}
+
+// guess_k = 2 H1_k - H2_k once two steps are kept (*hist >= 2), H1_k after one step: each stage's
+// own solutions in the last two steps, extrapolated linearly (dst: guesses, src: H1, aux: H2)
+__global__ void k_stage_guess_self(const int *hist, StageVecs S, long long n) {
+    wait_prior_kernel();
+    const int h = *hist;
+    if (h == 0) return;
+    GRID_STRIDE(i, n)
+        for (int k = 0; k < S.n; ++k) S.dst[k][i] = h >= 2 ? 2.0 * S.src[k][i] - S.aux[k][i] : S.src[k][i];
+}
+
+// the stage solutions of this step kept for the next step's guesses: aux_k = dst_k (the step
+// before, when aux is set), dst_k = src_k; set_hist: *hist counts the kept steps (at most 2)
+__global__ void k_stage_keep(StageVecs S, long long n, int *hist, int set_hist) {
+    wait_prior_kernel();
+    GRID_STRIDE(i, n)
+        for (int k = 0; k < S.n; ++k) {
+            if (S.aux[k]) S.aux[k][i] = S.dst[k][i];
+            S.dst[k][i] = S.src[k][i];
+        }
+    if (set_hist && blockIdx.x == 0 && threadIdx.x == 0) *hist = *hist < 2 ? *hist + 1 : 2;
+}
+
 // ------------------------------------------------------------------ condensation (CTA / cell)
 template <int K>
 __global__ void k_condense(RefDev R, MeshDev M, double c, double tau, double *Scell, double *Zc,

@@ -183,6 +183,13 @@ struct hdg_ctx {
     double t = 0.0;
     // IMEX stages
     std::vector<double *> Qs, rs, ps, ls;
+    // initial guesses of the stage solves (stage_guesses): the last step's stage solutions (HQs,
+    // Hps, Hls), the pressure and trace ones of the step before (H2ps, H2ls), the velocity at the
+    // last step's start (Qprev) and end (Qlast), and a device count of the steps kept (0..2)
+    std::vector<double *> HQs, Hps, Hls, H2ps, H2ls;
+    double *Qprev = nullptr, *Qlast = nullptr;
+    int *dhist = nullptr;
+    unsigned long long *dcheck = nullptr;                    // max |Q - Qlast|, max |Qlast| (bits)
     // forcing
     double *Fload = nullptr;
     bool has_forcing = false;
@@ -1801,6 +1808,48 @@ struct Impl {
     // ---------------------------------------------------------------- Alg. 1
     // One step from t0 (c->t is not advanced here). Inside a graph capture every solve is recorded
     // with device-side loops and the return value is 0 (non-convergence is counted on the device).
+    // Stage initial guesses across steps (stages solved to a tolerance only: a fixed number of
+    // Richardson sweeps, Alg. 2 as printed with n_richardson > 0, starts from the previous stage's
+    // solution, and its result depends on that start). keep = false (step start): with history,
+    // the velocity guess of each implicit stage i >= i0 is its solution in the previous step plus
+    // the state's change over that step (k_stage_guess); its pressure and trace guesses extrapolate
+    // the stage's own solutions of the last two steps linearly (k_stage_guess_self; after one kept
+    // step, the last solution). Without history each stage starts from the previous stage's
+    // solution (k_copy_unless in the stage loop). keep = true (after the stage solves): the
+    // solutions are kept and the count of kept steps raised. The count is a device value, so the
+    // recorded step graph takes every form; an entry point that sets the state from outside a
+    // step clears it unless the state is the one the last step left.
+    static void stage_guesses(hdg_ctx *c, int i0, bool keep) {
+        if (c->P.n_richardson > 0) return;          // the count stays zero
+        const int s = c->tab.s;
+        StageVecs SQ{}, SP{}, SL{};
+        for (int i = i0; i < s; ++i) {
+            const int k = SQ.n++;
+            SP.n++; SL.n++;
+            SP.aux[k] = c->H2ps[i]; SL.aux[k] = c->H2ls[i];
+            if (keep) {
+                SQ.dst[k] = c->HQs[i]; SQ.src[k] = c->Qs[i];
+                SP.dst[k] = c->Hps[i]; SP.src[k] = c->ps[i];
+                SL.dst[k] = c->Hls[i]; SL.src[k] = c->ls[i];
+            } else {
+                SQ.dst[k] = c->Qs[i]; SQ.src[k] = c->HQs[i];
+                SP.dst[k] = c->ps[i]; SP.src[k] = c->Hps[i];
+                SL.dst[k] = c->ls[i]; SL.src[k] = c->Hls[i];
+            }
+        }
+        if (keep) {
+            launch_k(k_stage_keep, grid_for(c->nQ), VEC_THREADS, 0, c->st, SQ, c->nQ, c->dhist, 0);
+            launch_k(k_stage_keep, grid_for(c->nPv), VEC_THREADS, 0, c->st, SP, c->nPv, c->dhist, 0);
+            launch_k(k_stage_keep, grid_for(c->nL), VEC_THREADS, 0, c->st, SL, c->nL, c->dhist, 1);
+        } else {
+            launch_k(k_stage_guess, grid_for(c->nQ), VEC_THREADS, 0, c->st, (const int *)c->dhist, (const double *)c->Q,
+                     c->Qprev, SQ, c->nQ);
+            launch_k(k_stage_guess_self, grid_for(c->nPv), VEC_THREADS, 0, c->st, (const int *)c->dhist, SP, c->nPv);
+            launch_k(k_stage_guess_self, grid_for(c->nL), VEC_THREADS, 0, c->st, (const int *)c->dhist, SL, c->nL);
+        }
+        CKL();
+    }
+
     static int imex_step_body(hdg_ctx *c, double t0) {
         const Tab &T = c->tab;
         const double dt = c->P.dt;
@@ -1817,6 +1866,7 @@ struct Impl {
         // P(Q^n), and every sum below runs over all implicit stages. M Q^n is read from the state,
         // which the step overwrites only in the final update.
         const int i0 = T.Ai[0][0] != 0.0 ? 0 : 1;
+        stage_guesses(c, i0, false);                // from the previous step, when it left them
         for (int i = i0; i < s; ++i) {
             // eq. imex_residual: r_i = M Q^n + sum_j (a_ij/a_jj)(M Q_j - r_j) + dt sum_j aex_ij (w.f_j)
             LinComb L = lincomb();
@@ -1838,14 +1888,20 @@ struct Impl {
             CKL();
             if (i > 0) {
                 bdm(c, c->Qs[i - 1], c->q[5]);                                   // Q*_{i-1}
-                CK(cudaMemcpyAsync(c->Qs[i], c->Qs[i - 1], bq, cudaMemcpyDeviceToDevice, c->st));
-                CK(cudaMemcpyAsync(c->ps[i], c->ps[i - 1], sizeof(double) * c->nPv, cudaMemcpyDeviceToDevice, c->st));
-                CK(cudaMemcpyAsync(c->ls[i], c->ls[i - 1], sizeof(double) * c->nL, cudaMemcpyDeviceToDevice, c->st));
+                // without history the stage starts from the previous stage's solution
+                launch_k(k_copy_unless, grid_for(c->nQ), VEC_THREADS, 0, c->st, (const int *)c->dhist,
+                         (const double *)c->Qs[i - 1], c->Qs[i], c->nQ);
+                launch_k(k_copy_unless, grid_for(c->nPv), VEC_THREADS, 0, c->st, (const int *)c->dhist,
+                         (const double *)c->ps[i - 1], c->ps[i], c->nPv);
+                launch_k(k_copy_unless, grid_for(c->nL), VEC_THREADS, 0, c->st, (const int *)c->dhist,
+                         (const double *)c->ls[i - 1], c->ls[i], c->nL);
+                CKL();
             } else {
                 bdm(c, c->Q, c->q[5]);                                           // P(Q^n); Q_0 starts at Q^n
             }
             nc |= stage_solve(c, T.Ai[i][i] * dt, c->rs[i], c->q[5], c->Qs[i], c->ps[i], c->ls[i]);
         }
+        stage_guesses(c, i0, true);                 // this step's stage solutions kept
         // eq. final_residual and eq. final_update (coefficient b_{s-1}^im dt)
         LinComb L = lincomb();
         int n = 0;
@@ -1868,6 +1924,8 @@ struct Impl {
         mixed_solve(c, dt * T.bi[s - 1], rn, nullptr, nullptr, nullptr, c->Q, c->pp[1], c->ll[1]);
         reconstruct(c, c->Q, t0 + dt, c->p, c->lam);                            // Sec. 2.7
         if (c->has_tracer) tracer_step(c);                                       // App. B
+        if (c->P.n_richardson <= 0)                 // the state this step leaves (see hdg_set_state)
+            CK(cudaMemcpyAsync(c->Qlast, c->Q, sizeof(double) * c->nQ, cudaMemcpyDeviceToDevice, c->st));
         return nc;
     }
 
@@ -2177,7 +2235,14 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
         for (int i = 0; i < c->tab.s; ++i) {
             c->Qs.push_back(c->alloc<double>(nQ)); c->rs.push_back(c->alloc<double>(nQ));
             c->ps.push_back(c->alloc<double>(nP)); c->ls.push_back(c->alloc<double>(nL));
+            c->HQs.push_back(c->alloc<double>(nQ)); c->Hps.push_back(c->alloc<double>(nP));
+            c->Hls.push_back(c->alloc<double>(nL));
+            c->H2ps.push_back(c->alloc<double>(nP)); c->H2ls.push_back(c->alloc<double>(nL));
         }
+        c->Qprev = c->alloc<double>(nQ); c->Qlast = c->alloc<double>(nQ);
+        c->dhist = c->alloc<int>(1);
+        CK(cudaMemset(c->dhist, 0, sizeof(int)));
+        c->dcheck = c->alloc<unsigned long long>(2);
         c->Fload = c->alloc<double>(nQ);
         c->dfv = c->alloc<double>(8);
         CK(cudaMallocHost(&c->hfv, 8 * sizeof(double)));
@@ -2339,6 +2404,13 @@ hdg_status hdg_set_state(hdg_ctx *c, const double *Q, const double *p, const dou
             if (p) I::to_modal(c, p, c->p, 1); else CK(cudaMemsetAsync(c->p, 0, c->nPv * 8, c->st));
             if (lam) I::to_modal(c, lam, c->lam, 2); else CK(cudaMemsetAsync(c->lam, 0, c->nL * 8, c->st));
         });
+        // the stage history stays only if the velocity is the one the last step left (up to the
+        // rounding of a round trip through get_state): max |Q - Qlast| <= 1e-9 max |Qlast|
+        CK(cudaMemsetAsync(c->dcheck, 0, 2 * sizeof(unsigned long long), c->st));
+        launch_k(k_max_diff, grid_for(c->nQ), VEC_THREADS, 0, c->st, (const double *)c->Q, (const double *)c->Qlast,
+                 c->nQ, c->dcheck);
+        launch_k(k_keep_if_close, 1, 1, 0, c->st, (const unsigned long long *)c->dcheck, 1e-9, c->dhist);
+        CKL();
         c->t = t;
         CK(cudaStreamSynchronize(c->st));
     } catch (...) {
@@ -2581,6 +2653,7 @@ double hdg_estimate_bytes(const hdg_mesh_desc *mesh, const hdg_params *params) {
     const double nstage_c = (double)cs.size(), ncond = nstage_c + 2;
     double b = 0;
     b += 8 * ((T.s + 1) * (nQ + nP + nL) + T.s * nQ + nQ);                 // state, stages, forcing
+    b += 8 * (T.s * (nQ + 2 * (nP + nL)) + 2 * nQ);                       // stage history (guesses)
     b += 8 * 2 * NU * nQ + 4 * nc * std::ceil(NU * 4 * std::ceil(NU / 4) / 32) * 32;   // Dblk, Binv, Binv32
     b += 8 * 3 * nc * 3 * nfq * 2 + 4 * 3 * nc * 3 * nfq * 2;             // weights, edge values
     b += 4 * (32 + 2) * nQ + 8 * (32 + 5) * nQ;                            // Step-I Krylov (FP32, FP64)
@@ -2733,6 +2806,7 @@ hdg_status hdg_div_free_project(hdg_ctx *c, hdg_stats *stats) {
     if (!c) return HDG_ERR_INVALID_ARG;
     try {
         begin_call(c);
+        CK(cudaMemsetAsync(c->dhist, 0, sizeof(int), c->st));     // the state changes outside a step
         DISPATCH(c, {
             I::mixed_solve(c, 1.0, nullptr, c->Q, nullptr, nullptr, c->q[0], c->pp[0], c->ll[0]);
             LinComb L = lincomb();
@@ -2754,6 +2828,7 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *c, hdg_stats *stats) {
     if (!c) return HDG_ERR_INVALID_ARG;
     try {
         begin_call(c);
+        CK(cudaMemsetAsync(c->dhist, 0, sizeof(int), c->st));     // the state changes outside a step
         DISPATCH(c, I::reconstruct(c, c->Q, c->t, c->p, c->lam));
         end_call(c, stats);
     } catch (...) {
