@@ -511,15 +511,20 @@ def stage_flops(k, ncells):
     return st_flop, s_flop
 
 
-def assembly_flops(k, ncells):
-    """Algorithmic FP64 flops of one launch of the Step-I assembly (k_fimpl_assemble, stage form):
-    the coefficients of J^-1 Q*, {Q*}.n at the facet points (own and neighbour traces), the
-    weighted facet rows, the volume advection block through the reference tensor (2 MU products per
-    entry), the three weighted facet masses, and the NU x NU block entries (an FMA counts two)."""
+def assembly_flops(k, ncells, df32=False):
+    """Algorithmic flops of one launch of the Step-I assembly (k_fimpl_assemble, stage form): the
+    coefficients of J^-1 Q*, {Q*}.n at the facet points (own and neighbour traces), the weighted
+    facet rows, the volume advection block through the reference tensor (2 MU products per entry),
+    the three weighted facet masses, and the NU x NU block entries (an FMA counts two). Returns
+    (FP64 flops, flops of the advection contraction when it runs in double-FP32 on the FP32 pipes
+    (df32, HDG_MIXED), else 0)."""
     mu = (k + 2) * (k + 3) // 2
     nu, nfq = 2 * mu, (3 * k + 5) // 2
-    fma = 4 * mu + 3 * nfq * 4 * mu + 3 * nfq * mu * 2 + 3 * nfq * 3 + mu * mu * 2 * mu + 3 * mu * mu * nfq + nu * nu * 5
-    return 2.0 * fma * ncells
+    adv = mu * mu * 2 * mu
+    fma = 4 * mu + 3 * nfq * 4 * mu + 3 * nfq * mu * 2 + 3 * nfq * 3 + 3 * mu * mu * nfq + nu * nu * 5
+    if df32:
+        return 2.0 * fma * ncells, 2.0 * adv * ncells
+    return 2.0 * (fma + adv) * ncells, 0.0
 
 
 def bdm_flops(k, ncells):
@@ -623,15 +628,18 @@ def run_gpu(args, rank, world, local_rank):
     outer = sum(s['richardson_iters'] for s in stats_all) / args.steps
     p32 = sum(s['stage_products32'] for s in stats_all) / args.steps
     inner = stepI_iters / args.steps
+    as_flop = assembly_flops(w['k'], ncells, df32=args.precision == 'MIXED')
     kernels = {
         f"k_stage_apply<{w['k']}>": {'what': 'FP64 stage operator (FGMRES products, restart residuals)',
                                      'ms_per_launch': st_ms, 'launches_per_step': outer - p32 + 2 * stages,
                                      'bytes': st_bytes, 'flop': st_flop, 'bound': 'alu'},
         f"k_cg_apply<{w['k'] + 1}>": {'what': 'FP64 trace operator apply (tight trace CG)', 'ms_per_launch': k_ms,
                                       'launches_per_step': trace_iters / args.steps, 'bytes': k_bytes, 'bound': 'hbm'},
-        f"k_fimpl_assemble<{w['k']}>": {'what': 'FP64 Step-I assembly (stage solves and the reconstruction f^impl)',
+        f"k_fimpl_assemble<{w['k']}>": {'what': 'Step-I assembly (stage solves and the reconstruction f^impl): FP64, '
+                                                'the advection contraction in double-FP32 under HDG_MIXED (flop: the '
+                                                'FP64 part, df32_flop: the contraction)',
                                         'ms_per_launch': as_ms, 'launches_per_step': stages + 1, 'bytes': as_bytes,
-                                        'flop': assembly_flops(w['k'], ncells), 'bound': 'alu'},
+                                        'flop': as_flop[0], 'df32_flop': as_flop[1], 'bound': 'alu'},
         f"k_bdm<{w['k']}>": {'what': 'FP64 BDM projection (stage advecting velocities and the reconstruction)',
                              'ms_per_launch': bd_ms, 'launches_per_step': stages + 1, 'bytes': bd_bytes,
                              'flop': bdm_flops(w['k'], ncells), 'bound': 'alu'}}

@@ -433,7 +433,8 @@ template <int K>
 __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const CellGeo &g,
                                          const double *QsK, const double *const *Qsn,
                                          const int *nbr_edge, double c, double alpha,
-                                         double dup, double *sm, double *D, double *wq) {
+                                         double dup, double *sm, double *D, double *wq,
+                                         const float *Tadv2 = nullptr) {
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
     double *gc = sm;                 // 2 x MU: coefficients of (J^-1 Q*)_r
@@ -441,9 +442,18 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
     double *adv = qsn + 3 * NFQ;     // MU x MU
     double *Wa = adv + MU * MU;      // 3 x MU x MU: sum_q fw phi_a phi_b (Q*.n/2 - delta |Q*.n|) on edge e
     double *T2 = Wa + 3 * MU * MU;   // 3 x NFQ x MU: fw_q phi_b(e, q) (Q*.n/2 - delta |Q*.n|) (0 on walls)
+    // with Tadv2 (device): g_rc also split into FP32 pairs (hi, lo) at the start of Wa, which is
+    // written only after the advection block is formed
+    float *gcf = reinterpret_cast<float *>(Wa);
     TFOR(i, 2 * MU) {
         const int r = i / MU, b = i % MU;
-        gc[i] = g.Jinv[2 * r] * QsK[b] + g.Jinv[2 * r + 1] * QsK[MU + b];
+        const double v = g.Jinv[2 * r] * QsK[b] + g.Jinv[2 * r + 1] * QsK[MU + b];
+        gc[i] = v;
+        if (Tadv2) {
+            const float h = (float)v;
+            gcf[i] = h;
+            gcf[2 * MU + i] = (float)(v - (double)h);
+        }
     }
     TFOR(i, 3 * NFQ) {
         int e = i / NFQ, q = i % NFQ;
@@ -472,11 +482,39 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
         int e = i / NFQ, q = i % NFQ;
         wq[i] = Qsn[e] ? -c * ldg(&R.fw[q]) * g.h[e] * (-0.5 * qsn[i] + dup * fabs(qsn[i])) : 0.0;
     }
-    TFOR(i, MU * MU) {                  // -(w.(Q*.grad)Q)_K for one component
-        double s = 0;
+    if (Tadv2) {
+#ifdef __CUDA_ARCH__
+        // -(w.(Q*.grad)Q)_K in double-FP32 on the FP32 pipes (GB300's FP64 rate is 1/64 of its FP32
+        // rate): T and g_rc as pairs hi + lo (48 significant bits), each hi*hi product split exactly
+        // (TwoProduct by FMA), the cross terms hi*lo + lo*hi added in FP32, the sum kept as an
+        // unevaluated pair (TwoSum; Dekker 1971, Ogita-Rump-Oishi's Dot2, SIAM J. Sci. Comput. 26
+        // (2005)): about 2^-46 of sum |g T| against FP64's 2^-53 per operation. The _rn intrinsics
+        // keep the compiler from fusing the products into the sums.
+        const float *Tl = Tadv2 + (size_t)2 * MU * MU * MU;
+        TFOR(i, MU * MU) {
+            float sh = 0.f, sl = 0.f;
 #pragma unroll 6
-        for (int rc = 0; rc < 2 * MU; ++rc) s += gc[rc] * ldg(&R.Tadv[(size_t)rc * MU * MU + i]);
-        adv[i] = -g.detJ * s;
+            for (int rc = 0; rc < 2 * MU; ++rc) {
+                const float th = __ldg(&Tadv2[(size_t)rc * MU * MU + i]), tl = __ldg(&Tl[(size_t)rc * MU * MU + i]);
+                const float gh = gcf[rc], gl = gcf[2 * MU + rc];
+                const float p = __fmul_rn(gh, th);
+                const float e = fmaf(gh, tl, fmaf(gl, th, fmaf(gh, th, -p)));
+                const float sn = __fadd_rn(sh, p);
+                const float bp = __fsub_rn(sn, sh);
+                const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(sn, bp)), __fsub_rn(p, bp));
+                sh = sn;
+                sl = __fadd_rn(sl, __fadd_rn(t, e));
+            }
+            adv[i] = -g.detJ * ((double)sh + (double)sl);
+        }
+#endif
+    } else {
+        TFOR(i, MU * MU) {              // -(w.(Q*.grad)Q)_K for one component
+            double s = 0;
+#pragma unroll 6
+            for (int rc = 0; rc < 2 * MU; ++rc) s += gc[rc] * ldg(&R.Tadv[(size_t)rc * MU * MU + i]);
+            adv[i] = -g.detJ * s;
+        }
     }
     tm.sync();
     TFOR(i, 3 * MU * MU) {              // Wa = sum_q phi_a(e, q) T2[e][q][b]

@@ -215,6 +215,7 @@ struct hdg_ctx {
     float *nrm32 = nullptr;                                  // cell normals in FP32 [6 cell + 2 e + d]
     // relaxed (FP32) stage-operator products: diagonal blocks, geometry, reference tables
     float *Dblk32 = nullptr, *geo32 = nullptr, *Dhat32 = nullptr, *Ehat32 = nullptr;
+    float *Tadv2 = nullptr;                                  // advection tensor: FP32 hi plane, lo plane
     bool gs_ok = false;                                      // cells 2-coloured by index parity (hdg_gs32.cuh)
     float *gV32 = nullptr, *gw32 = nullptr, *gu32 = nullptr;
     cudaGraphExec_t g_stepI32 = nullptr;                     // one loose Step-I solve (host-driven mode)
@@ -1129,6 +1130,8 @@ struct Impl {
 
     // Step-I operator M - cc F(Qs): diagonal blocks, neighbour and penalty weights, and the
     // block-Jacobi inverses named by inv (INV64 | INV32; with BLK32 also the blocks in FP32)
+    // the advection tensor as FP32 pairs for the assembly's double-FP32 contraction (HDG_MIXED)
+    static const float *tadv2(const hdg_ctx *c) { return c->P.precision == HDG_MIXED ? c->Tadv2 : nullptr; }
     static void assemble_stepI(hdg_ctx *c, const double *Qs, double cc, int inv) {
         CompTimer tm_(c, &c->S.ms_assembly);
         const size_t smem = sizeof(double) * ((inv & INV64) ? fimpl_smem_doubles<K>() : fimpl_smem_noinv_doubles<K>());
@@ -1137,7 +1140,7 @@ struct Impl {
         if (!c->capturing) CK(cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st));   // (graphs: once per launch)
         launch_k(k_fimpl_assemble<K>, (unsigned)c->ncells, 128, smem, c->st, 
             c->R, c->M, Qs, cc, c->P.alpha, c->P.delta_up, c->Dblk, c->wq, c->wq32, c->pen, c->pen32,
-            (inv & INV64) ? c->Binv : nullptr, c->dstatus);
+            (inv & INV64) ? c->Binv : nullptr, c->dstatus, tadv2(c));
         CKL();
         float *blk32 = (inv & BLK32) ? c->Dblk32 : nullptr;
         if (inv & INV32) {              // FP32 inverses: a warp per cell, the block in registers
@@ -2203,6 +2206,17 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
                                 &c->R.Ehat, &c->R.Tpp, &c->R.bdm_inv, &c->R.Iv, &c->R.nod_u, &c->R.nod_p,
                                 &c->R.mod_u, &c->R.mod_p, &c->R.nod_t, &c->R.mod_t, &c->R.Sfac, &c->R.Tadv};
         for (size_t i = 0; i < tabs.size(); ++i) *dst[i] = c->dref + offs[i];
+        {
+            const size_t n = T.Tadv.size();
+            std::vector<float> t2(2 * n);
+            for (size_t i = 0; i < n; ++i) {
+                const float h = (float)T.Tadv[i];
+                t2[i] = h;
+                t2[n + i] = (float)(T.Tadv[i] - (double)h);
+            }
+            c->Tadv2 = c->alloc<float>(2 * n);
+            CK(cudaMemcpy(c->Tadv2, t2.data(), 2 * n * sizeof(float), cudaMemcpyHostToDevice));
+        }
         // mesh
         c->geo = c->alloc<CellGeo>(c->ncells);
         CK(cudaMemcpy(c->geo, c->H.geo.data(), sizeof(CellGeo) * c->ncells, cudaMemcpyHostToDevice));
@@ -3035,7 +3049,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                     if (which == 15)
                         launch_k(k_fimpl_assemble<I::K_>, (unsigned)c->ncells, 128, smem, c->st, c->R, c->M,
                                  (const double *)c->q[5], cc, c->P.alpha, c->P.delta_up, c->Dblk, c->wq, c->wq32, c->pen,
-                                 c->pen32, (double *)nullptr, c->dstatus);
+                                 c->pen32, (double *)nullptr, c->dstatus, I::tadv2(c));
                     else
                         launch_k(k_bdm<I::K_>, cell_blocks(c), 128, sizeof(double) * TEAMS_PER_BLOCK * bdm_scratch<I::K_>(), c->st,
                                  c->R, c->M, (const double *)c->Q, c->q[5]);
