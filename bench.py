@@ -629,10 +629,16 @@ def run_gpu(args, rank, world, local_rank):
     p32 = sum(s['stage_products32'] for s in stats_all) / args.steps
     inner = stepI_iters / args.steps
     as_flop = assembly_flops(w['k'], ncells, df32=args.precision == 'MIXED')
+    if args.precision == 'MIXED':       # the pair-arithmetic kernel takes the FP64-accurate products
+        st_name, st_entry = f"k_stage_apply_f2<{w['k']}>", {
+            'what': 'stage operator in double-FP32 pairs, FP64-accurate (FGMRES products before the relaxed '
+                    'ones, restart residuals)', 'bound': 'hbm', 'flop_fp64_equiv': st_flop}
+    else:
+        st_name, st_entry = f"k_stage_apply<{w['k']}>", {
+            'what': 'FP64 stage operator (FGMRES products, restart residuals)', 'bound': 'alu', 'flop': st_flop}
+    st_entry.update({'ms_per_launch': st_ms, 'launches_per_step': outer - p32 + 2 * stages, 'bytes': st_bytes})
     kernels = {
-        f"k_stage_apply<{w['k']}>": {'what': 'FP64 stage operator (FGMRES products, restart residuals)',
-                                     'ms_per_launch': st_ms, 'launches_per_step': outer - p32 + 2 * stages,
-                                     'bytes': st_bytes, 'flop': st_flop, 'bound': 'alu'},
+        st_name: st_entry,
         f"k_cg_apply<{w['k'] + 1}>": {'what': 'FP64 trace operator apply (tight trace CG)', 'ms_per_launch': k_ms,
                                       'launches_per_step': trace_iters / args.steps, 'bytes': k_bytes, 'bound': 'hbm'},
         f"k_fimpl_assemble<{w['k']}>": {'what': 'Step-I assembly (stage solves and the reconstruction f^impl): FP64, '

@@ -118,9 +118,12 @@ typedef struct {
      * (default): the inner Step-I GMRES, the preconditioner's Step-II cell maps and V-cycle, the
      * tight trace CG's V-cycle and the first orthogonalisation pass of the stage FGMRES run in FP32;
      * the stage residual, its Krylov basis, the trace operator and the CG's iterates stay FP64, so
-     * the result meets the same FP64 stage tolerance. HDG_FP64: every kernel of the path computes
-     * in FP64 (inner Step I by FP64 GMRES with block Jacobi; inner_trace_fp32 and
-     * trace_fp32_vcycle are forced to 0). */
+     * the result meets the same FP64 stage tolerance. Under HDG_MIXED the FP64-bound contractions
+     * run on the FP32 pipes at FP64-class accuracy, as unevaluated pairs of FP32 numbers (about
+     * 2^-46 of the terms' magnitudes): the Step-I block's advection contraction, and, with
+     * relax_eta > 0 and richardson_rtol >= 5e-11, the stage FGMRES's FP64-accurate products.
+     * HDG_FP64: every kernel of the path computes in FP64 instructions (inner Step I by FP64 GMRES
+     * with block Jacobi; inner_trace_fp32 and trace_fp32_vcycle are forced to 0). */
     int precision;
     /* The one-V-cycle Step II inside the stage preconditioner (inner_trace_vcycles = 1): 1
      * (default) = the V-cycle in FP32 (operators rounded once per stage coefficient; the large P1
@@ -214,7 +217,10 @@ void hdg_destroy(hdg_ctx *ctx);
 /* Sizes (doubles) of the nodal Q, p and lambda arrays. */
 hdg_status hdg_dof_sizes(const hdg_ctx *ctx, int64_t *nQ, int64_t *np, int64_t *nlambda);
 
-/* State (device pointers, nodal). p and lam may be NULL (taken as zero). */
+/* State (device pointers, nodal). p and lam may be NULL (taken as zero). Setting a velocity
+ * other than the one the last step left (beyond 1e-9 of its largest coefficient) drops the
+ * stage history that hdg_imex_step starts its stage solves from; setting that same state again
+ * (a get/set round trip) keeps it. */
 hdg_status hdg_set_state(hdg_ctx *ctx, const double *Q, const double *p, const double *lam, double t);
 hdg_status hdg_get_state(hdg_ctx *ctx, double *Q, double *p, double *lam, double *t_host);
 
@@ -305,7 +311,12 @@ hdg_status hdg_cg_project(hdg_ctx *ctx, const double *Q, double *Qcg);
 hdg_status hdg_tracer_rhs(hdg_ctx *ctx, const double *q, const double *U, double *dq);
 
 /* Alg. 1 x nsteps: s-1 stage solves (Alg. 2), final update (eq. final_update) and pressure
- * reconstruction (Sec. 2.7) per step, on the context's state. */
+ * reconstruction (Sec. 2.7) per step, on the context's state. Stages solved to a tolerance
+ * (n_richardson = 0) start, once a step has been taken, from their own solutions in the
+ * previous steps (velocity shifted by the state's change over the last step, pressure and trace
+ * extrapolated from the last two); otherwise, and with a fixed number of Richardson sweeps, from
+ * the previous stage's values. hdg_div_free_project and hdg_reconstruct_pressure drop that
+ * history. */
 hdg_status hdg_imex_step(hdg_ctx *ctx, int nsteps, hdg_stats *stats);
 
 /* One stage solve (Alg. 2): find (Q, p, lambda) with
@@ -356,10 +367,12 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *ctx, hdg_stats *stats);
  * after a one-thread kernel that resets the step, whose time is subtracted); bytes = its
  * algorithmic bytes. which = 7 (bytes = 0): the preconditioner's Step II as the stage solves run it
  * (FP32 cell maps, then the inner trace solve: one V-cycle, in FP32 when inner_trace_fp32 is on),
- * recorded and replayed like 2..5. which = 8: the fused FP64 stage-operator kernel alone (the
- * FGMRES matrix-vector product without the facet gather) on the operator last assembled, input
- * the current state; bytes = its algorithmic bytes. which = 9: the FP32 preconditioner pass of
- * the inner Step-I GMRES (v_j formed from w and the projections, z = B^-1 v_j, z's edge values) at
+ * recorded and replayed like 2..5. which = 8: the fused stage-operator kernel the stage solves
+ * take for their FP64-accurate products, alone (the FGMRES matrix-vector product without the
+ * facet gather: FP64, or under HDG_MIXED with relax_eta > 0 and a stage tolerance of 5e-11 or
+ * more the pair-arithmetic kernel reading the block as its FP32 copy and rest), on the operator
+ * last assembled, input the current state; bytes = its algorithmic bytes. which = 9: the FP32
+ * preconditioner pass of the inner Step-I GMRES (v_j formed from w and the projections, z = B^-1 v_j, z's edge values) at
  * step j = 4, launched like 6; bytes = its algorithmic bytes. which = 10 (bytes = 0): one inner FP32
  * Arnoldi step as the solve runs it (preconditioner passes, product, finishing kernel), from 20 steps
  * launched back to back after a cycle start, less the cycle start alone. which = 11: the per-cell

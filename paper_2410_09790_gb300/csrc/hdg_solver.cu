@@ -27,6 +27,7 @@
 #include "hdg_mg32.cuh"
 #include "hdg_gs32.cuh"
 #include "hdg_stage32.cuh"
+#include "hdg_stage_f2.cuh"
 #include "hdg_tracer.cuh"
 #include "mesh.h"
 #include "refelem.h"
@@ -216,6 +217,12 @@ struct hdg_ctx {
     // relaxed (FP32) stage-operator products: diagonal blocks, geometry, reference tables
     float *Dblk32 = nullptr, *geo32 = nullptr, *Dhat32 = nullptr, *Ehat32 = nullptr;
     float *Tadv2 = nullptr;                                  // advection tensor: FP32 hi plane, lo plane
+    // pair-arithmetic stage operator (HDG_MIXED, k_stage_apply_f2): the blocks' rest after their
+    // FP32 rounding, the reference tables as pairs; blk32_ok: Dblk32 / Dblk32lo hold the
+    // operator last assembled
+    float *Dblk32lo = nullptr;
+    float2 *ephi2 = nullptr, *Ehat2 = nullptr, *Dhat2 = nullptr;
+    bool blk32_ok = false;
     bool gs_ok = false;                                      // cells 2-coloured by index parity (hdg_gs32.cuh)
     float *gV32 = nullptr, *gw32 = nullptr, *gu32 = nullptr;
     cudaGraphExec_t g_stepI32 = nullptr;                     // one loose Step-I solve (host-driven mode)
@@ -1143,6 +1150,7 @@ struct Impl {
             (inv & INV64) ? c->Binv : nullptr, c->dstatus, tadv2(c));
         CKL();
         float *blk32 = (inv & BLK32) ? c->Dblk32 : nullptr;
+        c->blk32_ok = blk32 && c->Dblk32lo;
         if (inv & INV32) {              // FP32 inverses: a warp per cell, the block in registers
             launch_k(k_block_inv32<K>, (unsigned)((c->ncells * 32 + 127) / 128), 128, 0, c->st, (const double *)c->Dblk,
                      c->Binv32, blk32, c->ncells, use_gs(c) ? 1 : 0, c->dstatus);
@@ -1150,6 +1158,11 @@ struct Impl {
         } else if (blk32) {
             launch_k(k_blocks_to_f32<K>, grid_for((long long)GsBlk<K>::SIZE * c->ncells), VEC_THREADS, 0, c->st,
                      (const double *)c->Dblk, blk32, (long long)c->ncells);
+            CKL();
+        }
+        if (c->blk32_ok) {              // the rest of each block after its FP32 rounding (pair products)
+            launch_k(k_blocks_lo<K>, grid_for((long long)GsBlk<K>::SIZE * c->ncells), VEC_THREADS, 0, c->st,
+                     (const double *)c->Dblk, c->Dblk32lo, (long long)c->ncells);
             CKL();
         }
         c->inv_ok = inv;
@@ -1414,6 +1427,24 @@ struct Impl {
                  p, lam, yQ, yp, c->vK, yQ32, yp32, zslot, zslot_j, gs, acc);
     }
 
+    // HDG_MIXED with the FP32 copy of the blocks current: the FP64-accurate products in pairs,
+    // for stage tolerances of PAIR_MIN_RTOL and above (pairs carry about 2^-46 = 1.4e-14 of the
+    // terms' magnitudes; at 1e-12 that already cost 8 % more outer iterations on a 16 x 16 walled
+    // channel, k = 4, so tighter tolerances take the FP64 kernel, whose products are 2^7 finer)
+    static constexpr double PAIR_MIN_RTOL = 5e-11;
+    static bool use_f2(const hdg_ctx *c) {
+        return c->P.precision == HDG_MIXED && c->blk32_ok && c->P.richardson_rtol >= PAIR_MIN_RTOL;
+    }
+    static void stage_apply_f2(hdg_ctx *c, double cc, const double *Q, const double *p, const double *lam, double *yQ,
+                               double *yp, float *yQ32, float *yp32, double *zslot, const int *zslot_j,
+                               const int *skip) {
+        const size_t smem = sizeof(f2) * STAGE32_WARPS * stage_f2_scratch<K>();
+        launch_k(k_stage_apply_f2<K>, (unsigned)((c->ncells + STAGE32_WARPS - 1) / STAGE32_WARPS), 32 * STAGE32_WARPS, smem,
+                 c->st, RefF2{c->ephi2, c->Ehat2, c->Dhat2}, (const double *)c->pen, c->M, (const float *)c->Dblk32,
+                 (const float *)c->Dblk32lo, (const double *)c->wq, cc, c->P.tau, Q, p, lam, yQ, yp, c->vK, yQ32, yp32,
+                 zslot, zslot_j, skip);
+    }
+
     // y = A(c) x (the stage operator). relax_gs (optional, with relaxed products in use): the
     // product is taken by the FP32 kernel when relax_gs->lowprec is set, else by the FP64 one
     // (both are launched; the other returns at once).
@@ -1425,10 +1456,14 @@ struct Impl {
         float *yQ32 = y32, *yp32 = y32 ? y32 + c->nQ : nullptr, *yl32 = y32 ? y32 + c->nQ + c->nPv : nullptr;
         const int *lowprec = relax_gs && relax_on(c) ? &relax_gs->lowprec : nullptr;
         const int *zj = zgs ? &zgs->j : (const int *)nullptr;
-        unsigned nb = cell_blocks(c);
-        launch_k(k_stage_apply<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (6 * Dm::NFQ + NL + 2 * MU), c->st, 
-            c->R, EdgeTab<double>{c->R.ephi, c->pen}, c->M, c->Dblk, c->wq, cc, c->P.tau, Q, p, lam, yQ, yp, c->vK,
-            yQ32, yp32, zslot, zj, lowprec);
+        if (use_f2(c)) {
+            stage_apply_f2(c, cc, Q, p, lam, yQ, yp, yQ32, yp32, zslot, zj, lowprec);
+        } else {
+            unsigned nb = cell_blocks(c);
+            launch_k(k_stage_apply<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * (6 * Dm::NFQ + NL + 2 * MU), c->st,
+                c->R, EdgeTab<double>{c->R.ephi, c->pen}, c->M, c->Dblk, c->wq, cc, c->P.tau, Q, p, lam, yQ, yp, c->vK,
+                yQ32, yp32, zslot, zj, lowprec);
+        }
         CKL();
         if (lowprec) {
             stage_apply32(c, cc, Q, p, lam, yQ, yp, yQ32, yp32, zslot, zj, relax_gs, c->capturing ? c->dcnt : nullptr);
@@ -2335,6 +2370,20 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
                 CK(cudaMemcpy(c->geo32, g32.data(), g32.size() * sizeof(float), cudaMemcpyHostToDevice));
                 c->Dhat32 = up32(c->T.Dhat);
                 c->Ehat32 = up32(c->T.Ehat);
+                c->Dblk32lo = c->alloc<float>(((size_t)c->NU * nup + 31) / 32 * 32 * (size_t)c->ncells);
+                auto up2 = [&](const std::vector<double> &v) {
+                    std::vector<float2> f(v.size());
+                    for (size_t i = 0; i < v.size(); ++i) {
+                        const float h = (float)v[i];
+                        f[i] = make_float2(h, (float)(v[i] - (double)h));
+                    }
+                    float2 *d = c->alloc<float2>(f.size());
+                    CK(cudaMemcpy(d, f.data(), f.size() * sizeof(float2), cudaMemcpyHostToDevice));
+                    return d;
+                };
+                c->ephi2 = up2(c->T.ephi);
+                c->Ehat2 = up2(c->T.Ehat);
+                c->Dhat2 = up2(c->T.Dhat);
             }
         }
         for (auto &x : c->q) x = c->alloc<double>(nQ);
@@ -3096,16 +3145,24 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                 // k_stage_apply alone on the operator last assembled (c scales the pressure and trace
                 // coupling), input the current state (Q, p, lambda); bytes: diagonal blocks +
                 // neighbour weights + neighbour maps + Q, p, lambda read + yQ, yp, v written
+                // (HDG_MIXED with relaxed products: the pair-arithmetic kernel k_stage_apply_f2, which
+                // the stage solves take, on the FP32 block copy and its rest: the same bytes)
                 const int nfq = (3 * c->K + 5) / 2;
-                b = 8.0 * c->ncells * ((double)NU * NU + 3 * nfq) + 4.0 * 6 * c->ncells +
+                const bool f2k = c->P.precision == HDG_MIXED && c->Dblk32lo && c->P.richardson_rtol >= I::PAIR_MIN_RTOL;
+                b = (f2k ? 8.0 * c->ncells * GsBlk<I::K_>::SIZE : 8.0 * c->ncells * (double)NU * NU) +
+                    8.0 * c->ncells * 3 * nfq + 4.0 * 6 * c->ncells +
                     8.0 * (2.0 * c->nQ + 2.0 * c->nPv + c->nL + (double)c->ncells * 3 * NT);
                 const unsigned nb = cell_blocks(c);
                 const size_t sm = sizeof(double) * TEAMS_PER_BLOCK * (6 * nfq + 3 * NT + 2 * I::MU);
                 auto launch = [&]() {
-                    launch_k(k_stage_apply<I::K_>, nb, 128, sm, c->st, c->R, EdgeTab<double>{c->R.ephi, c->pen}, c->M,
-                             c->Dblk, c->wq, cc, c->P.tau, c->Q, c->p, c->lam, c->q[6], c->pp[1], c->vK,
-                             (float *)nullptr, (float *)nullptr, (double *)nullptr, (const int *)nullptr,
-                             (const int *)nullptr);
+                    if (f2k)
+                        I::stage_apply_f2(c, cc, c->Q, c->p, c->lam, c->q[6], c->pp[1], (float *)nullptr,
+                                          (float *)nullptr, (double *)nullptr, (const int *)nullptr, (const int *)nullptr);
+                    else
+                        launch_k(k_stage_apply<I::K_>, nb, 128, sm, c->st, c->R, EdgeTab<double>{c->R.ephi, c->pen}, c->M,
+                                 c->Dblk, c->wq, cc, c->P.tau, c->Q, c->p, c->lam, c->q[6], c->pp[1], c->vK,
+                                 (float *)nullptr, (float *)nullptr, (double *)nullptr, (const int *)nullptr,
+                                 (const int *)nullptr);
                 };
                 launch();
                 CKL();

@@ -487,7 +487,20 @@ def test_time_kernel_modes_and_algorithmic_bytes():
         res[which] = b
     assert res[6] == 4.0 * (nc * 3 * nfq * 3 + 2 * ctx.nQ + 5 * ctx.nQ)
     assert res[9] == 4.0 * (nc * nu * nu + 6 * ctx.nQ + nc * 3 * nfq * 2)
-    assert res[8] == 8.0 * nc * (nu * nu + 3 * nfq) + 4.0 * 6 * nc + 8.0 * (2 * ctx.nQ + 2 * ctx.nP + ctx.nL + nc * 3 * nt)
+    # HDG_MIXED (default) at this stage tolerance: the pair-arithmetic kernel, whose block is read as
+    # its FP32 copy and rest in the padded per-cell layout (rows padded to 4, blocks to 32 floats)
+    nup = (nu + 3) // 4 * 4
+    size = (nu * nup + 31) // 32 * 32
+    vec = 8.0 * (2 * ctx.nQ + 2 * ctx.nP + ctx.nL + nc * 3 * nt)
+    assert res[8] == 8.0 * nc * (size + 3 * nfq) + 4.0 * 6 * nc + vec
+    ctx.close()
+    ctx = H().Context(n, k, periodic_x=True, tableau='ARS343', dt=0.01, n_richardson=0, stage_krylov=1,
+                      richardson_rtol=1e-10, richardson_max=400, precision='FP64')
+    ctx.hdg_set_state(cuda(Q0))
+    ctx.hdg_reconstruct_pressure()
+    ctx.hdg_imex_step(1)
+    ms, b = ctx.hdg_time_kernel(8, cstage, 3)
+    assert ms > 0.0 and b == 8.0 * nc * (nu * nu + 3 * nfq) + 4.0 * 6 * nc + vec
     ctx.close()
 
 
