@@ -516,15 +516,15 @@ def assembly_flops(k, ncells, df32=False):
     coefficients of J^-1 Q*, {Q*}.n at the facet points (own and neighbour traces), the weighted
     facet rows, the volume advection block through the reference tensor (2 MU products per entry),
     the three weighted facet masses, and the NU x NU block entries (an FMA counts two). Returns
-    (FP64 flops, flops of the advection contraction when it runs in double-FP32 on the FP32 pipes
-    (df32, HDG_MIXED), else 0)."""
+    (FP64 flops, flops of the parts that run in double-FP32 pairs on the FP32 pipes (df32,
+    HDG_MIXED: the advection contraction, the weighted facet masses and the block entries), else 0)."""
     mu = (k + 2) * (k + 3) // 2
     nu, nfq = 2 * mu, (3 * k + 5) // 2
-    adv = mu * mu * 2 * mu
-    fma = 4 * mu + 3 * nfq * 4 * mu + 3 * nfq * mu * 2 + 3 * nfq * 3 + 3 * mu * mu * nfq + nu * nu * 5
+    fp64 = 4 * mu + 3 * nfq * 4 * mu + 3 * nfq * mu * 2 + 3 * nfq * 3
+    pair = mu * mu * 2 * mu + 3 * mu * mu * nfq + nu * nu * 5
     if df32:
-        return 2.0 * fma * ncells, 2.0 * adv * ncells
-    return 2.0 * (fma + adv) * ncells, 0.0
+        return 2.0 * fp64 * ncells, 2.0 * pair * ncells
+    return 2.0 * (fp64 + pair) * ncells, 0.0
 
 
 def bdm_flops(k, ncells):
@@ -641,9 +641,10 @@ def run_gpu(args, rank, world, local_rank):
         st_name: st_entry,
         f"k_cg_apply<{w['k'] + 1}>": {'what': 'FP64 trace operator apply (tight trace CG)', 'ms_per_launch': k_ms,
                                       'launches_per_step': trace_iters / args.steps, 'bytes': k_bytes, 'bound': 'hbm'},
-        f"k_fimpl_assemble<{w['k']}>": {'what': 'Step-I assembly (stage solves and the reconstruction f^impl): FP64, '
-                                                'the advection contraction in double-FP32 under HDG_MIXED (flop: the '
-                                                'FP64 part, df32_flop: the contraction)',
+        f"k_fimpl_assemble<{w['k']}>": {'what': 'Step-I assembly (stage solves and the reconstruction f^impl): FP64; '
+                                                'under HDG_MIXED the block (advection contraction, facet masses, '
+                                                'entries) in double-FP32 pairs (flop: the FP64 part, df32_flop: '
+                                                'the pair part)',
                                         'ms_per_launch': as_ms, 'launches_per_step': stages + 1, 'bytes': as_bytes,
                                         'flop': as_flop[0], 'df32_flop': as_flop[1], 'bound': 'alu'},
         f"k_bdm<{w['k']}>": {'what': 'FP64 BDM projection (stage advecting velocities and the reconstruction)',

@@ -30,6 +30,9 @@
 #define __device__
 #define __forceinline__ inline
 #endif
+#ifdef __CUDACC__
+#include "hdg_df64.cuh"
+#endif
 
 namespace hdg {
 
@@ -423,18 +426,75 @@ __host__ __device__ void cell_bdm(const Team &tm, const RefDev &R, const CellGeo
 // facet masses Sfac, and the central/upwind facet term through per-edge MU x MU weighted facet
 // masses, so that each D entry combines a handful of precomputed numbers.
 // Scratch: fimpl_diag_scratch<K>() doubles. D: row-major [row][col].
+// The reference tables of the assembly's pair-arithmetic form (HDG_MIXED, device only): the
+// advection tensor as an FP32 hi plane and lo plane, the facet-point values and the reference
+// facet masses as pairs. All null: FP64.
+struct AsmF2 {
+    const float *Tadv2 = nullptr;
+    const float2 *ephi2 = nullptr, *Sfac2 = nullptr;
+};
+
 template <int K>
 constexpr int fimpl_diag_scratch() {
     typedef Dims<K> Dm;
     return 2 * Dm::MU + 3 * Dm::NFQ + Dm::MU * Dm::MU + 3 * Dm::MU * Dm::MU + 3 * Dm::NFQ * Dm::MU;
 }
 
+#ifdef __CUDACC__
+// The tail of cell_fimpl_diag in pairs (HDG_MIXED): the advection block adv and the weighted facet
+// rows T2 arrive as pairs in their own bytes; the weighted facet masses Wa and the block entries
+// are summed as pairs, the entries written to D in FP64.
+template <int K>
+__device__ void cell_fimpl_diag_f2(const Team &tm, const RefDev &R, const CellGeo &g, const double *const *Qsn,
+                                   double c, double alpha, const AsmF2 &F2, const double *adv_, double *Wa_,
+                                   const double *T2_, double *D) {
+    typedef Dims<K> Dm;
+    constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
+    const f2 *adv = reinterpret_cast<const f2 *>(adv_), *T2 = reinterpret_cast<const f2 *>(T2_);
+    f2 *Wa = reinterpret_cast<f2 *>(Wa_);
+    TFOR(i, 3 * MU * MU) {              // Wa = sum_q phi_a(e, q) T2[e][q][b]
+        const int e = i / (MU * MU), a = (i / MU) % MU, b = i % MU;
+        acc2 s;
+#pragma unroll
+        for (int q = 0; q < NFQ; ++q) s.fma(f2_of(__ldg(&F2.ephi2[(e * NFQ + q) * MU + a])), T2[(e * NFQ + q) * MU + b]);
+        Wa[i] = s.get();
+    }
+    tm.sync();
+    // per edge: -alpha n_d n_d2 for (d, d2) = (x, x), (x, y) = (y, x), (y, y); upwind weight h_e on
+    // interior edges
+    f2 pk[3][3], hw[3];
+    for (int e = 0; e < 3; ++e) {
+        pk[0][e] = f2_of(-alpha * g.nx[e] * g.nx[e]);
+        pk[1][e] = f2_of(-alpha * g.nx[e] * g.ny[e]);
+        pk[2][e] = f2_of(-alpha * g.ny[e] * g.ny[e]);
+        hw[e] = f2_of(Qsn[e] ? g.h[e] : 0.0);
+    }
+    const f2 cf = f2_of(c), dj = f2_of(g.detJ);
+    TFOR(i, NU * NU) {                  // diagonal block
+        const int r = i / NU, x = i % NU, d = r / MU, a = r % MU, d2 = x / MU, b = x % MU;
+        const int ab = a * MU + b, k = d + d2;
+        acc2 F;
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+            F.fma(k == 0 ? pk[0][e] : (k == 1 ? pk[1][e] : pk[2][e]), f2_of(__ldg(&F2.Sfac2[e * MU * MU + ab])));
+        if (d == d2) {
+            F.add(adv[ab]);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) F.fma(hw[e], Wa[e * MU * MU + ab]);
+        }
+        const f2 cF = f2_mul(cf, F.get());
+        D[i] = f2_dbl(r == x ? f2_sub(dj, cF) : f2_neg(cF));
+    }
+    tm.sync();
+}
+#endif
+
 template <int K>
 __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const CellGeo &g,
                                          const double *QsK, const double *const *Qsn,
                                          const int *nbr_edge, double c, double alpha,
                                          double dup, double *sm, double *D, double *wq,
-                                         const float *Tadv2 = nullptr) {
+                                         const AsmF2 F2 = AsmF2{}) {
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
     double *gc = sm;                 // 2 x MU: coefficients of (J^-1 Q*)_r
@@ -444,6 +504,7 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
     double *T2 = Wa + 3 * MU * MU;   // 3 x NFQ x MU: fw_q phi_b(e, q) (Q*.n/2 - delta |Q*.n|) (0 on walls)
     // with Tadv2 (device): g_rc also split into FP32 pairs (hi, lo) at the start of Wa, which is
     // written only after the advection block is formed
+    const float *Tadv2 = F2.Tadv2;
     float *gcf = reinterpret_cast<float *>(Wa);
     TFOR(i, 2 * MU) {
         const int r = i / MU, b = i % MU;
@@ -476,7 +537,13 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
     TFOR(i, 3 * NFQ * MU) {             // facet masses as E^T diag(weights) E: the weighted rows first
         const int e = i / (NFQ * MU), q = (i / MU) % NFQ, b = i % MU;
         const double sq = qsn[e * NFQ + q];
-        T2[i] = Qsn[e] ? ldg(&R.fw[q]) * ldg(&R.ephi[(e * NFQ + q) * MU + b]) * (0.5 * sq - dup * fabs(sq)) : 0.0;
+        const double v = Qsn[e] ? ldg(&R.fw[q]) * ldg(&R.ephi[(e * NFQ + q) * MU + b]) * (0.5 * sq - dup * fabs(sq)) : 0.0;
+#ifdef __CUDA_ARCH__
+        if (Tadv2) reinterpret_cast<f2 *>(T2)[i] = f2_of(v);    // (pairs in the same bytes)
+        else T2[i] = v;
+#else
+        T2[i] = v;
+#endif
     }
     TFOR(i, 3 * NFQ) {
         int e = i / NFQ, q = i % NFQ;
@@ -505,8 +572,11 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
                 sh = sn;
                 sl = __fadd_rn(sl, __fadd_rn(t, e));
             }
-            adv[i] = -g.detJ * ((double)sh + (double)sl);
+            reinterpret_cast<f2 *>(adv)[i] = f2_mul(f2_of(-g.detJ), f2_norm(sh, sl));   // (pairs)
         }
+        tm.sync();
+        cell_fimpl_diag_f2<K>(tm, R, g, Qsn, c, alpha, F2, adv, Wa, T2, D);
+        return;
 #endif
     } else {
         TFOR(i, MU * MU) {              // -(w.(Q*.grad)Q)_K for one component

@@ -717,12 +717,12 @@ constexpr int fimpl_smem_noinv_doubles() {
 // Step-I operator of one stage, one block per cell: diagonal block -> Dblk, neighbour weights
 // -> wq (and wq32 in FP32), the penalty weights -> pen / pen32 (cell 0), and the inverse of the
 // diagonal block in FP64 -> Binv when non-null (dynamic shared memory: fimpl_smem_doubles, or
-// fimpl_smem_noinv_doubles without Binv). The FP32 inverses come from k_block_inv32. Tadv2
-// (optional): the advection tensor as FP32 pairs, its contraction then in double-FP32.
+// fimpl_smem_noinv_doubles without Binv). The FP32 inverses come from k_block_inv32. F2 (tables
+// non-null): the block formed in pair arithmetic (cell_fimpl_diag_f2), written in FP64.
 template <int K>
 __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c, double alpha,
                                  double dup, double *Dblk, double *wq, float *wq32, double *pen, float *pen32,
-                                 double *Binv, int *status, const float *__restrict__ Tadv2) {
+                                 double *Binv, int *status, const AsmF2 F2) {
     wait_prior_kernel();
     typedef Dims<K> Dm;
     constexpr int NU = Dm::NU, NFQ = Dm::NFQ;
@@ -745,7 +745,7 @@ __global__ void k_fimpl_assemble(RefDev R, MeshDev M, const double *Qs, double c
     }
     double *D = sm + fimpl_diag_scratch<K>();
     double *wqs = D + NU * NU;
-    cell_fimpl_diag<K>(tm, R, g, Qs + (size_t)cell * NU, Qn, ne, c, alpha, dup, sm, D, wqs, Tadv2);
+    cell_fimpl_diag<K>(tm, R, g, Qs + (size_t)cell * NU, Qn, ne, c, alpha, dup, sm, D, wqs, F2);
     const long long nrows = (long long)M.ncells * NU;
     TFOR(i, NU * NU) {
         int col = i / NU, row = i % NU;

@@ -217,6 +217,7 @@ struct hdg_ctx {
     // relaxed (FP32) stage-operator products: diagonal blocks, geometry, reference tables
     float *Dblk32 = nullptr, *geo32 = nullptr, *Dhat32 = nullptr, *Ehat32 = nullptr;
     float *Tadv2 = nullptr;                                  // advection tensor: FP32 hi plane, lo plane
+    float2 *ephi2a = nullptr, *Sfac2 = nullptr;              // facet values, facet masses as pairs
     // pair-arithmetic stage operator (HDG_MIXED, k_stage_apply_f2): the blocks' rest after their
     // FP32 rounding, the reference tables as pairs; blk32_ok: Dblk32 / Dblk32lo hold the
     // operator last assembled
@@ -1137,8 +1138,10 @@ struct Impl {
 
     // Step-I operator M - cc F(Qs): diagonal blocks, neighbour and penalty weights, and the
     // block-Jacobi inverses named by inv (INV64 | INV32; with BLK32 also the blocks in FP32)
-    // the advection tensor as FP32 pairs for the assembly's double-FP32 contraction (HDG_MIXED)
-    static const float *tadv2(const hdg_ctx *c) { return c->P.precision == HDG_MIXED ? c->Tadv2 : nullptr; }
+    // the assembly's tables as pairs (HDG_MIXED: the block formed in pair arithmetic)
+    static AsmF2 tadv2(const hdg_ctx *c) {
+        return c->P.precision == HDG_MIXED ? AsmF2{c->Tadv2, c->ephi2a, c->Sfac2} : AsmF2{};
+    }
     static void assemble_stepI(hdg_ctx *c, const double *Qs, double cc, int inv) {
         CompTimer tm_(c, &c->S.ms_assembly);
         const size_t smem = sizeof(double) * ((inv & INV64) ? fimpl_smem_doubles<K>() : fimpl_smem_noinv_doubles<K>());
@@ -2251,6 +2254,18 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
             }
             c->Tadv2 = c->alloc<float>(2 * n);
             CK(cudaMemcpy(c->Tadv2, t2.data(), 2 * n * sizeof(float), cudaMemcpyHostToDevice));
+            auto pairs = [&](const std::vector<double> &v) {
+                std::vector<float2> f(v.size());
+                for (size_t i = 0; i < v.size(); ++i) {
+                    const float h = (float)v[i];
+                    f[i] = make_float2(h, (float)(v[i] - (double)h));
+                }
+                float2 *d = c->alloc<float2>(f.size());
+                CK(cudaMemcpy(d, f.data(), f.size() * sizeof(float2), cudaMemcpyHostToDevice));
+                return d;
+            };
+            c->ephi2a = pairs(T.ephi);
+            c->Sfac2 = pairs(T.Sfac);
         }
         // mesh
         c->geo = c->alloc<CellGeo>(c->ncells);
