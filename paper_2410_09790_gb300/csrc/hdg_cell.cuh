@@ -558,6 +558,7 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
         // (2005)): about 2^-46 of sum |g T| against FP64's 2^-53 per operation. The _rn intrinsics
         // keep the compiler from fusing the products into the sums.
         const float *Tl = Tadv2 + (size_t)2 * MU * MU * MU;
+        const f2 mdj = f2_of(-g.detJ);
         TFOR(i, MU * MU) {
             float sh = 0.f, sl = 0.f;
 #pragma unroll 6
@@ -572,7 +573,7 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
                 sh = sn;
                 sl = __fadd_rn(sl, __fadd_rn(t, e));
             }
-            reinterpret_cast<f2 *>(adv)[i] = f2_mul(f2_of(-g.detJ), f2_norm(sh, sl));   // (pairs)
+            reinterpret_cast<f2 *>(adv)[i] = f2_mul(mdj, f2_norm(sh, sl));   // (pairs)
         }
         tm.sync();
         cell_fimpl_diag_f2<K>(tm, R, g, Qsn, c, alpha, F2, adv, Wa, T2, D);

@@ -59,11 +59,14 @@ __global__ void k_gs_diag(EdgeTab<float> E, MeshDev M, const float *__restrict__
     constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
     constexpr int SCR = 2 * NU + 6 * NFQ;
     __shared__ float hproj[GM_M + 2];
+    GS_CELL(col)
+    float4 pre[GsPre<K>::NC];                   // the block read ahead (small K)
+    if constexpr (GsPre<K>::ON)
+        if (cell < M.ncells) warp_block_prefetch<K>(Binv, gs_slot(cell, M.ncells), pre);
     const int j = gs->j;
     if ((int)threadIdx.x < j) hproj[threadIdx.x] = gs->hcol32[threadIdx.x];
     __syncthreads();
     extern __shared__ double smd[];
-    GS_CELL(col)
     if (cell >= M.ncells) return;
     float *vK = reinterpret_cast<float *>(smd) + team * SCR, *zK = vK + NU, *t = zK + NU;
     const float inv = gs->inv32;
@@ -84,7 +87,8 @@ __global__ void k_gs_diag(EdgeTab<float> E, MeshDev M, const float *__restrict__
         TFOR(r, NU) vK[r] -= nbr_row<K, float>(E, t, r / MU, r % MU);
     }
     tm.sync();
-    warp_block_apply<K>(Binv, gs_slot(cell, M.ncells), vK, zK);
+    if constexpr (GsPre<K>::ON) warp_block_apply_pre<K>(pre, vK, zK);
+    else warp_block_apply<K>(Binv, gs_slot(cell, M.ncells), vK, zK);
     tm.sync();
     team_edge_values<K>(tm, E, cell, zK, utr);
 }

@@ -821,6 +821,60 @@ __device__ __forceinline__ void warp_block_apply(const float *__restrict__ Binv,
     }
 }
 
+// The same product with the block read ahead into registers (warp_block_prefetch at the start of
+// a kernel, so that its loads overlap the kernel's other loads; warp_block_apply_pre once v is
+// ready): the same sums in the same order as warp_block_apply. Only for K <= 3, where a lane holds
+// at most 8 of the block's 16-byte column pieces.
+template <int K>
+struct GsPre {
+    static constexpr int NC = (GsBlk<K>::NU + GsBlk<K>::S - 1) / GsBlk<K>::S;   // columns per lane
+    static constexpr bool ON = NC <= 8;
+};
+
+template <int K>
+__device__ __forceinline__ void warp_block_prefetch(const float *__restrict__ Binv, long long slot,
+                                                    float4 (&pre)[GsPre<K>::NC]) {
+    typedef GsBlk<K> B;
+    const int lane = (int)(threadIdx.x & 31), g = lane % B::G, s = lane / B::G;
+    const float4 *blk = reinterpret_cast<const float4 *>(Binv + (size_t)slot * B::SIZE);
+#pragma unroll
+    for (int u = 0; u < GsPre<K>::NC; ++u) {
+        const int q = s + u * B::S;
+        pre[u] = (s < B::S && q < B::NU) ? __ldg(blk + q * (B::NUP / 4) + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void warp_block_apply_pre(const float4 (&pre)[GsPre<K>::NC], const float *v, float *z) {
+    typedef GsBlk<K> B;
+    const int lane = (int)(threadIdx.x & 31), g = lane % B::G, s = lane / B::G;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+    for (int u = 0; u < GsPre<K>::NC; ++u) {
+        const int q = s + u * B::S;
+        if (s < B::S && q < B::NU) {
+            const float4 b = pre[u];
+            const float vq = v[q];
+            a0 = fmaf(b.x, vq, a0); a1 = fmaf(b.y, vq, a1);
+            a2 = fmaf(b.z, vq, a2); a3 = fmaf(b.w, vq, a3);
+        }
+    }
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+#pragma unroll
+    for (int s2 = 0; s2 < B::S; ++s2) {             // the subsets' partial sums, in order
+        const int src = s2 * B::G + g;
+        t0 += __shfl_sync(0xffffffffu, a0, src); t1 += __shfl_sync(0xffffffffu, a1, src);
+        t2 += __shfl_sync(0xffffffffu, a2, src); t3 += __shfl_sync(0xffffffffu, a3, src);
+    }
+    if (s == 0) {
+        const int r = 4 * g;
+        if (r < B::NU) z[r] = t0;
+        if (r + 1 < B::NU) z[r + 1] = t1;
+        if (r + 2 < B::NU) z[r + 2] = t2;
+        if (r + 3 < B::NU) z[r + 3] = t3;
+    }
+}
+
 // FP32 inverses of the Step-I diagonal blocks for the inner (preconditioner) solves, one warp per
 // cell with the block in registers: lane l holds rows l and l + 32 (< NU), Gauss-Jordan in place
 // without pivoting, row k reaching the other lanes by shuffles. No pivoting is needed: the block
