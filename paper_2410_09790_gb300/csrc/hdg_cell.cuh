@@ -437,7 +437,7 @@ struct AsmF2 {
 template <int K>
 constexpr int fimpl_diag_scratch() {
     typedef Dims<K> Dm;
-    return 2 * Dm::MU + 3 * Dm::NFQ + Dm::MU * Dm::MU + 3 * Dm::MU * Dm::MU + 3 * Dm::NFQ * Dm::MU;
+    return 2 * Dm::MU + 3 * Dm::NFQ + Dm::MU * Dm::MU + 3 * Dm::MU * Dm::MU + 3 * Dm::NFQ * Dm::MU + 16;
 }
 
 #ifdef __CUDACC__
@@ -445,9 +445,8 @@ constexpr int fimpl_diag_scratch() {
 // rows T2 arrive as pairs in their own bytes; the weighted facet masses Wa and the block entries
 // are summed as pairs, the entries written to D in FP64.
 template <int K>
-__device__ void cell_fimpl_diag_f2(const Team &tm, const RefDev &R, const CellGeo &g, const double *const *Qsn,
-                                   double c, double alpha, const AsmF2 &F2, const double *adv_, double *Wa_,
-                                   const double *T2_, double *D) {
+__device__ void cell_fimpl_diag_f2(const Team &tm, const AsmF2 &F2, const double *adv_, double *Wa_,
+                                   const double *T2_, const double *cst_, double *D) {
     typedef Dims<K> Dm;
     constexpr int MU = Dm::MU, NU = Dm::NU, NFQ = Dm::NFQ;
     const f2 *adv = reinterpret_cast<const f2 *>(adv_), *T2 = reinterpret_cast<const f2 *>(T2_);
@@ -460,23 +459,17 @@ __device__ void cell_fimpl_diag_f2(const Team &tm, const RefDev &R, const CellGe
         Wa[i] = s.get();
     }
     tm.sync();
-    // per edge: -alpha n_d n_d2 for (d, d2) = (x, x), (x, y) = (y, x), (y, y); upwind weight h_e on
-    // interior edges
-    f2 pk[3][3], hw[3];
-    for (int e = 0; e < 3; ++e) {
-        pk[0][e] = f2_of(-alpha * g.nx[e] * g.nx[e]);
-        pk[1][e] = f2_of(-alpha * g.nx[e] * g.ny[e]);
-        pk[2][e] = f2_of(-alpha * g.ny[e] * g.ny[e]);
-        hw[e] = f2_of(Qsn[e] ? g.h[e] : 0.0);
-    }
-    const f2 cf = f2_of(c), dj = f2_of(g.detJ);
+    // the cell's constants as pairs (cst, formed once per cell): pk[k][e] = -alpha n_d n_d2 for
+    // k = d + d2 (xx, xy = yx, yy) on edge e, the upwind weight h_e on interior edges, c, detJ
+    const f2 *cst = reinterpret_cast<const f2 *>(cst_);
+    const f2 *pk = cst, *hw = cst + 9, cf = cst[12], dj = cst[13];
     TFOR(i, NU * NU) {                  // diagonal block
         const int r = i / NU, x = i % NU, d = r / MU, a = r % MU, d2 = x / MU, b = x % MU;
         const int ab = a * MU + b, k = d + d2;
         acc2 F;
 #pragma unroll
         for (int e = 0; e < 3; ++e)
-            F.fma(k == 0 ? pk[0][e] : (k == 1 ? pk[1][e] : pk[2][e]), f2_of(__ldg(&F2.Sfac2[e * MU * MU + ab])));
+            F.fma(pk[3 * k + e], f2_of(__ldg(&F2.Sfac2[e * MU * MU + ab])));
         if (d == d2) {
             F.add(adv[ab]);
 #pragma unroll
@@ -502,10 +495,27 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
     double *adv = qsn + 3 * NFQ;     // MU x MU
     double *Wa = adv + MU * MU;      // 3 x MU x MU: sum_q fw phi_a phi_b (Q*.n/2 - delta |Q*.n|) on edge e
     double *T2 = Wa + 3 * MU * MU;   // 3 x NFQ x MU: fw_q phi_b(e, q) (Q*.n/2 - delta |Q*.n|) (0 on walls)
+    double *cst = T2 + 3 * NFQ * MU; // 16: the pair form's per-cell constants (cell_fimpl_diag_f2)
     // with Tadv2 (device): g_rc also split into FP32 pairs (hi, lo) at the start of Wa, which is
     // written only after the advection block is formed
     const float *Tadv2 = F2.Tadv2;
     float *gcf = reinterpret_cast<float *>(Wa);
+#ifdef __CUDA_ARCH__
+    if (Tadv2 && tm.tid < 15) {         // pair constants: pk[k][e] (9), hw[e] (3), c, detJ, -detJ
+        const int i = tm.tid;
+        double v;
+        if (i < 9) {
+            const int k = i / 3, e = i % 3;
+            const double na = k == 2 ? g.ny[e] : g.nx[e], nb = k == 0 ? g.nx[e] : g.ny[e];
+            v = -alpha * na * nb;
+        } else if (i < 12) {
+            v = Qsn[i - 9] ? g.h[i - 9] : 0.0;
+        } else {
+            v = i == 12 ? c : (i == 13 ? g.detJ : -g.detJ);
+        }
+        reinterpret_cast<f2 *>(cst)[i] = f2_of(v);
+    }
+#endif
     TFOR(i, 2 * MU) {
         const int r = i / MU, b = i % MU;
         const double v = g.Jinv[2 * r] * QsK[b] + g.Jinv[2 * r + 1] * QsK[MU + b];
@@ -558,7 +568,7 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
         // (2005)): about 2^-46 of sum |g T| against FP64's 2^-53 per operation. The _rn intrinsics
         // keep the compiler from fusing the products into the sums.
         const float *Tl = Tadv2 + (size_t)2 * MU * MU * MU;
-        const f2 mdj = f2_of(-g.detJ);
+        const f2 mdj = reinterpret_cast<const f2 *>(cst)[14];
         TFOR(i, MU * MU) {
             float sh = 0.f, sl = 0.f;
 #pragma unroll 6
@@ -576,7 +586,7 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
             reinterpret_cast<f2 *>(adv)[i] = f2_mul(mdj, f2_norm(sh, sl));   // (pairs)
         }
         tm.sync();
-        cell_fimpl_diag_f2<K>(tm, R, g, Qsn, c, alpha, F2, adv, Wa, T2, D);
+        cell_fimpl_diag_f2<K>(tm, F2, adv, Wa, T2, cst, D);
         return;
 #endif
     } else {

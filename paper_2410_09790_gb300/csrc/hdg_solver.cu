@@ -1430,6 +1430,10 @@ struct Impl {
                  p, lam, yQ, yp, c->vK, yQ32, yp32, zslot, zslot_j, gs, acc);
     }
 
+    static f2 pair_of(double x) {
+        const float h = (float)x;
+        return f2{h, (float)(x - (double)h)};
+    }
     // HDG_MIXED with the FP32 copy of the blocks current: the FP64-accurate products in pairs,
     // for stage tolerances of PAIR_MIN_RTOL and above (pairs carry about 2^-46 = 1.4e-14 of the
     // terms' magnitudes; at 1e-12 that already cost 8 % more outer iterations on a 16 x 16 walled
@@ -1444,7 +1448,8 @@ struct Impl {
         const size_t smem = sizeof(f2) * STAGE32_WARPS * stage_f2_scratch<K>();
         launch_k(k_stage_apply_f2<K>, (unsigned)((c->ncells + STAGE32_WARPS - 1) / STAGE32_WARPS), 32 * STAGE32_WARPS, smem,
                  c->st, RefF2{c->ephi2, c->Ehat2, c->Dhat2}, (const double *)c->pen, c->M, (const float *)c->Dblk32,
-                 (const float *)c->Dblk32lo, (const double *)c->wq, cc, c->P.tau, Q, p, lam, yQ, yp, c->vK, yQ32, yp32,
+                 (const float *)c->Dblk32lo, (const double *)c->wq, pair_of(cc), pair_of(c->P.tau), Q, p, lam, yQ, yp,
+                 c->vK, yQ32, yp32,
                  zslot, zslot_j, skip);
     }
 

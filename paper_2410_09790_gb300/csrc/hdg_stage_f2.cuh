@@ -88,11 +88,12 @@ __global__ void k_blocks_lo(const double *__restrict__ Dblk, float *__restrict__
 // yp, the cell's lambda-row contributions v, the FP32 shadows yQ32 / yp32 when set, and the copy
 // of x into the FGMRES's preconditioned-vector slot *zslot_j when set). skip (optional): return
 // at once when *skip is set (k_stage_apply32 takes that product). Dhi, Dlo: the diagonal block's
-// FP32 rounding and rest (GsBlk, slot = cell); wq, pen: the assembly's FP64 weights.
+// FP32 rounding and rest (GsBlk, slot = cell); wq, pen: the assembly's FP64 weights; cf, tf: the
+// stage coefficient c and the stabilisation tau as pairs.
 template <int K>
 __global__ void __launch_bounds__(128) k_stage_apply_f2(RefF2 T, const double *__restrict__ pen, MeshDev M,
                                                         const float *__restrict__ Dhi, const float *__restrict__ Dlo,
-                                                        const double *__restrict__ wq, double c, double tau,
+                                                        const double *__restrict__ wq, f2 cf, f2 tf,
                                                         const double *Q, const double *p, const double *lam, double *yQ,
                                                         double *yp, double *v, float *yQ32, float *yp32, double *zslot,
                                                         const int *zslot_j, const int *skip) {
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(128) k_stage_apply_f2(RefF2 T, const double *_
     tm.sync();
     warp_block_apply_f2<K>(Dhi, Dlo, cell, xK, dq);
     tm.sync();
-    const f2 cf = f2_of(c), tf = f2_of(tau), detJ = gg[4];
+    const f2 detJ = gg[4];
     // velocity rows: (M - cF) Q (diagonal block dense, neighbours from t) - c (detJ Jinv-mapped
     // Dhat^T p - sum_e h_e n_e Ehat^T lambda)
     TFOR(x, NU) {
