@@ -437,7 +437,7 @@ struct AsmF2 {
 template <int K>
 constexpr int fimpl_diag_scratch() {
     typedef Dims<K> Dm;
-    return 2 * Dm::MU + 3 * Dm::NFQ + Dm::MU * Dm::MU + 3 * Dm::MU * Dm::MU + 3 * Dm::NFQ * Dm::MU + 16;
+    return 2 * Dm::MU + 3 * Dm::NFQ + Dm::MU * Dm::MU + 3 * Dm::MU * Dm::MU + 3 * Dm::NFQ * Dm::MU + 16 + 3 * Dm::NFQ;
 }
 
 #ifdef __CUDACC__
@@ -496,6 +496,7 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
     double *Wa = adv + MU * MU;      // 3 x MU x MU: sum_q fw phi_a phi_b (Q*.n/2 - delta |Q*.n|) on edge e
     double *T2 = Wa + 3 * MU * MU;   // 3 x NFQ x MU: fw_q phi_b(e, q) (Q*.n/2 - delta |Q*.n|) (0 on walls)
     double *cst = T2 + 3 * NFQ * MU; // 16: the pair form's per-cell constants (cell_fimpl_diag_f2)
+    double *weq = cst + 16;          // 3 x NFQ: the pair form's facet-point weights fw_q (Q*.n/2 - delta |Q*.n|)
     // with Tadv2 (device): g_rc also split into FP32 pairs (hi, lo) at the start of Wa, which is
     // written only after the advection block is formed
     const float *Tadv2 = F2.Tadv2;
@@ -542,18 +543,22 @@ __host__ __device__ void cell_fimpl_diag(const Team &tm, const RefDev &R, const 
             s = 0.5 * ((k0 + o0) * g.nx[e] + (k1 + o1) * g.ny[e]);
         }
         qsn[i] = s;
+#ifdef __CUDA_ARCH__
+        if (Tadv2) reinterpret_cast<f2 *>(weq)[i] = f2_of(Qsn[e] ? ldg(&R.fw[q]) * (0.5 * s - dup * fabs(s)) : 0.0);
+#endif
     }
     tm.sync();
     TFOR(i, 3 * NFQ * MU) {             // facet masses as E^T diag(weights) E: the weighted rows first
         const int e = i / (NFQ * MU), q = (i / MU) % NFQ, b = i % MU;
         const double sq = qsn[e * NFQ + q];
-        const double v = Qsn[e] ? ldg(&R.fw[q]) * ldg(&R.ephi[(e * NFQ + q) * MU + b]) * (0.5 * sq - dup * fabs(sq)) : 0.0;
 #ifdef __CUDA_ARCH__
-        if (Tadv2) reinterpret_cast<f2 *>(T2)[i] = f2_of(v);    // (pairs in the same bytes)
-        else T2[i] = v;
-#else
-        T2[i] = v;
+        if (Tadv2) {                    // (pairs in the same bytes)
+            reinterpret_cast<f2 *>(T2)[i] = f2_mul(reinterpret_cast<const f2 *>(weq)[e * NFQ + q],
+                                                   f2_of(__ldg(&F2.ephi2[(e * NFQ + q) * MU + b])));
+            continue;
+        }
 #endif
+        T2[i] = Qsn[e] ? ldg(&R.fw[q]) * ldg(&R.ephi[(e * NFQ + q) * MU + b]) * (0.5 * sq - dup * fabs(sq)) : 0.0;
     }
     TFOR(i, 3 * NFQ) {
         int e = i / NFQ, q = i % NFQ;

@@ -25,7 +25,19 @@ __device__ __forceinline__ f2 f2_of(double x) {
 
 __device__ __forceinline__ f2 f2_of(float2 v) { return f2{v.x, v.y}; }
 
-__device__ __forceinline__ double f2_dbl(f2 a) { return (double)a.h + (double)a.l; }
+// an FP32 number widened to FP64 by assembling the FP64 bit pattern on the integer pipes (exact
+// for normal numbers; zeros and subnormals give a signed zero, an error below 2^-126): keeps the
+// conversion off GB300's narrow FP64 pipe
+__device__ __forceinline__ double f32_widen(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xFFu, s = b & 0x80000000u, m = b & 0x7FFFFFu;
+    if (e == 0u) return __hiloint2double((int)s, 0);
+    const unsigned ed = e == 0xFFu ? 0x7FFu : e + 896u;         // (inf / NaN keep their class)
+    return __hiloint2double((int)(s | (ed << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// the pair as one FP64 number: both words widened exactly, one FP64 addition
+__device__ __forceinline__ double f2_dbl(f2 a) { return f32_widen(a.h) + f32_widen(a.l); }
 
 // s + t = a + b exactly (TwoSum)
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
