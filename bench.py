@@ -647,9 +647,13 @@ def run_gpu(args, rank, world, local_rank):
                                                 'the pair part)',
                                         'ms_per_launch': as_ms, 'launches_per_step': stages + 1, 'bytes': as_bytes,
                                         'flop': as_flop[0], 'df32_flop': as_flop[1], 'bound': 'alu'},
-        f"k_bdm<{w['k']}>": {'what': 'FP64 BDM projection (stage advecting velocities and the reconstruction)',
-                             'ms_per_launch': bd_ms, 'launches_per_step': stages + 1, 'bytes': bd_bytes,
-                             'flop': bdm_flops(w['k'], ncells), 'bound': 'alu'}}
+        (f"k_bdm_f2<{w['k']}>" if args.precision == 'MIXED' else f"k_bdm<{w['k']}>"): (
+            {'what': 'BDM projection in double-FP32 pairs (stage advecting velocities and the reconstruction)',
+             'ms_per_launch': bd_ms, 'launches_per_step': stages + 1, 'bytes': bd_bytes,
+             'flop_fp64_equiv': bdm_flops(w['k'], ncells), 'bound': 'hbm'} if args.precision == 'MIXED' else
+            {'what': 'FP64 BDM projection (stage advecting velocities and the reconstruction)',
+             'ms_per_launch': bd_ms, 'launches_per_step': stages + 1, 'bytes': bd_bytes,
+             'flop': bdm_flops(w['k'], ncells), 'bound': 'alu'})}
     if s32_ms is not None:
         kernels[f"k_stage_apply32<{w['k']}>"] = {'what': 'FP32 stage operator (relaxed FGMRES products)',
                                                  'ms_per_launch': s32_ms, 'launches_per_step': p32,

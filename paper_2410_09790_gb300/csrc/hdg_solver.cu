@@ -218,6 +218,7 @@ struct hdg_ctx {
     float *Dblk32 = nullptr, *geo32 = nullptr, *Dhat32 = nullptr, *Ehat32 = nullptr;
     float *Tadv2 = nullptr;                                  // advection tensor: FP32 hi plane, lo plane
     float2 *ephi2a = nullptr, *Sfac2 = nullptr;              // facet values, facet masses as pairs
+    float2 *fw2 = nullptr, *leg2 = nullptr, *Iv2 = nullptr, *bdminv2 = nullptr;   // BDM tables as pairs
     // pair-arithmetic stage operator (HDG_MIXED, k_stage_apply_f2): the blocks' rest after their
     // FP32 rounding, the reference tables as pairs; blk32_ok: Dblk32 / Dblk32lo hold the
     // operator last assembled
@@ -1714,8 +1715,16 @@ struct Impl {
 
     static void bdm(hdg_ctx *c, const double *Q, double *Qs) {
         CompTimer tm_(c, &c->S.ms_bdm);
+        bdm_launch(c, Q, Qs);
+    }
+    // the BDM kernel: in pairs under HDG_MIXED (k_bdm_f2), FP64 otherwise
+    static void bdm_launch(hdg_ctx *c, const double *Q, double *Qs) {
         unsigned nb = cell_blocks(c);
-        launch_k(k_bdm<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * bdm_scratch<K_>(), c->st, c->R, c->M, Q, Qs);
+        if (c->P.precision == HDG_MIXED)
+            launch_k(k_bdm_f2<K>, nb, 128, sizeof(f2) * TEAMS_PER_BLOCK * bdm_f2_scratch<K_>(), c->st,
+                     BdmF2{c->ephi2a, c->fw2, c->leg2, c->Iv2, c->bdminv2}, c->M, Q, Qs);
+        else
+            launch_k(k_bdm<K>, nb, 128, sizeof(double) * TEAMS_PER_BLOCK * bdm_scratch<K_>(), c->st, c->R, c->M, Q, Qs);
         CKL();
     }
 
@@ -2271,6 +2280,10 @@ hdg_status hdg_setup_mesh(hdg_ctx **out, const hdg_mesh_desc *mesh, const hdg_pa
             };
             c->ephi2a = pairs(T.ephi);
             c->Sfac2 = pairs(T.Sfac);
+            c->fw2 = pairs(T.fw);
+            c->leg2 = pairs(T.leg);
+            c->Iv2 = pairs(T.Iv);
+            c->bdminv2 = pairs(T.bdm_inv);
         }
         // mesh
         c->geo = c->alloc<CellGeo>(c->ncells);
@@ -3120,8 +3133,7 @@ hdg_status hdg_time_kernel(hdg_ctx *c, int which, double cc, int reps, double *m
                                  (const double *)c->q[5], cc, c->P.alpha, c->P.delta_up, c->Dblk, c->wq, c->wq32, c->pen,
                                  c->pen32, (double *)nullptr, c->dstatus, I::tadv2(c));
                     else
-                        launch_k(k_bdm<I::K_>, cell_blocks(c), 128, sizeof(double) * TEAMS_PER_BLOCK * bdm_scratch<I::K_>(), c->st,
-                                 c->R, c->M, (const double *)c->Q, c->q[5]);
+                        I::bdm_launch(c, (const double *)c->Q, c->q[5]);
                 };
                 launch();
                 CKL();

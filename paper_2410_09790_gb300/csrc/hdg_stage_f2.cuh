@@ -247,4 +247,112 @@ __global__ void __launch_bounds__(128) k_stage_apply_f2(RefF2 T, const double *_
     }
 }
 
+// ------------------------------------------------------------------ BDM projection in pairs
+// The canonical BDM_{k+1} interpolant Q* = P(Q) per cell (Sec. 2.3; cell_bdm's steps) in pair
+// arithmetic for HDG_MIXED: the normal averages {Q}.n at the facet points (own and neighbour
+// traces), their moments against the Legendre polynomials, the interior Nedelec moments, the
+// local solve through the reference inverse moment matrix and the Piola map back. Tables as pairs
+// (layouts as in RefDev): facet-point values, facet weights, Legendre values, interior moment
+// tensor, inverse moment matrix.
+struct BdmF2 {
+    const float2 *ephi, *fw, *leg, *Iv, *inv;
+};
+
+template <int K>
+constexpr int bdm_f2_scratch() {
+    typedef Dims<K> Dm;
+    return 4 * Dm::NU + Dm::NU + Dm::NU + 3 * Dm::NFQ + 2 * Dm::MU + 20;
+}
+
+template <int K>
+__global__ void k_bdm_f2(BdmF2 T, MeshDev M, const double *Q, double *Qs) {
+    wait_prior_kernel();
+    typedef Dims<K> Dm;
+    constexpr int MU = Dm::MU, NU = Dm::NU, NB = Dm::NB, NV = Dm::NV, NFQ = Dm::NFQ;
+    extern __shared__ double sm[];
+    const int team = threadIdx.x / TEAM_LANES;
+    const int cell = (blockIdx.x * blockDim.x + threadIdx.x) / TEAM_LANES;
+    if (cell >= M.ncells) return;
+    Team tm{(int)(threadIdx.x % TEAM_LANES), TEAM_LANES};
+    f2 *xq = reinterpret_cast<f2 *>(sm) + (size_t)team * bdm_f2_scratch<K>();   // own Q (NU)
+    f2 *xo = xq + NU;                   // neighbours' Q (3 x NU)
+    f2 *m = xo + 3 * NU, *qh = m + NU, *an = qh + NU, *r = an + 3 * NFQ;
+    f2 *gg = r + 2 * MU;                // J[4], Jinv[4], detJ, 1/detJ, h[3], nx[3], ny[3], (0)
+    const int *nbr = M.cell_nbr + 3 * cell;
+    TFOR(i, NU) xq[i] = f2_of(Q[(size_t)cell * NU + i]);
+    TFOR(i, 3 * NU) {
+        const int o = __ldg(&nbr[i / NU]);
+        xo[i] = o >= 0 ? f2_of(Q[(size_t)o * NU + i % NU]) : f2{0.f, 0.f};
+    }
+    TFOR(i, 20) {                       // (a 16-lane team: some lanes take two)
+        const CellGeo &G = M.geo[cell];
+        double v;
+        if (i < 4) v = G.J[i];
+        else if (i < 8) v = G.Jinv[i - 4];
+        else if (i == 8) v = G.detJ;
+        else if (i == 9) v = 1.0 / G.detJ;
+        else if (i < 13) v = G.h[i - 10];
+        else if (i < 16) v = G.nx[i - 13];
+        else if (i < 19) v = G.ny[i - 16];
+        else v = 0.0;
+        gg[i] = f2_of(v);
+    }
+    tm.sync();
+    TFOR(i, 3 * NFQ) {                  // h_e fw_q {Q}.n at the facet points (0 on walls)
+        const int e = i / NFQ, q = i % NFQ;
+        const int o = __ldg(&nbr[e]);
+        f2 sv{0.f, 0.f};
+        if (o >= 0) {
+            const int eo = __ldg(&M.cell_nbr_edge[3 * cell + e]);
+            const float2 *pk = &T.ephi[(e * NFQ + q) * MU], *po = &T.ephi[(eo * NFQ + (NFQ - 1 - q)) * MU];
+            const f2 *xe = xo + e * NU;
+            acc2 s0, s1;
+#pragma unroll 7
+            for (int a = 0; a < MU; ++a) {
+                const f2 fk = f2_of(__ldg(pk + a)), fo = f2_of(__ldg(po + a));
+                s0.fma(fk, xq[a]); s1.fma(fk, xq[MU + a]);
+                s0.fma(fo, xe[a]); s1.fma(fo, xe[MU + a]);
+            }
+            const f2 un = f2_add(f2_mul(s0.get(), gg[13 + e]), f2_mul(s1.get(), gg[16 + e]));
+            const f2 w = f2_mul(gg[10 + e], f2_of(__ldg(&T.fw[q])));
+            sv = f2_mul(w, f2{0.5f * un.h, 0.5f * un.l});
+        }
+        an[i] = sv;
+    }
+    TFOR(a, MU) {                       // Jinv-mapped velocity for the interior moments
+        r[a] = f2_add(f2_mul(gg[4], xq[a]), f2_mul(gg[5], xq[MU + a]));
+        r[MU + a] = f2_add(f2_mul(gg[6], xq[a]), f2_mul(gg[7], xq[MU + a]));
+    }
+    tm.sync();
+    TFOR(i, 3 * NB) {                   // edge moments against the Legendre polynomials
+        const int e = i / NB, j = i % NB;
+        acc2 s;
+#pragma unroll
+        for (int q = 0; q < NFQ; ++q) s.fma(an[e * NFQ + q], f2_of(__ldg(&T.leg[q * NB + j])));
+        m[i] = s.get();
+    }
+    TFOR(v, NV) {                       // interior moments
+        acc2 s;
+#pragma unroll 7
+        for (int a = 0; a < MU; ++a) {
+            s.fma(r[a], f2_of(__ldg(&T.Iv[(a * NV + v) * 2])));
+            s.fma(r[MU + a], f2_of(__ldg(&T.Iv[(a * NV + v) * 2 + 1])));
+        }
+        m[3 * NB + v] = f2_mul(gg[8], s.get());
+    }
+    tm.sync();
+    TFOR(x, NU) {                       // reference coefficients through the inverse moment matrix
+        acc2 s;
+#pragma unroll 6
+        for (int k = 0; k < NU; ++k) s.fma(f2_of(__ldg(&T.inv[x * NU + k])), m[k]);
+        qh[x] = s.get();
+    }
+    tm.sync();
+    TFOR(x, NU) {                       // Piola map back
+        const int d = x / MU, a = x % MU;
+        const f2 v = f2_add(f2_mul(gg[2 * d], qh[a]), f2_mul(gg[2 * d + 1], qh[MU + a]));
+        Qs[(size_t)cell * NU + x] = f2_dbl(f2_mul(v, gg[9]));
+    }
+}
+
 }  // namespace hdg
