@@ -680,6 +680,7 @@ def run_gpu(args, rank, world, local_rank):
     # size; C3's colour pass captured at 128x128 (the size rule for a full capture) and scaled by
     # the cell ratio (its traffic is proportional to the cells: one block inverse per cell)
     traffic_src = {('c2', 'k_stage_apply<3>'): ('k_stage_apply_fp64_c2.md', 1.0),
+                   ('c2', 'k_stage_apply_f2<3>'): ('k_stage_apply_f2_pairs_c2.md', 1.0),
                    ('c2', 'k_gs_diag<3>'): ('k_gs_diag_fp32_c2.md', 1.0),
                    ('c3', 'k_gs_diag<4>'): ('k_gs_diag_fp32_tg128_k4.md', (w['n'] / 128.0) ** 2)}.get((args.workload, top))
     if kt['bound'] == 'alu':

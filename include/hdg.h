@@ -120,8 +120,9 @@ typedef struct {
      * the stage residual, its Krylov basis, the trace operator and the CG's iterates stay FP64, so
      * the result meets the same FP64 stage tolerance. Under HDG_MIXED the FP64-bound contractions
      * run on the FP32 pipes at FP64-class accuracy, as unevaluated pairs of FP32 numbers (about
-     * 2^-46 of the terms' magnitudes): the Step-I block's advection contraction, and, with
-     * relax_eta > 0 and richardson_rtol >= 5e-11, the stage FGMRES's FP64-accurate products.
+     * 2^-46 of the terms' magnitudes): the Step-I block (advection contraction, weighted facet
+     * masses, entries), the BDM projection and, with relax_eta > 0 and richardson_rtol >= 5e-11,
+     * the stage FGMRES's FP64-accurate products.
      * HDG_FP64: every kernel of the path computes in FP64 instructions (inner Step I by FP64 GMRES
      * with block Jacobi; inner_trace_fp32 and trace_fp32_vcycle are forced to 0). */
     int precision;
@@ -387,7 +388,7 @@ hdg_status hdg_reconstruct_pressure(hdg_ctx *ctx, hdg_stats *stats);
  * (k_fimpl_assemble in the stage solves' form: block and weights, no FP64 inverse) for coefficient
  * c around the current state's BDM projection (the context's Step-I operator is overwritten; the
  * next stage solve assembles its own); which = 16: the BDM projection kernel alone on the current
- * state; bytes = their algorithmic bytes. */
+ * state (in pairs under HDG_MIXED, as the stage solves take it); bytes = their algorithmic bytes. */
 hdg_status hdg_time_kernel(hdg_ctx *ctx, int which, double c, int reps, double *ms_per_launch,
                            double *bytes_per_launch);
 
