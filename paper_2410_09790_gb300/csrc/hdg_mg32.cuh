@@ -203,10 +203,12 @@ __global__ void k_tv_cheb(TraceOp32 T, const float *__restrict__ r, const float 
 }
 
 // ---------------------------------------------------------------- P1 levels in one block
-// Shared-memory layout of P1 level l (l = 0: the mesh vertices) at off[l]: b, xa, xb, d, dinv (nv
-// floats each), then for l >= 1 the stencil A (7 nv floats, by vertex); the stencil of level 0
-// is read from global memory. Threads take the points of a level as rows of nvx columns, so a
-// thread's column and its neighbours' columns are fixed and rows step without a division.
+// Shared-memory layout of P1 level l (l = 0: the tail's first level) at off[l]: b, xa, xb, d, dinv
+// (nv floats each), then the stencil A (7 nv floats, by vertex). The constant parts (dinv, A) come
+// from an image of the whole layout in global memory (img, built once per coefficient: zeros in
+// the vector parts), copied in with 16-byte loads at the kernel's start. Threads take the points of
+// a level as rows of nvx columns, so a thread's column and its neighbours' columns are fixed and
+// rows step without a division.
 struct Tail32 {
     int L, Nc, nfacets;
     P1Grid G[MG_MAX_LEVELS];
@@ -216,13 +218,15 @@ struct Tail32 {
     const float *Minv;             // coarsest grid: (A + 1 1^T / N)^{-1}, row-major
     const float *b1;               // right-hand side on level 0 (P^T of the trace residual)
     float *e1;                     // correction on level 0 (out)
+    const float4 *img;             // the shared-memory image (tail32_floats, padded to 4 floats)
+    int nimg4;                     // its length in float4
 };
 
 // shared floats the tail needs for the grids G[0..L-1]
 inline size_t tail32_floats(const P1Grid *G, int L) {
     size_t n = 0;
-    for (int l = 0; l < L; ++l) n += (size_t)(l >= 1 ? 12 : 5) * G[l].nverts;
-    return n;
+    for (int l = 0; l < L; ++l) n += (size_t)12 * G[l].nverts;
+    return (n + 3) / 4 * 4;
 }
 
 // index k + one step on a line of n points: wrapped when periodic, -1 outside otherwise
@@ -243,7 +247,7 @@ __device__ __forceinline__ TLevel tail_level(const Tail32 &T, float *tsm, int l)
     const P1Grid &G = T.G[l];
     V.nvx = G.nvx; V.nvy = G.nvy; V.px = G.px; V.py = G.py; V.nv = G.nverts;
     V.b = tsm + T.off[l]; V.xa = V.b + V.nv; V.xb = V.xa + V.nv; V.d = V.xb + V.nv; V.dv = V.d + V.nv;
-    V.A = l >= 1 ? V.dv + V.nv : T.A[0];
+    V.A = V.dv + V.nv;
     V.invth = T.invth[l]; V.c1 = T.c1[l]; V.c2 = T.c2[l];
     return V;
 }
@@ -268,11 +272,11 @@ __device__ __forceinline__ Stencil stencil(const TLevel &V, int i, int j, int ip
     return S;
 }
 
-__device__ __forceinline__ float apply_st(const TLevel &V, const Stencil &S, const float *x, bool gA) {
+__device__ __forceinline__ float apply_st(const TLevel &V, const Stencil &S, const float *x) {
     const float *a = V.A + P1_NS * S.p[0];
     float s = 0.f;
 #pragma unroll
-    for (int o = 0; o < P1_NS; ++o) s += (gA ? __ldg(a + o) : a[o]) * x[S.p[o]];
+    for (int o = 0; o < P1_NS; ++o) s += a[o] * x[S.p[o]];
     return s;
 }
 
@@ -295,13 +299,12 @@ __global__ void __launch_bounds__(1024) k_tv_tail(Tail32 T) {
     wait_prior_kernel();
     extern __shared__ float tsm[];
     const int tid = threadIdx.x, nth = blockDim.x;
-    for (int l = 0; l < T.L; ++l) {                        // diagonals, and the stencils of l >= 1
-        const int nv = T.G[l].nverts;
-        float *dv = tsm + T.off[l] + 4 * nv;
-        for (int v = tid; v < nv; v += nth) dv[v] = __ldg(&T.dinv[l][v]);
-        if (l >= 1)
-            for (int q = tid; q < P1_NS * nv; q += nth) dv[nv + q] = __ldg(&T.A[l][q]);
+    {                                                      // diagonals and stencils: the image
+        float4 *dst = reinterpret_cast<float4 *>(tsm);
+#pragma unroll 4
+        for (int i = tid; i < T.nimg4; i += nth) dst[i] = __ldg(&T.img[i]);
     }
+    __syncthreads();
     {
         float *b = tsm + T.off[0];
         for (int v = tid; v < T.G[0].nverts; v += nth) b[v] = __ldcg(&T.b1[v]);
@@ -309,7 +312,6 @@ __global__ void __launch_bounds__(1024) k_tv_tail(Tail32 T) {
     __syncthreads();
     for (int l = 0; l < T.L - 1; ++l) {                    // down
         const TLevel V = tail_level(T, tsm, l);
-        const bool gA = l == 0;
         // two Chebyshev steps from 0: x0 = invth D^-1 b (formed at the stencil points), then
         // d = c1 x0 + c2 D^-1 (b - A x0), xb = x0 + d
         TL_FOR(V, {
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(1024) k_tv_tail(Tail32 T) {
 _Pragma("unroll")
             for (int o = 0; o < P1_NS; ++o) {
                 const int w = S.p[o];
-                ax += (gA ? __ldg(a + o) : a[o]) * (V.invth * V.dv[w] * V.b[w]);
+                ax += a[o] * (V.invth * V.dv[w] * V.b[w]);
             }
             const float x0 = V.invth * V.dv[v] * V.b[v];
             const float dn = V.c1 * x0 + V.c2 * V.dv[v] * (V.b[v] - ax);
@@ -329,7 +331,7 @@ _Pragma("unroll")
         __syncthreads();
         TL_FOR(V, {                                        // residual, kept in xa
             const Stencil S = stencil(V, i, j, ip, im);
-            V.xa[v] = V.b[v] - apply_st(V, S, V.xb, gA);
+            V.xa[v] = V.b[v] - apply_st(V, S, V.xb);
         })
         __syncthreads();
         const TLevel C = tail_level(T, tsm, l + 1);
@@ -372,7 +374,6 @@ _Pragma("unroll")
     }
     for (int l = T.L - 2; l >= 0; --l) {                   // up
         const TLevel V = tail_level(T, tsm, l), C = tail_level(T, tsm, l + 1);
-        const bool gA = l == 0;
         TL_FOR(V, {                                        // xb += I e (linear interpolation)
             const int i0 = i >> 1, j0 = j >> 1, oi = i & 1, oj = j & 1;
             float e = C.xb[j0 * C.nvx + i0];
@@ -385,14 +386,14 @@ _Pragma("unroll")
         __syncthreads();
         TL_FOR(V, {
             const Stencil S = stencil(V, i, j, ip, im);
-            const float dn = V.invth * V.dv[v] * (V.b[v] - apply_st(V, S, V.xb, gA));
+            const float dn = V.invth * V.dv[v] * (V.b[v] - apply_st(V, S, V.xb));
             V.d[v] = dn;
             V.xa[v] = V.xb[v] + dn;
         })
         __syncthreads();
         TL_FOR(V, {
             const Stencil S = stencil(V, i, j, ip, im);
-            const float dn = V.c1 * V.d[v] + V.c2 * V.dv[v] * (V.b[v] - apply_st(V, S, V.xa, gA));
+            const float dn = V.c1 * V.d[v] + V.c2 * V.dv[v] * (V.b[v] - apply_st(V, S, V.xa));
             V.d[v] = dn;
             V.xb[v] = V.xa[v] + dn;
         })

@@ -142,6 +142,7 @@ struct CondCache {
     float *Sell32 = nullptr, *Dinv32 = nullptr, *Minv32 = nullptr;
     std::vector<float *> A32, dinv32;
     size_t tail32_smem = 0;
+    float *tail_img = nullptr;                // the tail's shared-memory image (dinv, stencils)
     int first32 = 0;                          // P1 levels >= first32 run in the one-block tail
 };
 
@@ -1003,6 +1004,19 @@ struct Impl {
                 w.d = c->alloc<float>(nv); w.t = c->alloc<float>(nv);
                 c->mgw32.push_back(w);
             }
+        {   // the tail's shared-memory image: dinv and the stencil of each level at their offsets
+            E.tail_img = c->alloc<float>(smem / sizeof(float));
+            CK(cudaMemsetAsync(E.tail_img, 0, smem, c->st));
+            size_t off = 0;
+            for (int l = first; l < L; ++l) {
+                const size_t nv = (size_t)E.lv[l].G.nverts;
+                CK(cudaMemcpyAsync(E.tail_img + off + 4 * nv, E.dinv32[l], nv * sizeof(float), cudaMemcpyDeviceToDevice,
+                                   c->st));
+                CK(cudaMemcpyAsync(E.tail_img + off + 5 * nv, E.A32[l], P1_NS * nv * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, c->st));
+                off += 12 * nv;
+            }
+        }
         E.first32 = first;
         CK(cudaFuncSetAttribute(k_tv_tail<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         E.tail32_smem = smem;
@@ -1021,11 +1035,13 @@ struct Impl {
             T.G[l] = V.G; T.A[l] = E.A32[f0 + l]; T.dinv[l] = E.dinv32[f0 + l];
             T.invth[l] = (float)V.invth; T.c1[l] = (float)V.c1; T.c2[l] = (float)V.c2;
             T.off[l] = off;
-            off += (l >= 1 ? 12 : 5) * V.G.nverts;
+            off += 12 * V.G.nverts;
         }
         T.Minv = E.Minv32;
         T.b1 = c->mgw32[f0].b;
         T.e1 = c->mgw32[f0].xb;
+        T.img = reinterpret_cast<const float4 *>(E.tail_img);
+        T.nimg4 = (int)(E.tail32_smem / sizeof(float4));
         return T;
     }
 
