@@ -1561,8 +1561,9 @@ __device__ void finish32_block(LoopCtl L, int limit, const float *pf, int nblock
             float a[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) a[u] = 0.f;
-            for (int b = t; b < nblocks; b += blockDim.x) {
-#pragma unroll
+#pragma unroll 4
+            for (int b = t; b < nblocks; b += blockDim.x) {     // (unrolled: the loads of several
+#pragma unroll                                                  // block rows in flight at once)
                 for (int u = 0; u < 8; ++u)
                     if (i0 + u < nvec) a[u] += __ldcg(&pf[(size_t)b * (GM_M + 2) + i0 + u]);
             }

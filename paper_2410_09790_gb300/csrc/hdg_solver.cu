@@ -2772,7 +2772,7 @@ double hdg_estimate_bytes(const hdg_mesh_desc *mesh, const hdg_params *params) {
     if (params->n_richardson <= 0 && params->stage_krylov) {
         b += 8 * (31 + 30 + 7) * N + 4 * 32 * N;                           // stage FGMRES
         if (params->precision == HDG_MIXED && params->relax_eta > 0)
-            b += 4 * nc * std::ceil(NU * 4 * std::ceil(NU / 4) / 32) * 32 + 4 * 8 * nc;   // FP32 blocks, geometry
+            b += 2 * 4 * nc * std::ceil(NU * 4 * std::ceil(NU / 4) / 32) * 32 + 4 * 8 * nc;   // FP32 blocks + rest, geometry
     }
     b += 8 * (8 * nQ + 3 * nP + 3 * nL + nc * NL + 10 * nL);               // temporaries, trace work
     b += ncond * 8 * (nc * (NL * NL + NP * NL + NP * NP) + 6 * NT * nL) + ncond * 4 * 5 * nf;
